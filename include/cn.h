@@ -1,0 +1,134 @@
+/*
+ * cn.h -- C ABI of the B300-native N-shaped partition Crank-Nicolson library
+ * (libcn_b300.so).
+ *
+ * Method: Lutsyshyn, Navarrete, Bauer, "The N-shaped partition method: A novel
+ * parallel implementation of the Crank Nicolson algorithm".
+ *
+ * One Crank-Nicolson step of the 1D TDSE  i d/dt psi = H(t) psi,
+ * H = -1/2 d^2/dx^2 + V(x, t) on the grid x_j = x_min + j dx (j = 0..n-1,
+ * psi = 0 outside, Sec. 4), is (Sec. 2, Eq. Cn_both_steps)
+ *     d = T^dagger psi(t)            (explicit forward half-step, Eq. ForwardStep)
+ *     T psi(t + dt) = d              (implicit backward half-step, Eq. BackwardStep)
+ *     T = 1 + i dt/2 H(t + dt/2)
+ * with the 3-point stencil: T_jj = 1 + i dt/2 (1/dx^2 + V_j),
+ * T_{j,j+-1} = -i dt / (4 dx^2).  The tridiagonal solve is the N-shaped
+ * partition method of Sec. 4 (Table 1: RD, JD, RU, JU, RS, SS), applied
+ * recursively to its reduced system as in Eq. (iteration).
+ *
+ * Conventions for every entry point:
+ *   - complex values are complex128: interleaved (re, im) IEEE doubles, 16 B
+ *     per element (the layout of torch.complex128 / numpy complex128),
+ *     contiguous, 16-byte aligned;
+ *   - "device pointer" means memory the caller allocated on the CUDA device
+ *     the plan was created on; the caller keeps ownership; the library never
+ *     frees it;
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream); device
+ *     work is enqueued on it and the call returns without synchronising,
+ *     except where stated;
+ *   - argument errors are detected on the host before any work is enqueued
+ *     and returned as a cn_status; nothing is enqueued then;
+ *   - errors raised on the device (non-finite pivots, exhausted waits) are
+ *     recorded in the plan's device status word and returned by
+ *     cn_plan_status();
+ *   - no function throws or aborts; a plan must not be used from two host
+ *     threads at once, and calls that share a plan must be ordered on one
+ *     stream (they share the plan's workspace).
+ */
+#ifndef CN_B300_H
+#define CN_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cn_plan_s* cn_plan;
+
+typedef enum {
+    CN_OK = 0,
+    CN_ERR_INVALID_ARG = 1,  /* bad size, pointer, alignment or descriptor field */
+    CN_ERR_UNSUPPORTED = 2,  /* valid request this build does not implement      */
+    CN_ERR_OOM = 3,          /* device workspace allocation failed               */
+    CN_ERR_CUDA = 4,         /* a CUDA runtime call failed                       */
+    CN_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out               */
+    CN_ERR_NONFINITE = 6     /* a pivot or result was zero / inf / NaN           */
+} cn_status;
+
+/* Static part Vs(x) of V(x, t) = Vs(x) + x E(t) (length-gauge field term). */
+typedef enum {
+    CN_POT_NONE = 0,         /* Vs = 0                                                     */
+    CN_POT_ARRAY = 1,        /* Vs(x_j) = V0[j], V0 a device array of n doubles              */
+    CN_POT_SOFTCOULOMB = 2,  /* Vs(x) = -1 / sqrt(x^2 + soft_s), regenerated on the fly      */
+    CN_POT_COSSERIES = 3     /* Vs(x) = sum_{k=1..n_cos} cos_a[k-1] cos(2 pi k x / L)        */
+} cn_pot_kind;
+
+/* Arithmetic the solver runs in.  Inputs and outputs are complex128 in both. */
+typedef enum {
+    CN_ARITH_F64 = 0,        /* native IEEE binary64                                       */
+    CN_ARITH_DF64 = 1        /* double-float: value = hi + lo, two binary32 words (~48-bit
+                                significand; Dekker 1971, Joldes-Muller-Popescu 2017)        */
+} cn_arith;
+
+typedef struct {
+    int64_t n;               /* grid points (unknowns), n >= 3                              */
+    double dx, dt, x_min;    /* grid spacing, time step, first grid point                   */
+    int32_t pot;             /* cn_pot_kind                                                  */
+    int32_t n_cos;           /* CN_POT_COSSERIES: number of terms, 0..16                     */
+    const double* V0;        /* CN_POT_ARRAY: device pointer, n doubles, read at every step  */
+    double soft_s;           /* CN_POT_SOFTCOULOMB: softening s > 0                          */
+    const double* cos_a;     /* CN_POT_COSSERIES: HOST pointer, n_cos doubles (copied)       */
+    double L;                /* CN_POT_COSSERIES: period length                              */
+    int32_t block;           /* rows per level-0 block (one GPU thread each), 0 = default   */
+    int32_t arith;           /* cn_arith                                                     */
+} cn_desc;
+
+/* Create a plan for systems of size desc->n.  Allocates the device workspace
+ * (reduced systems of every nesting level, one state buffer of n complex128,
+ * a status word) on the current device.  On success *out owns it. */
+cn_status cn_plan_create(const cn_desc* desc, cn_plan* out);
+
+/* Free the plan and its workspace (synchronises the device first).  NULL is a no-op. */
+cn_status cn_plan_destroy(cn_plan plan);
+
+/* nsteps Crank-Nicolson steps (Sec. 2) starting from psi_in (device,
+ * complex128[n]); the result is written to psi_out (device, complex128[n]).
+ * E_mid: device array of nsteps doubles, E_mid[k] = E(t0 + (k + 1/2) dt), the
+ * field at the midpoint of step k (Sec. 2: T is built at t + dt/2); NULL
+ * means E = 0.  psi_in may equal psi_out; psi_in is otherwise not modified.
+ * nsteps = 0 copies psi_in to psi_out. */
+cn_status cn_step(cn_plan plan, const void* psi_in, void* psi_out, const double* E_mid,
+                  int64_t nsteps, void* stream);
+
+/* As cn_step, with psi_in, psi_out and E_mid in HOST memory (pageable or
+ * pinned).  The host-to-device copies, the steps and the device-to-host copy
+ * are enqueued on `stream`; the call synchronises the stream before it
+ * returns, so psi_out is valid on return. */
+cn_status cn_step_host(cn_plan plan, const void* psi_in_host, void* psi_out_host,
+                       const double* E_mid_host, int64_t nsteps, void* stream);
+
+/* Solve the general complex tridiagonal system T x = d (Sec. 4, Eq. algorithm)
+ * by the N-shaped partition method: b = lower diagonal (b[j] = T[j][j-1],
+ * b[0] ignored), a = diagonal, c = upper diagonal (c[j] = T[j][j+1], c[n-1]
+ * ignored), d = right-hand side; all device complex128[n]; x = device
+ * complex128[n] output (may alias d; must not alias b, a or c).  n must equal
+ * the plan's n.  No pivoting: T must admit an unpivoted LU factorisation of
+ * every block (true for the CN matrices and for diagonally dominant T). */
+cn_status cn_solve_tridiag(cn_plan plan, const void* b, const void* a, const void* c,
+                           const void* d, void* x, int64_t n, void* stream);
+
+/* Wait for the plan's stream work to finish (device synchronise) and return
+ * the first device-side error recorded since the last call (then clear it). */
+cn_status cn_plan_status(cn_plan plan);
+
+/* Static description of a status code. */
+const char* cn_status_string(cn_status s);
+
+/* Library build information: "<version> sm_<arch>". */
+const char* cn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

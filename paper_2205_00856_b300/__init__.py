@@ -1,0 +1,202 @@
+"""Python binding of libcn_b300.so: the B300-native N-shaped partition
+Crank-Nicolson library (C ABI in include/cn.h).
+
+Argument marshalling only: every step of the computation runs in the library's
+CUDA kernels.  Tensors must be contiguous CUDA tensors (complex128 states,
+float64 fields) on the plan's device.  There is no CPU fallback: if the shared
+library cannot be loaded, every call raises.
+
+Paper: Lutsyshyn, Navarrete, Bauer, "The N-shaped partition method: A novel
+parallel implementation of the Crank Nicolson algorithm" (Sec. 2: the CN step;
+Sec. 4: the N-shaped partition solve; Eq. iteration: its nesting).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+POT_NONE, POT_ARRAY, POT_SOFTCOULOMB, POT_COSSERIES = 0, 1, 2, 3
+ARITH_F64, ARITH_DF64 = 0, 1
+
+_STATUS = {0: "CN_OK", 1: "CN_ERR_INVALID_ARG", 2: "CN_ERR_UNSUPPORTED", 3: "CN_ERR_OOM", 4: "CN_ERR_CUDA",
+           5: "CN_ERR_TIMEOUT", 6: "CN_ERR_NONFINITE"}
+
+# every symbol declared in include/cn.h
+EXPORTS = ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_solve_tridiag",
+           "cn_plan_status", "cn_status_string", "cn_version")
+
+
+class CNError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {_STATUS.get(code, code)}")
+
+
+class _Desc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("dx", C.c_double), ("dt", C.c_double), ("x_min", C.c_double),
+                ("pot", C.c_int32), ("n_cos", C.c_int32), ("V0", C.c_void_p), ("soft_s", C.c_double),
+                ("cos_a", C.c_void_p), ("L", C.c_double), ("block", C.c_int32), ("arith", C.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libcn_b300.so (building it in-tree first if allowed)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing and _build.needs_build():
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise OSError(f"libcn_b300.so not built ({_build.LIB})")
+            lib = C.CDLL(_build.LIB)
+            vp, i64 = C.c_void_p, C.c_int64
+            lib.cn_plan_create.argtypes = [C.POINTER(_Desc), C.POINTER(vp)]
+            lib.cn_plan_destroy.argtypes = [vp]
+            lib.cn_step.argtypes = [vp, vp, vp, vp, i64, vp]
+            lib.cn_step_host.argtypes = [vp, vp, vp, vp, i64, vp]
+            lib.cn_solve_tridiag.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
+            lib.cn_plan_status.argtypes = [vp]
+            lib.cn_status_string.argtypes = [C.c_int]
+            lib.cn_status_string.restype = C.c_char_p
+            lib.cn_version.argtypes = []
+            lib.cn_version.restype = C.c_char_p
+            for f in ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_solve_tridiag",
+                      "cn_plan_status"):
+                getattr(lib, f).restype = C.c_int
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise CNError(rc, what)
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype, n: int, name: str) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be contiguous with {n} elements")
+    return t.data_ptr()
+
+
+class Plan:
+    """A cn_plan: workspace for systems of n unknowns on the current CUDA device.
+
+    pot / V0 / soft_s / cos_a / L describe the static potential Vs(x) of
+    H = -1/2 d^2/dx^2 + Vs(x) + x E(t) on x_j = x_min + j dx.
+    """
+
+    def __init__(self, n, dx, dt, x_min, pot=POT_NONE, V0=None, soft_s=2.0, cos_a=None, L=1.0,
+                 block=0, arith=ARITH_F64):
+        import torch
+        self._lib = load()
+        self.n = int(n)
+        self.dt = float(dt)
+        self.arith = int(arith)
+        self._V0 = None
+        v0p = None
+        if pot == POT_ARRAY:
+            self._V0 = V0
+            v0p = _dev_ptr(V0, torch.float64, self.n, "V0")
+        self._cos = None if cos_a is None else np.ascontiguousarray(cos_a, dtype=np.float64)
+        d = _Desc(self.n, float(dx), float(dt), float(x_min), int(pot),
+                  0 if self._cos is None else len(self._cos), v0p, float(soft_s),
+                  None if self._cos is None else self._cos.ctypes.data, float(L), int(block), self.arith)
+        h = C.c_void_p()
+        _check(self._lib.cn_plan_create(C.byref(d), C.byref(h)), "cn_plan_create")
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.cn_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, psi_in, nsteps: int, E_mid=None, psi_out=None, stream=None):
+        """nsteps CN steps on device tensors; returns psi_out (allocated if None)."""
+        import torch
+        pin = _dev_ptr(psi_in, torch.complex128, self.n, "psi_in")
+        if psi_out is None:
+            psi_out = torch.empty_like(psi_in)
+        pout = _dev_ptr(psi_out, torch.complex128, self.n, "psi_out")
+        pe = None
+        if E_mid is not None:
+            if E_mid.numel() < nsteps:
+                raise ValueError("E_mid shorter than nsteps")
+            pe = _dev_ptr(E_mid, torch.float64, E_mid.numel(), "E_mid")
+        _check(self._lib.cn_step(self._h, pin, pout, pe, int(nsteps), _stream_handle(stream)), "cn_step")
+        return psi_out
+
+    def step_host(self, psi_in, nsteps: int, E_mid=None, psi_out=None, stream=None):
+        """nsteps CN steps on host arrays (numpy or CPU tensors, pinned or not)."""
+        pin = np.ascontiguousarray(psi_in, dtype=np.complex128) if not hasattr(psi_in, "data_ptr") else psi_in
+        if psi_out is None:
+            psi_out = np.empty(self.n, np.complex128)
+
+        def hptr(a, dt, name, n):
+            if hasattr(a, "data_ptr"):
+                if a.is_cuda or not a.is_contiguous() or a.numel() < n:
+                    raise ValueError(f"{name} must be a contiguous host tensor")
+                return a.data_ptr()
+            if a.dtype != dt or not a.flags.c_contiguous or a.size < n:
+                raise ValueError(f"{name} must be contiguous {dt}")
+            return a.ctypes.data
+
+        E = None
+        if E_mid is not None:
+            E = E_mid if hasattr(E_mid, "data_ptr") else np.ascontiguousarray(E_mid, dtype=np.float64)
+        _check(self._lib.cn_step_host(self._h, hptr(pin, np.complex128, "psi_in", self.n),
+                                      hptr(psi_out, np.complex128, "psi_out", self.n),
+                                      None if E is None else hptr(E, np.float64, "E_mid", nsteps),
+                                      int(nsteps), _stream_handle(stream)), "cn_step_host")
+        return psi_out
+
+    def solve_tridiag(self, b, a, c, d, x=None, stream=None):
+        """Solve T x = d (b lower, a diagonal, c upper; complex128 device tensors)."""
+        import torch
+        ptrs = [_dev_ptr(v, torch.complex128, self.n, nm) for v, nm in ((b, "b"), (a, "a"), (c, "c"), (d, "d"))]
+        if x is None:
+            x = torch.empty_like(d)
+        px = _dev_ptr(x, torch.complex128, self.n, "x")
+        _check(self._lib.cn_solve_tridiag(self._h, *ptrs, px, self.n, _stream_handle(stream)), "cn_solve_tridiag")
+        return x
+
+    def status(self) -> int:
+        """Synchronise and return (then clear) the device-side status code."""
+        return int(self._lib.cn_plan_status(self._h))
+
+    def check(self) -> None:
+        _check(self.status(), "device status")
+
+
+def version() -> str:
+    return load().cn_version().decode()

@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads and exports every symbol include/cn.h declares;
+host-side argument checks work without a GPU (no compute calls here)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2205_00856_b300 as cnb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "cn.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(cn_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = cnb.load()
+    out = subprocess.run(["nm", "-D", "--defined-only", cnb.library_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    decl = declared_symbols()
+    assert decl, "no declarations parsed"
+    missing = [s for s in decl if s not in exported]
+    assert not missing, missing
+    for s in decl:
+        assert hasattr(lib, s)
+    assert set(cnb.EXPORTS) == set(decl)
+
+
+def test_status_strings_and_version():
+    lib = cnb.load()
+    assert lib.cn_status_string(0) == b"ok"
+    assert lib.cn_status_string(5) == b"device-side wait timed out"
+    assert cnb.version().endswith("sm_103a")
+
+
+def _desc(**kw):
+    d = dict(n=100, dx=0.1, dt=0.01, x_min=0.0, pot=0, n_cos=0, V0=None, soft_s=2.0, cos_a=None, L=1.0,
+             block=0, arith=0)
+    d.update(kw)
+    return cnb._Desc(*[d[f] for f, _ in cnb._Desc._fields_])
+
+
+@pytest.mark.parametrize("kw", [dict(n=2), dict(n=-5), dict(dx=0.0), dict(dx=float("nan")), dict(dt=0.0),
+                                dict(pot=9), dict(pot=1), dict(pot=2, soft_s=0.0), dict(pot=3, n_cos=17, L=1.0),
+                                dict(pot=3, n_cos=2, L=1.0), dict(block=5), dict(block=32), dict(arith=3)])
+def test_invalid_descriptor_rejected_on_host(kw):
+    lib = cnb.load()
+    h = C.c_void_p()
+    rc = lib.cn_plan_create(C.byref(_desc(**kw)), C.byref(h))
+    assert rc == 1 and not h.value
+
+
+def test_null_arguments_rejected():
+    lib = cnb.load()
+    assert lib.cn_plan_create(None, None) == 1
+    assert lib.cn_step(None, None, None, None, 1, None) == 1
+    assert lib.cn_step_host(None, None, None, None, 1, None) == 1
+    assert lib.cn_solve_tridiag(None, None, None, None, None, None, 10, None) == 1
+    assert lib.cn_plan_status(None) == 1
+    assert lib.cn_plan_destroy(None) == 0

@@ -1,0 +1,151 @@
+"""GPU parity: the CUDA N-shaped path (through the C ABI) against the FP64 oracle.
+
+Tolerances:
+  - Crank-Nicolson propagation: relative L2 error <= 1e-11 after 100 steps
+    (the stated accuracy target for the FP64 path);
+  - single tridiagonal solves of random diagonally dominant systems: 1e-12
+    for native FP64 (kappa(T) <= ~10; FP64 rounding gives ~1e-15).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines too
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2205_00856_b300 as cnb  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def rel(x, y):
+    return float(np.linalg.norm(x - y) / np.linalg.norm(y))
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def plan_for(cfg, arith=cnb.ARITH_F64, block=0):
+    return cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cfg.get("pot", 0),
+                    soft_s=cfg.get("soft_s", 2.0), block=block, arith=arith)
+
+
+def oracle_problem(cfg):
+    return oracle.Problem(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cfg.get("pot", 0),
+                          soft_s=cfg.get("soft_s", 2.0))
+
+
+# ------------------------------------------------------------------ tridiagonal solve
+@pytest.mark.parametrize("n", [3, 4, 5, 9, 10, 17, 18, 100, 1000, 4097, 65539, 1 << 20])
+@pytest.mark.parametrize("block", [4, 8, 16])
+def test_solve_tridiag_random(n, block):
+    rng = np.random.default_rng(n * 31 + block)
+    b, a, c, d = W.random_system(n, rng)
+    x_ref = oracle.thomas(b, a, c, d)
+    plan = cnb.Plan(n, 0.1, 0.01, 0.0, block=block)
+    x = plan.solve_tridiag(*map(to_dev, (b, a, c, d))).cpu().numpy()
+    plan.check()
+    assert rel(x, x_ref) <= 1e-12
+
+
+def test_solve_tridiag_in_place_rhs():
+    n = 5000
+    b, a, c, d = W.random_system(n, np.random.default_rng(2))
+    plan = cnb.Plan(n, 0.1, 0.01, 0.0)
+    tb, ta, tc, td = map(to_dev, (b, a, c, d))
+    plan.solve_tridiag(tb, ta, tc, td, x=td)
+    assert rel(td.cpu().numpy(), oracle.thomas(b, a, c, d)) <= 1e-12
+
+
+def test_solve_tridiag_deterministic():
+    n = 300001
+    b, a, c, d = W.random_system(n, np.random.default_rng(3))
+    plan = cnb.Plan(n, 0.1, 0.01, 0.0)
+    args = list(map(to_dev, (b, a, c, d)))
+    x1 = plan.solve_tridiag(*args).cpu().numpy()
+    x2 = plan.solve_tridiag(*args).cpu().numpy()
+    assert np.array_equal(x1, x2)
+
+
+def test_singular_pivot_flagged():
+    n = 64
+    b = np.zeros(n, np.complex128)
+    c = np.zeros(n, np.complex128)
+    a = np.ones(n, np.complex128)
+    a[37] = 0.0
+    d = np.ones(n, np.complex128)
+    plan = cnb.Plan(n, 0.1, 0.01, 0.0)
+    plan.solve_tridiag(*map(to_dev, (b, a, c, d)))
+    assert plan.status() == 6  # CN_ERR_NONFINITE
+    assert plan.status() == 0  # cleared
+
+
+# ------------------------------------------------------------------ CN step
+def test_free_packet_n4096_100_steps():
+    cfg = W.free_packet_config()
+    psi0 = W.initial_state(cfg)
+    ref = oracle.cn_run(oracle_problem(cfg), psi0, cfg["nsteps"])
+    plan = plan_for(cfg)
+    out = plan.step(to_dev(psi0), cfg["nsteps"]).cpu().numpy()
+    plan.check()
+    assert rel(out, ref) <= 1e-11
+
+
+@pytest.mark.parametrize("n", [3, 5, 64, 4097, 1 << 16])
+@pytest.mark.parametrize("block", [4, 8, 16])
+def test_soft_coulomb_field_100_steps(n, block):
+    cfg = W.soft_coulomb_config(n=n, nsteps=100)
+    psi0 = W.initial_state(cfg) if n >= 64 else (np.arange(n) + 1j).astype(np.complex128)
+    E = W.field_midpoints(100, cfg["dt"], t0=150.0)
+    ref = oracle.cn_run(oracle_problem(cfg), psi0, 100, E_mid=E)
+    plan = plan_for(cfg, block=block)
+    out = plan.step(to_dev(psi0), 100, E_mid=to_dev(E)).cpu().numpy()
+    plan.check()
+    assert rel(out, ref) <= 1e-11
+
+
+def test_step_in_place_and_zero_steps():
+    cfg = W.soft_coulomb_config(n=1000, nsteps=7)
+    psi0 = W.initial_state(cfg)
+    E = W.field_midpoints(7, cfg["dt"], t0=10.0)
+    ref = oracle.cn_run(oracle_problem(cfg), psi0, 7, E_mid=E)
+    plan = plan_for(cfg)
+    for k in (7, 6):  # odd and even step counts through the in-place path
+        t = to_dev(psi0)
+        plan.step(t, k, E_mid=to_dev(E), psi_out=t)
+        r = ref if k == 7 else oracle.cn_run(oracle_problem(cfg), psi0, 6, E_mid=E)
+        assert rel(t.cpu().numpy(), r) <= 1e-12
+    t = to_dev(psi0)
+    out = plan.step(t, 0)
+    assert np.array_equal(out.cpu().numpy(), psi0)
+
+
+def test_step_host_matches_device():
+    cfg = W.soft_coulomb_config(n=50000, nsteps=5)
+    psi0 = W.initial_state(cfg)
+    E = W.field_midpoints(5, cfg["dt"], t0=50.0)
+    plan = plan_for(cfg)
+    dev = plan.step(to_dev(psi0), 5, E_mid=to_dev(E)).cpu().numpy()
+    host = plan.step_host(psi0, 5, E_mid=E)
+    assert np.array_equal(dev, host)
+
+
+def test_full_size_soft_coulomb_2pow24():
+    # the benchmarked configuration, in the launch configuration bench.py times
+    cfg = W.soft_coulomb_config()
+    nsteps = 3
+    psi0 = W.initial_state(cfg)
+    E = W.field_midpoints(nsteps, cfg["dt"], t0=200.0)
+    plan = plan_for(cfg)
+    out = plan.step(to_dev(psi0), nsteps, E_mid=to_dev(E)).cpu().numpy()
+    plan.check()
+    ref = oracle.cn_run(oracle_problem(cfg), psi0, nsteps, E_mid=E)
+    assert rel(out, ref) <= 1e-12
+    # unitarity of the Cayley form at full size
+    assert abs(np.sum(np.abs(out) ** 2) / np.sum(np.abs(psi0) ** 2) - 1) <= 1e-12
