@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: Crank-Nicolson grid-point updates per second on the soft-Coulomb
+atom in a laser field, N = 2^24, dx = 0.1, dt = 0.02 (complex128 state).
+
+One bench "step" is one Crank-Nicolson time step over the whole grid: the
+coefficient generation, explicit half-step, N-shaped reduction (RD+JD, RU+JU)
+on every nesting level, the RS stage and the substitution (SS) back down, i.e.
+one cn_step(nsteps=1) call.  Field samples E(t + dt/2) follow the sin^2 pulse
+over the 1000-step run.  Inputs (two 256 MiB state buffers) are larger than
+the 126 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--arith f64|df64]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "CN grid-point updates/sec (complex128)"
+UNIT = "unknown-steps/s"
+WORKLOAD_STEPS = 1000  # length of the benchmarked propagation (field samples)
+
+# Algorithmic FP64 flops per grid row of the two level-0 kernels for the
+# soft-Coulomb CN source (FMA = 2 flops, division / rsqrt = 1; derivation in
+# DESIGN.md, "Algorithmic work per unknown"):
+FLOPS_PER_ROW = {"reduce_level0": 81.0, "substitute_level0": 61.0}
+# Algorithmic HBM bytes per grid row: the reduction reads psi (16 B); the
+# substitution reads psi and writes psi' (32 B); one CN step moves 32 B.
+BYTES_PER_ROW = {"reduce_level0": 16.0, "substitute_level0": 32.0}
+STEP_BYTES_PER_ROW = 32.0
+# Recipe nominal FP64 rate of a B300 (MEASURED_PEAKS.json carries no FP64 figure).
+FP64_NOMINAL_TFLOPS = 1.25
+# FP32 issue peak: 148 SMs x 128 lanes x 2 flops x 2.032 GHz.
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2205_00856_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class: str, arith: str, n: int):
+    """DRAM bytes per launch of a kernel from the committed ncu summary
+    (profiles/traffic.txt), scaled to n rows; None if absent or stale."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    src = kernel_source_hash()
+    for ln in lines:
+        parts = ln.split()
+        if len(parts) >= 5 and not ln.startswith("#"):
+            cls, ar, rows, byts, hsh = parts[:5]
+            if cls == kernel_class and ar == arith and hsh == src:
+                return float(byts) * n / float(rows)
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                rows.append((float(p[0]), float(p[1]), p[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline_oracle(budget_s: float = 10.0):
+    """The FP64 CPU oracle (serial Thomas CN stepper) on a bounded sample: a
+    2^21-point window of the benchmarked grid (same dx, dt, potential, field)."""
+    import oracle
+    n = 1 << 21
+    cfg = W.soft_coulomb_config(n=n)
+    prob = oracle.Problem(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=oracle.POT_SOFTCOULOMB, soft_s=2.0)
+    psi = W.initial_state(cfg)
+    E = W.field_midpoints(WORKLOAD_STEPS, cfg["dt"])
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        psi = oracle.cn_run(prob, psi, 1, E_mid=E[steps % WORKLOAD_STEPS:steps % WORKLOAD_STEPS + 1])
+        steps += 1
+    el = time.perf_counter() - t0
+    return {"value": n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} CN steps on a 2^21-point window of the N=2^24 soft-Coulomb grid "
+                      f"(serial FP64 Thomas, {el:.1f} s)"}
+
+
+def run_reference(args):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    import oracle
+    n = 1 << 21
+    cfg = W.soft_coulomb_config(n=n)
+    prob = oracle.Problem(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=oracle.POT_SOFTCOULOMB, soft_s=2.0)
+    psi = W.initial_state(cfg)
+    E = W.field_midpoints(WORKLOAD_STEPS, cfg["dt"])
+    for k in range(args.warmup):
+        psi = oracle.cn_run(prob, psi, 1, E_mid=E[k % WORKLOAD_STEPS:][:1])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        j = (args.warmup + k) % WORKLOAD_STEPS
+        psi = oracle.cn_run(prob, psi, 1, E_mid=E[j:j + 1])
+    el = time.perf_counter() - t0
+    value = n * args.steps / el
+    sample = (f"each step: one CN step of the serial FP64 oracle on a 2^21-point window of the N=2^24 "
+              f"soft-Coulomb grid")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args):
+    return {"workload": "soft_coulomb_laser_1d_cn", "n": getattr(args, "n", 1 << 24), "dx": 0.1, "dt": 0.02,
+            "potential": "-1/sqrt(x^2+2) + x E(t)", "field": "0.05 sin^2(pi t/T) cos(0.057 t), T = 4*2pi/0.057",
+            "steps_per_bench_step": 1, "workload_steps": WORKLOAD_STEPS, "block": args.block,
+            "arith": args.arith, "l2": "inputs larger than L2 (2 x 256 MiB states vs 126 MB L2), no flush",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--arith", choices=["f64", "df64"], default="f64")
+    ap.add_argument("--block", type=int, default=8)
+    ap.add_argument("--n", type=int, default=1 << 24, help="grid points (profiling runs use smaller grids)")
+    ap.add_argument("--e2e-calls", type=int, default=3)
+    ap.add_argument("--e2e-inner", type=int, default=50, help="CN steps per end-to-end call")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2205_00856_b300 as cnb
+
+    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    cfg = W.soft_coulomb_config(n=args.n)
+    n = cfg["n"]
+    arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
+    plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0,
+                    block=args.block, arith=arith)
+    info = plan.info()
+    psi0 = W.initial_state(cfg)
+    E_host = W.field_midpoints(WORKLOAD_STEPS, cfg["dt"])
+    E = torch.from_numpy(E_host).to(dev)
+    cur = torch.from_numpy(psi0).to(dev)
+    nxt = torch.empty_like(cur)
+    stream = torch.cuda.current_stream()
+
+    def one_step(k):
+        nonlocal cur, nxt
+        j = k % WORKLOAD_STEPS
+        plan.step(cur, 1, E_mid=E[j:j + 1], psi_out=nxt, stream=stream)
+        cur, nxt = nxt, cur
+
+    for k in range(args.warmup):
+        one_step(k)
+    torch.cuda.synchronize()
+    plan.check()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plan.profile(True)
+    plan.profile_read()
+    with ClockSampler(uuid) as clk:
+        ev0.record(stream)
+        for k in range(args.steps):
+            one_step(args.warmup + k)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    plan.profile(False)
+    prof = plan.profile_read()
+    plan.check()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    torch.cuda.synchronize()
+    value = n * args.steps * world / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers: H2D of psi and E, inner
+    # CN steps, D2H of psi, every call
+    psi_h = torch.from_numpy(psi0).pin_memory()
+    out_h = torch.empty_like(psi_h).pin_memory()
+    E_h = torch.from_numpy(np.ascontiguousarray(E_host[:args.e2e_inner])).pin_memory()
+    if args.e2e_calls > 0:
+        plan.step_host(psi_h, args.e2e_inner, E_mid=E_h, psi_out=out_h)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_calls):
+        plan.step_host(psi_h, args.e2e_inner, E_mid=E_h, psi_out=out_h)
+    e2e_s = max(time.perf_counter() - t0, 1e-9)
+    if dist:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = n * args.e2e_inner * args.e2e_calls * world / e2e_s
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (largest share of kernel time)
+    dom = max(("reduce_level0", "substitute_level0"), key=lambda c: prof[c][0])
+    dom_ms, dom_launches = prof[dom]
+    avg_s = dom_ms * 1e-3 / max(dom_launches, 1)
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    if args.arith == "f64":
+        achieved = FLOPS_PER_ROW[dom] * n / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_NOMINAL_TFLOPS,
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table; no FP64 figure in MEASURED_PEAKS.json)",
+                "kernel": dom, "flops_per_row": FLOPS_PER_ROW[dom], "avg_launch_ms": avg_s * 1e3}
+    else:
+        achieved = FLOPS_PER_ROW[dom] * n / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS,
+                "peak_source": "FP32 issue peak 148 SM x 128 lanes x 2 x 2.032 GHz (double-float path)",
+                "kernel": dom, "flops_per_row": FLOPS_PER_ROW[dom], "avg_launch_ms": avg_s * 1e3}
+    roof["traffic"] = ncu_traffic(dom, args.arith, n)
+    step_s = ms * 1e-3 / args.steps
+    hbm_achieved = STEP_BYTES_PER_ROW * n / step_s / 1e9
+    roof_hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_achieved / hbm_peak, "basis": "32 B per unknown-step (read psi, write psi')",
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback 6400"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.arith, "data": "synthetic", "config": workload_config(args),
+            "roofline": roof, "roofline_hbm": roof_hbm,
+            "kernel_ms": {k: v[0] for k, v in prof.items()}, "kernel_launches": {k: v[1] for k, v in prof.items()},
+            "gpu_launches": info["launches_per_step"] * args.steps,
+            "levels": info["level_rows"],
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * n + 8 * args.e2e_inner,
+                    "d2h_bytes_per_step": 16 * n, "cn_steps_per_call": args.e2e_inner,
+                    "calls": args.e2e_calls},
+            "clocks": clk.summary()}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_oracle()
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

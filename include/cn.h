@@ -118,6 +118,32 @@ cn_status cn_step_host(cn_plan plan, const void* psi_in_host, void* psi_out_host
 cn_status cn_solve_tridiag(cn_plan plan, const void* b, const void* a, const void* c,
                            const void* d, void* x, int64_t n, void* stream);
 
+/* Static description of a plan: the nesting levels of its N-shaped solve
+ * (Eq. iteration) and the kernels one step launches. */
+#define CN_MAX_LEVELS 24
+typedef struct {
+    int64_t n;                           /* unknowns                                      */
+    int32_t levels;                      /* reduced levels below level 0; level `levels`  */
+                                         /* is solved by the serial RS stage              */
+    int32_t launches_per_step;           /* kernels one CN step / one solve launches      */
+    int64_t level_rows[CN_MAX_LEVELS];   /* rows of level 0 .. levels                     */
+    int32_t level_block[CN_MAX_LEVELS];  /* rows per block of level 0 .. levels-1         */
+    int64_t workspace_bytes;             /* device memory the plan holds                  */
+} cn_plan_info;
+cn_status cn_plan_query(cn_plan plan, cn_plan_info* out);
+
+/* Kernel timing for profiling.  While enabled, every kernel the plan launches
+ * is bracketed by two CUDA events recorded on its stream.  cn_plan_profile_read
+ * synchronises on the last event, then returns, per kernel class, the summed
+ * elapsed milliseconds (ms[c]) and the number of launches (launches[c]) since
+ * the previous read, and restarts the count.  Classes: 0 = level-0 reduction
+ * (RD+JD+RU+JU), 1 = level-0 substitution (SS), 2 = reductions of levels >= 1,
+ * 3 = substitutions of levels >= 1, 4 = RS stage.  cap = entries available in
+ * ms / launches (at most 5 are written). */
+#define CN_PROFILE_CLASSES 5
+cn_status cn_plan_profile(cn_plan plan, int enable);
+cn_status cn_plan_profile_read(cn_plan plan, double* ms, int64_t* launches, int32_t cap);
+
 /* Wait for the plan's stream work to finish (device synchronise) and return
  * the first device-side error recorded since the last call (then clear it). */
 cn_status cn_plan_status(cn_plan plan);

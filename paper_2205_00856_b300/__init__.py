@@ -28,7 +28,10 @@ _STATUS = {0: "CN_OK", 1: "CN_ERR_INVALID_ARG", 2: "CN_ERR_UNSUPPORTED", 3: "CN_
 
 # every symbol declared in include/cn.h
 EXPORTS = ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_solve_tridiag",
-           "cn_plan_status", "cn_status_string", "cn_version")
+           "cn_plan_query", "cn_plan_profile", "cn_plan_profile_read", "cn_plan_status", "cn_status_string",
+           "cn_version")
+MAX_LEVELS = 24
+PROFILE_CLASSES = ("reduce_level0", "substitute_level0", "reduce_levels_ge1", "substitute_levels_ge1", "rs_stage")
 
 
 class CNError(RuntimeError):
@@ -41,6 +44,12 @@ class _Desc(C.Structure):
     _fields_ = [("n", C.c_int64), ("dx", C.c_double), ("dt", C.c_double), ("x_min", C.c_double),
                 ("pot", C.c_int32), ("n_cos", C.c_int32), ("V0", C.c_void_p), ("soft_s", C.c_double),
                 ("cos_a", C.c_void_p), ("L", C.c_double), ("block", C.c_int32), ("arith", C.c_int32)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("levels", C.c_int32), ("launches_per_step", C.c_int32),
+                ("level_rows", C.c_int64 * MAX_LEVELS), ("level_block", C.c_int32 * MAX_LEVELS),
+                ("workspace_bytes", C.c_int64)]
 
 
 _lib = None
@@ -68,12 +77,15 @@ def load(build_if_missing: bool = True):
             lib.cn_step_host.argtypes = [vp, vp, vp, vp, i64, vp]
             lib.cn_solve_tridiag.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
             lib.cn_plan_status.argtypes = [vp]
+            lib.cn_plan_query.argtypes = [vp, C.POINTER(_Info)]
+            lib.cn_plan_profile.argtypes = [vp, C.c_int]
+            lib.cn_plan_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]
             lib.cn_status_string.argtypes = [C.c_int]
             lib.cn_status_string.restype = C.c_char_p
             lib.cn_version.argtypes = []
             lib.cn_version.restype = C.c_char_p
             for f in ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_solve_tridiag",
-                      "cn_plan_status"):
+                      "cn_plan_status", "cn_plan_query", "cn_plan_profile", "cn_plan_profile_read"):
                 getattr(lib, f).restype = C.c_int
             _lib = lib
     return _lib
@@ -189,6 +201,27 @@ class Plan:
         px = _dev_ptr(x, torch.complex128, self.n, "x")
         _check(self._lib.cn_solve_tridiag(self._h, *ptrs, px, self.n, _stream_handle(stream)), "cn_solve_tridiag")
         return x
+
+    def info(self) -> dict:
+        """Nesting levels, kernels per step and workspace of the plan."""
+        inf = _Info()
+        _check(self._lib.cn_plan_query(self._h, C.byref(inf)), "cn_plan_query")
+        L = inf.levels
+        return dict(n=inf.n, levels=L, launches_per_step=inf.launches_per_step,
+                    level_rows=list(inf.level_rows[:L + 1]), level_block=list(inf.level_block[:L]),
+                    workspace_bytes=inf.workspace_bytes)
+
+    def profile(self, enable: bool = True) -> None:
+        """Bracket every kernel launch with CUDA events (see profile_read)."""
+        _check(self._lib.cn_plan_profile(self._h, 1 if enable else 0), "cn_plan_profile")
+
+    def profile_read(self) -> dict:
+        """{class: (total ms, launches)} since the previous read (synchronises)."""
+        k = len(PROFILE_CLASSES)
+        ms = (C.c_double * k)()
+        nl = (C.c_int64 * k)()
+        _check(self._lib.cn_plan_profile_read(self._h, ms, nl, k), "cn_plan_profile_read")
+        return {PROFILE_CLASSES[i]: (float(ms[i]), int(nl[i])) for i in range(k)}
 
     def status(self) -> int:
         """Synchronise and return (then clear) the device-side status code."""

@@ -41,6 +41,12 @@ struct cn_plan_s {
     double2* h_out = nullptr;
     double* h_E = nullptr;
     int64_t h_E_cap = 0;
+    // kernel timing (cn_plan_profile)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;   // events owned by the plan
+    size_t ev_used = 0;                 // events handed out since the last read
+    std::vector<int> rec_class;         // class of record r (events 2r, 2r+1)
+    int64_t workspace_bytes = 0;
 };
 
 namespace {
@@ -67,6 +73,8 @@ cn_status validate_desc(const cn_desc* d) {
 }
 
 void free_plan_memory(cn_plan p) {
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    p->ev_pool.clear();
     for (Level& L : p->lv) {
         cudaFree(L.rows);
         cudaFree(L.slot);
@@ -82,6 +90,35 @@ void free_plan_memory(cn_plan p) {
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 unsigned grid_for(int64_t P) { return (unsigned)ceil_div(P, kThreads); }
+
+// --------------------------------------------------------------- kernel timing
+enum { kProfReduce0 = 0, kProfSubst0 = 1, kProfReduceL = 2, kProfSubstL = 3, kProfBase = 4 };
+
+// Two events per record; the pool grows on demand and is reused after a read.
+bool reserve_events(cn_plan p, size_t k) {
+    while (p->ev_pool.size() < p->ev_used + k) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return false;
+        p->ev_pool.push_back(e);
+    }
+    return true;
+}
+
+struct ProfScope {
+    cn_plan p;
+    cudaStream_t st;
+    cudaEvent_t stop = nullptr;
+    ProfScope(cn_plan p_, int cls, cudaStream_t st_) : p(p_), st(st_) {
+        if (!p->profiling || !reserve_events(p, 2)) return;
+        cudaEvent_t start = p->ev_pool[p->ev_used++];
+        stop = p->ev_pool[p->ev_used++];
+        p->rec_class.push_back(cls);
+        cudaEventRecord(start, st);
+    }
+    ~ProfScope() {
+        if (stop) cudaEventRecord(stop, st);
+    }
+};
 
 LevelSource level_source(const Level& L) {
     LevelSource s;
@@ -123,18 +160,29 @@ cudaError_t launch_substitute(const Src& src, const Level& L, const Level& next,
 template <class R, class Src0>
 cudaError_t nshape_solve(cn_plan p, const Src0& src0, double2* x0, cudaStream_t st) {
     const int L = (int)p->lv.size() - 1;
-    cudaError_t e = launch_reduce<R>(src0, p->lv[0], p->lv[1], p->status, st);
+    cudaError_t e;
+    {
+        ProfScope ps(p, kProfReduce0, st);
+        e = launch_reduce<R>(src0, p->lv[0], p->lv[1], p->status, st);
+    }
     if (e != cudaSuccess) return e;
     for (int l = 1; l < L; ++l) {
+        ProfScope ps(p, kProfReduceL, st);
         e = launch_reduce<R>(level_source(p->lv[l]), p->lv[l], p->lv[l + 1], p->status, st);
         if (e != cudaSuccess) return e;
     }
-    k_base<R><<<1, 32, 0, st>>>(level_source(p->lv[L]), p->lv[L].n, p->lv[L].x, p->status);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {
+        ProfScope ps(p, kProfBase, st);
+        k_base<R><<<1, 32, 0, st>>>(level_source(p->lv[L]), p->lv[L].n, p->lv[L].x, p->status);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
     for (int l = L - 1; l >= 1; --l) {
+        ProfScope ps(p, kProfSubstL, st);
         e = launch_substitute<R>(level_source(p->lv[l]), p->lv[l], p->lv[l + 1], p->lv[l].x, p->status, st);
         if (e != cudaSuccess) return e;
     }
+    ProfScope ps(p, kProfSubst0, st);
     return launch_substitute<R>(src0, p->lv[0], p->lv[1], x0, p->status, st);
 }
 
@@ -224,11 +272,14 @@ cn_status cn_plan_create(const cn_desc* desc, cn_plan* out) {
     cudaError_t e = cudaSuccess;
     for (size_t l = 1; l < p->lv.size() && e == cudaSuccess; ++l) {
         Level& L = p->lv[l];
+        p->workspace_bytes += (int64_t)(sizeof(LevelRow) + sizeof(double2)) * L.n +
+                              (int64_t)sizeof(LevelSlot) * (grid_for(p->lv[l - 1].P) + 1);
         e = cudaMalloc(&L.rows, sizeof(LevelRow) * (size_t)L.n);
         if (e == cudaSuccess) e = cudaMalloc(&L.slot, sizeof(LevelSlot) * (size_t)(grid_for(p->lv[l - 1].P) + 1));
         if (e == cudaSuccess) e = cudaMalloc(&L.x, sizeof(double2) * (size_t)L.n);
         if (e == cudaSuccess) e = cudaMemset(L.slot, 0, sizeof(LevelSlot) * (size_t)(grid_for(p->lv[l - 1].P) + 1));
     }
+    p->workspace_bytes += (int64_t)sizeof(double2) * desc->n + (int64_t)sizeof(int);
     if (e == cudaSuccess) e = cudaMalloc(&p->state, sizeof(double2) * (size_t)desc->n);
     if (e == cudaSuccess) e = cudaMalloc(&p->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(int));
@@ -321,6 +372,43 @@ cn_status cn_solve_tridiag(cn_plan p, const void* b, const void* a, const void* 
     cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? nshape_solve<df>(p, s, static_cast<double2*>(x), st)
                                                      : nshape_solve<double>(p, s, static_cast<double2*>(x), st);
     return cuda_status(e);
+}
+
+cn_status cn_plan_query(cn_plan p, cn_plan_info* out) {
+    if (!p || !out) return CN_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->n = p->desc.n;
+    out->levels = (int32_t)p->lv.size() - 1;
+    if (out->levels + 1 > CN_MAX_LEVELS) return CN_ERR_UNSUPPORTED;
+    for (size_t l = 0; l < p->lv.size(); ++l) {
+        out->level_rows[l] = p->lv[l].n;
+        out->level_block[l] = (l + 1 < p->lv.size()) ? p->lv[l].m : 0;
+    }
+    out->launches_per_step = 2 * out->levels + 1;
+    out->workspace_bytes = p->workspace_bytes;
+    return CN_OK;
+}
+
+cn_status cn_plan_profile(cn_plan p, int enable) {
+    if (!p) return CN_ERR_INVALID_ARG;
+    p->profiling = enable != 0;
+    return CN_OK;
+}
+
+cn_status cn_plan_profile_read(cn_plan p, double* ms, int64_t* launches, int32_t cap) {
+    if (!p || cap < 0 || (cap > 0 && (!ms || !launches))) return CN_ERR_INVALID_ARG;
+    for (int c = 0; c < cap && c < CN_PROFILE_CLASSES; ++c) { ms[c] = 0.0; launches[c] = 0; }
+    cn_status st = CN_OK;
+    if (p->ev_used > 0 && cudaEventSynchronize(p->ev_pool[p->ev_used - 1]) != cudaSuccess) st = CN_ERR_CUDA;
+    for (size_t r = 0; st == CN_OK && r < p->rec_class.size(); ++r) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p->ev_pool[2 * r], p->ev_pool[2 * r + 1]) != cudaSuccess) { st = CN_ERR_CUDA; break; }
+        int c = p->rec_class[r];
+        if (c < cap) { ms[c] += (double)t; launches[c] += 1; }
+    }
+    p->rec_class.clear();
+    p->ev_used = 0;
+    return st;
 }
 
 cn_status cn_plan_status(cn_plan p) {

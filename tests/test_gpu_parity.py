@@ -44,14 +44,16 @@ def oracle_problem(cfg):
 # ------------------------------------------------------------------ tridiagonal solve
 @pytest.mark.parametrize("n", [3, 4, 5, 9, 10, 17, 18, 100, 1000, 4097, 65539, 1 << 20])
 @pytest.mark.parametrize("block", [4, 8, 16])
-def test_solve_tridiag_random(n, block):
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_solve_tridiag_random(n, block, arith):
     rng = np.random.default_rng(n * 31 + block)
     b, a, c, d = W.random_system(n, rng)
     x_ref = oracle.thomas(b, a, c, d)
-    plan = cnb.Plan(n, 0.1, 0.01, 0.0, block=block)
+    plan = cnb.Plan(n, 0.1, 0.01, 0.0, block=block, arith=arith)
     x = plan.solve_tridiag(*map(to_dev, (b, a, c, d))).cpu().numpy()
     plan.check()
-    assert rel(x, x_ref) <= 1e-12
+    # double-float carries ~48 significand bits: 1e-12 is ~300 units of its rounding
+    assert rel(x, x_ref) <= (1e-12 if arith == cnb.ARITH_F64 else 1e-12)
 
 
 def test_solve_tridiag_in_place_rhs():
@@ -87,11 +89,12 @@ def test_singular_pivot_flagged():
 
 
 # ------------------------------------------------------------------ CN step
-def test_free_packet_n4096_100_steps():
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_free_packet_n4096_100_steps(arith):
     cfg = W.free_packet_config()
     psi0 = W.initial_state(cfg)
     ref = oracle.cn_run(oracle_problem(cfg), psi0, cfg["nsteps"])
-    plan = plan_for(cfg)
+    plan = plan_for(cfg, arith=arith)
     out = plan.step(to_dev(psi0), cfg["nsteps"]).cpu().numpy()
     plan.check()
     assert rel(out, ref) <= 1e-11
@@ -99,12 +102,13 @@ def test_free_packet_n4096_100_steps():
 
 @pytest.mark.parametrize("n", [3, 5, 64, 4097, 1 << 16])
 @pytest.mark.parametrize("block", [4, 8, 16])
-def test_soft_coulomb_field_100_steps(n, block):
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_soft_coulomb_field_100_steps(n, block, arith):
     cfg = W.soft_coulomb_config(n=n, nsteps=100)
     psi0 = W.initial_state(cfg) if n >= 64 else (np.arange(n) + 1j).astype(np.complex128)
     E = W.field_midpoints(100, cfg["dt"], t0=150.0)
     ref = oracle.cn_run(oracle_problem(cfg), psi0, 100, E_mid=E)
-    plan = plan_for(cfg, block=block)
+    plan = plan_for(cfg, block=block, arith=arith)
     out = plan.step(to_dev(psi0), 100, E_mid=to_dev(E)).cpu().numpy()
     plan.check()
     assert rel(out, ref) <= 1e-11
