@@ -41,7 +41,7 @@ WORKLOAD_STEPS = 1000  # length of the benchmarked propagation (field samples)
 # Algorithmic FP64 flops per grid row of the two level-0 kernels for the
 # soft-Coulomb CN source (FMA = 2 flops, division / rsqrt = 1; derivation in
 # DESIGN.md, "Algorithmic work per unknown"):
-FLOPS_PER_ROW = {"reduce_level0": 81.0, "substitute_level0": 61.0}
+FLOPS_PER_ROW = {"reduce_level0": 65.0, "substitute_level0": 45.0}
 # Algorithmic HBM bytes per grid row: the reduction reads psi (16 B); the
 # substitution reads psi and writes psi' (32 B); one CN step moves 32 B.
 BYTES_PER_ROW = {"reduce_level0": 16.0, "substitute_level0": 32.0}

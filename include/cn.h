@@ -80,9 +80,18 @@ typedef struct {
     double soft_s;           /* CN_POT_SOFTCOULOMB: softening s > 0                          */
     const double* cos_a;     /* CN_POT_COSSERIES: HOST pointer, n_cos doubles (copied)       */
     double L;                /* CN_POT_COSSERIES: period length                              */
-    int32_t block;           /* rows per level-0 block (one GPU thread each), 0 = default   */
+    int32_t block;           /* rows per level-0 block (one GPU thread each): 4, 8 or 16;
+                                0 = default (8)                                              */
     int32_t arith;           /* cn_arith                                                     */
+    int32_t flags;           /* CN_FLAG_* bits                                               */
+    int32_t reserved;        /* must be 0                                                    */
 } cn_desc;
+
+/* cn_desc.flags: tabulate the static part of the diagonal, 2 + 2 dx^2 Vs(x_j),
+ * once at plan creation (8 B per grid point of plan workspace, read by every
+ * level-0 sweep) instead of regenerating it from x_j at every step.  Implied
+ * for CN_POT_ARRAY and CN_POT_COSSERIES with CN_ARITH_DF64. */
+#define CN_FLAG_COEFF_TABLE 1
 
 /* Create a plan for systems of size desc->n.  Allocates the device workspace
  * (reduced systems of every nesting level, one state buffer of n complex128,

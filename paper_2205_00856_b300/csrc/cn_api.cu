@@ -18,12 +18,12 @@ namespace {
 constexpr int kLevelBlock = 8;  // rows per block on the reduced levels (>= 1)
 
 struct Level {
-    int64_t n = 0;            // rows
-    int64_t P = 0;            // blocks (joint lines 0..P)
-    int m = 0;                // block size
-    LevelRow* rows = nullptr; // rows of this level (levels >= 1)
-    LevelSlot* slot = nullptr;
-    double2* x = nullptr;     // solution of this level (levels >= 1)
+    int64_t n = 0;         // rows
+    int64_t P = 0;         // blocks (joint lines 0..P)
+    int m = 0;             // block size
+    void* rows = nullptr;  // LevelRow<R>[n] (levels >= 1)
+    void* slot = nullptr;  // LevelSlot<R>[CTAs of the level below + 1]
+    void* x = nullptr;     // Store<R>::T[n]: solution of this level (levels >= 1)
 };
 
 }  // namespace
@@ -31,9 +31,10 @@ struct Level {
 struct cn_plan_s {
     cn_desc desc;
     int device = 0;
-    std::vector<Level> lv;    // lv[0]: the system itself; lv[L]: solved by the RS stage
-    double2* state = nullptr; // n complex128 scratch for the step ping-pong
-    int* status = nullptr;    // device status word
+    std::vector<Level> lv;     // lv[0]: the system itself; lv[L]: solved by the RS stage
+    double2* state = nullptr;  // n complex128 scratch for the step ping-pong
+    void* tab = nullptr;       // bt0 table (compute type) or NULL
+    int* status = nullptr;     // device status word
     CNParams cnp;
     std::vector<double> cos_a;
     // cn_step_host staging (allocated on first use)
@@ -43,9 +44,9 @@ struct cn_plan_s {
     int64_t h_E_cap = 0;
     // kernel timing (cn_plan_profile)
     bool profiling = false;
-    std::vector<cudaEvent_t> ev_pool;   // events owned by the plan
-    size_t ev_used = 0;                 // events handed out since the last read
-    std::vector<int> rec_class;         // class of record r (events 2r, 2r+1)
+    std::vector<cudaEvent_t> ev_pool;  // events owned by the plan
+    size_t ev_used = 0;                // events handed out since the last read
+    std::vector<int> rec_class;        // class of record r (events 2r, 2r+1)
     int64_t workspace_bytes = 0;
 };
 
@@ -69,6 +70,7 @@ cn_status validate_desc(const cn_desc* d) {
     }
     if (d->block != 0 && d->block != 4 && d->block != 8 && d->block != 16) return CN_ERR_INVALID_ARG;
     if (d->arith != CN_ARITH_F64 && d->arith != CN_ARITH_DF64) return CN_ERR_INVALID_ARG;
+    if ((d->flags & ~CN_FLAG_COEFF_TABLE) != 0 || d->reserved != 0) return CN_ERR_INVALID_ARG;
     return CN_OK;
 }
 
@@ -81,6 +83,7 @@ void free_plan_memory(cn_plan p) {
         cudaFree(L.x);
     }
     cudaFree(p->state);
+    cudaFree(p->tab);
     cudaFree(p->status);
     cudaFree(p->h_in);
     cudaFree(p->h_out);
@@ -120,70 +123,101 @@ struct ProfScope {
     }
 };
 
-LevelSource level_source(const Level& L) {
-    LevelSource s;
-    s.rows = L.rows;
-    s.slot = L.slot;
+template <class R> LevelRow<R>* rows_of(const Level& L) { return static_cast<LevelRow<R>*>(L.rows); }
+template <class R> LevelSlot<R>* slot_of(const Level& L) { return static_cast<LevelSlot<R>*>(L.slot); }
+template <class R> typename Store<R>::T* x_of(const Level& L) { return static_cast<typename Store<R>::T*>(L.x); }
+
+template <class R> LevelSource<R> level_source(const Level& L) {
+    LevelSource<R> s;
+    s.rows = rows_of<R>(L);
+    s.slot = slot_of<R>(L);
     s.n = L.n;
     s.slot_stride = kThreads;
     return s;
 }
 
 // --------------------------------------------------------------- launch helpers
+#define CNB_DISPATCH_M(M_, CALL)                    \
+    switch (M_) {                                   \
+    case 4: { constexpr int M = 4; CALL; } break;   \
+    case 8: { constexpr int M = 8; CALL; } break;   \
+    case 16: { constexpr int M = 16; CALL; } break; \
+    default: return cudaErrorInvalidValue;          \
+    }
+
 template <class R, class Src>
 cudaError_t launch_reduce(const Src& src, const Level& L, const Level& next, int* status, cudaStream_t st) {
     const unsigned grid = grid_for(L.P);
-    switch (L.m) {
-    case 4: k_reduce<R, 4, Src><<<grid, kThreads, 0, st>>>(src, L.n, L.P, L.m, next.rows, next.slot, status); break;
-    case 8: k_reduce<R, 8, Src><<<grid, kThreads, 0, st>>>(src, L.n, L.P, L.m, next.rows, next.slot, status); break;
-    case 16: k_reduce<R, 16, Src><<<grid, kThreads, 0, st>>>(src, L.n, L.P, L.m, next.rows, next.slot, status); break;
-    default: return cudaErrorInvalidValue;
-    }
+    CNB_DISPATCH_M(L.m, (k_reduce<R, M, Src><<<grid, kThreads, 0, st>>>(src, L.n, L.P, L.m, rows_of<R>(next),
+                                                                        slot_of<R>(next), status)));
     return cudaGetLastError();
 }
 
-template <class R, class Src>
-cudaError_t launch_substitute(const Src& src, const Level& L, const Level& next, double2* x, int* status,
-                              cudaStream_t st) {
+template <class R, class Src, class XT>
+cudaError_t launch_substitute(const Src& src, const Level& L, const Level& next, XT* x, int* status, cudaStream_t st) {
     const unsigned grid = grid_for(L.P);
-    switch (L.m) {
-    case 4: k_substitute<R, 4, Src><<<grid, kThreads, 0, st>>>(src, L.n, L.P, L.m, next.x, x, status); break;
-    case 8: k_substitute<R, 8, Src><<<grid, kThreads, 0, st>>>(src, L.n, L.P, L.m, next.x, x, status); break;
-    case 16: k_substitute<R, 16, Src><<<grid, kThreads, 0, st>>>(src, L.n, L.P, L.m, next.x, x, status); break;
-    default: return cudaErrorInvalidValue;
-    }
+    CNB_DISPATCH_M(L.m, (k_substitute<R, M, Src, XT><<<grid, kThreads, 0, st>>>(src, L.n, L.P, L.m, x_of<R>(next), x,
+                                                                                status)));
     return cudaGetLastError();
 }
 
-// The nested N-shaped solve of one system whose level-0 rows come from src0;
-// the solution of level 0 is written to x0.
-template <class R, class Src0>
-cudaError_t nshape_solve(cn_plan p, const Src0& src0, double2* x0, cudaStream_t st) {
+// Levels 1..L of the nested solve: reductions down, RS, substitutions up.
+template <class R>
+cudaError_t solve_levels(cn_plan p, cudaStream_t st) {
     const int L = (int)p->lv.size() - 1;
-    cudaError_t e;
-    {
-        ProfScope ps(p, kProfReduce0, st);
-        e = launch_reduce<R>(src0, p->lv[0], p->lv[1], p->status, st);
-    }
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
     for (int l = 1; l < L; ++l) {
         ProfScope ps(p, kProfReduceL, st);
-        e = launch_reduce<R>(level_source(p->lv[l]), p->lv[l], p->lv[l + 1], p->status, st);
+        e = launch_reduce<R>(level_source<R>(p->lv[l]), p->lv[l], p->lv[l + 1], p->status, st);
         if (e != cudaSuccess) return e;
     }
     {
         ProfScope ps(p, kProfBase, st);
-        k_base<R><<<1, 32, 0, st>>>(level_source(p->lv[L]), p->lv[L].n, p->lv[L].x, p->status);
+        k_base<R><<<1, 32, 0, st>>>(level_source<R>(p->lv[L]), p->lv[L].n, x_of<R>(p->lv[L]), p->status);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
     for (int l = L - 1; l >= 1; --l) {
         ProfScope ps(p, kProfSubstL, st);
-        e = launch_substitute<R>(level_source(p->lv[l]), p->lv[l], p->lv[l + 1], p->lv[l].x, p->status, st);
+        e = launch_substitute<R>(level_source<R>(p->lv[l]), p->lv[l], p->lv[l + 1], x_of<R>(p->lv[l]), p->status, st);
         if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
+}
+
+// General tridiagonal solve (arrays at level 0).
+template <class R>
+cudaError_t solve_arrays(cn_plan p, const ArraySource& src, double2* x, cudaStream_t st) {
+    cudaError_t e;
+    {
+        ProfScope ps(p, kProfReduce0, st);
+        e = launch_reduce<R>(src, p->lv[0], p->lv[1], p->status, st);
+    }
+    if (e != cudaSuccess) return e;
+    if ((e = solve_levels<R>(p, st)) != cudaSuccess) return e;
     ProfScope ps(p, kProfSubst0, st);
-    return launch_substitute<R>(src0, p->lv[0], p->lv[1], x0, p->status, st);
+    return launch_substitute<R>(src, p->lv[0], p->lv[1], x, p->status, st);
+}
+
+// One CN-type step (level 0 generated on the fly), result in x.
+template <class R>
+cudaError_t cn_solve(cn_plan p, const CNStep& s, double2* x, cudaStream_t st) {
+    const Level& L0 = p->lv[0];
+    const Level& L1 = p->lv[1];
+    const unsigned grid = grid_for(L0.P);
+    cudaError_t e;
+    {
+        ProfScope ps(p, kProfReduce0, st);
+        CNB_DISPATCH_M(L0.m, (k_cn_reduce<R, M><<<grid, kThreads, 0, st>>>(s, L0.P, L0.m, rows_of<R>(L1),
+                                                                           slot_of<R>(L1), p->status)));
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
+    if ((e = solve_levels<R>(p, st)) != cudaSuccess) return e;
+    ProfScope ps(p, kProfSubst0, st);
+    CNB_DISPATCH_M(L0.m, (k_cn_substitute<R, M><<<grid, kThreads, 0, st>>>(s, L0.P, L0.m, x_of<R>(L1), x,
+                                                                           p->status)));
+    return cudaGetLastError();
 }
 
 template <class R>
@@ -197,27 +231,29 @@ cudaError_t cn_steps(cn_plan p, const double2* in, double2* out, const double* E
     // Step k writes dest(k); the last step writes out; in is never written
     // unless it is out.  Destinations alternate between out and the scratch.
     const double2* src = in;
-    bool first_to_out = ((nsteps - 1) % 2) == 0;
-    if (in == out && first_to_out) {
+    if (in == out && ((nsteps - 1) % 2) == 0) {
         cudaError_t e = cudaMemcpyAsync(p->state, in, bytes, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
         src = p->state;
     }
     for (int64_t k = 0; k < nsteps; ++k) {
         double2* dst = (((nsteps - 1 - k) % 2) == 0) ? out : p->state;
-        CNSource s;
+        CNStep s;
         s.p = p->cnp;
         s.psi = src;
-        s.sgn_t = 1.0;
-        s.sgn_e = -1.0;
+        s.s = 1.0;
+        s.e = -1.0;
         s.E_t = E_mid ? E_mid + k : nullptr;
         s.E_e = s.E_t;
-        cudaError_t e = nshape_solve<R>(p, s, dst, st);
+        s.tab = p->tab;
+        cudaError_t e = cn_solve<R>(p, s, dst, st);
         if (e != cudaSuccess) return e;
         src = dst;
     }
     return cudaSuccess;
 }
+
+size_t real_size(int arith) { return arith == CN_ARITH_DF64 ? sizeof(df) : sizeof(double); }
 
 }  // namespace
 
@@ -236,7 +272,7 @@ const char* cn_status_string(cn_status s) {
     }
 }
 
-const char* cn_version(void) { return "cn_b300 0.1 sm_103a"; }
+const char* cn_version(void) { return "cn_b300 0.2 sm_103a"; }
 
 cn_status cn_plan_create(const cn_desc* desc, cn_plan* out) {
     if (!out) return CN_ERR_INVALID_ARG;
@@ -250,6 +286,9 @@ cn_status cn_plan_create(const cn_desc* desc, cn_plan* out) {
     if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return CN_ERR_CUDA; }
     if (desc->pot == CN_POT_COSSERIES && desc->n_cos > 0) p->cos_a.assign(desc->cos_a, desc->cos_a + desc->n_cos);
     p->desc.cos_a = nullptr;
+    const bool df_mode = desc->arith == CN_ARITH_DF64;
+    const bool use_table = (desc->flags & CN_FLAG_COEFF_TABLE) ||
+                           (df_mode && (desc->pot == CN_POT_ARRAY || desc->pot == CN_POT_COSSERIES));
 
     // levels: level l has n_l rows in P_l blocks of m_l rows; n_{l+1} = P_l + 1
     int64_t n = desc->n;
@@ -269,40 +308,51 @@ cn_status cn_plan_create(const cn_desc* desc, cn_plan* out) {
             break;
         }
     }
+    const size_t cplx = 16;  // bytes per complex in either compute type
     cudaError_t e = cudaSuccess;
     for (size_t l = 1; l < p->lv.size() && e == cudaSuccess; ++l) {
         Level& L = p->lv[l];
-        p->workspace_bytes += (int64_t)(sizeof(LevelRow) + sizeof(double2)) * L.n +
-                              (int64_t)sizeof(LevelSlot) * (grid_for(p->lv[l - 1].P) + 1);
-        e = cudaMalloc(&L.rows, sizeof(LevelRow) * (size_t)L.n);
-        if (e == cudaSuccess) e = cudaMalloc(&L.slot, sizeof(LevelSlot) * (size_t)(grid_for(p->lv[l - 1].P) + 1));
-        if (e == cudaSuccess) e = cudaMalloc(&L.x, sizeof(double2) * (size_t)L.n);
-        if (e == cudaSuccess) e = cudaMemset(L.slot, 0, sizeof(LevelSlot) * (size_t)(grid_for(p->lv[l - 1].P) + 1));
+        const size_t nslot = grid_for(p->lv[l - 1].P) + 1;
+        p->workspace_bytes += (int64_t)(5 * cplx * L.n + 3 * cplx * nslot);
+        e = cudaMalloc(&L.rows, 4 * cplx * (size_t)L.n);
+        if (e == cudaSuccess) e = cudaMalloc(&L.slot, 3 * cplx * nslot);
+        if (e == cudaSuccess) e = cudaMalloc(&L.x, cplx * (size_t)L.n);
+        if (e == cudaSuccess) e = cudaMemset(L.slot, 0, 3 * cplx * nslot);
     }
-    p->workspace_bytes += (int64_t)sizeof(double2) * desc->n + (int64_t)sizeof(int);
-    if (e == cudaSuccess) e = cudaMalloc(&p->state, sizeof(double2) * (size_t)desc->n);
+    p->workspace_bytes += (int64_t)(cplx * desc->n + sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&p->state, cplx * (size_t)desc->n);
     if (e == cudaSuccess) e = cudaMalloc(&p->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(int));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        free_plan_memory(p);
-        delete p;
-        return e == cudaErrorMemoryAllocation ? CN_ERR_OOM : CN_ERR_CUDA;
+    if (e == cudaSuccess && use_table) {
+        p->workspace_bytes += (int64_t)(real_size(desc->arith) * desc->n);
+        e = cudaMalloc(&p->tab, real_size(desc->arith) * (size_t)desc->n);
     }
     CNParams& c = p->cnp;
     std::memset(&c, 0, sizeof(c));
     c.n = desc->n;
     c.dx = desc->dx;
     c.x_min = desc->x_min;
-    c.half_dt = 0.5 * desc->dt;
-    c.inv_dx2 = 1.0 / (desc->dx * desc->dx);
-    c.gamma = desc->dt / (4.0 * desc->dx * desc->dx);
+    c.c1 = 2.0 * desc->dx * desc->dx;
+    c.gt = 4.0 * desc->dx * desc->dx / desc->dt;
     c.pot = desc->pot;
     c.V0 = desc->V0;
     c.soft_s = desc->soft_s;
     c.n_cos = desc->pot == CN_POT_COSSERIES ? desc->n_cos : 0;
     c.two_pi_over_L = desc->pot == CN_POT_COSSERIES ? 2.0 * 3.14159265358979323846 / desc->L : 0.0;
     for (int k = 0; k < c.n_cos; ++k) c.cos_a[k] = p->cos_a[(size_t)k];
+    if (e == cudaSuccess && use_table) {
+        const unsigned grid = (unsigned)ceil_div(desc->n, 256);
+        if (df_mode) k_beta0_table<df><<<grid, 256>>>(c, static_cast<df*>(p->tab));
+        else k_beta0_table<double><<<grid, 256>>>(c, static_cast<double*>(p->tab));
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_plan_memory(p);
+        delete p;
+        return e == cudaErrorMemoryAllocation ? CN_ERR_OOM : CN_ERR_CUDA;
+    }
     *out = p;
     return CN_OK;
 }
@@ -315,17 +365,15 @@ cn_status cn_plan_destroy(cn_plan p) {
     return CN_OK;
 }
 
-cn_status cn_step(cn_plan p, const void* psi_in, void* psi_out, const double* E_mid, int64_t nsteps,
-                  void* stream) {
+cn_status cn_step(cn_plan p, const void* psi_in, void* psi_out, const double* E_mid, int64_t nsteps, void* stream) {
     if (!p || !psi_in || !psi_out || nsteps < 0) return CN_ERR_INVALID_ARG;
     if (!aligned16(psi_in) || !aligned16(psi_out)) return CN_ERR_INVALID_ARG;
     if (E_mid && (reinterpret_cast<uintptr_t>(E_mid) & 7u)) return CN_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e;
-    if (p->desc.arith == CN_ARITH_DF64)
-        e = cn_steps<df>(p, static_cast<const double2*>(psi_in), static_cast<double2*>(psi_out), E_mid, nsteps, st);
-    else
-        e = cn_steps<double>(p, static_cast<const double2*>(psi_in), static_cast<double2*>(psi_out), E_mid, nsteps, st);
+    const double2* in = static_cast<const double2*>(psi_in);
+    double2* out = static_cast<double2*>(psi_out);
+    cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? cn_steps<df>(p, in, out, E_mid, nsteps, st)
+                                                     : cn_steps<double>(p, in, out, E_mid, nsteps, st);
     return cuda_status(e);
 }
 
@@ -344,7 +392,10 @@ cn_status cn_step_host(cn_plan p, const void* psi_in_host, void* psi_out_host, c
         e = cudaMalloc(&p->h_E, sizeof(double) * (size_t)nsteps);
         if (e == cudaSuccess) p->h_E_cap = nsteps;
     }
-    if (e != cudaSuccess) { cudaGetLastError(); return e == cudaErrorMemoryAllocation ? CN_ERR_OOM : CN_ERR_CUDA; }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? CN_ERR_OOM : CN_ERR_CUDA;
+    }
     e = cudaMemcpyAsync(p->h_in, psi_in_host, bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && E_mid_host && nsteps > 0)
         e = cudaMemcpyAsync(p->h_E, E_mid_host, sizeof(double) * (size_t)nsteps, cudaMemcpyHostToDevice, st);
@@ -356,8 +407,8 @@ cn_status cn_step_host(cn_plan p, const void* psi_in_host, void* psi_out_host, c
     return cuda_status(e);
 }
 
-cn_status cn_solve_tridiag(cn_plan p, const void* b, const void* a, const void* c, const void* d, void* x,
-                           int64_t n, void* stream) {
+cn_status cn_solve_tridiag(cn_plan p, const void* b, const void* a, const void* c, const void* d, void* x, int64_t n,
+                           void* stream) {
     if (!p || !b || !a || !c || !d || !x) return CN_ERR_INVALID_ARG;
     if (n != p->desc.n) return CN_ERR_INVALID_ARG;
     if (!aligned16(b) || !aligned16(a) || !aligned16(c) || !aligned16(d) || !aligned16(x)) return CN_ERR_INVALID_ARG;
@@ -369,8 +420,8 @@ cn_status cn_solve_tridiag(cn_plan p, const void* b, const void* a, const void* 
     s.d = static_cast<const double2*>(d);
     s.n = n;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? nshape_solve<df>(p, s, static_cast<double2*>(x), st)
-                                                     : nshape_solve<double>(p, s, static_cast<double2*>(x), st);
+    cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? solve_arrays<df>(p, s, static_cast<double2*>(x), st)
+                                                     : solve_arrays<double>(p, s, static_cast<double2*>(x), st);
     return cuda_status(e);
 }
 
@@ -416,9 +467,7 @@ cn_status cn_plan_status(cn_plan p) {
     if (cudaDeviceSynchronize() != cudaSuccess) return CN_ERR_CUDA;
     int h = 0;
     if (cudaMemcpy(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CN_ERR_CUDA;
-    if (h != 0) {
-        if (cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) return CN_ERR_CUDA;
-    }
+    if (h != 0 && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) return CN_ERR_CUDA;
     return static_cast<cn_status>(h);
 }
 

@@ -1,151 +1,345 @@
-// cn_arith.cuh -- real and complex arithmetic used by the N-shaped CN kernels.
+// cn_arith.cuh -- real and complex arithmetic of the N-shaped CN kernels.
 //
-// Two real types share one kernel source:
-//   double : native IEEE binary64 (on B300 the FP64 pipe issues ~1.6 FMA per
-//            clock per SM, ~74x below FP32);
-//   df     : double-float ("double-word") value hi + lo of two binary32 words,
-//            |lo| <= ulp(hi)/2, ~48-bit significand.  Its operations are the
-//            error-free transformations of Dekker (1971) and Knuth (TAOCP vol. 2,
-//            TwoSum) and the double-word algorithms of Joldes, Muller and
-//            Popescu, "Tight and rigorous error bounds for basic building blocks
-//            of double-word arithmetic", ACM TOMS 44(2), 2017 (their Algorithms
-//            1-2, 4, 6, 9 and 12 are named where used).  All binary32 steps use
-//            __fadd_rn / __fmul_rn / __fmaf_rn so that the compiler can neither
-//            contract nor reassociate them.
+// Two real types share the kernel sources:
+//   double : native IEEE binary64.  On B300 the FP64 pipe issues ~1.6 FMA per
+//            clock per SM, ~74x below the FP32 pipe.
+//   df     : double-float ("double-word") value hi + lo of two binary32 words
+//            with |lo| <= ulp(hi)/2, ~48-bit significand, built only from
+//            binary32 FMA/add/mul and integer instructions, so it runs on the
+//            FP32 pipe.  Its operations are the error-free transformations of
+//            Dekker (1971) and Knuth (TAOCP vol. 2: TwoSum) and the double-word
+//            algorithms of Joldes, Muller and Popescu, "Tight and rigorous error
+//            bounds for basic building blocks of double-word arithmetic", ACM
+//            TOMS 44(2), 2017 (JMP17; the algorithm used is named at each
+//            function).  Complex products and sums of products are evaluated as
+//            one double-word dot product per component (exact binary32 products
+//            by FMA, one TwoSum chain, one final renormalisation), a
+//            restatement of the compensated dot product of Ogita, Rump and
+//            Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26(6),
+//            2005, truncated to double-word precision.
 //
-// The complex type cx<R> holds (re, im).  Complex numbers are stored in
-// memory as complex128 (two doubles); df values are converted on load/store.
+// Range of df: binary32 exponents.  Conversions from binary64 flush |x| < 2^-70
+// to zero (that is below anything that contributes to a normalised state);
+// values must stay below ~1e30.  The CN coefficients and normalised states
+// satisfy both bounds.
+//
+// Every binary32 step goes through f_add / f_mul / f_fma, which the compiler
+// may neither contract nor reassociate (device: __fadd_rn etc.; host builds of
+// the checks use -ffp-contract=off), so the functions are bit-reproducible on
+// host and device except for the reciprocal / rsqrt seeds.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
+#if !defined(__CUDA_ARCH__)
+#include <math.h>
+#endif
+
+#define CNB_HD __host__ __device__ __forceinline__
 
 namespace cnb {
 
-// ---------------------------------------------------------------- double-float
+// ------------------------------------------------------------ binary32 steps
+CNB_HD float f_add(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fadd_rn(a, b);
+#else
+    return a + b;
+#endif
+}
+CNB_HD float f_mul(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+CNB_HD float f_fma(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+    return __fmaf_rn(a, b, c);
+#else
+    return fmaf(a, b, c);
+#endif
+}
+// correctly rounded reciprocal and reciprocal square root (seeds only)
+CNB_HD float f_rcp(float a) {
+#ifdef __CUDA_ARCH__
+    return __frcp_rn(a);
+#else
+    return 1.0f / a;
+#endif
+}
+CNB_HD float f_rsqrt(float a) {
+#ifdef __CUDA_ARCH__
+    return __frsqrt_rn(a);
+#else
+    return (float)(1.0 / sqrt((double)a));
+#endif
+}
+CNB_HD int32_t f_bits(float a) {
+#ifdef __CUDA_ARCH__
+    return __float_as_int(a);
+#else
+    int32_t i; memcpy(&i, &a, 4); return i;
+#endif
+}
+CNB_HD float f_from_bits(int32_t i) {
+#ifdef __CUDA_ARCH__
+    return __int_as_float(i);
+#else
+    float a; memcpy(&a, &i, 4); return a;
+#endif
+}
+CNB_HD int64_t d_bits(double a) {
+#ifdef __CUDA_ARCH__
+    return __double_as_longlong(a);
+#else
+    int64_t i; memcpy(&i, &a, 8); return i;
+#endif
+}
+CNB_HD double d_from_bits(int64_t i) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(i);
+#else
+    double a; memcpy(&a, &i, 8); return a;
+#endif
+}
+CNB_HD float i2f(int32_t i) {
+#ifdef __CUDA_ARCH__
+    return __int2float_rn(i);
+#else
+    return (float)i;
+#endif
+}
+// 2^k as binary32 for -126 <= k <= 127
+CNB_HD float pow2f(int k) { return f_from_bits((k + 127) << 23); }
+
+// ------------------------------------------------------------ double-float
 struct df {
     float hi, lo;
 };
+CNB_HD df df_make(float h, float l) { df r; r.hi = h; r.lo = l; return r; }
 
-__device__ __forceinline__ df df_make(float h, float l) { df r; r.hi = h; r.lo = l; return r; }
-
-// Fast2Sum (Dekker): exact s + t = a + b when |a| >= |b| (JMP17 Alg. 1).
-__device__ __forceinline__ df fast_two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    float z = __fadd_rn(s, -a);
-    return df_make(s, __fadd_rn(b, -z));
+// Fast2Sum (Dekker; JMP17 Alg. 1): s + t = a + b exactly when exp(a) >= exp(b).
+CNB_HD df fast_two_sum(float a, float b) {
+    float s = f_add(a, b);
+    float z = f_add(s, -a);
+    return df_make(s, f_add(b, -z));
 }
-// 2Sum (Knuth/Moller): exact s + t = a + b for any a, b (JMP17 Alg. 2).
-__device__ __forceinline__ df two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    float ap = __fadd_rn(s, -b);
-    float bp = __fadd_rn(s, -ap);
-    float da = __fadd_rn(a, -ap);
-    float db = __fadd_rn(b, -bp);
-    return df_make(s, __fadd_rn(da, db));
+// 2Sum (Knuth, Moller; JMP17 Alg. 2): s + t = a + b exactly.
+CNB_HD df two_sum(float a, float b) {
+    float s = f_add(a, b);
+    float ap = f_add(s, -b);
+    float bp = f_add(s, -ap);
+    return df_make(s, f_add(f_add(a, -ap), f_add(b, -bp)));
 }
-// Fast2Mult: exact p + e = a * b with one FMA.
-__device__ __forceinline__ df two_prod(float a, float b) {
-    float p = __fmul_rn(a, b);
-    return df_make(p, __fmaf_rn(a, b, -p));
+// Fast2Mult with an FMA: p + e = a b exactly.
+CNB_HD df two_prod(float a, float b) {
+    float p = f_mul(a, b);
+    return df_make(p, f_fma(a, b, -p));
 }
 
-__device__ __forceinline__ df df_from_double(double x) {
-    float h = __double2float_rn(x);
-    float l = __double2float_rn(x - (double)h);
-    return df_make(h, l);
-}
-__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+CNB_HD df df_neg(df a) { return df_make(-a.hi, -a.lo); }
 
-// AccurateDWPlusDW (JMP17 Alg. 6): relative error <= 3u^2 + 13u^3.
-__device__ __forceinline__ df operator+(df x, df y) {
+// SloppyDWPlusDW (JMP17 Alg. 5): absolute error <= 2u^2 (|x| + |y|) -- ample for
+// the well-conditioned sums of the elimination (no relative bound is needed).
+CNB_HD df df_add(df x, df y) {
     df s = two_sum(x.hi, y.hi);
-    df t = two_sum(x.lo, y.lo);
-    float c = __fadd_rn(s.lo, t.hi);
-    df v = fast_two_sum(s.hi, c);
-    float w = __fadd_rn(t.lo, v.lo);
-    return fast_two_sum(v.hi, w);
+    float v = f_add(x.lo, y.lo);
+    float w = f_add(s.lo, v);
+    return fast_two_sum(s.hi, w);
 }
-__device__ __forceinline__ df operator-(df x) { return df_make(-x.hi, -x.lo); }
-__device__ __forceinline__ df operator-(df x, df y) { return x + (-y); }
-
-// DWTimesDW3 (JMP17 Alg. 12, with FMA): relative error <= 4u^2.
-__device__ __forceinline__ df operator*(df x, df y) {
+CNB_HD df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
+// DWPlusFP (JMP17 Alg. 4): double-float plus binary32, relative error <= 2u^2.
+CNB_HD df df_add_f(df x, float y) {
+    df s = two_sum(x.hi, y);
+    float v = f_add(x.lo, s.lo);
+    return fast_two_sum(s.hi, v);
+}
+// DWTimesDW2 (JMP17 Alg. 11): relative error <= 5u^2.
+CNB_HD df df_mul(df x, df y) {
     df c = two_prod(x.hi, y.hi);
-    float tl0 = __fmul_rn(x.lo, y.lo);
-    float tl1 = __fmaf_rn(x.hi, y.lo, tl0);
-    float cl2 = __fmaf_rn(x.lo, y.hi, tl1);
-    float cl3 = __fadd_rn(c.lo, cl2);
-    return fast_two_sum(c.hi, cl3);
+    float t = f_mul(x.hi, y.lo);
+    float cl2 = f_fma(x.lo, y.hi, t);
+    return fast_two_sum(c.hi, f_add(c.lo, cl2));
 }
-// DWTimesFP3 (JMP17 Alg. 9): double-float times a binary32 value, error <= 2u^2.
-__device__ __forceinline__ df df_mul_f(df x, float y) {
+// DWTimesFP3 (JMP17 Alg. 9): relative error <= 2u^2.
+CNB_HD df df_mul_f(df x, float y) {
     df c = two_prod(x.hi, y);
-    float cl3 = __fmaf_rn(x.lo, y, c.lo);
-    return fast_two_sum(c.hi, cl3);
+    return fast_two_sum(c.hi, f_fma(x.lo, y, c.lo));
 }
-// Reciprocal by one Newton step on the correctly rounded binary32 reciprocal:
-// t = RN(1/y_h) has relative error <= u; e = 1 - y t is formed with two FMAs
-// (the first is exact); 1/y = t (1 + e + e^2 + ...) ~= t + t e.
-__device__ __forceinline__ df df_rcp(df y) {
-    float t = __frcp_rn(y.hi);
-    float e1 = __fmaf_rn(-y.hi, t, 1.0f);
-    float e2 = __fmaf_rn(-y.lo, t, e1);
-    return fast_two_sum(t, __fmul_rn(t, e2));
+// 1/y: one Newton step t + t (1 - y t) on the correctly rounded binary32
+// reciprocal t (relative error <= u), with the residual 1 - y t formed by two
+// FMAs (the first is exact); relative error ~ u^2.
+CNB_HD df df_rcp(df y) {
+    float t = f_rcp(y.hi);
+    float e1 = f_fma(-y.hi, t, 1.0f);
+    float e2 = f_fma(-y.lo, t, e1);
+    return fast_two_sum(t, f_mul(t, e2));
 }
-__device__ __forceinline__ df df_fma(df a, df b, df c) { return a * b + c; }
+// 1/sqrt(q), q > 0: one Newton step y = t + t (1 - q t^2) / 2 on the correctly
+// rounded binary32 value t; q t^2 is formed from the exact square t^2 = p + e.
+CNB_HD df df_rsqrt(df q) {
+    float t = f_rsqrt(q.hi);
+    df t2 = two_prod(t, t);
+    df qt2 = df_mul(q, t2);                       // ~ 1
+    df r = df_add_f(df_neg(qt2), 1.0f);           // 1 - q t^2, tiny
+    float corr = f_mul(f_mul(t, 0.5f), f_add(r.hi, r.lo));
+    return fast_two_sum(t, corr);
+}
 
-// ------------------------------------------------------------- real traits
-template <class R> struct RealOps;
+// binary64 -> double-float with integer operations only (no FP64 pipe work):
+// hi = the 53-bit significand rounded to 24 bits, lo = the remainder rounded
+// to 24 bits; |x| < 2^-70 (incl. zero and subnormals) gives 0.
+CNB_HD df df_from_double(double x) {
+    const int64_t b = d_bits(x);
+    const int e = (int)((b >> 52) & 0x7FF) - 1023;
+    if (e < -70) return df_make(0.0f, 0.0f);
+    if (e > 126) {
+        float inf = f_from_bits(0x7F800000 | (b < 0 ? (int32_t)0x80000000 : 0));
+        return df_make(inf, 0.0f);
+    }
+    const uint64_t M = ((uint64_t)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    uint32_t hm = (uint32_t)(M >> 29);              // 24 leading bits
+    int32_t rem = (int32_t)(M & 0x1FFFFFFFu);       // 29 trailing bits
+    if (rem >= (1 << 28)) { hm += 1; rem -= (1 << 29); }
+    // hm in [2^23, 2^24]: hm - 2^23 carries into the exponent field when hm = 2^24
+    float hi = f_from_bits(((e + 127) << 23) + (int32_t)(hm - (1u << 23)));
+    float lo = f_mul(i2f(rem), pow2f(e - 52));
+    if (b < 0) { hi = -hi; lo = -lo; }
+    return df_make(hi, lo);
+}
 
-template <> struct RealOps<double> {
-    static __device__ __forceinline__ double from_d(double x) { return x; }
-    static __device__ __forceinline__ double to_d(double x) { return x; }
-    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
-    static __device__ __forceinline__ bool finite_pos(double x) { return x > 0.0 && x < 1.0e300; }
-};
-template <> struct RealOps<df> {
-    static __device__ __forceinline__ df from_d(double x) { return df_from_double(x); }
-    static __device__ __forceinline__ double to_d(df x) { return df_to_double(x); }
-    static __device__ __forceinline__ df rcp(df x) { return df_rcp(x); }
-    static __device__ __forceinline__ df fma(df a, df b, df c) { return df_fma(a, b, c); }
-    static __device__ __forceinline__ bool finite_pos(df x) { return x.hi > 0.0f && x.hi < 1.0e37f; }
-};
+// double-float -> binary64 with integer operations only: the exact sum
+// hi + lo, truncated to 53 bits when lo reaches below the last bit of hi's
+// binary64 significand (error < 2^-52 relative).
+CNB_HD double df_to_double(df v) {
+    const int32_t hb = f_bits(v.hi), lb = f_bits(v.lo);
+    const int eh = (hb >> 23) & 0xFF;
+    if (eh == 0) return 0.0;                                    // zero (subnormals flushed)
+    if (eh == 0xFF) return d_from_bits(((int64_t)(hb < 0) << 63) | (0x7FFll << 52) | ((int64_t)(hb & 0x7FFFFF) << 29));
+    int64_t E = eh - 127;                                        // exponent of hi
+    int64_t S = (int64_t)((hb & 0x7FFFFF) | 0x800000) << 29;    // 53-bit significand, unit 2^(E-52)
+    const int el = (lb >> 23) & 0xFF;
+    if (el != 0) {
+        int64_t ml = (lb & 0x7FFFFF) | 0x800000;                 // 24-bit significand, unit 2^(El-23)
+        int sh = (el - 127) - 23 - ((int)E - 52);                // shift to unit 2^(E-52)
+        int64_t L = sh >= 0 ? (sh < 40 ? (ml << sh) : 0) : (sh > -40 ? (ml >> -sh) : 0);
+        S += ((lb < 0) == (hb < 0)) ? L : -L;
+        if (S >= (1ll << 53)) { S >>= 1; E += 1; }
+        else if (S < (1ll << 52)) { S <<= 1; E -= 1; }
+    }
+    const int64_t bits = ((int64_t)(hb < 0) << 63) | ((E + 1023) << 52) | (S & 0xFFFFFFFFFFFFFll);
+    return d_from_bits(bits);
+}
 
-// ---------------------------------------------------------------- complex
+// Double-word dot products, one renormalisation each (see header comment).
+// sum_k a_k b_k for two terms: a0 b0 + a1 b1.
+CNB_HD df df_dot2(df a0, df b0, df a1, df b1) {
+    df p0 = two_prod(a0.hi, b0.hi);
+    df p1 = two_prod(a1.hi, b1.hi);
+    df s = two_sum(p0.hi, p1.hi);
+    float e = f_add(f_add(p0.lo, p1.lo), s.lo);
+    e = f_fma(a0.hi, b0.lo, e);
+    e = f_fma(a0.lo, b0.hi, e);
+    e = f_fma(a1.hi, b1.lo, e);
+    e = f_fma(a1.lo, b1.hi, e);
+    return two_sum(s.hi, e);
+}
+// c + a0 b0 + a1 b1
+CNB_HD df df_dot2_add(df c, df a0, df b0, df a1, df b1) {
+    df p0 = two_prod(a0.hi, b0.hi);
+    df p1 = two_prod(a1.hi, b1.hi);
+    df s = two_sum(p0.hi, p1.hi);
+    df t = two_sum(c.hi, s.hi);
+    float e = f_add(f_add(p0.lo, p1.lo), f_add(s.lo, t.lo));
+    e = f_add(e, c.lo);
+    e = f_fma(a0.hi, b0.lo, e);
+    e = f_fma(a0.lo, b0.hi, e);
+    e = f_fma(a1.hi, b1.lo, e);
+    e = f_fma(a1.lo, b1.hi, e);
+    return two_sum(t.hi, e);
+}
+
+// ------------------------------------------------------------ complex
 template <class R> struct cx {
     R re, im;
 };
+template <class R> CNB_HD cx<R> mk(R re, R im) { cx<R> z; z.re = re; z.im = im; return z; }
 
-template <class R> __device__ __forceinline__ cx<R> mk(R re, R im) { cx<R> z; z.re = re; z.im = im; return z; }
-template <class R> __device__ __forceinline__ cx<R> czero() {
-    return mk<R>(RealOps<R>::from_d(0.0), RealOps<R>::from_d(0.0));
+// --- double
+CNB_HD cx<double> cadd(cx<double> a, cx<double> b) { return mk(a.re + b.re, a.im + b.im); }
+CNB_HD cx<double> csub(cx<double> a, cx<double> b) { return mk(a.re - b.re, a.im - b.im); }
+CNB_HD cx<double> cneg(cx<double> a) { return mk(-a.re, -a.im); }
+CNB_HD cx<double> cmul(cx<double> a, cx<double> b) {
+    return mk(fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re));
 }
-template <class R> __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return mk<R>(a.re + b.re, a.im + b.im); }
-template <class R> __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return mk<R>(a.re - b.re, a.im - b.im); }
-template <class R> __device__ __forceinline__ cx<R> operator-(cx<R> a) { return mk<R>(-a.re, -a.im); }
-// (a + ib)(c + id) = (ac - bd) + i(ad + bc)
-template <class R> __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
-    return mk<R>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+// c + a b
+CNB_HD cx<double> cfma(cx<double> c, cx<double> a, cx<double> b) {
+    return mk(fma(a.re, b.re, fma(-a.im, b.im, c.re)), fma(a.re, b.im, fma(a.im, b.re, c.im)));
 }
-template <class R> __device__ __forceinline__ cx<R> cscale(cx<R> a, R s) { return mk<R>(a.re * s, a.im * s); }
-// i * z
-template <class R> __device__ __forceinline__ cx<R> cmul_i(cx<R> z) { return mk<R>(-z.im, z.re); }
-template <class R> __device__ __forceinline__ R cabs2(cx<R> z) { return z.re * z.re + z.im * z.im; }
-// 1/z = conj(z) / |z|^2 (one real reciprocal); ok <- false when |z|^2 is 0, inf or NaN
-template <class R> __device__ __forceinline__ cx<R> crcp(cx<R> z, bool& ok) {
-    R m2 = cabs2(z);
-    ok = ok && RealOps<R>::finite_pos(m2);
-    R q = RealOps<R>::rcp(m2);
-    return mk<R>(z.re * q, -(z.im * q));
+CNB_HD cx<double> crcp(cx<double> z, bool& ok) {
+    double m2 = fma(z.re, z.re, z.im * z.im);
+    ok = ok && (m2 > 0.0 && m2 < 1.0e300);
+    double q = 1.0 / m2;
+    return mk(z.re * q, -(z.im * q));
 }
 
-// complex128 memory <-> cx<R>
-template <class R> __device__ __forceinline__ cx<R> cload(const double2* p) {
+// --- double-float
+CNB_HD cx<df> cadd(cx<df> a, cx<df> b) { return mk(df_add(a.re, b.re), df_add(a.im, b.im)); }
+CNB_HD cx<df> csub(cx<df> a, cx<df> b) { return mk(df_sub(a.re, b.re), df_sub(a.im, b.im)); }
+CNB_HD cx<df> cneg(cx<df> a) { return mk(df_neg(a.re), df_neg(a.im)); }
+CNB_HD cx<df> cmul(cx<df> a, cx<df> b) {
+    return mk(df_dot2(a.re, b.re, df_neg(a.im), b.im), df_dot2(a.re, b.im, a.im, b.re));
+}
+CNB_HD cx<df> cfma(cx<df> c, cx<df> a, cx<df> b) {
+    return mk(df_dot2_add(c.re, a.re, b.re, df_neg(a.im), b.im), df_dot2_add(c.im, a.re, b.im, a.im, b.re));
+}
+// 1/z = conj(z) / |z|^2
+CNB_HD cx<df> crcp(cx<df> z, bool& ok) {
+    df m2 = df_dot2(z.re, z.re, z.im, z.im);
+    ok = ok && (m2.hi > 0.0f && m2.hi < 1.0e37f);
+    df q = df_rcp(m2);
+    return mk(df_mul(z.re, q), df_neg(df_mul(z.im, q)));
+}
+
+// ------------------------------------------------------------ real helpers
+template <class R> struct RealOps;
+template <> struct RealOps<double> {
+    static CNB_HD double from_d(double x) { return x; }
+    static CNB_HD double to_d(double x) { return x; }
+};
+template <> struct RealOps<df> {
+    static CNB_HD df from_d(double x) { return df_from_double(x); }
+    static CNB_HD double to_d(df x) { return df_to_double(x); }
+};
+template <class R> CNB_HD cx<R> czero() { return mk<R>(RealOps<R>::from_d(0.0), RealOps<R>::from_d(0.0)); }
+template <class R> CNB_HD cx<R> cfrom(double re, double im) {
+    return mk<R>(RealOps<R>::from_d(re), RealOps<R>::from_d(im));
+}
+
+// ------------------------------------------------------------ storage
+// Workspace (reduced systems, their solutions) is stored in the compute type:
+// double2 (re, im) for double, float4 (re.hi, re.lo, im.hi, im.lo) for df --
+// 16 B per complex either way.  User-facing states are complex128 (double2).
+template <class R> struct Store;
+template <> struct Store<double> { typedef double2 T; };
+template <> struct Store<df> { typedef float4 T; };
+
+CNB_HD cx<double> sload(const double2* p) { double2 v = *p; return mk(v.x, v.y); }
+CNB_HD void sstore(double2* p, cx<double> z) { *p = make_double2(z.re, z.im); }
+CNB_HD cx<df> sload(const float4* p) {
+    float4 v = *p;
+    return mk(df_make(v.x, v.y), df_make(v.z, v.w));
+}
+CNB_HD void sstore(float4* p, cx<df> z) { *p = make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo); }
+
+// complex128 in memory <-> cx<R>
+template <class R> CNB_HD cx<R> load128(const double2* p) {
     double2 v = *p;
     return mk<R>(RealOps<R>::from_d(v.x), RealOps<R>::from_d(v.y));
 }
-template <class R> __device__ __forceinline__ void cstore(double2* p, cx<R> z) {
+template <class R> CNB_HD void store128(double2* p, cx<R> z) {
     *p = make_double2(RealOps<R>::to_d(z.re), RealOps<R>::to_d(z.im));
 }
 

@@ -1,0 +1,44 @@
+// Host build of the library's double-float arithmetic (cn_arith.cuh) for the
+// CPU checks in test_df_arith.py.  Compiled with -ffp-contract=off.
+#include "../paper_2205_00856_b300/csrc/cn_arith.cuh"
+using namespace cnb;
+
+extern "C" {
+void shim_from_double(const double* x, float* hl, long n) {
+    for (long i = 0; i < n; ++i) { df v = df_from_double(x[i]); hl[2 * i] = v.hi; hl[2 * i + 1] = v.lo; }
+}
+void shim_to_double(const float* hl, double* x, long n) {
+    for (long i = 0; i < n; ++i) x[i] = df_to_double(df_make(hl[2 * i], hl[2 * i + 1]));
+}
+// op: 0 add, 1 mul, 2 mul_f (b.hi), 3 rcp (a), 4 rsqrt (a), 5 dot2 (a0 b0 + a1 b1), 6 dot2_add (c + a0 b0 + a1 b1)
+void shim_op(int op, const float* a, const float* b, const float* c, const float* d, const float* e, float* out, long n) {
+    for (long i = 0; i < n; ++i) {
+        df A = df_make(a[2 * i], a[2 * i + 1]), B = df_make(b[2 * i], b[2 * i + 1]);
+        df C = df_make(c[2 * i], c[2 * i + 1]), D = df_make(d[2 * i], d[2 * i + 1]);
+        df E = df_make(e[2 * i], e[2 * i + 1]);
+        df r;
+        switch (op) {
+        case 0: r = df_add(A, B); break;
+        case 1: r = df_mul(A, B); break;
+        case 2: r = df_mul_f(A, B.hi); break;
+        case 3: r = df_rcp(A); break;
+        case 4: r = df_rsqrt(A); break;
+        case 5: r = df_dot2(A, B, C, D); break;
+        default: r = df_dot2_add(E, A, B, C, D); break;
+        }
+        out[2 * i] = r.hi; out[2 * i + 1] = r.lo;
+    }
+}
+// complex ops on (re.hi, re.lo, im.hi, im.lo): 0 cmul(a,b), 1 cfma(c,a,b) = c + a b, 2 crcp(a)
+void shim_cop(int op, const float* a, const float* b, const float* c, float* out, int* ok, long n) {
+    for (long i = 0; i < n; ++i) {
+        cx<df> A = mk(df_make(a[4 * i], a[4 * i + 1]), df_make(a[4 * i + 2], a[4 * i + 3]));
+        cx<df> B = mk(df_make(b[4 * i], b[4 * i + 1]), df_make(b[4 * i + 2], b[4 * i + 3]));
+        cx<df> Cc = mk(df_make(c[4 * i], c[4 * i + 1]), df_make(c[4 * i + 2], c[4 * i + 3]));
+        bool k = true;
+        cx<df> r = op == 0 ? cmul(A, B) : (op == 1 ? cfma(Cc, A, B) : crcp(A, k));
+        out[4 * i] = r.re.hi; out[4 * i + 1] = r.re.lo; out[4 * i + 2] = r.im.hi; out[4 * i + 3] = r.im.lo;
+        ok[i] = k;
+    }
+}
+}

@@ -153,3 +153,65 @@ def test_full_size_soft_coulomb_2pow24():
     assert rel(out, ref) <= 1e-12
     # unitarity of the Cayley form at full size
     assert abs(np.sum(np.abs(out) ** 2) / np.sum(np.abs(psi0) ** 2) - 1) <= 1e-12
+
+
+# ------------------------------------------------------------------ potentials and coefficient tables
+def _cos_cfg(n=5003):
+    c = W.batched_config(8)
+    dx, dt = c["dx"], c["dt"]
+    return dict(n=n, dx=dx, dt=dt, x_min=-(n // 2) * dx, pot=cnb.POT_COSSERIES, cos_a=c["cos_a"][3], L=n * dx)
+
+
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_cos_series_potential(arith):
+    cfg = _cos_cfg()
+    psi0 = W.gaussian(cfg["n"], cfg["dx"], cfg["x_min"], 0.0, cfg["L"] / 40, 1.0)
+    prob = oracle.Problem(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=oracle.POT_COSSERIES,
+                          cos_a=cfg["cos_a"], L=cfg["L"])
+    ref = oracle.cn_run(prob, psi0, 100)
+    plan = cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_COSSERIES, cos_a=cfg["cos_a"],
+                    L=cfg["L"], arith=arith)
+    out = plan.step(to_dev(psi0), 100).cpu().numpy()
+    plan.check()
+    assert rel(out, ref) <= 1e-11
+
+
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_array_potential_with_field(arith):
+    n, dx, dt = 7001, 0.1, 0.02
+    x_min = -(n // 2) * dx
+    x = W.grid(n, dx, x_min)
+    V0 = -0.8 * np.exp(-x ** 2 / 8.0) + 0.1 * np.tanh(x / 30.0)
+    psi0 = W.gaussian(n, dx, x_min, -3.0, 1.5, 0.4)
+    E = W.field_midpoints(100, dt, t0=80.0)
+    ref = oracle.cn_run(oracle.Problem(n, dx, dt, x_min, pot=oracle.POT_ARRAY, V0=V0), psi0, 100, E_mid=E)
+    plan = cnb.Plan(n, dx, dt, x_min, pot=cnb.POT_ARRAY, V0=to_dev(V0), arith=arith)
+    out = plan.step(to_dev(psi0), 100, E_mid=to_dev(E)).cpu().numpy()
+    plan.check()
+    assert rel(out, ref) <= 1e-11
+
+
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_coefficient_table_matches_on_the_fly(arith):
+    cfg = W.soft_coulomb_config(n=30011, nsteps=50)
+    psi0 = W.initial_state(cfg)
+    E = W.field_midpoints(50, cfg["dt"], t0=120.0)
+    ref = oracle.cn_run(oracle_problem(cfg), psi0, 50, E_mid=E)
+    plan = cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith,
+                    flags=cnb.FLAG_COEFF_TABLE)
+    out = plan.step(to_dev(psi0), 50, E_mid=to_dev(E)).cpu().numpy()
+    plan.check()
+    assert rel(out, ref) <= 1e-11
+
+
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_norm_conservation_1000_steps_2pow20(arith):
+    # unitarity of the Cayley form over a long run at a large size (any size: property)
+    cfg = W.soft_coulomb_config(n=1 << 20, nsteps=1000)
+    psi0 = W.initial_state(cfg)
+    E = W.field_midpoints(1000, cfg["dt"], t0=0.0)
+    plan = plan_for(cfg, arith=arith)
+    out = plan.step(to_dev(psi0), 1000, E_mid=to_dev(E)).cpu().numpy()
+    plan.check()
+    n0, n1 = np.sum(np.abs(psi0) ** 2), np.sum(np.abs(out) ** 2)
+    assert abs(n1 / n0 - 1) <= (1e-12 if arith == cnb.ARITH_F64 else 1e-11)
