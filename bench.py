@@ -38,13 +38,18 @@ METRIC = "CN grid-point updates/sec (complex128)"
 UNIT = "unknown-steps/s"
 WORKLOAD_STEPS = 1000  # length of the benchmarked propagation (field samples)
 
-# Algorithmic FP64 flops per grid row of the two level-0 kernels for the
-# soft-Coulomb CN source (FMA = 2 flops, division / rsqrt = 1; derivation in
-# DESIGN.md, "Algorithmic work per unknown"):
-FLOPS_PER_ROW = {"reduce_level0": 65.0, "substitute_level0": 45.0}
-# Algorithmic HBM bytes per grid row: the reduction reads psi (16 B); the
-# substitution reads psi and writes psi' (32 B); one CN step moves 32 B.
-BYTES_PER_ROW = {"reduce_level0": 16.0, "substitute_level0": 32.0}
+# Algorithmic flops per grid row of the two level-0 kernels (soft-Coulomb
+# potential regenerated on the fly, store mode), FMA = 2 flops, a reciprocal or
+# reciprocal square root = 1; m = rows per level-0 block.  Derivation (operation
+# counts of every step) in DESIGN.md, "Algorithmic work per unknown".
+#   FP64:          reduce 65 + 64/m,   substitute 16
+#   double-float:  reduce 604 + 600/m, substitute 150   (binary32 flops)
+def flops_per_row(kernel: str, arith: str, m: int) -> float:
+    if arith == "f64":
+        return 65.0 + 64.0 / m if kernel == "reduce_level0" else 16.0
+    return 604.0 + 600.0 / m if kernel == "reduce_level0" else 150.0
+
+
 STEP_BYTES_PER_ROW = 32.0
 # Recipe nominal FP64 rate of a B300 (MEASURED_PEAKS.json carries no FP64 figure).
 FP64_NOMINAL_TFLOPS = 1.25
@@ -204,8 +209,76 @@ def workload_config(args):
     return {"workload": "soft_coulomb_laser_1d_cn", "n": getattr(args, "n", 1 << 24), "dx": 0.1, "dt": 0.02,
             "potential": "-1/sqrt(x^2+2) + x E(t)", "field": "0.05 sin^2(pi t/T) cos(0.057 t), T = 4*2pi/0.057",
             "steps_per_bench_step": 1, "workload_steps": WORKLOAD_STEPS, "block": args.block,
+            "level_block": getattr(args, "level_block", 8),
             "arith": args.arith, "l2": "inputs larger than L2 (2 x 256 MiB states vs 126 MB L2), no flush",
             "parallelism": f"replicas x{args.gpus}"}
+
+
+def make_plan(cnb, cfg, args, arith):
+    return cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0,
+                    block=args.block, arith=arith, level_block=args.level_block)
+
+
+def time_steps(torch, plan, psi0, E, steps, warmup, dist, dev, sample_clocks):
+    """warmup + steps single CN steps (one cn_step call each), CUDA events on the
+    launching stream, per-kernel-class event times; returns (ms, prof, clocks)."""
+    cur = torch.from_numpy(psi0).to(dev)
+    stream = torch.cuda.current_stream()
+    def one_step(k):
+        j = k % WORKLOAD_STEPS
+        plan.step(cur, 1, E_mid=E[j:j + 1], psi_out=cur, stream=stream)
+    for k in range(warmup):
+        one_step(k)
+    torch.cuda.synchronize()
+    plan.check()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plan.profile(True)
+    plan.profile_read()
+    clk = ClockSampler(uuid) if sample_clocks else None
+    if clk:
+        clk.__enter__()
+    ev0.record(stream)
+    for k in range(steps):
+        one_step(warmup + k)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__()
+    plan.profile(False)
+    prof = plan.profile_read()
+    plan.check()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    return ms, prof, (clk.summary() if clk else None)
+
+
+def roofline(prof, n, arith, peaks, m):
+    dom = max(("reduce_level0", "substitute_level0"), key=lambda c: prof[c][0])
+    dom_ms, dom_launches = prof[dom]
+    avg_s = dom_ms * 1e-3 / max(dom_launches, 1)
+    if arith == "f64":
+        achieved = flops_per_row(dom, arith, m) * n / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_NOMINAL_TFLOPS,
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table; no FP64 figure in MEASURED_PEAKS.json)",
+                "basis": "algorithmic FP64 flops per grid row (FMA = 2)"}
+    else:
+        achieved = flops_per_row(dom, arith, m) * n / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS,
+                "peak_source": "FP32 issue peak 148 SM x 128 lanes x 2 x 2.032 GHz (recipe unit counts and clock)",
+                "basis": "binary32 flops (FMA = 2) of the double-float formulation per grid row"}
+    roof.update({"kernel": dom, "avg_launch_ms": avg_s * 1e3, "flops_per_row": flops_per_row(dom, arith, m),
+                 "traffic": ncu_traffic(dom, arith, n)})
+    return roof
 
 
 def main():
@@ -214,8 +287,11 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
-    ap.add_argument("--arith", choices=["f64", "df64"], default="f64")
+    ap.add_argument("--arith", choices=["f64", "df64"], default="df64")
+    ap.add_argument("--f64-steps", type=int, default=100,
+                    help="also time the native-FP64 path for this many steps (0: skip)")
     ap.add_argument("--block", type=int, default=8)
+    ap.add_argument("--level-block", type=int, default=8)
     ap.add_argument("--n", type=int, default=1 << 24, help="grid points (profiling runs use smaller grids)")
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--e2e-inner", type=int, default=50, help="CN steps per end-to-end call")
@@ -238,51 +314,13 @@ def main():
 
     cfg = W.soft_coulomb_config(n=args.n)
     n = cfg["n"]
-    arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
-    plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0,
-                    block=args.block, arith=arith)
-    info = plan.info()
     psi0 = W.initial_state(cfg)
     E_host = W.field_midpoints(WORKLOAD_STEPS, cfg["dt"])
     E = torch.from_numpy(E_host).to(dev)
-    cur = torch.from_numpy(psi0).to(dev)
-    nxt = torch.empty_like(cur)
-    stream = torch.cuda.current_stream()
-
-    def one_step(k):
-        nonlocal cur, nxt
-        j = k % WORKLOAD_STEPS
-        plan.step(cur, 1, E_mid=E[j:j + 1], psi_out=nxt, stream=stream)
-        cur, nxt = nxt, cur
-
-    for k in range(args.warmup):
-        one_step(k)
-    torch.cuda.synchronize()
-    plan.check()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-
-    uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    plan.profile(True)
-    plan.profile_read()
-    with ClockSampler(uuid) as clk:
-        ev0.record(stream)
-        for k in range(args.steps):
-            one_step(args.warmup + k)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    plan.profile(False)
-    prof = plan.profile_read()
-    plan.check()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    torch.cuda.synchronize()
+    arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
+    plan = make_plan(cnb, cfg, args, arith)
+    info = plan.info()
+    ms, prof, clocks = time_steps(torch, plan, psi0, E, args.steps, args.warmup, dist, dev, rank == 0)
     value = n * args.steps * world / (ms * 1e-3)
 
     # end to end through the C ABI with host buffers: H2D of psi and E, inner
@@ -303,31 +341,25 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e_val = n * args.e2e_inner * args.e2e_calls * world / e2e_s
+    plan.close()
+
+    alt = None
+    if args.f64_steps > 0 and args.arith != "f64":
+        plan64 = make_plan(cnb, cfg, args, cnb.ARITH_F64)
+        ms64, prof64, _ = time_steps(torch, plan64, psi0, E, args.f64_steps, args.warmup, dist, dev, False)
+        plan64.close()
+        alt = {"dtype": "f64", "value": n * args.f64_steps * world / (ms64 * 1e-3), "unit": UNIT,
+               "steps": args.f64_steps, "ms_per_step": ms64 / args.f64_steps,
+               "roofline": roofline(prof64, n, "f64", measured_peaks(), args.block) if rank == 0 else None}
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel (largest share of kernel time)
-    dom = max(("reduce_level0", "substitute_level0"), key=lambda c: prof[c][0])
-    dom_ms, dom_launches = prof[dom]
-    avg_s = dom_ms * 1e-3 / max(dom_launches, 1)
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
-    if args.arith == "f64":
-        achieved = FLOPS_PER_ROW[dom] * n / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_NOMINAL_TFLOPS,
-                "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table; no FP64 figure in MEASURED_PEAKS.json)",
-                "kernel": dom, "flops_per_row": FLOPS_PER_ROW[dom], "avg_launch_ms": avg_s * 1e3}
-    else:
-        achieved = FLOPS_PER_ROW[dom] * n / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS,
-                "peak_source": "FP32 issue peak 148 SM x 128 lanes x 2 x 2.032 GHz (double-float path)",
-                "kernel": dom, "flops_per_row": FLOPS_PER_ROW[dom], "avg_launch_ms": avg_s * 1e3}
-    roof["traffic"] = ncu_traffic(dom, args.arith, n)
+    roof = roofline(prof, n, args.arith, peaks, args.block)
     step_s = ms * 1e-3 / args.steps
     hbm_achieved = STEP_BYTES_PER_ROW * n / step_s / 1e9
     roof_hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -344,7 +376,9 @@ def main():
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * n + 8 * args.e2e_inner,
                     "d2h_bytes_per_step": 16 * n, "cn_steps_per_call": args.e2e_inner,
                     "calls": args.e2e_calls},
-            "clocks": clk.summary()}
+            "clocks": clocks}
+    if alt:
+        line["f64_path"] = alt
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle()
     print(json.dumps(line), flush=True)

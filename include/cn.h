@@ -80,11 +80,12 @@ typedef struct {
     double soft_s;           /* CN_POT_SOFTCOULOMB: softening s > 0                          */
     const double* cos_a;     /* CN_POT_COSSERIES: HOST pointer, n_cos doubles (copied)       */
     double L;                /* CN_POT_COSSERIES: period length                              */
-    int32_t block;           /* rows per level-0 block (one GPU thread each): 4, 8 or 16;
+    int32_t block;           /* rows per level-0 block (one GPU thread each): 3..32;
                                 0 = default (8)                                              */
     int32_t arith;           /* cn_arith                                                     */
     int32_t flags;           /* CN_FLAG_* bits                                               */
-    int32_t reserved;        /* must be 0                                                    */
+    int32_t level_block;     /* rows per block on the reduced levels (Eq. iteration): 3..32;
+                                0 = default (8)                                              */
 } cn_desc;
 
 /* cn_desc.flags: tabulate the static part of the diagonal, 2 + 2 dx^2 Vs(x_j),
@@ -92,6 +93,13 @@ typedef struct {
  * level-0 sweep) instead of regenerating it from x_j at every step.  Implied
  * for CN_POT_ARRAY and CN_POT_COSSERIES with CN_ARITH_DF64. */
 #define CN_FLAG_COEFF_TABLE 1
+/* cn_desc.flags: low-memory mode.  By default the level-0 reduction keeps, per
+ * grid point, the explicit right-hand side and the elimination pivot (32 B of
+ * plan workspace per point) so the substitution does not regenerate them and
+ * updates psi in place.  With CN_FLAG_RECOMPUTE the substitution regenerates
+ * both from psi instead, and the plan holds one n-point state buffer (16 B per
+ * point) for the step ping-pong -- for grids whose 32 B per point do not fit. */
+#define CN_FLAG_RECOMPUTE 2
 
 /* Create a plan for systems of size desc->n.  Allocates the device workspace
  * (reduced systems of every nesting level, one state buffer of n complex128,

@@ -23,6 +23,7 @@ from . import _build
 POT_NONE, POT_ARRAY, POT_SOFTCOULOMB, POT_COSSERIES = 0, 1, 2, 3
 ARITH_F64, ARITH_DF64 = 0, 1
 FLAG_COEFF_TABLE = 1
+FLAG_RECOMPUTE = 2
 
 _STATUS = {0: "CN_OK", 1: "CN_ERR_INVALID_ARG", 2: "CN_ERR_UNSUPPORTED", 3: "CN_ERR_OOM", 4: "CN_ERR_CUDA",
            5: "CN_ERR_TIMEOUT", 6: "CN_ERR_NONFINITE"}
@@ -45,7 +46,7 @@ class _Desc(C.Structure):
     _fields_ = [("n", C.c_int64), ("dx", C.c_double), ("dt", C.c_double), ("x_min", C.c_double),
                 ("pot", C.c_int32), ("n_cos", C.c_int32), ("V0", C.c_void_p), ("soft_s", C.c_double),
                 ("cos_a", C.c_void_p), ("L", C.c_double), ("block", C.c_int32), ("arith", C.c_int32),
-                ("flags", C.c_int32), ("reserved", C.c_int32)]
+                ("flags", C.c_int32), ("level_block", C.c_int32)]
 
 
 class _Info(C.Structure):
@@ -125,7 +126,7 @@ class Plan:
     """
 
     def __init__(self, n, dx, dt, x_min, pot=POT_NONE, V0=None, soft_s=2.0, cos_a=None, L=1.0,
-                 block=0, arith=ARITH_F64, flags=0):
+                 block=0, arith=ARITH_F64, flags=0, level_block=0):
         import torch
         self._lib = load()
         self.n = int(n)
@@ -140,7 +141,7 @@ class Plan:
         d = _Desc(self.n, float(dx), float(dt), float(x_min), int(pot),
                   0 if self._cos is None else len(self._cos), v0p, float(soft_s),
                   None if self._cos is None else self._cos.ctypes.data, float(L), int(block), self.arith,
-                  int(flags), 0)
+                  int(flags), int(level_block))
         h = C.c_void_p()
         _check(self._lib.cn_plan_create(C.byref(d), C.byref(h)), "cn_plan_create")
         self._h = h

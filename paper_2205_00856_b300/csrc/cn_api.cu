@@ -15,7 +15,9 @@ using namespace cnb;
 
 namespace {
 
-constexpr int kLevelBlock = 8;  // rows per block on the reduced levels (>= 1)
+constexpr int kDefaultLevelBlock = 8;  // rows per block on the reduced levels (>= 1)
+constexpr int kDefaultBlock = 8;       // rows per level-0 block unless the descriptor says otherwise
+constexpr int kMaxBlockRows = 32;      // shared memory of the substitution: 2 x 32 x 128 x 16 B
 
 struct Level {
     int64_t n = 0;         // rows
@@ -32,7 +34,8 @@ struct cn_plan_s {
     cn_desc desc;
     int device = 0;
     std::vector<Level> lv;     // lv[0]: the system itself; lv[L]: solved by the RS stage
-    double2* state = nullptr;  // n complex128 scratch for the step ping-pong
+    double2* state = nullptr;  // n complex128 scratch for the step ping-pong (recompute mode)
+    void* keep = nullptr;      // 2 n Store<R>::T: explicit rhs and pivot per point (store mode)
     void* tab = nullptr;       // bt0 table (compute type) or NULL
     int* status = nullptr;     // device status word
     CNParams cnp;
@@ -68,9 +71,10 @@ cn_status validate_desc(const cn_desc* d) {
         if (d->n_cos < 0 || d->n_cos > kMaxCos || (d->n_cos > 0 && !d->cos_a) || !(d->L > 0.0))
             return CN_ERR_INVALID_ARG;
     }
-    if (d->block != 0 && d->block != 4 && d->block != 8 && d->block != 16) return CN_ERR_INVALID_ARG;
+    if (d->block != 0 && (d->block < 3 || d->block > kMaxBlockRows)) return CN_ERR_INVALID_ARG;
+    if (d->level_block != 0 && (d->level_block < 3 || d->level_block > kMaxBlockRows)) return CN_ERR_INVALID_ARG;
     if (d->arith != CN_ARITH_F64 && d->arith != CN_ARITH_DF64) return CN_ERR_INVALID_ARG;
-    if ((d->flags & ~CN_FLAG_COEFF_TABLE) != 0 || d->reserved != 0) return CN_ERR_INVALID_ARG;
+    if ((d->flags & ~(CN_FLAG_COEFF_TABLE | CN_FLAG_RECOMPUTE)) != 0) return CN_ERR_INVALID_ARG;
     return CN_OK;
 }
 
@@ -83,6 +87,7 @@ void free_plan_memory(cn_plan p) {
         cudaFree(L.x);
     }
     cudaFree(p->state);
+    cudaFree(p->keep);
     cudaFree(p->tab);
     cudaFree(p->status);
     cudaFree(p->h_in);
@@ -137,28 +142,40 @@ template <class R> LevelSource<R> level_source(const Level& L) {
 }
 
 // --------------------------------------------------------------- launch helpers
-#define CNB_DISPATCH_M(M_, CALL)                    \
-    switch (M_) {                                   \
-    case 4: { constexpr int M = 4; CALL; } break;   \
-    case 8: { constexpr int M = 8; CALL; } break;   \
-    case 16: { constexpr int M = 16; CALL; } break; \
-    default: return cudaErrorInvalidValue;          \
-    }
+// Shared memory of the substitution kernels: per thread, one (kept) or two
+// complex values per block row.
+size_t subst_smem(int m, int arrays) { return (size_t)arrays * (size_t)m * kThreads * 16; }
+size_t kept_smem(int m) { return (size_t)m * kTileStride * 16; }
 
 template <class R, class Src>
 cudaError_t launch_reduce(const Src& src, const Level& L, const Level& next, int* status, cudaStream_t st) {
-    const unsigned grid = grid_for(L.P);
-    CNB_DISPATCH_M(L.m, (k_reduce<R, M, Src><<<grid, kThreads, 0, st>>>(src, L.n, L.P, L.m, rows_of<R>(next),
-                                                                        slot_of<R>(next), status)));
+    k_reduce<R, Src><<<grid_for(L.P), kThreads, 0, st>>>(src, L.n, L.P, L.m, rows_of<R>(next), slot_of<R>(next),
+                                                         status);
     return cudaGetLastError();
 }
 
 template <class R, class Src, class XT>
 cudaError_t launch_substitute(const Src& src, const Level& L, const Level& next, XT* x, int* status, cudaStream_t st) {
-    const unsigned grid = grid_for(L.P);
-    CNB_DISPATCH_M(L.m, (k_substitute<R, M, Src, XT><<<grid, kThreads, 0, st>>>(src, L.n, L.P, L.m, x_of<R>(next), x,
-                                                                                status)));
+    k_substitute<R, Src, XT><<<grid_for(L.P), kThreads, subst_smem(L.m, 2), st>>>(src, L.n, L.P, L.m, x_of<R>(next),
+                                                                                  x, status);
     return cudaGetLastError();
+}
+
+// Opt every substitution kernel into the dynamic shared memory its largest block needs.
+template <class R>
+cudaError_t set_smem_limits(int m0, int ml) {
+    cudaError_t e = cudaFuncSetAttribute(k_substitute<R, ArraySource, double2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)subst_smem(m0, 2));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_substitute<R, LevelSource<R>, typename Store<R>::T>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)subst_smem(ml, 2));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cn_substitute<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)subst_smem(m0, 2));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cn_substitute_kept<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kept_smem(m0));
+    return e;
 }
 
 // Levels 1..L of the nested solve: reductions down, RS, substitutions up.
@@ -205,18 +222,21 @@ cudaError_t cn_solve(cn_plan p, const CNStep& s, double2* x, cudaStream_t st) {
     const Level& L0 = p->lv[0];
     const Level& L1 = p->lv[1];
     const unsigned grid = grid_for(L0.P);
+    typedef typename Store<R>::T ST;
+    ST* keep = static_cast<ST*>(p->keep);
     cudaError_t e;
     {
         ProfScope ps(p, kProfReduce0, st);
-        CNB_DISPATCH_M(L0.m, (k_cn_reduce<R, M><<<grid, kThreads, 0, st>>>(s, L0.P, L0.m, rows_of<R>(L1),
-                                                                           slot_of<R>(L1), p->status)));
+        k_cn_reduce<R><<<grid, kThreads, 0, st>>>(s, L0.P, L0.m, rows_of<R>(L1), slot_of<R>(L1), keep, p->status);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
     if ((e = solve_levels<R>(p, st)) != cudaSuccess) return e;
     ProfScope ps(p, kProfSubst0, st);
-    CNB_DISPATCH_M(L0.m, (k_cn_substitute<R, M><<<grid, kThreads, 0, st>>>(s, L0.P, L0.m, x_of<R>(L1), x,
-                                                                           p->status)));
+    if (keep)
+        k_cn_substitute_kept<R><<<grid, kThreads, kept_smem(L0.m), st>>>(L0.n, L0.P, L0.m, keep, x_of<R>(L1), x);
+    else
+        k_cn_substitute<R><<<grid, kThreads, subst_smem(L0.m, 2), st>>>(s, L0.P, L0.m, x_of<R>(L1), x, p->status);
     return cudaGetLastError();
 }
 
@@ -228,21 +248,24 @@ cudaError_t cn_steps(cn_plan p, const double2* in, double2* out, const double* E
         if (in == out) return cudaSuccess;
         return cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st);
     }
-    // Step k writes dest(k); the last step writes out; in is never written
-    // unless it is out.  Destinations alternate between out and the scratch.
+    const bool kept = p->keep != nullptr;
+    // Store mode: the substitution does not read psi, so every step after the
+    // first updates out in place.  Recompute mode: step k writes dest(k), the
+    // last step writes out, destinations alternate between out and the
+    // scratch, and in is never written unless it is out.
     const double2* src = in;
-    if (in == out && ((nsteps - 1) % 2) == 0) {
+    if (!kept && in == out && ((nsteps - 1) % 2) == 0) {
         cudaError_t e = cudaMemcpyAsync(p->state, in, bytes, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
         src = p->state;
     }
     for (int64_t k = 0; k < nsteps; ++k) {
-        double2* dst = (((nsteps - 1 - k) % 2) == 0) ? out : p->state;
+        double2* dst = kept ? out : ((((nsteps - 1 - k) % 2) == 0) ? out : p->state);
         CNStep s;
         s.p = p->cnp;
         s.psi = src;
-        s.s = 1.0;
-        s.e = -1.0;
+        s.s = 1;
+        s.e = -1;
         s.E_t = E_mid ? E_mid + k : nullptr;
         s.E_e = s.E_t;
         s.tab = p->tab;
@@ -272,7 +295,7 @@ const char* cn_status_string(cn_status s) {
     }
 }
 
-const char* cn_version(void) { return "cn_b300 0.2 sm_103a"; }
+const char* cn_version(void) { return "cn_b300 0.4 sm_103a"; }
 
 cn_status cn_plan_create(const cn_desc* desc, cn_plan* out) {
     if (!out) return CN_ERR_INVALID_ARG;
@@ -282,7 +305,8 @@ cn_status cn_plan_create(const cn_desc* desc, cn_plan* out) {
     cn_plan p = new (std::nothrow) cn_plan_s();
     if (!p) return CN_ERR_OOM;
     p->desc = *desc;
-    if (p->desc.block == 0) p->desc.block = 8;
+    if (p->desc.block == 0) p->desc.block = kDefaultBlock;
+    if (p->desc.level_block == 0) p->desc.level_block = kDefaultLevelBlock;
     if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return CN_ERR_CUDA; }
     if (desc->pot == CN_POT_COSSERIES && desc->n_cos > 0) p->cos_a.assign(desc->cos_a, desc->cos_a + desc->n_cos);
     p->desc.cos_a = nullptr;
@@ -300,7 +324,7 @@ cn_status cn_plan_create(const cn_desc* desc, cn_plan* out) {
         L.P = ceil_div(n - 1, m);
         p->lv.push_back(L);
         n = L.P + 1;
-        m = kLevelBlock;
+        m = p->desc.level_block;
         if (n <= kBaseMax) {
             Level B;
             B.n = n;
@@ -319,8 +343,12 @@ cn_status cn_plan_create(const cn_desc* desc, cn_plan* out) {
         if (e == cudaSuccess) e = cudaMalloc(&L.x, cplx * (size_t)L.n);
         if (e == cudaSuccess) e = cudaMemset(L.slot, 0, 3 * cplx * nslot);
     }
-    p->workspace_bytes += (int64_t)(cplx * desc->n + sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&p->state, cplx * (size_t)desc->n);
+    const bool recompute = (desc->flags & CN_FLAG_RECOMPUTE) != 0;
+    // keep: entries (2k) P + t and (2k+1) P + t for block rows k = 1..m-1
+    const size_t keep_entries = 2 * (size_t)p->lv[0].m * (size_t)p->lv[0].P;
+    p->workspace_bytes += (int64_t)(recompute ? cplx * desc->n : cplx * keep_entries) + (int64_t)sizeof(int);
+    if (e == cudaSuccess && recompute) e = cudaMalloc(&p->state, cplx * (size_t)desc->n);
+    if (e == cudaSuccess && !recompute) e = cudaMalloc(&p->keep, cplx * keep_entries);
     if (e == cudaSuccess) e = cudaMalloc(&p->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(int));
     if (e == cudaSuccess && use_table) {
@@ -340,6 +368,19 @@ cn_status cn_plan_create(const cn_desc* desc, cn_plan* out) {
     c.n_cos = desc->pot == CN_POT_COSSERIES ? desc->n_cos : 0;
     c.two_pi_over_L = desc->pot == CN_POT_COSSERIES ? 2.0 * 3.14159265358979323846 / desc->L : 0.0;
     for (int k = 0; k < c.n_cos; ++k) c.cos_a[k] = p->cos_a[(size_t)k];
+    auto split = [](double v) { df d = df_from_double(v); DFc r; r.hi = d.hi; r.lo = d.lo; return r; };
+    c.dx_f = split(c.dx);
+    c.c1_f = split(c.c1);
+    c.gt_f = split(c.gt);
+    c.soft_f = split(c.soft_s);
+    {
+        double jo = std::nearbyint(-desc->x_min / desc->dx);
+        if (jo < 0) jo = 0;
+        if (jo > (double)(desc->n - 1)) jo = (double)(desc->n - 1);
+        c.j_o = (int64_t)jo;
+        c.x_o = desc->x_min + (double)c.j_o * desc->dx;
+        c.xo_f = split(c.x_o);
+    }
     if (e == cudaSuccess && use_table) {
         const unsigned grid = (unsigned)ceil_div(desc->n, 256);
         if (df_mode) k_beta0_table<df><<<grid, 256>>>(c, static_cast<df*>(p->tab));
@@ -347,6 +388,9 @@ cn_status cn_plan_create(const cn_desc* desc, cn_plan* out) {
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
+    if (e == cudaSuccess)
+        e = df_mode ? set_smem_limits<df>(p->desc.block, p->desc.level_block)
+                    : set_smem_limits<double>(p->desc.block, p->desc.level_block);
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_plan_memory(p);

@@ -6,19 +6,29 @@
 // the rows 0..n-1 of a level are cut into blocks by the joint lines
 //   J_t = min(t m, n - 1 - 2 (P - t)),  t = 0..P,  P = ceil((n - 1) / m),
 // so every block spans 2..m rows between its joint lines (at least one
-// interior row).  One GPU thread owns one block and runs Table 1 on it in
-// registers, in the order (RD + JD) + (RU + JU) of Sec. 5.2.1.  The two
-// contributions every joint line receives (the paper's atomic additions) are
-// exchanged through shared memory, or through a per-CTA slot in global memory
-// for the first row of each CTA range, and added in a fixed order (the "two
-// extra memory elements per joint line" of Sec. 4.1.3), so every result is
-// deterministic.  The joint lines form the reduced tridiagonal system of the
-// next level, which is reduced again by the same kernels (Eq. iteration) until
-// it is small enough for the serial RS stage (Table 1).  The SS stage then
-// returns level by level.  Instead of keeping the RD/RU fill-in columns in
-// memory between the two passes (the paper keeps all 5 n vectors in place),
-// the substitution kernel re-solves each block's interior rows with its two
-// support values as Dirichlet data (the same equations SS evaluates, Fig. 1f).
+// interior row).  One GPU thread owns one block and runs Table 1 on it, in the
+// order (RD + JD) + (RU + JU) of Sec. 5.2.1.
+//
+// RU is a linear recurrence over the RD results, and JU reads only its value
+// on the first interior row.  Written out, RU leaves on row 1
+//   b_1 = sum_k Q_k b_k^RD,  d_1 = sum_k Q_k d_k^RD,  c_1 = Q_{g-1} c_{g-1},
+//   Q_1 = 1,  Q_k = Q_{k-1} rho_{k-1},  rho_k = -c_k / a_{k+1}^RD,
+// and every term is known as soon as RD has passed row k.  The kernels
+// therefore accumulate RU + JU during the RD sweep: one downward pass, no
+// per-row storage (so blocks can be long and the loops stay rolled), and the
+// same reduced system as the upward sweep of Table 1.
+//
+// The two contributions every joint line receives (the paper's atomic
+// additions) are exchanged through shared memory, or through a per-CTA slot
+// in global memory for the first row of each CTA range, and added in a fixed
+// order (the "two extra memory elements per joint line" of Sec. 4.1.3), so
+// every result is deterministic.  The joint lines form the reduced
+// tridiagonal system of the next level, which is reduced again by the same
+// kernels (Eq. iteration) until it is small enough for the serial RS stage.
+// The SS stage then returns level by level: each block's interior rows, with
+// the two support values as Dirichlet data, are the equations SS evaluates
+// (Fig. 1f); the kernels solve them by the block's forward pivots and a
+// back-substitution.
 //
 // Level 0 of a Crank-Nicolson step never reads a matrix: it regenerates the
 // diagonal of T = 1 + i dt/2 H(t + dt/2) from V(x) and E(t + dt/2) and forms the
@@ -34,9 +44,10 @@
 
 namespace cnb {
 
-constexpr int kThreads = 128;  // threads per CTA of the reduce / substitute kernels
-constexpr int kMaxCos = 16;    // cos-series terms held in the kernel parameters
-constexpr int kBaseMax = 16;   // largest reduced system solved by the serial RS stage
+constexpr int kThreads = 128;   // threads per CTA of the reduce / substitute kernels
+constexpr int kMaxCos = 16;     // cos-series terms held in the kernel parameters
+constexpr int kBaseMax = 16;    // largest reduced system solved by the serial RS stage
+constexpr int kMaxBlock = 64;   // largest block (rows between joint lines)
 
 // joint line t of a level with n rows, block size m and P blocks
 __host__ __device__ __forceinline__ int64_t joint_line(int64_t t, int64_t P, int64_t m, int64_t n) {
@@ -45,22 +56,6 @@ __host__ __device__ __forceinline__ int64_t joint_line(int64_t t, int64_t P, int
 }
 
 constexpr int kStatusNonfinite = 6;  // cn_status CN_ERR_NONFINITE
-
-// Row predicates of a block with gap g (rows 0..g) as bit masks.  Loops over
-// the rows are fully unrolled and test bits instead of comparing k with g: a
-// comparison lets the compiler shorten the loop to a run-time trip count,
-// which stops the unrolling and moves the per-row arrays to local memory.
-struct RowMask {
-    unsigned all;      // rows 0..g
-    unsigned inner;    // interior rows 1..g-1
-    unsigned last_in;  // row g-1
-    unsigned ru;       // rows 1..g-2 (RU rows)
-    unsigned joint1;   // row g
-    __device__ __forceinline__ explicit RowMask(int g)
-        : all((2u << g) - 1u), inner((1u << g) - 2u), last_in(1u << (g - 1)), ru((1u << (g - 1)) - 2u),
-          joint1(1u << g) {}
-};
-__device__ __forceinline__ bool bit(unsigned m, int k) { return (m >> k) & 1u; }
 
 __device__ __forceinline__ void flag_error(int* status, int code) {
     if (status) atomicCAS(status, 0, code);
@@ -77,30 +72,24 @@ template <class R> struct LevelSlot {
 template <class R> struct JDPart {
     cx<R> b, a, d;
 };
+template <class R> struct Row {
+    cx<R> b, a, c, d;
+};
 
-// ------------------------------------------------------------------ generic sources
-// A source yields rows k = k0..k1 (k0 = 0 or 1, k1 = g or g-1) of the block
-// starting at J0: lower b_k, diagonal a_k, upper c_k, rhs d_k, with b = 0 on
-// row 0 of the level and c = 0 on its last row.
-
-// General tridiagonal system in four complex128 arrays (cn_solve_tridiag).
+// ------------------------------------------------------------------ generic rows
+// General tridiagonal system in four complex128 arrays (cn_solve_tridiag);
+// b_0 and c_{n-1} are taken as 0.
 struct ArraySource {
     const double2 *b, *a, *c, *d;
     int64_t n;
-    template <class R, int M, bool kInterior>
-    __device__ __forceinline__ void load(int64_t J0, int g, cx<R>* B, cx<R>* A, cx<R>* C, cx<R>* D) const {
-        const RowMask rm(g);
-        const unsigned use = kInterior ? rm.inner : rm.all;
-#pragma unroll
-        for (int k = kInterior ? 1 : 0; k <= M; ++k) {
-            if (bit(use, k)) {
-                int64_t i = J0 + k;
-                B[k] = (i > 0) ? load128<R>(b + i) : czero<R>();
-                A[k] = load128<R>(a + i);
-                C[k] = (i < n - 1) ? load128<R>(c + i) : czero<R>();
-                D[k] = load128<R>(d + i);
-            }
-        }
+    template <class R>
+    __device__ __forceinline__ Row<R> row(int64_t i) const {
+        Row<R> r;
+        r.b = (i > 0) ? load128<R>(b + i) : czero<R>();
+        r.a = load128<R>(a + i);
+        r.c = (i < n - 1) ? load128<R>(c + i) : czero<R>();
+        r.d = load128<R>(d + i);
+        return r;
     }
 };
 
@@ -111,26 +100,21 @@ template <class R> struct LevelSource {
     const LevelSlot<R>* slot;
     int64_t n;            // rows of this level
     int64_t slot_stride;  // rows per CTA range of the producing kernel
-    template <class RR, int M, bool kInterior>
-    __device__ __forceinline__ void load(int64_t J0, int g, cx<R>* B, cx<R>* A, cx<R>* C, cx<R>* D) const {
-        const unsigned use = (M == 0) ? 1u : (kInterior ? RowMask(g).inner : RowMask(g).all);
-#pragma unroll
-        for (int k = kInterior ? 1 : 0; k <= M; ++k) {
-            if (bit(use, k)) {
-                int64_t i = J0 + k;
-                const LevelRow<R>* r = rows + i;
-                B[k] = sload(&r->b);
-                A[k] = sload(&r->a);
-                C[k] = sload(&r->c);
-                D[k] = sload(&r->d);
-                if (i > 0 && i < n - 1 && (i % slot_stride) == 0) {
-                    const LevelSlot<R>* s = slot + i / slot_stride;
-                    B[k] = sload(&s->b);
-                    A[k] = cadd(A[k], sload(&s->a));
-                    D[k] = cadd(D[k], sload(&s->d));
-                }
-            }
+    template <class RR>
+    __device__ __forceinline__ Row<R> row(int64_t i) const {
+        const LevelRow<R>* p = rows + i;
+        Row<R> r;
+        r.b = sload(&p->b);
+        r.a = sload(&p->a);
+        r.c = sload(&p->c);
+        r.d = sload(&p->d);
+        if (i > 0 && i < n - 1 && (i % slot_stride) == 0) {
+            const LevelSlot<R>* s = slot + i / slot_stride;
+            r.b = sload(&s->b);
+            r.a = cadd(r.a, sload(&s->a));
+            r.d = cadd(r.d, sload(&s->d));
         }
+        return r;
     }
 };
 
@@ -178,8 +162,8 @@ __device__ __forceinline__ void write_reduced_row(bool active, int64_t t, int64_
 }
 
 // ------------------------------------------------------------------ generic reduction
-// One thread per block: Table 1 RD + JD, then RU + JU.
-template <class R, int M, class Src>
+// One thread per block: RD + JD downwards with RU + JU accumulated on the way.
+template <class R, class Src>
 __global__ void __launch_bounds__(kThreads)
 k_reduce(Src src, int64_t n, int64_t P, int m, LevelRow<R>* out, LevelSlot<R>* out_slot, int* status) {
     const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -192,107 +176,98 @@ k_reduce(Src src, int64_t n, int64_t P, int m, LevelRow<R>* out, LevelSlot<R>* o
     if (active) {
         const int64_t J0 = joint_line(t, P, m, n);
         const int g = (int)(joint_line(t + 1, P, m, n) - J0);
-        const RowMask rm(g);
-        cx<R> B[M + 1], A[M + 1], C[M + 1], D[M + 1], W[M + 1];
-        src.template load<R, M, false>(J0, g, B, A, C, D);
-        A0 = A[0];
-        D0 = D[0];
-        // RD: r_k = -b_k / a_{k-1}; b_k = r b_{k-1}; a_k += r c_{k-1}; d_k += r d_{k-1}
-        W[1] = crcp(A[1], ok);
-#pragma unroll
-        for (int k = 2; k < M; ++k) {
-            if (bit(rm.inner, k)) {
-                cx<R> r = cneg(cmul(B[k], W[k - 1]));
-                B[k] = cmul(r, B[k - 1]);
-                A[k] = cfma(A[k], r, C[k - 1]);
-                D[k] = cfma(D[k], r, D[k - 1]);
-                W[k] = crcp(A[k], ok);
-            }
+        const Row<R> r0 = src.template row<R>(J0);
+        A0 = r0.a;
+        D0 = r0.d;
+        // row 1: untouched by RD
+        const Row<R> r1 = src.template row<R>(J0 + 1);
+        cx<R> w = crcp(r1.a, ok);       // 1 / a_k^RD of the previous row
+        const cx<R> w1 = w;
+        cx<R> bRD = r1.b, dRD = r1.d;   // RD fill-in column J0 and rhs of the previous row
+        cx<R> cprev = r1.c;             // upper diagonal of the previous row
+        cx<R> Q = cfrom<R>(1.0, 0.0);   // prod_{i<k} rho_i
+        cx<R> nb = bRD, nd = dRD;       // RU values accumulated on row 1
+        Row<R> nxt = src.template row<R>(J0 + 2);  // one row ahead (row g when g == 2)
+        for (int k = 2; k < g; ++k) {
+            const Row<R> rk = nxt;
+            nxt = src.template row<R>(J0 + k + 1);
+            // RD: r = -b_k / a_{k-1};  b_k = r b_{k-1};  a_k += r c_{k-1};  d_k += r d_{k-1}
+            const cx<R> r = cneg(cmul(rk.b, w));
+            bRD = cmul(r, bRD);
+            dRD = cfma(rk.d, r, dRD);
+            const cx<R> wk = crcp(cfma(rk.a, r, cprev), ok);
+            // RU coefficient of row k-1: rho_{k-1} = -c_{k-1} / a_k
+            Q = cmul(Q, cneg(cmul(cprev, wk)));
+            nb = cfma(nb, Q, bRD);
+            nd = cfma(nd, Q, dRD);
+            w = wk;
+            cprev = rk.c;
         }
-        // JD on row J_{t+1} (k = g)
-#pragma unroll
-        for (int k = 2; k <= M; ++k) {
-            if (bit(rm.joint1, k)) {
-                cx<R> r = cneg(cmul(B[k], W[k - 1]));
-                jd.b = cmul(r, B[k - 1]);
-                jd.a = cmul(r, C[k - 1]);
-                jd.d = cmul(r, D[k - 1]);
-                Ag = A[k];
-                Dg = D[k];
-            }
-        }
-        // RU: r_k = -c_k / a_{k+1}; b_k += r b_{k+1}; c_k = r c_{k+1}; d_k += r d_{k+1}
-        cx<R> nb = czero<R>(), nc = czero<R>(), nd = czero<R>();
-#pragma unroll
-        for (int k = M - 1; k >= 1; --k) {
-            if (bit(rm.last_in, k)) {
-                nb = B[k]; nc = C[k]; nd = D[k];
-            } else if (bit(rm.ru, k)) {
-                cx<R> r = cneg(cmul(C[k], W[k + 1]));
-                nb = cfma(B[k], r, nb);
-                nc = cmul(r, nc);
-                nd = cfma(D[k], r, nd);
-            }
-        }
-        // JU on row J_t (k = 0) with row 1 after RU
-        cx<R> r = cneg(cmul(C[0], W[1]));
-        JUc = cmul(r, nc);
-        JUa = cmul(r, nb);
-        JUd = cmul(r, nd);
+        const cx<R> nc = cmul(Q, cprev);  // c_1 after RU = Q_{g-1} c_{g-1}
+        // JD on row J_{t+1}: r = -b_g / a_{g-1};  b = r b_{g-1};  a += r c_{g-1};  d += r d_{g-1}
+        const Row<R> rg = nxt;
+        const cx<R> r = cneg(cmul(rg.b, w));
+        jd.b = cmul(r, bRD);
+        jd.a = cmul(r, cprev);
+        jd.d = cmul(r, dRD);
+        Ag = rg.a;
+        Dg = rg.d;
+        // JU on row J_t with row 1 after RU: r = -c_0 / a_1
+        const cx<R> r0u = cneg(cmul(r0.c, w1));
+        JUc = cmul(r0u, nc);
+        JUa = cmul(r0u, nb);
+        JUd = cmul(r0u, nd);
     }
     write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, out, out_slot);
     if (!ok) flag_error(status, kStatusNonfinite);
 }
 
 // ------------------------------------------------------------------ generic substitution
-// One thread per block: the interior rows with the support values xL (row 0)
-// and xR (row g) known form a tridiagonal system, solved by Thomas (Sec. 2).
+// One thread per block: the interior rows 1..g-1 with the support values xL
+// (row 0) and xR (row g) known form a tridiagonal system, solved by Thomas
+// (Sec. 2).  The forward values z_k and c'_k wait in shared memory, one slice
+// per thread (index k * kThreads + tid: consecutive threads, consecutive words).
 template <class XT, class R> __device__ __forceinline__ void put(XT* p, cx<R> z);
 template <> __device__ __forceinline__ void put<double2, double>(double2* p, cx<double> z) { store128(p, z); }
 template <> __device__ __forceinline__ void put<double2, df>(double2* p, cx<df> z) { store128(p, z); }
 template <> __device__ __forceinline__ void put<float4, df>(float4* p, cx<df> z) { sstore(p, z); }
 
-template <class R, int M, class Src, class XT>
+template <class R, class Src, class XT>
 __global__ void __launch_bounds__(kThreads)
 k_substitute(Src src, int64_t n, int64_t P, int m, const typename Store<R>::T* x_next, XT* x, int* status) {
-    const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    typedef typename Store<R>::T ST;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ST* zs = reinterpret_cast<ST*>(smem_raw);   // [m][kThreads]
+    ST* cs = zs + (size_t)m * kThreads;         // [m][kThreads]
+    const int tid = threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * kThreads + tid;
     if (t >= P) return;
     bool ok = true;
     const int64_t J0 = joint_line(t, P, m, n);
     const int g = (int)(joint_line(t + 1, P, m, n) - J0);
-    const RowMask rm(g);
-    cx<R> B[M + 1], A[M + 1], C[M + 1], D[M + 1];
-    src.template load<R, M, true>(J0, g, B, A, C, D);
     const cx<R> xL = sload(x_next + t);
     const cx<R> xR = sload(x_next + t + 1);
-    cx<R> Z[M + 1], CP[M + 1];
     cx<R> zp = czero<R>(), cpp = czero<R>();
-#pragma unroll
-    for (int k = 1; k < M + 1; ++k) {
-        if (bit(rm.inner, k)) {
-            cx<R> rhs = D[k];
-            if (k == 1) rhs = csub(rhs, cmul(B[1], xL));
-            if (bit(rm.last_in, k)) rhs = csub(rhs, cmul(C[k], xR));
-            cx<R> piv = (k == 1) ? A[1] : csub(A[k], cmul(B[k], cpp));
-            cx<R> w = crcp(piv, ok);
-            cx<R> z = (k == 1) ? cmul(rhs, w) : cmul(csub(rhs, cmul(B[k], zp)), w);
-            cx<R> cp = cmul(C[k], w);
-            Z[k] = z;
-            CP[k] = cp;
-            zp = z;
-            cpp = cp;
-        }
+    Row<R> nxt = src.template row<R>(J0 + 1);
+    for (int k = 1; k < g; ++k) {
+        const Row<R> rk = nxt;
+        if (k + 1 < g) nxt = src.template row<R>(J0 + k + 1);
+        cx<R> rhs = rk.d;
+        if (k == 1) rhs = csub(rhs, cmul(rk.b, xL));
+        if (k == g - 1) rhs = csub(rhs, cmul(rk.c, xR));
+        // m_k = a_k - b_k c'_{k-1};  z_k = (rhs_k - b_k z_{k-1}) / m_k;  c'_k = c_k / m_k
+        const cx<R> piv = (k == 1) ? rk.a : csub(rk.a, cmul(rk.b, cpp));
+        const cx<R> w = crcp(piv, ok);
+        zp = (k == 1) ? cmul(rhs, w) : cmul(csub(rhs, cmul(rk.b, zp)), w);
+        cpp = cmul(rk.c, w);
+        sstore(zs + k * kThreads + tid, zp);
+        sstore(cs + k * kThreads + tid, cpp);
     }
-    cx<R> y = czero<R>();
-#pragma unroll
-    for (int k = M; k >= 1; --k) {
-        if (bit(rm.last_in, k)) {
-            y = Z[k];
-            put<XT, R>(x + J0 + k, y);
-        } else if (bit(rm.ru, k)) {
-            y = csub(Z[k], cmul(CP[k], y));
-            put<XT, R>(x + J0 + k, y);
-        }
+    cx<R> y = zp;
+    put<XT, R>(x + J0 + g - 1, y);
+    for (int k = g - 2; k >= 1; --k) {
+        y = csub(sload(zs + k * kThreads + tid), cmul(sload(cs + k * kThreads + tid), y));
+        put<XT, R>(x + J0 + k, y);
     }
     put<XT, R>(x + J0, xL);
     if (t == P - 1) put<XT, R>(x + J0 + g, xR);
@@ -308,16 +283,16 @@ __global__ void k_base(LevelSource<R> src, int64_t n, typename Store<R>::T* x, i
     cx<R> a_prev = czero<R>(), c_prev = czero<R>(), d_prev = czero<R>();
     cx<R> A[kBaseMax], C[kBaseMax], D[kBaseMax];
     for (int64_t w = 0; w < n; ++w) {
-        cx<R> b, a, c, d;
-        src.template load<R, 0, false>(w, 0, &b, &a, &c, &d);
+        Row<R> rw = src.template row<R>(w);
+        cx<R> a = rw.a, d = rw.d;
         if (w > 0) {
             // r = -b_w / a_{w-1};  a_w += r c_{w-1};  d_w += r d_{w-1}
-            cx<R> r = cneg(cmul(b, crcp(a_prev, ok)));
+            cx<R> r = cneg(cmul(rw.b, crcp(a_prev, ok)));
             a = cfma(a, r, c_prev);
             d = cfma(d, r, d_prev);
         }
-        A[w] = a; C[w] = c; D[w] = d;
-        a_prev = a; c_prev = c; d_prev = d;
+        A[w] = a; C[w] = rw.c; D[w] = d;
+        a_prev = a; c_prev = rw.c; d_prev = d;
     }
     cx<R> y = cmul(D[n - 1], crcp(A[n - 1], ok));
     sstore(x + n - 1, y);
@@ -329,6 +304,9 @@ __global__ void k_base(LevelSource<R> src, int64_t n, typename Store<R>::T* x, i
 }
 
 // ------------------------------------------------------------------ CN level 0
+struct DFc {
+    float hi, lo;  // a binary64 constant split on the host into double-float words
+};
 struct CNParams {
     int64_t n;
     double dx, x_min;
@@ -340,7 +318,15 @@ struct CNParams {
     double soft_s;
     double two_pi_over_L;
     double cos_a[kMaxCos];
+    DFc dx_f, c1_f, gt_f, soft_f;  // the same constants for the double-float kernels
+    // Grid coordinates are formed as x_j = x_o + (j - j_o) dx around the grid point
+    // j_o nearest x = 0 (x_o = x_min + j_o dx, on the host): x_min + j dx directly
+    // would cancel two ~|x_min| terms near the origin, where the state lives.
+    int64_t j_o;
+    double x_o;
+    DFc xo_f;
 };
+__device__ __forceinline__ df dfc(DFc c) { return df_make(c.hi, c.lo); }
 
 // Static potential Vs(x_j) in binary64 (the FP64 path and the table builder).
 __device__ __forceinline__ double static_potential_d(const CNParams& p, int64_t j, double x) {
@@ -362,11 +348,11 @@ template <class R>
 __global__ void k_beta0_table(CNParams p, R* tab) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= p.n) return;
-    double x = fma((double)j, p.dx, p.x_min);
+    double x = fma((double)(j - p.j_o), p.dx, p.x_o);
     tab[j] = RealOps<R>::from_d(fma(p.c1, static_potential_d(p, j, x), 2.0));
 }
 
-// Per-thread coefficient generator walking rows J0, J0+1, ...: returns bt_j for
+// Per-thread coefficient generator walking rows j0, j0+1, ...: returns bt_j for
 // the field values E_t (implicit matrix) and E_e (explicit matrix).
 template <class R> struct CoefGen;
 
@@ -375,20 +361,20 @@ template <> struct CoefGen<double> {
     const double* tab;
     double c1Et, c1Ee, x;
     int64_t j;
+    __device__ __forceinline__ double xj(int64_t jj) const { return fma((double)(jj - p->j_o), p->dx, p->x_o); }
     __device__ __forceinline__ void init(const CNParams& pp, const double* tb, double Et, double Ee, int64_t j0) {
         p = &pp; tab = tb; j = j0;
         c1Et = pp.c1 * Et; c1Ee = pp.c1 * Ee;
-        x = fma((double)j0, pp.dx, pp.x_min);
+        x = xj(j0);
     }
-    // bt for row j (then advance)
     __device__ __forceinline__ void next(double& bt_t, double& bt_e) {
         double b0 = tab ? tab[j] : fma(p->c1, static_potential_d(*p, j, x), 2.0);
         bt_t = fma(c1Et, x, b0);
         bt_e = (c1Ee == c1Et) ? bt_t : fma(c1Ee, x, b0);
         ++j;
-        x = fma((double)j, p->dx, p->x_min);
+        x = xj(j);
     }
-    __device__ __forceinline__ void skip() { ++j; x = fma((double)j, p->dx, p->x_min); }
+    __device__ __forceinline__ void skip() { ++j; x = xj(j); }
 };
 
 template <> struct CoefGen<df> {
@@ -397,18 +383,20 @@ template <> struct CoefGen<df> {
     int pot;
     bool same;  // E_e == E_t: one diagonal serves both matrices
     int64_t j;
+    // All binary64 constants arrive pre-split (DFc); the fields are converted
+    // with integer operations, so no FP64-pipe instruction runs here.
     __device__ __forceinline__ void init(const CNParams& pp, const df* tb, double Et, double Ee, int64_t j0) {
         tab = tb; j = j0; pot = pp.pot;
-        same = (Et == Ee);
-        c1Et = df_from_double(pp.c1 * Et);
-        c1Ee = df_from_double(pp.c1 * Ee);
-        dx = df_from_double(pp.dx);
-        c1 = df_from_double(pp.c1);
-        soft_s = df_from_double(pp.soft_s);
-        // x_j0 = x_min + j0 dx with j0 = hi 2^16 + lo split into exact binary32 parts
-        df xm = df_from_double(pp.x_min);
-        float jh = (float)(j0 >> 16), jl = (float)(j0 & 0xFFFF);
-        x = df_add(xm, df_add(df_mul_f(df_mul_f(dx, jh), 65536.0f), df_mul_f(dx, jl)));
+        same = d_bits(Et) == d_bits(Ee);
+        dx = dfc(pp.dx_f);
+        c1 = dfc(pp.c1_f);
+        soft_s = dfc(pp.soft_f);
+        c1Et = df_mul(c1, df_from_double(Et));
+        c1Ee = same ? c1Et : df_mul(c1, df_from_double(Ee));
+        // x_j0 = x_o + (j0 - j_o) dx with j0 - j_o = hi 2^16 + lo split into exact binary32 parts
+        const int64_t dj = j0 - pp.j_o;
+        float jh = i2f((int32_t)(dj >> 16)), jl = i2f((int32_t)(dj & 0xFFFF));
+        x = df_add(dfc(pp.xo_f), df_add(df_mul_f(df_mul_f(dx, jh), 65536.0f), df_mul_f(dx, jl)));
     }
     __device__ __forceinline__ void next(df& bt_t, df& bt_e) {
         df b0;
@@ -430,13 +418,14 @@ template <> struct CoefGen<df> {
 };
 
 // Scaled explicit row: d^ = (e s)(bt_e psi - sigma) - i s g~ psi, sigma = psi_{j-1} + psi_{j+1}.
-__device__ __forceinline__ cx<double> explicit_row(cx<double> pm, cx<double> p0, cx<double> pp, double bte,
-                                                   double es, double sg) {
+__device__ __forceinline__ cx<double> explicit_row(cx<double> pm, cx<double> p0, cx<double> pp, double bte, int es,
+                                                   double sg) {
     double sr = pm.re + pp.re, si = pm.im + pp.im;
-    double eb = es * bte;
-    return mk(fma(eb, p0.re, fma(sg, p0.im, -es * sr)), fma(eb, p0.im, fma(-sg, p0.re, -es * si)));
+    double eb = es > 0 ? bte : -bte;
+    if (es > 0) { sr = -sr; si = -si; }
+    return mk(fma(eb, p0.re, fma(sg, p0.im, sr)), fma(eb, p0.im, fma(-sg, p0.re, si)));
 }
-__device__ __forceinline__ cx<df> explicit_row(cx<df> pm, cx<df> p0, cx<df> pp, df bte, double es, df sg) {
+__device__ __forceinline__ cx<df> explicit_row(cx<df> pm, cx<df> p0, cx<df> pp, df bte, int es, df sg) {
     df sr = df_add(pm.re, pp.re), si = df_add(pm.im, pp.im);
     df eb = es > 0 ? bte : df_neg(bte);
     df nsr = es > 0 ? df_neg(sr) : sr;
@@ -444,31 +433,85 @@ __device__ __forceinline__ cx<df> explicit_row(cx<df> pm, cx<df> p0, cx<df> pp, 
     return mk(df_dot2_add(nsr, eb, p0.re, sg, p0.im), df_dot2_add(nsi, eb, p0.im, df_neg(sg), p0.re));
 }
 
-template <class R> struct CNTypes;
-template <> struct CNTypes<double> { typedef double real; };
-template <> struct CNTypes<df> { typedef df real; };
-
 // Level-0 CN source: sign s of the implicit matrix, sign e of the explicit one,
 // fields read from device memory (NULL: 0).
 struct CNStep {
     CNParams p;
     const double2* psi;   // state the explicit half-step is applied to
-    double s, e;          // T_s = 1 + i s dt/2 H(E_t);  explicit S_e = 1 + i e dt/2 H(E_e)
+    int s, e;             // T_s = 1 + i s dt/2 H(E_t);  explicit S_e = 1 + i e dt/2 H(E_e)
     const double* E_t;
     const double* E_e;
     const void* tab;      // bt0 table in the compute type, or NULL (regenerate)
 };
 
-template <class R>
-__device__ __forceinline__ R rconst(double v);
-template <> __device__ __forceinline__ double rconst<double>(double v) { return v; }
-template <> __device__ __forceinline__ df rconst<df>(double v) { return df_from_double(v); }
+__device__ __forceinline__ double rneg(double a) { return -a; }
+__device__ __forceinline__ df rneg(df a) { return df_neg(a); }
+
+// s g~ in the compute type
+__device__ __forceinline__ double signed_gt(const CNStep& st, double) { return st.s > 0 ? st.p.gt : -st.p.gt; }
+__device__ __forceinline__ df signed_gt(const CNStep& st, df) {
+    df g = dfc(st.p.gt_f);
+    return st.s > 0 ? g : df_neg(g);
+}
+
+// Streams the scaled rows of a CN block: row i's a~_i and d^_i, with the psi
+// stencil window and the coefficient generator carried from row to row.
+template <class R> struct CNRowStream {
+    CoefGen<R> cg;
+    cx<R> pm, p0, pp;  // psi_{i-1}, psi_i, psi_{i+1}: the next row's stencil is already loaded
+    R sg, msg;
+    int es;
+    const double2* psi;
+    int64_t n, i;
+    __device__ __forceinline__ cx<R> ld(int64_t j) const {
+        return (j >= 0 && j < n) ? load128<R>(psi + j) : czero<R>();
+    }
+    __device__ __forceinline__ void init(const CNStep& st, int64_t j0) {
+        const double Et = st.E_t ? *st.E_t : 0.0, Ee = st.E_e ? *st.E_e : 0.0;
+        sg = signed_gt(st, R());
+        msg = rneg(sg);  // imaginary part of a~: -s g~
+        es = st.e * st.s;
+        psi = st.psi;
+        n = st.p.n;
+        i = j0;
+        cg.init(st.p, (const R*)st.tab, Et, Ee, j0);
+        pm = ld(j0 - 1);
+        p0 = ld(j0);
+        pp = ld(j0 + 1);
+    }
+    // scaled row i (then advance): a~ = bt - i s g~, d^ = explicit row
+    __device__ __forceinline__ void next(cx<R>& a, cx<R>& d) {
+        const cx<R> pn = ld(i + 2);  // issued before the arithmetic of row i
+        R bt, be;
+        cg.next(bt, be);
+        a = mk(bt, msg);
+        d = explicit_row(pm, p0, pp, be, es, sg);
+        pm = p0;
+        p0 = pp;
+        pp = pn;
+        ++i;
+    }
+    __device__ __forceinline__ void skip() {
+        pm = p0;
+        p0 = pp;
+        pp = ld(i + 2);
+        cg.skip();
+        ++i;
+    }
+};
 
 // One thread per block at level 0 of a CN step: coefficients + explicit
-// half-step + Table 1 (RD + JD, RU + JU) on the scaled rows (off-diagonals -1).
-template <class R, int M>
+// half-step + RD/JD with RU/JU accumulated, on the scaled rows (b = c = -1):
+//   RD:  w_k = 1/(a~_k - w_{k-1}),  d_k += w_{k-1} d_{k-1},  b_k = w_{k-1} b_{k-1} (b_1 = -1)
+//   RU:  rho_{k-1} = w_k,  Q_k = Q_{k-1} w_k,  b_1 += Q_k b_k,  d_1 += Q_k d_k,  c_1 = -Q_{g-1}
+// With keep != NULL it also saves, for every interior row k of block t, d^ and
+// the pivot inverse w at keep[(2k) P + t] and keep[(2k+1) P + t] (block-row
+// major: a warp's 32 blocks touch 32 consecutive entries): all the
+// substitution needs (store mode).
+template <class R>
 __global__ void __launch_bounds__(kThreads)
-k_cn_reduce(CNStep st, int64_t P, int m, LevelRow<R>* out, LevelSlot<R>* out_slot, int* status) {
+k_cn_reduce(CNStep st, int64_t P, int m, LevelRow<R>* out, LevelSlot<R>* out_slot,
+            typename Store<R>::T* keep, int* status) {
     const int64_t n = st.p.n;
     const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const bool active = t < P;
@@ -480,78 +523,43 @@ k_cn_reduce(CNStep st, int64_t P, int m, LevelRow<R>* out, LevelSlot<R>* out_slo
     if (active) {
         const int64_t J0 = joint_line(t, P, m, n);
         const int g = (int)(joint_line(t + 1, P, m, n) - J0);
-        const bool last = (t == P - 1);
-        const double Et = st.E_t ? *st.E_t : 0.0, Ee = st.E_e ? *st.E_e : 0.0;
-        const R sg = rconst<R>(st.s * st.p.gt);        // s g~
-        const R msg = rconst<R>(-st.s * st.p.gt);      // imaginary part of a~
-        const double es = st.e * st.s;
-        CoefGen<R> cg;
-        cg.init(st.p, (const R*)st.tab, Et, Ee, J0);
-        cx<R> pm = (J0 > 0) ? load128<R>(st.psi + J0 - 1) : czero<R>();
-        cx<R> p0 = load128<R>(st.psi + J0);
-        const RowMask rm(g);
-        const unsigned need = last ? rm.all : (rm.all & ~rm.joint1);  // rows with coefficients
-        cx<R> D[M + 1], W[M + 1], BT[M + 1];
-        R AT[M + 1];  // real part of a~ (bt_t)
-#pragma unroll
-        for (int k = 0; k <= M; ++k) {
-            if (bit(rm.all, k)) {
-                cx<R> pp = (J0 + k + 1 < n) ? load128<R>(st.psi + J0 + k + 1) : czero<R>();
-                if (bit(need, k)) {
-                    R bt, be;
-                    cg.next(bt, be);
-                    AT[k] = bt;
-                    D[k] = explicit_row(pm, p0, pp, be, es, sg);
-                }
-                pm = p0;
-                p0 = pp;
-            }
+        CNRowStream<R> rs;
+        rs.init(st, J0);
+        rs.next(A0, D0);
+        cx<R> a, d;
+        rs.next(a, d);  // row 1
+        cx<R> w = crcp(a, ok);
+        if (keep) {
+            sstore(keep + 2 * P + t, d);
+            sstore(keep + 3 * P + t, w);
         }
-        A0 = mk(AT[0], msg);
-        D0 = D[0];
-        // RD (b_k = c_k = -1): w = 1/a; a_k -= w_{k-1}; d_k += w_{k-1} d_{k-1}; b~_k = w_{k-1} b~_{k-1}
-        W[1] = crcp(mk(AT[1], msg), ok);
-#pragma unroll
-        for (int k = 2; k < M; ++k) {
-            if (bit(rm.inner, k)) {
-                cx<R> a = csub(mk(AT[k], msg), W[k - 1]);
-                W[k] = crcp(a, ok);
-                D[k] = cfma(D[k], W[k - 1], D[k - 1]);
-                BT[k] = (k == 2) ? W[1] : cmul(W[k - 1], BT[k - 1]);
+        const cx<R> w1 = w;
+        cx<R> bRD = cfrom<R>(-1.0, 0.0), dRD = d;
+        cx<R> Q = cfrom<R>(1.0, 0.0);
+        cx<R> nb = bRD, nd = dRD;
+        for (int k = 2; k < g; ++k) {
+            rs.next(a, d);
+            bRD = cmul(w, bRD);
+            dRD = cfma(d, w, dRD);
+            const cx<R> wk = crcp(csub(a, w), ok);
+            if (keep) {
+                sstore(keep + (2 * k) * P + t, d);
+                sstore(keep + (2 * k + 1) * P + t, wk);
             }
+            Q = cmul(Q, wk);
+            nb = cfma(nb, Q, bRD);
+            nd = cfma(nd, Q, dRD);
+            w = wk;
         }
-        // JD on row J_{t+1}: b = -w_{g-1} b~_{g-1}, a += -w_{g-1}, d += w_{g-1} d_{g-1}
-#pragma unroll
-        for (int k = 2; k <= M; ++k) {
-            if (bit(rm.joint1, k)) {
-                jd.b = (k == 2) ? cneg(W[1]) : cneg(cmul(W[k - 1], BT[k - 1]));
-                jd.a = cneg(W[k - 1]);
-                jd.d = cmul(W[k - 1], D[k - 1]);
-                if (last) {
-                    Ag = mk(AT[k], msg);
-                    Dg = D[k];
-                }
-            }
-        }
-        // RU: b~_k += w_{k+1} b~_{k+1}; c~_k = w_{k+1} c~_{k+1}; d_k += w_{k+1} d_{k+1}
-        const cx<R> one = cfrom<R>(1.0, 0.0);
-        cx<R> nb = one, nc = one, nd = czero<R>();
-#pragma unroll
-        for (int k = M - 1; k >= 1; --k) {
-            if (bit(rm.last_in, k)) {
-                nb = (k == 1) ? one : BT[k];
-                nc = one;
-                nd = D[k];
-            } else if (bit(rm.ru, k)) {
-                nb = (k == 1) ? cfma(one, W[k + 1], nb) : cfma(BT[k], W[k + 1], nb);
-                nc = bit(rm.last_in, k + 1) ? W[k + 1] : cmul(W[k + 1], nc);
-                nd = cfma(D[k], W[k + 1], nd);
-            }
-        }
-        // JU on row J_t with row 1 after RU: c = -w_1 c~_1, a += -w_1 b~_1, d += w_1 d_1
-        JUc = cneg(cmul(W[1], nc));
-        JUa = cneg(cmul(W[1], nb));
-        JUd = cmul(W[1], nd);
+        // JD on row J_{t+1}: r = w_{g-1};  b = r b_{g-1};  a += -r;  d += r d_{g-1}
+        jd.b = cmul(w, bRD);
+        jd.a = cneg(w);
+        jd.d = cmul(w, dRD);
+        if (t == P - 1) rs.next(Ag, Dg);
+        // JU on row J_t: r = w_1;  c = -w_1 Q_{g-1};  a += w_1 b_1;  d += w_1 d_1
+        JUc = cneg(cmul(w1, Q));
+        JUa = cmul(w1, nb);
+        JUd = cmul(w1, nd);
     }
     write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, out, out_slot);
     if (!ok) flag_error(status, kStatusNonfinite);
@@ -561,60 +569,115 @@ k_cn_reduce(CNStep st, int64_t P, int m, LevelRow<R>* out, LevelSlot<R>* out_slo
 // from level 1 as Dirichlet data, by Thomas on the scaled rows:
 //   a_1 = a~_1, a_k = a~_k - w_{k-1}, w = 1/a, z_k = (d^_k + z_{k-1}) w_k
 //   (z_0 = xL, xR added on the last interior row), y_k = z_k + w_k y_{k+1}.
-template <class R, int M>
+// Recompute mode: coefficients, explicit half-step and pivots are regenerated
+// from psi (x must differ from the psi read).  z and w wait in shared memory.
+template <class R>
 __global__ void __launch_bounds__(kThreads)
 k_cn_substitute(CNStep st, int64_t P, int m, const typename Store<R>::T* x_next, double2* x, int* status) {
+    typedef typename Store<R>::T ST;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ST* zs = reinterpret_cast<ST*>(smem_raw);   // [m][kThreads]
+    ST* ws = zs + (size_t)m * kThreads;         // [m][kThreads]
+    const int tid = threadIdx.x;
     const int64_t n = st.p.n;
-    const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * kThreads + tid;
     if (t >= P) return;
     bool ok = true;
     const int64_t J0 = joint_line(t, P, m, n);
     const int g = (int)(joint_line(t + 1, P, m, n) - J0);
-    const double Et = st.E_t ? *st.E_t : 0.0, Ee = st.E_e ? *st.E_e : 0.0;
-    const R sg = rconst<R>(st.s * st.p.gt);
-    const R msg = rconst<R>(-st.s * st.p.gt);
-    const double es = st.e * st.s;
     const cx<R> xL = sload(x_next + t);
     const cx<R> xR = sload(x_next + t + 1);
-    CoefGen<R> cg;
-    cg.init(st.p, (const R*)st.tab, Et, Ee, J0);
-    cg.skip();
-    cx<R> pm = load128<R>(st.psi + J0);
-    cx<R> p0 = load128<R>(st.psi + J0 + 1);
-    const RowMask rm(g);
-    cx<R> W[M + 1], Z[M + 1];
-    cx<R> zp = xL;
-#pragma unroll
-    for (int k = 1; k < M; ++k) {
-        if (bit(rm.inner, k)) {
-            cx<R> pp = load128<R>(st.psi + J0 + k + 1);  // row J0+g exists
-            R bt, be;
-            cg.next(bt, be);
-            cx<R> d = explicit_row(pm, p0, pp, be, es, sg);
-            cx<R> a = (k == 1) ? mk(bt, msg) : csub(mk(bt, msg), W[k - 1]);
-            W[k] = crcp(a, ok);
-            cx<R> rhs = cadd(d, zp);
-            if (bit(rm.last_in, k)) rhs = cadd(rhs, xR);
-            zp = cmul(rhs, W[k]);
-            Z[k] = zp;
-            pm = p0;
-            p0 = pp;
-        }
+    CNRowStream<R> rs;
+    rs.init(st, J0);
+    rs.skip();
+    cx<R> zp = xL, w = czero<R>();
+    for (int k = 1; k < g; ++k) {
+        cx<R> a, d;
+        rs.next(a, d);
+        w = crcp(k == 1 ? a : csub(a, w), ok);
+        cx<R> rhs = cadd(d, zp);
+        if (k == g - 1) rhs = cadd(rhs, xR);
+        zp = cmul(rhs, w);
+        sstore(zs + k * kThreads + tid, zp);
+        sstore(ws + k * kThreads + tid, w);
     }
-    cx<R> y = czero<R>();
-#pragma unroll
-    for (int k = M - 1; k >= 1; --k) {
-        if (bit(rm.last_in, k)) {
-            y = Z[k];
-            store128(x + J0 + k, y);
-        } else if (bit(rm.ru, k)) {
-            y = cfma(Z[k], W[k], y);
-            store128(x + J0 + k, y);
-        }
+    cx<R> y = zp;
+    store128(x + J0 + g - 1, y);
+    for (int k = g - 2; k >= 1; --k) {
+        y = cfma(sload(zs + k * kThreads + tid), sload(ws + k * kThreads + tid), y);
+        store128(x + J0 + k, y);
     }
     store128(x + J0, xL);
     if (t == P - 1) store128(x + J0 + g, xR);
     if (!ok) flag_error(status, kStatusNonfinite);
+}
+
+// Store mode of the same substitution: d^ and w come from keep (written by
+// k_cn_reduce), so psi is not read and x may be the state the step started
+// from.  z, then y, wait in shared memory ([k][tid] with a row stride of
+// kThreads + 1 entries, so both the per-thread column walk and the tile-order
+// read-out below hit distinct banks); when all 128 blocks of the CTA are
+// full-length, the CTA writes its contiguous tile of x in order (coalesced).
+constexpr int kTileStride = kThreads + 1;
+template <class R>
+__global__ void __launch_bounds__(kThreads)
+k_cn_substitute_kept(int64_t n, int64_t P, int m, const typename Store<R>::T* keep,
+                     const typename Store<R>::T* x_next, double2* x) {
+    typedef typename Store<R>::T ST;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ST* zs = reinterpret_cast<ST*>(smem_raw);   // [m][kTileStride]
+    const int tid = threadIdx.x;
+    const int64_t t0 = (int64_t)blockIdx.x * kThreads;
+    const int64_t t = t0 + tid;
+    // all blocks of this CTA span exactly m rows (every CTA but the last one or two)
+    const bool regular = (t0 + kThreads <= P) && joint_line(t0 + kThreads, P, m, n) == (t0 + kThreads) * m;
+    if (t < P) {
+        const int64_t J0 = joint_line(t, P, m, n);
+        const int g = (int)(joint_line(t + 1, P, m, n) - J0);
+        const cx<R> xL = sload(x_next + t);
+        const cx<R> xR = sload(x_next + t + 1);
+        cx<R> zp = xL;
+        cx<R> dn = sload(keep + 2 * P + t), wn = sload(keep + 3 * P + t);
+        for (int k = 1; k < g; ++k) {
+            const cx<R> d = dn, w = wn;
+            if (k + 1 < g) {  // next row's values, issued before this row's arithmetic
+                dn = sload(keep + (2 * k + 2) * P + t);
+                wn = sload(keep + (2 * k + 3) * P + t);
+            }
+            cx<R> rhs = cadd(d, zp);
+            if (k == g - 1) rhs = cadd(rhs, xR);
+            zp = cmul(rhs, w);
+            sstore(zs + k * kTileStride + tid, zp);
+        }
+        cx<R> y = zp;
+        if (regular) {
+            sstore(zs + tid, xL);  // row 0 of the block: its top joint line
+            for (int k = g - 2; k >= 1; --k) {
+                y = cfma(sload(zs + k * kTileStride + tid), sload(keep + (2 * k + 1) * P + t), y);
+                sstore(zs + k * kTileStride + tid, y);
+            }
+        } else {
+            store128(x + J0 + g - 1, y);
+            for (int k = g - 2; k >= 1; --k) {
+                y = cfma(sload(zs + k * kTileStride + tid), sload(keep + (2 * k + 1) * P + t), y);
+                store128(x + J0 + k, y);
+            }
+            store128(x + J0, xL);
+            if (t == P - 1) store128(x + J0 + g, xR);
+        }
+    }
+    if (!regular) return;  // uniform per CTA
+    __syncthreads();
+    // tile row i = (block b, row k) with i = b m + k; rows J_{t0} .. J_{t0} + 128 m - 1
+    const int64_t base = t0 * m;
+    for (int i = tid; i < kThreads * m; i += kThreads) {
+        const int b = i / m, k = i - b * m;
+        store128(x + base + i, sload(zs + k * kTileStride + b));
+    }
+    if (t0 + kThreads == P) {
+        // the CTA holding the last block also writes the last joint line
+        if (tid == kThreads - 1) store128(x + n - 1, sload(x_next + P));
+    }
 }
 
 }  // namespace cnb

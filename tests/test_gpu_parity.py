@@ -31,9 +31,9 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-def plan_for(cfg, arith=cnb.ARITH_F64, block=0):
+def plan_for(cfg, arith=cnb.ARITH_F64, block=0, flags=0):
     return cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cfg.get("pot", 0),
-                    soft_s=cfg.get("soft_s", 2.0), block=block, arith=arith)
+                    soft_s=cfg.get("soft_s", 2.0), block=block, arith=arith, flags=flags)
 
 
 def oracle_problem(cfg):
@@ -103,23 +103,25 @@ def test_free_packet_n4096_100_steps(arith):
 @pytest.mark.parametrize("n", [3, 5, 64, 4097, 1 << 16])
 @pytest.mark.parametrize("block", [4, 8, 16])
 @pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
-def test_soft_coulomb_field_100_steps(n, block, arith):
+@pytest.mark.parametrize("flags", [0, cnb.FLAG_RECOMPUTE])
+def test_soft_coulomb_field_100_steps(n, block, arith, flags):
     cfg = W.soft_coulomb_config(n=n, nsteps=100)
     psi0 = W.initial_state(cfg) if n >= 64 else (np.arange(n) + 1j).astype(np.complex128)
     E = W.field_midpoints(100, cfg["dt"], t0=150.0)
     ref = oracle.cn_run(oracle_problem(cfg), psi0, 100, E_mid=E)
-    plan = plan_for(cfg, block=block, arith=arith)
+    plan = plan_for(cfg, block=block, arith=arith, flags=flags)
     out = plan.step(to_dev(psi0), 100, E_mid=to_dev(E)).cpu().numpy()
     plan.check()
     assert rel(out, ref) <= 1e-11
 
 
-def test_step_in_place_and_zero_steps():
+@pytest.mark.parametrize("flags", [0, cnb.FLAG_RECOMPUTE])
+def test_step_in_place_and_zero_steps(flags):
     cfg = W.soft_coulomb_config(n=1000, nsteps=7)
     psi0 = W.initial_state(cfg)
     E = W.field_midpoints(7, cfg["dt"], t0=10.0)
     ref = oracle.cn_run(oracle_problem(cfg), psi0, 7, E_mid=E)
-    plan = plan_for(cfg)
+    plan = plan_for(cfg, flags=flags)
     for k in (7, 6):  # odd and even step counts through the in-place path
         t = to_dev(psi0)
         plan.step(t, k, E_mid=to_dev(E), psi_out=t)
@@ -128,6 +130,10 @@ def test_step_in_place_and_zero_steps():
     t = to_dev(psi0)
     out = plan.step(t, 0)
     assert np.array_equal(out.cpu().numpy(), psi0)
+    # psi_in is left untouched when psi_out differs
+    t = to_dev(psi0)
+    plan.step(t, 7, E_mid=to_dev(E))
+    assert np.array_equal(t.cpu().numpy(), psi0)
 
 
 def test_step_host_matches_device():
@@ -140,13 +146,14 @@ def test_step_host_matches_device():
     assert np.array_equal(dev, host)
 
 
-def test_full_size_soft_coulomb_2pow24():
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_full_size_soft_coulomb_2pow24(arith):
     # the benchmarked configuration, in the launch configuration bench.py times
     cfg = W.soft_coulomb_config()
     nsteps = 3
     psi0 = W.initial_state(cfg)
     E = W.field_midpoints(nsteps, cfg["dt"], t0=200.0)
-    plan = plan_for(cfg)
+    plan = plan_for(cfg, arith=arith)
     out = plan.step(to_dev(psi0), nsteps, E_mid=to_dev(E)).cpu().numpy()
     plan.check()
     ref = oracle.cn_run(oracle_problem(cfg), psi0, nsteps, E_mid=E)
