@@ -161,6 +161,30 @@ cn_status cn_plan_query(cn_plan plan, cn_plan_info* out);
 cn_status cn_plan_profile(cn_plan plan, int enable);
 cn_status cn_plan_profile_read(cn_plan plan, double* ms, int64_t* launches, int32_t cap);
 
+/* cn_solve_tridiag_noalloc: the tridiagonal solve of cn_solve_tridiag for
+ * callers that cannot allocate device memory on their solve path (code under a
+ * framework whose memory pool owns all device memory, or a latency-critical
+ * loop where cudaMalloc / cudaFree would synchronise the device).  It takes no
+ * plan and allocates nothing: the reduced systems of all nesting levels live
+ * in one fixed 16 MiB device array inside the library, which every GPU that
+ * loads the library holds until the process exits.  The paper has no
+ * counterpart; this is a deployment variant of the same N-shaped solve.
+ *   b, a, c, d, x, n: as for cn_solve_tridiag (device complex128[n]; x may
+ *     alias d); n <= CN_NOALLOC_MAX_N, larger n returns CN_ERR_UNSUPPORTED
+ *     before any work is enqueued;
+ *   arith: CN_ARITH_F64 or CN_ARITH_DF64; blocks of 8 rows on every level;
+ *   stream: as elsewhere; the call returns without synchronising.
+ * The first call on each device looks up the device address of the array
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same array: calls that may overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Each call writes every scratch word it reads, so nothing has to be cleared
+ * between calls.  Zero or non-finite pivots are not reported through a
+ * status word (there is no plan); they show up as non-finite values in x. */
+#define CN_NOALLOC_MAX_N 1048576
+cn_status cn_solve_tridiag_noalloc(const void* b, const void* a, const void* c, const void* d, void* x,
+                                   int64_t n, int32_t arith, void* stream);
+
 /* Wait for the plan's stream work to finish (device synchronise) and return
  * the first device-side error recorded since the last call (then clear it). */
 cn_status cn_plan_status(cn_plan plan);

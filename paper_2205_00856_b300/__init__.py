@@ -31,7 +31,8 @@ _STATUS = {0: "CN_OK", 1: "CN_ERR_INVALID_ARG", 2: "CN_ERR_UNSUPPORTED", 3: "CN_
 # every symbol declared in include/cn.h
 EXPORTS = ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_solve_tridiag",
            "cn_plan_query", "cn_plan_profile", "cn_plan_profile_read", "cn_plan_status", "cn_status_string",
-           "cn_version")
+           "cn_version", "cn_solve_tridiag_noalloc")
+NOALLOC_MAX_N = 1048576
 MAX_LEVELS = 24
 PROFILE_CLASSES = ("reduce_level0", "substitute_level0", "reduce_levels_ge1", "substitute_levels_ge1", "rs_stage")
 
@@ -83,6 +84,8 @@ def load(build_if_missing: bool = True):
             lib.cn_plan_query.argtypes = [vp, C.POINTER(_Info)]
             lib.cn_plan_profile.argtypes = [vp, C.c_int]
             lib.cn_plan_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]
+            lib.cn_solve_tridiag_noalloc.argtypes = [vp, vp, vp, vp, vp, i64, C.c_int32, vp]
+            lib.cn_solve_tridiag_noalloc.restype = C.c_int
             lib.cn_status_string.argtypes = [C.c_int]
             lib.cn_status_string.restype = C.c_char_p
             lib.cn_version.argtypes = []
@@ -233,6 +236,22 @@ class Plan:
 
     def check(self) -> None:
         _check(self.status(), "device status")
+
+
+def solve_tridiag_noalloc(b, a, c, d, x=None, arith=ARITH_F64, stream=None):
+    """Solve T x = d without a plan and without allocating device memory inside
+    the library (cn_solve_tridiag_noalloc), for callers that cannot allocate on
+    their solve path.  n <= NOALLOC_MAX_N; calls that overlap on the GPU race."""
+    import torch
+    lib = load()
+    n = a.numel()
+    ptrs = [_dev_ptr(v, torch.complex128, n, nm) for v, nm in ((b, "b"), (a, "a"), (c, "c"), (d, "d"))]
+    if x is None:
+        x = torch.empty_like(d)
+    px = _dev_ptr(x, torch.complex128, n, "x")
+    _check(lib.cn_solve_tridiag_noalloc(*ptrs, px, n, int(arith), _stream_handle(stream)),
+           "cn_solve_tridiag_noalloc")
+    return x
 
 
 def version() -> str:

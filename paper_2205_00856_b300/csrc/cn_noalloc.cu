@@ -1,0 +1,149 @@
+// cn_noalloc.cu -- cn_solve_tridiag_noalloc: the general tridiagonal solve of
+// cn_solve_tridiag without a plan and without allocating device memory.
+//
+// Some callers cannot allocate device memory on their solve path: code that
+// runs inside a framework whose memory pool owns all device memory, or a
+// latency-critical loop where cudaMalloc / cudaFree would synchronise the
+// device.  For them the reduced systems of every nesting level live in one
+// file-scope device array of fixed size, g_noalloc_scratch, that every GPU
+// which loads this library holds until the process exits.  The caller passes
+// only the system and the output, as for cn_solve_tridiag.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "../../include/cn.h"
+#include "cn_kernels.cuh"
+
+using namespace cnb;
+
+namespace {
+
+constexpr int kNaBlock = 8;            // rows per block on every level
+constexpr size_t kNaScratchBytes = 16u << 20;  // 16 MiB, enough for CN_NOALLOC_MAX_N rows
+constexpr int kNaMaxDevices = 64;
+constexpr int kNaMaxLevels = CN_MAX_LEVELS;
+
+}  // namespace
+
+// The shared scratch.  In host code this name is only a host-side stand-in for
+// the device array: its address must be looked up with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes];
+
+namespace {
+
+std::mutex g_na_mutex;
+void* g_na_ptr[kNaMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device.
+cudaError_t scratch_address(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_na_ptr[dev] = p;
+    }
+    *out = g_na_ptr[dev];
+    return cudaSuccess;
+}
+
+struct NaLevel {
+    int64_t n, P;
+    size_t rows, slot, x;  // byte offsets into the scratch
+};
+
+int64_t na_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+size_t na_align(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Level sizes and scratch offsets (host arithmetic only); returns the number of
+// levels below level 0, or -1 if they do not fit.
+int plan_levels(int64_t n, NaLevel* lv, size_t* used) {
+    int L = 0;
+    lv[0].n = n;
+    lv[0].P = na_ceil_div(n - 1, kNaBlock);
+    size_t off = 0;
+    for (;;) {
+        const int64_t nn = lv[L].P + 1;
+        if (L + 1 >= kNaMaxLevels) return -1;
+        NaLevel& nx = lv[L + 1];
+        nx.n = nn;
+        nx.P = na_ceil_div(nn - 1, kNaBlock);
+        nx.rows = off;
+        off = na_align(off + (size_t)nn * 4 * 16);
+        nx.slot = off;
+        off = na_align(off + (size_t)(na_ceil_div(lv[L].P, kThreads) + 1) * 3 * 16);
+        nx.x = off;
+        off = na_align(off + (size_t)nn * 16);
+        ++L;
+        if (nn <= kBaseMax) break;
+    }
+    *used = off;
+    return L;
+}
+
+template <class R>
+cudaError_t na_solve(unsigned char* base, const NaLevel* lv, int L, const ArraySource& src, double2* x,
+                     cudaStream_t st) {
+    typedef typename Store<R>::T ST;
+    auto rows = [&](int l) { return reinterpret_cast<LevelRow<R>*>(base + lv[l].rows); };
+    auto slot = [&](int l) { return reinterpret_cast<LevelSlot<R>*>(base + lv[l].slot); };
+    auto xs = [&](int l) { return reinterpret_cast<ST*>(base + lv[l].x); };
+    auto lsrc = [&](int l) {
+        LevelSource<R> s;
+        s.rows = rows(l);
+        s.slot = slot(l);
+        s.n = lv[l].n;
+        s.slot_stride = kThreads;
+        return s;
+    };
+    const size_t smem = 2 * (size_t)kNaBlock * kThreads * 16;  // 32 KiB: below the default limit
+    k_reduce<R, ArraySource><<<(unsigned)na_ceil_div(lv[0].P, kThreads), kThreads, 0, st>>>(
+        src, lv[0].n, lv[0].P, kNaBlock, rows(1), slot(1), nullptr);
+    for (int l = 1; l < L; ++l)
+        k_reduce<R, LevelSource<R>><<<(unsigned)na_ceil_div(lv[l].P, kThreads), kThreads, 0, st>>>(
+            lsrc(l), lv[l].n, lv[l].P, kNaBlock, rows(l + 1), slot(l + 1), nullptr);
+    k_base<R><<<1, 32, 0, st>>>(lsrc(L), lv[L].n, xs(L), nullptr);
+    for (int l = L - 1; l >= 1; --l)
+        k_substitute<R, LevelSource<R>, ST><<<(unsigned)na_ceil_div(lv[l].P, kThreads), kThreads, smem, st>>>(
+            lsrc(l), lv[l].n, lv[l].P, kNaBlock, xs(l + 1), xs(l), nullptr);
+    k_substitute<R, ArraySource, double2><<<(unsigned)na_ceil_div(lv[0].P, kThreads), kThreads, smem, st>>>(
+        src, lv[0].n, lv[0].P, kNaBlock, xs(1), x, nullptr);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" cn_status cn_solve_tridiag_noalloc(const void* b, const void* a, const void* c, const void* d, void* x,
+                                              int64_t n, int32_t arith, void* stream) {
+    if (!b || !a || !c || !d || !x || n < 3) return CN_ERR_INVALID_ARG;
+    if (arith != CN_ARITH_F64 && arith != CN_ARITH_DF64) return CN_ERR_INVALID_ARG;
+    const uintptr_t mis = reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(a) |
+                          reinterpret_cast<uintptr_t>(c) | reinterpret_cast<uintptr_t>(d) |
+                          reinterpret_cast<uintptr_t>(x);
+    if (mis & 15u) return CN_ERR_INVALID_ARG;
+    if (x == b || x == a || x == c) return CN_ERR_INVALID_ARG;
+    if (n > CN_NOALLOC_MAX_N) return CN_ERR_UNSUPPORTED;
+    NaLevel lv[kNaMaxLevels];
+    size_t used = 0;
+    const int L = plan_levels(n, lv, &used);
+    if (L < 1 || used > kNaScratchBytes) return CN_ERR_UNSUPPORTED;
+    void* base = nullptr;
+    if (scratch_address(&base) != cudaSuccess) return CN_ERR_CUDA;
+    ArraySource s;
+    s.b = static_cast<const double2*>(b);
+    s.a = static_cast<const double2*>(a);
+    s.c = static_cast<const double2*>(c);
+    s.d = static_cast<const double2*>(d);
+    s.n = n;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char* p = static_cast<unsigned char*>(base);
+    cudaError_t e = (arith == CN_ARITH_DF64) ? na_solve<df>(p, lv, L, s, static_cast<double2*>(x), st)
+                                             : na_solve<double>(p, lv, L, s, static_cast<double2*>(x), st);
+    return e == cudaSuccess ? CN_OK : CN_ERR_CUDA;
+}
