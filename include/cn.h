@@ -135,6 +135,30 @@ cn_status cn_step_host(cn_plan plan, const void* psi_in_host, void* psi_out_host
 cn_status cn_solve_tridiag(cn_plan plan, const void* b, const void* a, const void* c,
                            const void* d, void* x, int64_t n, void* stream);
 
+/* One step of the discrete adjoint of the CN recursion T_n psi_{n+1} = T_n^dagger psi_n
+ * (Sec. 2; the paper has no adjoint: this is the hand-written backward pass for a
+ * real loss L(psi_N) with the convention dL = 2 Re(lam^H dpsi)):
+ *   mu      = (T_n^dagger)^{-1} lam_{n+1}      (N-shaped solve, Sec. 4)
+ *   lam_n   = T_n mu                            (= 2 mu - lam_{n+1}, since T + T^dagger = 2)
+ *   *dLdE  += dL/dE_n = dt Im( sum_j conj(mu_j) x_j (psi_n,j + psi_{n+1},j) )
+ * psi_n, psi_np1, lam_np1: device complex128[n] (psi_n, psi_np1 the forward states of
+ * step n); lam_n: device complex128[n] output, may alias lam_np1; E_mid: device pointer
+ * to E(t_n + dt/2) (NULL: 0); dLdE: device double, accumulated (not overwritten).  The
+ * plan allocates an n-point buffer for mu on its first adjoint call.  The sum is
+ * formed in a fixed order: results are bitwise reproducible. */
+cn_status cn_adjoint_step(cn_plan plan, const void* psi_n, const void* psi_np1, const void* lam_np1,
+                          void* lam_n, const double* E_mid, double* dLdE, void* stream);
+
+/* Piecewise-linear field from n_controls >= 2 samples u_c on the uniform nodes
+ * t_c = c t_final / (n_controls - 1), clamped outside [0, t_final]:
+ *   E_mid[k] = sum_c u_c hat_c(t0 + (k + 1/2) dt),  k = 0..nsteps-1,
+ * and its transpose  grad_u[c] = sum_k dLdE[k] hat_c(t0 + (k + 1/2) dt)
+ * (overwritten).  All arrays are device doubles. */
+cn_status cn_field_from_controls(const double* u, int64_t n_controls, double t_final, double t0, double dt,
+                                 int64_t nsteps, double* E_mid, void* stream);
+cn_status cn_field_grad_to_controls(const double* dLdE, int64_t nsteps, double t_final, double t0, double dt,
+                                    int64_t n_controls, double* grad_u, void* stream);
+
 /* Static description of a plan: the nesting levels of its N-shaped solve
  * (Eq. iteration) and the kernels one step launches. */
 #define CN_MAX_LEVELS 24

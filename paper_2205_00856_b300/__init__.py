@@ -31,7 +31,8 @@ _STATUS = {0: "CN_OK", 1: "CN_ERR_INVALID_ARG", 2: "CN_ERR_UNSUPPORTED", 3: "CN_
 # every symbol declared in include/cn.h
 EXPORTS = ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_solve_tridiag",
            "cn_plan_query", "cn_plan_profile", "cn_plan_profile_read", "cn_plan_status", "cn_status_string",
-           "cn_version", "cn_solve_tridiag_noalloc")
+           "cn_version", "cn_solve_tridiag_noalloc", "cn_adjoint_step", "cn_field_from_controls",
+           "cn_field_grad_to_controls")
 NOALLOC_MAX_N = 1048576
 MAX_LEVELS = 24
 PROFILE_CLASSES = ("reduce_level0", "substitute_level0", "reduce_levels_ge1", "substitute_levels_ge1", "rs_stage")
@@ -85,6 +86,13 @@ def load(build_if_missing: bool = True):
             lib.cn_plan_profile.argtypes = [vp, C.c_int]
             lib.cn_plan_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]
             lib.cn_solve_tridiag_noalloc.argtypes = [vp, vp, vp, vp, vp, i64, C.c_int32, vp]
+            lib.cn_adjoint_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+            lib.cn_adjoint_step.restype = C.c_int
+            dbl = C.c_double
+            lib.cn_field_from_controls.argtypes = [vp, i64, dbl, dbl, dbl, i64, vp, vp]
+            lib.cn_field_from_controls.restype = C.c_int
+            lib.cn_field_grad_to_controls.argtypes = [vp, i64, dbl, dbl, dbl, i64, vp, vp]
+            lib.cn_field_grad_to_controls.restype = C.c_int
             lib.cn_solve_tridiag_noalloc.restype = C.c_int
             lib.cn_status_string.argtypes = [C.c_int]
             lib.cn_status_string.restype = C.c_char_p
@@ -209,6 +217,20 @@ class Plan:
         _check(self._lib.cn_solve_tridiag(self._h, *ptrs, px, self.n, _stream_handle(stream)), "cn_solve_tridiag")
         return x
 
+    def adjoint_step(self, psi_n, psi_np1, lam_np1, dLdE, E_mid=None, lam_n=None, stream=None):
+        """One adjoint step (cn_adjoint_step): lam_n = T_n (T_n^dagger)^{-1} lam_np1 and
+        dLdE[0] += dL/dE_n.  dLdE and E_mid are float64 device tensors (E_mid[0] is used)."""
+        import torch
+        ptrs = [_dev_ptr(v, torch.complex128, self.n, nm)
+                for v, nm in ((psi_n, "psi_n"), (psi_np1, "psi_np1"), (lam_np1, "lam_np1"))]
+        if lam_n is None:
+            lam_n = torch.empty_like(lam_np1)
+        pl = _dev_ptr(lam_n, torch.complex128, self.n, "lam_n")
+        pg = _dev_ptr(dLdE, torch.float64, dLdE.numel(), "dLdE")
+        pe = None if E_mid is None else _dev_ptr(E_mid, torch.float64, E_mid.numel(), "E_mid")
+        _check(self._lib.cn_adjoint_step(self._h, *ptrs, pl, pe, pg, _stream_handle(stream)), "cn_adjoint_step")
+        return lam_n
+
     def info(self) -> dict:
         """Nesting levels, kernels per step and workspace of the plan."""
         inf = _Info()
@@ -252,6 +274,32 @@ def solve_tridiag_noalloc(b, a, c, d, x=None, arith=ARITH_F64, stream=None):
     _check(lib.cn_solve_tridiag_noalloc(*ptrs, px, n, int(arith), _stream_handle(stream)),
            "cn_solve_tridiag_noalloc")
     return x
+
+
+def field_from_controls(u, t_final: float, t0: float, dt: float, nsteps: int, out=None, stream=None):
+    """E_mid[k] = piecewise-linear field of the control samples u at t0 + (k + 1/2) dt."""
+    import torch
+    lib = load()
+    pu = _dev_ptr(u, torch.float64, u.numel(), "u")
+    if out is None:
+        out = torch.empty(nsteps, dtype=torch.float64, device=u.device)
+    po = _dev_ptr(out, torch.float64, nsteps, "E_mid")
+    _check(lib.cn_field_from_controls(pu, u.numel(), float(t_final), float(t0), float(dt), int(nsteps), po,
+                                      _stream_handle(stream)), "cn_field_from_controls")
+    return out
+
+
+def field_grad_to_controls(dLdE, t_final: float, t0: float, dt: float, n_controls: int, out=None, stream=None):
+    """Transpose of field_from_controls: gradient with respect to the control samples."""
+    import torch
+    lib = load()
+    pg = _dev_ptr(dLdE, torch.float64, dLdE.numel(), "dLdE")
+    if out is None:
+        out = torch.empty(n_controls, dtype=torch.float64, device=dLdE.device)
+    po = _dev_ptr(out, torch.float64, n_controls, "grad_u")
+    _check(lib.cn_field_grad_to_controls(pg, dLdE.numel(), float(t_final), float(t0), float(dt), int(n_controls), po,
+                                         _stream_handle(stream)), "cn_field_grad_to_controls")
+    return out
 
 
 def version() -> str:

@@ -45,6 +45,10 @@ struct cn_plan_s {
     double2* h_out = nullptr;
     double* h_E = nullptr;
     int64_t h_E_cap = 0;
+    // adjoint (allocated on first use)
+    double2* mu = nullptr;
+    void* part = nullptr;
+    int part_n = 0;
     // kernel timing (cn_plan_profile)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;  // events owned by the plan
@@ -93,6 +97,8 @@ void free_plan_memory(cn_plan p) {
     cudaFree(p->h_in);
     cudaFree(p->h_out);
     cudaFree(p->h_E);
+    cudaFree(p->mu);
+    cudaFree(p->part);
 }
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -467,6 +473,70 @@ cn_status cn_solve_tridiag(cn_plan p, const void* b, const void* a, const void* 
     cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? solve_arrays<df>(p, s, static_cast<double2*>(x), st)
                                                      : solve_arrays<double>(p, s, static_cast<double2*>(x), st);
     return cuda_status(e);
+}
+
+cn_status cn_adjoint_step(cn_plan p, const void* psi_n, const void* psi_np1, const void* lam_np1, void* lam_n,
+                          const double* E_mid, double* dLdE, void* stream) {
+    if (!p || !psi_n || !psi_np1 || !lam_np1 || !lam_n || !dLdE) return CN_ERR_INVALID_ARG;
+    if (!aligned16(psi_n) || !aligned16(psi_np1) || !aligned16(lam_np1) || !aligned16(lam_n)) return CN_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(dLdE) & 7u) || (E_mid && (reinterpret_cast<uintptr_t>(E_mid) & 7u)))
+        return CN_ERR_INVALID_ARG;
+    const int nparts = 148 * 4;
+    cudaError_t e = cudaSuccess;
+    if (!p->mu) e = cudaMalloc(&p->mu, sizeof(double2) * (size_t)p->desc.n);
+    if (e == cudaSuccess && !p->part) {
+        e = cudaMalloc(&p->part, 16 * (size_t)nparts);
+        p->part_n = nparts;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? CN_ERR_OOM : CN_ERR_CUDA;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CNStep s;
+    s.p = p->cnp;
+    s.psi = static_cast<const double2*>(lam_np1);
+    s.s = -1;  // implicit matrix T^dagger = 1 - i dt/2 H
+    s.e = 0;   // right-hand side lam_{n+1} itself
+    s.E_t = E_mid;
+    s.E_e = E_mid;
+    s.tab = p->tab;
+    const bool dfm = p->desc.arith == CN_ARITH_DF64;
+    e = dfm ? cn_solve<df>(p, s, p->mu, st) : cn_solve<double>(p, s, p->mu, st);
+    if (e != cudaSuccess) return CN_ERR_CUDA;
+    if (dfm) {
+        k_adjoint_finish<df><<<p->part_n, kAdjThreads, 0, st>>>(
+            p->cnp, p->mu, static_cast<const double2*>(lam_np1), static_cast<const double2*>(psi_n),
+            static_cast<const double2*>(psi_np1), static_cast<double2*>(lam_n), static_cast<df*>(p->part));
+        k_adjoint_sum<df><<<1, 32, 0, st>>>(static_cast<const df*>(p->part), p->part_n, p->desc.dt, dLdE);
+    } else {
+        k_adjoint_finish<double><<<p->part_n, kAdjThreads, 0, st>>>(
+            p->cnp, p->mu, static_cast<const double2*>(lam_np1), static_cast<const double2*>(psi_n),
+            static_cast<const double2*>(psi_np1), static_cast<double2*>(lam_n), static_cast<double*>(p->part));
+        k_adjoint_sum<double><<<1, 32, 0, st>>>(static_cast<const double*>(p->part), p->part_n, p->desc.dt, dLdE);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+cn_status cn_field_from_controls(const double* u, int64_t n_controls, double t_final, double t0, double dt,
+                                 int64_t nsteps, double* E_mid, void* stream) {
+    if (!u || !E_mid || n_controls < 2 || nsteps < 0 || !(t_final > 0.0) || !std::isfinite(t0) ||
+        !std::isfinite(dt) || dt == 0.0)
+        return CN_ERR_INVALID_ARG;
+    if (nsteps == 0) return CN_OK;
+    k_hat_field<<<(unsigned)ceil_div(nsteps, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        u, n_controls, t_final, t0, dt, nsteps, E_mid);
+    return cuda_status(cudaGetLastError());
+}
+
+cn_status cn_field_grad_to_controls(const double* dLdE, int64_t nsteps, double t_final, double t0, double dt,
+                                    int64_t n_controls, double* grad_u, void* stream) {
+    if (!dLdE || !grad_u || n_controls < 2 || nsteps < 0 || !(t_final > 0.0) || !std::isfinite(t0) ||
+        !(dt > 0.0))
+        return CN_ERR_INVALID_ARG;
+    k_hat_field_grad<<<(unsigned)ceil_div(n_controls, 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        dLdE, nsteps, t_final, t0, dt, n_controls, grad_u);
+    return cuda_status(cudaGetLastError());
 }
 
 cn_status cn_plan_query(cn_plan p, cn_plan_info* out) {

@@ -418,14 +418,17 @@ template <> struct CoefGen<df> {
 };
 
 // Scaled explicit row: d^ = (e s)(bt_e psi - sigma) - i s g~ psi, sigma = psi_{j-1} + psi_{j+1}.
+// es == 0: no explicit matrix, the right-hand side is psi itself (d^ = -i s g~ psi).
 __device__ __forceinline__ cx<double> explicit_row(cx<double> pm, cx<double> p0, cx<double> pp, double bte, int es,
                                                    double sg) {
+    if (es == 0) return mk(sg * p0.im, -sg * p0.re);
     double sr = pm.re + pp.re, si = pm.im + pp.im;
     double eb = es > 0 ? bte : -bte;
     if (es > 0) { sr = -sr; si = -si; }
     return mk(fma(eb, p0.re, fma(sg, p0.im, sr)), fma(eb, p0.im, fma(-sg, p0.re, si)));
 }
 __device__ __forceinline__ cx<df> explicit_row(cx<df> pm, cx<df> p0, cx<df> pp, df bte, int es, df sg) {
+    if (es == 0) return mk(df_mul(sg, p0.im), df_neg(df_mul(sg, p0.re)));
     df sr = df_add(pm.re, pp.re), si = df_add(pm.im, pp.im);
     df eb = es > 0 ? bte : df_neg(bte);
     df nsr = es > 0 ? df_neg(sr) : sr;
@@ -438,7 +441,8 @@ __device__ __forceinline__ cx<df> explicit_row(cx<df> pm, cx<df> p0, cx<df> pp, 
 struct CNStep {
     CNParams p;
     const double2* psi;   // state the explicit half-step is applied to
-    int s, e;             // T_s = 1 + i s dt/2 H(E_t);  explicit S_e = 1 + i e dt/2 H(E_e)
+    int s, e;             // T_s = 1 + i s dt/2 H(E_t);  explicit S_e = 1 + i e dt/2 H(E_e);
+                          // e = 0: the right-hand side is psi itself
     const double* E_t;
     const double* E_e;
     const void* tab;      // bt0 table in the compute type, or NULL (regenerate)
@@ -678,6 +682,112 @@ k_cn_substitute_kept(int64_t n, int64_t P, int m, const typename Store<R>::T* ke
         // the CTA holding the last block also writes the last joint line
         if (tid == kThreads - 1) store128(x + n - 1, sload(x_next + P));
     }
+}
+
+// ------------------------------------------------------------------ adjoint step
+// After mu = (T_n^dagger)^{-1} lam_{n+1} (the N-shaped solve with s = -1 and the
+// identity right-hand side):
+//   lam_n = T_n mu = 2 mu - lam_{n+1}          (T_n + T_n^dagger = 2 for CN)
+//   dL/dE_n = dt Im( sum_j conj(mu_j) x_j (psi_n,j + psi_{n+1},j) ),
+// from d(T psi_{n+1} - T^dagger psi_n) = i dt/2 X (psi_{n+1} + psi_n) dE and
+// dL = 2 Re(lam^H dpsi).  Per-CTA partial sums go to `part`; k_adjoint_sum adds
+// them in a fixed order (deterministic) and accumulates dt * sum into *dLdE.
+constexpr int kAdjThreads = 256;
+
+__device__ __forceinline__ double adj_term(cx<double> mu, cx<double> s, double x) {
+    // Im(conj(mu) s) x = (mu.re s.im - mu.im s.re) x
+    return fma(mu.re, s.im, -mu.im * s.re) * x;
+}
+__device__ __forceinline__ df adj_term(cx<df> mu, cx<df> s, df x) {
+    return df_mul(df_dot2(mu.re, s.im, df_neg(mu.im), s.re), x);
+}
+__device__ __forceinline__ double radd(double a, double b) { return a + b; }
+__device__ __forceinline__ df radd(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ double xcoord(const CNParams& p, int64_t j, double) {
+    return fma((double)(j - p.j_o), p.dx, p.x_o);
+}
+__device__ __forceinline__ df xcoord(const CNParams& p, int64_t j, df) {
+    const int64_t dj = j - p.j_o;
+    float jh = i2f((int32_t)(dj >> 16)), jl = i2f((int32_t)(dj & 0xFFFF));
+    df dx = dfc(p.dx_f);
+    return df_add(dfc(p.xo_f), df_add(df_mul_f(df_mul_f(dx, jh), 65536.0f), df_mul_f(dx, jl)));
+}
+
+template <class R>
+__global__ void __launch_bounds__(kAdjThreads)
+k_adjoint_finish(CNParams p, const double2* mu, const double2* lam_np1, const double2* psi_n, const double2* psi_np1,
+                 double2* lam_n, R* part) {
+    __shared__ R red[kAdjThreads];
+    R acc = RealOps<R>::from_d(0.0);
+    for (int64_t j = (int64_t)blockIdx.x * kAdjThreads + threadIdx.x; j < p.n; j += (int64_t)gridDim.x * kAdjThreads) {
+        const cx<R> m = load128<R>(mu + j);
+        const cx<R> l1 = load128<R>(lam_np1 + j);
+        const cx<R> s = cadd(load128<R>(psi_n + j), load128<R>(psi_np1 + j));
+        acc = radd(acc, adj_term(m, s, xcoord(p, j, R())));
+        store128(lam_n + j, csub(cadd(m, m), l1));
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kAdjThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = radd(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+template <class R>
+__global__ void k_adjoint_sum(const R* part, int nparts, double dt, double* dLdE) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    R acc = RealOps<R>::from_d(0.0);
+    for (int i = 0; i < nparts; ++i) acc = radd(acc, part[i]);
+    *dLdE += dt * RealOps<R>::to_d(acc);
+}
+
+// ------------------------------------------------------------------ control samples
+// Piecewise-linear field from n_c control samples on the uniform nodes
+// t_c = c h, h = t_final / (n_c - 1), clamped outside [0, t_final]:
+//   E(t) = sum_c u_c hat_c(t);  E_mid[k] = E(t0 + (k + 1/2) dt),
+// and the transpose map  g_c = sum_k dLdE_k hat_c(t0 + (k + 1/2) dt)  (each
+// control gathers the steps in its support: no atomics).
+__device__ __forceinline__ void hat_locate(double t, double t_final, int64_t nc, int64_t& i0, double& f) {
+    t = fmin(fmax(t, 0.0), t_final);
+    const double s = t * (double)(nc - 1) / t_final;
+    i0 = (int64_t)floor(s);
+    if (i0 > nc - 2) i0 = nc - 2;
+    f = s - (double)i0;
+}
+
+static __global__ void k_hat_field(const double* u, int64_t nc, double t_final, double t0, double dt, int64_t nsteps,
+                            double* E_mid) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nsteps) return;
+    int64_t i0;
+    double f;
+    hat_locate(t0 + ((double)k + 0.5) * dt, t_final, nc, i0, f);
+    E_mid[k] = (1.0 - f) * u[i0] + f * u[i0 + 1];
+}
+
+static __global__ void k_hat_field_grad(const double* dLdE, int64_t nsteps, double t_final, double t0, double dt,
+                                 int64_t nc, double* g) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const double h = t_final / (double)(nc - 1);
+    // steps whose midpoint lies in [t_{c-1}, t_{c+1}], widened by one step each side
+    int64_t k_lo = (int64_t)floor(((double)(c - 1) * h - t0) / dt - 1.5);
+    int64_t k_hi = (int64_t)ceil(((double)(c + 1) * h - t0) / dt + 0.5);
+    if (c == 0) k_lo = 0;            // clamped times below 0 map to control 0
+    if (c == nc - 1) k_hi = nsteps;  // and above t_final to the last control
+    if (k_lo < 0) k_lo = 0;
+    if (k_hi > nsteps) k_hi = nsteps;
+    double acc = 0.0;
+    for (int64_t k = k_lo; k < k_hi; ++k) {
+        int64_t i0;
+        double f;
+        hat_locate(t0 + ((double)k + 0.5) * dt, t_final, nc, i0, f);
+        if (i0 == c) acc = fma(dLdE[k], 1.0 - f, acc);
+        else if (i0 + 1 == c) acc = fma(dLdE[k], f, acc);
+    }
+    g[c] = acc;
 }
 
 }  // namespace cnb
