@@ -281,6 +281,42 @@ def roofline(prof, n, arith, peaks, m):
     return roof
 
 
+def adjoint_ratio(torch, cnb, args, dev):
+    """Gradient run: soft-Coulomb atom, N = 2^20, dt = 0.02, E(t) from 500 control
+    samples (sin^2 pulse), loss = population outside |x| < 20; backward (sqrt(T)
+    checkpoint recompute + adjoint steps) time over forward time, CUDA events."""
+    from paper_2205_00856_b300.autograd import propagate
+    cfg = W.gradient_config()
+    n, nsteps, nc = cfg["n"], args.adjoint_steps, cfg["n_controls"]
+    tf = nsteps * cfg["dt"]
+    arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
+    plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith,
+                    block=args.block, level_block=args.level_block)
+    psi0 = torch.from_numpy(W.initial_state(cfg)).to(dev)
+    u0 = torch.from_numpy(W.initial_controls(nc, tf)).to(dev)
+    wt = torch.from_numpy(W.outside_mask_weights(n, cfg["dx"], cfg["loss_cut"])).to(dev)
+    fw, bw = [], []
+    for _ in range(2):  # the first pass warms up
+        u = u0.clone().requires_grad_(True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record()
+        psiN = propagate(psi0, u, plan, nsteps, tf)
+        loss = torch.sum(wt * (psiN.real ** 2 + psiN.imag ** 2))
+        e1.record()
+        loss.backward()
+        e2.record()
+        torch.cuda.synchronize()
+        fw.append(e0.elapsed_time(e1))
+        bw.append(e1.elapsed_time(e2))
+    plan.check()
+    plan.close()
+    return {"workload": "soft_coulomb_laser_1d_gradient", "n": n, "steps": nsteps, "controls": nc,
+            "dtype": args.arith, "forward_ms": fw[-1], "backward_ms": bw[-1], "ratio": bw[-1] / fw[-1],
+            "grad_norm": float(torch.linalg.norm(u.grad).item()), "loss": float(loss.item()),
+            "checkpoints": int(np.ceil(np.sqrt(nsteps)))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -296,6 +332,8 @@ def main():
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--e2e-inner", type=int, default=50, help="CN steps per end-to-end call")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=2000,
+                    help="gradient run (N=2^20, 500 controls): steps for the adjoint/forward ratio (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -352,6 +390,8 @@ def main():
                "steps": args.f64_steps, "ms_per_step": ms64 / args.f64_steps,
                "roofline": roofline(prof64, n, "f64", measured_peaks(), args.block) if rank == 0 else None}
 
+    adj = adjoint_ratio(torch, cnb, args, dev) if (args.adjoint_steps > 0 and rank == 0) else None
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -379,6 +419,8 @@ def main():
             "clocks": clocks}
     if alt:
         line["f64_path"] = alt
+    if adj:
+        line["adjoint"] = adj
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle()
     print(json.dumps(line), flush=True)
