@@ -45,6 +45,7 @@ extern "C" {
 #endif
 
 typedef struct cn_plan_s* cn_plan;
+typedef struct cn_batch_s* cn_batch;
 
 typedef enum {
     CN_OK = 0,
@@ -212,6 +213,49 @@ cn_status cn_solve_tridiag_noalloc(const void* b, const void* a, const void* c, 
 /* Wait for the plan's stream work to finish (device synchronise) and return
  * the first device-side error recorded since the last call (then clear it). */
 cn_status cn_plan_status(cn_plan plan);
+
+/* ---- Batches: many independent systems of uneven sizes in one launch per stage.
+ *
+ * The paper solves one system at a time; a batch runs the same N-shaped solve
+ * (Sec. 4, Table 1; nested as in Eq. iteration) over `nsys` independent CN
+ * systems whose rows lie back to back in one complex128 array.  Every stage
+ * of every nesting level is ONE launch for all systems: a thread finds its
+ * system by binary search over the per-level block offsets, so the work of a
+ * launch is balanced across systems of any size mix.  Launches per step:
+ * 2 L + 1, with L the deepest system's level count.
+ *
+ * The systems share dx, dt, the potential kind, block sizes, arithmetic and
+ * flags (from `common`; common->n, x_min and cos_a are ignored).  System s
+ * has sizes[s] >= 3 rows, starts at row offset offsets[s] (cn_batch_offsets:
+ * the prefix sum of sizes) and its grid is x_j = x_min[s] + j dx.
+ *   x_min: host double[nsys], or NULL for x_min[s] = -floor(sizes[s]/2) dx;
+ *   cos_a: host double[nsys * n_cos] (CN_POT_COSSERIES; row s = system s's
+ *     coefficients), copied; the period is common->L when > 0, else the
+ *     system's own length sizes[s] dx;
+ *   CN_POT_ARRAY: common->V0 is a device double[sum of sizes], indexed like
+ *     the state; read only during cn_batch_create.
+ * The static diagonal part (2 + 2 dx^2 Vs) of every system is tabulated once
+ * at creation.  Ownership, streams and errors: as for plans. */
+cn_status cn_batch_create(const cn_desc* common, int64_t nsys, const int64_t* sizes, const double* x_min,
+                          const double* cos_a, cn_batch* out);
+
+/* Free the batch and its workspace (synchronises the device first).  NULL is a no-op. */
+cn_status cn_batch_destroy(cn_batch batch);
+
+/* offsets: host int64[nsys + 1]; receives the row offset of each system and,
+ * last, the total row count (the length of the batch state). */
+cn_status cn_batch_offsets(cn_batch batch, int64_t* offsets);
+
+/* nsteps CN steps of every system, as cn_step: psi_in / psi_out are device
+ * complex128[total rows] (may be equal); E_mid (device double[nsteps] or
+ * NULL) is the field shared by all systems.  Enqueues a fixed launch
+ * sequence with no host synchronisation and no allocation, so it may be
+ * captured into a CUDA graph and replayed. */
+cn_status cn_batch_step(cn_batch batch, const void* psi_in, void* psi_out, const double* E_mid, int64_t nsteps,
+                        void* stream);
+
+/* As cn_plan_status, for a batch. */
+cn_status cn_batch_status(cn_batch batch);
 
 /* Static description of a status code. */
 const char* cn_status_string(cn_status s);

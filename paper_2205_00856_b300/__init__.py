@@ -32,7 +32,8 @@ _STATUS = {0: "CN_OK", 1: "CN_ERR_INVALID_ARG", 2: "CN_ERR_UNSUPPORTED", 3: "CN_
 EXPORTS = ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_solve_tridiag",
            "cn_plan_query", "cn_plan_profile", "cn_plan_profile_read", "cn_plan_status", "cn_status_string",
            "cn_version", "cn_solve_tridiag_noalloc", "cn_adjoint_step", "cn_field_from_controls",
-           "cn_field_grad_to_controls")
+           "cn_field_grad_to_controls", "cn_batch_create", "cn_batch_destroy", "cn_batch_offsets",
+           "cn_batch_step", "cn_batch_status")
 NOALLOC_MAX_N = 1048576
 MAX_LEVELS = 24
 PROFILE_CLASSES = ("reduce_level0", "substitute_level0", "reduce_levels_ge1", "substitute_levels_ge1", "rs_stage")
@@ -98,6 +99,13 @@ def load(build_if_missing: bool = True):
             lib.cn_status_string.restype = C.c_char_p
             lib.cn_version.argtypes = []
             lib.cn_version.restype = C.c_char_p
+            lib.cn_batch_create.argtypes = [C.POINTER(_Desc), i64, vp, vp, vp, C.POINTER(vp)]
+            lib.cn_batch_destroy.argtypes = [vp]
+            lib.cn_batch_offsets.argtypes = [vp, vp]
+            lib.cn_batch_step.argtypes = [vp, vp, vp, vp, i64, vp]
+            lib.cn_batch_status.argtypes = [vp]
+            for f in ("cn_batch_create", "cn_batch_destroy", "cn_batch_offsets", "cn_batch_step", "cn_batch_status"):
+                getattr(lib, f).restype = C.c_int
             for f in ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_solve_tridiag",
                       "cn_plan_status", "cn_plan_query", "cn_plan_profile", "cn_plan_profile_read"):
                 getattr(lib, f).restype = C.c_int
@@ -258,6 +266,123 @@ class Plan:
 
     def check(self) -> None:
         _check(self.status(), "device status")
+
+
+class Batch:
+    """A cn_batch: nsys independent CN systems of uneven sizes stepped together,
+    one launch per stage and nesting level for all of them.
+
+    sizes: rows per system; the batch state is one complex128 tensor of
+    `total` rows with system s at rows offsets[s]:offsets[s+1].  x_min: per
+    system (None: -floor(n_s/2) dx).  cos_a: (nsys, n_cos) coefficients for
+    POT_COSSERIES, period L (<= 0: each system's own length n_s dx).  V0
+    (POT_ARRAY): float64 tensor of `total` values, read at creation only.
+    """
+
+    def __init__(self, sizes, dx, dt, x_min=None, pot=POT_NONE, V0=None, soft_s=2.0, cos_a=None, L=0.0,
+                 block=0, arith=ARITH_F64, flags=0, level_block=0):
+        import torch
+        self._lib = load()
+        self.sizes = np.ascontiguousarray(sizes, dtype=np.int64)
+        self.nsys = int(self.sizes.size)
+        self.dt = float(dt)
+        self.arith = int(arith)
+        self.block, self.level_block = int(block), int(level_block)
+        xm = None if x_min is None else np.ascontiguousarray(x_min, dtype=np.float64)
+        if xm is not None and xm.size != self.nsys:
+            raise ValueError("x_min needs one value per system")
+        cos = None if cos_a is None else np.ascontiguousarray(cos_a, dtype=np.float64)
+        n_cos = 0
+        if cos is not None:
+            if cos.ndim != 2 or cos.shape[0] != self.nsys:
+                raise ValueError("cos_a must have shape (nsys, n_cos)")
+            n_cos = cos.shape[1]
+        v0p = None
+        if pot == POT_ARRAY:
+            v0p = _dev_ptr(V0, torch.float64, int(self.sizes.sum()), "V0")
+        d = _Desc(0, float(dx), float(dt), 0.0, int(pot), n_cos, v0p, float(soft_s), None, float(L), int(block),
+                  self.arith, int(flags), int(level_block))
+        h = C.c_void_p()
+        _check(self._lib.cn_batch_create(C.byref(d), self.nsys, self.sizes.ctypes.data,
+                                         None if xm is None else xm.ctypes.data,
+                                         None if cos is None else cos.ctypes.data, C.byref(h)), "cn_batch_create")
+        self._h = h
+        self.offsets = np.empty(self.nsys + 1, np.int64)
+        _check(self._lib.cn_batch_offsets(self._h, self.offsets.ctypes.data), "cn_batch_offsets")
+        self.total = int(self.offsets[-1])
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.cn_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, psi_in, nsteps: int, E_mid=None, psi_out=None, stream=None):
+        """nsteps CN steps of every system; returns psi_out (allocated if None)."""
+        import torch
+        pin = _dev_ptr(psi_in, torch.complex128, self.total, "psi_in")
+        if psi_out is None:
+            psi_out = torch.empty_like(psi_in)
+        pout = _dev_ptr(psi_out, torch.complex128, self.total, "psi_out")
+        pe = None
+        if E_mid is not None:
+            if E_mid.numel() < nsteps:
+                raise ValueError("E_mid shorter than nsteps")
+            pe = _dev_ptr(E_mid, torch.float64, E_mid.numel(), "E_mid")
+        _check(self._lib.cn_batch_step(self._h, pin, pout, pe, int(nsteps), _stream_handle(stream)), "cn_batch_step")
+        return psi_out
+
+    def capture(self, psi, nsteps: int, E_mid=None):
+        """Record nsteps in-place steps of the batch state psi into a CUDA graph;
+        graph.replay() then runs them with one host call."""
+        import torch
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                self.step(psi, nsteps, E_mid=E_mid, psi_out=psi)
+        torch.cuda.current_stream().wait_stream(side)
+        return g
+
+    def status(self) -> int:
+        return int(self._lib.cn_batch_status(self._h))
+
+    def check(self) -> None:
+        _check(self.status(), "device status")
+
+
+def autotune_batch(sizes, dx, dt, candidates=None, steps: int = 3, repeats: int = 2, **kw):
+    """Pick (block, level_block) for a batch by timing `steps` CN steps of each
+    candidate on a synthetic state (the CN step costs the same for any state).
+    Returns (best_block, best_level_block, {candidate: ms per step})."""
+    import torch
+    if candidates is None:
+        candidates = [(m0, ml) for m0 in (6, 8, 10, 12, 16) for ml in (8, 16)]
+    times = {}
+    for m0, ml in candidates:
+        b = Batch(sizes, dx, dt, block=m0, level_block=ml, **kw)
+        psi = torch.zeros(b.total, dtype=torch.complex128, device="cuda")
+        b.step(psi, 1, psi_out=psi)  # warm-up
+        best = float("inf")
+        for _ in range(repeats):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.step(psi, steps, psi_out=psi)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / steps)
+        b.check()
+        times[(m0, ml)] = best
+        del psi
+        b.close()
+    m0, ml = min(times, key=times.get)
+    return m0, ml, times
 
 
 def solve_tridiag_noalloc(b, a, c, d, x=None, arith=ARITH_F64, stream=None):

@@ -1,7 +1,13 @@
-// cn_api.cu -- C ABI (include/cn.h): plans, argument validation, and the launch
-// sequence of the nested N-shaped solve (Eq. iteration of the paper).
+// cn_api.cu -- C ABI (include/cn.h): plans and batches, argument validation, and
+// the launch sequence of the nested N-shaped solve (Eq. iteration of the paper).
+//
+// A plan is a batch of one system.  Both hold an Engine: the level hierarchy of
+// every system (rows, blocks and offsets per level), the reduced-system storage
+// of all levels, and the CN parameters.  One launch per stage and level serves
+// all systems of a batch; a plan passes its single system's entries by value.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -18,28 +24,38 @@ namespace {
 constexpr int kDefaultLevelBlock = 8;  // rows per block on the reduced levels (>= 1)
 constexpr int kDefaultBlock = 8;       // rows per level-0 block unless the descriptor says otherwise
 constexpr int kMaxBlockRows = 32;      // shared memory of the substitution: 2 x 32 x 128 x 16 B
+constexpr size_t kCplx = 16;           // bytes per complex in either compute type
+constexpr int64_t kMaxBatch = 1 << 24;
 
-struct Level {
-    int64_t n = 0;         // rows
-    int64_t P = 0;         // blocks (joint lines 0..P)
-    int m = 0;             // block size
-    void* rows = nullptr;  // LevelRow<R>[n] (levels >= 1)
-    void* slot = nullptr;  // LevelSlot<R>[CTAs of the level below + 1]
-    void* x = nullptr;     // Store<R>::T[n]: solution of this level (levels >= 1)
+struct LevelData {
+    int m = 0;                // rows per block at this level
+    int64_t total = 0;        // blocks of all systems (sum of P)
+    int64_t rows_total = 0;   // rows of all systems present at this level
+    std::vector<LvlSys> sys;  // one entry per system
+    LvlSys* d_sys = nullptr;  // device copy (batches)
+    void* rows = nullptr;     // LevelRow<R>[rows_total] (levels >= 1)
+    void* slot = nullptr;     // LevelSlot<R>[CTAs of the level below + 1]
+    void* x = nullptr;        // Store<R>::T[rows_total]: solution (levels >= 1)
 };
 
 }  // namespace
 
-struct cn_plan_s {
-    cn_desc desc;
+struct Engine {
+    cn_desc desc;                 // desc.n: rows of all systems
     int device = 0;
-    std::vector<Level> lv;     // lv[0]: the system itself; lv[L]: solved by the RS stage
-    double2* state = nullptr;  // n complex128 scratch for the step ping-pong (recompute mode)
-    void* keep = nullptr;      // 2 n Store<R>::T: explicit rhs and pivot per point (store mode)
-    void* tab = nullptr;       // bt0 table (compute type) or NULL
-    int* status = nullptr;     // device status word
+    bool batched = false;
+    int nsys = 0;
+    std::vector<LevelData> lv;    // lv[0]: the systems themselves
+    std::vector<int> base_level;  // per system: the level the RS stage solves
+    void* d_base = nullptr;       // BaseSys<R>[nsys] (batches)
+    std::vector<SysGrid> grid;    // per system
+    SysGrid* d_grid = nullptr;    // device copy (batches)
+    double2* state = nullptr;     // ping-pong state (recompute mode)
+    void* keep = nullptr;         // 2 m P entries per system: d^ and pivot (store mode)
+    void* tab = nullptr;          // bt0 table (compute type) or NULL
+    int* status = nullptr;        // device status word
     CNParams cnp;
-    std::vector<double> cos_a;
+    std::vector<double> cos_a;    // n_cos coefficients per system
     // cn_step_host staging (allocated on first use)
     double2* h_in = nullptr;
     double2* h_out = nullptr;
@@ -51,29 +67,42 @@ struct cn_plan_s {
     int part_n = 0;
     // kernel timing (cn_plan_profile)
     bool profiling = false;
-    std::vector<cudaEvent_t> ev_pool;  // events owned by the plan
+    std::vector<cudaEvent_t> ev_pool;  // events owned by the engine
     size_t ev_used = 0;                // events handed out since the last read
     std::vector<int> rec_class;        // class of record r (events 2r, 2r+1)
     int64_t workspace_bytes = 0;
 };
 
+struct cn_plan_s : Engine {};
+struct cn_batch_s : Engine {};
+
 namespace {
 
 cn_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CN_OK : CN_ERR_CUDA; }
+cn_status alloc_status(cudaError_t e) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? CN_ERR_OOM : CN_ERR_CUDA;
+}
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
-cn_status validate_desc(const cn_desc* d) {
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+unsigned grid_for(int64_t P) { return (unsigned)ceil_div(P, kThreads); }
+
+// need_n: a plan (one system of desc->n rows); a batch gives its sizes apart.
+cn_status validate_desc(const cn_desc* d, bool need_n) {
     if (!d) return CN_ERR_INVALID_ARG;
-    if (d->n < 3) return CN_ERR_INVALID_ARG;
+    if (need_n && d->n < 3) return CN_ERR_INVALID_ARG;
     if (!(d->dx > 0.0) || !std::isfinite(d->dx)) return CN_ERR_INVALID_ARG;
     if (!std::isfinite(d->dt) || d->dt == 0.0 || !std::isfinite(d->x_min)) return CN_ERR_INVALID_ARG;
     if (d->pot < CN_POT_NONE || d->pot > CN_POT_COSSERIES) return CN_ERR_INVALID_ARG;
-    if (d->pot == CN_POT_ARRAY && (!d->V0 || (reinterpret_cast<uintptr_t>(d->V0) & 7u))) return CN_ERR_INVALID_ARG;
+    if (d->pot == CN_POT_ARRAY && (!d->V0 || !aligned8(d->V0))) return CN_ERR_INVALID_ARG;
     if (d->pot == CN_POT_SOFTCOULOMB && !(d->soft_s > 0.0)) return CN_ERR_INVALID_ARG;
     if (d->pot == CN_POT_COSSERIES) {
-        if (d->n_cos < 0 || d->n_cos > kMaxCos || (d->n_cos > 0 && !d->cos_a) || !(d->L > 0.0))
-            return CN_ERR_INVALID_ARG;
+        if (d->n_cos < 0 || d->n_cos > kMaxCos) return CN_ERR_INVALID_ARG;
+        if (need_n && ((d->n_cos > 0 && !d->cos_a) || !(d->L > 0.0))) return CN_ERR_INVALID_ARG;
+        if (!std::isfinite(d->L)) return CN_ERR_INVALID_ARG;
     }
     if (d->block != 0 && (d->block < 3 || d->block > kMaxBlockRows)) return CN_ERR_INVALID_ARG;
     if (d->level_block != 0 && (d->level_block < 3 || d->level_block > kMaxBlockRows)) return CN_ERR_INVALID_ARG;
@@ -82,14 +111,17 @@ cn_status validate_desc(const cn_desc* d) {
     return CN_OK;
 }
 
-void free_plan_memory(cn_plan p) {
+void free_engine(Engine* p) {
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     p->ev_pool.clear();
-    for (Level& L : p->lv) {
+    for (LevelData& L : p->lv) {
         cudaFree(L.rows);
         cudaFree(L.slot);
         cudaFree(L.x);
+        cudaFree(L.d_sys);
     }
+    cudaFree(p->d_base);
+    cudaFree(p->d_grid);
     cudaFree(p->state);
     cudaFree(p->keep);
     cudaFree(p->tab);
@@ -101,15 +133,11 @@ void free_plan_memory(cn_plan p) {
     cudaFree(p->part);
 }
 
-int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
-
-unsigned grid_for(int64_t P) { return (unsigned)ceil_div(P, kThreads); }
-
 // --------------------------------------------------------------- kernel timing
 enum { kProfReduce0 = 0, kProfSubst0 = 1, kProfReduceL = 2, kProfSubstL = 3, kProfBase = 4 };
 
 // Two events per record; the pool grows on demand and is reused after a read.
-bool reserve_events(cn_plan p, size_t k) {
+bool reserve_events(Engine* p, size_t k) {
     while (p->ev_pool.size() < p->ev_used + k) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return false;
@@ -119,10 +147,10 @@ bool reserve_events(cn_plan p, size_t k) {
 }
 
 struct ProfScope {
-    cn_plan p;
+    Engine* p;
     cudaStream_t st;
     cudaEvent_t stop = nullptr;
-    ProfScope(cn_plan p_, int cls, cudaStream_t st_) : p(p_), st(st_) {
+    ProfScope(Engine* p_, int cls, cudaStream_t st_) : p(p_), st(st_) {
         if (!p->profiling || !reserve_events(p, 2)) return;
         cudaEvent_t start = p->ev_pool[p->ev_used++];
         stop = p->ev_pool[p->ev_used++];
@@ -134,122 +162,256 @@ struct ProfScope {
     }
 };
 
-template <class R> LevelRow<R>* rows_of(const Level& L) { return static_cast<LevelRow<R>*>(L.rows); }
-template <class R> LevelSlot<R>* slot_of(const Level& L) { return static_cast<LevelSlot<R>*>(L.slot); }
-template <class R> typename Store<R>::T* x_of(const Level& L) { return static_cast<typename Store<R>::T*>(L.x); }
-
-template <class R> LevelSource<R> level_source(const Level& L) {
-    LevelSource<R> s;
-    s.rows = rows_of<R>(L);
-    s.slot = slot_of<R>(L);
-    s.n = L.n;
-    s.slot_stride = kThreads;
-    return s;
-}
-
-// --------------------------------------------------------------- launch helpers
-// Shared memory of the substitution kernels: per thread, one (kept) or two
-// complex values per block row.
-size_t subst_smem(int m, int arrays) { return (size_t)arrays * (size_t)m * kThreads * 16; }
-size_t kept_smem(int m) { return (size_t)m * kTileStride * 16; }
-
-template <class R, class Src>
-cudaError_t launch_reduce(const Src& src, const Level& L, const Level& next, int* status, cudaStream_t st) {
-    k_reduce<R, Src><<<grid_for(L.P), kThreads, 0, st>>>(src, L.n, L.P, L.m, rows_of<R>(next), slot_of<R>(next),
-                                                         status);
-    return cudaGetLastError();
-}
-
-template <class R, class Src, class XT>
-cudaError_t launch_substitute(const Src& src, const Level& L, const Level& next, XT* x, int* status, cudaStream_t st) {
-    k_substitute<R, Src, XT><<<grid_for(L.P), kThreads, subst_smem(L.m, 2), st>>>(src, L.n, L.P, L.m, x_of<R>(next),
-                                                                                  x, status);
-    return cudaGetLastError();
-}
-
-// Opt every substitution kernel into the dynamic shared memory its largest block needs.
-template <class R>
-cudaError_t set_smem_limits(int m0, int ml) {
-    cudaError_t e = cudaFuncSetAttribute(k_substitute<R, ArraySource, double2>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)subst_smem(m0, 2));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_substitute<R, LevelSource<R>, typename Store<R>::T>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)subst_smem(ml, 2));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_cn_substitute<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)subst_smem(m0, 2));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_cn_substitute_kept<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kept_smem(m0));
+// --------------------------------------------------------------- hierarchy
+// Level l of system s has n rows cut into P = ceil((n-1)/m) blocks; its P + 1
+// joint lines are the rows of level l + 1, until a level has <= kBaseMax rows
+// (the RS stage).  Systems that reached their RS level have no rows below it.
+cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
+    const int ns = (int)sizes.size();
+    p->nsys = ns;
+    p->base_level.assign(ns, -1);
+    {
+        LevelData L0;
+        L0.m = p->desc.block;
+        L0.sys.resize(ns);
+        int64_t roff = 0, boff = 0;
+        for (int s = 0; s < ns; ++s) {
+            LvlSys& e = L0.sys[s];
+            e.n = sizes[s];
+            e.P = ceil_div(e.n - 1, L0.m);
+            e.row_off = roff;
+            e.blk_off = boff;
+            e.prod_blk_off = 0;
+            roff += e.n;
+            boff += e.P;
+        }
+        L0.rows_total = roff;
+        L0.total = boff;
+        p->lv.push_back(std::move(L0));
+    }
+    for (;;) {
+        const int l = (int)p->lv.size();
+        if (l >= CN_MAX_LEVELS) return cudaErrorInvalidValue;
+        LevelData L;
+        L.m = p->desc.level_block;
+        L.sys.resize(ns);
+        int64_t roff = 0, boff = 0;
+        for (int s = 0; s < ns; ++s) {
+            LvlSys& e = L.sys[s];
+            const LvlSys& q = p->lv[(size_t)l - 1].sys[s];
+            e.n = q.P > 0 ? q.P + 1 : 0;
+            e.P = 0;
+            if (e.n > 0) {
+                if (e.n <= kBaseMax) p->base_level[s] = l;
+                else e.P = ceil_div(e.n - 1, L.m);
+            }
+            e.row_off = roff;
+            e.blk_off = boff;
+            e.prod_blk_off = q.blk_off;
+            roff += e.n;
+            boff += e.P;
+        }
+        L.rows_total = roff;
+        L.total = boff;
+        p->lv.push_back(std::move(L));
+        if (boff == 0) break;
+    }
+    cudaError_t e = cudaSuccess;
+    for (size_t l = 1; l < p->lv.size() && e == cudaSuccess; ++l) {
+        LevelData& L = p->lv[l];
+        const size_t nslot = grid_for(p->lv[l - 1].total) + 1;
+        p->workspace_bytes += (int64_t)(5 * kCplx * L.rows_total + 3 * kCplx * nslot);
+        e = cudaMalloc(&L.rows, 4 * kCplx * (size_t)L.rows_total);
+        if (e == cudaSuccess) e = cudaMalloc(&L.slot, 3 * kCplx * nslot);
+        if (e == cudaSuccess) e = cudaMalloc(&L.x, kCplx * (size_t)L.rows_total);
+        if (e == cudaSuccess) e = cudaMemset(L.slot, 0, 3 * kCplx * nslot);
+    }
+    if (e == cudaSuccess && p->batched) {
+        for (LevelData& L : p->lv) {
+            p->workspace_bytes += (int64_t)(sizeof(LvlSys) * (size_t)ns);
+            e = cudaMalloc(&L.d_sys, sizeof(LvlSys) * (size_t)ns);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(L.d_sys, L.sys.data(), sizeof(LvlSys) * (size_t)ns, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) break;
+        }
+    }
     return e;
 }
 
-// Levels 1..L of the nested solve: reductions down, RS, substitutions up.
+template <class R> LevelRow<R>* rows_of(const LevelData& L) { return static_cast<LevelRow<R>*>(L.rows); }
+template <class R> LevelSlot<R>* slot_of(const LevelData& L) { return static_cast<LevelSlot<R>*>(L.slot); }
+template <class R> typename Store<R>::T* x_of(const LevelData& L) { return static_cast<typename Store<R>::T*>(L.x); }
+
+template <class R> LevelSource<R> level_source(const LevelData& L) {
+    LevelSource<R> s;
+    s.rows = rows_of<R>(L);
+    s.slot = slot_of<R>(L);
+    s.n = 0;
+    s.prod = 0;
+    return s;
+}
+
+// Per-system RS inputs of a batch, on the device.
 template <class R>
-cudaError_t solve_levels(cn_plan p, cudaStream_t st) {
-    const int L = (int)p->lv.size() - 1;
-    cudaError_t e = cudaSuccess;
-    for (int l = 1; l < L; ++l) {
-        ProfScope ps(p, kProfReduceL, st);
-        e = launch_reduce<R>(level_source<R>(p->lv[l]), p->lv[l], p->lv[l + 1], p->status, st);
-        if (e != cudaSuccess) return e;
+cudaError_t build_base_table(Engine* p) {
+    std::vector<BaseSys<R>> tb((size_t)p->nsys);
+    for (int s = 0; s < p->nsys; ++s) {
+        const LevelData& L = p->lv[(size_t)p->base_level[s]];
+        tb[s].src = level_source<R>(L).bind(L.sys[s]);
+        tb[s].x = x_of<R>(L) + L.sys[s].row_off;
     }
+    p->workspace_bytes += (int64_t)(sizeof(BaseSys<R>) * tb.size());
+    cudaError_t e = cudaMalloc(&p->d_base, sizeof(BaseSys<R>) * tb.size());
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_base, tb.data(), sizeof(BaseSys<R>) * tb.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+// Calls f(map of level l, map of level l + 1).
+template <class F>
+void with_maps(const Engine* p, size_t l, F f) {
+    const LevelData& L = p->lv[l];
+    const LevelData& N = p->lv[std::min(l + 1, p->lv.size() - 1)];
+    if (p->batched) f(ManySys{L.d_sys, p->nsys, L.total}, ManySys{N.d_sys, p->nsys, N.total});
+    else f(OneSys{L.sys[0]}, OneSys{N.sys[0]});
+}
+
+// Calls f(map of level 0, map of level 1, per-system grids).
+template <class F>
+void with_maps_grid(const Engine* p, F f) {
+    const LevelData& L = p->lv[0];
+    const LevelData& N = p->lv[1];
+    if (p->batched) f(ManySys{L.d_sys, p->nsys, L.total}, ManySys{N.d_sys, p->nsys, N.total}, ManyGrid{p->d_grid});
+    else f(OneSys{L.sys[0]}, OneSys{N.sys[0]}, OneGrid{p->grid[0]});
+}
+
+// --------------------------------------------------------------- launches
+// Shared memory of the substitutions: two complex values per block row and thread.
+size_t subst_smem(int m) { return 2 * (size_t)m * kThreads * kCplx; }
+size_t kept_smem(int m) { return (size_t)m * kTileStride * kCplx; }
+
+template <class R, class Src, class Map>
+cudaError_t launch_reduce(const Src& src, Map sys, Map next, int m, const LevelData& nextL, int* status,
+                          int64_t total, cudaStream_t st) {
+    if (total == 0) return cudaSuccess;
+    k_reduce<R, Src, Map><<<grid_for(total), kThreads, 0, st>>>(src, sys, next, m, rows_of<R>(nextL),
+                                                                slot_of<R>(nextL), status);
+    return cudaGetLastError();
+}
+
+template <class R, class Src, class Map, class XT>
+cudaError_t launch_substitute(const Src& src, Map sys, Map next, int m, const LevelData& nextL, XT* x, int* status,
+                              int64_t total, cudaStream_t st) {
+    if (total == 0) return cudaSuccess;
+    k_substitute<R, Src, Map, XT><<<grid_for(total), kThreads, subst_smem(m), st>>>(src, sys, next, m,
+                                                                                  x_of<R>(nextL), x, status);
+    return cudaGetLastError();
+}
+
+// Opt the substitution kernels into the dynamic shared memory their largest block needs.
+template <class R, class Map, class Grid>
+cudaError_t set_smem_limits_map(int m0, int ml) {
+    typedef typename Store<R>::T ST;
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_substitute<R, ArraySource, Map, double2>, a, (int)subst_smem(m0));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_substitute<R, LevelSource<R>, Map, ST>, a, (int)subst_smem(ml));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute<R, Map, Grid>, a, (int)subst_smem(m0));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute_kept<R, Map>, a, (int)kept_smem(m0));
+    return e;
+}
+
+template <class R>
+cudaError_t set_smem_limits(const Engine* p) {
+    if (p->batched) return set_smem_limits_map<R, ManySys, ManyGrid>(p->desc.block, p->desc.level_block);
+    return set_smem_limits_map<R, OneSys, OneGrid>(p->desc.block, p->desc.level_block);
+}
+
+// Levels >= 1 of the nested solve: reductions down, RS, substitutions up.
+template <class R>
+cudaError_t solve_levels(Engine* p, cudaStream_t st) {
+    const size_t L = p->lv.size();
+    cudaError_t e = cudaSuccess;
+    for (size_t l = 1; l + 1 < L && e == cudaSuccess; ++l) {
+        ProfScope ps(p, kProfReduceL, st);
+        with_maps(p, l, [&](auto a, auto b) {
+            e = launch_reduce<R>(level_source<R>(p->lv[l]), a, b, p->lv[l].m, p->lv[l + 1], p->status,
+                                 p->lv[l].total, st);
+        });
+    }
+    if (e != cudaSuccess) return e;
     {
         ProfScope ps(p, kProfBase, st);
-        k_base<R><<<1, 32, 0, st>>>(level_source<R>(p->lv[L]), p->lv[L].n, x_of<R>(p->lv[L]), p->status);
+        if (p->batched) {
+            k_base_many<R><<<(unsigned)ceil_div(p->nsys, 128), 128, 0, st>>>(
+                static_cast<const BaseSys<R>*>(p->d_base), p->nsys, p->status);
+        } else {
+            const LevelData& B = p->lv[(size_t)p->base_level[0]];
+            k_base<R><<<1, 32, 0, st>>>(level_source<R>(B).bind(B.sys[0]), x_of<R>(B), p->status);
+        }
         e = cudaGetLastError();
     }
-    if (e != cudaSuccess) return e;
-    for (int l = L - 1; l >= 1; --l) {
+    for (size_t l = L - 2; l >= 1 && e == cudaSuccess; --l) {
         ProfScope ps(p, kProfSubstL, st);
-        e = launch_substitute<R>(level_source<R>(p->lv[l]), p->lv[l], p->lv[l + 1], x_of<R>(p->lv[l]), p->status, st);
-        if (e != cudaSuccess) return e;
+        with_maps(p, l, [&](auto a, auto b) {
+            e = launch_substitute<R>(level_source<R>(p->lv[l]), a, b, p->lv[l].m, p->lv[l + 1], x_of<R>(p->lv[l]),
+                                     p->status, p->lv[l].total, st);
+        });
     }
-    return cudaSuccess;
+    return e;
 }
 
-// General tridiagonal solve (arrays at level 0).
+// General tridiagonal solve (arrays at level 0, one system).
 template <class R>
-cudaError_t solve_arrays(cn_plan p, const ArraySource& src, double2* x, cudaStream_t st) {
-    cudaError_t e;
+cudaError_t solve_arrays(Engine* p, const ArraySource& src, double2* x, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
     {
         ProfScope ps(p, kProfReduce0, st);
-        e = launch_reduce<R>(src, p->lv[0], p->lv[1], p->status, st);
+        with_maps(p, 0, [&](auto a, auto b) {
+            e = launch_reduce<R>(src, a, b, p->lv[0].m, p->lv[1], p->status, p->lv[0].total, st);
+        });
     }
     if (e != cudaSuccess) return e;
     if ((e = solve_levels<R>(p, st)) != cudaSuccess) return e;
     ProfScope ps(p, kProfSubst0, st);
-    return launch_substitute<R>(src, p->lv[0], p->lv[1], x, p->status, st);
+    with_maps(p, 0, [&](auto a, auto b) {
+        e = launch_substitute<R>(src, a, b, p->lv[0].m, p->lv[1], x, p->status, p->lv[0].total, st);
+    });
+    return e;
 }
 
-// One CN-type step (level 0 generated on the fly), result in x.
+// One CN-type step of every system (level 0 generated on the fly), result in x.
 template <class R>
-cudaError_t cn_solve(cn_plan p, const CNStep& s, double2* x, cudaStream_t st) {
-    const Level& L0 = p->lv[0];
-    const Level& L1 = p->lv[1];
-    const unsigned grid = grid_for(L0.P);
+cudaError_t cn_solve(Engine* p, const CNStep& s, double2* x, cudaStream_t st) {
     typedef typename Store<R>::T ST;
+    const LevelData& L0 = p->lv[0];
+    const LevelData& L1 = p->lv[1];
+    const unsigned grid = grid_for(L0.total);
     ST* keep = static_cast<ST*>(p->keep);
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
     {
         ProfScope ps(p, kProfReduce0, st);
-        k_cn_reduce<R><<<grid, kThreads, 0, st>>>(s, L0.P, L0.m, rows_of<R>(L1), slot_of<R>(L1), keep, p->status);
+        with_maps_grid(p, [&](auto a, auto b, auto gr) {
+            k_cn_reduce<R><<<grid, kThreads, 0, st>>>(s, a, b, gr, L0.m, rows_of<R>(L1), slot_of<R>(L1), keep,
+                                                      p->status);
+        });
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
     if ((e = solve_levels<R>(p, st)) != cudaSuccess) return e;
     ProfScope ps(p, kProfSubst0, st);
-    if (keep)
-        k_cn_substitute_kept<R><<<grid, kThreads, kept_smem(L0.m), st>>>(L0.n, L0.P, L0.m, keep, x_of<R>(L1), x);
-    else
-        k_cn_substitute<R><<<grid, kThreads, subst_smem(L0.m, 2), st>>>(s, L0.P, L0.m, x_of<R>(L1), x, p->status);
+    with_maps_grid(p, [&](auto a, auto b, auto gr) {
+        if (keep)
+            k_cn_substitute_kept<R><<<grid, kThreads, kept_smem(L0.m), st>>>(a, b, L0.m, keep, x_of<R>(L1), x);
+        else
+            k_cn_substitute<R><<<grid, kThreads, subst_smem(L0.m), st>>>(s, a, b, gr, L0.m, x_of<R>(L1), x,
+                                                                         p->status);
+    });
     return cudaGetLastError();
 }
 
 template <class R>
-cudaError_t cn_steps(cn_plan p, const double2* in, double2* out, const double* E_mid, int64_t nsteps,
+cudaError_t cn_steps(Engine* p, const double2* in, double2* out, const double* E_mid, int64_t nsteps,
                      cudaStream_t st) {
-    const size_t bytes = sizeof(double2) * (size_t)p->desc.n;
+    const size_t bytes = sizeof(double2) * (size_t)p->lv[0].rows_total;
     if (nsteps == 0) {
         if (in == out) return cudaSuccess;
         return cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st);
@@ -284,6 +446,134 @@ cudaError_t cn_steps(cn_plan p, const double2* in, double2* out, const double* E
 
 size_t real_size(int arith) { return arith == CN_ARITH_DF64 ? sizeof(df) : sizeof(double); }
 
+DFc split(double v) {
+    df d = df_from_double(v);
+    DFc r;
+    r.hi = d.hi;
+    r.lo = d.lo;
+    return r;
+}
+
+SysGrid make_grid(double x_min, double dx, int64_t n) {
+    SysGrid g;
+    double jo = std::nearbyint(-x_min / dx);
+    if (jo < 0) jo = 0;
+    if (jo > (double)(n - 1)) jo = (double)(n - 1);
+    g.j_o = (int64_t)jo;
+    g.x_o = x_min + (double)g.j_o * dx;
+    g.xo_f = split(g.x_o);
+    return g;
+}
+
+// Common part of plan and batch creation: sizes and x_min per system, cos_a
+// (n_cos per system, row-major) for CN_POT_COSSERIES with period desc->L if
+// > 0, else the system's own length n_s dx.
+cn_status create_engine(Engine* p, const cn_desc* desc, const std::vector<int64_t>& sizes,
+                        const std::vector<double>& x_min, const double* cos_a) {
+    p->desc = *desc;
+    if (p->desc.block == 0) p->desc.block = kDefaultBlock;
+    if (p->desc.level_block == 0) p->desc.level_block = kDefaultLevelBlock;
+    if (cudaGetDevice(&p->device) != cudaSuccess) return CN_ERR_CUDA;
+    const int ns = (int)sizes.size();
+    const int ncos = desc->pot == CN_POT_COSSERIES ? desc->n_cos : 0;
+    if (ncos > 0) p->cos_a.assign(cos_a, cos_a + (size_t)ncos * (size_t)ns);
+    p->desc.cos_a = nullptr;
+    const bool df_mode = desc->arith == CN_ARITH_DF64;
+    // A batch always tabulates bt0 (one launch per system here, none per step).
+    const bool use_table = (desc->flags & CN_FLAG_COEFF_TABLE) || p->batched ||
+                           (df_mode && (desc->pot == CN_POT_ARRAY || desc->pot == CN_POT_COSSERIES));
+    const bool recompute = (desc->flags & CN_FLAG_RECOMPUTE) != 0;
+
+    cudaError_t e = build_hierarchy(p, sizes);
+    if (e != cudaSuccess) return e == cudaErrorInvalidValue ? CN_ERR_UNSUPPORTED : alloc_status(e);
+    const int64_t rows0 = p->lv[0].rows_total;
+    // keep: entries (2k) P + t and (2k+1) P + t for block rows k = 1..m-1 of each system
+    const size_t keep_entries = 2 * (size_t)p->lv[0].m * (size_t)p->lv[0].total;
+    p->workspace_bytes += (int64_t)(recompute ? kCplx * rows0 : kCplx * keep_entries) + (int64_t)sizeof(int);
+    if (recompute) e = cudaMalloc(&p->state, kCplx * (size_t)rows0);
+    else e = cudaMalloc(&p->keep, kCplx * keep_entries);
+    if (e == cudaSuccess) e = cudaMalloc(&p->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(int));
+    if (e == cudaSuccess && use_table) {
+        p->workspace_bytes += (int64_t)(real_size(desc->arith) * (size_t)rows0);
+        e = cudaMalloc(&p->tab, real_size(desc->arith) * (size_t)rows0);
+    }
+    p->grid.resize(ns);
+    for (int s = 0; s < ns; ++s) p->grid[s] = make_grid(x_min[s], desc->dx, sizes[s]);
+    if (e == cudaSuccess && p->batched) {
+        p->workspace_bytes += (int64_t)(sizeof(SysGrid) * (size_t)ns);
+        e = cudaMalloc(&p->d_grid, sizeof(SysGrid) * (size_t)ns);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_grid, p->grid.data(), sizeof(SysGrid) * (size_t)ns, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = df_mode ? build_base_table<df>(p) : build_base_table<double>(p);
+    }
+    if (e != cudaSuccess) return alloc_status(e);
+
+    CNParams& c = p->cnp;
+    std::memset(&c, 0, sizeof(c));
+    c.dx = desc->dx;
+    c.c1 = 2.0 * desc->dx * desc->dx;
+    c.gt = 4.0 * desc->dx * desc->dx / desc->dt;
+    c.pot = desc->pot;
+    c.V0 = desc->V0;
+    c.soft_s = desc->soft_s;
+    c.n_cos = ncos;
+    c.dx_f = split(c.dx);
+    c.c1_f = split(c.c1);
+    c.gt_f = split(c.gt);
+    c.soft_f = split(c.soft_s);
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    if (use_table) {
+        // static part of the diagonal, one system at a time (once per plan or batch)
+        for (int s = 0; s < ns && e == cudaSuccess; ++s) {
+            CNParams cs = c;
+            const int64_t ro = p->lv[0].sys[s].row_off;
+            if (desc->pot == CN_POT_ARRAY) cs.V0 = desc->V0 + ro;
+            if (ncos > 0) {
+                const double L = desc->L > 0.0 ? desc->L : (double)sizes[s] * desc->dx;
+                cs.two_pi_over_L = two_pi / L;
+                for (int k = 0; k < ncos; ++k) cs.cos_a[k] = p->cos_a[(size_t)s * ncos + k];
+            }
+            const unsigned g = (unsigned)ceil_div(sizes[s], 256);
+            if (df_mode) k_beta0_table<df><<<g, 256>>>(cs, p->grid[s], sizes[s], static_cast<df*>(p->tab) + ro);
+            else k_beta0_table<double><<<g, 256>>>(cs, p->grid[s], sizes[s], static_cast<double*>(p->tab) + ro);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    } else if (ncos > 0) {
+        c.two_pi_over_L = two_pi / desc->L;
+        for (int k = 0; k < ncos; ++k) c.cos_a[k] = p->cos_a[(size_t)k];
+    }
+    if (e == cudaSuccess) e = df_mode ? set_smem_limits<df>(p) : set_smem_limits<double>(p);
+    if (e != cudaSuccess) return alloc_status(e);
+    return CN_OK;
+}
+
+cn_status run_steps(Engine* p, const void* psi_in, void* psi_out, const double* E_mid, int64_t nsteps, void* stream) {
+    if (!psi_in || !psi_out || nsteps < 0) return CN_ERR_INVALID_ARG;
+    if (!aligned16(psi_in) || !aligned16(psi_out)) return CN_ERR_INVALID_ARG;
+    if (E_mid && !aligned8(E_mid)) return CN_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const double2* in = static_cast<const double2*>(psi_in);
+    double2* out = static_cast<double2*>(psi_out);
+    cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? cn_steps<df>(p, in, out, E_mid, nsteps, st)
+                                                     : cn_steps<double>(p, in, out, E_mid, nsteps, st);
+    return cuda_status(e);
+}
+
+cn_status read_status(Engine* p) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return CN_ERR_CUDA;
+    int h = 0;
+    if (cudaMemcpy(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CN_ERR_CUDA;
+    if (h != 0 && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) return CN_ERR_CUDA;
+    return static_cast<cn_status>(h);
+}
+
+void destroy_engine(Engine* p) {
+    cudaDeviceSynchronize();
+    free_engine(p);
+}
+
 }  // namespace
 
 extern "C" {
@@ -301,107 +591,20 @@ const char* cn_status_string(cn_status s) {
     }
 }
 
-const char* cn_version(void) { return "cn_b300 0.4 sm_103a"; }
+const char* cn_version(void) { return "cn_b300 0.5 sm_103a"; }
 
 cn_status cn_plan_create(const cn_desc* desc, cn_plan* out) {
     if (!out) return CN_ERR_INVALID_ARG;
     *out = nullptr;
-    cn_status v = validate_desc(desc);
+    cn_status v = validate_desc(desc, true);
     if (v != CN_OK) return v;
     cn_plan p = new (std::nothrow) cn_plan_s();
     if (!p) return CN_ERR_OOM;
-    p->desc = *desc;
-    if (p->desc.block == 0) p->desc.block = kDefaultBlock;
-    if (p->desc.level_block == 0) p->desc.level_block = kDefaultLevelBlock;
-    if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return CN_ERR_CUDA; }
-    if (desc->pot == CN_POT_COSSERIES && desc->n_cos > 0) p->cos_a.assign(desc->cos_a, desc->cos_a + desc->n_cos);
-    p->desc.cos_a = nullptr;
-    const bool df_mode = desc->arith == CN_ARITH_DF64;
-    const bool use_table = (desc->flags & CN_FLAG_COEFF_TABLE) ||
-                           (df_mode && (desc->pot == CN_POT_ARRAY || desc->pot == CN_POT_COSSERIES));
-
-    // levels: level l has n_l rows in P_l blocks of m_l rows; n_{l+1} = P_l + 1
-    int64_t n = desc->n;
-    int m = p->desc.block;
-    for (;;) {
-        Level L;
-        L.n = n;
-        L.m = m;
-        L.P = ceil_div(n - 1, m);
-        p->lv.push_back(L);
-        n = L.P + 1;
-        m = p->desc.level_block;
-        if (n <= kBaseMax) {
-            Level B;
-            B.n = n;
-            p->lv.push_back(B);
-            break;
-        }
-    }
-    const size_t cplx = 16;  // bytes per complex in either compute type
-    cudaError_t e = cudaSuccess;
-    for (size_t l = 1; l < p->lv.size() && e == cudaSuccess; ++l) {
-        Level& L = p->lv[l];
-        const size_t nslot = grid_for(p->lv[l - 1].P) + 1;
-        p->workspace_bytes += (int64_t)(5 * cplx * L.n + 3 * cplx * nslot);
-        e = cudaMalloc(&L.rows, 4 * cplx * (size_t)L.n);
-        if (e == cudaSuccess) e = cudaMalloc(&L.slot, 3 * cplx * nslot);
-        if (e == cudaSuccess) e = cudaMalloc(&L.x, cplx * (size_t)L.n);
-        if (e == cudaSuccess) e = cudaMemset(L.slot, 0, 3 * cplx * nslot);
-    }
-    const bool recompute = (desc->flags & CN_FLAG_RECOMPUTE) != 0;
-    // keep: entries (2k) P + t and (2k+1) P + t for block rows k = 1..m-1
-    const size_t keep_entries = 2 * (size_t)p->lv[0].m * (size_t)p->lv[0].P;
-    p->workspace_bytes += (int64_t)(recompute ? cplx * desc->n : cplx * keep_entries) + (int64_t)sizeof(int);
-    if (e == cudaSuccess && recompute) e = cudaMalloc(&p->state, cplx * (size_t)desc->n);
-    if (e == cudaSuccess && !recompute) e = cudaMalloc(&p->keep, cplx * keep_entries);
-    if (e == cudaSuccess) e = cudaMalloc(&p->status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(int));
-    if (e == cudaSuccess && use_table) {
-        p->workspace_bytes += (int64_t)(real_size(desc->arith) * desc->n);
-        e = cudaMalloc(&p->tab, real_size(desc->arith) * (size_t)desc->n);
-    }
-    CNParams& c = p->cnp;
-    std::memset(&c, 0, sizeof(c));
-    c.n = desc->n;
-    c.dx = desc->dx;
-    c.x_min = desc->x_min;
-    c.c1 = 2.0 * desc->dx * desc->dx;
-    c.gt = 4.0 * desc->dx * desc->dx / desc->dt;
-    c.pot = desc->pot;
-    c.V0 = desc->V0;
-    c.soft_s = desc->soft_s;
-    c.n_cos = desc->pot == CN_POT_COSSERIES ? desc->n_cos : 0;
-    c.two_pi_over_L = desc->pot == CN_POT_COSSERIES ? 2.0 * 3.14159265358979323846 / desc->L : 0.0;
-    for (int k = 0; k < c.n_cos; ++k) c.cos_a[k] = p->cos_a[(size_t)k];
-    auto split = [](double v) { df d = df_from_double(v); DFc r; r.hi = d.hi; r.lo = d.lo; return r; };
-    c.dx_f = split(c.dx);
-    c.c1_f = split(c.c1);
-    c.gt_f = split(c.gt);
-    c.soft_f = split(c.soft_s);
-    {
-        double jo = std::nearbyint(-desc->x_min / desc->dx);
-        if (jo < 0) jo = 0;
-        if (jo > (double)(desc->n - 1)) jo = (double)(desc->n - 1);
-        c.j_o = (int64_t)jo;
-        c.x_o = desc->x_min + (double)c.j_o * desc->dx;
-        c.xo_f = split(c.x_o);
-    }
-    if (e == cudaSuccess && use_table) {
-        const unsigned grid = (unsigned)ceil_div(desc->n, 256);
-        if (df_mode) k_beta0_table<df><<<grid, 256>>>(c, static_cast<df*>(p->tab));
-        else k_beta0_table<double><<<grid, 256>>>(c, static_cast<double*>(p->tab));
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    }
-    if (e == cudaSuccess)
-        e = df_mode ? set_smem_limits<df>(p->desc.block, p->desc.level_block)
-                    : set_smem_limits<double>(p->desc.block, p->desc.level_block);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        free_plan_memory(p);
+    v = create_engine(p, desc, std::vector<int64_t>{desc->n}, std::vector<double>{desc->x_min}, desc->cos_a);
+    if (v != CN_OK) {
+        destroy_engine(p);
         delete p;
-        return e == cudaErrorMemoryAllocation ? CN_ERR_OOM : CN_ERR_CUDA;
+        return v;
     }
     *out = p;
     return CN_OK;
@@ -409,22 +612,14 @@ cn_status cn_plan_create(const cn_desc* desc, cn_plan* out) {
 
 cn_status cn_plan_destroy(cn_plan p) {
     if (!p) return CN_OK;
-    cudaDeviceSynchronize();
-    free_plan_memory(p);
+    destroy_engine(p);
     delete p;
     return CN_OK;
 }
 
 cn_status cn_step(cn_plan p, const void* psi_in, void* psi_out, const double* E_mid, int64_t nsteps, void* stream) {
-    if (!p || !psi_in || !psi_out || nsteps < 0) return CN_ERR_INVALID_ARG;
-    if (!aligned16(psi_in) || !aligned16(psi_out)) return CN_ERR_INVALID_ARG;
-    if (E_mid && (reinterpret_cast<uintptr_t>(E_mid) & 7u)) return CN_ERR_INVALID_ARG;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const double2* in = static_cast<const double2*>(psi_in);
-    double2* out = static_cast<double2*>(psi_out);
-    cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? cn_steps<df>(p, in, out, E_mid, nsteps, st)
-                                                     : cn_steps<double>(p, in, out, E_mid, nsteps, st);
-    return cuda_status(e);
+    if (!p) return CN_ERR_INVALID_ARG;
+    return run_steps(p, psi_in, psi_out, E_mid, nsteps, stream);
 }
 
 cn_status cn_step_host(cn_plan p, const void* psi_in_host, void* psi_out_host, const double* E_mid_host,
@@ -442,10 +637,7 @@ cn_status cn_step_host(cn_plan p, const void* psi_in_host, void* psi_out_host, c
         e = cudaMalloc(&p->h_E, sizeof(double) * (size_t)nsteps);
         if (e == cudaSuccess) p->h_E_cap = nsteps;
     }
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return e == cudaErrorMemoryAllocation ? CN_ERR_OOM : CN_ERR_CUDA;
-    }
+    if (e != cudaSuccess) return alloc_status(e);
     e = cudaMemcpyAsync(p->h_in, psi_in_host, bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && E_mid_host && nsteps > 0)
         e = cudaMemcpyAsync(p->h_E, E_mid_host, sizeof(double) * (size_t)nsteps, cudaMemcpyHostToDevice, st);
@@ -479,8 +671,7 @@ cn_status cn_adjoint_step(cn_plan p, const void* psi_n, const void* psi_np1, con
                           const double* E_mid, double* dLdE, void* stream) {
     if (!p || !psi_n || !psi_np1 || !lam_np1 || !lam_n || !dLdE) return CN_ERR_INVALID_ARG;
     if (!aligned16(psi_n) || !aligned16(psi_np1) || !aligned16(lam_np1) || !aligned16(lam_n)) return CN_ERR_INVALID_ARG;
-    if ((reinterpret_cast<uintptr_t>(dLdE) & 7u) || (E_mid && (reinterpret_cast<uintptr_t>(E_mid) & 7u)))
-        return CN_ERR_INVALID_ARG;
+    if (!aligned8(dLdE) || (E_mid && !aligned8(E_mid))) return CN_ERR_INVALID_ARG;
     const int nparts = 148 * 4;
     cudaError_t e = cudaSuccess;
     if (!p->mu) e = cudaMalloc(&p->mu, sizeof(double2) * (size_t)p->desc.n);
@@ -488,10 +679,7 @@ cn_status cn_adjoint_step(cn_plan p, const void* psi_n, const void* psi_np1, con
         e = cudaMalloc(&p->part, 16 * (size_t)nparts);
         p->part_n = nparts;
     }
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return e == cudaErrorMemoryAllocation ? CN_ERR_OOM : CN_ERR_CUDA;
-    }
+    if (e != cudaSuccess) return alloc_status(e);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CNStep s;
     s.p = p->cnp;
@@ -504,15 +692,19 @@ cn_status cn_adjoint_step(cn_plan p, const void* psi_n, const void* psi_np1, con
     const bool dfm = p->desc.arith == CN_ARITH_DF64;
     e = dfm ? cn_solve<df>(p, s, p->mu, st) : cn_solve<double>(p, s, p->mu, st);
     if (e != cudaSuccess) return CN_ERR_CUDA;
+    const SysGrid& g = p->grid[0];
+    const int64_t n = p->desc.n;
+    const double2* l1 = static_cast<const double2*>(lam_np1);
+    const double2* pn = static_cast<const double2*>(psi_n);
+    const double2* pn1 = static_cast<const double2*>(psi_np1);
+    double2* ln = static_cast<double2*>(lam_n);
     if (dfm) {
-        k_adjoint_finish<df><<<p->part_n, kAdjThreads, 0, st>>>(
-            p->cnp, p->mu, static_cast<const double2*>(lam_np1), static_cast<const double2*>(psi_n),
-            static_cast<const double2*>(psi_np1), static_cast<double2*>(lam_n), static_cast<df*>(p->part));
+        k_adjoint_finish<df><<<p->part_n, kAdjThreads, 0, st>>>(p->cnp, g, n, p->mu, l1, pn, pn1, ln,
+                                                                static_cast<df*>(p->part));
         k_adjoint_sum<df><<<1, 32, 0, st>>>(static_cast<const df*>(p->part), p->part_n, p->desc.dt, dLdE);
     } else {
-        k_adjoint_finish<double><<<p->part_n, kAdjThreads, 0, st>>>(
-            p->cnp, p->mu, static_cast<const double2*>(lam_np1), static_cast<const double2*>(psi_n),
-            static_cast<const double2*>(psi_np1), static_cast<double2*>(lam_n), static_cast<double*>(p->part));
+        k_adjoint_finish<double><<<p->part_n, kAdjThreads, 0, st>>>(p->cnp, g, n, p->mu, l1, pn, pn1, ln,
+                                                                    static_cast<double*>(p->part));
         k_adjoint_sum<double><<<1, 32, 0, st>>>(static_cast<const double*>(p->part), p->part_n, p->desc.dt, dLdE);
     }
     return cuda_status(cudaGetLastError());
@@ -543,11 +735,10 @@ cn_status cn_plan_query(cn_plan p, cn_plan_info* out) {
     if (!p || !out) return CN_ERR_INVALID_ARG;
     std::memset(out, 0, sizeof(*out));
     out->n = p->desc.n;
-    out->levels = (int32_t)p->lv.size() - 1;
-    if (out->levels + 1 > CN_MAX_LEVELS) return CN_ERR_UNSUPPORTED;
-    for (size_t l = 0; l < p->lv.size(); ++l) {
-        out->level_rows[l] = p->lv[l].n;
-        out->level_block[l] = (l + 1 < p->lv.size()) ? p->lv[l].m : 0;
+    out->levels = p->base_level[0];
+    for (int l = 0; l <= out->levels; ++l) {
+        out->level_rows[l] = p->lv[(size_t)l].sys[0].n;
+        out->level_block[l] = (l < out->levels) ? p->lv[(size_t)l].m : 0;
     }
     out->launches_per_step = 2 * out->levels + 1;
     out->workspace_bytes = p->workspace_bytes;
@@ -578,11 +769,69 @@ cn_status cn_plan_profile_read(cn_plan p, double* ms, int64_t* launches, int32_t
 
 cn_status cn_plan_status(cn_plan p) {
     if (!p) return CN_ERR_INVALID_ARG;
-    if (cudaDeviceSynchronize() != cudaSuccess) return CN_ERR_CUDA;
-    int h = 0;
-    if (cudaMemcpy(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CN_ERR_CUDA;
-    if (h != 0 && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) return CN_ERR_CUDA;
-    return static_cast<cn_status>(h);
+    return read_status(p);
+}
+
+// ------------------------------------------------------------------ batches
+cn_status cn_batch_create(const cn_desc* common, int64_t nsys, const int64_t* sizes, const double* x_min,
+                          const double* cos_a, cn_batch* out) {
+    if (!out) return CN_ERR_INVALID_ARG;
+    *out = nullptr;
+    cn_status v = validate_desc(common, false);
+    if (v != CN_OK) return v;
+    if (nsys < 1 || nsys > kMaxBatch || !sizes) return CN_ERR_INVALID_ARG;
+    if (common->pot == CN_POT_COSSERIES && common->n_cos > 0 && !cos_a) return CN_ERR_INVALID_ARG;
+    std::vector<int64_t> sz((size_t)nsys);
+    std::vector<double> xm((size_t)nsys);
+    cn_desc d = *common;
+    d.n = 0;
+    for (int64_t s = 0; s < nsys; ++s) {
+        if (sizes[s] < 3 || sizes[s] > (INT64_C(1) << 40)) return CN_ERR_INVALID_ARG;
+        sz[(size_t)s] = sizes[s];
+        xm[(size_t)s] = x_min ? x_min[s] : -(double)(sizes[s] / 2) * common->dx;
+        if (!std::isfinite(xm[(size_t)s])) return CN_ERR_INVALID_ARG;
+        d.n += sizes[s];
+    }
+    if (common->pot == CN_POT_COSSERIES && common->n_cos > 0) {
+        for (int64_t i = 0; i < nsys * common->n_cos; ++i)
+            if (!std::isfinite(cos_a[i])) return CN_ERR_INVALID_ARG;
+    }
+    cn_batch p = new (std::nothrow) cn_batch_s();
+    if (!p) return CN_ERR_OOM;
+    p->batched = true;
+    v = create_engine(p, &d, sz, xm, cos_a);
+    if (v != CN_OK) {
+        destroy_engine(p);
+        delete p;
+        return v;
+    }
+    *out = p;
+    return CN_OK;
+}
+
+cn_status cn_batch_destroy(cn_batch p) {
+    if (!p) return CN_OK;
+    destroy_engine(p);
+    delete p;
+    return CN_OK;
+}
+
+cn_status cn_batch_offsets(cn_batch p, int64_t* offsets) {
+    if (!p || !offsets) return CN_ERR_INVALID_ARG;
+    for (int s = 0; s < p->nsys; ++s) offsets[s] = p->lv[0].sys[(size_t)s].row_off;
+    offsets[p->nsys] = p->lv[0].rows_total;
+    return CN_OK;
+}
+
+cn_status cn_batch_step(cn_batch p, const void* psi_in, void* psi_out, const double* E_mid, int64_t nsteps,
+                        void* stream) {
+    if (!p) return CN_ERR_INVALID_ARG;
+    return run_steps(p, psi_in, psi_out, E_mid, nsteps, stream);
+}
+
+cn_status cn_batch_status(cn_batch p) {
+    if (!p) return CN_ERR_INVALID_ARG;
+    return read_status(p);
 }
 
 }  // extern "C"

@@ -61,6 +61,46 @@ __device__ __forceinline__ void flag_error(int* status, int code) {
     if (status) atomicCAS(status, 0, code);
 }
 
+// ------------------------------------------------------------------ systems and levels
+// Several independent systems can be solved in one launch per stage (batched
+// uneven sizes).  Per level, every system s is described by a LvlSys entry: its
+// rows n (0 if it has no such level), its blocks P (0 if it does not reduce at
+// this level), the offset of its row 0 in the level's concatenated arrays, the
+// global index of its first block (block offsets are a prefix sum of P) and the
+// global index of its first block at the level that produced these rows (for
+// the CTA slot of Sec. 4.1.3's second joint-line contribution).  A thread maps
+// its global block index g to (s, t) by binary search over the block offsets.
+struct LvlSys {
+    int64_t n, P, row_off, blk_off, prod_blk_off;
+};
+
+// One system, its entry held by value in the kernel parameters.
+struct OneSys {
+    LvlSys e;
+    __device__ __forceinline__ int64_t total() const { return e.P; }
+    __device__ __forceinline__ int find(int64_t) const { return 0; }
+    __device__ __forceinline__ const LvlSys& at(int) const { return e; }
+};
+// Many systems, entries in device memory.
+struct ManySys {
+    const LvlSys* tab;
+    int nsys;
+    int64_t tot;
+    __device__ __forceinline__ int64_t total() const { return tot; }
+    // largest s with blk_off[s] <= g (systems without blocks at this level have
+    // empty ranges and are skipped by this rule)
+    __device__ __forceinline__ int find(int64_t g) const {
+        int lo = 0, hi = nsys - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (tab[mid].blk_off <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    }
+    __device__ __forceinline__ const LvlSys& at(int s) const { return tab[s]; }
+};
+
 // ------------------------------------------------------------------ reduced rows
 // Row {b, a, c, d} of a reduced system (levels >= 1), stored in the compute type.
 template <class R> struct LevelRow {
@@ -77,11 +117,12 @@ template <class R> struct Row {
 };
 
 // ------------------------------------------------------------------ generic rows
-// General tridiagonal system in four complex128 arrays (cn_solve_tridiag);
-// b_0 and c_{n-1} are taken as 0.
+// General tridiagonal system in four complex128 arrays (cn_solve_tridiag, one
+// system); b_0 and c_{n-1} are taken as 0.
 struct ArraySource {
     const double2 *b, *a, *c, *d;
     int64_t n;
+    __device__ __forceinline__ ArraySource bind(const LvlSys&) const { return *this; }
     template <class R>
     __device__ __forceinline__ Row<R> row(int64_t i) const {
         Row<R> r;
@@ -93,13 +134,21 @@ struct ArraySource {
     }
 };
 
-// Reduced system of a level >= 1, plus the contribution of the previous CTA's
-// last block to the first row of every CTA range (slot).
+// Reduced systems of a level >= 1 (all systems' rows concatenated), plus the
+// contribution of the previous CTA's last block to the rows whose producing
+// block was the first thread of a CTA (slot, indexed by that CTA).
 template <class R> struct LevelSource {
-    const LevelRow<R>* rows;
+    const LevelRow<R>* rows;  // row 0 of the bound system
     const LevelSlot<R>* slot;
-    int64_t n;            // rows of this level
-    int64_t slot_stride;  // rows per CTA range of the producing kernel
+    int64_t n;                // rows of the bound system
+    int64_t prod;             // global block index that produced row 0 of the bound system
+    __host__ __device__ __forceinline__ LevelSource bind(const LvlSys& e) const {
+        LevelSource r = *this;
+        r.rows = rows + e.row_off;
+        r.n = e.n;
+        r.prod = e.prod_blk_off;
+        return r;
+    }
     template <class RR>
     __device__ __forceinline__ Row<R> row(int64_t i) const {
         const LevelRow<R>* p = rows + i;
@@ -108,8 +157,9 @@ template <class R> struct LevelSource {
         r.a = sload(&p->a);
         r.c = sload(&p->c);
         r.d = sload(&p->d);
-        if (i > 0 && i < n - 1 && (i % slot_stride) == 0) {
-            const LevelSlot<R>* s = slot + i / slot_stride;
+        const int64_t g = prod + i;
+        if (i > 0 && i < n - 1 && (g % kThreads) == 0) {
+            const LevelSlot<R>* s = slot + g / kThreads;
             r.b = sload(&s->b);
             r.a = cadd(r.a, sload(&s->a));
             r.d = cadd(r.d, sload(&s->d));
@@ -119,9 +169,10 @@ template <class R> struct LevelSource {
 };
 
 // ------------------------------------------------------------------ output of a block
-// Writes row t of the next level from this block's JU part and (via shared
-// memory or the CTA slot) the previous block's JD part; the last block also
-// writes row P.
+// Writes row t of the next level from this block's JU part and the previous
+// block's JD part: from shared memory when that block ran in the same CTA, else
+// (first thread of a CTA, t > 0) the next level adds it from the CTA slot.  The
+// last block of a system also writes row P.
 template <class R>
 __device__ __forceinline__ void write_reduced_row(bool active, int64_t t, int64_t P, JDPart<R> jd, cx<R> A0, cx<R> D0,
                                                   cx<R> JUa, cx<R> JUc, cx<R> JUd, cx<R> Ag, cx<R> Dg,
@@ -132,11 +183,13 @@ __device__ __forceinline__ void write_reduced_row(bool active, int64_t t, int64_
     __syncthreads();
     if (!active) return;
     LevelRow<R> row;
-    if (tid > 0) {
+    if (tid > 0 && t > 0) {
         JDPart<R> pj = xch[tid - 1];
         sstore(&row.b, pj.b);
-        sstore(&row.a, cadd(A0, cadd(pj.a, JUa)));
-        sstore(&row.d, cadd(D0, cadd(pj.d, JUd)));
+        // (A0 + JU) + JD: the order the slot path below takes too, so a row's
+        // value does not depend on where CTA boundaries fall
+        sstore(&row.a, cadd(cadd(A0, JUa), pj.a));
+        sstore(&row.d, cadd(cadd(D0, JUd), pj.d));
     } else {
         // t == 0: no block above; otherwise the previous CTA's slot completes the row
         sstore(&row.b, czero<R>());
@@ -163,19 +216,28 @@ __device__ __forceinline__ void write_reduced_row(bool active, int64_t t, int64_
 
 // ------------------------------------------------------------------ generic reduction
 // One thread per block: RD + JD downwards with RU + JU accumulated on the way.
-template <class R, class Src>
+template <class R, class Src, class Map>
 __global__ void __launch_bounds__(kThreads)
-k_reduce(Src src, int64_t n, int64_t P, int m, LevelRow<R>* out, LevelSlot<R>* out_slot, int* status) {
-    const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    const bool active = t < P;
+k_reduce(Src src0, Map sys, Map next, int m, LevelRow<R>* out, LevelSlot<R>* out_slot, int* status) {
+    const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const bool active = g < sys.total();
     bool ok = true;
     cx<R> JUa = czero<R>(), JUc = czero<R>(), JUd = czero<R>(), A0 = czero<R>(), D0 = czero<R>();
     cx<R> Ag = czero<R>(), Dg = czero<R>();
     JDPart<R> jd;
     jd.b = czero<R>(); jd.a = czero<R>(); jd.d = czero<R>();
+    int64_t t = 0, P = 0;
+    LevelRow<R>* outs = out;
     if (active) {
+        const int si = sys.find(g);
+        const LvlSys& e = sys.at(si);
+        const Src src = src0.bind(e);
+        const int64_t n = e.n;
+        P = e.P;
+        t = g - e.blk_off;
+        outs = out + next.at(si).row_off;
         const int64_t J0 = joint_line(t, P, m, n);
-        const int g = (int)(joint_line(t + 1, P, m, n) - J0);
+        const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
         const Row<R> r0 = src.template row<R>(J0);
         A0 = r0.a;
         D0 = r0.d;
@@ -188,7 +250,7 @@ k_reduce(Src src, int64_t n, int64_t P, int m, LevelRow<R>* out, LevelSlot<R>* o
         cx<R> Q = cfrom<R>(1.0, 0.0);   // prod_{i<k} rho_i
         cx<R> nb = bRD, nd = dRD;       // RU values accumulated on row 1
         Row<R> nxt = src.template row<R>(J0 + 2);  // one row ahead (row g when g == 2)
-        for (int k = 2; k < g; ++k) {
+        for (int k = 2; k < gap; ++k) {
             const Row<R> rk = nxt;
             nxt = src.template row<R>(J0 + k + 1);
             // RD: r = -b_k / a_{k-1};  b_k = r b_{k-1};  a_k += r c_{k-1};  d_k += r d_{k-1}
@@ -218,7 +280,7 @@ k_reduce(Src src, int64_t n, int64_t P, int m, LevelRow<R>* out, LevelSlot<R>* o
         JUa = cmul(r0u, nb);
         JUd = cmul(r0u, nd);
     }
-    write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, out, out_slot);
+    write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, outs, out_slot);
     if (!ok) flag_error(status, kStatusNonfinite);
 }
 
@@ -232,29 +294,35 @@ template <> __device__ __forceinline__ void put<double2, double>(double2* p, cx<
 template <> __device__ __forceinline__ void put<double2, df>(double2* p, cx<df> z) { store128(p, z); }
 template <> __device__ __forceinline__ void put<float4, df>(float4* p, cx<df> z) { sstore(p, z); }
 
-template <class R, class Src, class XT>
+template <class R, class Src, class Map, class XT>
 __global__ void __launch_bounds__(kThreads)
-k_substitute(Src src, int64_t n, int64_t P, int m, const typename Store<R>::T* x_next, XT* x, int* status) {
+k_substitute(Src src0, Map sys, Map next, int m, const typename Store<R>::T* x_next0, XT* x0, int* status) {
     typedef typename Store<R>::T ST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ST* zs = reinterpret_cast<ST*>(smem_raw);   // [m][kThreads]
     ST* cs = zs + (size_t)m * kThreads;         // [m][kThreads]
     const int tid = threadIdx.x;
-    const int64_t t = (int64_t)blockIdx.x * kThreads + tid;
-    if (t >= P) return;
+    const int64_t g = (int64_t)blockIdx.x * kThreads + tid;
+    if (g >= sys.total()) return;
     bool ok = true;
+    const int si = sys.find(g);
+    const LvlSys& e = sys.at(si);
+    const Src src = src0.bind(e);
+    const int64_t n = e.n, P = e.P, t = g - e.blk_off;
+    const ST* x_next = x_next0 + next.at(si).row_off;
+    XT* x = x0 + e.row_off;
     const int64_t J0 = joint_line(t, P, m, n);
-    const int g = (int)(joint_line(t + 1, P, m, n) - J0);
+    const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
     const cx<R> xL = sload(x_next + t);
     const cx<R> xR = sload(x_next + t + 1);
     cx<R> zp = czero<R>(), cpp = czero<R>();
     Row<R> nxt = src.template row<R>(J0 + 1);
-    for (int k = 1; k < g; ++k) {
+    for (int k = 1; k < gap; ++k) {
         const Row<R> rk = nxt;
-        if (k + 1 < g) nxt = src.template row<R>(J0 + k + 1);
+        if (k + 1 < gap) nxt = src.template row<R>(J0 + k + 1);
         cx<R> rhs = rk.d;
         if (k == 1) rhs = csub(rhs, cmul(rk.b, xL));
-        if (k == g - 1) rhs = csub(rhs, cmul(rk.c, xR));
+        if (k == gap - 1) rhs = csub(rhs, cmul(rk.c, xR));
         // m_k = a_k - b_k c'_{k-1};  z_k = (rhs_k - b_k z_{k-1}) / m_k;  c'_k = c_k / m_k
         const cx<R> piv = (k == 1) ? rk.a : csub(rk.a, cmul(rk.b, cpp));
         const cx<R> w = crcp(piv, ok);
@@ -264,22 +332,28 @@ k_substitute(Src src, int64_t n, int64_t P, int m, const typename Store<R>::T* x
         sstore(cs + k * kThreads + tid, cpp);
     }
     cx<R> y = zp;
-    put<XT, R>(x + J0 + g - 1, y);
-    for (int k = g - 2; k >= 1; --k) {
+    put<XT, R>(x + J0 + gap - 1, y);
+    for (int k = gap - 2; k >= 1; --k) {
         y = csub(sload(zs + k * kThreads + tid), cmul(sload(cs + k * kThreads + tid), y));
         put<XT, R>(x + J0 + k, y);
     }
     put<XT, R>(x + J0, xL);
-    if (t == P - 1) put<XT, R>(x + J0 + g, xR);
+    if (t == P - 1) put<XT, R>(x + J0 + gap, xR);
     if (!ok) flag_error(status, kStatusNonfinite);
 }
 
 // ------------------------------------------------------------------ RS stage
-// Serial Thomas elimination of the last reduced system (Table 1, RS), one thread.
+// Serial Thomas elimination of each system's last reduced system (Table 1, RS),
+// one thread per system.
+template <class R> struct BaseSys {
+    LevelSource<R> src;            // bound to the system's last level
+    typename Store<R>::T* x;       // its solution
+};
+
 template <class R>
-__global__ void k_base(LevelSource<R> src, int64_t n, typename Store<R>::T* x, int* status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ __forceinline__ void base_solve(const LevelSource<R>& src, typename Store<R>::T* x, int* status) {
     bool ok = true;
+    const int64_t n = src.n;
     cx<R> a_prev = czero<R>(), c_prev = czero<R>(), d_prev = czero<R>();
     cx<R> A[kBaseMax], C[kBaseMax], D[kBaseMax];
     for (int64_t w = 0; w < n; ++w) {
@@ -303,30 +377,55 @@ __global__ void k_base(LevelSource<R> src, int64_t n, typename Store<R>::T* x, i
     if (!ok) flag_error(status, kStatusNonfinite);
 }
 
+template <class R>
+__global__ void k_base(LevelSource<R> src, typename Store<R>::T* x, int* status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    base_solve<R>(src, x, status);
+}
+
+template <class R>
+__global__ void k_base_many(const BaseSys<R>* sys, int nsys, int* status) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    base_solve<R>(sys[s].src, sys[s].x, status);
+}
+
 // ------------------------------------------------------------------ CN level 0
 struct DFc {
     float hi, lo;  // a binary64 constant split on the host into double-float words
 };
+__device__ __forceinline__ df dfc(DFc c) { return df_make(c.hi, c.lo); }
+
+// Parameters shared by every system of a launch.
 struct CNParams {
-    int64_t n;
-    double dx, x_min;
+    double dx;
     double c1;             // 2 dx^2:  bt_j = 2 + c1 V_j
     double gt;             // 4 dx^2 / dt
     int pot;               // cn_pot_kind
     int n_cos;
-    const double* V0;      // CN_POT_ARRAY (on-the-fly FP64 path)
+    const double* V0;      // CN_POT_ARRAY (on-the-fly FP64 path), indexed from the system's row 0
     double soft_s;
     double two_pi_over_L;
     double cos_a[kMaxCos];
     DFc dx_f, c1_f, gt_f, soft_f;  // the same constants for the double-float kernels
-    // Grid coordinates are formed as x_j = x_o + (j - j_o) dx around the grid point
-    // j_o nearest x = 0 (x_o = x_min + j_o dx, on the host): x_min + j dx directly
-    // would cancel two ~|x_min| terms near the origin, where the state lives.
+};
+
+// Grid coordinates of one system, formed as x_j = x_o + (j - j_o) dx around the
+// grid point j_o nearest x = 0 (x_o = x_min + j_o dx, on the host): x_min + j dx
+// directly would cancel two ~|x_min| terms near the origin, where the state lives.
+struct SysGrid {
     int64_t j_o;
     double x_o;
     DFc xo_f;
 };
-__device__ __forceinline__ df dfc(DFc c) { return df_make(c.hi, c.lo); }
+struct OneGrid {
+    SysGrid g;
+    __device__ __forceinline__ const SysGrid& at(int) const { return g; }
+};
+struct ManyGrid {
+    const SysGrid* tab;
+    __device__ __forceinline__ const SysGrid& at(int s) const { return tab[s]; }
+};
 
 // Static potential Vs(x_j) in binary64 (the FP64 path and the table builder).
 __device__ __forceinline__ double static_potential_d(const CNParams& p, int64_t j, double x) {
@@ -342,13 +441,13 @@ __device__ __forceinline__ double static_potential_d(const CNParams& p, int64_t 
     }
 }
 
-// bt0_j = 2 + c1 Vs(x_j): the static part of the scaled diagonal, tabulated once
-// per plan when the potential is not regenerated on the fly.
+// bt0_j = 2 + c1 Vs(x_j): the static part of the scaled diagonal of one system,
+// tabulated once when the potential is not regenerated on the fly.
 template <class R>
-__global__ void k_beta0_table(CNParams p, R* tab) {
+__global__ void k_beta0_table(CNParams p, SysGrid sg, int64_t n, R* tab) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= p.n) return;
-    double x = fma((double)(j - p.j_o), p.dx, p.x_o);
+    if (j >= n) return;
+    double x = fma((double)(j - sg.j_o), p.dx, sg.x_o);
     tab[j] = RealOps<R>::from_d(fma(p.c1, static_potential_d(p, j, x), 2.0));
 }
 
@@ -359,16 +458,22 @@ template <class R> struct CoefGen;
 template <> struct CoefGen<double> {
     const CNParams* p;
     const double* tab;
+    const double* V0;
+    SysGrid sg;
     double c1Et, c1Ee, x;
     int64_t j;
-    __device__ __forceinline__ double xj(int64_t jj) const { return fma((double)(jj - p->j_o), p->dx, p->x_o); }
-    __device__ __forceinline__ void init(const CNParams& pp, const double* tb, double Et, double Ee, int64_t j0) {
-        p = &pp; tab = tb; j = j0;
+    __device__ __forceinline__ double xj(int64_t jj) const { return fma((double)(jj - sg.j_o), p->dx, sg.x_o); }
+    __device__ __forceinline__ void init(const CNParams& pp, const SysGrid& g, const double* tb, const double* v0,
+                                         double Et, double Ee, int64_t j0) {
+        p = &pp; sg = g; tab = tb; V0 = v0; j = j0;
         c1Et = pp.c1 * Et; c1Ee = pp.c1 * Ee;
         x = xj(j0);
     }
     __device__ __forceinline__ void next(double& bt_t, double& bt_e) {
-        double b0 = tab ? tab[j] : fma(p->c1, static_potential_d(*p, j, x), 2.0);
+        double b0;
+        if (tab) b0 = tab[j];
+        else if (p->pot == 1) b0 = fma(p->c1, V0[j], 2.0);
+        else b0 = fma(p->c1, static_potential_d(*p, j, x), 2.0);
         bt_t = fma(c1Et, x, b0);
         bt_e = (c1Ee == c1Et) ? bt_t : fma(c1Ee, x, b0);
         ++j;
@@ -385,7 +490,8 @@ template <> struct CoefGen<df> {
     int64_t j;
     // All binary64 constants arrive pre-split (DFc); the fields are converted
     // with integer operations, so no FP64-pipe instruction runs here.
-    __device__ __forceinline__ void init(const CNParams& pp, const df* tb, double Et, double Ee, int64_t j0) {
+    __device__ __forceinline__ void init(const CNParams& pp, const SysGrid& g, const df* tb, const double*,
+                                         double Et, double Ee, int64_t j0) {
         tab = tb; j = j0; pot = pp.pot;
         same = d_bits(Et) == d_bits(Ee);
         dx = dfc(pp.dx_f);
@@ -394,9 +500,9 @@ template <> struct CoefGen<df> {
         c1Et = df_mul(c1, df_from_double(Et));
         c1Ee = same ? c1Et : df_mul(c1, df_from_double(Ee));
         // x_j0 = x_o + (j0 - j_o) dx with j0 - j_o = hi 2^16 + lo split into exact binary32 parts
-        const int64_t dj = j0 - pp.j_o;
+        const int64_t dj = j0 - g.j_o;
         float jh = i2f((int32_t)(dj >> 16)), jl = i2f((int32_t)(dj & 0xFFFF));
-        x = df_add(dfc(pp.xo_f), df_add(df_mul_f(df_mul_f(dx, jh), 65536.0f), df_mul_f(dx, jl)));
+        x = df_add(dfc(g.xo_f), df_add(df_mul_f(df_mul_f(dx, jh), 65536.0f), df_mul_f(dx, jl)));
     }
     __device__ __forceinline__ void next(df& bt_t, df& bt_e) {
         df b0;
@@ -436,8 +542,9 @@ __device__ __forceinline__ cx<df> explicit_row(cx<df> pm, cx<df> p0, cx<df> pp, 
     return mk(df_dot2_add(nsr, eb, p0.re, sg, p0.im), df_dot2_add(nsi, eb, p0.im, df_neg(sg), p0.re));
 }
 
-// Level-0 CN source: sign s of the implicit matrix, sign e of the explicit one,
-// fields read from device memory (NULL: 0).
+// A CN-type step at level 0: sign s of the implicit matrix, sign e of the
+// explicit one, fields read from device memory (NULL: 0).  psi and tab are the
+// arrays of all systems; each system starts at its level-0 row offset.
 struct CNStep {
     CNParams p;
     const double2* psi;   // state the explicit half-step is applied to
@@ -458,7 +565,7 @@ __device__ __forceinline__ df signed_gt(const CNStep& st, df) {
     return st.s > 0 ? g : df_neg(g);
 }
 
-// Streams the scaled rows of a CN block: row i's a~_i and d^_i, with the psi
+// Streams the scaled rows of one CN block: row i's a~_i and d^_i, with the psi
 // stencil window and the coefficient generator carried from row to row.
 template <class R> struct CNRowStream {
     CoefGen<R> cg;
@@ -470,15 +577,16 @@ template <class R> struct CNRowStream {
     __device__ __forceinline__ cx<R> ld(int64_t j) const {
         return (j >= 0 && j < n) ? load128<R>(psi + j) : czero<R>();
     }
-    __device__ __forceinline__ void init(const CNStep& st, int64_t j0) {
+    __device__ __forceinline__ void init(const CNStep& st, const LvlSys& e, const SysGrid& g, int64_t j0) {
         const double Et = st.E_t ? *st.E_t : 0.0, Ee = st.E_e ? *st.E_e : 0.0;
         sg = signed_gt(st, R());
         msg = rneg(sg);  // imaginary part of a~: -s g~
         es = st.e * st.s;
-        psi = st.psi;
-        n = st.p.n;
+        psi = st.psi + e.row_off;
+        n = e.n;
         i = j0;
-        cg.init(st.p, (const R*)st.tab, Et, Ee, j0);
+        const R* tab = st.tab ? static_cast<const R*>(st.tab) + e.row_off : nullptr;
+        cg.init(st.p, g, tab, st.p.V0 ? st.p.V0 + e.row_off : nullptr, Et, Ee, j0);
         pm = ld(j0 - 1);
         p0 = ld(j0);
         pp = ld(j0 + 1);
@@ -508,27 +616,36 @@ template <class R> struct CNRowStream {
 // half-step + RD/JD with RU/JU accumulated, on the scaled rows (b = c = -1):
 //   RD:  w_k = 1/(a~_k - w_{k-1}),  d_k += w_{k-1} d_{k-1},  b_k = w_{k-1} b_{k-1} (b_1 = -1)
 //   RU:  rho_{k-1} = w_k,  Q_k = Q_{k-1} w_k,  b_1 += Q_k b_k,  d_1 += Q_k d_k,  c_1 = -Q_{g-1}
-// With keep != NULL it also saves, for every interior row k of block t, d^ and
-// the pivot inverse w at keep[(2k) P + t] and keep[(2k+1) P + t] (block-row
-// major: a warp's 32 blocks touch 32 consecutive entries): all the
-// substitution needs (store mode).
-template <class R>
+// With keep != NULL it also saves, for every interior row k of block t of a
+// system, d^ and the pivot inverse w at keep[(2k) P + t] and keep[(2k+1) P + t]
+// from the system's base 2 m blk_off (block-row major: a warp's 32 blocks touch
+// 32 consecutive entries): all the substitution needs (store mode).
+template <class R, class Map, class Grid>
 __global__ void __launch_bounds__(kThreads)
-k_cn_reduce(CNStep st, int64_t P, int m, LevelRow<R>* out, LevelSlot<R>* out_slot,
-            typename Store<R>::T* keep, int* status) {
-    const int64_t n = st.p.n;
-    const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    const bool active = t < P;
+k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, LevelRow<R>* out, LevelSlot<R>* out_slot,
+            typename Store<R>::T* keep0, int* status) {
+    typedef typename Store<R>::T ST;
+    const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const bool active = g < sys.total();
     bool ok = true;
     cx<R> JUa = czero<R>(), JUc = czero<R>(), JUd = czero<R>(), A0 = czero<R>(), D0 = czero<R>();
     cx<R> Ag = czero<R>(), Dg = czero<R>();
     JDPart<R> jd;
     jd.b = czero<R>(); jd.a = czero<R>(); jd.d = czero<R>();
+    int64_t t = 0, P = 0;
+    LevelRow<R>* outs = out;
     if (active) {
+        const int si = sys.find(g);
+        const LvlSys& e = sys.at(si);
+        const int64_t n = e.n;
+        P = e.P;
+        t = g - e.blk_off;
+        outs = out + next.at(si).row_off;
+        ST* keep = keep0 ? keep0 + 2 * (int64_t)m * e.blk_off : nullptr;
         const int64_t J0 = joint_line(t, P, m, n);
-        const int g = (int)(joint_line(t + 1, P, m, n) - J0);
+        const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
         CNRowStream<R> rs;
-        rs.init(st, J0);
+        rs.init(st, e, grid.at(si), J0);
         rs.next(A0, D0);
         cx<R> a, d;
         rs.next(a, d);  // row 1
@@ -541,7 +658,7 @@ k_cn_reduce(CNStep st, int64_t P, int m, LevelRow<R>* out, LevelSlot<R>* out_slo
         cx<R> bRD = cfrom<R>(-1.0, 0.0), dRD = d;
         cx<R> Q = cfrom<R>(1.0, 0.0);
         cx<R> nb = bRD, nd = dRD;
-        for (int k = 2; k < g; ++k) {
+        for (int k = 2; k < gap; ++k) {
             rs.next(a, d);
             bRD = cmul(w, bRD);
             dRD = cfma(d, w, dRD);
@@ -565,7 +682,7 @@ k_cn_reduce(CNStep st, int64_t P, int m, LevelRow<R>* out, LevelSlot<R>* out_slo
         JUa = cmul(w1, nb);
         JUd = cmul(w1, nd);
     }
-    write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, out, out_slot);
+    write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, outs, out_slot);
     if (!ok) flag_error(status, kStatusNonfinite);
 }
 
@@ -575,44 +692,49 @@ k_cn_reduce(CNStep st, int64_t P, int m, LevelRow<R>* out, LevelSlot<R>* out_slo
 //   (z_0 = xL, xR added on the last interior row), y_k = z_k + w_k y_{k+1}.
 // Recompute mode: coefficients, explicit half-step and pivots are regenerated
 // from psi (x must differ from the psi read).  z and w wait in shared memory.
-template <class R>
+template <class R, class Map, class Grid>
 __global__ void __launch_bounds__(kThreads)
-k_cn_substitute(CNStep st, int64_t P, int m, const typename Store<R>::T* x_next, double2* x, int* status) {
+k_cn_substitute(CNStep st, Map sys, Map next, Grid grid, int m, const typename Store<R>::T* x_next0, double2* x0,
+                int* status) {
     typedef typename Store<R>::T ST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ST* zs = reinterpret_cast<ST*>(smem_raw);   // [m][kThreads]
     ST* ws = zs + (size_t)m * kThreads;         // [m][kThreads]
     const int tid = threadIdx.x;
-    const int64_t n = st.p.n;
-    const int64_t t = (int64_t)blockIdx.x * kThreads + tid;
-    if (t >= P) return;
+    const int64_t g = (int64_t)blockIdx.x * kThreads + tid;
+    if (g >= sys.total()) return;
     bool ok = true;
+    const int si = sys.find(g);
+    const LvlSys& e = sys.at(si);
+    const int64_t n = e.n, P = e.P, t = g - e.blk_off;
+    const ST* x_next = x_next0 + next.at(si).row_off;
+    double2* x = x0 + e.row_off;
     const int64_t J0 = joint_line(t, P, m, n);
-    const int g = (int)(joint_line(t + 1, P, m, n) - J0);
+    const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
     const cx<R> xL = sload(x_next + t);
     const cx<R> xR = sload(x_next + t + 1);
     CNRowStream<R> rs;
-    rs.init(st, J0);
+    rs.init(st, e, grid.at(si), J0);
     rs.skip();
     cx<R> zp = xL, w = czero<R>();
-    for (int k = 1; k < g; ++k) {
+    for (int k = 1; k < gap; ++k) {
         cx<R> a, d;
         rs.next(a, d);
         w = crcp(k == 1 ? a : csub(a, w), ok);
         cx<R> rhs = cadd(d, zp);
-        if (k == g - 1) rhs = cadd(rhs, xR);
+        if (k == gap - 1) rhs = cadd(rhs, xR);
         zp = cmul(rhs, w);
         sstore(zs + k * kThreads + tid, zp);
         sstore(ws + k * kThreads + tid, w);
     }
     cx<R> y = zp;
-    store128(x + J0 + g - 1, y);
-    for (int k = g - 2; k >= 1; --k) {
+    store128(x + J0 + gap - 1, y);
+    for (int k = gap - 2; k >= 1; --k) {
         y = cfma(sload(zs + k * kThreads + tid), sload(ws + k * kThreads + tid), y);
         store128(x + J0 + k, y);
     }
     store128(x + J0, xL);
-    if (t == P - 1) store128(x + J0 + g, xR);
+    if (t == P - 1) store128(x + J0 + gap, xR);
     if (!ok) flag_error(status, kStatusNonfinite);
 }
 
@@ -620,67 +742,86 @@ k_cn_substitute(CNStep st, int64_t P, int m, const typename Store<R>::T* x_next,
 // k_cn_reduce), so psi is not read and x may be the state the step started
 // from.  z, then y, wait in shared memory ([k][tid] with a row stride of
 // kThreads + 1 entries, so both the per-thread column walk and the tile-order
-// read-out below hit distinct banks); when all 128 blocks of the CTA are
-// full-length, the CTA writes its contiguous tile of x in order (coalesced).
+// read-out below hit distinct banks); when all 128 blocks of the CTA belong to
+// one system and are full-length, the CTA writes its contiguous tile of x in
+// order (coalesced).
 constexpr int kTileStride = kThreads + 1;
-template <class R>
+template <class R, class Map>
 __global__ void __launch_bounds__(kThreads)
-k_cn_substitute_kept(int64_t n, int64_t P, int m, const typename Store<R>::T* keep,
-                     const typename Store<R>::T* x_next, double2* x) {
+k_cn_substitute_kept(Map sys, Map next, int m, const typename Store<R>::T* keep0,
+                     const typename Store<R>::T* x_next0, double2* x0) {
     typedef typename Store<R>::T ST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ST* zs = reinterpret_cast<ST*>(smem_raw);   // [m][kTileStride]
     const int tid = threadIdx.x;
-    const int64_t t0 = (int64_t)blockIdx.x * kThreads;
-    const int64_t t = t0 + tid;
-    // all blocks of this CTA span exactly m rows (every CTA but the last one or two)
-    const bool regular = (t0 + kThreads <= P) && joint_line(t0 + kThreads, P, m, n) == (t0 + kThreads) * m;
-    if (t < P) {
+    const int64_t g0 = (int64_t)blockIdx.x * kThreads;
+    const int64_t g = g0 + tid;
+    const int64_t total = sys.total();
+    // CTA-uniform: are all 128 blocks full-length blocks of one system?
+    bool regular = false;
+    int s0 = 0;
+    int64_t t0 = 0;
+    if (g0 + kThreads <= total) {
+        s0 = sys.find(g0);
+        const LvlSys& e0 = sys.at(s0);
+        t0 = g0 - e0.blk_off;
+        regular = (sys.find(g0 + kThreads - 1) == s0) &&
+                  joint_line(t0 + kThreads, e0.P, m, e0.n) == (t0 + kThreads) * m;
+    }
+    if (g < total) {
+        const int si = sys.find(g);
+        const LvlSys& e = sys.at(si);
+        const int64_t n = e.n, P = e.P, t = g - e.blk_off;
+        const ST* keep = keep0 + 2 * (int64_t)m * e.blk_off;
+        const ST* x_next = x_next0 + next.at(si).row_off;
+        double2* x = x0 + e.row_off;
         const int64_t J0 = joint_line(t, P, m, n);
-        const int g = (int)(joint_line(t + 1, P, m, n) - J0);
+        const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
         const cx<R> xL = sload(x_next + t);
         const cx<R> xR = sload(x_next + t + 1);
         cx<R> zp = xL;
         cx<R> dn = sload(keep + 2 * P + t), wn = sload(keep + 3 * P + t);
-        for (int k = 1; k < g; ++k) {
+        for (int k = 1; k < gap; ++k) {
             const cx<R> d = dn, w = wn;
-            if (k + 1 < g) {  // next row's values, issued before this row's arithmetic
+            if (k + 1 < gap) {  // next row's values, issued before this row's arithmetic
                 dn = sload(keep + (2 * k + 2) * P + t);
                 wn = sload(keep + (2 * k + 3) * P + t);
             }
             cx<R> rhs = cadd(d, zp);
-            if (k == g - 1) rhs = cadd(rhs, xR);
+            if (k == gap - 1) rhs = cadd(rhs, xR);
             zp = cmul(rhs, w);
             sstore(zs + k * kTileStride + tid, zp);
         }
         cx<R> y = zp;
         if (regular) {
             sstore(zs + tid, xL);  // row 0 of the block: its top joint line
-            for (int k = g - 2; k >= 1; --k) {
+            for (int k = gap - 2; k >= 1; --k) {
                 y = cfma(sload(zs + k * kTileStride + tid), sload(keep + (2 * k + 1) * P + t), y);
                 sstore(zs + k * kTileStride + tid, y);
             }
         } else {
-            store128(x + J0 + g - 1, y);
-            for (int k = g - 2; k >= 1; --k) {
+            store128(x + J0 + gap - 1, y);
+            for (int k = gap - 2; k >= 1; --k) {
                 y = cfma(sload(zs + k * kTileStride + tid), sload(keep + (2 * k + 1) * P + t), y);
                 store128(x + J0 + k, y);
             }
             store128(x + J0, xL);
-            if (t == P - 1) store128(x + J0 + g, xR);
+            if (t == P - 1) store128(x + J0 + gap, xR);
         }
     }
     if (!regular) return;  // uniform per CTA
     __syncthreads();
-    // tile row i = (block b, row k) with i = b m + k; rows J_{t0} .. J_{t0} + 128 m - 1
+    const LvlSys& e0 = sys.at(s0);
+    double2* x = x0 + e0.row_off;
+    // tile row i = (block b, row k) with i = b m + k; rows t0 m .. (t0 + 128) m - 1
     const int64_t base = t0 * m;
     for (int i = tid; i < kThreads * m; i += kThreads) {
         const int b = i / m, k = i - b * m;
         store128(x + base + i, sload(zs + k * kTileStride + b));
     }
-    if (t0 + kThreads == P) {
-        // the CTA holding the last block also writes the last joint line
-        if (tid == kThreads - 1) store128(x + n - 1, sload(x_next + P));
+    if (t0 + kThreads == e0.P && tid == kThreads - 1) {
+        // the CTA holding the last block of the system also writes its last joint line
+        store128(x + e0.n - 1, sload(x_next0 + next.at(s0).row_off + e0.P));
     }
 }
 
@@ -703,27 +844,27 @@ __device__ __forceinline__ df adj_term(cx<df> mu, cx<df> s, df x) {
 }
 __device__ __forceinline__ double radd(double a, double b) { return a + b; }
 __device__ __forceinline__ df radd(df a, df b) { return df_add(a, b); }
-__device__ __forceinline__ double xcoord(const CNParams& p, int64_t j, double) {
-    return fma((double)(j - p.j_o), p.dx, p.x_o);
+__device__ __forceinline__ double xcoord(const CNParams& p, const SysGrid& g, int64_t j, double) {
+    return fma((double)(j - g.j_o), p.dx, g.x_o);
 }
-__device__ __forceinline__ df xcoord(const CNParams& p, int64_t j, df) {
-    const int64_t dj = j - p.j_o;
+__device__ __forceinline__ df xcoord(const CNParams& p, const SysGrid& g, int64_t j, df) {
+    const int64_t dj = j - g.j_o;
     float jh = i2f((int32_t)(dj >> 16)), jl = i2f((int32_t)(dj & 0xFFFF));
     df dx = dfc(p.dx_f);
-    return df_add(dfc(p.xo_f), df_add(df_mul_f(df_mul_f(dx, jh), 65536.0f), df_mul_f(dx, jl)));
+    return df_add(dfc(g.xo_f), df_add(df_mul_f(df_mul_f(dx, jh), 65536.0f), df_mul_f(dx, jl)));
 }
 
 template <class R>
 __global__ void __launch_bounds__(kAdjThreads)
-k_adjoint_finish(CNParams p, const double2* mu, const double2* lam_np1, const double2* psi_n, const double2* psi_np1,
-                 double2* lam_n, R* part) {
+k_adjoint_finish(CNParams p, SysGrid sg, int64_t n, const double2* mu, const double2* lam_np1, const double2* psi_n,
+                 const double2* psi_np1, double2* lam_n, R* part) {
     __shared__ R red[kAdjThreads];
     R acc = RealOps<R>::from_d(0.0);
-    for (int64_t j = (int64_t)blockIdx.x * kAdjThreads + threadIdx.x; j < p.n; j += (int64_t)gridDim.x * kAdjThreads) {
+    for (int64_t j = (int64_t)blockIdx.x * kAdjThreads + threadIdx.x; j < n; j += (int64_t)gridDim.x * kAdjThreads) {
         const cx<R> m = load128<R>(mu + j);
         const cx<R> l1 = load128<R>(lam_np1 + j);
         const cx<R> s = cadd(load128<R>(psi_n + j), load128<R>(psi_np1 + j));
-        acc = radd(acc, adj_term(m, s, xcoord(p, j, R())));
+        acc = radd(acc, adj_term(m, s, xcoord(p, sg, j, R())));
         store128(lam_n + j, csub(cadd(m, m), l1));
     }
     red[threadIdx.x] = acc;

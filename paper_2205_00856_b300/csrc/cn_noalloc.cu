@@ -73,7 +73,7 @@ int plan_levels(int64_t n, NaLevel* lv, size_t* used) {
         if (L + 1 >= kNaMaxLevels) return -1;
         NaLevel& nx = lv[L + 1];
         nx.n = nn;
-        nx.P = na_ceil_div(nn - 1, kNaBlock);
+        nx.P = nn <= kBaseMax ? 0 : na_ceil_div(nn - 1, kNaBlock);
         nx.rows = off;
         off = na_align(off + (size_t)nn * 4 * 16);
         nx.slot = off;
@@ -85,6 +85,17 @@ int plan_levels(int64_t n, NaLevel* lv, size_t* used) {
     }
     *used = off;
     return L;
+}
+
+// The single system's entry at level l (row and block offsets 0).
+OneSys na_sys(const NaLevel* lv, int l) {
+    OneSys s;
+    s.e.n = lv[l].n;
+    s.e.P = lv[l].P;
+    s.e.row_off = 0;
+    s.e.blk_off = 0;
+    s.e.prod_blk_off = 0;
+    return s;
 }
 
 template <class R>
@@ -99,21 +110,22 @@ cudaError_t na_solve(unsigned char* base, const NaLevel* lv, int L, const ArrayS
         s.rows = rows(l);
         s.slot = slot(l);
         s.n = lv[l].n;
-        s.slot_stride = kThreads;
+        s.prod = 0;
         return s;
     };
+    auto grid = [&](int l) { return (unsigned)na_ceil_div(lv[l].P, kThreads); };
     const size_t smem = 2 * (size_t)kNaBlock * kThreads * 16;  // 32 KiB: below the default limit
-    k_reduce<R, ArraySource><<<(unsigned)na_ceil_div(lv[0].P, kThreads), kThreads, 0, st>>>(
-        src, lv[0].n, lv[0].P, kNaBlock, rows(1), slot(1), nullptr);
+    k_reduce<R, ArraySource, OneSys><<<grid(0), kThreads, 0, st>>>(src, na_sys(lv, 0), na_sys(lv, 1), kNaBlock,
+                                                                   rows(1), slot(1), nullptr);
     for (int l = 1; l < L; ++l)
-        k_reduce<R, LevelSource<R>><<<(unsigned)na_ceil_div(lv[l].P, kThreads), kThreads, 0, st>>>(
-            lsrc(l), lv[l].n, lv[l].P, kNaBlock, rows(l + 1), slot(l + 1), nullptr);
-    k_base<R><<<1, 32, 0, st>>>(lsrc(L), lv[L].n, xs(L), nullptr);
+        k_reduce<R, LevelSource<R>, OneSys><<<grid(l), kThreads, 0, st>>>(lsrc(l), na_sys(lv, l), na_sys(lv, l + 1),
+                                                                          kNaBlock, rows(l + 1), slot(l + 1), nullptr);
+    k_base<R><<<1, 32, 0, st>>>(lsrc(L), xs(L), nullptr);
     for (int l = L - 1; l >= 1; --l)
-        k_substitute<R, LevelSource<R>, ST><<<(unsigned)na_ceil_div(lv[l].P, kThreads), kThreads, smem, st>>>(
-            lsrc(l), lv[l].n, lv[l].P, kNaBlock, xs(l + 1), xs(l), nullptr);
-    k_substitute<R, ArraySource, double2><<<(unsigned)na_ceil_div(lv[0].P, kThreads), kThreads, smem, st>>>(
-        src, lv[0].n, lv[0].P, kNaBlock, xs(1), x, nullptr);
+        k_substitute<R, LevelSource<R>, OneSys, ST><<<grid(l), kThreads, smem, st>>>(
+            lsrc(l), na_sys(lv, l), na_sys(lv, l + 1), kNaBlock, xs(l + 1), xs(l), nullptr);
+    k_substitute<R, ArraySource, OneSys, double2><<<grid(0), kThreads, smem, st>>>(
+        src, na_sys(lv, 0), na_sys(lv, 1), kNaBlock, xs(1), x, nullptr);
     return cudaGetLastError();
 }
 

@@ -65,3 +65,40 @@ def test_null_arguments_rejected():
     assert lib.cn_solve_tridiag(None, None, None, None, None, None, 10, None) == 1
     assert lib.cn_plan_status(None) == 1
     assert lib.cn_plan_destroy(None) == 0
+
+
+@pytest.mark.parametrize("case", ["nsys0", "small_size", "cos_null", "bad_desc", "nan_xmin", "nan_cos"])
+def test_invalid_batch_rejected_on_host(case):
+    import numpy as np
+    lib = cnb.load()
+    h = C.c_void_p()
+    sizes = np.array([100, 3, 5000], np.int64)
+    xm = None
+    cos = None
+    d = _desc(n=0)
+    nsys = 3
+    if case == "nsys0":
+        nsys = 0
+    elif case == "small_size":
+        sizes[1] = 2
+    elif case == "cos_null":
+        d = _desc(n=0, pot=3, n_cos=4, L=0.0)
+    elif case == "bad_desc":
+        d = _desc(n=0, dx=-1.0)
+    elif case == "nan_xmin":
+        xm = np.array([0.0, float("nan"), 1.0])
+    elif case == "nan_cos":
+        d = _desc(n=0, pot=3, n_cos=2, L=0.0)
+        cos = np.array([[0.1, 0.2], [0.3, float("inf")], [0.0, 0.0]])
+    rc = lib.cn_batch_create(C.byref(d), nsys, sizes.ctypes.data, None if xm is None else xm.ctypes.data,
+                             None if cos is None else cos.ctypes.data, C.byref(h))
+    assert rc == 1 and not h.value
+
+
+def test_null_batch_arguments_rejected():
+    lib = cnb.load()
+    assert lib.cn_batch_create(None, 1, None, None, None, None) == 1
+    assert lib.cn_batch_step(None, None, None, None, 1, None) == 1
+    assert lib.cn_batch_offsets(None, None) == 1
+    assert lib.cn_batch_status(None) == 1
+    assert lib.cn_batch_destroy(None) == 0
