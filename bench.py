@@ -317,6 +317,106 @@ def adjoint_ratio(torch, cnb, args, dev):
             "checkpoints": int(np.ceil(np.sqrt(nsteps)))}
 
 
+def batch_gaussians(torch, sizes_t, offsets_t, dx, dev, seed):
+    """Batch state on the device: per system a Gaussian at the origin, width a
+    twentieth of the box, random momentum in [-1, 1) (input generation only)."""
+    nsys = sizes_t.numel()
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    k0 = (torch.rand(nsys, generator=g, dtype=torch.float64) * 2 - 1).to(dev)
+    seg = torch.repeat_interleave(torch.arange(nsys, device=dev), sizes_t)
+    j = torch.arange(int(offsets_t[-1]), device=dev, dtype=torch.int64) - offsets_t[:-1][seg]
+    x = (j - torch.div(sizes_t, 2, rounding_mode="floor")[seg]).to(torch.float64) * dx
+    sig = torch.clamp(0.05 * sizes_t.to(torch.float64) * dx, min=1.0)[seg]
+    psi = torch.polar(torch.exp(-x * x / (4 * sig * sig)), k0[seg] * x)
+    del seg, j, x, sig
+    return psi
+
+
+def batched_bench(torch, cnb, args, dev):
+    """4096 independent CN systems, sizes log-uniform in [1024, 2^20], random
+    8-term cosine potentials, dx = 0.1, dt = 0.01: (block, level_block) picked
+    by the autotuner on every 8th system, then 200 steps of the whole batch
+    replayed from one CUDA graph, against the same systems stepped one plan
+    (one launch sequence) per system -- eager, and captured in a graph."""
+    cfg = W.batched_config(n_systems=args.batched_systems)
+    sizes, cos_a, dx, dt = cfg["sizes"], cfg["cos_a"], cfg["dx"], cfg["dt"]
+    arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
+    kw = dict(pot=cnb.POT_COSSERIES, arith=arith)
+    m0, ml, tune = cnb.autotune_batch(sizes[::8], dx, dt, cos_a=cos_a[::8], steps=3, repeats=2, **kw)
+    b = cnb.Batch(sizes, dx, dt, cos_a=cos_a, block=m0, level_block=ml, **kw)
+    total = b.total
+    offs = torch.from_numpy(b.offsets).to(dev)
+    psi = batch_gaussians(torch, torch.from_numpy(sizes).to(dev), offs, dx, dev, 7)
+    nst = args.batched_steps
+    graph = b.capture(psi, nst)
+    graph.replay()  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    graph.replay()
+    e1.record()
+    e1.synchronize()
+    b.check()
+    g_ms = e0.elapsed_time(e1)
+    # eager launches of the same batch, for the graph's effect
+    e0.record()
+    b.step(psi, 20, psi_out=psi)
+    e1.record()
+    e1.synchronize()
+    eager_ms = e0.elapsed_time(e1) / 20
+    del graph
+    b.close()
+
+    # one plan per system on views of the same state
+    plans = [cnb.Plan(int(n), dx, dt, -(int(n) // 2) * dx, cos_a=cos_a[s], L=int(n) * dx, block=m0,
+                      level_block=ml, **kw) for s, n in enumerate(sizes)]
+    views = [psi[int(b.offsets[s]):int(b.offsets[s + 1])] for s in range(len(sizes))]
+
+    def per_system_step():
+        for p, v in zip(plans, views):
+            p.step(v, 1, psi_out=v)
+
+    per_system_step()  # warm-up
+    torch.cuda.synchronize()
+    reps = args.batched_baseline_steps
+    e0.record()
+    for _ in range(reps):
+        per_system_step()
+    e1.record()
+    e1.synchronize()
+    ps_ms = e0.elapsed_time(e1) / reps
+    pg = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(pg, stream=side):
+            per_system_step()
+    torch.cuda.current_stream().wait_stream(side)
+    pg.replay()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        pg.replay()
+    e1.record()
+    e1.synchronize()
+    psg_ms = e0.elapsed_time(e1) / reps
+    for p in plans:
+        p.check()
+        p.close()
+    del pg, views, psi
+    torch.cuda.empty_cache()
+    ms = g_ms / nst
+    return {"workload": cfg["name"], "systems": int(len(sizes)), "total_rows": int(total),
+            "size_min": int(sizes.min()), "size_max": int(sizes.max()), "steps": nst, "dtype": args.arith,
+            "block": m0, "level_block": ml, "autotune_ms_per_step": {f"{a}x{c}": t for (a, c), t in tune.items()},
+            "autotune_sample": "every 8th system",
+            "value": total * nst / (g_ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "eager_ms_per_step": eager_ms,
+            "per_system_eager_ms_per_step": ps_ms, "per_system_graph_ms_per_step": psg_ms,
+            "speedup_vs_per_system": ps_ms / ms, "speedup_vs_per_system_graph": psg_ms / ms,
+            "per_system_steps_timed": reps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -332,6 +432,11 @@ def main():
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--e2e-inner", type=int, default=50, help="CN steps per end-to-end call")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-systems", type=int, default=4096,
+                    help="batched uneven-size workload: systems (0: skip)")
+    ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--batched-baseline-steps", type=int, default=3,
+                    help="steps of the one-plan-per-system baseline timed")
     ap.add_argument("--adjoint-steps", type=int, default=2000,
                     help="gradient run (N=2^20, 500 controls): steps for the adjoint/forward ratio (0: skip)")
     args = ap.parse_args()
@@ -391,6 +496,7 @@ def main():
                "roofline": roofline(prof64, n, "f64", measured_peaks(), args.block) if rank == 0 else None}
 
     adj = adjoint_ratio(torch, cnb, args, dev) if (args.adjoint_steps > 0 and rank == 0) else None
+    bat = batched_bench(torch, cnb, args, dev) if (args.batched_systems > 0 and rank == 0) else None
 
     if rank != 0:
         if dist:
@@ -421,6 +527,8 @@ def main():
         line["f64_path"] = alt
     if adj:
         line["adjoint"] = adj
+    if bat:
+        line["batched"] = bat
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle()
     print(json.dumps(line), flush=True)

@@ -64,6 +64,7 @@ struct Engine {
     // adjoint (allocated on first use)
     double2* mu = nullptr;
     void* part = nullptr;
+    unsigned int* ticket = nullptr;  // inside the part allocation
     int part_n = 0;
     // kernel timing (cn_plan_profile)
     bool profiling = false;
@@ -676,8 +677,16 @@ cn_status cn_adjoint_step(cn_plan p, const void* psi_n, const void* psi_np1, con
     cudaError_t e = cudaSuccess;
     if (!p->mu) e = cudaMalloc(&p->mu, sizeof(double2) * (size_t)p->desc.n);
     if (e == cudaSuccess && !p->part) {
-        e = cudaMalloc(&p->part, 16 * (size_t)nparts);
-        p->part_n = nparts;
+        // partials, then the ticket counter of k_adjoint_finish (zero between launches)
+        e = cudaMalloc(&p->part, 16 * (size_t)nparts + 16);
+        if (e == cudaSuccess) e = cudaMemset(p->part, 0, 16 * (size_t)nparts + 16);
+        if (e == cudaSuccess) {
+            p->part_n = nparts;
+            p->ticket = reinterpret_cast<unsigned int*>(static_cast<char*>(p->part) + 16 * (size_t)nparts);
+        } else {
+            cudaFree(p->part);
+            p->part = nullptr;
+        }
     }
     if (e != cudaSuccess) return alloc_status(e);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -698,15 +707,14 @@ cn_status cn_adjoint_step(cn_plan p, const void* psi_n, const void* psi_np1, con
     const double2* pn = static_cast<const double2*>(psi_n);
     const double2* pn1 = static_cast<const double2*>(psi_np1);
     double2* ln = static_cast<double2*>(lam_n);
-    if (dfm) {
+    if (dfm)
         k_adjoint_finish<df><<<p->part_n, kAdjThreads, 0, st>>>(p->cnp, g, n, p->mu, l1, pn, pn1, ln,
-                                                                static_cast<df*>(p->part));
-        k_adjoint_sum<df><<<1, 32, 0, st>>>(static_cast<const df*>(p->part), p->part_n, p->desc.dt, dLdE);
-    } else {
+                                                                static_cast<df*>(p->part), p->ticket, p->desc.dt,
+                                                                dLdE);
+    else
         k_adjoint_finish<double><<<p->part_n, kAdjThreads, 0, st>>>(p->cnp, g, n, p->mu, l1, pn, pn1, ln,
-                                                                    static_cast<double*>(p->part));
-        k_adjoint_sum<double><<<1, 32, 0, st>>>(static_cast<const double*>(p->part), p->part_n, p->desc.dt, dLdE);
-    }
+                                                                    static_cast<double*>(p->part), p->ticket,
+                                                                    p->desc.dt, dLdE);
     return cuda_status(cudaGetLastError());
 }
 

@@ -831,8 +831,9 @@ k_cn_substitute_kept(Map sys, Map next, int m, const typename Store<R>::T* keep0
 //   lam_n = T_n mu = 2 mu - lam_{n+1}          (T_n + T_n^dagger = 2 for CN)
 //   dL/dE_n = dt Im( sum_j conj(mu_j) x_j (psi_n,j + psi_{n+1},j) ),
 // from d(T psi_{n+1} - T^dagger psi_n) = i dt/2 X (psi_{n+1} + psi_n) dE and
-// dL = 2 Re(lam^H dpsi).  Per-CTA partial sums go to `part`; k_adjoint_sum adds
-// them in a fixed order (deterministic) and accumulates dt * sum into *dLdE.
+// dL = 2 Re(lam^H dpsi).  Each CTA writes its partial sum to `part`; the CTA
+// that finishes last (a ticket counter) adds all partials in a fixed tree order
+// (deterministic), accumulates dt * sum into *dLdE and resets the ticket.
 constexpr int kAdjThreads = 256;
 
 __device__ __forceinline__ double adj_term(cx<double> mu, cx<double> s, double x) {
@@ -853,12 +854,31 @@ __device__ __forceinline__ df xcoord(const CNParams& p, const SysGrid& g, int64_
     df dx = dfc(p.dx_f);
     return df_add(dfc(g.xo_f), df_add(df_mul_f(df_mul_f(dx, jh), 65536.0f), df_mul_f(dx, jl)));
 }
+// L2-coherent loads of another CTA's partial (not through this SM's L1)
+__device__ __forceinline__ double ld_part(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ df ld_part(const df* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return df_make(v.x, v.y);
+}
+
+// Fixed-order sum over the CTA's threads (thread 0 holds the result).
+template <class R>
+__device__ __forceinline__ R cta_sum(R v, R* red) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = kAdjThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = radd(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    return red[0];
+}
 
 template <class R>
 __global__ void __launch_bounds__(kAdjThreads)
 k_adjoint_finish(CNParams p, SysGrid sg, int64_t n, const double2* mu, const double2* lam_np1, const double2* psi_n,
-                 const double2* psi_np1, double2* lam_n, R* part) {
+                 const double2* psi_np1, double2* lam_n, R* part, unsigned int* ticket, double dt, double* dLdE) {
     __shared__ R red[kAdjThreads];
+    __shared__ bool last;
     R acc = RealOps<R>::from_d(0.0);
     for (int64_t j = (int64_t)blockIdx.x * kAdjThreads + threadIdx.x; j < n; j += (int64_t)gridDim.x * kAdjThreads) {
         const cx<R> m = load128<R>(mu + j);
@@ -867,21 +887,23 @@ k_adjoint_finish(CNParams p, SysGrid sg, int64_t n, const double2* mu, const dou
         acc = radd(acc, adj_term(m, s, xcoord(p, sg, j, R())));
         store128(lam_n + j, csub(cadd(m, m), l1));
     }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int w = kAdjThreads / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] = radd(red[threadIdx.x], red[threadIdx.x + w]);
-        __syncthreads();
+    const R blk = cta_sum(acc, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = blk;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
-    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
-}
-
-template <class R>
-__global__ void k_adjoint_sum(const R* part, int nparts, double dt, double* dLdE) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    R acc = RealOps<R>::from_d(0.0);
-    for (int i = 0; i < nparts; ++i) acc = radd(acc, part[i]);
-    *dLdE += dt * RealOps<R>::to_d(acc);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    R t = RealOps<R>::from_d(0.0);
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kAdjThreads) t = radd(t, ld_part(part + i));
+    __syncthreads();  // red is reused
+    const R tot = cta_sum(t, red);
+    if (threadIdx.x == 0) {
+        *dLdE += dt * RealOps<R>::to_d(tot);
+        *ticket = 0u;
+    }
 }
 
 // ------------------------------------------------------------------ control samples

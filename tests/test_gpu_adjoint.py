@@ -162,3 +162,24 @@ def test_gradcheck_tiny():
         return loss_fn(propagate(p, uu, plan, nsteps, tf), wt)
 
     assert torch.autograd.gradcheck(f, (psi0, u), eps=1e-6, atol=1e-7, rtol=1e-6)
+
+
+def test_segment_graphs_match_eager_bitwise():
+    n, nsteps, nc = 3000, 37, 6  # K = 7: five graph-replayed segments and a partial one
+    cfg = W.soft_coulomb_config(n=n, dt=0.02, nsteps=nsteps)
+    tf = nsteps * cfg["dt"]
+    plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0,
+                    arith=cnb.ARITH_DF64)
+    psi0 = to_dev(W.gaussian(n, cfg["dx"], cfg["x_min"], 0.0, 1.0, 0.5))
+    wt = to_dev(W.outside_mask_weights(n, cfg["dx"], 40))
+    res = []
+    for graphs in (False, True, True):  # the second graph pass replays the cached graphs
+        ut = to_dev(0.1 * np.sin(np.arange(nc))).requires_grad_(True)
+        p0 = psi0.clone().requires_grad_(True)
+        out = propagate(p0, ut, plan, nsteps, tf, use_graphs=graphs)
+        loss_fn(out, wt).backward()
+        res.append((out.detach().cpu().numpy(), ut.grad.cpu().numpy(), p0.grad.cpu().numpy()))
+    plan.check()
+    for r in res[1:]:
+        for a, b in zip(r, res[0]):
+            assert np.array_equal(a, b)
