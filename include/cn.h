@@ -107,6 +107,24 @@ typedef struct {
  * a status word) on the current device.  On success *out owns it. */
 cn_status cn_plan_create(const cn_desc* desc, cn_plan* out);
 
+/* Create a plan with an explicit nesting depth and block sizes, for studying
+ * the partition (Sec. 4.3: the single- and multiple-iteration time model and
+ * Eq. optimal_nblocks / optimal-P-multistage; Fig. 2).  Level i, i = 0 ..
+ * nlevels-1, is cut into blocks of blocks[i] rows (n_bl(i+1) = ceil((rows_i -
+ * 1) / blocks[i]) parallel blocks, one thread each) and reduced; level
+ * nlevels is solved by the serial RS stage whatever its size (one thread).
+ *   nlevels: 1 .. CN_MAX_LEVELS - 1;
+ *   blocks: host int32[nlevels], each 3 .. CN_LEVELS_MAX_BLOCK; blocks longer
+ *     than 32 rows take a substitution that stages its values in device
+ *     scratch instead of shared memory (the plan allocates it);
+ *   desc: as for cn_plan_create; desc->block and desc->level_block are ignored.
+ * Returns CN_ERR_INVALID_ARG if some level i < nlevels has fewer than 3 rows,
+ * and CN_ERR_UNSUPPORTED for CN_FLAG_RECOMPUTE with blocks[0] > 32.  The plan
+ * is used with every cn_plan_* / cn_step* / cn_solve_tridiag / cn_adjoint_step
+ * call like any other. */
+#define CN_LEVELS_MAX_BLOCK 1048576
+cn_status cn_plan_create_levels(const cn_desc* desc, int32_t nlevels, const int32_t* blocks, cn_plan* out);
+
 /* Free the plan and its workspace (synchronises the device first).  NULL is a no-op. */
 cn_status cn_plan_destroy(cn_plan plan);
 

@@ -33,7 +33,7 @@ EXPORTS = ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_s
            "cn_plan_query", "cn_plan_profile", "cn_plan_profile_read", "cn_plan_status", "cn_status_string",
            "cn_version", "cn_solve_tridiag_noalloc", "cn_adjoint_step", "cn_field_from_controls",
            "cn_field_grad_to_controls", "cn_batch_create", "cn_batch_destroy", "cn_batch_offsets",
-           "cn_batch_step", "cn_batch_status")
+           "cn_batch_step", "cn_batch_status", "cn_plan_create_levels")
 NOALLOC_MAX_N = 1048576
 MAX_LEVELS = 24
 PROFILE_CLASSES = ("reduce_level0", "substitute_level0", "reduce_levels_ge1", "substitute_levels_ge1", "rs_stage")
@@ -99,6 +99,8 @@ def load(build_if_missing: bool = True):
             lib.cn_status_string.restype = C.c_char_p
             lib.cn_version.argtypes = []
             lib.cn_version.restype = C.c_char_p
+            lib.cn_plan_create_levels.argtypes = [C.POINTER(_Desc), C.c_int32, vp, C.POINTER(vp)]
+            lib.cn_plan_create_levels.restype = C.c_int
             lib.cn_batch_create.argtypes = [C.POINTER(_Desc), i64, vp, vp, vp, C.POINTER(vp)]
             lib.cn_batch_destroy.argtypes = [vp]
             lib.cn_batch_offsets.argtypes = [vp, vp]
@@ -142,10 +144,13 @@ class Plan:
 
     pot / V0 / soft_s / cos_a / L describe the static potential Vs(x) of
     H = -1/2 d^2/dx^2 + Vs(x) + x E(t) on x_j = x_min + j dx.
+    levels: explicit nesting (cn_plan_create_levels): the block size of each
+    reduced level, the last level solved serially whatever its size; None
+    nests with block / level_block until the reduced system has <= 16 rows.
     """
 
     def __init__(self, n, dx, dt, x_min, pot=POT_NONE, V0=None, soft_s=2.0, cos_a=None, L=1.0,
-                 block=0, arith=ARITH_F64, flags=0, level_block=0):
+                 block=0, arith=ARITH_F64, flags=0, level_block=0, levels=None):
         import torch
         self._lib = load()
         self.n = int(n)
@@ -162,7 +167,12 @@ class Plan:
                   None if self._cos is None else self._cos.ctypes.data, float(L), int(block), self.arith,
                   int(flags), int(level_block))
         h = C.c_void_p()
-        _check(self._lib.cn_plan_create(C.byref(d), C.byref(h)), "cn_plan_create")
+        if levels is None:
+            _check(self._lib.cn_plan_create(C.byref(d), C.byref(h)), "cn_plan_create")
+        else:
+            lv = np.ascontiguousarray(levels, dtype=np.int32)
+            _check(self._lib.cn_plan_create_levels(C.byref(d), int(lv.size), lv.ctypes.data, C.byref(h)),
+                   "cn_plan_create_levels")
         self._h = h
 
     def close(self) -> None:

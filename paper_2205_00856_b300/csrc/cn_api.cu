@@ -47,6 +47,9 @@ struct Engine {
     int nsys = 0;
     std::vector<LevelData> lv;    // lv[0]: the systems themselves
     std::vector<int> base_level;  // per system: the level the RS stage solves
+    std::vector<int> lvl_m;       // explicit block size per reduced level (cn_plan_create_levels), else empty
+    void* zc = nullptr;           // substitution scratch for blocks longer than kSmemRowsMax
+    void* base_cs = nullptr;      // serial RS scratch for a last level longer than kBaseMax
     void* d_base = nullptr;       // BaseSys<R>[nsys] (batches)
     std::vector<SysGrid> grid;    // per system
     SysGrid* d_grid = nullptr;    // device copy (batches)
@@ -122,6 +125,8 @@ void free_engine(Engine* p) {
         cudaFree(L.d_sys);
     }
     cudaFree(p->d_base);
+    cudaFree(p->zc);
+    cudaFree(p->base_cs);
     cudaFree(p->d_grid);
     cudaFree(p->state);
     cudaFree(p->keep);
@@ -173,7 +178,7 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
     p->base_level.assign(ns, -1);
     {
         LevelData L0;
-        L0.m = p->desc.block;
+        L0.m = p->lvl_m.empty() ? p->desc.block : p->lvl_m[0];
         L0.sys.resize(ns);
         int64_t roff = 0, boff = 0;
         for (int s = 0; s < ns; ++s) {
@@ -190,11 +195,12 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
         L0.total = boff;
         p->lv.push_back(std::move(L0));
     }
+    const int nlev = (int)p->lvl_m.size();
     for (;;) {
         const int l = (int)p->lv.size();
         if (l >= CN_MAX_LEVELS) return cudaErrorInvalidValue;
         LevelData L;
-        L.m = p->desc.level_block;
+        L.m = nlev ? (l < nlev ? p->lvl_m[(size_t)l] : 0) : p->desc.level_block;
         L.sys.resize(ns);
         int64_t roff = 0, boff = 0;
         for (int s = 0; s < ns; ++s) {
@@ -203,7 +209,10 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
             e.n = q.P > 0 ? q.P + 1 : 0;
             e.P = 0;
             if (e.n > 0) {
-                if (e.n <= kBaseMax) p->base_level[s] = l;
+                // explicit depth: reduce exactly nlev levels; else until <= kBaseMax rows
+                const bool base = nlev ? (l == nlev) : (e.n <= kBaseMax);
+                if (base) p->base_level[s] = l;
+                else if (e.n < 3) return cudaErrorInvalidValue;  // too short to cut into blocks
                 else e.P = ceil_div(e.n - 1, L.m);
             }
             e.row_off = roff;
@@ -226,6 +235,21 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
         if (e == cudaSuccess) e = cudaMalloc(&L.slot, 3 * kCplx * nslot);
         if (e == cudaSuccess) e = cudaMalloc(&L.x, kCplx * (size_t)L.rows_total);
         if (e == cudaSuccess) e = cudaMemset(L.slot, 0, 3 * kCplx * nslot);
+    }
+    // long blocks (substitution scratch, two entries per row) and a long last level (serial RS)
+    size_t zc_entries = 0;
+    for (size_t l = 0; l + 1 < p->lv.size(); ++l)
+        if (p->lv[l].m > kSmemRowsMax) zc_entries = std::max(zc_entries, 2 * (size_t)p->lv[l].rows_total);
+    if (e == cudaSuccess && zc_entries) {
+        p->workspace_bytes += (int64_t)(kCplx * zc_entries);
+        e = cudaMalloc(&p->zc, kCplx * zc_entries);
+    }
+    if (e == cudaSuccess && !p->batched) {
+        const int64_t nb = p->lv[(size_t)p->base_level[0]].sys[0].n;
+        if (nb > kBaseMax) {
+            p->workspace_bytes += (int64_t)(kCplx * (size_t)nb);
+            e = cudaMalloc(&p->base_cs, kCplx * (size_t)nb);
+        }
     }
     if (e == cudaSuccess && p->batched) {
         for (LevelData& L : p->lv) {
@@ -301,10 +325,14 @@ cudaError_t launch_reduce(const Src& src, Map sys, Map next, int m, const LevelD
 
 template <class R, class Src, class Map, class XT>
 cudaError_t launch_substitute(const Src& src, Map sys, Map next, int m, const LevelData& nextL, XT* x, int* status,
-                              int64_t total, cudaStream_t st) {
+                              int64_t total, void* zc, cudaStream_t st) {
     if (total == 0) return cudaSuccess;
-    k_substitute<R, Src, Map, XT><<<grid_for(total), kThreads, subst_smem(m), st>>>(src, sys, next, m,
-                                                                                  x_of<R>(nextL), x, status);
+    if (m > kSmemRowsMax)
+        k_substitute_gmem<R, Src, Map, XT><<<grid_for(total), kThreads, 0, st>>>(
+            src, sys, next, m, x_of<R>(nextL), x, static_cast<typename Store<R>::T*>(zc), status);
+    else
+        k_substitute<R, Src, Map, XT><<<grid_for(total), kThreads, subst_smem(m), st>>>(src, sys, next, m,
+                                                                                      x_of<R>(nextL), x, status);
     return cudaGetLastError();
 }
 
@@ -322,8 +350,11 @@ cudaError_t set_smem_limits_map(int m0, int ml) {
 
 template <class R>
 cudaError_t set_smem_limits(const Engine* p) {
-    if (p->batched) return set_smem_limits_map<R, ManySys, ManyGrid>(p->desc.block, p->desc.level_block);
-    return set_smem_limits_map<R, OneSys, OneGrid>(p->desc.block, p->desc.level_block);
+    // the largest staged block per kernel kind (longer blocks take the scratch variants)
+    int m0 = std::min(p->lv[0].m, kSmemRowsMax), ml = 3;
+    for (size_t l = 1; l + 1 < p->lv.size(); ++l) ml = std::max(ml, std::min(p->lv[l].m, kSmemRowsMax));
+    if (p->batched) return set_smem_limits_map<R, ManySys, ManyGrid>(m0, ml);
+    return set_smem_limits_map<R, OneSys, OneGrid>(m0, ml);
 }
 
 // Levels >= 1 of the nested solve: reductions down, RS, substitutions up.
@@ -346,7 +377,11 @@ cudaError_t solve_levels(Engine* p, cudaStream_t st) {
                 static_cast<const BaseSys<R>*>(p->d_base), p->nsys, p->status);
         } else {
             const LevelData& B = p->lv[(size_t)p->base_level[0]];
-            k_base<R><<<1, 32, 0, st>>>(level_source<R>(B).bind(B.sys[0]), x_of<R>(B), p->status);
+            if (p->base_cs)
+                k_base_serial<R><<<1, 32, 0, st>>>(level_source<R>(B).bind(B.sys[0]), x_of<R>(B),
+                                                   static_cast<typename Store<R>::T*>(p->base_cs), p->status);
+            else
+                k_base<R><<<1, 32, 0, st>>>(level_source<R>(B).bind(B.sys[0]), x_of<R>(B), p->status);
         }
         e = cudaGetLastError();
     }
@@ -354,7 +389,7 @@ cudaError_t solve_levels(Engine* p, cudaStream_t st) {
         ProfScope ps(p, kProfSubstL, st);
         with_maps(p, l, [&](auto a, auto b) {
             e = launch_substitute<R>(level_source<R>(p->lv[l]), a, b, p->lv[l].m, p->lv[l + 1], x_of<R>(p->lv[l]),
-                                     p->status, p->lv[l].total, st);
+                                     p->status, p->lv[l].total, p->zc, st);
         });
     }
     return e;
@@ -374,7 +409,7 @@ cudaError_t solve_arrays(Engine* p, const ArraySource& src, double2* x, cudaStre
     if ((e = solve_levels<R>(p, st)) != cudaSuccess) return e;
     ProfScope ps(p, kProfSubst0, st);
     with_maps(p, 0, [&](auto a, auto b) {
-        e = launch_substitute<R>(src, a, b, p->lv[0].m, p->lv[1], x, p->status, p->lv[0].total, st);
+        e = launch_substitute<R>(src, a, b, p->lv[0].m, p->lv[1], x, p->status, p->lv[0].total, p->zc, st);
     });
     return e;
 }
@@ -400,7 +435,10 @@ cudaError_t cn_solve(Engine* p, const CNStep& s, double2* x, cudaStream_t st) {
     if ((e = solve_levels<R>(p, st)) != cudaSuccess) return e;
     ProfScope ps(p, kProfSubst0, st);
     with_maps_grid(p, [&](auto a, auto b, auto gr) {
-        if (keep)
+        if (keep && L0.m > kSmemRowsMax)
+            k_cn_substitute_kept_gmem<R><<<grid, kThreads, 0, st>>>(a, b, L0.m, keep, x_of<R>(L1), x,
+                                                                    static_cast<ST*>(p->zc));
+        else if (keep)
             k_cn_substitute_kept<R><<<grid, kThreads, kept_smem(L0.m), st>>>(a, b, L0.m, keep, x_of<R>(L1), x);
         else
             k_cn_substitute<R><<<grid, kThreads, subst_smem(L0.m), st>>>(s, a, b, gr, L0.m, x_of<R>(L1), x,
@@ -484,9 +522,11 @@ cn_status create_engine(Engine* p, const cn_desc* desc, const std::vector<int64_
     const bool use_table = (desc->flags & CN_FLAG_COEFF_TABLE) || p->batched ||
                            (df_mode && (desc->pot == CN_POT_ARRAY || desc->pot == CN_POT_COSSERIES));
     const bool recompute = (desc->flags & CN_FLAG_RECOMPUTE) != 0;
+    if (recompute && !p->lvl_m.empty() && p->lvl_m[0] > kSmemRowsMax) return CN_ERR_UNSUPPORTED;
 
     cudaError_t e = build_hierarchy(p, sizes);
-    if (e != cudaSuccess) return e == cudaErrorInvalidValue ? CN_ERR_UNSUPPORTED : alloc_status(e);
+    if (e == cudaErrorInvalidValue) return p->lvl_m.empty() ? CN_ERR_UNSUPPORTED : CN_ERR_INVALID_ARG;
+    if (e != cudaSuccess) return alloc_status(e);
     const int64_t rows0 = p->lv[0].rows_total;
     // keep: entries (2k) P + t and (2k+1) P + t for block rows k = 1..m-1 of each system
     const size_t keep_entries = 2 * (size_t)p->lv[0].m * (size_t)p->lv[0].total;
@@ -602,6 +642,30 @@ cn_status cn_plan_create(const cn_desc* desc, cn_plan* out) {
     cn_plan p = new (std::nothrow) cn_plan_s();
     if (!p) return CN_ERR_OOM;
     v = create_engine(p, desc, std::vector<int64_t>{desc->n}, std::vector<double>{desc->x_min}, desc->cos_a);
+    if (v != CN_OK) {
+        destroy_engine(p);
+        delete p;
+        return v;
+    }
+    *out = p;
+    return CN_OK;
+}
+
+cn_status cn_plan_create_levels(const cn_desc* desc, int32_t nlevels, const int32_t* blocks, cn_plan* out) {
+    if (!out) return CN_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!desc || !blocks || nlevels < 1 || nlevels >= CN_MAX_LEVELS) return CN_ERR_INVALID_ARG;
+    for (int l = 0; l < nlevels; ++l)
+        if (blocks[l] < 3 || blocks[l] > CN_LEVELS_MAX_BLOCK) return CN_ERR_INVALID_ARG;
+    cn_desc d = *desc;
+    d.block = 0;
+    d.level_block = 0;
+    cn_status v = validate_desc(&d, true);
+    if (v != CN_OK) return v;
+    cn_plan p = new (std::nothrow) cn_plan_s();
+    if (!p) return CN_ERR_OOM;
+    p->lvl_m.assign(blocks, blocks + nlevels);
+    v = create_engine(p, &d, std::vector<int64_t>{d.n}, std::vector<double>{d.x_min}, d.cos_a);
     if (v != CN_OK) {
         destroy_engine(p);
         delete p;

@@ -47,7 +47,7 @@ namespace cnb {
 constexpr int kThreads = 128;   // threads per CTA of the reduce / substitute kernels
 constexpr int kMaxCos = 16;     // cos-series terms held in the kernel parameters
 constexpr int kBaseMax = 16;    // largest reduced system solved by the serial RS stage
-constexpr int kMaxBlock = 64;   // largest block (rows between joint lines)
+constexpr int kSmemRowsMax = 32; // longest block whose substitution stages in shared memory
 
 // joint line t of a level with n rows, block size m and P blocks
 __host__ __device__ __forceinline__ int64_t joint_line(int64_t t, int64_t P, int64_t m, int64_t n) {
@@ -342,6 +342,53 @@ k_substitute(Src src0, Map sys, Map next, int m, const typename Store<R>::T* x_n
     if (!ok) flag_error(status, kStatusNonfinite);
 }
 
+// Same substitution for blocks longer than the shared-memory staging allows:
+// z_k and c'_k go to a scratch array of two entries per row of the level
+// (zc[2 r], zc[2 r + 1] for row r; a thread's rows are contiguous) and the
+// backward pass reads them back.
+template <class R, class Src, class Map, class XT>
+__global__ void __launch_bounds__(kThreads)
+k_substitute_gmem(Src src0, Map sys, Map next, int m, const typename Store<R>::T* x_next0, XT* x0,
+                  typename Store<R>::T* zc0, int* status) {
+    typedef typename Store<R>::T ST;
+    const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (g >= sys.total()) return;
+    bool ok = true;
+    const int si = sys.find(g);
+    const LvlSys& e = sys.at(si);
+    const Src src = src0.bind(e);
+    const int64_t n = e.n, P = e.P, t = g - e.blk_off;
+    const ST* x_next = x_next0 + next.at(si).row_off;
+    XT* x = x0 + e.row_off;
+    const int64_t J0 = joint_line(t, P, m, n);
+    const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
+    ST* zc = zc0 + 2 * (e.row_off + J0);
+    const cx<R> xL = sload(x_next + t);
+    const cx<R> xR = sload(x_next + t + 1);
+    cx<R> zp = czero<R>(), cpp = czero<R>();
+    for (int k = 1; k < gap; ++k) {
+        const Row<R> rk = src.template row<R>(J0 + k);
+        cx<R> rhs = rk.d;
+        if (k == 1) rhs = csub(rhs, cmul(rk.b, xL));
+        if (k == gap - 1) rhs = csub(rhs, cmul(rk.c, xR));
+        const cx<R> piv = (k == 1) ? rk.a : csub(rk.a, cmul(rk.b, cpp));
+        const cx<R> w = crcp(piv, ok);
+        zp = (k == 1) ? cmul(rhs, w) : cmul(csub(rhs, cmul(rk.b, zp)), w);
+        cpp = cmul(rk.c, w);
+        sstore(zc + 2 * k, zp);
+        sstore(zc + 2 * k + 1, cpp);
+    }
+    cx<R> y = zp;
+    put<XT, R>(x + J0 + gap - 1, y);
+    for (int k = gap - 2; k >= 1; --k) {
+        y = csub(sload(zc + 2 * k), cmul(sload(zc + 2 * k + 1), y));
+        put<XT, R>(x + J0 + k, y);
+    }
+    put<XT, R>(x + J0, xL);
+    if (t == P - 1) put<XT, R>(x + J0 + gap, xR);
+    if (!ok) flag_error(status, kStatusNonfinite);
+}
+
 // ------------------------------------------------------------------ RS stage
 // Serial Thomas elimination of each system's last reduced system (Table 1, RS),
 // one thread per system.
@@ -372,6 +419,32 @@ __device__ __forceinline__ void base_solve(const LevelSource<R>& src, typename S
     sstore(x + n - 1, y);
     for (int64_t w = n - 2; w >= 0; --w) {
         y = cmul(csub(D[w], cmul(C[w], y)), crcp(A[w], ok));
+        sstore(x + w, y);
+    }
+    if (!ok) flag_error(status, kStatusNonfinite);
+}
+
+// Serial Thomas elimination of a reduced system of any size by one thread
+// (explicit nesting depth, where the last level can be long): z in x, c' in cs.
+template <class R>
+__global__ void k_base_serial(LevelSource<R> src, typename Store<R>::T* x, typename Store<R>::T* cs, int* status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    bool ok = true;
+    const int64_t n = src.n;
+    cx<R> zp = czero<R>(), cpp = czero<R>();
+    for (int64_t w = 0; w < n; ++w) {
+        const Row<R> r = src.template row<R>(w);
+        // m_w = a_w - b_w c'_{w-1};  z_w = (d_w - b_w z_{w-1}) / m_w;  c'_w = c_w / m_w
+        const cx<R> piv = (w == 0) ? r.a : csub(r.a, cmul(r.b, cpp));
+        const cx<R> iv = crcp(piv, ok);
+        zp = (w == 0) ? cmul(r.d, iv) : cmul(csub(r.d, cmul(r.b, zp)), iv);
+        cpp = cmul(r.c, iv);
+        sstore(x + w, zp);
+        sstore(cs + w, cpp);
+    }
+    cx<R> y = zp;
+    for (int64_t w = n - 2; w >= 0; --w) {
+        y = csub(sload(x + w), cmul(sload(cs + w), y));
         sstore(x + w, y);
     }
     if (!ok) flag_error(status, kStatusNonfinite);
@@ -823,6 +896,44 @@ k_cn_substitute_kept(Map sys, Map next, int m, const typename Store<R>::T* keep0
         // the CTA holding the last block of the system also writes its last joint line
         store128(x + e0.n - 1, sload(x_next0 + next.at(s0).row_off + e0.P));
     }
+}
+
+// Store-mode substitution for blocks longer than the shared-memory tile: z goes
+// to a scratch array (one entry per row, a thread's rows contiguous) and the
+// backward pass reads it back with the kept pivots.
+template <class R, class Map>
+__global__ void __launch_bounds__(kThreads)
+k_cn_substitute_kept_gmem(Map sys, Map next, int m, const typename Store<R>::T* keep0,
+                          const typename Store<R>::T* x_next0, double2* x0, typename Store<R>::T* zs0) {
+    typedef typename Store<R>::T ST;
+    const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (g >= sys.total()) return;
+    const int si = sys.find(g);
+    const LvlSys& e = sys.at(si);
+    const int64_t n = e.n, P = e.P, t = g - e.blk_off;
+    const ST* keep = keep0 + 2 * (int64_t)m * e.blk_off;
+    const ST* x_next = x_next0 + next.at(si).row_off;
+    double2* x = x0 + e.row_off;
+    const int64_t J0 = joint_line(t, P, m, n);
+    const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
+    ST* zs = zs0 + e.row_off + J0;
+    const cx<R> xL = sload(x_next + t);
+    const cx<R> xR = sload(x_next + t + 1);
+    cx<R> zp = xL;
+    for (int k = 1; k < gap; ++k) {
+        cx<R> rhs = cadd(sload(keep + (2 * k) * P + t), zp);
+        if (k == gap - 1) rhs = cadd(rhs, xR);
+        zp = cmul(rhs, sload(keep + (2 * k + 1) * P + t));
+        sstore(zs + k, zp);
+    }
+    cx<R> y = zp;
+    store128(x + J0 + gap - 1, y);
+    for (int k = gap - 2; k >= 1; --k) {
+        y = cfma(sload(zs + k), sload(keep + (2 * k + 1) * P + t), y);
+        store128(x + J0 + k, y);
+    }
+    store128(x + J0, xL);
+    if (t == P - 1) store128(x + J0 + gap, xR);
 }
 
 // ------------------------------------------------------------------ adjoint step
