@@ -45,9 +45,14 @@ WORKLOAD_STEPS = 1000  # length of the benchmarked propagation (field samples)
 #   FP64:          reduce 65 + 64/m,   substitute 16
 #   double-float:  reduce 604 + 600/m, substitute 150   (binary32 flops)
 def flops_per_row(kernel: str, arith: str, m: int) -> float:
+    """Flops per grid row of the level-0 kernels (FMA = 2; binary32 flops of the
+    double-float formulation, binary64 flops of the FP64 one).  A block of m rows
+    costs one loop body per row 2..m-1, plus its two first rows and its JD/JU and
+    joint-row exchange (reduction), or one forward/back pair per interior row
+    (substitution)."""
     if arith == "f64":
-        return 65.0 + 64.0 / m if kernel == "reduce_level0" else 16.0
-    return 604.0 + 600.0 / m if kernel == "reduce_level0" else 150.0
+        return 59.0 - 30.0 / m if kernel == "reduce_level0" else 16.0 - 14.0 / m
+    return 548.0 - 261.0 / m if kernel == "reduce_level0" else 150.0 - 128.0 / m
 
 
 STEP_BYTES_PER_ROW = 32.0
@@ -83,9 +88,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_class: str, arith: str, n: int):
-    """DRAM bytes per launch of a kernel from the committed ncu summary
-    (profiles/traffic.txt), scaled to n rows; None if absent or stale."""
+def ncu_traffic(kernel_class: str, arith: str, n: int, m: int):
+    """DRAM bytes per launch of a level-0 kernel with block m from the committed
+    ncu summary (profiles/traffic.txt), scaled to n rows; None if absent or if
+    the kernel sources changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         lines = open(path).read().splitlines()
@@ -94,9 +100,9 @@ def ncu_traffic(kernel_class: str, arith: str, n: int):
     src = kernel_source_hash()
     for ln in lines:
         parts = ln.split()
-        if len(parts) >= 5 and not ln.startswith("#"):
-            cls, ar, rows, byts, hsh = parts[:5]
-            if cls == kernel_class and ar == arith and hsh == src:
+        if len(parts) >= 6 and not ln.startswith("#"):
+            cls, ar, rows, byts, hsh, blk = parts[:6]
+            if cls == kernel_class and ar == arith and hsh == src and int(blk) == m:
                 return float(byts) * n / float(rows)
     return None
 
@@ -210,18 +216,23 @@ def workload_config(args):
             "potential": "-1/sqrt(x^2+2) + x E(t)", "field": "0.05 sin^2(pi t/T) cos(0.057 t), T = 4*2pi/0.057",
             "steps_per_bench_step": 1, "workload_steps": WORKLOAD_STEPS, "block": args.block,
             "level_block": getattr(args, "level_block", 8),
+            "coefficients": "static part tabulated once" if getattr(args, "coeff_table", False)
+            else "regenerated from V(x) and E(t) every step",
             "arith": args.arith, "l2": "inputs larger than L2 (2 x 256 MiB states vs 126 MB L2), no flush",
             "parallelism": f"replicas x{args.gpus}"}
 
 
 def make_plan(cnb, cfg, args, arith):
     return cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0,
-                    block=args.block, arith=arith, level_block=args.level_block)
+                    block=args.block, arith=arith, level_block=args.level_block,
+                    flags=cnb.FLAG_COEFF_TABLE if args.coeff_table else 0)
 
 
 def time_steps(torch, plan, psi0, E, steps, warmup, dist, dev, sample_clocks):
     """warmup + steps single CN steps (one cn_step call each), CUDA events on the
-    launching stream, per-kernel-class event times; returns (ms, prof, clocks)."""
+    launching stream; then the same steps again with per-kernel-class events
+    (cn_plan_profile) for the kernel breakdown, kept out of the timed region so
+    the event records between kernels do not inflate it.  Returns (ms, prof, clocks)."""
     cur = torch.from_numpy(psi0).to(dev)
     stream = torch.cuda.current_stream()
     def one_step(k):
@@ -236,8 +247,6 @@ def time_steps(torch, plan, psi0, E, steps, warmup, dist, dev, sample_clocks):
     torch.cuda.synchronize()
     uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    plan.profile(True)
-    plan.profile_read()
     clk = ClockSampler(uuid) if sample_clocks else None
     if clk:
         clk.__enter__()
@@ -248,10 +257,16 @@ def time_steps(torch, plan, psi0, E, steps, warmup, dist, dev, sample_clocks):
     torch.cuda.synchronize()
     if clk:
         clk.__exit__()
+    ms = ev0.elapsed_time(ev1)
+    # kernel breakdown: same steps, per-kernel-class events on the same stream
+    plan.profile(True)
+    plan.profile_read()
+    for k in range(steps):
+        one_step(warmup + steps + k)
+    torch.cuda.synchronize()
     plan.profile(False)
     prof = plan.profile_read()
     plan.check()
-    ms = ev0.elapsed_time(ev1)
     if dist:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -277,7 +292,7 @@ def roofline(prof, n, arith, peaks, m):
                 "peak_source": "FP32 issue peak 148 SM x 128 lanes x 2 x 2.032 GHz (recipe unit counts and clock)",
                 "basis": "binary32 flops (FMA = 2) of the double-float formulation per grid row"}
     roof.update({"kernel": dom, "avg_launch_ms": avg_s * 1e3, "flops_per_row": flops_per_row(dom, arith, m),
-                 "traffic": ncu_traffic(dom, arith, n)})
+                 "traffic": ncu_traffic(dom, arith, n, m)})
     return roof
 
 
@@ -426,8 +441,10 @@ def main():
     ap.add_argument("--arith", choices=["f64", "df64"], default="df64")
     ap.add_argument("--f64-steps", type=int, default=100,
                     help="also time the native-FP64 path for this many steps (0: skip)")
-    ap.add_argument("--block", type=int, default=8)
-    ap.add_argument("--level-block", type=int, default=8)
+    ap.add_argument("--block", type=int, default=0, help="level-0 block rows (0: autotune with --level-block)")
+    ap.add_argument("--level-block", type=int, default=0, help="rows per block on levels >= 1 (0: autotune)")
+    ap.add_argument("--coeff-table", action="store_true",
+                    help="tabulate the static diagonal part once instead of regenerating V(x) every step")
     ap.add_argument("--n", type=int, default=1 << 24, help="grid points (profiling runs use smaller grids)")
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--e2e-inner", type=int, default=50, help="CN steps per end-to-end call")
@@ -461,6 +478,13 @@ def main():
     E_host = W.field_midpoints(WORKLOAD_STEPS, cfg["dt"])
     E = torch.from_numpy(E_host).to(dev)
     arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
+    tune = None
+    if args.block == 0 or args.level_block == 0:
+        b0, l0, tt = cnb.autotune_plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0,
+                                       arith=arith, flags=cnb.FLAG_COEFF_TABLE if args.coeff_table else 0)
+        args.block = args.block or b0
+        args.level_block = args.level_block or l0
+        tune = {f"{a}x{c}": t for (a, c), t in tt.items()}
     plan = make_plan(cnb, cfg, args, arith)
     info = plan.info()
     ms, prof, clocks = time_steps(torch, plan, psi0, E, args.steps, args.warmup, dist, dev, rank == 0)
@@ -517,12 +541,16 @@ def main():
             "vs_baseline": None, "dtype": args.arith, "data": "synthetic", "config": workload_config(args),
             "roofline": roof, "roofline_hbm": roof_hbm,
             "kernel_ms": {k: v[0] for k, v in prof.items()}, "kernel_launches": {k: v[1] for k, v in prof.items()},
+            "kernel_timing": "per-kernel-class CUDA events on the launching stream, over a second pass of the same "
+                             "steps right after the timed region (events between kernels would add gaps to it)",
             "gpu_launches": info["launches_per_step"] * args.steps,
             "levels": info["level_rows"],
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * n + 8 * args.e2e_inner,
                     "d2h_bytes_per_step": 16 * n, "cn_steps_per_call": args.e2e_inner,
                     "calls": args.e2e_calls},
             "clocks": clocks}
+    if tune:
+        line["config"]["autotune_ms_per_step"] = tune
     if alt:
         line["f64_path"] = alt
     if adj:

@@ -395,6 +395,34 @@ def autotune_batch(sizes, dx, dt, candidates=None, steps: int = 3, repeats: int 
     return m0, ml, times
 
 
+def autotune_plan(n, dx, dt, x_min, candidates=None, steps: int = 3, repeats: int = 2, **kw):
+    """Pick (block, level_block) for a single-system plan by timing `steps` CN steps
+    of each candidate in place (same cost for any state; a zero state here).
+    Returns (best_block, best_level_block, {candidate: ms per step})."""
+    import torch
+    if candidates is None:
+        candidates = [(m0, ml) for m0 in (8, 10, 12, 16) for ml in (8, 12)]
+    times = {}
+    psi = torch.zeros(int(n), dtype=torch.complex128, device="cuda")
+    for m0, ml in candidates:
+        p = Plan(n, dx, dt, x_min, block=m0, level_block=ml, **kw)
+        p.step(psi, 1, psi_out=psi)  # warm-up
+        best = float("inf")
+        for _ in range(repeats):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            p.step(psi, steps, psi_out=psi)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / steps)
+        p.check()
+        p.close()
+        times[(m0, ml)] = best
+    del psi
+    m0, ml = min(times, key=times.get)
+    return m0, ml, times
+
+
 def solve_tridiag_noalloc(b, a, c, d, x=None, arith=ARITH_F64, stream=None):
     """Solve T x = d without a plan and without allocating device memory inside
     the library (cn_solve_tridiag_noalloc), for callers that cannot allocate on

@@ -54,7 +54,7 @@ struct Engine {
     std::vector<SysGrid> grid;    // per system
     SysGrid* d_grid = nullptr;    // device copy (batches)
     double2* state = nullptr;     // ping-pong state (recompute mode)
-    void* keep = nullptr;         // 2 m P entries per system: d^ and pivot (store mode)
+    void* keep = nullptr;         // 2 m entries per level-0 block: d^ and pivot (store mode)
     void* tab = nullptr;          // bt0 table (compute type) or NULL
     int* status = nullptr;        // device status word
     CNParams cnp;
@@ -170,8 +170,10 @@ struct ProfScope {
 
 // --------------------------------------------------------------- hierarchy
 // Level l of system s has n rows cut into P = ceil((n-1)/m) blocks; its P + 1
-// joint lines are the rows of level l + 1, until a level has <= kBaseMax rows
-// (the RS stage).  Systems that reached their RS level have no rows below it.
+// joint lines are the rows of level l + 1, until a level has <= kCrMax rows,
+// which the RS stage solves in one CTA by cyclic reduction (explicit-depth plans: exactly
+// the requested levels, then the serial RS).  Systems that reached their RS
+// level have no rows below it.
 cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
     const int ns = (int)sizes.size();
     p->nsys = ns;
@@ -209,8 +211,8 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
             e.n = q.P > 0 ? q.P + 1 : 0;
             e.P = 0;
             if (e.n > 0) {
-                // explicit depth: reduce exactly nlev levels; else until <= kBaseMax rows
-                const bool base = nlev ? (l == nlev) : (e.n <= kBaseMax);
+                // explicit depth: reduce exactly nlev levels; else until the CR stage can take it
+                const bool base = nlev ? (l == nlev) : (e.n <= kCrMax);
                 if (base) p->base_level[s] = l;
                 else if (e.n < 3) return cudaErrorInvalidValue;  // too short to cut into blocks
                 else e.P = ceil_div(e.n - 1, L.m);
@@ -244,7 +246,7 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
         p->workspace_bytes += (int64_t)(kCplx * zc_entries);
         e = cudaMalloc(&p->zc, kCplx * zc_entries);
     }
-    if (e == cudaSuccess && !p->batched) {
+    if (e == cudaSuccess && !p->batched && !p->lvl_m.empty()) {
         const int64_t nb = p->lv[(size_t)p->base_level[0]].sys[0].n;
         if (nb > kBaseMax) {
             p->workspace_bytes += (int64_t)(kCplx * (size_t)nb);
@@ -313,6 +315,7 @@ void with_maps_grid(const Engine* p, F f) {
 // Shared memory of the substitutions: two complex values per block row and thread.
 size_t subst_smem(int m) { return 2 * (size_t)m * kThreads * kCplx; }
 size_t kept_smem(int m) { return (size_t)m * kTileStride * kCplx; }
+size_t cr_smem() { return 5 * (size_t)kCrMax * kCplx; }
 
 template <class R, class Src, class Map>
 cudaError_t launch_reduce(const Src& src, Map sys, Map next, int m, const LevelData& nextL, int* status,
@@ -345,6 +348,8 @@ cudaError_t set_smem_limits_map(int m0, int ml) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_substitute<R, LevelSource<R>, Map, ST>, a, (int)subst_smem(ml));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute<R, Map, Grid>, a, (int)subst_smem(m0));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute_kept<R, Map>, a, (int)kept_smem(m0));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr<R>, a, (int)cr_smem());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr_many<R>, a, (int)cr_smem());
     return e;
 }
 
@@ -373,15 +378,18 @@ cudaError_t solve_levels(Engine* p, cudaStream_t st) {
     {
         ProfScope ps(p, kProfBase, st);
         if (p->batched) {
-            k_base_many<R><<<(unsigned)ceil_div(p->nsys, 128), 128, 0, st>>>(
-                static_cast<const BaseSys<R>*>(p->d_base), p->nsys, p->status);
+            k_base_cr_many<R><<<(unsigned)p->nsys, kCrThreads, cr_smem(), st>>>(
+                static_cast<const BaseSys<R>*>(p->d_base), p->status);
         } else {
             const LevelData& B = p->lv[(size_t)p->base_level[0]];
-            if (p->base_cs)
-                k_base_serial<R><<<1, 32, 0, st>>>(level_source<R>(B).bind(B.sys[0]), x_of<R>(B),
-                                                   static_cast<typename Store<R>::T*>(p->base_cs), p->status);
+            const LevelSource<R> src = level_source<R>(B).bind(B.sys[0]);
+            if (p->lvl_m.empty())
+                k_base_cr<R><<<1, kCrThreads, cr_smem(), st>>>(src, x_of<R>(B), p->status);
+            else if (p->base_cs)
+                k_base_serial<R><<<1, 32, 0, st>>>(src, x_of<R>(B), static_cast<typename Store<R>::T*>(p->base_cs),
+                                                   p->status);
             else
-                k_base<R><<<1, 32, 0, st>>>(level_source<R>(B).bind(B.sys[0]), x_of<R>(B), p->status);
+                k_base<R><<<1, 32, 0, st>>>(src, x_of<R>(B), p->status);
         }
         e = cudaGetLastError();
     }
@@ -528,8 +536,8 @@ cn_status create_engine(Engine* p, const cn_desc* desc, const std::vector<int64_
     if (e == cudaErrorInvalidValue) return p->lvl_m.empty() ? CN_ERR_UNSUPPORTED : CN_ERR_INVALID_ARG;
     if (e != cudaSuccess) return alloc_status(e);
     const int64_t rows0 = p->lv[0].rows_total;
-    // keep: entries (2k) P + t and (2k+1) P + t for block rows k = 1..m-1 of each system
-    const size_t keep_entries = 2 * (size_t)p->lv[0].m * (size_t)p->lv[0].total;
+    // keep: 2 m entries per block, in chunks of 128 blocks (one per CTA of the level-0 grid)
+    const size_t keep_entries = 2 * (size_t)p->lv[0].m * (size_t)grid_for(p->lv[0].total) * kThreads;
     p->workspace_bytes += (int64_t)(recompute ? kCplx * rows0 : kCplx * keep_entries) + (int64_t)sizeof(int);
     if (recompute) e = cudaMalloc(&p->state, kCplx * (size_t)rows0);
     else e = cudaMalloc(&p->keep, kCplx * keep_entries);

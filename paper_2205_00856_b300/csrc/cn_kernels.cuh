@@ -456,11 +456,94 @@ __global__ void k_base(LevelSource<R> src, typename Store<R>::T* x, int* status)
     base_solve<R>(src, x, status);
 }
 
+// ------------------------------------------------------------------ RS stage: cyclic reduction
+// The last reduced system of the default hierarchy (<= kCrMax rows) is solved
+// inside one CTA by cyclic reduction, staged in shared memory.  Forward, for
+// strides s = 1, 2, 4, ...: every row i with i + 1 a multiple of 2s eliminates
+// its couplings to rows i - s and i + s with those rows' current equations,
+//   k1 = b_i / a_{i-s},  k2 = c_i / a_{i+s},
+//   a_i -= k1 c_{i-s} + k2 b_{i+s},  d_i -= k1 d_{i-s} + k2 d_{i+s},
+//   b_i  = -k1 b_{i-s},              c_i  = -k2 c_{i+s}
+// (rows outside 0..n-1 contribute nothing), leaving it coupled to i -+ 2s;
+// the rows it read are not updated at that stride, so the update is in place.
+// The last updated row (i = S - 1, S the first stride with 2S - 1 >= n) then
+// stands alone.  Backward, for s = S/2 .. 1: every row i = s - 1 + 2 s j solves
+// its equation, kept as it was when it stopped being updated, with the already
+// known x_{i-s} and x_{i+s}.  Work is O(n) with ~2 log2 n barrier-separated
+// steps.  Every elimination is a Schur complement of a matrix whose Hermitian
+// part is positive definite (T = I + iK, and the reduced systems inherit it),
+// so no pivot vanishes, as for the serial elimination.
+constexpr int kCrMax = 1024;      // rows
+constexpr int kCrThreads = 512;   // threads of the CTA
+
 template <class R>
-__global__ void k_base_many(const BaseSys<R>* sys, int nsys, int* status) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nsys) return;
-    base_solve<R>(sys[s].src, sys[s].x, status);
+__device__ __forceinline__ void cr_solve(const LevelSource<R>& src, typename Store<R>::T* x, int* status) {
+    typedef typename Store<R>::T ST;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ST* sb = reinterpret_cast<ST*>(smem_raw);
+    ST* sa = sb + kCrMax;
+    ST* sc = sa + kCrMax;
+    ST* sd = sc + kCrMax;
+    ST* sx = sd + kCrMax;
+    const int n = (int)src.n;
+    const int tid = threadIdx.x;
+    bool ok = true;
+    for (int i = tid; i < n; i += kCrThreads) {
+        const Row<R> r = src.template row<R>(i);
+        sstore(sb + i, r.b);
+        sstore(sa + i, r.a);
+        sstore(sc + i, r.c);
+        sstore(sd + i, r.d);
+    }
+    __syncthreads();
+    int s = 1;
+    for (; 2 * s - 1 < n; s <<= 1) {
+        for (int i = 2 * s * (tid + 1) - 1; i < n; i += 2 * s * kCrThreads) {
+            const cx<R> k1 = cmul(sload(sb + i), crcp(sload(sa + i - s), ok));
+            cx<R> a = csub(sload(sa + i), cmul(k1, sload(sc + i - s)));
+            cx<R> d = csub(sload(sd + i), cmul(k1, sload(sd + i - s)));
+            const cx<R> b = cneg(cmul(k1, sload(sb + i - s)));
+            cx<R> c = czero<R>();
+            if (i + s < n) {
+                const cx<R> k2 = cmul(sload(sc + i), crcp(sload(sa + i + s), ok));
+                a = csub(a, cmul(k2, sload(sb + i + s)));
+                d = csub(d, cmul(k2, sload(sd + i + s)));
+                c = cneg(cmul(k2, sload(sc + i + s)));
+            }
+            sstore(sa + i, a);
+            sstore(sb + i, b);
+            sstore(sc + i, c);
+            sstore(sd + i, d);
+        }
+        __syncthreads();
+    }
+    if (tid == 0) sstore(sx + s - 1, cmul(sload(sd + s - 1), crcp(sload(sa + s - 1), ok)));
+    __syncthreads();
+    for (s >>= 1; s >= 1; s >>= 1) {
+        for (int i = s - 1 + 2 * s * tid; i < n; i += 2 * s * kCrThreads) {
+            cx<R> y = sload(sd + i);
+            if (i - s >= 0) y = csub(y, cmul(sload(sb + i), sload(sx + i - s)));
+            if (i + s < n) y = csub(y, cmul(sload(sc + i), sload(sx + i + s)));
+            sstore(sx + i, cmul(y, crcp(sload(sa + i), ok)));
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += kCrThreads) x[i] = sx[i];
+    if (!ok) flag_error(status, kStatusNonfinite);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kCrThreads)
+k_base_cr(LevelSource<R> src, typename Store<R>::T* x, int* status) {
+    cr_solve<R>(src, x, status);
+}
+
+// one CTA per system
+template <class R>
+__global__ void __launch_bounds__(kCrThreads)
+k_base_cr_many(const BaseSys<R>* sys, int* status) {
+    const BaseSys<R> b = sys[blockIdx.x];
+    cr_solve<R>(b.src, b.x, status);
 }
 
 // ------------------------------------------------------------------ CN level 0
@@ -689,10 +772,18 @@ template <class R> struct CNRowStream {
 // half-step + RD/JD with RU/JU accumulated, on the scaled rows (b = c = -1):
 //   RD:  w_k = 1/(a~_k - w_{k-1}),  d_k += w_{k-1} d_{k-1},  b_k = w_{k-1} b_{k-1} (b_1 = -1)
 //   RU:  rho_{k-1} = w_k,  Q_k = Q_{k-1} w_k,  b_1 += Q_k b_k,  d_1 += Q_k d_k,  c_1 = -Q_{g-1}
-// With keep != NULL it also saves, for every interior row k of block t of a
-// system, d^ and the pivot inverse w at keep[(2k) P + t] and keep[(2k+1) P + t]
-// from the system's base 2 m blk_off (block-row major: a warp's 32 blocks touch
-// 32 consecutive entries): all the substitution needs (store mode).
+// With keep != NULL it also saves, for every interior row k of its block, d^
+// and the pivot inverse w: all the substitution needs (store mode).  Entries
+// are block-row major within each CTA (keep_base): row k of the block of
+// thread tid in CTA c sits at (c 2m + 2k + {0, 1}) 128 + tid, so a warp's 32
+// blocks touch 32 consecutive entries and each CTA's entries form one
+// contiguous 2 m 128-entry chunk.
+// First keep entry of this thread's block (the reduction and the store-mode
+// substitutions run on the same grid, so the CTA / thread pair names the block).
+__device__ __forceinline__ int64_t keep_base(int m) {
+    return (int64_t)blockIdx.x * (2 * (int64_t)m * kThreads) + threadIdx.x;
+}
+
 template <class R, class Map, class Grid>
 __global__ void __launch_bounds__(kThreads)
 k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, LevelRow<R>* out, LevelSlot<R>* out_slot,
@@ -714,7 +805,7 @@ k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, LevelRow<R>* out, Le
         P = e.P;
         t = g - e.blk_off;
         outs = out + next.at(si).row_off;
-        ST* keep = keep0 ? keep0 + 2 * (int64_t)m * e.blk_off : nullptr;
+        ST* keep = keep0 ? keep0 + keep_base(m) : nullptr;
         const int64_t J0 = joint_line(t, P, m, n);
         const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
         CNRowStream<R> rs;
@@ -724,35 +815,41 @@ k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, LevelRow<R>* out, Le
         rs.next(a, d);  // row 1
         cx<R> w = crcp(a, ok);
         if (keep) {
-            sstore(keep + 2 * P + t, d);
-            sstore(keep + 3 * P + t, w);
+            sstore(keep + 2 * kThreads, d);
+            sstore(keep + 3 * kThreads, w);
         }
+        // With b = c = -1 the RD fill-in column is a product of the same pivots
+        // as RU's Q:  b_k^RD = -prod_{i<k} w_i = -w_1 Q_{k-1}  (k >= 2, b_1 = -1),
+        // so RU's sum on row 1 is  b_1 = -1 - w_1 S,  S = sum_{k>=2} Q_k Q_{k-1},
+        // and no b^RD chain is carried.
         const cx<R> w1 = w;
-        cx<R> bRD = cfrom<R>(-1.0, 0.0), dRD = d;
-        cx<R> Q = cfrom<R>(1.0, 0.0);
-        cx<R> nb = bRD, nd = dRD;
+        const cx<R> one = cfrom<R>(1.0, 0.0);
+        cx<R> dRD = d;
+        cx<R> Q = one, S = czero<R>();
+        cx<R> nd = dRD;
         for (int k = 2; k < gap; ++k) {
             rs.next(a, d);
-            bRD = cmul(w, bRD);
             dRD = cfma(d, w, dRD);
             const cx<R> wk = crcp(csub(a, w), ok);
             if (keep) {
-                sstore(keep + (2 * k) * P + t, d);
-                sstore(keep + (2 * k + 1) * P + t, wk);
+                sstore(keep + (2 * k) * kThreads, d);
+                sstore(keep + (2 * k + 1) * kThreads, wk);
             }
-            Q = cmul(Q, wk);
-            nb = cfma(nb, Q, bRD);
-            nd = cfma(nd, Q, dRD);
+            const cx<R> Qk = cmul(Q, wk);
+            S = cfma(S, Qk, Q);
+            nd = cfma(nd, Qk, dRD);
+            Q = Qk;
             w = wk;
         }
-        // JD on row J_{t+1}: r = w_{g-1};  b = r b_{g-1};  a += -r;  d += r d_{g-1}
-        jd.b = cmul(w, bRD);
+        // JD on row J_{t+1}: r = w_{g-1};  b = r b_{g-1} = -w_1 Q_{g-1};  a += -r;  d += r d_{g-1}
+        // JU on row J_t: r = w_1;  c = -w_1 Q_{g-1};  a += w_1 b_1 = -w_1 (1 + w_1 S);  d += w_1 d_1
+        const cx<R> wQ = cneg(cmul(w1, Q));
+        jd.b = wQ;
         jd.a = cneg(w);
         jd.d = cmul(w, dRD);
         if (t == P - 1) rs.next(Ag, Dg);
-        // JU on row J_t: r = w_1;  c = -w_1 Q_{g-1};  a += w_1 b_1;  d += w_1 d_1
-        JUc = cneg(cmul(w1, Q));
-        JUa = cmul(w1, nb);
+        JUc = wQ;
+        JUa = cneg(cmul(w1, cfma(one, w1, S)));
         JUd = cmul(w1, nd);
     }
     write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, outs, out_slot);
@@ -845,7 +942,7 @@ k_cn_substitute_kept(Map sys, Map next, int m, const typename Store<R>::T* keep0
         const int si = sys.find(g);
         const LvlSys& e = sys.at(si);
         const int64_t n = e.n, P = e.P, t = g - e.blk_off;
-        const ST* keep = keep0 + 2 * (int64_t)m * e.blk_off;
+        const ST* keep = keep0 + keep_base(m);
         const ST* x_next = x_next0 + next.at(si).row_off;
         double2* x = x0 + e.row_off;
         const int64_t J0 = joint_line(t, P, m, n);
@@ -853,12 +950,12 @@ k_cn_substitute_kept(Map sys, Map next, int m, const typename Store<R>::T* keep0
         const cx<R> xL = sload(x_next + t);
         const cx<R> xR = sload(x_next + t + 1);
         cx<R> zp = xL;
-        cx<R> dn = sload(keep + 2 * P + t), wn = sload(keep + 3 * P + t);
+        cx<R> dn = sload(keep + 2 * kThreads), wn = sload(keep + 3 * kThreads);
         for (int k = 1; k < gap; ++k) {
             const cx<R> d = dn, w = wn;
             if (k + 1 < gap) {  // next row's values, issued before this row's arithmetic
-                dn = sload(keep + (2 * k + 2) * P + t);
-                wn = sload(keep + (2 * k + 3) * P + t);
+                dn = sload(keep + (2 * k + 2) * kThreads);
+                wn = sload(keep + (2 * k + 3) * kThreads);
             }
             cx<R> rhs = cadd(d, zp);
             if (k == gap - 1) rhs = cadd(rhs, xR);
@@ -869,13 +966,13 @@ k_cn_substitute_kept(Map sys, Map next, int m, const typename Store<R>::T* keep0
         if (regular) {
             sstore(zs + tid, xL);  // row 0 of the block: its top joint line
             for (int k = gap - 2; k >= 1; --k) {
-                y = cfma(sload(zs + k * kTileStride + tid), sload(keep + (2 * k + 1) * P + t), y);
+                y = cfma(sload(zs + k * kTileStride + tid), sload(keep + (2 * k + 1) * kThreads), y);
                 sstore(zs + k * kTileStride + tid, y);
             }
         } else {
             store128(x + J0 + gap - 1, y);
             for (int k = gap - 2; k >= 1; --k) {
-                y = cfma(sload(zs + k * kTileStride + tid), sload(keep + (2 * k + 1) * P + t), y);
+                y = cfma(sload(zs + k * kTileStride + tid), sload(keep + (2 * k + 1) * kThreads), y);
                 store128(x + J0 + k, y);
             }
             store128(x + J0, xL);
@@ -911,7 +1008,7 @@ k_cn_substitute_kept_gmem(Map sys, Map next, int m, const typename Store<R>::T* 
     const int si = sys.find(g);
     const LvlSys& e = sys.at(si);
     const int64_t n = e.n, P = e.P, t = g - e.blk_off;
-    const ST* keep = keep0 + 2 * (int64_t)m * e.blk_off;
+    const ST* keep = keep0 + keep_base(m);
     const ST* x_next = x_next0 + next.at(si).row_off;
     double2* x = x0 + e.row_off;
     const int64_t J0 = joint_line(t, P, m, n);
@@ -921,15 +1018,15 @@ k_cn_substitute_kept_gmem(Map sys, Map next, int m, const typename Store<R>::T* 
     const cx<R> xR = sload(x_next + t + 1);
     cx<R> zp = xL;
     for (int k = 1; k < gap; ++k) {
-        cx<R> rhs = cadd(sload(keep + (2 * k) * P + t), zp);
+        cx<R> rhs = cadd(sload(keep + (2 * k) * kThreads), zp);
         if (k == gap - 1) rhs = cadd(rhs, xR);
-        zp = cmul(rhs, sload(keep + (2 * k + 1) * P + t));
+        zp = cmul(rhs, sload(keep + (2 * k + 1) * kThreads));
         sstore(zs + k, zp);
     }
     cx<R> y = zp;
     store128(x + J0 + gap - 1, y);
     for (int k = gap - 2; k >= 1; --k) {
-        y = cfma(sload(zs + k), sload(keep + (2 * k + 1) * P + t), y);
+        y = cfma(sload(zs + k), sload(keep + (2 * k + 1) * kThreads), y);
         store128(x + J0 + k, y);
     }
     store128(x + J0, xL);
