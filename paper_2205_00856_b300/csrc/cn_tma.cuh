@@ -1,0 +1,58 @@
+// cn_tma.cuh -- bulk asynchronous copies global -> shared (TMA, cp.async.bulk)
+// completed on a shared-memory mbarrier, with a bounded wait.
+//
+// One thread initialises the barrier, announces the byte count the phase will
+// receive (arrive.expect_tx) and issues the copies; every thread then waits on
+// phase 0.  A copy must start and end on 16-byte boundaries (both addresses and
+// the size), which the callers' layouts guarantee.
+#pragma once
+#include <cstdint>
+
+namespace cnb {
+
+constexpr int kStatusTimeout = 5;        // cn_status CN_ERR_TIMEOUT
+constexpr int kWaitSpinLimit = 1 << 24;  // polls of a barrier (with a 64 ns back-off: about a second)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    // make the initialised barrier visible to the async proxy that completes it
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// bytes: multiple of 16; dst and src 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for phase `parity` of the barrier, giving up after kWaitSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (int i = 0; i < kWaitSpinLimit; ++i) {
+        if (mbar_test_wait(bar, parity)) return true;
+        if (i >= 32) __nanosleep(64);
+    }
+    return false;
+}
+
+}  // namespace cnb
