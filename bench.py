@@ -40,10 +40,9 @@ WORKLOAD_STEPS = 1000  # length of the benchmarked propagation (field samples)
 
 # Algorithmic flops per grid row of the two level-0 kernels (soft-Coulomb
 # potential regenerated on the fly, store mode), FMA = 2 flops, a reciprocal or
-# reciprocal square root = 1; m = rows per level-0 block.  Derivation (operation
-# counts of every step) in DESIGN.md, "Algorithmic work per unknown".
-#   FP64:          reduce 65 + 64/m,   substitute 16
-#   double-float:  reduce 604 + 600/m, substitute 150   (binary32 flops)
+# reciprocal square root = 1; m = rows per level-0 block (flops_per_row):
+#   FP64:          reduce 59 - 30/m,   substitute 16 - 14/m
+#   double-float:  reduce 548 - 261/m, substitute 150 - 128/m   (binary32 flops)
 def flops_per_row(kernel: str, arith: str, m: int) -> float:
     """Flops per grid row of the level-0 kernels (FMA = 2; binary32 flops of the
     double-float formulation, binary64 flops of the FP64 one).  A block of m rows
@@ -60,6 +59,22 @@ STEP_BYTES_PER_ROW = 32.0
 FP64_NOMINAL_TFLOPS = 1.25
 # FP32 issue peak: 148 SMs x 128 lanes x 2 flops x 2.032 GHz.
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def max_over_ranks(dist, value: float, device) -> float:
+    """The largest value over all ranks, returned on every rank (the value itself
+    without a process group): the job's time is its slowest rank's."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (ms * 1e-3)
 
 
 def env_int(k, d):
@@ -257,7 +272,7 @@ def time_steps(torch, plan, psi0, E, steps, warmup, dist, dev, sample_clocks):
     torch.cuda.synchronize()
     if clk:
         clk.__exit__()
-    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(dist, ev0.elapsed_time(ev1), dev)
     # kernel breakdown: same steps, per-kernel-class events on the same stream
     plan.profile(True)
     plan.profile_read()
@@ -268,9 +283,6 @@ def time_steps(torch, plan, psi0, E, steps, warmup, dist, dev, sample_clocks):
     prof = plan.profile_read()
     plan.check()
     if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     return ms, prof, (clk.summary() if clk else None)
 
@@ -488,7 +500,7 @@ def main():
     plan = make_plan(cnb, cfg, args, arith)
     info = plan.info()
     ms, prof, clocks = time_steps(torch, plan, psi0, E, args.steps, args.warmup, dist, dev, rank == 0)
-    value = n * args.steps * world / (ms * 1e-3)
+    value = job_rate(n * args.steps, world, ms)
 
     # end to end through the C ABI with host buffers: H2D of psi and E, inner
     # CN steps, D2H of psi, every call
@@ -502,12 +514,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.e2e_calls):
         plan.step_host(psi_h, args.e2e_inner, E_mid=E_h, psi_out=out_h)
-    e2e_s = max(time.perf_counter() - t0, 1e-9)
-    if dist:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = n * args.e2e_inner * args.e2e_calls * world / e2e_s
+    e2e_s = max_over_ranks(dist, max(time.perf_counter() - t0, 1e-9), dev)
+    e2e_val = job_rate(n * args.e2e_inner * args.e2e_calls, world, e2e_s * 1e3)
     plan.close()
 
     alt = None
