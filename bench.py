@@ -444,6 +444,63 @@ def batched_bench(torch, cnb, args, dev):
             "per_system_steps_timed": reps}
 
 
+def largest_bench(torch, cnb, args, dev):
+    """The largest single system: N = 2^32 (64 GiB complex128 state), dx = 0.05,
+    dt = 0.01, soft-Coulomb atom in the field, 50 steps, coefficients regenerated
+    on the fly, blocks from the autotuner.  One JSON line of its own."""
+    cfg = W.largest_config()
+    n, dx, dt, nst = cfg["n"], cfg["dx"], cfg["dt"], cfg["nsteps"]
+    arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
+    kw = dict(pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith)
+    m0, ml, tt = cnb.autotune_plan(n, dx, dt, cfg["x_min"], candidates=[(8, 8), (12, 12), (16, 12)], steps=2,
+                                   repeats=1, **kw)
+    torch.cuda.empty_cache()
+    nw = 1 << 20
+    j0 = n // 2 - nw // 2
+    psi = torch.zeros(n, dtype=torch.complex128, device=dev)
+    psi[j0:j0 + nw] = torch.from_numpy(W.gaussian(nw, dx, -(nw // 2) * dx, 0.0, 1.0, 0.0)).to(dev)
+    E = torch.from_numpy(W.field_midpoints(nst + args.warmup, dt)).to(dev)
+    plan = cnb.Plan(n, dx, dt, cfg["x_min"], block=m0, level_block=ml, **kw)
+    info = plan.info()
+    stream = torch.cuda.current_stream()
+    for k in range(args.warmup):
+        plan.step(psi, 1, E_mid=E[k:k + 1], psi_out=psi, stream=stream)
+    torch.cuda.synchronize()
+    uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    clk = ClockSampler(uuid)
+    clk.__enter__()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(nst):
+        plan.step(psi, 1, E_mid=E[args.warmup + k:args.warmup + k + 1], psi_out=psi, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk.__exit__()
+    ms = ev0.elapsed_time(ev1)
+    plan.profile(True)
+    plan.profile_read()
+    for k in range(3):
+        plan.step(psi, 1, E_mid=E[k:k + 1], psi_out=psi, stream=stream)
+    prof = plan.profile_read()
+    plan.check()
+    plan.close()
+    value = job_rate(n * nst, 1, ms)
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    hbm = STEP_BYTES_PER_ROW * value / 1e9
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": nst, "warmup": args.warmup,
+            "ms_per_step": ms / nst, "higher_is_better": True, "dtype": args.arith, "data": "synthetic",
+            "config": {"workload": "soft_coulomb_laser_1d_cn_largest", "n": n, "dx": dx, "dt": dt,
+                       "block": m0, "level_block": ml, "autotune_ms_per_step": {f"{a}x{c}": t for (a, c), t in tt.items()},
+                       "coefficients": "regenerated from V(x) and E(t) every step",
+                       "state": "64 GiB complex128, in place (store mode)"},
+            "levels": info["level_rows"], "workspace_bytes": info["workspace_bytes"],
+            "roofline": roofline(prof, n, args.arith, peaks, m0),
+            "roofline_hbm": {"bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": hbm / hbm_peak, "basis": "32 B per unknown-step (read psi, write psi')"},
+            "kernel_ms_3_steps": {k: v[0] for k, v in prof.items()}, "clocks": clk.summary()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -466,6 +523,8 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--batched-baseline-steps", type=int, default=3,
                     help="steps of the one-plan-per-system baseline timed")
+    ap.add_argument("--largest", action="store_true",
+                    help="instead: the largest single system, N = 2^32, dx = 0.05, dt = 0.01, 50 steps")
     ap.add_argument("--adjoint-steps", type=int, default=2000,
                     help="gradient run (N=2^20, 500 controls): steps for the adjoint/forward ratio (0: skip)")
     args = ap.parse_args()
@@ -483,6 +542,13 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+
+    if args.largest:
+        if rank == 0:
+            print(json.dumps(largest_bench(torch, cnb, args, dev)), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return 0
 
     cfg = W.soft_coulomb_config(n=args.n)
     n = cfg["n"]

@@ -1,0 +1,77 @@
+"""The largest single system: N = 2^32 points (a 64 GiB complex128 state), dx = 0.05,
+dt = 0.01, 50 steps of the soft-Coulomb atom in the laser field, coefficients
+regenerated on the fly, double-float arithmetic, blocks of 12 rows.
+
+The oracle cannot hold this grid, so parity is checked by properties that hold at
+any size plus a windowed oracle run:
+  - the norm, which a CN step conserves exactly for Hermitian H (rel <= 1e-11 after
+    50 steps, as the 1000-step norm test at 2^20);
+  - the central 2^20 points against the oracle run on that window alone.  The state
+    occupies ~1600 points around the origin, and the entries of T^{-1} shrink by
+    |z| ~ 0.48 per point (root of b z^2 + a z + b with a = 1 + 2i, b = -i here), so
+    over the 2^19 points to the window's own Dirichlet ends the difference is far
+    below rounding: rel L2 <= 1e-11, as the other parity tests;
+  - outside the window the state stays zero to rounding.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2205_00856_b300 as cnb  # noqa: E402
+
+DEV = torch.device("cuda:0")
+NEED_BYTES = 250e9  # state 69 GB + keep 137 GB + reduced levels 31 GB + headroom
+
+
+def sq_norm(t, chunk=1 << 28):
+    s = 0.0
+    for i in range(0, t.numel(), chunk):
+        v = torch.view_as_real(t[i:i + chunk])
+        s += float(torch.sum(v * v).item())
+    return s
+
+
+def rel(x, y):
+    return float(np.linalg.norm(x - y) / np.linalg.norm(y))
+
+
+def test_largest_single_system_n2p32():
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if free < NEED_BYTES:
+        pytest.skip(f"needs ~{NEED_BYTES / 1e9:.0f} GB of free device memory, {free / 1e9:.0f} GB free")
+    cfg = W.largest_config()
+    N, dx, dt, nsteps = cfg["n"], cfg["dx"], cfg["dt"], cfg["nsteps"]
+    nw = 1 << 20
+    j0 = N // 2 - nw // 2
+    x_min_w = -(nw // 2) * dx  # x at grid point j0 (the grid's origin is j = N/2)
+    psi0_w = W.gaussian(nw, dx, x_min_w, 0.0, 1.0, 0.0)
+    E = W.field_midpoints(nsteps, dt)
+    psi = torch.zeros(N, dtype=torch.complex128, device=DEV)
+    psi[j0:j0 + nw] = torch.from_numpy(psi0_w).to(DEV)
+    n0 = sq_norm(psi)
+    plan = cnb.Plan(N, dx, dt, cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=cnb.ARITH_DF64,
+                    block=12, level_block=12)
+    try:
+        plan.step(psi, nsteps, E_mid=torch.from_numpy(E).to(DEV), psi_out=psi)
+        plan.check()
+    finally:
+        plan.close()
+    n1 = sq_norm(psi)
+    assert abs(n1 / n0 - 1.0) <= 1e-11
+    win = psi[j0:j0 + nw].cpu().numpy()
+    outside = sq_norm(psi[:j0]) + sq_norm(psi[j0 + nw:])
+    del psi
+    torch.cuda.empty_cache()
+    prob = oracle.Problem(nw, dx, dt, x_min_w, pot=oracle.POT_SOFTCOULOMB, soft_s=2.0)
+    ref = oracle.cn_run(prob, psi0_w, nsteps, E_mid=E)
+    assert rel(win, ref) <= 1e-11
+    assert outside <= 1e-20 * n1
