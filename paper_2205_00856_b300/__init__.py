@@ -401,7 +401,7 @@ def autotune_plan(n, dx, dt, x_min, candidates=None, steps: int = 3, repeats: in
     Returns (best_block, best_level_block, {candidate: ms per step})."""
     import torch
     if candidates is None:
-        candidates = [(m0, ml) for m0 in (8, 10, 12, 16) for ml in (8, 12)]
+        candidates = [(m0, ml) for m0 in (8, 10, 12, 16) for ml in (8, 12, 16, 24)]
     times = {}
     psi = torch.zeros(int(n), dtype=torch.complex128, device="cuda")
     for m0, ml in candidates:

@@ -785,8 +785,16 @@ __device__ __forceinline__ int64_t keep_base(int m) {
     return (int64_t)blockIdx.x * (2 * (int64_t)m * kThreads) + threadIdx.x;
 }
 
+// CTAs per SM the level-0 reduction is compiled for: the double-float single-
+// system kernel fits 6 (80 registers, no spills), which keeps its FMA pipe
+// fed better than 5; the other instantiations would spill at 6 and get 5 (the
+// FP64 batch kernel 4).
+template <class R, class Map> struct ReduceOccupancy { static constexpr int min_blocks = 5; };
+template <> struct ReduceOccupancy<df, OneSys> { static constexpr int min_blocks = 6; };
+template <> struct ReduceOccupancy<double, ManySys> { static constexpr int min_blocks = 4; };
+
 template <class R, class Map, class Grid>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, ReduceOccupancy<R, Map>::min_blocks)
 k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, LevelRow<R>* out, LevelSlot<R>* out_slot,
             typename Store<R>::T* keep0, int* status) {
     typedef typename Store<R>::T ST;
