@@ -33,7 +33,8 @@ struct LevelData {
     int64_t rows_total = 0;   // rows of all systems present at this level
     std::vector<LvlSys> sys;  // one entry per system
     LvlSys* d_sys = nullptr;  // device copy (batches)
-    void* rows = nullptr;     // LevelRow<R>[rows_total] (levels >= 1)
+    int64_t L = 0;            // entries per plane (levels >= 1): sum of the systems' slots
+    void* rows = nullptr;     // planes b, a, c, d of L entries each (levels >= 1)
     void* slot = nullptr;     // LevelSlot<R>[CTAs of the level below + 1]
     void* x = nullptr;        // Store<R>::T[rows_total]: solution (levels >= 1)
 };
@@ -185,11 +186,11 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
         int64_t roff = 0, boff = 0;
         for (int s = 0; s < ns; ++s) {
             LvlSys& e = L0.sys[s];
+            e = LvlSys{};
             e.n = sizes[s];
             e.P = ceil_div(e.n - 1, L0.m);
             e.row_off = roff;
             e.blk_off = boff;
-            e.prod_blk_off = 0;
             roff += e.n;
             boff += e.P;
         }
@@ -204,10 +205,11 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
         LevelData L;
         L.m = nlev ? (l < nlev ? p->lvl_m[(size_t)l] : 0) : p->desc.level_block;
         L.sys.resize(ns);
-        int64_t roff = 0, boff = 0;
+        int64_t roff = 0, boff = 0, soff = 0;
         for (int s = 0; s < ns; ++s) {
             LvlSys& e = L.sys[s];
             const LvlSys& q = p->lv[(size_t)l - 1].sys[s];
+            e = LvlSys{};
             e.n = q.P > 0 ? q.P + 1 : 0;
             e.P = 0;
             if (e.n > 0) {
@@ -220,11 +222,23 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
             e.row_off = roff;
             e.blk_off = boff;
             e.prod_blk_off = q.blk_off;
+            // plane layout for the kernels that read this level (see LvlSys)
+            e.slot_off = soff;
+            if (e.P > 0) {
+                e.stride = e.P + 1;
+                const int64_t excess = e.n - 1 - 2 * e.P;
+                e.tc = excess > 0 ? ceil_div(excess, L.m - 2) : 0;
+                e.Jtc = joint_line(e.tc, e.P, L.m, e.n);
+                soff += (int64_t)L.m * (e.P + 1);
+            } else {
+                soff += e.n;
+            }
             roff += e.n;
             boff += e.P;
         }
         L.rows_total = roff;
         L.total = boff;
+        L.L = soff;
         p->lv.push_back(std::move(L));
         if (boff == 0) break;
     }
@@ -232,8 +246,8 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
     for (size_t l = 1; l < p->lv.size() && e == cudaSuccess; ++l) {
         LevelData& L = p->lv[l];
         const size_t nslot = grid_for(p->lv[l - 1].total) + 1;
-        p->workspace_bytes += (int64_t)(5 * kCplx * L.rows_total + 3 * kCplx * nslot);
-        e = cudaMalloc(&L.rows, 4 * kCplx * (size_t)L.rows_total);
+        p->workspace_bytes += (int64_t)(4 * kCplx * L.L + kCplx * L.rows_total + 3 * kCplx * nslot);
+        e = cudaMalloc(&L.rows, 4 * kCplx * (size_t)std::max<int64_t>(L.L, 1));
         if (e == cudaSuccess) e = cudaMalloc(&L.slot, 3 * kCplx * nslot);
         if (e == cudaSuccess) e = cudaMalloc(&L.x, kCplx * (size_t)L.rows_total);
         if (e == cudaSuccess) e = cudaMemset(L.slot, 0, 3 * kCplx * nslot);
@@ -265,16 +279,21 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
     return e;
 }
 
-template <class R> LevelRow<R>* rows_of(const LevelData& L) { return static_cast<LevelRow<R>*>(L.rows); }
+template <class R> LevelPlanes<R> planes_of(const LevelData& L) {
+    return LevelPlanes<R>{static_cast<typename Store<R>::T*>(L.rows), L.L};
+}
 template <class R> LevelSlot<R>* slot_of(const LevelData& L) { return static_cast<LevelSlot<R>*>(L.slot); }
 template <class R> typename Store<R>::T* x_of(const LevelData& L) { return static_cast<typename Store<R>::T*>(L.x); }
 
 template <class R> LevelSource<R> level_source(const LevelData& L) {
+    const LevelPlanes<R> pl = planes_of<R>(L);
     LevelSource<R> s;
-    s.rows = rows_of<R>(L);
+    s.b = pl.p;
+    s.L = pl.L;
     s.slot = slot_of<R>(L);
     s.n = 0;
     s.prod = 0;
+    s.stride = 0;
     return s;
 }
 
@@ -325,7 +344,7 @@ template <class R, class Src, class Map>
 cudaError_t launch_reduce(const Src& src, Map sys, Map next, int m, const LevelData& nextL, int* status,
                           int64_t total, cudaStream_t st) {
     if (total == 0) return cudaSuccess;
-    k_reduce<R, Src, Map><<<grid_for(total), kThreads, 0, st>>>(src, sys, next, m, rows_of<R>(nextL),
+    k_reduce<R, Src, Map><<<grid_for(total), kThreads, 0, st>>>(src, sys, next, m, nextL.m, planes_of<R>(nextL),
                                                                 slot_of<R>(nextL), status);
     return cudaGetLastError();
 }
@@ -440,8 +459,8 @@ cudaError_t cn_solve(Engine* p, const CNStep& s, double2* x, cudaStream_t st) {
     {
         ProfScope ps(p, kProfReduce0, st);
         with_maps_grid(p, [&](auto a, auto b, auto gr) {
-            k_cn_reduce<R><<<grid, kThreads, 0, st>>>(s, a, b, gr, L0.m, rows_of<R>(L1), slot_of<R>(L1), keep,
-                                                      p->status);
+            k_cn_reduce<R><<<grid, kThreads, 0, st>>>(s, a, b, gr, L0.m, L1.m, planes_of<R>(L1), slot_of<R>(L1),
+                                                      keep, p->status);
         });
         e = cudaGetLastError();
     }

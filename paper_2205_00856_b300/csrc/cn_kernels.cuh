@@ -71,9 +71,34 @@ __device__ __forceinline__ void flag_error(int* status, int code) {
 // global index of its first block at the level that produced these rows (for
 // the CTA slot of Sec. 4.1.3's second joint-line contribution).  A thread maps
 // its global block index g to (s, t) by binary search over the block offsets.
+//
+// Rows of a reduced level are stored for the kernels that read them (RowLayout):
+// four planes b, a, c, d, and in each the row k of block t of a system that is
+// reduced at this level sits at slot_off + k (P + 1) + t, so the k-th rows of
+// consecutive blocks (consecutive threads) are consecutive entries: every
+// row load of a warp is one contiguous 512-byte access.  A system solved by the
+// RS stage at this level keeps row order (stride 0: row r at slot_off + r).
 struct LvlSys {
     int64_t n, P, row_off, blk_off, prod_blk_off;
+    int64_t slot_off;  // first entry of the system in the level's planes
+    int64_t stride;    // P + 1, or 0 for row order
+    int64_t tc, Jtc;   // first block of gap 2 (joint_line(t) = n - 1 - 2 (P - t) from it) and its joint line
 };
+
+// Plane position of row r (the producer's view: block and row within it from r).
+__host__ __device__ __forceinline__ int64_t row_slot(const LvlSys& e, int m, int64_t r) {
+    if (e.stride == 0) return r;
+    int64_t t, k;
+    if (r < e.Jtc) {
+        t = r / m;
+        k = r - t * m;
+    } else {
+        const int64_t d = r - e.Jtc;
+        t = e.tc + (d >> 1);
+        k = d & 1;
+    }
+    return k * e.stride + t;
+}
 
 // One system, its entry held by value in the kernel parameters.
 struct OneSys {
@@ -103,9 +128,11 @@ struct ManySys {
 };
 
 // ------------------------------------------------------------------ reduced rows
-// Row {b, a, c, d} of a reduced system (levels >= 1), stored in the compute type.
-template <class R> struct LevelRow {
-    typename Store<R>::T b, a, c, d;
+// The four planes of a reduced level (compute type, 16 B per complex): b at p,
+// a at p + L, c at p + 2L, d at p + 3L.
+template <class R> struct LevelPlanes {
+    typename Store<R>::T* p;
+    int64_t L;
 };
 template <class R> struct LevelSlot {
     typename Store<R>::T b, a, d;
@@ -124,8 +151,9 @@ struct ArraySource {
     const double2 *b, *a, *c, *d;
     int64_t n;
     __device__ __forceinline__ ArraySource bind(const LvlSys&) const { return *this; }
+    // row i = row k of block t (the arrays are in row order)
     template <class R>
-    __device__ __forceinline__ Row<R> row(int64_t i) const {
+    __device__ __forceinline__ Row<R> row(int64_t, int64_t, int64_t i) const {
         Row<R> r;
         r.b = (i > 0) ? load128<R>(b + i) : czero<R>();
         r.a = load128<R>(a + i);
@@ -135,29 +163,34 @@ struct ArraySource {
     }
 };
 
-// Reduced systems of a level >= 1 (all systems' rows concatenated), plus the
+// Reduced systems of a level >= 1 (all systems' planes concatenated), plus the
 // contribution of the previous CTA's last block to the rows whose producing
 // block was the first thread of a CTA (slot, indexed by that CTA).
 template <class R> struct LevelSource {
-    const LevelRow<R>* rows;  // row 0 of the bound system
+    typedef typename Store<R>::T ST;
+    const ST* b;              // b plane at the bound system's slot_off; a, c, d follow at L apart
+    int64_t L;
     const LevelSlot<R>* slot;
     int64_t n;                // rows of the bound system
     int64_t prod;             // global block index that produced row 0 of the bound system
+    int64_t stride;           // layout of the bound system (LvlSys)
     __host__ __device__ __forceinline__ LevelSource bind(const LvlSys& e) const {
         LevelSource r = *this;
-        r.rows = rows + e.row_off;
+        r.b = b + e.slot_off;
         r.n = e.n;
         r.prod = e.prod_blk_off;
+        r.stride = e.stride;
         return r;
     }
+    // row i = row k of block t
     template <class RR>
-    __device__ __forceinline__ Row<R> row(int64_t i) const {
-        const LevelRow<R>* p = rows + i;
+    __device__ __forceinline__ Row<R> row(int64_t t, int64_t k, int64_t i) const {
+        const ST* q = b + (stride ? k * stride + t : i);
         Row<R> r;
-        r.b = sload(&p->b);
-        r.a = sload(&p->a);
-        r.c = sload(&p->c);
-        r.d = sload(&p->d);
+        r.b = sload(q);
+        r.a = sload(q + L);
+        r.c = sload(q + 2 * L);
+        r.d = sload(q + 3 * L);
         const int64_t g = prod + i;
         if (i > 0 && i < n - 1 && (g % kThreads) == 0) {
             const LevelSlot<R>* s = slot + g / kThreads;
@@ -166,6 +199,32 @@ template <class R> struct LevelSource {
             r.d = cadd(r.d, sload(&s->d));
         }
         return r;
+    }
+    // row i of a system kept in row order (the RS stage's level)
+    template <class RR>
+    __device__ __forceinline__ Row<R> row_at(int64_t i) const { return row<RR>(0, 0, i); }
+};
+
+// Where a block writes the rows of the next level: that level's planes bound to
+// the system, with the system's layout there and the next level's block size.
+template <class R> struct RowSink {
+    typedef typename Store<R>::T ST;
+    ST* b;      // b plane at the system's slot_off; a, c, d follow at L apart
+    int64_t L;
+    LvlSys e;   // layout fields of the system at the next level (stride, tc, Jtc)
+    int m;
+    __device__ __forceinline__ RowSink(LevelPlanes<R> pl, const LvlSys& en, int m_next)
+        : b(pl.p + en.slot_off), L(pl.L), m(m_next) {
+        e.stride = en.stride;
+        e.tc = en.tc;
+        e.Jtc = en.Jtc;
+    }
+    __device__ __forceinline__ void put(int64_t r, cx<R> vb, cx<R> va, cx<R> vc, cx<R> vd) const {
+        ST* q = b + row_slot(e, m, r);
+        sstore(q, vb);
+        sstore(q + L, va);
+        sstore(q + 2 * L, vc);
+        sstore(q + 3 * L, vd);
     }
 };
 
@@ -177,35 +236,23 @@ template <class R> struct LevelSource {
 template <class R>
 __device__ __forceinline__ void write_reduced_row(bool active, int64_t t, int64_t P, JDPart<R> jd, cx<R> A0, cx<R> D0,
                                                   cx<R> JUa, cx<R> JUc, cx<R> JUd, cx<R> Ag, cx<R> Dg,
-                                                  LevelRow<R>* out, LevelSlot<R>* out_slot) {
+                                                  const RowSink<R>& out, LevelSlot<R>* out_slot) {
     __shared__ JDPart<R> xch[kThreads];
     const int tid = threadIdx.x;
     xch[tid] = jd;
     __syncthreads();
     if (!active) return;
-    LevelRow<R> row;
     if (tid > 0 && t > 0) {
-        JDPart<R> pj = xch[tid - 1];
-        sstore(&row.b, pj.b);
+        const JDPart<R> pj = xch[tid - 1];
         // (A0 + JU) + JD: the order the slot path below takes too, so a row's
         // value does not depend on where CTA boundaries fall
-        sstore(&row.a, cadd(cadd(A0, JUa), pj.a));
-        sstore(&row.d, cadd(cadd(D0, JUd), pj.d));
+        out.put(t, pj.b, cadd(cadd(A0, JUa), pj.a), JUc, cadd(cadd(D0, JUd), pj.d));
     } else {
         // t == 0: no block above; otherwise the previous CTA's slot completes the row
-        sstore(&row.b, czero<R>());
-        sstore(&row.a, cadd(A0, JUa));
-        sstore(&row.d, cadd(D0, JUd));
+        out.put(t, czero<R>(), cadd(A0, JUa), JUc, cadd(D0, JUd));
     }
-    sstore(&row.c, JUc);
-    out[t] = row;
     if (t == P - 1) {
-        LevelRow<R> last;
-        sstore(&last.b, jd.b);
-        sstore(&last.a, cadd(Ag, jd.a));
-        sstore(&last.c, czero<R>());
-        sstore(&last.d, cadd(Dg, jd.d));
-        out[P] = last;
+        out.put(P, jd.b, cadd(Ag, jd.a), czero<R>(), cadd(Dg, jd.d));
     } else if (tid == kThreads - 1) {
         LevelSlot<R> s;
         sstore(&s.b, jd.b);
@@ -219,7 +266,7 @@ __device__ __forceinline__ void write_reduced_row(bool active, int64_t t, int64_
 // One thread per block: RD + JD downwards with RU + JU accumulated on the way.
 template <class R, class Src, class Map>
 __global__ void __launch_bounds__(kThreads)
-k_reduce(Src src0, Map sys, Map next, int m, LevelRow<R>* out, LevelSlot<R>* out_slot, int* status) {
+k_reduce(Src src0, Map sys, Map next, int m, int m_next, LevelPlanes<R> out, LevelSlot<R>* out_slot, int* status) {
     const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const bool active = g < sys.total();
     bool ok = true;
@@ -228,32 +275,35 @@ k_reduce(Src src0, Map sys, Map next, int m, LevelRow<R>* out, LevelSlot<R>* out
     JDPart<R> jd;
     jd.b = czero<R>(); jd.a = czero<R>(); jd.d = czero<R>();
     int64_t t = 0, P = 0;
-    LevelRow<R>* outs = out;
+    int si = 0;
     if (active) {
-        const int si = sys.find(g);
+        si = sys.find(g);
         const LvlSys& e = sys.at(si);
         const Src src = src0.bind(e);
         const int64_t n = e.n;
         P = e.P;
         t = g - e.blk_off;
-        outs = out + next.at(si).row_off;
         const int64_t J0 = joint_line(t, P, m, n);
         const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
-        const Row<R> r0 = src.template row<R>(J0);
+        // row k of the block (k = gap: row 0 of the next block)
+        auto row_k = [&](int k) {
+            return k < gap ? src.template row<R>(t, k, J0 + k) : src.template row<R>(t + 1, 0, J0 + k);
+        };
+        const Row<R> r0 = row_k(0);
         A0 = r0.a;
         D0 = r0.d;
         // row 1: untouched by RD
-        const Row<R> r1 = src.template row<R>(J0 + 1);
+        const Row<R> r1 = row_k(1);
         cx<R> w = crcp(r1.a, ok);       // 1 / a_k^RD of the previous row
         const cx<R> w1 = w;
         cx<R> bRD = r1.b, dRD = r1.d;   // RD fill-in column J0 and rhs of the previous row
         cx<R> cprev = r1.c;             // upper diagonal of the previous row
         cx<R> Q = cfrom<R>(1.0, 0.0);   // prod_{i<k} rho_i
         cx<R> nb = bRD, nd = dRD;       // RU values accumulated on row 1
-        Row<R> nxt = src.template row<R>(J0 + 2);  // one row ahead (row g when g == 2)
+        Row<R> nxt = row_k(2);  // one row ahead (row g when g == 2)
         for (int k = 2; k < gap; ++k) {
             const Row<R> rk = nxt;
-            nxt = src.template row<R>(J0 + k + 1);
+            nxt = row_k(k + 1);
             // RD: r = -b_k / a_{k-1};  b_k = r b_{k-1};  a_k += r c_{k-1};  d_k += r d_{k-1}
             const cx<R> r = cneg(cmul(rk.b, w));
             bRD = cmul(r, bRD);
@@ -281,7 +331,8 @@ k_reduce(Src src0, Map sys, Map next, int m, LevelRow<R>* out, LevelSlot<R>* out
         JUa = cmul(r0u, nb);
         JUd = cmul(r0u, nd);
     }
-    write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, outs, out_slot);
+    write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, RowSink<R>(out, next.at(si), m_next),
+                         out_slot);
     if (!ok) flag_error(status, kStatusNonfinite);
 }
 
@@ -317,10 +368,10 @@ k_substitute(Src src0, Map sys, Map next, int m, const typename Store<R>::T* x_n
     const cx<R> xL = sload(x_next + t);
     const cx<R> xR = sload(x_next + t + 1);
     cx<R> zp = czero<R>(), cpp = czero<R>();
-    Row<R> nxt = src.template row<R>(J0 + 1);
+    Row<R> nxt = src.template row<R>(t, 1, J0 + 1);
     for (int k = 1; k < gap; ++k) {
         const Row<R> rk = nxt;
-        if (k + 1 < gap) nxt = src.template row<R>(J0 + k + 1);
+        if (k + 1 < gap) nxt = src.template row<R>(t, k + 1, J0 + k + 1);
         cx<R> rhs = rk.d;
         if (k == 1) rhs = csub(rhs, cmul(rk.b, xL));
         if (k == gap - 1) rhs = csub(rhs, cmul(rk.c, xR));
@@ -368,7 +419,7 @@ k_substitute_gmem(Src src0, Map sys, Map next, int m, const typename Store<R>::T
     const cx<R> xR = sload(x_next + t + 1);
     cx<R> zp = czero<R>(), cpp = czero<R>();
     for (int k = 1; k < gap; ++k) {
-        const Row<R> rk = src.template row<R>(J0 + k);
+        const Row<R> rk = src.template row<R>(t, k, J0 + k);
         cx<R> rhs = rk.d;
         if (k == 1) rhs = csub(rhs, cmul(rk.b, xL));
         if (k == gap - 1) rhs = csub(rhs, cmul(rk.c, xR));
@@ -405,7 +456,7 @@ __device__ __forceinline__ void base_solve(const LevelSource<R>& src, typename S
     cx<R> a_prev = czero<R>(), c_prev = czero<R>(), d_prev = czero<R>();
     cx<R> A[kBaseMax], C[kBaseMax], D[kBaseMax];
     for (int64_t w = 0; w < n; ++w) {
-        Row<R> rw = src.template row<R>(w);
+        Row<R> rw = src.template row_at<R>(w);
         cx<R> a = rw.a, d = rw.d;
         if (w > 0) {
             // r = -b_w / a_{w-1};  a_w += r c_{w-1};  d_w += r d_{w-1}
@@ -434,7 +485,7 @@ __global__ void k_base_serial(LevelSource<R> src, typename Store<R>::T* x, typen
     const int64_t n = src.n;
     cx<R> zp = czero<R>(), cpp = czero<R>();
     for (int64_t w = 0; w < n; ++w) {
-        const Row<R> r = src.template row<R>(w);
+        const Row<R> r = src.template row_at<R>(w);
         // m_w = a_w - b_w c'_{w-1};  z_w = (d_w - b_w z_{w-1}) / m_w;  c'_w = c_w / m_w
         const cx<R> piv = (w == 0) ? r.a : csub(r.a, cmul(r.b, cpp));
         const cx<R> iv = crcp(piv, ok);
@@ -490,7 +541,7 @@ __device__ __forceinline__ void cr_solve(const LevelSource<R>& src, typename Sto
     const int tid = threadIdx.x;
     bool ok = true;
     for (int i = tid; i < n; i += kCrThreads) {
-        const Row<R> r = src.template row<R>(i);
+        const Row<R> r = src.template row_at<R>(i);
         sstore(sb + i, r.b);
         sstore(sa + i, r.a);
         sstore(sc + i, r.c);
@@ -795,7 +846,7 @@ template <> struct ReduceOccupancy<double, ManySys> { static constexpr int min_b
 
 template <class R, class Map, class Grid>
 __global__ void __launch_bounds__(kThreads, ReduceOccupancy<R, Map>::min_blocks)
-k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, LevelRow<R>* out, LevelSlot<R>* out_slot,
+k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, LevelPlanes<R> out, LevelSlot<R>* out_slot,
             typename Store<R>::T* keep0, int* status) {
     typedef typename Store<R>::T ST;
     const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -806,14 +857,13 @@ k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, LevelRow<R>* out, Le
     JDPart<R> jd;
     jd.b = czero<R>(); jd.a = czero<R>(); jd.d = czero<R>();
     int64_t t = 0, P = 0;
-    LevelRow<R>* outs = out;
+    int si = 0;
     if (active) {
-        const int si = sys.find(g);
+        si = sys.find(g);
         const LvlSys& e = sys.at(si);
         const int64_t n = e.n;
         P = e.P;
         t = g - e.blk_off;
-        outs = out + next.at(si).row_off;
         ST* keep = keep0 ? keep0 + keep_base(m) : nullptr;
         const int64_t J0 = joint_line(t, P, m, n);
         const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
@@ -861,7 +911,8 @@ k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, LevelRow<R>* out, Le
         JUa = cneg(cmul(w1, cfma(one, w1, S)));
         JUd = cmul(w1, nd);
     }
-    write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, outs, out_slot);
+    write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, RowSink<R>(out, next.at(si), m_next),
+                         out_slot);
     if (!ok) flag_error(status, kStatusNonfinite);
 }
 

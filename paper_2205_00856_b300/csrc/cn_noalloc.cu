@@ -87,14 +87,12 @@ int plan_levels(int64_t n, NaLevel* lv, size_t* used) {
     return L;
 }
 
-// The single system's entry at level l (row and block offsets 0).
+// The single system's entry at level l (offsets 0; every level in row order).
 OneSys na_sys(const NaLevel* lv, int l) {
     OneSys s;
+    s.e = LvlSys{};
     s.e.n = lv[l].n;
     s.e.P = lv[l].P;
-    s.e.row_off = 0;
-    s.e.blk_off = 0;
-    s.e.prod_blk_off = 0;
     return s;
 }
 
@@ -102,24 +100,28 @@ template <class R>
 cudaError_t na_solve(unsigned char* base, const NaLevel* lv, int L, const ArraySource& src, double2* x,
                      cudaStream_t st) {
     typedef typename Store<R>::T ST;
-    auto rows = [&](int l) { return reinterpret_cast<LevelRow<R>*>(base + lv[l].rows); };
+    auto planes = [&](int l) { return LevelPlanes<R>{reinterpret_cast<ST*>(base + lv[l].rows), lv[l].n}; };
     auto slot = [&](int l) { return reinterpret_cast<LevelSlot<R>*>(base + lv[l].slot); };
     auto xs = [&](int l) { return reinterpret_cast<ST*>(base + lv[l].x); };
     auto lsrc = [&](int l) {
+        const LevelPlanes<R> pl = planes(l);
         LevelSource<R> s;
-        s.rows = rows(l);
+        s.b = pl.p;
+        s.L = pl.L;
         s.slot = slot(l);
         s.n = lv[l].n;
         s.prod = 0;
+        s.stride = 0;
         return s;
     };
     auto grid = [&](int l) { return (unsigned)na_ceil_div(lv[l].P, kThreads); };
     const size_t smem = 2 * (size_t)kNaBlock * kThreads * 16;  // 32 KiB: below the default limit
     k_reduce<R, ArraySource, OneSys><<<grid(0), kThreads, 0, st>>>(src, na_sys(lv, 0), na_sys(lv, 1), kNaBlock,
-                                                                   rows(1), slot(1), nullptr);
+                                                                   kNaBlock, planes(1), slot(1), nullptr);
     for (int l = 1; l < L; ++l)
         k_reduce<R, LevelSource<R>, OneSys><<<grid(l), kThreads, 0, st>>>(lsrc(l), na_sys(lv, l), na_sys(lv, l + 1),
-                                                                          kNaBlock, rows(l + 1), slot(l + 1), nullptr);
+                                                                          kNaBlock, kNaBlock, planes(l + 1), slot(l + 1),
+                                                                          nullptr);
     k_base<R><<<1, 32, 0, st>>>(lsrc(L), xs(L), nullptr);
     for (int l = L - 1; l >= 1; --l)
         k_substitute<R, LevelSource<R>, OneSys, ST><<<grid(l), kThreads, smem, st>>>(
