@@ -35,6 +35,8 @@ EXPORTS = ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_s
            "cn_field_grad_to_controls", "cn_batch_create", "cn_batch_destroy", "cn_batch_offsets",
            "cn_batch_step", "cn_batch_status", "cn_plan_create_levels")
 NOALLOC_MAX_N = 1048576
+# (level-0 block, level block) pairs autotune_plan tries by default
+PLAN_TUNE_CANDIDATES = tuple((m0, ml) for m0 in (8, 10, 12, 16) for ml in (8, 12, 16, 24))
 MAX_LEVELS = 24
 PROFILE_CLASSES = ("reduce_level0", "substitute_level0", "reduce_levels_ge1", "substitute_levels_ge1", "rs_stage")
 
@@ -401,7 +403,7 @@ def autotune_plan(n, dx, dt, x_min, candidates=None, steps: int = 3, repeats: in
     Returns (best_block, best_level_block, {candidate: ms per step})."""
     import torch
     if candidates is None:
-        candidates = [(m0, ml) for m0 in (8, 10, 12, 16) for ml in (8, 12, 16, 24)]
+        candidates = list(PLAN_TUNE_CANDIDATES)
     times = {}
     psi = torch.zeros(int(n), dtype=torch.complex128, device="cuda")
     for m0, ml in candidates:

@@ -183,3 +183,33 @@ def test_segment_graphs_match_eager_bitwise():
     for r in res[1:]:
         for a, b in zip(r, res[0]):
             assert np.array_equal(a, b)
+
+
+def test_full_size_gradient_vs_finite_differences():
+    # the gradient workload at full size (N = 2^20, 2000 steps, 500 controls, sqrt(N)
+    # checkpoints, segment graphs) as bench.py times it; the oracle adjoint would take
+    # minutes here, so the three largest components are checked against central
+    # differences of the GPU forward map.  h = 1e-5 keeps the loss's rounding
+    # (~1e-15 absolute) / h below 1e-6 of those components and the O(h^2)
+    # truncation (|u| ~ 0.05) below 1e-7; tolerance 1e-5.
+    cfg = W.gradient_config()
+    n, nsteps, nc = cfg["n"], cfg["nsteps"], cfg["n_controls"]
+    tf = nsteps * cfg["dt"]
+    plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0,
+                    arith=cnb.ARITH_DF64, block=12, level_block=12)
+    psi0 = to_dev(W.initial_state(cfg))
+    u0 = W.initial_controls(nc, tf)
+    wt = to_dev(W.outside_mask_weights(n, cfg["dx"], cfg["loss_cut"]))
+    ut = to_dev(u0).requires_grad_(True)
+    loss_fn(propagate(psi0, ut, plan, nsteps, tf), wt).backward()
+    g = ut.grad.cpu().numpy()
+    plan.check()
+    h = 1e-5
+    with torch.no_grad():
+        for c in np.argsort(-np.abs(g))[:3]:
+            up, um = u0.copy(), u0.copy()
+            up[c] += h
+            um[c] -= h
+            fd = (loss_fn(propagate(psi0, to_dev(up), plan, nsteps, tf), wt).item()
+                  - loss_fn(propagate(psi0, to_dev(um), plan, nsteps, tf), wt).item()) / (2 * h)
+            assert abs(fd - g[c]) <= 1e-5 * abs(g[c]), (int(c), fd, g[c])

@@ -28,6 +28,17 @@ def rel(x, y):
     return float(np.linalg.norm(np.asarray(x) - np.asarray(y)) / np.linalg.norm(np.asarray(y)))
 
 
+def system_norms(psi, offsets):
+    """sum |psi|^2 of every system, each from its own slice (a running sum over the
+    whole batch would lose the small systems' digits)."""
+    v = torch.view_as_real(psi)
+    out = torch.empty(len(offsets) - 1, dtype=torch.float64, device=psi.device)
+    for s in range(len(offsets) - 1):
+        w = v[int(offsets[s]):int(offsets[s + 1])]
+        out[s] = torch.sum(w * w)
+    return out.cpu().numpy()
+
+
 def batch_state(sizes, seed=0):
     """Per system a Gaussian at the origin, width a twentieth of the box, random momentum."""
     rng = np.random.default_rng(seed)
@@ -131,17 +142,12 @@ def test_batch_norm_conserved_large():
     sizes = cfg["sizes"]
     b = cnb.Batch(sizes, cfg["dx"], cfg["dt"], pot=cnb.POT_COSSERIES, cos_a=cfg["cos_a"], arith=cnb.ARITH_DF64)
     psi = torch.from_numpy(np.concatenate(batch_state(sizes, seed=4))).to(DEV)
-    off = torch.from_numpy(b.offsets).to(DEV)
 
-    def norms(p):
-        w = (p.real ** 2 + p.imag ** 2)
-        c = torch.cumsum(torch.cat([torch.zeros(1, dtype=w.dtype, device=DEV), w]), 0)
-        return (c[off[1:]] - c[off[:-1]]).cpu().numpy()
 
-    n0 = norms(psi)
+    n0 = system_norms(psi, b.offsets)
     b.step(psi, 50, psi_out=psi)
     b.check()
-    assert np.max(np.abs(norms(psi) / n0 - 1)) <= 1e-11
+    assert np.max(np.abs(system_norms(psi, b.offsets) / n0 - 1)) <= 1e-11
     # sampled systems against the oracle (smallest, largest, median size)
     out = psi.cpu().numpy()
     parts = batch_state(sizes, seed=4)
@@ -156,3 +162,46 @@ def test_autotune_returns_a_candidate():
     sizes = [5000, 17, 70000, 1024]
     m0, ml, times = cnb.autotune_batch(sizes, DX, DT, candidates=[(8, 8), (12, 8)], steps=2, repeats=1)
     assert (m0, ml) in times and len(times) == 2 and all(t > 0 for t in times.values())
+
+
+def _device_gaussians(sizes_t, offsets_t, dx, seed):
+    """Per system a Gaussian at the origin, width max(1, n dx / 20), momentum in [-1, 1)."""
+    nsys = sizes_t.numel()
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    k0 = (torch.rand(nsys, generator=g, dtype=torch.float64) * 2 - 1).to(DEV)
+    seg = torch.repeat_interleave(torch.arange(nsys, device=DEV), sizes_t)
+    j = torch.arange(int(offsets_t[-1]), device=DEV, dtype=torch.int64) - offsets_t[:-1][seg]
+    x = (j - torch.div(sizes_t, 2, rounding_mode="floor")[seg]).to(torch.float64) * dx
+    sig = torch.clamp(0.05 * sizes_t.to(torch.float64) * dx, min=1.0)[seg]
+    return torch.polar(torch.exp(-x * x / (4 * sig * sig)), k0[seg] * x)
+
+
+@pytest.mark.parametrize("blocks", [(12, 16), (8, 8)])
+def test_full_size_batch_4096_systems(blocks):
+    # the batched workload at full size (4096 systems, 634 M rows), replayed from a
+    # CUDA graph as bench.py times it: every system's norm, and sampled systems
+    # (smallest, largest, three others) against the oracle from the same initial state
+    cfg = W.batched_config()
+    sizes, dx, dt = cfg["sizes"], cfg["dx"], cfg["dt"]
+    nsteps = 20
+    b = cnb.Batch(sizes, dx, dt, pot=cnb.POT_COSSERIES, cos_a=cfg["cos_a"], arith=cnb.ARITH_DF64,
+                  block=blocks[0], level_block=blocks[1])
+    off = torch.from_numpy(b.offsets).to(DEV)
+    psi = _device_gaussians(torch.from_numpy(sizes).to(DEV), off, dx, 7)
+    pick = [int(np.argmin(sizes)), int(np.argmax(sizes))] + [int(v) for v in np.random.default_rng(5).integers(0, 4096, 3)]
+    init = {s: psi[int(b.offsets[s]):int(b.offsets[s + 1])].cpu().numpy() for s in pick}
+
+
+    n0 = system_norms(psi, b.offsets)
+    g = b.capture(psi, nsteps)
+    g.replay()
+    torch.cuda.synchronize()
+    b.check()
+    assert np.max(np.abs(system_norms(psi, b.offsets) / n0 - 1)) <= 1e-11
+    for s in pick:
+        n = int(sizes[s])
+        prob = oracle.Problem(n, dx, dt, -(n // 2) * dx, pot=oracle.POT_COSSERIES, cos_a=cfg["cos_a"][s], L=n * dx)
+        got = psi[int(b.offsets[s]):int(b.offsets[s + 1])].cpu().numpy()
+        assert rel(got, oracle.cn_run(prob, init[s], nsteps)) <= 1e-11, (s, n)
+    del g
+    b.close()

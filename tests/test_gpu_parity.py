@@ -146,20 +146,52 @@ def test_step_host_matches_device():
     assert np.array_equal(dev, host)
 
 
+_FULL = {}
+
+
+def _full_size_reference():
+    """Oracle run of the benchmarked configuration (N = 2^24, 3 steps), computed once."""
+    if not _FULL:
+        cfg = W.soft_coulomb_config()
+        nsteps = 3
+        psi0 = W.initial_state(cfg)
+        E = W.field_midpoints(nsteps, cfg["dt"], t0=200.0)
+        _FULL.update(cfg=cfg, nsteps=nsteps, psi0=psi0, E=E,
+                     ref=oracle.cn_run(oracle_problem(cfg), psi0, nsteps, E_mid=E))
+    return _FULL
+
+
+# the benchmarked configuration in every launch configuration bench.py's autotuner can pick
+@pytest.mark.parametrize("blocks", list(cnb.PLAN_TUNE_CANDIDATES))
 @pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
-def test_full_size_soft_coulomb_2pow24(arith):
-    # the benchmarked configuration, in the launch configuration bench.py times
-    cfg = W.soft_coulomb_config()
-    nsteps = 3
-    psi0 = W.initial_state(cfg)
-    E = W.field_midpoints(nsteps, cfg["dt"], t0=200.0)
-    plan = plan_for(cfg, arith=arith)
+def test_full_size_soft_coulomb_2pow24(arith, blocks):
+    if arith == cnb.ARITH_F64 and blocks not in ((8, 8), (12, 12)):
+        pytest.skip("FP64 path: two block configurations suffice")
+    f = _full_size_reference()
+    cfg, nsteps, psi0, E, ref = f["cfg"], f["nsteps"], f["psi0"], f["E"], f["ref"]
+    plan = cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith,
+                    block=blocks[0], level_block=blocks[1])
     out = plan.step(to_dev(psi0), nsteps, E_mid=to_dev(E)).cpu().numpy()
     plan.check()
-    ref = oracle.cn_run(oracle_problem(cfg), psi0, nsteps, E_mid=E)
+    plan.close()
     assert rel(out, ref) <= 1e-12
     # unitarity of the Cayley form at full size
     assert abs(np.sum(np.abs(out) ** 2) / np.sum(np.abs(psi0) ** 2) - 1) <= 1e-12
+
+
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_free_packet_p16_partitions(arith):
+    # the free-packet configuration with the N-shaped partition into P = 16 blocks
+    # (one level of 256-row blocks, the 17-row reduced system solved serially)
+    cfg = W.free_packet_config()
+    psi0 = W.initial_state(cfg)
+    ref = oracle.cn_run(oracle_problem(cfg), psi0, cfg["nsteps"])
+    plan = cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], arith=arith, levels=[256])
+    info = plan.info()
+    assert info["levels"] == 1 and info["level_rows"][:2] == [4096, 17]
+    out = plan.step(to_dev(psi0), cfg["nsteps"]).cpu().numpy()
+    plan.check()
+    assert rel(out, ref) <= 1e-11
 
 
 # ------------------------------------------------------------------ potentials and coefficient tables
