@@ -102,9 +102,15 @@ typedef struct {
  * point) for the step ping-pong -- for grids whose 32 B per point do not fit. */
 #define CN_FLAG_RECOMPUTE 2
 
-/* Create a plan for systems of size desc->n.  Allocates the device workspace
- * (reduced systems of every nesting level, one state buffer of n complex128,
- * a status word) on the current device.  On success *out owns it. */
+/* Create a plan for systems of size desc->n.  The N-shaped solve is nested
+ * (Eq. iteration): level 0 is cut into blocks of desc->block rows, each reduced
+ * level into blocks of desc->level_block rows, until a level has at most 1024
+ * rows; that system (the RS stage) is solved inside one CTA by cyclic
+ * reduction.  Allocates the device workspace on the current device: the
+ * reduced systems of every level (~80 B per row of level 1 and below), 32 B
+ * per grid point of kept right-hand sides and pivots (16 B of state buffer
+ * instead with CN_FLAG_RECOMPUTE), the optional coefficient table, a status
+ * word.  On success *out owns it. */
 cn_status cn_plan_create(const cn_desc* desc, cn_plan* out);
 
 /* Create a plan with an explicit nesting depth and block sizes, for studying
@@ -184,7 +190,8 @@ cn_status cn_field_grad_to_controls(const double* dLdE, int64_t nsteps, double t
 typedef struct {
     int64_t n;                           /* unknowns                                      */
     int32_t levels;                      /* reduced levels below level 0; level `levels`  */
-                                         /* is solved by the serial RS stage              */
+                                         /* is solved by the RS stage (one CTA, cyclic    */
+                                         /* reduction; serial for cn_plan_create_levels)  */
     int32_t launches_per_step;           /* kernels one CN step / one solve launches      */
     int64_t level_rows[CN_MAX_LEVELS];   /* rows of level 0 .. levels                     */
     int32_t level_block[CN_MAX_LEVELS];  /* rows per block of level 0 .. levels-1         */
