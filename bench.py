@@ -34,7 +34,8 @@ import numpy as np  # noqa: E402
 
 import workloads as W  # noqa: E402
 
-METRIC = "CN grid-point updates/sec (complex128)"
+METRIC = ("CN grid-point updates/sec (complex128) and % of HBM roofline; adjoint/forward cost ratio")
+# value: grid-point updates/s; roofline_hbm.frac: the fraction of HBM roofline; adjoint.ratio: the cost ratio
 UNIT = "unknown-steps/s"
 WORKLOAD_STEPS = 1000  # length of the benchmarked propagation (field samples)
 
