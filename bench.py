@@ -38,6 +38,7 @@ METRIC = ("CN grid-point updates/sec (complex128) and % of HBM roofline; adjoint
 # value: grid-point updates/s; roofline_hbm.frac: the fraction of HBM roofline; adjoint.ratio: the cost ratio
 UNIT = "unknown-steps/s"
 WORKLOAD_STEPS = 1000  # length of the benchmarked propagation (field samples)
+PG_TIMEOUT_S = 900     # process-group timeout: longer than any phase between two collectives
 
 # Algorithmic flops per grid row of the two level-0 kernels (soft-Coulomb
 # potential regenerated on the fly, store mode), FMA = 2 flops, a reciprocal or
@@ -541,8 +542,12 @@ def main():
     dev = torch.device("cuda", local)
     dist = None
     if world > 1:
+        import datetime
+
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+        # a rank that dies makes the others' next collective fail after this long
+        # instead of waiting for ever
+        dist.init_process_group("nccl", device_id=dev, timeout=datetime.timedelta(seconds=PG_TIMEOUT_S))
 
     if args.largest:
         if rank == 0:

@@ -881,6 +881,23 @@ cn_status cn_plan_status(cn_plan p) {
     return read_status(p);
 }
 
+cn_status cn_diag_wait_timeout(int32_t polls) {
+    if (polls < 1) return CN_ERR_INVALID_ARG;
+    int* st = nullptr;
+    if (cudaMalloc(&st, sizeof(int)) != cudaSuccess) return alloc_status(cudaErrorMemoryAllocation);
+    cudaError_t e = cudaMemset(st, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        k_diag_wait_timeout<<<1, 32>>>(st, polls);
+        e = cudaGetLastError();
+    }
+    int h = 0;
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&h, st, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(st);
+    if (e != cudaSuccess) return CN_ERR_CUDA;
+    return static_cast<cn_status>(h);
+}
+
 // ------------------------------------------------------------------ batches
 cn_status cn_batch_create(const cn_desc* common, int64_t nsys, const int64_t* sizes, const double* x_min,
                           const double* cos_a, cn_batch* out) {

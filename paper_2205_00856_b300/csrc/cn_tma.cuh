@@ -46,13 +46,24 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
     return done != 0;
 }
 
-// Wait for phase `parity` of the barrier, giving up after kWaitSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (int i = 0; i < kWaitSpinLimit; ++i) {
+// Wait for phase `parity` of the barrier, giving up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int limit = kWaitSpinLimit) {
+    for (int i = 0; i < limit; ++i) {
         if (mbar_test_wait(bar, parity)) return true;
         if (i >= 32) __nanosleep(64);
     }
     return false;
+}
+
+// Diagnostics: one CTA waits, as the TMA-staged kernels do, on a barrier that
+// nothing completes (it expects one arrival that never comes), with a limit of
+// `limit` polls, and reports the timeout in the status word like they do.
+static __global__ void k_diag_wait_timeout(int* status, int limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    const bool landed = mbar_wait_bounded(&bar, 0, limit);
+    if (!landed && threadIdx.x == 0) atomicCAS(status, 0, kStatusTimeout);
 }
 
 }  // namespace cnb

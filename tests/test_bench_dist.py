@@ -83,3 +83,35 @@ def test_reference_arm_rank0_line(monkeypatch, capsys):
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "unknown-steps/s" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def _dying_rank_main(rank, world, port, q):
+    import datetime
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=5))
+    if rank == 1:
+        q.put((rank, "left"))
+        q.close()
+        q.join_thread()  # the message is out before the process goes
+        os._exit(0)  # leaves between steps, before the timing collective, without cleanup
+    try:
+        bench.max_over_ranks(dist, 1.0, torch.device("cpu"))
+        q.put((rank, "no error"))
+    except Exception as e:  # the surviving rank learns of it through the collective
+        q.put((rank, "error: " + type(e).__name__))
+
+
+def test_rank_that_dies_fails_the_collective_instead_of_hanging():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dying_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+    assert res[1] == "left"
+    assert res[0].startswith("error"), res[0]
