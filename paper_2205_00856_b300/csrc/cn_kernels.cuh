@@ -987,6 +987,11 @@ k_cn_substitute_kept(Map sys, Map next, int m, const typename Store<R>::T* keep0
     const int64_t g0 = (int64_t)blockIdx.x * kThreads;
     const int64_t g = g0 + tid;
     const int64_t total = sys.total();
+    // the CTA's keep chunk is contiguous: pull all of it towards L2 at once, so the
+    // per-row loads below wait on L2 rather than DRAM
+    if (tid == 0)
+        bulk_prefetch_l2(keep0 + (int64_t)blockIdx.x * (2 * (int64_t)m * kThreads) + 2 * kThreads,
+                         2u * (uint32_t)(m - 1) * kThreads * (uint32_t)sizeof(typename Store<R>::T));
     // CTA-uniform: are all 128 blocks full-length blocks of one system?
     bool regular = false;
     int s0 = 0;
