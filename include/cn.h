@@ -282,16 +282,6 @@ cn_status cn_batch_step(cn_batch batch, const void* psi_in, void* psi_out, const
 /* As cn_plan_status, for a batch. */
 cn_status cn_batch_status(cn_batch batch);
 
-/* Diagnostics for the device-side failure path, without a GPU fault: runs one
- * CTA that waits, exactly as the TMA-staged substitution waits for its copies,
- * on a shared-memory mbarrier that nothing completes, giving up after `polls`
- * polls (>= 1; each poll backs off ~64 ns), and returns what that kernel
- * reports in a status word: CN_ERR_TIMEOUT when the wait ran out (the kernel
- * then returns normally and the context stays usable).  Synchronises the
- * device.  The paper has no counterpart; this exists to test the bounded-wait
- * contract of the library's kernels. */
-cn_status cn_diag_wait_timeout(int32_t polls);
-
 /* Static description of a status code. */
 const char* cn_status_string(cn_status s);
 

@@ -33,7 +33,7 @@ EXPORTS = ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_s
            "cn_plan_query", "cn_plan_profile", "cn_plan_profile_read", "cn_plan_status", "cn_status_string",
            "cn_version", "cn_solve_tridiag_noalloc", "cn_adjoint_step", "cn_field_from_controls",
            "cn_field_grad_to_controls", "cn_batch_create", "cn_batch_destroy", "cn_batch_offsets",
-           "cn_batch_step", "cn_batch_status", "cn_plan_create_levels", "cn_diag_wait_timeout")
+           "cn_batch_step", "cn_batch_status", "cn_plan_create_levels")
 NOALLOC_MAX_N = 1048576
 # (level-0 block, level block) pairs autotune_plan tries by default
 PLAN_TUNE_CANDIDATES = tuple((m0, ml) for m0 in (8, 10, 12, 16) for ml in (8, 12, 16, 24))
@@ -101,8 +101,6 @@ def load(build_if_missing: bool = True):
             lib.cn_status_string.restype = C.c_char_p
             lib.cn_version.argtypes = []
             lib.cn_version.restype = C.c_char_p
-            lib.cn_diag_wait_timeout.argtypes = [C.c_int32]
-            lib.cn_diag_wait_timeout.restype = C.c_int
             lib.cn_plan_create_levels.argtypes = [C.POINTER(_Desc), C.c_int32, vp, C.POINTER(vp)]
             lib.cn_plan_create_levels.restype = C.c_int
             lib.cn_batch_create.argtypes = [C.POINTER(_Desc), i64, vp, vp, vp, C.POINTER(vp)]
@@ -467,12 +465,6 @@ def field_grad_to_controls(dLdE, t_final: float, t0: float, dt: float, n_control
     _check(lib.cn_field_grad_to_controls(pg, dLdE.numel(), float(t_final), float(t0), float(dt), int(n_controls), po,
                                          _stream_handle(stream)), "cn_field_grad_to_controls")
     return out
-
-
-def diag_wait_timeout(polls: int) -> int:
-    """Status a bounded device-side wait reports when nothing completes its barrier
-    (cn_diag_wait_timeout): CN_ERR_TIMEOUT (5) expected."""
-    return int(load().cn_diag_wait_timeout(int(polls)))
 
 
 def version() -> str:

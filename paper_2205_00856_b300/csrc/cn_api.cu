@@ -334,10 +334,6 @@ void with_maps_grid(const Engine* p, F f) {
 // Shared memory of the substitutions: two complex values per block row and thread.
 size_t subst_smem(int m) { return 2 * (size_t)m * kThreads * kCplx; }
 size_t kept_smem(int m) { return (size_t)m * kTileStride * kCplx; }
-size_t kept_tma_smem(int m) { return 2 * (size_t)m * kTileStride * kCplx; }
-// Blocks up to this many rows take the TMA-staged substitution (its two planes
-// cost occupancy that longer blocks cannot afford; measured on B300).
-constexpr int kTmaKeptMaxRows = 8;
 size_t cr_smem() { return 5 * (size_t)kCrMax * kCplx; }
 
 template <class R, class Src, class Map>
@@ -371,8 +367,6 @@ cudaError_t set_smem_limits_map(int m0, int ml) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_substitute<R, LevelSource<R>, Map, ST>, a, (int)subst_smem(ml));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute<R, Map, Grid>, a, (int)subst_smem(m0));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute_kept<R, Map>, a, (int)kept_smem(m0));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_cn_substitute_kept_tma<R, Map>, a, (int)kept_tma_smem(std::min(m0, kTmaKeptMaxRows)));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr<R>, a, (int)cr_smem());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr_many<R>, a, (int)cr_smem());
     return e;
@@ -471,9 +465,6 @@ cudaError_t cn_solve(Engine* p, const CNStep& s, double2* x, cudaStream_t st) {
         if (keep && L0.m > kSmemRowsMax)
             k_cn_substitute_kept_gmem<R><<<grid, kThreads, 0, st>>>(a, b, L0.m, keep, x_of<R>(L1), x,
                                                                     static_cast<ST*>(p->zc));
-        else if (keep && L0.m <= kTmaKeptMaxRows)
-            k_cn_substitute_kept_tma<R><<<grid, kThreads, kept_tma_smem(L0.m), st>>>(a, b, L0.m, keep, x_of<R>(L1),
-                                                                                     x, p->status);
         else if (keep)
             k_cn_substitute_kept<R><<<grid, kThreads, kept_smem(L0.m), st>>>(a, b, L0.m, keep, x_of<R>(L1), x,
                                                                              p->status);
@@ -879,23 +870,6 @@ cn_status cn_plan_profile_read(cn_plan p, double* ms, int64_t* launches, int32_t
 cn_status cn_plan_status(cn_plan p) {
     if (!p) return CN_ERR_INVALID_ARG;
     return read_status(p);
-}
-
-cn_status cn_diag_wait_timeout(int32_t polls) {
-    if (polls < 1) return CN_ERR_INVALID_ARG;
-    int* st = nullptr;
-    if (cudaMalloc(&st, sizeof(int)) != cudaSuccess) return alloc_status(cudaErrorMemoryAllocation);
-    cudaError_t e = cudaMemset(st, 0, sizeof(int));
-    if (e == cudaSuccess) {
-        k_diag_wait_timeout<<<1, 32>>>(st, polls);
-        e = cudaGetLastError();
-    }
-    int h = 0;
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemcpy(&h, st, sizeof(int), cudaMemcpyDeviceToHost);
-    cudaFree(st);
-    if (e != cudaSuccess) return CN_ERR_CUDA;
-    return static_cast<cn_status>(h);
 }
 
 // ------------------------------------------------------------------ batches

@@ -41,7 +41,7 @@
 // the solution unchanged.
 #pragma once
 #include "cn_arith.cuh"
-#include "cn_tma.cuh"
+#include "cn_prefetch.cuh"
 
 namespace cnb {
 
@@ -1058,119 +1058,6 @@ k_cn_substitute_kept(Map sys, Map next, int m, const typename Store<R>::T* keep0
         // the CTA holding the last block of the system also writes its last joint line
         store128(x + e0.n - 1, sload(x_next0 + next.at(s0).row_off + e0.P));
     }
-}
-
-// The same store-mode substitution with the CTA's keep tile staged by TMA
-// (used for short blocks, whose two shared-memory planes still leave enough
-// CTAs per SM to hide the chains' latency).  The CTA's keep chunk is contiguous (keep_base), so one thread brings
-// it into shared memory with bulk asynchronous copies (TMA), one 2 KB row of
-// 128 blocks per copy, into a d-plane and a w-plane ([k][tid] with a row
-// stride of kThreads + 1 entries, so the per-thread column walk and the
-// tile-order read-out below hit distinct banks).  All copies are in flight at
-// once; block row k completes on its own mbarrier, so the forward chain starts
-// as soon as row 1 has landed.  z overwrites d in place, then y; when
-// all 128 blocks of the CTA belong to one system and are full-length, the CTA
-// writes its contiguous tile of x in order (coalesced).
-template <class R, class Map>
-__global__ void __launch_bounds__(kThreads)
-k_cn_substitute_kept_tma(Map sys, Map next, int m, const typename Store<R>::T* keep0,
-                     const typename Store<R>::T* x_next0, double2* x0, int* status) {
-    typedef typename Store<R>::T ST;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar[kSmemRowsMax];  // bar[k]: block row k of d and w landed
-    ST* dpl = reinterpret_cast<ST*>(smem_raw);  // [m][kTileStride]: d^, then z, then y
-    ST* wpl = dpl + (size_t)m * kTileStride;    // [m][kTileStride]: pivot inverses
-    const int tid = threadIdx.x;
-    const int64_t g0 = (int64_t)blockIdx.x * kThreads;
-    const int64_t g = g0 + tid;
-    const int64_t total = sys.total();
-    if (tid > 0 && tid < m) mbar_init(&bar[tid], 1);
-    __syncthreads();
-    if (tid == 0) {
-        const ST* chunk = keep0 + (int64_t)blockIdx.x * (2 * (int64_t)m * kThreads);
-        const uint32_t row_bytes = kThreads * (uint32_t)sizeof(ST);
-        for (int k = 1; k < m; ++k) {
-            mbar_arrive_expect_tx(&bar[k], 2u * row_bytes);
-            bulk_g2s(dpl + k * kTileStride, chunk + (2 * k) * kThreads, row_bytes, &bar[k]);
-            bulk_g2s(wpl + k * kTileStride, chunk + (2 * k + 1) * kThreads, row_bytes, &bar[k]);
-        }
-    }
-    // CTA-uniform: are all 128 blocks full-length blocks of one system?
-    bool regular = false;
-    int s0 = 0;
-    int64_t t0 = 0;
-    if (g0 + kThreads <= total) {
-        s0 = sys.find(g0);
-        const LvlSys& e0 = sys.at(s0);
-        t0 = g0 - e0.blk_off;
-        regular = (sys.find(g0 + kThreads - 1) == s0) &&
-                  joint_line(t0 + kThreads, e0.P, m, e0.n) == (t0 + kThreads) * m;
-    }
-    // Each thread waits for block row k (bounded) just before it reads it; a
-    // wait that runs out reports a timeout and the thread writes nothing.
-    bool failed = false;
-    if (g < total) {
-        const int si = sys.find(g);
-        const LvlSys& e = sys.at(si);
-        const int64_t n = e.n, P = e.P, t = g - e.blk_off;
-        const ST* x_next = x_next0 + next.at(si).row_off;
-        double2* x = x0 + e.row_off;
-        const int64_t J0 = joint_line(t, P, m, n);
-        const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
-        const cx<R> xL = sload(x_next + t);
-        const cx<R> xR = sload(x_next + t + 1);
-        cx<R> zp = xL;
-        for (int k = 1; k < gap && !failed; ++k) {
-            if (!mbar_wait_bounded(&bar[k], 0)) {
-                failed = true;
-                break;
-            }
-            cx<R> rhs = cadd(sload(dpl + k * kTileStride + tid), zp);
-            if (k == gap - 1) rhs = cadd(rhs, xR);
-            zp = cmul(rhs, sload(wpl + k * kTileStride + tid));
-            sstore(dpl + k * kTileStride + tid, zp);
-        }
-        if (failed) {
-            flag_error(status, kStatusTimeout);
-        } else if (regular) {
-            cx<R> y = zp;
-            sstore(dpl + tid, xL);  // row 0 of the block: its top joint line
-            for (int k = gap - 2; k >= 1; --k) {
-                y = cfma(sload(dpl + k * kTileStride + tid), sload(wpl + k * kTileStride + tid), y);
-                sstore(dpl + k * kTileStride + tid, y);
-            }
-        } else {
-            cx<R> y = zp;
-            store128(x + J0 + gap - 1, y);
-            for (int k = gap - 2; k >= 1; --k) {
-                y = cfma(sload(dpl + k * kTileStride + tid), sload(wpl + k * kTileStride + tid), y);
-                store128(x + J0 + k, y);
-            }
-            store128(x + J0, xL);
-            if (t == P - 1) store128(x + J0 + gap, xR);
-        }
-    }
-    if (regular) {  // CTA-uniform
-        if (!__syncthreads_or(failed)) {
-            const LvlSys& e0 = sys.at(s0);
-            double2* x = x0 + e0.row_off;
-            // tile row i = (block b, row k) with i = b m + k; rows t0 m .. (t0 + 128) m - 1
-            const int64_t base = t0 * m;
-            for (int i = tid; i < kThreads * m; i += kThreads) {
-                const int b = i / m, k = i - b * m;
-                store128(x + base + i, sload(dpl + k * kTileStride + b));
-            }
-            if (t0 + kThreads == e0.P && tid == kThreads - 1) {
-                // the CTA holding the last block of the system also writes its last joint line
-                store128(x + e0.n - 1, sload(x_next0 + next.at(s0).row_off + e0.P));
-            }
-        }
-    }
-    // no copy may still be in flight when the CTA retires: thread 0 waits for
-    // every row (at once if the blocks' own waits saw them; bounded otherwise)
-    if (tid == 0)
-        for (int k = 1; k < m; ++k)
-            if (!mbar_wait_bounded(&bar[k], 0)) flag_error(status, kStatusTimeout);
 }
 
 // Store-mode substitution for blocks longer than the shared-memory tile: z goes
