@@ -512,8 +512,11 @@ def main():
     ap.add_argument("--arith", choices=["f64", "df64"], default="df64")
     ap.add_argument("--f64-steps", type=int, default=100,
                     help="also time the native-FP64 path for this many steps (0: skip)")
-    ap.add_argument("--block", type=int, default=0, help="level-0 block rows (0: autotune with --level-block)")
-    ap.add_argument("--level-block", type=int, default=0, help="rows per block on levels >= 1 (0: autotune)")
+    # 12 / 12: the plan autotuner's pick for this workload on B300 (its candidates are
+    # within 1 % of each other at the top, so a run-time pick would wander between
+    # them and away from the block size the committed ncu captures were taken at)
+    ap.add_argument("--block", type=int, default=12, help="level-0 block rows (0: autotune with --level-block)")
+    ap.add_argument("--level-block", type=int, default=12, help="rows per block on levels >= 1 (0: autotune)")
     ap.add_argument("--coeff-table", action="store_true",
                     help="tabulate the static diagonal part once instead of regenerating V(x) every step")
     ap.add_argument("--n", type=int, default=1 << 24, help="grid points (profiling runs use smaller grids)")
