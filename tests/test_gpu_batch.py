@@ -205,3 +205,35 @@ def test_full_size_batch_4096_systems(blocks):
         assert rel(got, oracle.cn_run(prob, init[s], nsteps)) <= 1e-11, (s, n)
     del g
     b.close()
+
+
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_many_tiny_systems(arith):
+    # 5000 systems of 3..20 rows: a single block each, many systems per CTA, RS on 2..3 rows
+    rng = np.random.default_rng(21)
+    sizes = [int(v) for v in rng.integers(3, 21, 5000)]
+    cos_a = rng.uniform(-0.5, 0.5, (len(sizes), 3))
+    parts = batch_state(sizes, seed=6)
+    b = cnb.Batch(sizes, DX, DT, pot=cnb.POT_COSSERIES, cos_a=cos_a, arith=arith)
+    out = b.step(torch.from_numpy(np.concatenate(parts)).to(DEV), 9).cpu().numpy()
+    b.check()
+    for s in rng.choice(len(sizes), 40, replace=False):
+        n = sizes[s]
+        prob = oracle.Problem(n, DX, DT, -(n // 2) * DX, pot=oracle.POT_COSSERIES, cos_a=cos_a[s], L=n * DX)
+        assert rel(out[b.offsets[s]:b.offsets[s + 1]], oracle.cn_run(prob, parts[s], 9)) <= 1e-11, (int(s), n)
+
+
+def test_batch_array_potential_with_field():
+    # CN_POT_ARRAY over the whole batch (one device array indexed like the state), a shared field
+    rng = np.random.default_rng(22)
+    sizes = [777, 3, 4100, 1500]
+    V0 = rng.uniform(-1, 1, sum(sizes))
+    E = 0.02 * np.cos(np.arange(12) * 0.4)
+    parts = batch_state(sizes, seed=7)
+    b = cnb.Batch(sizes, DX, DT, pot=cnb.POT_ARRAY, V0=torch.from_numpy(V0).to(DEV), arith=cnb.ARITH_DF64)
+    out = b.step(torch.from_numpy(np.concatenate(parts)).to(DEV), 12, E_mid=torch.from_numpy(E).to(DEV)).cpu().numpy()
+    b.check()
+    for s, n in enumerate(sizes):
+        o = int(b.offsets[s])
+        prob = oracle.Problem(n, DX, DT, -(n // 2) * DX, pot=oracle.POT_ARRAY, V0=V0[o:o + n])
+        assert rel(out[o:o + n], oracle.cn_run(prob, parts[s], 12, E_mid=E)) <= 1e-11, (s, n)
