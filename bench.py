@@ -195,7 +195,63 @@ def cpu_baseline_oracle(budget_s: float = 10.0):
     el = time.perf_counter() - t0
     return {"value": n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{steps} CN steps on a 2^21-point window of the N=2^24 soft-Coulomb grid "
-                      f"(serial FP64 Thomas, {el:.1f} s)"}
+                      f"(serial FP64 Thomas, {el:.1f} s)", **host_info()}
+
+
+def host_info() -> dict:
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
+def _oracle_system(job):
+    """Worker: the oracle's CN steps on one batched system (size, cos coefficients)."""
+    n, a, dx, dt, nsteps = job
+    import oracle
+    x_min = -(n // 2) * dx
+    prob = oracle.Problem(n, dx, dt, x_min, pot=oracle.POT_COSSERIES, cos_a=a, L=n * dx)
+    oracle.cn_run(prob, W.gaussian(n, dx, x_min, 0.0, max(1.0, 0.05 * n * dx), 0.0), nsteps)
+    return n * nsteps
+
+
+def _worker_ready(_):
+    import oracle  # noqa: F401
+    return 0
+
+
+def cpu_baseline_batched(cfg: dict, budget_s: float = 10.0) -> dict:
+    """The oracle on the batched workload, systems spread over all host cores (a
+    spawn-started process pool, after the GPU work): a random sample of the
+    systems sized to ~budget_s of wall time, 5 CN steps each, largest first."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    nsteps = 5
+    order = np.random.default_rng(3).permutation(len(cfg["sizes"]))
+    target = 2.0e6 * budget_s * cores / nsteps  # ~2e6 unknown-steps/s per core for this oracle
+    pick, tot = [], 0
+    for s in order:
+        if tot >= target:
+            break
+        pick.append(int(s))
+        tot += int(cfg["sizes"][s])
+    pick.sort(key=lambda s: -int(cfg["sizes"][s]))
+    jobs = [(int(cfg["sizes"][s]), cfg["cos_a"][s], cfg["dx"], cfg["dt"], nsteps) for s in pick]
+    procs = min(cores, len(jobs))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        pool.map(_worker_ready, range(procs), chunksize=1)  # start-up and imports, untimed
+        t0 = time.perf_counter()
+        work = sum(pool.imap_unordered(_oracle_system, jobs, chunksize=1))
+        el = time.perf_counter() - t0
+    return {"value": work / el, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{len(pick)} of the {len(cfg['sizes'])} systems ({tot} rows), {nsteps} CN steps each, "
+                      f"over {procs} processes, largest first ({el:.1f} s)", **host_info()}
 
 
 def run_reference(args):
@@ -443,7 +499,8 @@ def batched_bench(torch, cnb, args, dev):
             "eager_ms_per_step": eager_ms,
             "per_system_eager_ms_per_step": ps_ms, "per_system_graph_ms_per_step": psg_ms,
             "speedup_vs_per_system": ps_ms / ms, "speedup_vs_per_system_graph": psg_ms / ms,
-            "per_system_steps_timed": reps}
+            "per_system_steps_timed": reps,
+            "cpu_baseline": cpu_baseline_batched(cfg) if args.batched_cpu_baseline else None}
 
 
 def largest_bench(torch, cnb, args, dev):
@@ -526,6 +583,8 @@ def main():
     ap.add_argument("--batched-systems", type=int, default=4096,
                     help="batched uneven-size workload: systems (0: skip)")
     ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--no-batched-cpu-baseline", dest="batched_cpu_baseline", action="store_false",
+                    help="skip the oracle on a sample of the batched systems over all host cores")
     ap.add_argument("--batched-baseline-steps", type=int, default=3,
                     help="steps of the one-plan-per-system baseline timed")
     ap.add_argument("--largest", action="store_true",
