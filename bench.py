@@ -40,27 +40,50 @@ UNIT = "unknown-steps/s"
 WORKLOAD_STEPS = 1000  # length of the benchmarked propagation (field samples)
 PG_TIMEOUT_S = 900     # process-group timeout: longer than any phase between two collectives
 
-# Algorithmic flops per grid row of the two level-0 kernels (soft-Coulomb
-# potential regenerated on the fly, store mode), FMA = 2 flops, a reciprocal or
-# reciprocal square root = 1; m = rows per level-0 block (flops_per_row):
-#   FP64:          reduce 59 - 30/m,   substitute 16 - 14/m
-#   double-float:  reduce 548 - 261/m, substitute 150 - 128/m   (binary32 flops)
-def flops_per_row(kernel: str, arith: str, m: int) -> float:
+# Work per grid row of the two level-0 kernels (soft-Coulomb potential, store
+# mode), m = rows per level-0 block.  The static diagonal part 2 + 2 dx^2 V(x) is
+# either regenerated every step (x^2 + s, a reciprocal square root, a scale) or
+# read from a table built once (table=True).
+#
+# Flops (FMA = 2, reciprocal / rsqrt = 1), flops_per_row:
+#   FP64:          reduce 59 - 30/m (table: 54 - 30/m), substitute 16 - 14/m
+#   double-float:  reduce 548 - 261/m (table: 477 - 261/m), substitute 150 - 128/m  (binary32 flops)
+# binary32 operations of the double-float kernels (add, multiply and FMA count one
+# each: what the FP32 pipe retires per lane and clock), ops_per_row:
+#   reduce 465 - 212/m (table: 402 - 212/m), substitute 126 - 126/m
+def flops_per_row(kernel: str, arith: str, m: int, table: bool = False) -> float:
     """Flops per grid row of the level-0 kernels (FMA = 2; binary32 flops of the
     double-float formulation, binary64 flops of the FP64 one).  A block of m rows
     costs one loop body per row 2..m-1, plus its two first rows and its JD/JU and
     joint-row exchange (reduction), or one forward/back pair per interior row
     (substitution)."""
     if arith == "f64":
-        return 59.0 - 30.0 / m if kernel == "reduce_level0" else 16.0 - 14.0 / m
-    return 548.0 - 261.0 / m if kernel == "reduce_level0" else 150.0 - 128.0 / m
+        return (54.0 if table else 59.0) - 30.0 / m if kernel == "reduce_level0" else 16.0 - 14.0 / m
+    if kernel == "reduce_level0":
+        return (477.0 if table else 548.0) - 261.0 / m
+    return 150.0 - 128.0 / m
 
 
-STEP_BYTES_PER_ROW = 32.0
+def ops_per_row(kernel: str, m: int, table: bool = False) -> float:
+    """binary32 operations (add, mul, FMA: one each) per grid row of the
+    double-float level-0 kernels.  Loop row of the reduction: coefficients 93
+    (table: 30), explicit row 82, elimination 290 (complex reciprocal 44 + a
+    subtraction 22, products 44, three multiply-adds of 60); per block rows 0 and
+    1 (175, 219; table 112, 156), JD/JU 236 and the joint-row exchange 88.
+    Substitution: a forward step (22 + 44) and a back step (60) per interior row."""
+    if kernel == "reduce_level0":
+        return (402.0 if table else 465.0) - 212.0 / m
+    return 126.0 - 126.0 / m
+
+
+STEP_BYTES_PER_ROW = 32.0   # read psi_n, write psi_n+1
+TABLE_BYTES_PER_ROW = 8.0   # read the tabulated static diagonal part (double-float)
 # Recipe nominal FP64 rate of a B300 (MEASURED_PEAKS.json carries no FP64 figure).
 FP64_NOMINAL_TFLOPS = 1.25
-# FP32 issue peak: 148 SMs x 128 lanes x 2 flops x 2.032 GHz.
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# FP32 pipe peak: 148 SMs x 128 lanes x 2.032 GHz binary32 operations per second
+# (x 2 flops when every operation is an FMA).
+FP32_PEAK_TOPS = 148 * 128 * 2.032e9 / 1e12
+FP32_PEAK_TFLOPS = 2 * FP32_PEAK_TOPS
 
 
 def max_over_ranks(dist, value: float, device) -> float:
@@ -105,21 +128,23 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_class: str, arith: str, n: int, m: int):
-    """DRAM bytes per launch of a level-0 kernel with block m from the committed
-    ncu summary (profiles/traffic.txt), scaled to n rows; None if absent or if
-    the kernel sources changed since the capture."""
+def ncu_traffic(kernel_class: str, arith: str, n: int, m: int, table: bool = False):
+    """DRAM bytes per launch of a level-0 kernel with block m (coefficients
+    regenerated or tabulated) from the committed ncu summary
+    (profiles/traffic.txt), scaled to n rows; None if absent or if the kernel
+    sources changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         lines = open(path).read().splitlines()
     except OSError:
         return None
     src = kernel_source_hash()
+    coeff = "table" if table else "regen"
     for ln in lines:
         parts = ln.split()
-        if len(parts) >= 6 and not ln.startswith("#"):
-            cls, ar, rows, byts, hsh, blk = parts[:6]
-            if cls == kernel_class and ar == arith and hsh == src and int(blk) == m:
+        if len(parts) >= 7 and not ln.startswith("#"):
+            cls, ar, co, rows, byts, hsh, blk = parts[:7]
+            if cls == kernel_class and ar == arith and co == coeff and hsh == src and int(blk) == m:
                 return float(byts) * n / float(rows)
     return None
 
@@ -345,24 +370,33 @@ def time_steps(torch, plan, psi0, E, steps, warmup, dist, dev, sample_clocks):
     return ms, prof, (clk.summary() if clk else None)
 
 
-def roofline(prof, n, arith, peaks, m):
+def roofline(prof, n, arith, peaks, m, table=False):
     dom = max(("reduce_level0", "substitute_level0"), key=lambda c: prof[c][0])
     dom_ms, dom_launches = prof[dom]
     avg_s = dom_ms * 1e-3 / max(dom_launches, 1)
+    fl = flops_per_row(dom, arith, m, table)
     if arith == "f64":
-        achieved = flops_per_row(dom, arith, m) * n / avg_s / 1e12
+        achieved = fl * n / avg_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_NOMINAL_TFLOPS,
                 "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table; no FP64 figure in MEASURED_PEAKS.json)",
                 "basis": "algorithmic FP64 flops per grid row (FMA = 2)"}
     else:
-        achieved = flops_per_row(dom, arith, m) * n / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS,
-                "peak_source": "FP32 issue peak 148 SM x 128 lanes x 2 x 2.032 GHz (recipe unit counts and clock)",
-                "basis": "binary32 flops (FMA = 2) of the double-float formulation per grid row"}
-    roof.update({"kernel": dom, "avg_launch_ms": avg_s * 1e3, "flops_per_row": flops_per_row(dom, arith, m),
-                 "traffic": ncu_traffic(dom, arith, n, m)})
+        # The double-float kernels are bound by the FP32 pipe's operation rate:
+        # mostly additions (the error-free transformations), so the flop rate with
+        # FMA = 2 understates how busy the pipe is; both are given.
+        ops = ops_per_row(dom, m, table)
+        achieved = ops * n / avg_s / 1e12
+        tflops = fl * n / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TOPS, "unit": "Top/s",
+                "frac": achieved / FP32_PEAK_TOPS,
+                "peak_source": "FP32 pipe peak 148 SM x 128 lanes x 2.032 GHz (recipe unit counts and clock)",
+                "basis": "binary32 operations (add, mul, FMA: one each) of the double-float formulation per grid row",
+                "ops_per_row": ops,
+                "flops": {"achieved": tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                          "frac": tflops / FP32_PEAK_TFLOPS, "basis": "binary32 flops, FMA = 2"}}
+    roof.update({"kernel": dom, "avg_launch_ms": avg_s * 1e3, "flops_per_row": fl,
+                 "traffic": ncu_traffic(dom, arith, n, m, table)})
     return roof
 
 
@@ -376,7 +410,8 @@ def adjoint_ratio(torch, cnb, args, dev):
     tf = nsteps * cfg["dt"]
     arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
     plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith,
-                    block=args.block, level_block=args.level_block)
+                    block=args.block, level_block=args.level_block,
+                    flags=cnb.FLAG_COEFF_TABLE if args.coeff_table else 0)
     psi0 = torch.from_numpy(W.initial_state(cfg)).to(dev)
     u0 = torch.from_numpy(W.initial_controls(nc, tf)).to(dev)
     wt = torch.from_numpy(W.outside_mask_weights(n, cfg["dx"], cfg["loss_cut"])).to(dev)
@@ -397,7 +432,8 @@ def adjoint_ratio(torch, cnb, args, dev):
     plan.check()
     plan.close()
     return {"workload": "soft_coulomb_laser_1d_gradient", "n": n, "steps": nsteps, "controls": nc,
-            "dtype": args.arith, "forward_ms": fw[-1], "backward_ms": bw[-1], "ratio": bw[-1] / fw[-1],
+            "dtype": args.arith, "coefficients": "static part tabulated once" if args.coeff_table else "regenerated",
+            "forward_ms": fw[-1], "backward_ms": bw[-1], "ratio": bw[-1] / fw[-1],
             "grad_norm": float(torch.linalg.norm(u.grad).item()), "loss": float(loss.item()),
             "checkpoints": int(np.ceil(np.sqrt(nsteps)))}
 
@@ -554,7 +590,7 @@ def largest_bench(torch, cnb, args, dev):
                        "coefficients": "regenerated from V(x) and E(t) every step",
                        "state": "64 GiB complex128, in place (store mode)"},
             "levels": info["level_rows"], "workspace_bytes": info["workspace_bytes"],
-            "roofline": roofline(prof, n, args.arith, peaks, m0),
+            "roofline": roofline(prof, n, args.arith, peaks, m0, False),
             "roofline_hbm": {"bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
                              "frac": hbm / hbm_peak, "basis": "32 B per unknown-step (read psi, write psi')"},
             "kernel_ms_3_steps": {k: v[0] for k, v in prof.items()}, "clocks": clk.summary()}
@@ -574,8 +610,10 @@ def main():
     # them and away from the block size the committed ncu captures were taken at)
     ap.add_argument("--block", type=int, default=12, help="level-0 block rows (0: autotune with --level-block)")
     ap.add_argument("--level-block", type=int, default=12, help="rows per block on levels >= 1 (0: autotune)")
-    ap.add_argument("--coeff-table", action="store_true",
-                    help="tabulate the static diagonal part once instead of regenerating V(x) every step")
+    ap.add_argument("--coeff-table", dest="coeff_table", action="store_true", default=True,
+                    help="tabulate the static diagonal part 2 + 2 dx^2 V(x) once (default)")
+    ap.add_argument("--no-coeff-table", dest="coeff_table", action="store_false",
+                    help="regenerate V(x) every step instead")
     ap.add_argument("--n", type=int, default=1 << 24, help="grid points (profiling runs use smaller grids)")
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--e2e-inner", type=int, default=50, help="CN steps per end-to-end call")
@@ -659,7 +697,8 @@ def main():
         plan64.close()
         alt = {"dtype": "f64", "value": n * args.f64_steps * world / (ms64 * 1e-3), "unit": UNIT,
                "steps": args.f64_steps, "ms_per_step": ms64 / args.f64_steps,
-               "roofline": roofline(prof64, n, "f64", measured_peaks(), args.block) if rank == 0 else None}
+               "roofline": roofline(prof64, n, "f64", measured_peaks(), args.block, args.coeff_table)
+               if rank == 0 else None}
 
     adj = adjoint_ratio(torch, cnb, args, dev) if (args.adjoint_steps > 0 and rank == 0) else None
     bat = batched_bench(torch, cnb, args, dev) if (args.batched_systems > 0 and rank == 0) else None
@@ -671,11 +710,14 @@ def main():
 
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
-    roof = roofline(prof, n, args.arith, peaks, args.block)
+    roof = roofline(prof, n, args.arith, peaks, args.block, args.coeff_table)
     step_s = ms * 1e-3 / args.steps
-    hbm_achieved = STEP_BYTES_PER_ROW * n / step_s / 1e9
+    step_bytes = STEP_BYTES_PER_ROW + (TABLE_BYTES_PER_ROW if args.coeff_table else 0.0)
+    hbm_achieved = step_bytes * n / step_s / 1e9
     roof_hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": hbm_achieved / hbm_peak, "basis": "32 B per unknown-step (read psi, write psi')",
+                "frac": hbm_achieved / hbm_peak,
+                "basis": ("40 B per unknown-step (read psi and the tabulated diagonal part, write psi')"
+                          if args.coeff_table else "32 B per unknown-step (read psi, write psi')"),
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback 6400"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -40,7 +40,7 @@ def problem(n=3001, dt=0.02):
 
 
 @pytest.mark.parametrize("arith,tol", [(cnb.ARITH_F64, 1e-10), (cnb.ARITH_DF64, 1e-9)])
-@pytest.mark.parametrize("flags", [0, cnb.FLAG_RECOMPUTE])
+@pytest.mark.parametrize("flags", [0, cnb.FLAG_RECOMPUTE, cnb.FLAG_COEFF_TABLE])
 def test_adjoint_steps_match_oracle(arith, tol, flags):
     cfg, prob = problem()
     n, nsteps = cfg["n"], 25

@@ -161,16 +161,18 @@ def _full_size_reference():
     return _FULL
 
 
-# the benchmarked configuration in every launch configuration bench.py's autotuner can pick
+# the benchmarked configuration in every launch configuration bench.py's autotuner can
+# pick, with the static diagonal part regenerated or tabulated (bench.py's default)
+@pytest.mark.parametrize("flags", [0, cnb.FLAG_COEFF_TABLE])
 @pytest.mark.parametrize("blocks", list(cnb.PLAN_TUNE_CANDIDATES))
 @pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
-def test_full_size_soft_coulomb_2pow24(arith, blocks):
-    if arith == cnb.ARITH_F64 and blocks not in ((8, 8), (12, 12)):
+def test_full_size_soft_coulomb_2pow24(arith, blocks, flags):
+    if arith == cnb.ARITH_F64 and (blocks not in ((8, 8), (12, 12)) or flags):
         pytest.skip("FP64 path: two block configurations suffice")
     f = _full_size_reference()
     cfg, nsteps, psi0, E, ref = f["cfg"], f["nsteps"], f["psi0"], f["E"], f["ref"]
     plan = cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith,
-                    block=blocks[0], level_block=blocks[1])
+                    block=blocks[0], level_block=blocks[1], flags=flags)
     out = plan.step(to_dev(psi0), nsteps, E_mid=to_dev(E)).cpu().numpy()
     plan.check()
     plan.close()
