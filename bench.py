@@ -453,6 +453,49 @@ def batch_gaussians(torch, sizes_t, offsets_t, dx, dev, seed):
     return psi
 
 
+def small_bench(torch, cnb, args, dev):
+    """Free packet, N = 4096, 100 steps (latency-bound: microseconds per step, no
+    roofline): one cn_step call of 100 steps, with the paper's P = 16 partition
+    (one level of 256-row blocks, serial RS on 17 rows) and with the default
+    hierarchy; and the oracle's full run on one host core."""
+    cfg = W.free_packet_config()
+    n, nst = cfg["n"], cfg["nsteps"]
+    psi0 = W.initial_state(cfg)
+    arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
+    out = {"workload": cfg["name"], "n": n, "steps": nst, "dtype": args.arith}
+    stream = torch.cuda.current_stream()
+    for key, kw in (("p16", {"levels": [256]}), ("default", {})):
+        plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], arith=arith, **kw)
+        psi = torch.from_numpy(psi0).to(dev)
+        res = torch.empty_like(psi)
+        for _ in range(3):
+            plan.step(psi, nst, psi_out=res, stream=stream)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            plan.step(psi, nst, psi_out=res, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        plan.check()
+        info = plan.info()
+        out[key] = {"us_per_step": 1e3 * ev0.elapsed_time(ev1) / (reps * nst), "level_rows": info["level_rows"],
+                    "launches_per_step": info["launches_per_step"]}
+        plan.close()
+    if not args.no_cpu_baseline:
+        import oracle
+        prob = oracle.Problem(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=oracle.POT_NONE)
+        t0 = time.perf_counter()
+        reps = 20
+        for _ in range(reps):
+            oracle.cn_run(prob, psi0, nst)
+        el = time.perf_counter() - t0
+        out["cpu_baseline"] = {"us_per_step": 1e6 * el / (reps * nst), "cores": 1, "kind": "oracle",
+                               "sample": f"the full 100-step run, {reps} times (serial FP64 Thomas)"}
+    return out
+
+
 def batched_bench(torch, cnb, args, dev):
     """4096 independent CN systems, sizes log-uniform in [1024, 2^20], random
     8-term cosine potentials, dx = 0.1, dt = 0.01: (block, level_block) picked
@@ -621,6 +664,8 @@ def main():
     ap.add_argument("--batched-systems", type=int, default=4096,
                     help="batched uneven-size workload: systems (0: skip)")
     ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--no-small", dest="small", action="store_false",
+                    help="skip the N = 4096 free-packet latency line")
     ap.add_argument("--no-batched-cpu-baseline", dest="batched_cpu_baseline", action="store_false",
                     help="skip the oracle on a sample of the batched systems over all host cores")
     ap.add_argument("--batched-baseline-steps", type=int, default=3,
@@ -702,6 +747,7 @@ def main():
 
     adj = adjoint_ratio(torch, cnb, args, dev) if (args.adjoint_steps > 0 and rank == 0) else None
     bat = batched_bench(torch, cnb, args, dev) if (args.batched_systems > 0 and rank == 0) else None
+    small = small_bench(torch, cnb, args, dev) if (args.small and rank == 0) else None
 
     if rank != 0:
         if dist:
@@ -741,6 +787,8 @@ def main():
         line["adjoint"] = adj
     if bat:
         line["batched"] = bat
+    if small:
+        line["small"] = small
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle()
     print(json.dumps(line), flush=True)

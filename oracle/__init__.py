@@ -18,6 +18,11 @@ parallel implementation of the Crank Nicolson algorithm".
   - ``nshape_solve``       Sec. 4.2, Eq. (iteration) (nested application).
   - ``adjoint_run``        discrete adjoint of the CN recursion (the paper
                            has no adjoint; derived from Eq. Cn_both_steps).
+  - ``slab``               (module) the CN step over block-owning ranks with
+                           the joint-line exchange, Sec. "MPI Implementation"
+                           and "Communication and masking of the JD and JU
+                           stages"; checked against ``cn_run`` on CPU thread
+                           ranks and gloo processes.
 
 Parity status: every function is pinned by ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py``; none is "parity unpinned".
