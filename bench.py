@@ -4,10 +4,14 @@ atom in a laser field, N = 2^24, dx = 0.1, dt = 0.02 (complex128 state).
 
 One bench "step" is one Crank-Nicolson time step over the whole grid: the
 coefficient generation, explicit half-step, N-shaped reduction (RD+JD, RU+JU)
-on every nesting level, the RS stage and the substitution (SS) back down, i.e.
-one cn_step(nsteps=1) call.  Field samples E(t + dt/2) follow the sin^2 pulse
-over the 1000-step run.  Inputs (two 256 MiB state buffers) are larger than
-the 126 MB L2, so no flush is needed between steps.
+on every nesting level, the RS stage and the substitution (SS) back down.  The
+timed region runs the steps through cn_step calls of --steps-per-call steps
+each (default 50: the step loop of a propagation, where one step's level-0
+substitution and the next step's level-0 reduction run as one kernel and only
+the last step of a call writes psi; 1: one call per step).  Field samples
+E(t + dt/2) follow the sin^2 pulse over the 1000-step run.  The level-0 arrays
+(state 256 MiB, kept values 512 MiB) are larger than the 126 MB L2, so no flush
+is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--arith f64|df64]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
@@ -57,6 +61,8 @@ def flops_per_row(kernel: str, arith: str, m: int, table: bool = False) -> float
     costs one loop body per row 2..m-1, plus its two first rows and its JD/JU and
     joint-row exchange (reduction), or one forward/back pair per interior row
     (substitution)."""
+    if kernel == "fused_level0":  # SS of one step + the level-0 reduction of the next
+        return flops_per_row("substitute_level0", arith, m, table) + flops_per_row("reduce_level0", arith, m, table)
     if arith == "f64":
         return (54.0 if table else 59.0) - 30.0 / m if kernel == "reduce_level0" else 16.0 - 14.0 / m
     if kernel == "reduce_level0":
@@ -71,6 +77,8 @@ def ops_per_row(kernel: str, m: int, table: bool = False) -> float:
     subtraction 22, products 44, three multiply-adds of 60); per block rows 0 and
     1 (175, 219; table 112, 156), JD/JU 236 and the joint-row exchange 88.
     Substitution: a forward step (22 + 44) and a back step (60) per interior row."""
+    if kernel == "fused_level0":
+        return ops_per_row("substitute_level0", m, table) + ops_per_row("reduce_level0", m, table)
     if kernel == "reduce_level0":
         return (402.0 if table else 465.0) - 212.0 / m
     return 126.0 - 126.0 / m
@@ -312,7 +320,8 @@ def run_reference(args):
 def workload_config(args):
     return {"workload": "soft_coulomb_laser_1d_cn", "n": getattr(args, "n", 1 << 24), "dx": 0.1, "dt": 0.02,
             "potential": "-1/sqrt(x^2+2) + x E(t)", "field": "0.05 sin^2(pi t/T) cos(0.057 t), T = 4*2pi/0.057",
-            "steps_per_bench_step": 1, "workload_steps": WORKLOAD_STEPS, "block": args.block,
+            "steps_per_bench_step": 1, "steps_per_call": getattr(args, "steps_per_call", 1),
+            "workload_steps": WORKLOAD_STEPS, "block": args.block,
             "level_block": getattr(args, "level_block", 8),
             "coefficients": "static part tabulated once" if getattr(args, "coeff_table", False)
             else "regenerated from V(x) and E(t) every step",
@@ -326,18 +335,26 @@ def make_plan(cnb, cfg, args, arith):
                     flags=cnb.FLAG_COEFF_TABLE if args.coeff_table else 0)
 
 
-def time_steps(torch, plan, psi0, E, steps, warmup, dist, dev, sample_clocks):
-    """warmup + steps single CN steps (one cn_step call each), CUDA events on the
-    launching stream; then the same steps again with per-kernel-class events
-    (cn_plan_profile) for the kernel breakdown, kept out of the timed region so
-    the event records between kernels do not inflate it.  Returns (ms, prof, clocks)."""
+def time_steps(torch, plan, psi0, E, steps, warmup, dist, dev, sample_clocks, per_call=1):
+    """warmup + steps CN steps in cn_step calls of per_call steps each (the last
+    call of a run may be shorter), CUDA events on the launching stream; then the
+    same steps again with per-kernel-class events (cn_plan_profile) for the
+    kernel breakdown, kept out of the timed region so the event records between
+    kernels do not inflate it.  Field samples E(t_k + dt/2) of the WORKLOAD_STEPS
+    run are cycled.  Returns (ms, prof, clocks)."""
     cur = torch.from_numpy(psi0).to(dev)
     stream = torch.cuda.current_stream()
-    def one_step(k):
-        j = k % WORKLOAD_STEPS
-        plan.step(cur, 1, E_mid=E[j:j + 1], psi_out=cur, stream=stream)
-    for k in range(warmup):
-        one_step(k)
+    per_call = max(1, int(per_call))
+    E_ext = torch.cat([E[:WORKLOAD_STEPS], E[:per_call]])  # any window of per_call samples is contiguous
+
+    def run(k0, count):
+        k = 0
+        while k < count:
+            c = min(per_call, count - k)
+            j = (k0 + k) % WORKLOAD_STEPS
+            plan.step(cur, c, E_mid=E_ext[j:j + c], psi_out=cur, stream=stream)
+            k += c
+    run(0, warmup)
     torch.cuda.synchronize()
     plan.check()
     if dist:
@@ -349,8 +366,7 @@ def time_steps(torch, plan, psi0, E, steps, warmup, dist, dev, sample_clocks):
     if clk:
         clk.__enter__()
     ev0.record(stream)
-    for k in range(steps):
-        one_step(warmup + k)
+    run(warmup, steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     if clk:
@@ -359,8 +375,7 @@ def time_steps(torch, plan, psi0, E, steps, warmup, dist, dev, sample_clocks):
     # kernel breakdown: same steps, per-kernel-class events on the same stream
     plan.profile(True)
     plan.profile_read()
-    for k in range(steps):
-        one_step(warmup + steps + k)
+    run(warmup + steps, steps)
     torch.cuda.synchronize()
     plan.profile(False)
     prof = plan.profile_read()
@@ -371,7 +386,7 @@ def time_steps(torch, plan, psi0, E, steps, warmup, dist, dev, sample_clocks):
 
 
 def roofline(prof, n, arith, peaks, m, table=False):
-    dom = max(("reduce_level0", "substitute_level0"), key=lambda c: prof[c][0])
+    dom = max(("reduce_level0", "substitute_level0", "fused_level0"), key=lambda c: prof.get(c, (0.0, 0))[0])
     dom_ms, dom_launches = prof[dom]
     avg_s = dom_ms * 1e-3 / max(dom_launches, 1)
     fl = flops_per_row(dom, arith, m, table)
@@ -658,6 +673,8 @@ def main():
     ap.add_argument("--no-coeff-table", dest="coeff_table", action="store_false",
                     help="regenerate V(x) every step instead")
     ap.add_argument("--n", type=int, default=1 << 24, help="grid points (profiling runs use smaller grids)")
+    ap.add_argument("--steps-per-call", type=int, default=50,
+                    help="CN steps per cn_step call in the timed region (1: one call per step)")
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--e2e-inner", type=int, default=50, help="CN steps per end-to-end call")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -716,7 +733,8 @@ def main():
         tune = {f"{a}x{c}": t for (a, c), t in tt.items()}
     plan = make_plan(cnb, cfg, args, arith)
     info = plan.info()
-    ms, prof, clocks = time_steps(torch, plan, psi0, E, args.steps, args.warmup, dist, dev, rank == 0)
+    ms, prof, clocks = time_steps(torch, plan, psi0, E, args.steps, args.warmup, dist, dev, rank == 0,
+                                  args.steps_per_call)
     value = job_rate(n * args.steps, world, ms)
 
     # end to end through the C ABI with host buffers: H2D of psi and E, inner
@@ -738,7 +756,8 @@ def main():
     alt = None
     if args.f64_steps > 0 and args.arith != "f64":
         plan64 = make_plan(cnb, cfg, args, cnb.ARITH_F64)
-        ms64, prof64, _ = time_steps(torch, plan64, psi0, E, args.f64_steps, args.warmup, dist, dev, False)
+        ms64, prof64, _ = time_steps(torch, plan64, psi0, E, args.f64_steps, args.warmup, dist, dev, False,
+                                     args.steps_per_call)
         plan64.close()
         alt = {"dtype": "f64", "value": n * args.f64_steps * world / (ms64 * 1e-3), "unit": UNIT,
                "steps": args.f64_steps, "ms_per_step": ms64 / args.f64_steps,
@@ -773,7 +792,8 @@ def main():
             "kernel_ms": {k: v[0] for k, v in prof.items()}, "kernel_launches": {k: v[1] for k, v in prof.items()},
             "kernel_timing": "per-kernel-class CUDA events on the launching stream, over a second pass of the same "
                              "steps right after the timed region (events between kernels would add gaps to it)",
-            "gpu_launches": info["launches_per_step"] * args.steps,
+            # the profiled pass repeats the timed region's call pattern launch for launch
+            "gpu_launches": sum(v[1] for v in prof.values()),
             "levels": info["level_rows"],
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * n + 8 * args.e2e_inner,
                     "d2h_bytes_per_step": 16 * n, "cn_steps_per_call": args.e2e_inner,

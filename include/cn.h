@@ -192,7 +192,10 @@ typedef struct {
     int32_t levels;                      /* reduced levels below level 0; level `levels`  */
                                          /* is solved by the RS stage (one CTA, cyclic    */
                                          /* reduction; serial for cn_plan_create_levels)  */
-    int32_t launches_per_step;           /* kernels one CN step / one solve launches      */
+    int32_t launches_per_step;           /* kernels one single-step cn_step / one solve
+                                            launches (2 levels + 1); inside a cn_step of
+                                            nsteps >= 2 in store mode a step launches one
+                                            fewer, plus one substitution per call          */
     int64_t level_rows[CN_MAX_LEVELS];   /* rows of level 0 .. levels                     */
     int32_t level_block[CN_MAX_LEVELS];  /* rows per block of level 0 .. levels-1         */
     int64_t workspace_bytes;             /* device memory the plan holds                  */
@@ -205,9 +208,11 @@ cn_status cn_plan_query(cn_plan plan, cn_plan_info* out);
  * elapsed milliseconds (ms[c]) and the number of launches (launches[c]) since
  * the previous read, and restarts the count.  Classes: 0 = level-0 reduction
  * (RD+JD+RU+JU), 1 = level-0 substitution (SS), 2 = reductions of levels >= 1,
- * 3 = substitutions of levels >= 1, 4 = RS stage.  cap = entries available in
- * ms / launches (at most 5 are written). */
-#define CN_PROFILE_CLASSES 5
+ * 3 = substitutions of levels >= 1, 4 = RS stage, 5 = level-0 SS of one step
+ * fused with the level-0 reduction of the next (cn_step with nsteps >= 2 in
+ * store mode).  cap = entries available in ms / launches (at most 6 are
+ * written). */
+#define CN_PROFILE_CLASSES 6
 cn_status cn_plan_profile(cn_plan plan, int enable);
 cn_status cn_plan_profile_read(cn_plan plan, double* ms, int64_t* launches, int32_t cap);
 

@@ -38,7 +38,8 @@ NOALLOC_MAX_N = 1048576
 # (level-0 block, level block) pairs autotune_plan tries by default
 PLAN_TUNE_CANDIDATES = tuple((m0, ml) for m0 in (8, 10, 12, 16) for ml in (8, 12, 16, 24))
 MAX_LEVELS = 24
-PROFILE_CLASSES = ("reduce_level0", "substitute_level0", "reduce_levels_ge1", "substitute_levels_ge1", "rs_stage")
+PROFILE_CLASSES = ("reduce_level0", "substitute_level0", "reduce_levels_ge1", "substitute_levels_ge1", "rs_stage",
+                   "fused_level0")
 
 
 class CNError(RuntimeError):
@@ -397,7 +398,7 @@ def autotune_batch(sizes, dx, dt, candidates=None, steps: int = 3, repeats: int 
     return m0, ml, times
 
 
-def autotune_plan(n, dx, dt, x_min, candidates=None, steps: int = 3, repeats: int = 2, **kw):
+def autotune_plan(n, dx, dt, x_min, candidates=None, steps: int = 10, repeats: int = 2, **kw):
     """Pick (block, level_block) for a single-system plan by timing `steps` CN steps
     of each candidate in place (same cost for any state; a zero state here).
     Returns (best_block, best_level_block, {candidate: ms per step})."""

@@ -141,7 +141,7 @@ void free_engine(Engine* p) {
 }
 
 // --------------------------------------------------------------- kernel timing
-enum { kProfReduce0 = 0, kProfSubst0 = 1, kProfReduceL = 2, kProfSubstL = 3, kProfBase = 4 };
+enum { kProfReduce0 = 0, kProfSubst0 = 1, kProfReduceL = 2, kProfSubstL = 3, kProfBase = 4, kProfFused0 = 5 };
 
 // Two events per record; the pool grows on demand and is reused after a read.
 bool reserve_events(Engine* p, size_t k) {
@@ -367,6 +367,7 @@ cudaError_t set_smem_limits_map(int m0, int ml) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_substitute<R, LevelSource<R>, Map, ST>, a, (int)subst_smem(ml));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute<R, Map, Grid>, a, (int)subst_smem(m0));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute_kept<R, Map>, a, (int)kept_smem(m0));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_fused<R, Map, Grid>, a, (int)kept_smem(m0));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr<R>, a, (int)cr_smem());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr_many<R>, a, (int)cr_smem());
     return e;
@@ -443,23 +444,25 @@ cudaError_t solve_arrays(Engine* p, const ArraySource& src, double2* x, cudaStre
 
 // One CN-type step of every system (level 0 generated on the fly), result in x.
 template <class R>
-cudaError_t cn_solve(Engine* p, const CNStep& s, double2* x, cudaStream_t st) {
+cudaError_t cn_reduce0(Engine* p, const CNStep& s, cudaStream_t st) {
+    typedef typename Store<R>::T ST;
+    const LevelData& L0 = p->lv[0];
+    const LevelData& L1 = p->lv[1];
+    ProfScope ps(p, kProfReduce0, st);
+    with_maps_grid(p, [&](auto a, auto b, auto gr) {
+        k_cn_reduce<R><<<grid_for(L0.total), kThreads, 0, st>>>(s, a, b, gr, L0.m, L1.m, planes_of<R>(L1),
+                                                                 slot_of<R>(L1), static_cast<ST*>(p->keep), p->status);
+    });
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t cn_subst0(Engine* p, const CNStep& s, double2* x, cudaStream_t st) {
     typedef typename Store<R>::T ST;
     const LevelData& L0 = p->lv[0];
     const LevelData& L1 = p->lv[1];
     const unsigned grid = grid_for(L0.total);
     ST* keep = static_cast<ST*>(p->keep);
-    cudaError_t e = cudaSuccess;
-    {
-        ProfScope ps(p, kProfReduce0, st);
-        with_maps_grid(p, [&](auto a, auto b, auto gr) {
-            k_cn_reduce<R><<<grid, kThreads, 0, st>>>(s, a, b, gr, L0.m, L1.m, planes_of<R>(L1), slot_of<R>(L1),
-                                                      keep, p->status);
-        });
-        e = cudaGetLastError();
-    }
-    if (e != cudaSuccess) return e;
-    if ((e = solve_levels<R>(p, st)) != cudaSuccess) return e;
     ProfScope ps(p, kProfSubst0, st);
     with_maps_grid(p, [&](auto a, auto b, auto gr) {
         if (keep && L0.m > kSmemRowsMax)
@@ -475,6 +478,35 @@ cudaError_t cn_solve(Engine* p, const CNStep& s, double2* x, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// SS of the previous step fused with the level-0 reduction of step s (store mode).
+template <class R>
+cudaError_t cn_fused0(Engine* p, const CNStep& s, cudaStream_t st) {
+    typedef typename Store<R>::T ST;
+    const LevelData& L0 = p->lv[0];
+    const LevelData& L1 = p->lv[1];
+    ProfScope ps(p, kProfFused0, st);
+    with_maps_grid(p, [&](auto a, auto b, auto gr) {
+        k_cn_fused<R><<<grid_for(L0.total), kThreads, kept_smem(L0.m), st>>>(
+            s, a, b, gr, L0.m, L1.m, x_of<R>(L1), planes_of<R>(L1), slot_of<R>(L1), static_cast<ST*>(p->keep),
+            p->status);
+    });
+    return cudaGetLastError();
+}
+
+// One CN-type step of every system (level 0 generated on the fly), result in x.
+template <class R>
+cudaError_t cn_solve(Engine* p, const CNStep& s, double2* x, cudaStream_t st) {
+    cudaError_t e = cn_reduce0<R>(p, s, st);
+    if (e == cudaSuccess) e = solve_levels<R>(p, st);
+    if (e == cudaSuccess) e = cn_subst0<R>(p, s, x, st);
+    return e;
+}
+
+// Whether consecutive steps pass psi on chip (store mode with the block staged in
+// shared memory): step k's substitution and step k + 1's level-0 reduction then
+// run as one kernel, and only the last step writes psi.
+bool fuses_steps(const Engine* p) { return p->keep != nullptr && p->lv[0].m <= kSmemRowsMax; }
+
 template <class R>
 cudaError_t cn_steps(Engine* p, const double2* in, double2* out, const double* E_mid, int64_t nsteps,
                      cudaStream_t st) {
@@ -484,6 +516,29 @@ cudaError_t cn_steps(Engine* p, const double2* in, double2* out, const double* E
         return cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st);
     }
     const bool kept = p->keep != nullptr;
+    auto step_k = [&](int64_t k, const double2* psi) {
+        CNStep s;
+        s.p = p->cnp;
+        s.psi = psi;
+        s.s = 1;
+        s.e = -1;
+        s.E_t = E_mid ? E_mid + k : nullptr;
+        s.E_e = s.E_t;
+        s.tab = p->tab;
+        return s;
+    };
+    if (fuses_steps(p)) {
+        // reduce(0), levels, [fused(k), levels] for k = 1..nsteps-1, SS(last) -> out;
+        // in is read by the first reduction only, so in == out is fine
+        cudaError_t e = cn_reduce0<R>(p, step_k(0, in), st);
+        if (e == cudaSuccess) e = solve_levels<R>(p, st);
+        for (int64_t k = 1; k < nsteps && e == cudaSuccess; ++k) {
+            e = cn_fused0<R>(p, step_k(k, nullptr), st);
+            if (e == cudaSuccess) e = solve_levels<R>(p, st);
+        }
+        if (e == cudaSuccess) e = cn_subst0<R>(p, step_k(nsteps - 1, nullptr), out, st);
+        return e;
+    }
     // Store mode: the substitution does not read psi, so every step after the
     // first updates out in place.  Recompute mode: step k writes dest(k), the
     // last step writes out, destinations alternate between out and the
@@ -496,15 +551,7 @@ cudaError_t cn_steps(Engine* p, const double2* in, double2* out, const double* E
     }
     for (int64_t k = 0; k < nsteps; ++k) {
         double2* dst = kept ? out : ((((nsteps - 1 - k) % 2) == 0) ? out : p->state);
-        CNStep s;
-        s.p = p->cnp;
-        s.psi = src;
-        s.s = 1;
-        s.e = -1;
-        s.E_t = E_mid ? E_mid + k : nullptr;
-        s.E_e = s.E_t;
-        s.tab = p->tab;
-        cudaError_t e = cn_solve<R>(p, s, dst, st);
+        cudaError_t e = cn_solve<R>(p, step_k(k, src), dst, st);
         if (e != cudaSuccess) return e;
         src = dst;
     }

@@ -795,7 +795,7 @@ template <class R> struct CNRowStream {
         i = j0;
         const R* tab = st.tab ? static_cast<const R*>(st.tab) + e.row_off : nullptr;
         cg.init(st.p, g, tab, st.p.V0 ? st.p.V0 + e.row_off : nullptr, Et, Ee, j0);
-        pm = ld(j0 - 1);
+        pm = czero<R>();  // row j0 is a joint row: its stencil term with psi_{j0-1} is the block above's
         p0 = ld(j0);
         pp = ld(j0 + 1);
     }
@@ -817,6 +817,17 @@ template <class R> struct CNRowStream {
         pp = ld(i + 2);
         cg.skip();
         ++i;
+    }
+    // the last joint row of a system (row J_P): its own share, psi beyond it 0
+    __device__ __forceinline__ void next_joint(cx<R>& a, cx<R>& d) {
+        pm = czero<R>();
+        next(a, d);
+    }
+    // the share of row J_{t+1} that only this block can form: -es psi_{J_{t+1} - 1}
+    // (called right after row J_{t+1} - 1 was produced, which left psi of that row in pm)
+    __device__ __forceinline__ cx<R> jd_d(cx<R> x) const {
+        if (es == 0) return x;
+        return es > 0 ? csub(x, pm) : cadd(x, pm);
     }
 };
 
@@ -844,6 +855,60 @@ template <class R, class Map> struct ReduceOccupancy { static constexpr int min_
 template <> struct ReduceOccupancy<df, OneSys> { static constexpr int min_blocks = 6; };
 template <> struct ReduceOccupancy<double, ManySys> { static constexpr int min_blocks = 4; };
 
+// The reduction of one level-0 block on scaled rows: RD/JD with RU/JU
+// accumulated, rows 0..g taken in order from the row source rs (rs.next(a, d):
+// row k's a~ and d^; rs.next_joint: the system's last row J_P).  The explicit
+// stencil of a joint row is split between the two blocks that meet there: the
+// block below forms the row with psi_{J-1} left out (row 0 here, and row J_P),
+// the block above adds -es psi_{J-1} to its JD part (rs.jd_d), and the two meet
+// in the next level's row.  So a block needs no state outside rows J_t..J_{t+1}.
+template <class R, class RS>
+__device__ __forceinline__ void cn_reduce_block(RS& rs, int gap, bool last, typename Store<R>::T* keep, cx<R>& A0,
+                                                cx<R>& D0, cx<R>& JUa, cx<R>& JUc, cx<R>& JUd, JDPart<R>& jd,
+                                                cx<R>& Ag, cx<R>& Dg, bool& ok) {
+    rs.next(A0, D0);
+    cx<R> a, d;
+    rs.next(a, d);  // row 1
+    cx<R> w = crcp(a, ok);
+    if (keep) {
+        sstore(keep + 2 * kThreads, d);
+        sstore(keep + 3 * kThreads, w);
+    }
+    // With b = c = -1 the RD fill-in column is a product of the same pivots
+    // as RU's Q:  b_k^RD = -prod_{i<k} w_i = -w_1 Q_{k-1}  (k >= 2, b_1 = -1),
+    // so RU's sum on row 1 is  b_1 = -1 - w_1 S,  S = sum_{k>=2} Q_k Q_{k-1},
+    // and no b^RD chain is carried.
+    const cx<R> w1 = w;
+    const cx<R> one = cfrom<R>(1.0, 0.0);
+    cx<R> dRD = d;
+    cx<R> Q = one, S = czero<R>();
+    cx<R> nd = dRD;
+    for (int k = 2; k < gap; ++k) {
+        rs.next(a, d);
+        dRD = cfma(d, w, dRD);
+        const cx<R> wk = crcp(csub(a, w), ok);
+        if (keep) {
+            sstore(keep + (2 * k) * kThreads, d);
+            sstore(keep + (2 * k + 1) * kThreads, wk);
+        }
+        const cx<R> Qk = cmul(Q, wk);
+        S = cfma(S, Qk, Q);
+        nd = cfma(nd, Qk, dRD);
+        Q = Qk;
+        w = wk;
+    }
+    // JD on row J_{t+1}: r = w_{g-1};  b = r b_{g-1} = -w_1 Q_{g-1};  a += -r;  d += r d_{g-1}
+    // JU on row J_t: r = w_1;  c = -w_1 Q_{g-1};  a += w_1 b_1 = -w_1 (1 + w_1 S);  d += w_1 d_1
+    const cx<R> wQ = cneg(cmul(w1, Q));
+    jd.b = wQ;
+    jd.a = cneg(w);
+    jd.d = rs.jd_d(cmul(w, dRD));
+    if (last) rs.next_joint(Ag, Dg);
+    JUc = wQ;
+    JUa = cneg(cmul(w1, cfma(one, w1, S)));
+    JUd = cmul(w1, nd);
+}
+
 template <class R, class Map, class Grid>
 __global__ void __launch_bounds__(kThreads, ReduceOccupancy<R, Map>::min_blocks)
 k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, LevelPlanes<R> out, LevelSlot<R>* out_slot,
@@ -869,47 +934,7 @@ k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, LevelPla
         const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
         CNRowStream<R> rs;
         rs.init(st, e, grid.at(si), J0);
-        rs.next(A0, D0);
-        cx<R> a, d;
-        rs.next(a, d);  // row 1
-        cx<R> w = crcp(a, ok);
-        if (keep) {
-            sstore(keep + 2 * kThreads, d);
-            sstore(keep + 3 * kThreads, w);
-        }
-        // With b = c = -1 the RD fill-in column is a product of the same pivots
-        // as RU's Q:  b_k^RD = -prod_{i<k} w_i = -w_1 Q_{k-1}  (k >= 2, b_1 = -1),
-        // so RU's sum on row 1 is  b_1 = -1 - w_1 S,  S = sum_{k>=2} Q_k Q_{k-1},
-        // and no b^RD chain is carried.
-        const cx<R> w1 = w;
-        const cx<R> one = cfrom<R>(1.0, 0.0);
-        cx<R> dRD = d;
-        cx<R> Q = one, S = czero<R>();
-        cx<R> nd = dRD;
-        for (int k = 2; k < gap; ++k) {
-            rs.next(a, d);
-            dRD = cfma(d, w, dRD);
-            const cx<R> wk = crcp(csub(a, w), ok);
-            if (keep) {
-                sstore(keep + (2 * k) * kThreads, d);
-                sstore(keep + (2 * k + 1) * kThreads, wk);
-            }
-            const cx<R> Qk = cmul(Q, wk);
-            S = cfma(S, Qk, Q);
-            nd = cfma(nd, Qk, dRD);
-            Q = Qk;
-            w = wk;
-        }
-        // JD on row J_{t+1}: r = w_{g-1};  b = r b_{g-1} = -w_1 Q_{g-1};  a += -r;  d += r d_{g-1}
-        // JU on row J_t: r = w_1;  c = -w_1 Q_{g-1};  a += w_1 b_1 = -w_1 (1 + w_1 S);  d += w_1 d_1
-        const cx<R> wQ = cneg(cmul(w1, Q));
-        jd.b = wQ;
-        jd.a = cneg(w);
-        jd.d = cmul(w, dRD);
-        if (t == P - 1) rs.next(Ag, Dg);
-        JUc = wQ;
-        JUa = cneg(cmul(w1, cfma(one, w1, S)));
-        JUd = cmul(w1, nd);
+        cn_reduce_block<R>(rs, gap, t == P - 1, keep, A0, D0, JUa, JUc, JUd, jd, Ag, Dg, ok);
     }
     write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, RowSink<R>(out, next.at(si), m_next),
                          out_slot);
@@ -1096,6 +1121,126 @@ k_cn_substitute_kept_gmem(Map sys, Map next, int m, const typename Store<R>::T* 
     }
     store128(x + J0, xL);
     if (t == P - 1) store128(x + J0 + gap, xR);
+}
+
+// ------------------------------------------------------------------ fused step boundary
+// Rows of a level-0 block for the reduction of step n + 1 when psi_{n+1} is still
+// on chip: rows 1..g-1 in this thread's shared-memory column, the joint rows in
+// registers (the support values xL, xR of step n).  The joint rows' stencils are
+// split as in cn_reduce_block, so rows J_t..J_{t+1} are all the block needs.
+template <class R> struct CNRowFused {
+    typedef typename Store<R>::T ST;
+    CoefGen<R> cg;
+    cx<R> pm, p0, pp;  // stencil of the next row to produce (pm = 0 on the joint rows)
+    cx<R> xR;
+    R sg, msg;
+    int es, gap, k;
+    const ST* ys;      // row j of the block at ys[j * kTileStride]
+    __device__ __forceinline__ void init(const CNStep& st, const LvlSys& e, const SysGrid& g, int64_t J0,
+                                         const ST* col, cx<R> xl, cx<R> xr, int gp) {
+        const double Et = st.E_t ? *st.E_t : 0.0, Ee = st.E_e ? *st.E_e : 0.0;
+        sg = signed_gt(st, R());
+        msg = rneg(sg);
+        es = st.e * st.s;
+        const R* tab = st.tab ? static_cast<const R*>(st.tab) + e.row_off : nullptr;
+        cg.init(st.p, g, tab, st.p.V0 ? st.p.V0 + e.row_off : nullptr, Et, Ee, J0);
+        ys = col;
+        gap = gp;
+        xR = xr;
+        k = 0;
+        pm = czero<R>();
+        p0 = xl;
+        pp = sload(ys + kTileStride);  // gap >= 2: row 1 is interior
+    }
+    __device__ __forceinline__ void next(cx<R>& a, cx<R>& d) {
+        R bt, be;
+        cg.next(bt, be);
+        a = mk(bt, msg);
+        d = explicit_row(pm, p0, pp, be, es, sg);
+        pm = p0;
+        p0 = pp;
+        ++k;
+        pp = (k + 1 < gap) ? sload(ys + (k + 1) * kTileStride) : (k + 1 == gap ? xR : czero<R>());
+    }
+    __device__ __forceinline__ void next_joint(cx<R>& a, cx<R>& d) {
+        pm = czero<R>();
+        next(a, d);
+    }
+    // the share of row J_{t+1} that only this block can form: -es psi_{J_{t+1} - 1}
+    __device__ __forceinline__ cx<R> jd_d(cx<R> x) const {
+        if (es == 0) return x;
+        const cx<R> y = sload(ys + (gap - 1) * kTileStride);
+        return es > 0 ? csub(x, y) : cadd(x, y);
+    }
+};
+
+// SS of step n and the level-0 reduction of step n + 1 in one pass over the kept
+// values: the block's psi_{n+1} never leaves the SM (no store and reload of the
+// state, no conversions to and from complex128 between the steps), and the kept
+// (d^, w) of step n are replaced by those of step n + 1 in place.  st describes
+// step n + 1; x_next0 holds the level-1 solution of step n (the support values).
+// CTAs per SM the fused kernel is compiled for (as the level-0 reduction's).
+template <class R, class Map> struct FusedOccupancy { static constexpr int min_blocks = ReduceOccupancy<R, Map>::min_blocks; };
+
+template <class R, class Map, class Grid>
+__global__ void __launch_bounds__(kThreads, FusedOccupancy<R, Map>::min_blocks)
+k_cn_fused(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, const typename Store<R>::T* x_next0,
+           LevelPlanes<R> out, LevelSlot<R>* out_slot, typename Store<R>::T* keep0, int* status) {
+    typedef typename Store<R>::T ST;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ST* ys = reinterpret_cast<ST*>(smem_raw);  // [m][kTileStride]
+    const int tid = threadIdx.x;
+    const int64_t g = (int64_t)blockIdx.x * kThreads + tid;
+    const bool active = g < sys.total();
+    if (tid == 0)
+        bulk_prefetch_l2(keep0 + (int64_t)blockIdx.x * (2 * (int64_t)m * kThreads) + 2 * kThreads,
+                         2u * (uint32_t)(m - 1) * kThreads * (uint32_t)sizeof(ST));
+    bool ok = true;
+    cx<R> JUa = czero<R>(), JUc = czero<R>(), JUd = czero<R>(), A0 = czero<R>(), D0 = czero<R>();
+    cx<R> Ag = czero<R>(), Dg = czero<R>();
+    JDPart<R> jd;
+    jd.b = czero<R>(); jd.a = czero<R>(); jd.d = czero<R>();
+    int64_t t = 0, P = 0;
+    int si = 0;
+    if (active) {
+        si = sys.find(g);
+        const LvlSys& e = sys.at(si);
+        const int64_t n = e.n;
+        P = e.P;
+        t = g - e.blk_off;
+        ST* keep = keep0 + keep_base(m);
+        const ST* x_next = x_next0 + next.at(si).row_off;
+        const int64_t J0 = joint_line(t, P, m, n);
+        const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
+        const cx<R> xL = sload(x_next + t);
+        const cx<R> xR = sload(x_next + t + 1);
+        // SS of step n: z forward, psi_{n+1} backward, both in this thread's column
+        cx<R> zp = xL;
+        cx<R> dn = sload(keep + 2 * kThreads), wn = sload(keep + 3 * kThreads);
+        for (int k = 1; k < gap; ++k) {
+            const cx<R> d = dn, w = wn;
+            if (k + 1 < gap) {
+                dn = sload(keep + (2 * k + 2) * kThreads);
+                wn = sload(keep + (2 * k + 3) * kThreads);
+            }
+            cx<R> rhs = cadd(d, zp);
+            if (k == gap - 1) rhs = cadd(rhs, xR);
+            zp = cmul(rhs, w);
+            sstore(ys + k * kTileStride + tid, zp);
+        }
+        cx<R> y = zp;
+        for (int k = gap - 2; k >= 1; --k) {
+            y = cfma(sload(ys + k * kTileStride + tid), sload(keep + (2 * k + 1) * kThreads), y);
+            sstore(ys + k * kTileStride + tid, y);
+        }
+        // reduction of step n + 1 from psi_{n+1}
+        CNRowFused<R> rs;
+        rs.init(st, e, grid.at(si), J0, ys + tid, xL, xR, gap);
+        cn_reduce_block<R>(rs, gap, t == P - 1, keep, A0, D0, JUa, JUc, JUd, jd, Ag, Dg, ok);
+    }
+    write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, RowSink<R>(out, next.at(si), m_next),
+                         out_slot);
+    if (!ok) flag_error(status, kStatusNonfinite);
 }
 
 // ------------------------------------------------------------------ adjoint step

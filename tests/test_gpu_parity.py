@@ -115,6 +115,43 @@ def test_soft_coulomb_field_100_steps(n, block, arith, flags):
     assert rel(out, ref) <= 1e-11
 
 
+@pytest.mark.parametrize("table", [0, cnb.FLAG_COEFF_TABLE])
+@pytest.mark.parametrize("block", [3, 8, 12, 32])
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_multi_step_call_matches_single_steps(arith, block, table):
+    # a cn_step of K steps runs each step's level-0 substitution fused with the next
+    # step's level-0 reduction (psi stays on chip, split joint-row stencils); K calls
+    # of one step round-trip psi through complex128 between the steps.  Binary64:
+    # the same operations in the same order, bitwise; double-float: psi keeps its
+    # ~48-bit form instead of being rounded to binary64 and back, so the two agree
+    # to rounding.  Both against the oracle as well.
+    cfg = W.soft_coulomb_config(n=20011, nsteps=24)
+    psi0 = W.initial_state(cfg)
+    E = W.field_midpoints(24, cfg["dt"], t0=60.0)
+    plan = plan_for(cfg, arith=arith, block=block, flags=table)
+    Ed = to_dev(E)
+    fused = plan.step(to_dev(psi0), 24, E_mid=Ed)
+    single = to_dev(psi0)
+    for k in range(24):
+        single = plan.step(single, 1, E_mid=Ed[k:k + 1])
+    plan.check()
+    prof = None
+    plan.profile(True)
+    plan.profile_read()
+    plan.step(to_dev(psi0), 24, E_mid=Ed)
+    prof = plan.profile_read()
+    plan.profile(False)
+    plan.close()
+    a, b = fused.cpu().numpy(), single.cpu().numpy()
+    assert prof["fused_level0"][1] == 23 and prof["reduce_level0"][1] == 1 and prof["substitute_level0"][1] == 1
+    if arith == cnb.ARITH_F64:
+        assert np.array_equal(a, b)
+    else:
+        assert rel(a, b) <= 1e-13
+    ref = oracle.cn_run(oracle_problem(cfg), psi0, 24, E_mid=E)
+    assert rel(a, ref) <= 1e-11
+
+
 @pytest.mark.parametrize("flags", [0, cnb.FLAG_RECOMPUTE])
 def test_step_in_place_and_zero_steps(flags):
     cfg = W.soft_coulomb_config(n=1000, nsteps=7)
