@@ -599,13 +599,15 @@ def batched_bench(torch, cnb, args, dev):
 
 def largest_bench(torch, cnb, args, dev):
     """The largest single system: N = 2^32 (64 GiB complex128 state), dx = 0.05,
-    dt = 0.01, soft-Coulomb atom in the field, 50 steps, coefficients regenerated
-    on the fly, blocks from the autotuner.  One JSON line of its own."""
+    dt = 0.01, soft-Coulomb atom in the field, 50 steps in one cn_step call (the
+    fused step loop), coefficients regenerated on the fly (a table would add 32 GiB
+    to the ~200 GiB the plan holds), blocks from the autotuner.  One JSON line of
+    its own."""
     cfg = W.largest_config()
     n, dx, dt, nst = cfg["n"], cfg["dx"], cfg["dt"], cfg["nsteps"]
     arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
     kw = dict(pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith)
-    m0, ml, tt = cnb.autotune_plan(n, dx, dt, cfg["x_min"], candidates=[(8, 8), (12, 12), (16, 12)], steps=2,
+    m0, ml, tt = cnb.autotune_plan(n, dx, dt, cfg["x_min"], candidates=[(8, 8), (12, 12), (16, 12)], steps=4,
                                    repeats=1, **kw)
     torch.cuda.empty_cache()
     nw = 1 << 20
@@ -616,24 +618,21 @@ def largest_bench(torch, cnb, args, dev):
     plan = cnb.Plan(n, dx, dt, cfg["x_min"], block=m0, level_block=ml, **kw)
     info = plan.info()
     stream = torch.cuda.current_stream()
-    for k in range(args.warmup):
-        plan.step(psi, 1, E_mid=E[k:k + 1], psi_out=psi, stream=stream)
+    plan.step(psi, args.warmup, E_mid=E[:args.warmup], psi_out=psi, stream=stream)
     torch.cuda.synchronize()
     uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     clk = ClockSampler(uuid)
     clk.__enter__()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for k in range(nst):
-        plan.step(psi, 1, E_mid=E[args.warmup + k:args.warmup + k + 1], psi_out=psi, stream=stream)
+    plan.step(psi, nst, E_mid=E[args.warmup:args.warmup + nst], psi_out=psi, stream=stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     clk.__exit__()
     ms = ev0.elapsed_time(ev1)
     plan.profile(True)
     plan.profile_read()
-    for k in range(3):
-        plan.step(psi, 1, E_mid=E[k:k + 1], psi_out=psi, stream=stream)
+    plan.step(psi, 3, E_mid=E[:3], psi_out=psi, stream=stream)
     prof = plan.profile_read()
     plan.check()
     plan.close()
@@ -651,6 +650,7 @@ def largest_bench(torch, cnb, args, dev):
             "roofline": roofline(prof, n, args.arith, peaks, m0, False),
             "roofline_hbm": {"bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
                              "frac": hbm / hbm_peak, "basis": "32 B per unknown-step (read psi, write psi')"},
+            "steps_per_call": nst,
             "kernel_ms_3_steps": {k: v[0] for k, v in prof.items()}, "clocks": clk.summary()}
 
 
