@@ -322,7 +322,7 @@ def workload_config(args):
             "potential": "-1/sqrt(x^2+2) + x E(t)", "field": "0.05 sin^2(pi t/T) cos(0.057 t), T = 4*2pi/0.057",
             "steps_per_bench_step": 1, "steps_per_call": getattr(args, "steps_per_call", 1),
             "workload_steps": WORKLOAD_STEPS, "block": args.block,
-            "level_block": getattr(args, "level_block", 8),
+            "level_block": getattr(args, "level_block", 8), "level1_block": getattr(args, "level1_block", 0),
             "coefficients": "static part tabulated once" if getattr(args, "coeff_table", False)
             else "regenerated from V(x) and E(t) every step",
             "arith": args.arith, "l2": "inputs larger than L2 (2 x 256 MiB states vs 126 MB L2), no flush",
@@ -332,6 +332,7 @@ def workload_config(args):
 def make_plan(cnb, cfg, args, arith):
     return cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0,
                     block=args.block, arith=arith, level_block=args.level_block,
+                    level1_block=getattr(args, "level1_block", 0),
                     flags=cnb.FLAG_COEFF_TABLE if args.coeff_table else 0)
 
 
@@ -668,6 +669,8 @@ def main():
     # them and away from the block size the committed ncu captures were taken at)
     ap.add_argument("--block", type=int, default=12, help="level-0 block rows (0: autotune with --level-block)")
     ap.add_argument("--level-block", type=int, default=12, help="rows per block on levels >= 1 (0: autotune)")
+    # level 1 in blocks of 10: 0.502 vs 0.506 ms per step at 12 (swept 10..24 with level blocks 8 and 12)
+    ap.add_argument("--level1-block", type=int, default=10, help="rows per block on level 1 alone (0: --level-block)")
     ap.add_argument("--coeff-table", dest="coeff_table", action="store_true", default=True,
                     help="tabulate the static diagonal part 2 + 2 dx^2 V(x) once (default)")
     ap.add_argument("--no-coeff-table", dest="coeff_table", action="store_false",

@@ -87,6 +87,9 @@ typedef struct {
     int32_t flags;           /* CN_FLAG_* bits                                               */
     int32_t level_block;     /* rows per block on the reduced levels (Eq. iteration): 3..32;
                                 0 = default (8)                                              */
+    int32_t level1_block;    /* rows per block on level 1 alone: 3..32; 0 = level_block.  Lets
+                                the largest reduced level fill whole waves of the GPU while
+                                the small levels keep short serial chains                    */
 } cn_desc;
 
 /* cn_desc.flags: tabulate the static part of the diagonal, 2 + 2 dx^2 Vs(x_j),
@@ -103,8 +106,9 @@ typedef struct {
 #define CN_FLAG_RECOMPUTE 2
 
 /* Create a plan for systems of size desc->n.  The N-shaped solve is nested
- * (Eq. iteration): level 0 is cut into blocks of desc->block rows, each reduced
- * level into blocks of desc->level_block rows, until a level has at most 1024
+ * (Eq. iteration): level 0 is cut into blocks of desc->block rows, level 1 into
+ * blocks of desc->level1_block rows (if nonzero), every other reduced level into
+ * blocks of desc->level_block rows, until a level has at most 1024
  * rows; that system (the RS stage) is solved inside one CTA by cyclic
  * reduction.  Allocates the device workspace on the current device: the
  * reduced systems of every level (~80 B per row of level 1 and below), 32 B
@@ -123,7 +127,8 @@ cn_status cn_plan_create(const cn_desc* desc, cn_plan* out);
  *   blocks: host int32[nlevels], each 3 .. CN_LEVELS_MAX_BLOCK; blocks longer
  *     than 32 rows take a substitution that stages its values in device
  *     scratch instead of shared memory (the plan allocates it);
- *   desc: as for cn_plan_create; desc->block and desc->level_block are ignored.
+ *   desc: as for cn_plan_create; desc->block, desc->level_block and
+ *     desc->level1_block are ignored.
  * Returns CN_ERR_INVALID_ARG if some level i < nlevels has fewer than 3 rows,
  * and CN_ERR_UNSUPPORTED for CN_FLAG_RECOMPUTE with blocks[0] > 32.  The plan
  * is used with every cn_plan_* / cn_step* / cn_solve_tridiag / cn_adjoint_step

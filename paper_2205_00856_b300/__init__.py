@@ -52,7 +52,7 @@ class _Desc(C.Structure):
     _fields_ = [("n", C.c_int64), ("dx", C.c_double), ("dt", C.c_double), ("x_min", C.c_double),
                 ("pot", C.c_int32), ("n_cos", C.c_int32), ("V0", C.c_void_p), ("soft_s", C.c_double),
                 ("cos_a", C.c_void_p), ("L", C.c_double), ("block", C.c_int32), ("arith", C.c_int32),
-                ("flags", C.c_int32), ("level_block", C.c_int32)]
+                ("flags", C.c_int32), ("level_block", C.c_int32), ("level1_block", C.c_int32)]
 
 
 class _Info(C.Structure):
@@ -149,11 +149,13 @@ class Plan:
     H = -1/2 d^2/dx^2 + Vs(x) + x E(t) on x_j = x_min + j dx.
     levels: explicit nesting (cn_plan_create_levels): the block size of each
     reduced level, the last level solved serially whatever its size; None
-    nests with block / level_block until the reduced system has <= 16 rows.
+    nests with block (level 0) / level1_block (level 1; 0: level_block) /
+    level_block until the reduced system has <= 1024 rows, which is solved by
+    cyclic reduction.
     """
 
     def __init__(self, n, dx, dt, x_min, pot=POT_NONE, V0=None, soft_s=2.0, cos_a=None, L=1.0,
-                 block=0, arith=ARITH_F64, flags=0, level_block=0, levels=None):
+                 block=0, arith=ARITH_F64, flags=0, level_block=0, levels=None, level1_block=0):
         import torch
         self._lib = load()
         self.n = int(n)
@@ -168,7 +170,7 @@ class Plan:
         d = _Desc(self.n, float(dx), float(dt), float(x_min), int(pot),
                   0 if self._cos is None else len(self._cos), v0p, float(soft_s),
                   None if self._cos is None else self._cos.ctypes.data, float(L), int(block), self.arith,
-                  int(flags), int(level_block))
+                  int(flags), int(level_block), int(level1_block))
         h = C.c_void_p()
         if levels is None:
             _check(self._lib.cn_plan_create(C.byref(d), C.byref(h)), "cn_plan_create")
@@ -293,7 +295,7 @@ class Batch:
     """
 
     def __init__(self, sizes, dx, dt, x_min=None, pot=POT_NONE, V0=None, soft_s=2.0, cos_a=None, L=0.0,
-                 block=0, arith=ARITH_F64, flags=0, level_block=0):
+                 block=0, arith=ARITH_F64, flags=0, level_block=0, level1_block=0):
         import torch
         self._lib = load()
         self.sizes = np.ascontiguousarray(sizes, dtype=np.int64)
@@ -314,7 +316,7 @@ class Batch:
         if pot == POT_ARRAY:
             v0p = _dev_ptr(V0, torch.float64, int(self.sizes.sum()), "V0")
         d = _Desc(0, float(dx), float(dt), 0.0, int(pot), n_cos, v0p, float(soft_s), None, float(L), int(block),
-                  self.arith, int(flags), int(level_block))
+                  self.arith, int(flags), int(level_block), int(level1_block))
         h = C.c_void_p()
         _check(self._lib.cn_batch_create(C.byref(d), self.nsys, self.sizes.ctypes.data,
                                          None if xm is None else xm.ctypes.data,

@@ -111,6 +111,7 @@ cn_status validate_desc(const cn_desc* d, bool need_n) {
     }
     if (d->block != 0 && (d->block < 3 || d->block > kMaxBlockRows)) return CN_ERR_INVALID_ARG;
     if (d->level_block != 0 && (d->level_block < 3 || d->level_block > kMaxBlockRows)) return CN_ERR_INVALID_ARG;
+    if (d->level1_block != 0 && (d->level1_block < 3 || d->level1_block > kMaxBlockRows)) return CN_ERR_INVALID_ARG;
     if (d->arith != CN_ARITH_F64 && d->arith != CN_ARITH_DF64) return CN_ERR_INVALID_ARG;
     if ((d->flags & ~(CN_FLAG_COEFF_TABLE | CN_FLAG_RECOMPUTE)) != 0) return CN_ERR_INVALID_ARG;
     return CN_OK;
@@ -203,7 +204,8 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
         const int l = (int)p->lv.size();
         if (l >= CN_MAX_LEVELS) return cudaErrorInvalidValue;
         LevelData L;
-        L.m = nlev ? (l < nlev ? p->lvl_m[(size_t)l] : 0) : p->desc.level_block;
+        L.m = nlev ? (l < nlev ? p->lvl_m[(size_t)l] : 0)
+                   : ((l == 1 && p->desc.level1_block) ? p->desc.level1_block : p->desc.level_block);
         L.sys.resize(ns);
         int64_t roff = 0, boff = 0, soff = 0;
         for (int s = 0; s < ns; ++s) {
@@ -739,6 +741,7 @@ cn_status cn_plan_create_levels(const cn_desc* desc, int32_t nlevels, const int3
     cn_desc d = *desc;
     d.block = 0;
     d.level_block = 0;
+    d.level1_block = 0;
     cn_status v = validate_desc(&d, true);
     if (v != CN_OK) return v;
     cn_plan p = new (std::nothrow) cn_plan_s();

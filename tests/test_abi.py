@@ -41,7 +41,7 @@ def test_status_strings_and_version():
 
 def _desc(**kw):
     d = dict(n=100, dx=0.1, dt=0.01, x_min=0.0, pot=0, n_cos=0, V0=None, soft_s=2.0, cos_a=None, L=1.0,
-             block=0, arith=0, flags=0, level_block=0)
+             block=0, arith=0, flags=0, level_block=0, level1_block=0)
     d.update(kw)
     return cnb._Desc(*[d[f] for f, _ in cnb._Desc._fields_])
 
@@ -49,7 +49,8 @@ def _desc(**kw):
 @pytest.mark.parametrize("kw", [dict(n=2), dict(n=-5), dict(dx=0.0), dict(dx=float("nan")), dict(dt=0.0),
                                 dict(pot=9), dict(pot=1), dict(pot=2, soft_s=0.0), dict(pot=3, n_cos=17, L=1.0),
                                 dict(pot=3, n_cos=2, L=1.0), dict(block=2), dict(block=33), dict(arith=3),
-                                dict(flags=4), dict(level_block=2), dict(level_block=40)])
+                                dict(flags=4), dict(level_block=2), dict(level_block=40), dict(level1_block=2),
+                                dict(level1_block=33)])
 def test_invalid_descriptor_rejected_on_host(kw):
     lib = cnb.load()
     h = C.c_void_p()
