@@ -126,10 +126,12 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the headers that define the kernels (their code, launch bounds and
+    layouts); the host launch code in the .cu files is not part of it."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2205_00856_b300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name.endswith(".cuh"):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode())
                 h.update(f.read())
