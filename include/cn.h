@@ -148,6 +148,16 @@ cn_status cn_plan_destroy(cn_plan plan);
 cn_status cn_step(cn_plan plan, const void* psi_in, void* psi_out, const double* E_mid,
                   int64_t nsteps, void* stream);
 
+/* As cn_step, but every step's result is kept: step k (k = 0 .. nsteps-1)
+ * writes psi_{k+1} to states_out + k n (device, complex128[nsteps n], the
+ * states back to back) -- what a backward pass that recomputes a segment of a
+ * propagation needs.  psi_in must not overlap states_out (CN_ERR_INVALID_ARG).
+ * In double-float store mode the steps run as in cn_step's step loop (psi
+ * stays on chip from one step to the next; the stored state is its complex128
+ * rounding), so states_out[nsteps-1] equals cn_step's result bitwise. */
+cn_status cn_step_states(cn_plan plan, const void* psi_in, void* states_out, const double* E_mid,
+                         int64_t nsteps, void* stream);
+
 /* As cn_step, with psi_in, psi_out and E_mid in HOST memory (pageable or
  * pinned).  The host-to-device copies, the steps and the device-to-host copy
  * are enqueued on `stream`; the call synchronises the stream before it

@@ -33,7 +33,7 @@ EXPORTS = ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_s
            "cn_plan_query", "cn_plan_profile", "cn_plan_profile_read", "cn_plan_status", "cn_status_string",
            "cn_version", "cn_solve_tridiag_noalloc", "cn_adjoint_step", "cn_field_from_controls",
            "cn_field_grad_to_controls", "cn_batch_create", "cn_batch_destroy", "cn_batch_offsets",
-           "cn_batch_step", "cn_batch_status", "cn_plan_create_levels")
+           "cn_batch_step", "cn_batch_status", "cn_plan_create_levels", "cn_step_states")
 NOALLOC_MAX_N = 1048576
 # (level-0 block, level block) pairs autotune_plan tries by default
 PLAN_TUNE_CANDIDATES = tuple((m0, ml) for m0 in (8, 10, 12, 16) for ml in (8, 12, 16, 24))
@@ -83,6 +83,8 @@ def load(build_if_missing: bool = True):
             lib.cn_plan_create.argtypes = [C.POINTER(_Desc), C.POINTER(vp)]
             lib.cn_plan_destroy.argtypes = [vp]
             lib.cn_step.argtypes = [vp, vp, vp, vp, i64, vp]
+            lib.cn_step_states.argtypes = [vp, vp, vp, vp, i64, vp]
+            lib.cn_step_states.restype = C.c_int
             lib.cn_step_host.argtypes = [vp, vp, vp, vp, i64, vp]
             lib.cn_solve_tridiag.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
             lib.cn_plan_status.argtypes = [vp]
@@ -205,6 +207,23 @@ class Plan:
             pe = _dev_ptr(E_mid, torch.float64, E_mid.numel(), "E_mid")
         _check(self._lib.cn_step(self._h, pin, pout, pe, int(nsteps), _stream_handle(stream)), "cn_step")
         return psi_out
+
+    def step_states(self, psi_in, nsteps: int, E_mid=None, states_out=None, stream=None):
+        """nsteps CN steps keeping every result: states_out[k] = psi after step k
+        ((nsteps, n) complex128, allocated if None; must not overlap psi_in)."""
+        import torch
+        pin = _dev_ptr(psi_in, torch.complex128, self.n, "psi_in")
+        if states_out is None:
+            states_out = torch.empty((int(nsteps), self.n), dtype=torch.complex128, device=psi_in.device)
+        pst = _dev_ptr(states_out, torch.complex128, int(nsteps) * self.n, "states_out")
+        pe = None
+        if E_mid is not None:
+            if E_mid.numel() < nsteps:
+                raise ValueError("E_mid shorter than nsteps")
+            pe = _dev_ptr(E_mid, torch.float64, E_mid.numel(), "E_mid")
+        _check(self._lib.cn_step_states(self._h, pin, pst, pe, int(nsteps), _stream_handle(stream)),
+               "cn_step_states")
+        return states_out
 
     def step_host(self, psi_in, nsteps: int, E_mid=None, psi_out=None, stream=None):
         """nsteps CN steps on host arrays (numpy or CPU tensors, pinned or not)."""

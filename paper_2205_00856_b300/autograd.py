@@ -57,8 +57,8 @@ class _SegmentGraphs:
         self.fwd = _capture(lambda: plan.step(self.state, K, E_mid=self.E, psi_out=self.state))
 
         def bwd():
-            for k in range(K):
-                plan.step(self.seg[k], 1, E_mid=self.E[k:], psi_out=self.seg[k + 1])
+            # the segment's states, every one kept (the steps run as in the forward pass)
+            plan.step_states(self.seg[0], K, E_mid=self.E, states_out=self.seg[1:])
             for k in range(K - 1, -1, -1):
                 plan.adjoint_step(self.seg[k], self.seg[k + 1], self.lam, self.g[k:k + 1], E_mid=self.E[k:k + 1],
                                   lam_n=self.lam)
@@ -120,8 +120,7 @@ class CNPropagate(torch.autograd.Function):
                 G.bwd.replay()
                 gE[s0:s1].copy_(G.g)
                 continue
-            for k in range(s1 - s0):
-                plan.step(seg[k], 1, E_mid=E[s0 + k:], psi_out=seg[k + 1])
+            plan.step_states(seg[0], s1 - s0, E_mid=E[s0:], states_out=seg[1:s1 - s0 + 1])
             for nn in range(s1 - 1, s0 - 1, -1):
                 k = nn - s0
                 plan.adjoint_step(seg[k], seg[k + 1], lam, gE[nn:nn + 1], E_mid=E[nn:nn + 1], lam_n=lam)

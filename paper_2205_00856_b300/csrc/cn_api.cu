@@ -369,7 +369,8 @@ cudaError_t set_smem_limits_map(int m0, int ml) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_substitute<R, LevelSource<R>, Map, ST>, a, (int)subst_smem(ml));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute<R, Map, Grid>, a, (int)subst_smem(m0));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute_kept<R, Map>, a, (int)kept_smem(m0));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_fused<R, Map, Grid>, a, (int)kept_smem(m0));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_fused<R, Map, Grid, false>, a, (int)kept_smem(m0));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_fused<R, Map, Grid, true>, a, (int)kept_smem(m0));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr<R>, a, (int)cr_smem());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr_many<R>, a, (int)cr_smem());
     return e;
@@ -480,17 +481,21 @@ cudaError_t cn_subst0(Engine* p, const CNStep& s, double2* x, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// SS of the previous step fused with the level-0 reduction of step s (store mode).
+// SS of the previous step fused with the level-0 reduction of step s (store mode);
+// x_out != NULL also receives the previous step's result.
 template <class R>
-cudaError_t cn_fused0(Engine* p, const CNStep& s, cudaStream_t st) {
+cudaError_t cn_fused0(Engine* p, const CNStep& s, double2* x_out, cudaStream_t st) {
     typedef typename Store<R>::T ST;
     const LevelData& L0 = p->lv[0];
     const LevelData& L1 = p->lv[1];
     ProfScope ps(p, kProfFused0, st);
     with_maps_grid(p, [&](auto a, auto b, auto gr) {
-        k_cn_fused<R><<<grid_for(L0.total), kThreads, kept_smem(L0.m), st>>>(
-            s, a, b, gr, L0.m, L1.m, x_of<R>(L1), planes_of<R>(L1), slot_of<R>(L1), static_cast<ST*>(p->keep),
-            p->status);
+        typedef decltype(a) M;
+        typedef decltype(gr) G;
+        auto kern = x_out ? k_cn_fused<R, M, G, true> : k_cn_fused<R, M, G, false>;
+        kern<<<grid_for(L0.total), kThreads, kept_smem(L0.m), st>>>(s, a, b, gr, L0.m, L1.m, x_of<R>(L1),
+                                                                    planes_of<R>(L1), slot_of<R>(L1),
+                                                                    static_cast<ST*>(p->keep), x_out, p->status);
     });
     return cudaGetLastError();
 }
@@ -513,15 +518,20 @@ bool fuses_steps(const Engine* p) {
     return p->keep != nullptr && p->lv[0].m <= kSmemRowsMax && p->desc.arith == CN_ARITH_DF64;
 }
 
+// nsteps CN steps from in; the result goes to out, or with states != NULL every
+// step's result to states + k rows (k = 0 .. nsteps-1; in must not lie in states).
 template <class R>
 cudaError_t cn_steps(Engine* p, const double2* in, double2* out, const double* E_mid, int64_t nsteps,
-                     cudaStream_t st) {
-    const size_t bytes = sizeof(double2) * (size_t)p->lv[0].rows_total;
+                     cudaStream_t st, double2* states = nullptr) {
+    const int64_t rows = p->lv[0].rows_total;
+    const size_t bytes = sizeof(double2) * (size_t)rows;
     if (nsteps == 0) {
-        if (in == out) return cudaSuccess;
+        if (in == out || states) return cudaSuccess;
         return cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st);
     }
     const bool kept = p->keep != nullptr;
+    auto state_k = [&](int64_t k) { return states + k * rows; };
+    if (states) out = state_k(nsteps - 1);
     auto step_k = [&](int64_t k, const double2* psi) {
         CNStep s;
         s.p = p->cnp;
@@ -539,11 +549,20 @@ cudaError_t cn_steps(Engine* p, const double2* in, double2* out, const double* E
         cudaError_t e = cn_reduce0<R>(p, step_k(0, in), st);
         if (e == cudaSuccess) e = solve_levels<R>(p, st);
         for (int64_t k = 1; k < nsteps && e == cudaSuccess; ++k) {
-            e = cn_fused0<R>(p, step_k(k, nullptr), st);
+            e = cn_fused0<R>(p, step_k(k, nullptr), states ? state_k(k - 1) : nullptr, st);
             if (e == cudaSuccess) e = solve_levels<R>(p, st);
         }
         if (e == cudaSuccess) e = cn_subst0<R>(p, step_k(nsteps - 1, nullptr), out, st);
         return e;
+    }
+    if (states) {  // every step writes its own state; recompute mode reads the previous one
+        const double2* src = in;
+        for (int64_t k = 0; k < nsteps; ++k) {
+            cudaError_t e = cn_solve<R>(p, step_k(k, src), state_k(k), st);
+            if (e != cudaSuccess) return e;
+            src = state_k(k);
+        }
+        return cudaSuccess;
     }
     // Store mode: the substitution does not read psi, so every step after the
     // first updates out in place.  Recompute mode: step k writes dest(k), the
@@ -671,15 +690,23 @@ cn_status create_engine(Engine* p, const cn_desc* desc, const std::vector<int64_
     return CN_OK;
 }
 
-cn_status run_steps(Engine* p, const void* psi_in, void* psi_out, const double* E_mid, int64_t nsteps, void* stream) {
-    if (!psi_in || !psi_out || nsteps < 0) return CN_ERR_INVALID_ARG;
-    if (!aligned16(psi_in) || !aligned16(psi_out)) return CN_ERR_INVALID_ARG;
+cn_status run_steps(Engine* p, const void* psi_in, void* psi_out, const double* E_mid, int64_t nsteps, void* stream,
+                    void* states = nullptr) {
+    if (!psi_in || (!psi_out && !states) || nsteps < 0) return CN_ERR_INVALID_ARG;
+    if (!aligned16(psi_in) || (psi_out && !aligned16(psi_out)) || (states && !aligned16(states)))
+        return CN_ERR_INVALID_ARG;
     if (E_mid && !aligned8(E_mid)) return CN_ERR_INVALID_ARG;
+    if (states) {  // psi_in must not lie inside the states
+        const uintptr_t a = reinterpret_cast<uintptr_t>(psi_in), s0 = reinterpret_cast<uintptr_t>(states);
+        const uintptr_t len = sizeof(double2) * (uintptr_t)p->lv[0].rows_total;
+        if (a + len > s0 && a < s0 + len * (uintptr_t)nsteps) return CN_ERR_INVALID_ARG;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const double2* in = static_cast<const double2*>(psi_in);
     double2* out = static_cast<double2*>(psi_out);
-    cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? cn_steps<df>(p, in, out, E_mid, nsteps, st)
-                                                     : cn_steps<double>(p, in, out, E_mid, nsteps, st);
+    double2* sts = static_cast<double2*>(states);
+    cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? cn_steps<df>(p, in, out, E_mid, nsteps, st, sts)
+                                                     : cn_steps<double>(p, in, out, E_mid, nsteps, st, sts);
     return cuda_status(e);
 }
 
@@ -767,6 +794,12 @@ cn_status cn_plan_destroy(cn_plan p) {
 cn_status cn_step(cn_plan p, const void* psi_in, void* psi_out, const double* E_mid, int64_t nsteps, void* stream) {
     if (!p) return CN_ERR_INVALID_ARG;
     return run_steps(p, psi_in, psi_out, E_mid, nsteps, stream);
+}
+
+cn_status cn_step_states(cn_plan p, const void* psi_in, void* states_out, const double* E_mid, int64_t nsteps,
+                         void* stream) {
+    if (!p || !states_out) return CN_ERR_INVALID_ARG;
+    return run_steps(p, psi_in, nullptr, E_mid, nsteps, stream, states_out);
 }
 
 cn_status cn_step_host(cn_plan p, const void* psi_in_host, void* psi_out_host, const double* E_mid_host,

@@ -1059,6 +1059,8 @@ k_cn_substitute_kept(Map sys, Map next, int m, const typename Store<R>::T* keep0
                 y = cfma(sload(zs + k * kTileStride + tid), sload(keep + (2 * k + 1) * kThreads), y);
                 sstore(zs + k * kTileStride + tid, y);
             }
+            // the system's last row J_P lies past the tile (n - 1 = P m here)
+            if (t == P - 1) store128(x + J0 + gap, xR);
         } else {
             store128(x + J0 + gap - 1, y);
             for (int k = gap - 2; k >= 1; --k) {
@@ -1174,27 +1176,44 @@ template <class R> struct CNRowFused {
     }
 };
 
+// CTAs per SM the fused kernel is compiled for (as the level-0 reduction's: 6 for
+// double-float single systems, measured best against 5 and 4).
+template <class R, class Map> struct FusedOccupancy { static constexpr int min_blocks = ReduceOccupancy<R, Map>::min_blocks; };
+
 // SS of step n and the level-0 reduction of step n + 1 in one pass over the kept
 // values: the block's psi_{n+1} never leaves the SM (no store and reload of the
 // state, no conversions to and from complex128 between the steps), and the kept
 // (d^, w) of step n are replaced by those of step n + 1 in place.  st describes
 // step n + 1; x_next0 holds the level-1 solution of step n (the support values).
-// CTAs per SM the fused kernel is compiled for (as the level-0 reduction's).
-template <class R, class Map> struct FusedOccupancy { static constexpr int min_blocks = ReduceOccupancy<R, Map>::min_blocks; };
-
-template <class R, class Map, class Grid>
+// kStore: also store psi_{n+1} to x_out (complex128, the systems' rows back to
+// back), at the end through the shared-memory tile where a CTA's 128 blocks are
+// full-length blocks of one system (coalesced; the reduction only reads the tile).
+template <class R, class Map, class Grid, bool kStore>
 __global__ void __launch_bounds__(kThreads, FusedOccupancy<R, Map>::min_blocks)
 k_cn_fused(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, const typename Store<R>::T* x_next0,
-           LevelPlanes<R> out, LevelSlot<R>* out_slot, typename Store<R>::T* keep0, int* status) {
+           LevelPlanes<R> out, LevelSlot<R>* out_slot, typename Store<R>::T* keep0, double2* x_out, int* status) {
     typedef typename Store<R>::T ST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ST* ys = reinterpret_cast<ST*>(smem_raw);  // [m][kTileStride]
     const int tid = threadIdx.x;
-    const int64_t g = (int64_t)blockIdx.x * kThreads + tid;
-    const bool active = g < sys.total();
+    const int64_t g0 = (int64_t)blockIdx.x * kThreads;
+    const int64_t g = g0 + tid;
+    const int64_t total = sys.total();
+    const bool active = g < total;
     if (tid == 0)
         bulk_prefetch_l2(keep0 + (int64_t)blockIdx.x * (2 * (int64_t)m * kThreads) + 2 * kThreads,
                          2u * (uint32_t)(m - 1) * kThreads * (uint32_t)sizeof(ST));
+    // kStore, CTA-uniform: are all 128 blocks full-length blocks of one system?
+    bool regular = false;
+    int s0 = 0;
+    int64_t t0 = 0;
+    if (kStore && g0 + kThreads <= total) {
+        s0 = sys.find(g0);
+        const LvlSys& e0 = sys.at(s0);
+        t0 = g0 - e0.blk_off;
+        regular = (sys.find(g0 + kThreads - 1) == s0) &&
+                  joint_line(t0 + kThreads, e0.P, m, e0.n) == (t0 + kThreads) * m;
+    }
     bool ok = true;
     cx<R> JUa = czero<R>(), JUc = czero<R>(), JUd = czero<R>(), A0 = czero<R>(), D0 = czero<R>();
     cx<R> Ag = czero<R>(), Dg = czero<R>();
@@ -1233,14 +1252,33 @@ k_cn_fused(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, const typ
             y = cfma(sload(ys + k * kTileStride + tid), sload(keep + (2 * k + 1) * kThreads), y);
             sstore(ys + k * kTileStride + tid, y);
         }
+        if (kStore) {
+            double2* x = x_out + e.row_off;
+            if (regular) {
+                sstore(ys + tid, xL);  // row 0 of the block joins the tile
+            } else {                    // psi_{n+1} of this block, row by row
+                for (int k = 1; k < gap; ++k) store128(x + J0 + k, sload(ys + k * kTileStride + tid));
+                store128(x + J0, xL);
+            }
+            if (t == P - 1) store128(x + J0 + gap, xR);  // the system's last row J_P
+        }
         // reduction of step n + 1 from psi_{n+1}
         CNRowFused<R> rs;
         rs.init(st, e, grid.at(si), J0, ys + tid, xL, xR, gap);
         cn_reduce_block<R>(rs, gap, t == P - 1, keep, A0, D0, JUa, JUc, JUd, jd, Ag, Dg, ok);
     }
+    // (its barrier also orders every thread's tile writes before the tile store)
     write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, RowSink<R>(out, next.at(si), m_next),
                          out_slot);
     if (!ok) flag_error(status, kStatusNonfinite);
+    if (kStore && regular) {  // uniform per CTA: every thread is active
+        double2* x = x_out + sys.at(s0).row_off;
+        const int64_t base = t0 * m;  // tile row i = (block b, row k), i = b m + k
+        for (int i = tid; i < kThreads * m; i += kThreads) {
+            const int b = i / m, k = i - b * m;
+            store128(x + base + i, sload(ys + k * kTileStride + b));
+        }
+    }
 }
 
 // ------------------------------------------------------------------ adjoint step

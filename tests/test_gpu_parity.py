@@ -154,6 +154,69 @@ def test_multi_step_call_matches_single_steps(arith, block, table):
     assert rel(a, ref) <= 1e-11
 
 
+@pytest.mark.parametrize("flags", [0, cnb.FLAG_COEFF_TABLE, cnb.FLAG_RECOMPUTE])
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_step_states(arith, flags):
+    # every step's state kept: the last equals a cn_step of the same length
+    # bitwise, each state agrees with one-step calls (bitwise in binary64) and
+    # with the oracle
+    cfg = W.soft_coulomb_config(n=9001, nsteps=7)
+    psi0 = W.initial_state(cfg)
+    E = W.field_midpoints(7, cfg["dt"], t0=30.0)
+    plan = plan_for(cfg, arith=arith, block=12, flags=flags)
+    Ed = to_dev(E)
+    st = plan.step_states(to_dev(psi0), 7, E_mid=Ed)
+    last = plan.step(to_dev(psi0), 7, E_mid=Ed)
+    cur = to_dev(psi0)
+    singles = []
+    for k in range(7):
+        cur = plan.step(cur, 1, E_mid=Ed[k:k + 1])
+        singles.append(cur.cpu().numpy())
+    plan.check()
+    plan.close()
+    st = st.cpu().numpy()
+    assert np.array_equal(st[-1], last.cpu().numpy())
+    prob = oracle_problem(cfg)
+    for k in range(7):
+        if arith == cnb.ARITH_F64:
+            assert np.array_equal(st[k], singles[k])
+        else:
+            assert rel(st[k], singles[k]) <= 1e-13
+        assert rel(st[k], oracle.cn_run(prob, psi0, k + 1, E_mid=E)) <= 1e-11
+
+
+def test_step_states_rejects_overlap():
+    cfg = W.soft_coulomb_config(n=1001, nsteps=2)
+    plan = plan_for(cfg)
+    buf = torch.zeros((3, cfg["n"]), dtype=torch.complex128, device=DEV)
+    with pytest.raises(cnb.CNError):
+        plan.step_states(buf[1], 2, states_out=buf[1:])
+    plan.close()
+
+
+# n - 1 = P m with P a multiple of 128: every CTA of the level-0 grid is a full
+# tile of one system, and the system's last row lies just past the last tile
+@pytest.mark.parametrize("n,block", [(3073, 12), (2049, 8), (128 * 16 * 3 + 1, 16)])
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_last_row_after_full_tiles(n, block, arith):
+    dx, dt = 0.1, 0.01
+    x_min = -(n // 2) * dx
+    rng = np.random.default_rng(n)
+    psi0 = rng.standard_normal(n) + 1j * rng.standard_normal(n)  # amplitude up to the last row
+    psi0 /= np.linalg.norm(psi0)
+    prob = oracle.Problem(n, dx, dt, x_min, pot=oracle.POT_SOFTCOULOMB, soft_s=2.0)
+    plan = cnb.Plan(n, dx, dt, x_min, pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith, block=block)
+    assert plan.info()["level_rows"][1] == (n - 1) // block + 1 and ((n - 1) // block) % 128 == 0
+    for nsteps in (1, 4):
+        out = plan.step(to_dev(psi0), nsteps).cpu().numpy()
+        st = plan.step_states(to_dev(psi0), nsteps).cpu().numpy()
+        ref = oracle.cn_run(prob, psi0, nsteps)
+        assert rel(out, ref) <= 1e-11 and abs(out[-1] - ref[-1]) <= 1e-12
+        assert rel(st[-1], ref) <= 1e-11 and abs(st[-1][-1] - ref[-1]) <= 1e-12
+    plan.check()
+    plan.close()
+
+
 @pytest.mark.parametrize("flags", [0, cnb.FLAG_RECOMPUTE])
 def test_step_in_place_and_zero_steps(flags):
     cfg = W.soft_coulomb_config(n=1000, nsteps=7)
