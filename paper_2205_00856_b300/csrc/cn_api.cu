@@ -336,6 +336,7 @@ void with_maps_grid(const Engine* p, F f) {
 // Shared memory of the substitutions: two complex values per block row and thread.
 size_t subst_smem(int m) { return 2 * (size_t)m * kThreads * kCplx; }
 size_t kept_smem(int m) { return (size_t)m * kTileStride * kCplx; }
+size_t fused_smem(int m) { return (size_t)(m + 2) * kTileStride * kCplx; }  // rows 0..g+1 per column
 size_t cr_smem() { return 5 * (size_t)kCrMax * kCplx; }
 
 template <class R, class Src, class Map>
@@ -367,10 +368,11 @@ cudaError_t set_smem_limits_map(int m0, int ml) {
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e = cudaFuncSetAttribute(k_substitute<R, ArraySource, Map, double2>, a, (int)subst_smem(m0));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_substitute<R, LevelSource<R>, Map, ST>, a, (int)subst_smem(ml));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute<R, Map, Grid>, a, (int)subst_smem(m0));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute<R, -1, Map, Grid>, a, (int)subst_smem(m0));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute<R, 0, Map, Grid>, a, (int)subst_smem(m0));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute_kept<R, Map>, a, (int)kept_smem(m0));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_fused<R, Map, Grid, false>, a, (int)kept_smem(m0));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_fused<R, Map, Grid, true>, a, (int)kept_smem(m0));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_fused<R, -1, Map, Grid, false>, a, (int)fused_smem(m0));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_fused<R, -1, Map, Grid, true>, a, (int)fused_smem(m0));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr<R>, a, (int)cr_smem());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr_many<R>, a, (int)cr_smem());
     return e;
@@ -445,18 +447,30 @@ cudaError_t solve_arrays(Engine* p, const ArraySource& src, double2* x, cudaStre
     return e;
 }
 
-// One CN-type step of every system (level 0 generated on the fly), result in x.
+// e s of a step as the kernels' template argument: -1 for the CN step (its
+// right-hand side T^dagger psi), 0 for the adjoint's identity right-hand side.
+template <class F>
+cudaError_t with_es(const CNStep& s, F f) {
+    switch (s.e * s.s) {
+    case -1: return f(std::integral_constant<int, -1>());
+    case 0: return f(std::integral_constant<int, 0>());
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 template <class R>
 cudaError_t cn_reduce0(Engine* p, const CNStep& s, cudaStream_t st) {
     typedef typename Store<R>::T ST;
     const LevelData& L0 = p->lv[0];
     const LevelData& L1 = p->lv[1];
     ProfScope ps(p, kProfReduce0, st);
-    with_maps_grid(p, [&](auto a, auto b, auto gr) {
-        k_cn_reduce<R><<<grid_for(L0.total), kThreads, 0, st>>>(s, a, b, gr, L0.m, L1.m, planes_of<R>(L1),
-                                                                 slot_of<R>(L1), static_cast<ST*>(p->keep), p->status);
+    return with_es(s, [&](auto es) {
+        with_maps_grid(p, [&](auto a, auto b, auto gr) {
+            k_cn_reduce<R, decltype(es)::value><<<grid_for(L0.total), kThreads, 0, st>>>(
+                s, a, b, gr, L0.m, L1.m, planes_of<R>(L1), slot_of<R>(L1), static_cast<ST*>(p->keep), p->status);
+        });
+        return cudaGetLastError();
     });
-    return cudaGetLastError();
 }
 
 template <class R>
@@ -467,35 +481,38 @@ cudaError_t cn_subst0(Engine* p, const CNStep& s, double2* x, cudaStream_t st) {
     const unsigned grid = grid_for(L0.total);
     ST* keep = static_cast<ST*>(p->keep);
     ProfScope ps(p, kProfSubst0, st);
-    with_maps_grid(p, [&](auto a, auto b, auto gr) {
-        if (keep && L0.m > kSmemRowsMax)
-            k_cn_substitute_kept_gmem<R><<<grid, kThreads, 0, st>>>(a, b, L0.m, keep, x_of<R>(L1), x,
-                                                                    static_cast<ST*>(p->zc));
-        else if (keep)
-            k_cn_substitute_kept<R><<<grid, kThreads, kept_smem(L0.m), st>>>(a, b, L0.m, keep, x_of<R>(L1), x,
-                                                                             p->status);
-        else
-            k_cn_substitute<R><<<grid, kThreads, subst_smem(L0.m), st>>>(s, a, b, gr, L0.m, x_of<R>(L1), x,
-                                                                         p->status);
+    return with_es(s, [&](auto es) {
+        with_maps_grid(p, [&](auto a, auto b, auto gr) {
+            if (keep && L0.m > kSmemRowsMax)
+                k_cn_substitute_kept_gmem<R><<<grid, kThreads, 0, st>>>(a, b, L0.m, keep, x_of<R>(L1), x,
+                                                                        static_cast<ST*>(p->zc));
+            else if (keep)
+                k_cn_substitute_kept<R><<<grid, kThreads, kept_smem(L0.m), st>>>(a, b, L0.m, keep, x_of<R>(L1), x,
+                                                                                 p->status);
+            else
+                k_cn_substitute<R, decltype(es)::value><<<grid, kThreads, subst_smem(L0.m), st>>>(
+                    s, a, b, gr, L0.m, x_of<R>(L1), x, p->status);
+        });
+        return cudaGetLastError();
     });
-    return cudaGetLastError();
 }
 
-// SS of the previous step fused with the level-0 reduction of step s (store mode);
-// x_out != NULL also receives the previous step's result.
+// SS of the previous step fused with the level-0 reduction of step s (store mode,
+// CN steps: e s = -1); x_out != NULL also receives the previous step's result.
 template <class R>
 cudaError_t cn_fused0(Engine* p, const CNStep& s, double2* x_out, cudaStream_t st) {
     typedef typename Store<R>::T ST;
     const LevelData& L0 = p->lv[0];
     const LevelData& L1 = p->lv[1];
+    if (s.e * s.s != -1) return cudaErrorInvalidValue;
     ProfScope ps(p, kProfFused0, st);
     with_maps_grid(p, [&](auto a, auto b, auto gr) {
         typedef decltype(a) M;
         typedef decltype(gr) G;
-        auto kern = x_out ? k_cn_fused<R, M, G, true> : k_cn_fused<R, M, G, false>;
-        kern<<<grid_for(L0.total), kThreads, kept_smem(L0.m), st>>>(s, a, b, gr, L0.m, L1.m, x_of<R>(L1),
-                                                                    planes_of<R>(L1), slot_of<R>(L1),
-                                                                    static_cast<ST*>(p->keep), x_out, p->status);
+        auto kern = x_out ? k_cn_fused<R, -1, M, G, true> : k_cn_fused<R, -1, M, G, false>;
+        kern<<<grid_for(L0.total), kThreads, fused_smem(L0.m), st>>>(s, a, b, gr, L0.m, L1.m, x_of<R>(L1),
+                                                                     planes_of<R>(L1), slot_of<R>(L1),
+                                                                     static_cast<ST*>(p->keep), x_out, p->status);
     });
     return cudaGetLastError();
 }
@@ -538,8 +555,7 @@ cudaError_t cn_steps(Engine* p, const double2* in, double2* out, const double* E
         s.psi = psi;
         s.s = 1;
         s.e = -1;
-        s.E_t = E_mid ? E_mid + k : nullptr;
-        s.E_e = s.E_t;
+        s.E = E_mid ? E_mid + k : nullptr;
         s.tab = p->tab;
         return s;
     };
@@ -874,8 +890,7 @@ cn_status cn_adjoint_step(cn_plan p, const void* psi_n, const void* psi_np1, con
     s.psi = static_cast<const double2*>(lam_np1);
     s.s = -1;  // implicit matrix T^dagger = 1 - i dt/2 H
     s.e = 0;   // right-hand side lam_{n+1} itself
-    s.E_t = E_mid;
-    s.E_e = E_mid;
+    s.E = E_mid;
     s.tab = p->tab;
     const bool dfm = p->desc.arith == CN_ARITH_DF64;
     e = dfm ? cn_solve<df>(p, s, p->mu, st) : cn_solve<double>(p, s, p->mu, st);

@@ -660,7 +660,7 @@ __global__ void k_beta0_table(CNParams p, SysGrid sg, int64_t n, R* tab) {
 }
 
 // Per-thread coefficient generator walking rows j0, j0+1, ...: returns bt_j for
-// the field values E_t (implicit matrix) and E_e (explicit matrix).
+// the field value E (the same midpoint field for T and T^dagger, Sec. 2).
 template <class R> struct CoefGen;
 
 template <> struct CoefGen<double> {
@@ -668,22 +668,21 @@ template <> struct CoefGen<double> {
     const double* tab;
     const double* V0;
     SysGrid sg;
-    double c1Et, c1Ee, x;
+    double c1E, x;
     int64_t j;
     __device__ __forceinline__ double xj(int64_t jj) const { return fma((double)(jj - sg.j_o), p->dx, sg.x_o); }
     __device__ __forceinline__ void init(const CNParams& pp, const SysGrid& g, const double* tb, const double* v0,
-                                         double Et, double Ee, int64_t j0) {
+                                         double E, int64_t j0) {
         p = &pp; sg = g; tab = tb; V0 = v0; j = j0;
-        c1Et = pp.c1 * Et; c1Ee = pp.c1 * Ee;
+        c1E = pp.c1 * E;
         x = xj(j0);
     }
-    __device__ __forceinline__ void next(double& bt_t, double& bt_e) {
+    __device__ __forceinline__ void next(double& bt) {
         double b0;
         if (tab) b0 = tab[j];
         else if (p->pot == 1) b0 = fma(p->c1, V0[j], 2.0);
         else b0 = fma(p->c1, static_potential_d(*p, j, x), 2.0);
-        bt_t = fma(c1Et, x, b0);
-        bt_e = (c1Ee == c1Et) ? bt_t : fma(c1Ee, x, b0);
+        bt = fma(c1E, x, b0);
         ++j;
         x = xj(j);
     }
@@ -692,27 +691,24 @@ template <> struct CoefGen<double> {
 
 template <> struct CoefGen<df> {
     const df* tab;
-    df c1Et, c1Ee, x, dx, c1, soft_s;
+    df c1E, x, dx, c1, soft_s;
     int pot;
-    bool same;  // E_e == E_t: one diagonal serves both matrices
     int64_t j;
-    // All binary64 constants arrive pre-split (DFc); the fields are converted
+    // All binary64 constants arrive pre-split (DFc); the field is converted
     // with integer operations, so no FP64-pipe instruction runs here.
     __device__ __forceinline__ void init(const CNParams& pp, const SysGrid& g, const df* tb, const double*,
-                                         double Et, double Ee, int64_t j0) {
+                                         double E, int64_t j0) {
         tab = tb; j = j0; pot = pp.pot;
-        same = d_bits(Et) == d_bits(Ee);
         dx = dfc(pp.dx_f);
         c1 = dfc(pp.c1_f);
         soft_s = dfc(pp.soft_f);
-        c1Et = df_mul(c1, df_from_double(Et));
-        c1Ee = same ? c1Et : df_mul(c1, df_from_double(Ee));
+        c1E = df_mul(c1, df_from_double(E));
         // x_j0 = x_o + (j0 - j_o) dx with j0 - j_o = hi 2^16 + lo split into exact binary32 parts
         const int64_t dj = j0 - g.j_o;
         float jh = i2f((int32_t)(dj >> 16)), jl = i2f((int32_t)(dj & 0xFFFF));
         x = df_add(dfc(g.xo_f), df_add(df_mul_f(df_mul_f(dx, jh), 65536.0f), df_mul_f(dx, jl)));
     }
-    __device__ __forceinline__ void next(df& bt_t, df& bt_e) {
+    __device__ __forceinline__ void next(df& bt) {
         df b0;
         if (tab) {
             b0 = tab[j];
@@ -723,43 +719,53 @@ template <> struct CoefGen<df> {
         } else {
             b0 = df_make(2.0f, 0.0f);
         }
-        bt_t = df_add(b0, df_mul(c1Et, x));
-        bt_e = same ? bt_t : df_add(b0, df_mul(c1Ee, x));
+        bt = df_add(b0, df_mul(c1E, x));
         ++j;
         x = df_add(x, dx);
     }
     __device__ __forceinline__ void skip() { ++j; x = df_add(x, dx); }
 };
 
-// Scaled explicit row: d^ = (e s)(bt_e psi - sigma) - i s g~ psi, sigma = psi_{j-1} + psi_{j+1}.
-// es == 0: no explicit matrix, the right-hand side is psi itself (d^ = -i s g~ psi).
-__device__ __forceinline__ cx<double> explicit_row(cx<double> pm, cx<double> p0, cx<double> pp, double bte, int es,
+// Scaled explicit row: d^ = (e s)(bt psi - sigma) - i s g~ psi, sigma = psi_{j-1} + psi_{j+1},
+// with ES = e s a compile-time constant (-1: the CN step's T^dagger psi; 0: no
+// explicit matrix, the right-hand side is psi itself, d^ = -i s g~ psi).
+template <int ES>
+__device__ __forceinline__ cx<double> explicit_row(cx<double> pm, cx<double> p0, cx<double> pp, double bt,
                                                    double sg) {
-    if (es == 0) return mk(sg * p0.im, -sg * p0.re);
-    double sr = pm.re + pp.re, si = pm.im + pp.im;
-    double eb = es > 0 ? bte : -bte;
-    if (es > 0) { sr = -sr; si = -si; }
-    return mk(fma(eb, p0.re, fma(sg, p0.im, sr)), fma(eb, p0.im, fma(-sg, p0.re, si)));
+    static_assert(ES == -1 || ES == 0 || ES == 1, "e s is -1, 0 or 1");
+    if constexpr (ES == 0) {
+        return mk(sg * p0.im, -sg * p0.re);
+    } else {
+        double sr = pm.re + pp.re, si = pm.im + pp.im;
+        const double eb = ES > 0 ? bt : -bt;
+        if (ES > 0) { sr = -sr; si = -si; }
+        return mk(fma(eb, p0.re, fma(sg, p0.im, sr)), fma(eb, p0.im, fma(-sg, p0.re, si)));
+    }
 }
-__device__ __forceinline__ cx<df> explicit_row(cx<df> pm, cx<df> p0, cx<df> pp, df bte, int es, df sg) {
-    if (es == 0) return mk(df_mul(sg, p0.im), df_neg(df_mul(sg, p0.re)));
-    df sr = df_add(pm.re, pp.re), si = df_add(pm.im, pp.im);
-    df eb = es > 0 ? bte : df_neg(bte);
-    df nsr = es > 0 ? df_neg(sr) : sr;
-    df nsi = es > 0 ? df_neg(si) : si;
-    return mk(df_dot2_add(nsr, eb, p0.re, sg, p0.im), df_dot2_add(nsi, eb, p0.im, df_neg(sg), p0.re));
+template <int ES>
+__device__ __forceinline__ cx<df> explicit_row(cx<df> pm, cx<df> p0, cx<df> pp, df bt, df sg) {
+    static_assert(ES == -1 || ES == 0 || ES == 1, "e s is -1, 0 or 1");
+    if constexpr (ES == 0) {
+        return mk(df_mul(sg, p0.im), df_neg(df_mul(sg, p0.re)));
+    } else {
+        const df sr = df_add(pm.re, pp.re), si = df_add(pm.im, pp.im);
+        const df eb = ES > 0 ? bt : df_neg(bt);
+        const df nsr = ES > 0 ? df_neg(sr) : sr;
+        const df nsi = ES > 0 ? df_neg(si) : si;
+        return mk(df_dot2_add(nsr, eb, p0.re, sg, p0.im), df_dot2_add(nsi, eb, p0.im, df_neg(sg), p0.re));
+    }
 }
 
 // A CN-type step at level 0: sign s of the implicit matrix, sign e of the
-// explicit one, fields read from device memory (NULL: 0).  psi and tab are the
-// arrays of all systems; each system starts at its level-0 row offset.
+// explicit one (the kernels take e s as their template argument ES), field read
+// from device memory (NULL: 0).  psi and tab are the arrays of all systems; each
+// system starts at its level-0 row offset.
 struct CNStep {
     CNParams p;
     const double2* psi;   // state the explicit half-step is applied to
-    int s, e;             // T_s = 1 + i s dt/2 H(E_t);  explicit S_e = 1 + i e dt/2 H(E_e);
+    int s, e;             // T_s = 1 + i s dt/2 H(E);  explicit S_e = 1 + i e dt/2 H(E);
                           // e = 0: the right-hand side is psi itself
-    const double* E_t;
-    const double* E_e;
+    const double* E;      // the field at the step's midpoint (both matrices)
     const void* tab;      // bt0 table in the compute type, or NULL (regenerate)
 };
 
@@ -775,26 +781,24 @@ __device__ __forceinline__ df signed_gt(const CNStep& st, df) {
 
 // Streams the scaled rows of one CN block: row i's a~_i and d^_i, with the psi
 // stencil window and the coefficient generator carried from row to row.
-template <class R> struct CNRowStream {
+template <class R, int ES> struct CNRowStream {
     CoefGen<R> cg;
     cx<R> pm, p0, pp;  // psi_{i-1}, psi_i, psi_{i+1}: the next row's stencil is already loaded
     R sg, msg;
-    int es;
     const double2* psi;
     int64_t n, i;
     __device__ __forceinline__ cx<R> ld(int64_t j) const {
         return (j >= 0 && j < n) ? load128<R>(psi + j) : czero<R>();
     }
     __device__ __forceinline__ void init(const CNStep& st, const LvlSys& e, const SysGrid& g, int64_t j0) {
-        const double Et = st.E_t ? *st.E_t : 0.0, Ee = st.E_e ? *st.E_e : 0.0;
+        const double E = st.E ? *st.E : 0.0;
         sg = signed_gt(st, R());
         msg = rneg(sg);  // imaginary part of a~: -s g~
-        es = st.e * st.s;
         psi = st.psi + e.row_off;
         n = e.n;
         i = j0;
         const R* tab = st.tab ? static_cast<const R*>(st.tab) + e.row_off : nullptr;
-        cg.init(st.p, g, tab, st.p.V0 ? st.p.V0 + e.row_off : nullptr, Et, Ee, j0);
+        cg.init(st.p, g, tab, st.p.V0 ? st.p.V0 + e.row_off : nullptr, E, j0);
         pm = czero<R>();  // row j0 is a joint row: its stencil term with psi_{j0-1} is the block above's
         p0 = ld(j0);
         pp = ld(j0 + 1);
@@ -802,10 +806,10 @@ template <class R> struct CNRowStream {
     // scaled row i (then advance): a~ = bt - i s g~, d^ = explicit row
     __device__ __forceinline__ void next(cx<R>& a, cx<R>& d) {
         const cx<R> pn = ld(i + 2);  // issued before the arithmetic of row i
-        R bt, be;
-        cg.next(bt, be);
+        R bt;
+        cg.next(bt);
         a = mk(bt, msg);
-        d = explicit_row(pm, p0, pp, be, es, sg);
+        d = explicit_row<ES>(pm, p0, pp, bt, sg);
         pm = p0;
         p0 = pp;
         pp = pn;
@@ -826,8 +830,8 @@ template <class R> struct CNRowStream {
     // the share of row J_{t+1} that only this block can form: -es psi_{J_{t+1} - 1}
     // (called right after row J_{t+1} - 1 was produced, which left psi of that row in pm)
     __device__ __forceinline__ cx<R> jd_d(cx<R> x) const {
-        if (es == 0) return x;
-        return es > 0 ? csub(x, pm) : cadd(x, pm);
+        if constexpr (ES == 0) return x;
+        else return ES > 0 ? csub(x, pm) : cadd(x, pm);
     }
 };
 
@@ -909,7 +913,7 @@ __device__ __forceinline__ void cn_reduce_block(RS& rs, int gap, bool last, type
     JUd = cmul(w1, nd);
 }
 
-template <class R, class Map, class Grid>
+template <class R, int ES, class Map, class Grid>
 __global__ void __launch_bounds__(kThreads, ReduceOccupancy<R, Map>::min_blocks)
 k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, LevelPlanes<R> out, LevelSlot<R>* out_slot,
             typename Store<R>::T* keep0, int* status) {
@@ -932,7 +936,7 @@ k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, LevelPla
         ST* keep = keep0 ? keep0 + keep_base(m) : nullptr;
         const int64_t J0 = joint_line(t, P, m, n);
         const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
-        CNRowStream<R> rs;
+        CNRowStream<R, ES> rs;
         rs.init(st, e, grid.at(si), J0);
         cn_reduce_block<R>(rs, gap, t == P - 1, keep, A0, D0, JUa, JUc, JUd, jd, Ag, Dg, ok);
     }
@@ -947,7 +951,7 @@ k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, LevelPla
 //   (z_0 = xL, xR added on the last interior row), y_k = z_k + w_k y_{k+1}.
 // Recompute mode: coefficients, explicit half-step and pivots are regenerated
 // from psi (x must differ from the psi read).  z and w wait in shared memory.
-template <class R, class Map, class Grid>
+template <class R, int ES, class Map, class Grid>
 __global__ void __launch_bounds__(kThreads)
 k_cn_substitute(CNStep st, Map sys, Map next, Grid grid, int m, const typename Store<R>::T* x_next0, double2* x0,
                 int* status) {
@@ -968,7 +972,7 @@ k_cn_substitute(CNStep st, Map sys, Map next, Grid grid, int m, const typename S
     const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
     const cx<R> xL = sload(x_next + t);
     const cx<R> xR = sload(x_next + t + 1);
-    CNRowStream<R> rs;
+    CNRowStream<R, ES> rs;
     rs.init(st, e, grid.at(si), J0);
     rs.skip();
     cx<R> zp = xL, w = czero<R>();
@@ -1130,49 +1134,48 @@ k_cn_substitute_kept_gmem(Map sys, Map next, int m, const typename Store<R>::T* 
 // on chip: rows 1..g-1 in this thread's shared-memory column, the joint rows in
 // registers (the support values xL, xR of step n).  The joint rows' stencils are
 // split as in cn_reduce_block, so rows J_t..J_{t+1} are all the block needs.
-template <class R> struct CNRowFused {
+template <class R, int ES> struct CNRowFused {
     typedef typename Store<R>::T ST;
     CoefGen<R> cg;
     cx<R> pm, p0, pp;  // stencil of the next row to produce (pm = 0 on the joint rows)
-    cx<R> xR;
     R sg, msg;
-    int es, gap, k;
-    const ST* ys;      // row j of the block at ys[j * kTileStride]
+    int k;
+    const ST* ys;      // row j of the block at ys[j * kTileStride]: xL at 0, psi at 1..g-1, xR at g, 0 at g+1
     __device__ __forceinline__ void init(const CNStep& st, const LvlSys& e, const SysGrid& g, int64_t J0,
-                                         const ST* col, cx<R> xl, cx<R> xr, int gp) {
-        const double Et = st.E_t ? *st.E_t : 0.0, Ee = st.E_e ? *st.E_e : 0.0;
+                                         const ST* col) {
+        const double E = st.E ? *st.E : 0.0;
         sg = signed_gt(st, R());
         msg = rneg(sg);
-        es = st.e * st.s;
         const R* tab = st.tab ? static_cast<const R*>(st.tab) + e.row_off : nullptr;
-        cg.init(st.p, g, tab, st.p.V0 ? st.p.V0 + e.row_off : nullptr, Et, Ee, J0);
+        cg.init(st.p, g, tab, st.p.V0 ? st.p.V0 + e.row_off : nullptr, E, J0);
         ys = col;
-        gap = gp;
-        xR = xr;
         k = 0;
         pm = czero<R>();
-        p0 = xl;
-        pp = sload(ys + kTileStride);  // gap >= 2: row 1 is interior
+        p0 = sload(ys);
+        pp = sload(ys + kTileStride);
     }
     __device__ __forceinline__ void next(cx<R>& a, cx<R>& d) {
-        R bt, be;
-        cg.next(bt, be);
+        R bt;
+        cg.next(bt);
         a = mk(bt, msg);
-        d = explicit_row(pm, p0, pp, be, es, sg);
+        d = explicit_row<ES>(pm, p0, pp, bt, sg);
         pm = p0;
         p0 = pp;
         ++k;
-        pp = (k + 1 < gap) ? sload(ys + (k + 1) * kTileStride) : (k + 1 == gap ? xR : czero<R>());
+        pp = sload(ys + (k + 1) * kTileStride);
     }
+    // the system's last row J_P (row g): its own share; nothing is read after it
     __device__ __forceinline__ void next_joint(cx<R>& a, cx<R>& d) {
-        pm = czero<R>();
-        next(a, d);
+        R bt;
+        cg.next(bt);
+        a = mk(bt, msg);
+        d = explicit_row<ES>(czero<R>(), p0, pp, bt, sg);
     }
     // the share of row J_{t+1} that only this block can form: -es psi_{J_{t+1} - 1}
+    // (called right after row J_{t+1} - 1 was produced, which left psi of that row in pm)
     __device__ __forceinline__ cx<R> jd_d(cx<R> x) const {
-        if (es == 0) return x;
-        const cx<R> y = sload(ys + (gap - 1) * kTileStride);
-        return es > 0 ? csub(x, y) : cadd(x, y);
+        if constexpr (ES == 0) return x;
+        else return ES > 0 ? csub(x, pm) : cadd(x, pm);
     }
 };
 
@@ -1185,16 +1188,19 @@ template <class R, class Map> struct FusedOccupancy { static constexpr int min_b
 // state, no conversions to and from complex128 between the steps), and the kept
 // (d^, w) of step n are replaced by those of step n + 1 in place.  st describes
 // step n + 1; x_next0 holds the level-1 solution of step n (the support values).
-// kStore: also store psi_{n+1} to x_out (complex128, the systems' rows back to
-// back), at the end through the shared-memory tile where a CTA's 128 blocks are
-// full-length blocks of one system (coalesced; the reduction only reads the tile).
-template <class R, class Map, class Grid, bool kStore>
+// Each thread's shared-memory column holds rows 0..g+1 of its block (m + 2
+// entries: xL, psi_{n+1} on the interior rows, xR, 0), so the reduction reads its
+// stencil without branches.  kStore: also store psi_{n+1} to x_out (complex128,
+// the systems' rows back to back), at the end through the shared-memory tile
+// where a CTA's 128 blocks are full-length blocks of one system (coalesced; the
+// reduction only reads the tile).
+template <class R, int ES, class Map, class Grid, bool kStore>
 __global__ void __launch_bounds__(kThreads, FusedOccupancy<R, Map>::min_blocks)
 k_cn_fused(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, const typename Store<R>::T* x_next0,
            LevelPlanes<R> out, LevelSlot<R>* out_slot, typename Store<R>::T* keep0, double2* x_out, int* status) {
     typedef typename Store<R>::T ST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ST* ys = reinterpret_cast<ST*>(smem_raw);  // [m][kTileStride]
+    ST* ys = reinterpret_cast<ST*>(smem_raw);  // [m + 2][kTileStride]
     const int tid = threadIdx.x;
     const int64_t g0 = (int64_t)blockIdx.x * kThreads;
     const int64_t g = g0 + tid;
@@ -1228,6 +1234,7 @@ k_cn_fused(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, const typ
         P = e.P;
         t = g - e.blk_off;
         ST* keep = keep0 + keep_base(m);
+        ST* col = ys + tid;
         const ST* x_next = x_next0 + next.at(si).row_off;
         const int64_t J0 = joint_line(t, P, m, n);
         const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
@@ -1235,43 +1242,43 @@ k_cn_fused(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, const typ
         const cx<R> xR = sload(x_next + t + 1);
         // SS of step n: z forward, psi_{n+1} backward, both in this thread's column
         cx<R> zp = xL;
-        cx<R> dn = sload(keep + 2 * kThreads), wn = sload(keep + 3 * kThreads);
-        for (int k = 1; k < gap; ++k) {
-            const cx<R> d = dn, w = wn;
-            if (k + 1 < gap) {
-                dn = sload(keep + (2 * k + 2) * kThreads);
-                wn = sload(keep + (2 * k + 3) * kThreads);
-            }
-            cx<R> rhs = cadd(d, zp);
-            if (k == gap - 1) rhs = cadd(rhs, xR);
-            zp = cmul(rhs, w);
-            sstore(ys + k * kTileStride + tid, zp);
+        cx<R> d = sload(keep + 2 * kThreads), w = sload(keep + 3 * kThreads);
+        for (int k = 1; k < gap - 1; ++k) {
+            const cx<R> dn = sload(keep + (2 * k + 2) * kThreads);  // next row's values first
+            const cx<R> wn = sload(keep + (2 * k + 3) * kThreads);
+            zp = cmul(cadd(d, zp), w);
+            sstore(col + k * kTileStride, zp);
+            d = dn;
+            w = wn;
         }
+        zp = cmul(cadd(cadd(d, zp), xR), w);  // row g-1 takes xR
+        sstore(col + (gap - 1) * kTileStride, zp);
         cx<R> y = zp;
         for (int k = gap - 2; k >= 1; --k) {
-            y = cfma(sload(ys + k * kTileStride + tid), sload(keep + (2 * k + 1) * kThreads), y);
-            sstore(ys + k * kTileStride + tid, y);
+            y = cfma(sload(col + k * kTileStride), sload(keep + (2 * k + 1) * kThreads), y);
+            sstore(col + k * kTileStride, y);
         }
+        sstore(col, xL);
+        sstore(col + gap * kTileStride, xR);
+        sstore(col + (gap + 1) * kTileStride, czero<R>());
         if (kStore) {
             double2* x = x_out + e.row_off;
-            if (regular) {
-                sstore(ys + tid, xL);  // row 0 of the block joins the tile
-            } else {                    // psi_{n+1} of this block, row by row
-                for (int k = 1; k < gap; ++k) store128(x + J0 + k, sload(ys + k * kTileStride + tid));
+            if (!regular) {  // psi_{n+1} of this block, row by row
+                for (int k = 1; k < gap; ++k) store128(x + J0 + k, sload(col + k * kTileStride));
                 store128(x + J0, xL);
             }
             if (t == P - 1) store128(x + J0 + gap, xR);  // the system's last row J_P
         }
         // reduction of step n + 1 from psi_{n+1}
-        CNRowFused<R> rs;
-        rs.init(st, e, grid.at(si), J0, ys + tid, xL, xR, gap);
+        CNRowFused<R, ES> rs;
+        rs.init(st, e, grid.at(si), J0, col);
         cn_reduce_block<R>(rs, gap, t == P - 1, keep, A0, D0, JUa, JUc, JUd, jd, Ag, Dg, ok);
     }
     // (its barrier also orders every thread's tile writes before the tile store)
     write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, RowSink<R>(out, next.at(si), m_next),
                          out_slot);
     if (!ok) flag_error(status, kStatusNonfinite);
-    if (kStore && regular) {  // uniform per CTA: every thread is active
+    if (kStore && regular) {  // uniform per CTA: every thread is active; rows 0..m-1 of each column
         double2* x = x_out + sys.at(s0).row_off;
         const int64_t base = t0 * m;  // tile row i = (block b, row k), i = b m + k
         for (int i = tid; i < kThreads * m; i += kThreads) {
