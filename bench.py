@@ -428,7 +428,7 @@ def adjoint_ratio(torch, cnb, args, dev):
     tf = nsteps * cfg["dt"]
     arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
     plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith,
-                    block=args.block, level_block=args.level_block,
+                    block=args.block, level_block=args.level_block, level1_block=args.level1_block,
                     flags=cnb.FLAG_COEFF_TABLE if args.coeff_table else 0)
     psi0 = torch.from_numpy(W.initial_state(cfg)).to(dev)
     u0 = torch.from_numpy(W.initial_controls(nc, tf)).to(dev)

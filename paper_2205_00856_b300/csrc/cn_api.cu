@@ -337,7 +337,7 @@ void with_maps_grid(const Engine* p, F f) {
 size_t subst_smem(int m) { return 2 * (size_t)m * kThreads * kCplx; }
 size_t kept_smem(int m) { return (size_t)m * kTileStride * kCplx; }
 size_t fused_smem(int m) { return (size_t)(m + 2) * kTileStride * kCplx; }  // rows 0..g+1 per column
-size_t cr_smem() { return 5 * (size_t)kCrMax * kCplx; }
+size_t cr_smem() { return 6 * (size_t)kCrMax * kCplx; }
 
 template <class R, class Src, class Map>
 cudaError_t launch_reduce(const Src& src, Map sys, Map next, int m, const LevelData& nextL, int* status,

@@ -261,6 +261,31 @@ CNB_HD df df_dot2_add(df c, df a0, df b0, df a1, df b1) {
     return two_sum(t.hi, e);
 }
 
+// c + a0 b0 + a1 b1 + a2 b2 + a3 b3: four exact products, the five leading terms
+// summed by a TwoSum tree, every error term and cross product collected in one
+// binary32 sum, one final renormalisation.
+CNB_HD df df_dot4_add(df c, df a0, df b0, df a1, df b1, df a2, df b2, df a3, df b3) {
+    df p0 = two_prod(a0.hi, b0.hi);
+    df p1 = two_prod(a1.hi, b1.hi);
+    df p2 = two_prod(a2.hi, b2.hi);
+    df p3 = two_prod(a3.hi, b3.hi);
+    df s01 = two_sum(p0.hi, p1.hi);
+    df s23 = two_sum(p2.hi, p3.hi);
+    df s = two_sum(s01.hi, s23.hi);
+    df t = two_sum(c.hi, s.hi);
+    float e = f_add(f_add(f_add(p0.lo, p1.lo), f_add(p2.lo, p3.lo)), f_add(f_add(s01.lo, s23.lo), f_add(s.lo, t.lo)));
+    e = f_add(e, c.lo);
+    e = f_fma(a0.hi, b0.lo, e);
+    e = f_fma(a0.lo, b0.hi, e);
+    e = f_fma(a1.hi, b1.lo, e);
+    e = f_fma(a1.lo, b1.hi, e);
+    e = f_fma(a2.hi, b2.lo, e);
+    e = f_fma(a2.lo, b2.hi, e);
+    e = f_fma(a3.hi, b3.lo, e);
+    e = f_fma(a3.lo, b3.hi, e);
+    return two_sum(t.hi, e);
+}
+
 // ------------------------------------------------------------ complex
 template <class R> struct cx {
     R re, im;
@@ -278,6 +303,11 @@ CNB_HD cx<double> cmul(cx<double> a, cx<double> b) {
 CNB_HD cx<double> cfma(cx<double> c, cx<double> a, cx<double> b) {
     return mk(fma(a.re, b.re, fma(-a.im, b.im, c.re)), fma(a.re, b.im, fma(a.im, b.re, c.im)));
 }
+// c - a b - e f
+CNB_HD cx<double> csub2mul(cx<double> c, cx<double> a, cx<double> b, cx<double> e, cx<double> f) {
+    return mk(fma(-a.re, b.re, fma(a.im, b.im, fma(-e.re, f.re, fma(e.im, f.im, c.re)))),
+              fma(-a.re, b.im, fma(-a.im, b.re, fma(-e.re, f.im, fma(-e.im, f.re, c.im)))));
+}
 CNB_HD cx<double> crcp(cx<double> z, bool& ok) {
     double m2 = fma(z.re, z.re, z.im * z.im);
     ok = ok && (m2 > 0.0 && m2 < 1.0e300);
@@ -294,6 +324,11 @@ CNB_HD cx<df> cmul(cx<df> a, cx<df> b) {
 }
 CNB_HD cx<df> cfma(cx<df> c, cx<df> a, cx<df> b) {
     return mk(df_dot2_add(c.re, a.re, b.re, df_neg(a.im), b.im), df_dot2_add(c.im, a.re, b.im, a.im, b.re));
+}
+// c - a b - e f, one dot product per component
+CNB_HD cx<df> csub2mul(cx<df> c, cx<df> a, cx<df> b, cx<df> e, cx<df> f) {
+    return mk(df_dot4_add(c.re, df_neg(a.re), b.re, a.im, b.im, df_neg(e.re), f.re, e.im, f.im),
+              df_dot4_add(c.im, df_neg(a.re), b.im, df_neg(a.im), b.re, df_neg(e.re), f.im, df_neg(e.im), f.re));
 }
 // 1/z = conj(z) / |z|^2
 CNB_HD cx<df> crcp(cx<df> z, bool& ok) {

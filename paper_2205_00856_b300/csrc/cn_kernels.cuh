@@ -536,7 +536,8 @@ __device__ __forceinline__ void cr_solve(const LevelSource<R>& src, typename Sto
     ST* sa = sb + kCrMax;
     ST* sc = sa + kCrMax;
     ST* sd = sc + kCrMax;
-    ST* sx = sd + kCrMax;
+    ST* sw = sd + kCrMax;  // 1 / a of every row, formed once where a is formed
+    ST* sx = sw + kCrMax;
     const int n = (int)src.n;
     const int tid = threadIdx.x;
     bool ok = true;
@@ -546,37 +547,42 @@ __device__ __forceinline__ void cr_solve(const LevelSource<R>& src, typename Sto
         sstore(sa + i, r.a);
         sstore(sc + i, r.c);
         sstore(sd + i, r.d);
+        sstore(sw + i, crcp(r.a, ok));
     }
     __syncthreads();
+    // row i (index + 1 a multiple of 2s) eliminates its neighbours at distance s:
+    //   k1 = b_i / a_{i-s},  k2 = c_i / a_{i+s}
+    //   a_i -= k1 c_{i-s} + k2 b_{i+s},  d_i -= k1 d_{i-s} + k2 d_{i+s},
+    //   b_i = -k1 b_{i-s},  c_i = -k2 c_{i+s}
     int s = 1;
     for (; 2 * s - 1 < n; s <<= 1) {
         for (int i = 2 * s * (tid + 1) - 1; i < n; i += 2 * s * kCrThreads) {
-            const cx<R> k1 = cmul(sload(sb + i), crcp(sload(sa + i - s), ok));
-            cx<R> a = csub(sload(sa + i), cmul(k1, sload(sc + i - s)));
-            cx<R> d = csub(sload(sd + i), cmul(k1, sload(sd + i - s)));
+            const cx<R> k1 = cmul(sload(sb + i), sload(sw + i - s));
+            const bool right = i + s < n;
+            const cx<R> k2 = right ? cmul(sload(sc + i), sload(sw + i + s)) : czero<R>();
+            const cx<R> br = right ? sload(sb + i + s) : czero<R>();
+            const cx<R> dr = right ? sload(sd + i + s) : czero<R>();
+            const cx<R> a = csub2mul(sload(sa + i), k1, sload(sc + i - s), k2, br);
+            const cx<R> d = csub2mul(sload(sd + i), k1, sload(sd + i - s), k2, dr);
             const cx<R> b = cneg(cmul(k1, sload(sb + i - s)));
-            cx<R> c = czero<R>();
-            if (i + s < n) {
-                const cx<R> k2 = cmul(sload(sc + i), crcp(sload(sa + i + s), ok));
-                a = csub(a, cmul(k2, sload(sb + i + s)));
-                d = csub(d, cmul(k2, sload(sd + i + s)));
-                c = cneg(cmul(k2, sload(sc + i + s)));
-            }
+            const cx<R> c = right ? cneg(cmul(k2, sload(sc + i + s))) : czero<R>();
             sstore(sa + i, a);
             sstore(sb + i, b);
             sstore(sc + i, c);
             sstore(sd + i, d);
+            sstore(sw + i, crcp(a, ok));
         }
         __syncthreads();
     }
-    if (tid == 0) sstore(sx + s - 1, cmul(sload(sd + s - 1), crcp(sload(sa + s - 1), ok)));
+    if (tid == 0) sstore(sx + s - 1, cmul(sload(sd + s - 1), sload(sw + s - 1)));
     __syncthreads();
+    // back: x_i = (d_i - b_i x_{i-s} - c_i x_{i+s}) / a_i
     for (s >>= 1; s >= 1; s >>= 1) {
         for (int i = s - 1 + 2 * s * tid; i < n; i += 2 * s * kCrThreads) {
-            cx<R> y = sload(sd + i);
-            if (i - s >= 0) y = csub(y, cmul(sload(sb + i), sload(sx + i - s)));
-            if (i + s < n) y = csub(y, cmul(sload(sc + i), sload(sx + i + s)));
-            sstore(sx + i, cmul(y, crcp(sload(sa + i), ok)));
+            const cx<R> xl = i - s >= 0 ? sload(sx + i - s) : czero<R>();
+            const cx<R> xr = i + s < n ? sload(sx + i + s) : czero<R>();
+            const cx<R> y = csub2mul(sload(sd + i), sload(sb + i), xl, sload(sc + i), xr);
+            sstore(sx + i, cmul(y, sload(sw + i)));
         }
         __syncthreads();
     }

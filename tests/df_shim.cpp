@@ -29,6 +29,26 @@ void shim_op(int op, const float* a, const float* b, const float* c, const float
         out[2 * i] = r.hi; out[2 * i + 1] = r.lo;
     }
 }
+// c + a0 b0 + a1 b1 + a2 b2 + a3 b3 on arrays of df pairs (a, b of length 4 per item)
+void shim_dot4(const float* c, const float* a, const float* b, float* out, long n) {
+    for (long i = 0; i < n; ++i) {
+        df A[4], B[4];
+        for (int k = 0; k < 4; ++k) {
+            A[k] = df_make(a[8 * i + 2 * k], a[8 * i + 2 * k + 1]);
+            B[k] = df_make(b[8 * i + 2 * k], b[8 * i + 2 * k + 1]);
+        }
+        df r = df_dot4_add(df_make(c[2 * i], c[2 * i + 1]), A[0], B[0], A[1], B[1], A[2], B[2], A[3], B[3]);
+        out[2 * i] = r.hi; out[2 * i + 1] = r.lo;
+    }
+}
+// complex c - a b - e f on (re.hi, re.lo, im.hi, im.lo)
+void shim_csub2mul(const float* c, const float* a, const float* b, const float* e, const float* f, float* out, long n) {
+    auto ld = [](const float* p, long i) { return mk(df_make(p[4 * i], p[4 * i + 1]), df_make(p[4 * i + 2], p[4 * i + 3])); };
+    for (long i = 0; i < n; ++i) {
+        cx<df> r = csub2mul(ld(c, i), ld(a, i), ld(b, i), ld(e, i), ld(f, i));
+        out[4 * i] = r.re.hi; out[4 * i + 1] = r.re.lo; out[4 * i + 2] = r.im.hi; out[4 * i + 3] = r.im.lo;
+    }
+}
 // complex ops on (re.hi, re.lo, im.hi, im.lo): 0 cmul(a,b), 1 cfma(c,a,b) = c + a b, 2 crcp(a)
 void shim_cop(int op, const float* a, const float* b, const float* c, float* out, int* ok, long n) {
     for (long i = 0; i < n; ++i) {

@@ -166,3 +166,43 @@ def test_complex_ops(shim):
                 er, ei = ar / m2, -ai / m2
                 scale = abs(er) + abs(ei)
             assert abs(rr - er) + abs(ri - ei) <= scale * F(24 * U2), (op, i)
+
+
+def test_dot4_and_complex_two_product_update(shim):
+    # df_dot4_add (c + sum of four products) and csub2mul (c - a b - e f) against
+    # exact arithmetic, with heavy cancellation forced on a third of the cases
+    shim.shim_dot4.argtypes = [C.c_void_p] * 4 + [C.c_long]
+    shim.shim_csub2mul.argtypes = [C.c_void_p] * 6 + [C.c_long]
+    rng = np.random.default_rng(11)
+    n = 2000
+    a = to_df(shim, rand_doubles(rng, 4 * n, -5, 5))
+    b = to_df(shim, rand_doubles(rng, 4 * n, -5, 5))
+    c = to_df(shim, rand_doubles(rng, n, -5, 5))
+    for i in range(0, n, 3):  # a1 b1 ~ -a0 b0 and c ~ -(a2 b2)
+        a[8 * i + 2], a[8 * i + 3] = -a[8 * i], -a[8 * i + 1]
+        b[8 * i + 2], b[8 * i + 3] = b[8 * i], b[8 * i + 1] * 0.5
+    out = np.empty(2 * n, np.float32)
+    shim.shim_dot4(ptr(c), ptr(a), ptr(b), ptr(out), n)
+    for i in range(n):
+        prods = [(F(float(a[8 * i + 2 * k])) + F(float(a[8 * i + 2 * k + 1])))
+                 * (F(float(b[8 * i + 2 * k])) + F(float(b[8 * i + 2 * k + 1]))) for k in range(4)]
+        cc = exact(c, i)
+        want = cc + sum(prods)
+        scale = abs(cc) + sum(abs(p) for p in prods)
+        assert abs(exact(out, i) - want) <= scale * F(14 * U2), i
+
+    def cdf(m):
+        return to_df(shim, rand_doubles(rng, 2 * m, -4, 4))
+    cz, az, bz, ez, fz = (cdf(n) for _ in range(5))
+    outz = np.empty(4 * n, np.float32)
+    shim.shim_csub2mul(ptr(cz), ptr(az), ptr(bz), ptr(ez), ptr(fz), ptr(outz), n)
+
+    def cval(x, i):
+        return (F(float(x[4 * i])) + F(float(x[4 * i + 1])), F(float(x[4 * i + 2])) + F(float(x[4 * i + 3])))
+    for i in range(n):
+        (cr, ci), (ar, ai), (br, bi), (er, ei), (fr, fi) = (cval(x, i) for x in (cz, az, bz, ez, fz))
+        wr = cr - (ar * br - ai * bi) - (er * fr - ei * fi)
+        wi = ci - (ar * bi + ai * br) - (er * fi + ei * fr)
+        rr, ri = cval(outz, i)
+        scale = abs(cr) + abs(ci) + (abs(ar) + abs(ai)) * (abs(br) + abs(bi)) + (abs(er) + abs(ei)) * (abs(fr) + abs(fi))
+        assert abs(rr - wr) + abs(ri - wi) <= scale * F(28 * U2), i
