@@ -72,18 +72,22 @@ def test_batch_matches_oracle_per_system(arith, block):
         assert rel(got, ref) <= 1e-11, (s, n)
 
 
+@pytest.mark.parametrize("blocks", [(0, 0, 0), (12, 8, 5)])
 @pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
-def test_batch_equals_single_plans_bitwise(arith):
+def test_batch_equals_single_plans_bitwise(arith, blocks):
+    # (block, level block, level-1 block); 0 = defaults
+    m0, ml, m1 = blocks
     rng = np.random.default_rng(12)
     sizes = [int(v) for v in rng.integers(3, 30000, 24)]
     cos_a = rng.uniform(-0.5, 0.5, (len(sizes), 8))
     parts = batch_state(sizes, seed=1)
     E = torch.from_numpy(0.05 * np.sin(np.arange(7))).to(DEV)
-    b = cnb.Batch(sizes, DX, DT, pot=cnb.POT_COSSERIES, cos_a=cos_a, arith=arith)
+    b = cnb.Batch(sizes, DX, DT, pot=cnb.POT_COSSERIES, cos_a=cos_a, arith=arith, block=m0, level_block=ml,
+                  level1_block=m1)
     out = b.step(torch.from_numpy(np.concatenate(parts)).to(DEV), 7, E_mid=E).cpu().numpy()
     for s, n in enumerate(sizes):
         p = cnb.Plan(n, DX, DT, -(n // 2) * DX, pot=cnb.POT_COSSERIES, cos_a=cos_a[s], L=n * DX, arith=arith,
-                     flags=cnb.FLAG_COEFF_TABLE)
+                     flags=cnb.FLAG_COEFF_TABLE, block=m0, level_block=ml, level1_block=m1)
         ref = p.step(torch.from_numpy(parts[s]).to(DEV), 7, E_mid=E).cpu().numpy()
         p.close()
         assert np.array_equal(out[b.offsets[s]:b.offsets[s + 1]], ref), (s, n)

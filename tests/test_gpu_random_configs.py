@@ -1,7 +1,8 @@
 """Seeded random configurations of the CN step against the FP64 oracle: sizes from 3
 to 60000 (ragged tails, single-block and base-only levels), level-0 and level block
-sizes 3..32, both arithmetics, store and recompute modes, the three potential kinds,
-default and explicit nesting.  Tolerance as the other parity tests (rel L2 <= 1e-11)."""
+sizes 3..32 (level 1 on its own or not), both arithmetics, store and recompute modes,
+the three potential kinds, default and explicit nesting; the states kept by
+cn_step_states end on the plain step's result bitwise.  Tolerance as the other parity tests (rel L2 <= 1e-11)."""
 import numpy as np
 import pytest
 
@@ -44,10 +45,11 @@ def _case(seed):
     c["psi0"] = W.gaussian(n, c["dx"], c["x_min"], float(rng.uniform(-2, 2)), max(0.5, 0.02 * n * c["dx"]),
                            float(rng.uniform(-1, 1)))
     c["E"] = 0.05 * np.sin(np.arange(c["nsteps"]) * 0.7 + seed) if c["field"] else None
+    c["level1_block"] = int(rng.choice([0, int(rng.integers(3, 33))]))  # drawn last: earlier draws unchanged
     return c
 
 
-@pytest.mark.parametrize("seed", range(40))
+@pytest.mark.parametrize("seed", range(60))
 def test_random_configuration_vs_oracle(seed):
     c = _case(seed)
     n = c["n"]
@@ -61,12 +63,16 @@ def test_random_configuration_vs_oracle(seed):
             c["flags"] = kw["flags"] = 0
         plan = cnb.Plan(n, c["dx"], c["dt"], c["x_min"], levels=c["explicit"], **kw)
     else:
-        plan = cnb.Plan(n, c["dx"], c["dt"], c["x_min"], block=c["block"], level_block=c["level_block"], **kw)
+        plan = cnb.Plan(n, c["dx"], c["dt"], c["x_min"], block=c["block"], level_block=c["level_block"],
+                        level1_block=c["level1_block"], **kw)
     E_dev = None if c["E"] is None else torch.from_numpy(c["E"]).to(DEV)
     out = plan.step(torch.from_numpy(c["psi0"]).to(DEV), c["nsteps"], E_mid=E_dev).cpu().numpy()
+    # every state kept: the last equals the plain step's result bitwise
+    states = plan.step_states(torch.from_numpy(c["psi0"]).to(DEV), c["nsteps"], E_mid=E_dev).cpu().numpy()
     plan.check()
     plan.close()
+    assert np.array_equal(states[-1], out)
     ref = oracle.cn_run(oracle.Problem(n, c["dx"], c["dt"], c["x_min"], **okw), c["psi0"], c["nsteps"], E_mid=c["E"])
     err = float(np.linalg.norm(out - ref) / np.linalg.norm(ref))
-    assert err <= 1e-11, {k: c[k] for k in ("n", "block", "level_block", "arith", "flags", "pot", "nsteps",
-                                            "explicit")} | {"err": err}
+    assert err <= 1e-11, {k: c[k] for k in ("n", "block", "level_block", "level1_block", "arith", "flags", "pot",
+                                            "nsteps", "explicit")} | {"err": err}
