@@ -666,10 +666,11 @@ def main():
     ap.add_argument("--arith", choices=["f64", "df64"], default="df64")
     ap.add_argument("--f64-steps", type=int, default=100,
                     help="also time the native-FP64 path for this many steps (0: skip)")
-    # 12 / 12: the plan autotuner's pick for this workload on B300 (its candidates are
-    # within 1 % of each other at the top, so a run-time pick would wander between
-    # them and away from the block size the committed ncu captures were taken at)
-    ap.add_argument("--block", type=int, default=12, help="level-0 block rows (0: autotune with --level-block)")
+    # 13 / level 1: 10 / 12, from sweeps on B300 of the fused step loop (level-0 blocks
+    # 10..16: 13 best, 0.482 vs 0.485 ms at 12; the top candidates are within 1 % of
+    # each other, so a run-time pick would wander between them and away from the
+    # block size the committed ncu captures were taken at)
+    ap.add_argument("--block", type=int, default=13, help="level-0 block rows (0: autotune with --level-block)")
     ap.add_argument("--level-block", type=int, default=12, help="rows per block on levels >= 1 (0: autotune)")
     # level 1 in blocks of 10: 0.502 vs 0.506 ms per step at 12 (swept 10..24 with level blocks 8 and 12)
     ap.add_argument("--level1-block", type=int, default=10, help="rows per block on level 1 alone (0: --level-block)")
