@@ -144,7 +144,14 @@ cn_status cn_plan_destroy(cn_plan plan);
  * E_mid: device array of nsteps doubles, E_mid[k] = E(t0 + (k + 1/2) dt), the
  * field at the midpoint of step k (Sec. 2: T is built at t + dt/2); NULL
  * means E = 0.  psi_in may equal psi_out; psi_in is otherwise not modified.
- * nsteps = 0 copies psi_in to psi_out. */
+ * nsteps = 0 copies psi_in to psi_out.  In double-float store mode the steps
+ * of one call pass psi on chip: each step's level-0 substitution and the next
+ * step's level-0 reduction run as one kernel, and psi is written once, by the
+ * last step.  psi then keeps its double-float form between the steps of a
+ * call instead of being rounded to complex128, so a call of K steps and K
+ * calls of one step agree to rounding (bitwise in binary64, recompute mode and
+ * blocks longer than 32 rows, which keep every step separate).  Asynchronous
+ * on `stream`; device-side errors go to the plan status (cn_plan_status). */
 cn_status cn_step(cn_plan plan, const void* psi_in, void* psi_out, const double* E_mid,
                   int64_t nsteps, void* stream);
 
