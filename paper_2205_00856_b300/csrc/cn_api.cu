@@ -44,6 +44,7 @@ struct LevelData {
 struct Engine {
     cn_desc desc;                 // desc.n: rows of all systems
     int device = 0;
+    int sms = 0;                  // multiprocessors of the device
     bool batched = false;
     int nsys = 0;
     std::vector<LevelData> lv;    // lv[0]: the systems themselves
@@ -333,19 +334,49 @@ void with_maps_grid(const Engine* p, F f) {
 }
 
 // --------------------------------------------------------------- launches
+// Every kernel of the solve and step paths is launched with programmatic stream
+// serialization: it may be scheduled while the previous kernel in the stream is
+// still running and waits on the device (grid_dep_enter) for its results.
+template <class... KArgs, class... Args>
+cudaError_t launch(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                   Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Shared memory of the substitutions: two complex values per block row and thread.
 size_t subst_smem(int m) { return 2 * (size_t)m * kThreads * kCplx; }
 size_t kept_smem(int m) { return (size_t)m * kTileStride * kCplx; }
 size_t fused_smem(int m) { return (size_t)(m + 2) * kTileStride * kCplx; }  // rows 0..g+1 per column
 size_t cr_smem() { return 6 * (size_t)kCrMax * kCplx; }
+size_t ws_reduce_smem(int m) { return ws_reduce_entries(m) * kCplx; }
+size_t ws_subst_smem(int m) { return ws_subst_entries(m) * kCplx; }
+
+// The two-group kernels take the reduced levels below level 1 that need at most
+// one CTA of kThreads blocks per multiprocessor, with blocks of at most
+// kWsRowsMax rows.  (Level 1 stays on the one-thread-per-block kernels: where it
+// qualifies, at n = 2^20, the two-group kernels there made the step 5 % slower
+// on B300, while levels 2 and 3 at n = 2^24 gain 1.3 % of the step.)
+bool two_group_level(const Engine* p, size_t l) {
+    const LevelData& L = p->lv[l];
+    return l >= 2 && L.m <= kWsRowsMax && L.total > 0 && (int64_t)grid_for(L.total) <= (int64_t)p->sms;
+}
 
 template <class R, class Src, class Map>
 cudaError_t launch_reduce(const Src& src, Map sys, Map next, int m, const LevelData& nextL, int* status,
                           int64_t total, cudaStream_t st) {
     if (total == 0) return cudaSuccess;
-    k_reduce<R, Src, Map><<<grid_for(total), kThreads, 0, st>>>(src, sys, next, m, nextL.m, planes_of<R>(nextL),
-                                                                slot_of<R>(nextL), status);
-    return cudaGetLastError();
+    return launch(k_reduce<R, Src, Map>, grid_for(total), kThreads, 0, st, src, sys, next, m, nextL.m,
+                  planes_of<R>(nextL), slot_of<R>(nextL), status);
 }
 
 template <class R, class Src, class Map, class XT>
@@ -353,12 +384,10 @@ cudaError_t launch_substitute(const Src& src, Map sys, Map next, int m, const Le
                               int64_t total, void* zc, cudaStream_t st) {
     if (total == 0) return cudaSuccess;
     if (m > kSmemRowsMax)
-        k_substitute_gmem<R, Src, Map, XT><<<grid_for(total), kThreads, 0, st>>>(
-            src, sys, next, m, x_of<R>(nextL), x, static_cast<typename Store<R>::T*>(zc), status);
-    else
-        k_substitute<R, Src, Map, XT><<<grid_for(total), kThreads, subst_smem(m), st>>>(src, sys, next, m,
-                                                                                      x_of<R>(nextL), x, status);
-    return cudaGetLastError();
+        return launch(k_substitute_gmem<R, Src, Map, XT>, grid_for(total), kThreads, 0, st, src, sys, next, m,
+                      x_of<R>(nextL), x, static_cast<typename Store<R>::T*>(zc), status);
+    return launch(k_substitute<R, Src, Map, XT>, grid_for(total), kThreads, subst_smem(m), st, src, sys, next, m,
+                  x_of<R>(nextL), x, status);
 }
 
 // Opt the substitution kernels into the dynamic shared memory their largest block needs.
@@ -375,6 +404,8 @@ cudaError_t set_smem_limits_map(int m0, int ml) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_fused<R, -1, Map, Grid, true>, a, (int)fused_smem(m0));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr<R>, a, (int)cr_smem());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr_many<R>, a, (int)cr_smem());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_reduce_ws<R, Map>, a, (int)ws_reduce_smem(kWsRowsMax));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_substitute_ws<R, Map>, a, (int)ws_subst_smem(kWsRowsMax));
     return e;
 }
 
@@ -395,34 +426,47 @@ cudaError_t solve_levels(Engine* p, cudaStream_t st) {
     for (size_t l = 1; l + 1 < L && e == cudaSuccess; ++l) {
         ProfScope ps(p, kProfReduceL, st);
         with_maps(p, l, [&](auto a, auto b) {
-            e = launch_reduce<R>(level_source<R>(p->lv[l]), a, b, p->lv[l].m, p->lv[l + 1], p->status,
-                                 p->lv[l].total, st);
+            const LevelData& L = p->lv[l];
+            const LevelData& N = p->lv[l + 1];
+            if (two_group_level(p, l)) {
+                e = launch(k_reduce_ws<R, decltype(a)>, kWsCluster * grid_for(L.total), 2 * kWsLanes,
+                           ws_reduce_smem(L.m), st, level_source<R>(L), a, b, L.m, N.m, planes_of<R>(N),
+                           slot_of<R>(N), p->status);
+            } else {
+                e = launch_reduce<R>(level_source<R>(L), a, b, L.m, N, p->status, L.total, st);
+            }
         });
     }
     if (e != cudaSuccess) return e;
     {
         ProfScope ps(p, kProfBase, st);
         if (p->batched) {
-            k_base_cr_many<R><<<(unsigned)p->nsys, kCrThreads, cr_smem(), st>>>(
-                static_cast<const BaseSys<R>*>(p->d_base), p->status);
+            e = launch(k_base_cr_many<R>, (unsigned)p->nsys, kCrThreads, cr_smem(), st,
+                       static_cast<const BaseSys<R>*>(p->d_base), p->status);
         } else {
             const LevelData& B = p->lv[(size_t)p->base_level[0]];
             const LevelSource<R> src = level_source<R>(B).bind(B.sys[0]);
             if (p->lvl_m.empty())
-                k_base_cr<R><<<1, kCrThreads, cr_smem(), st>>>(src, x_of<R>(B), p->status);
+                e = launch(k_base_cr<R>, 1, kCrThreads, cr_smem(), st, src, x_of<R>(B), p->status);
             else if (p->base_cs)
-                k_base_serial<R><<<1, 32, 0, st>>>(src, x_of<R>(B), static_cast<typename Store<R>::T*>(p->base_cs),
-                                                   p->status);
+                e = launch(k_base_serial<R>, 1, 32, 0, st, src, x_of<R>(B),
+                           static_cast<typename Store<R>::T*>(p->base_cs), p->status);
             else
-                k_base<R><<<1, 32, 0, st>>>(src, x_of<R>(B), p->status);
+                e = launch(k_base<R>, 1, 32, 0, st, src, x_of<R>(B), p->status);
         }
-        e = cudaGetLastError();
     }
     for (size_t l = L - 2; l >= 1 && e == cudaSuccess; --l) {
         ProfScope ps(p, kProfSubstL, st);
         with_maps(p, l, [&](auto a, auto b) {
-            e = launch_substitute<R>(level_source<R>(p->lv[l]), a, b, p->lv[l].m, p->lv[l + 1], x_of<R>(p->lv[l]),
-                                     p->status, p->lv[l].total, p->zc, st);
+            const LevelData& L = p->lv[l];
+            const LevelData& N = p->lv[l + 1];
+            if (two_group_level(p, l)) {
+                e = launch(k_substitute_ws<R, decltype(a)>, (unsigned)ceil_div(L.total, kWsLanes), 2 * kWsLanes,
+                           ws_subst_smem(L.m), st, level_source<R>(L), a, b, L.m, x_of<R>(N), x_of<R>(L),
+                           p->status);
+            } else {
+                e = launch_substitute<R>(level_source<R>(L), a, b, L.m, N, x_of<R>(L), p->status, L.total, p->zc, st);
+            }
         });
     }
     return e;
@@ -465,11 +509,13 @@ cudaError_t cn_reduce0(Engine* p, const CNStep& s, cudaStream_t st) {
     const LevelData& L1 = p->lv[1];
     ProfScope ps(p, kProfReduce0, st);
     return with_es(s, [&](auto es) {
+        cudaError_t e = cudaSuccess;
         with_maps_grid(p, [&](auto a, auto b, auto gr) {
-            k_cn_reduce<R, decltype(es)::value><<<grid_for(L0.total), kThreads, 0, st>>>(
-                s, a, b, gr, L0.m, L1.m, planes_of<R>(L1), slot_of<R>(L1), static_cast<ST*>(p->keep), p->status);
+            e = launch(k_cn_reduce<R, decltype(es)::value, decltype(a), decltype(gr)>, grid_for(L0.total), kThreads,
+                       0, st, s, a, b, gr, L0.m, L1.m, planes_of<R>(L1), slot_of<R>(L1), static_cast<ST*>(p->keep),
+                       p->status);
         });
-        return cudaGetLastError();
+        return e;
     });
 }
 
@@ -482,18 +528,22 @@ cudaError_t cn_subst0(Engine* p, const CNStep& s, double2* x, cudaStream_t st) {
     ST* keep = static_cast<ST*>(p->keep);
     ProfScope ps(p, kProfSubst0, st);
     return with_es(s, [&](auto es) {
+        cudaError_t e = cudaSuccess;
         with_maps_grid(p, [&](auto a, auto b, auto gr) {
+            typedef decltype(a) M;
             if (keep && L0.m > kSmemRowsMax)
-                k_cn_substitute_kept_gmem<R><<<grid, kThreads, 0, st>>>(a, b, L0.m, keep, x_of<R>(L1), x,
-                                                                        static_cast<ST*>(p->zc));
+                e = launch(k_cn_substitute_kept_gmem<R, M>, grid, kThreads, 0, st, a, b, L0.m,
+                           static_cast<const ST*>(keep), static_cast<const ST*>(x_of<R>(L1)), x,
+                           static_cast<ST*>(p->zc));
             else if (keep)
-                k_cn_substitute_kept<R><<<grid, kThreads, kept_smem(L0.m), st>>>(a, b, L0.m, keep, x_of<R>(L1), x,
-                                                                                 p->status);
+                e = launch(k_cn_substitute_kept<R, M>, grid, kThreads, kept_smem(L0.m), st, a, b, L0.m,
+                           static_cast<const ST*>(keep), static_cast<const ST*>(x_of<R>(L1)), x, p->status);
             else
-                k_cn_substitute<R, decltype(es)::value><<<grid, kThreads, subst_smem(L0.m), st>>>(
-                    s, a, b, gr, L0.m, x_of<R>(L1), x, p->status);
+                e = launch(k_cn_substitute<R, decltype(es)::value, M, decltype(gr)>, grid, kThreads,
+                           subst_smem(L0.m), st, s, a, b, gr, L0.m, static_cast<const ST*>(x_of<R>(L1)), x,
+                           p->status);
         });
-        return cudaGetLastError();
+        return e;
     });
 }
 
@@ -506,15 +556,16 @@ cudaError_t cn_fused0(Engine* p, const CNStep& s, double2* x_out, cudaStream_t s
     const LevelData& L1 = p->lv[1];
     if (s.e * s.s != -1) return cudaErrorInvalidValue;
     ProfScope ps(p, kProfFused0, st);
+    cudaError_t e = cudaSuccess;
     with_maps_grid(p, [&](auto a, auto b, auto gr) {
         typedef decltype(a) M;
         typedef decltype(gr) G;
         auto kern = x_out ? k_cn_fused<R, -1, M, G, true> : k_cn_fused<R, -1, M, G, false>;
-        kern<<<grid_for(L0.total), kThreads, fused_smem(L0.m), st>>>(s, a, b, gr, L0.m, L1.m, x_of<R>(L1),
-                                                                     planes_of<R>(L1), slot_of<R>(L1),
-                                                                     static_cast<ST*>(p->keep), x_out, p->status);
+        e = launch(kern, grid_for(L0.total), kThreads, fused_smem(L0.m), st, s, a, b, gr, L0.m, L1.m,
+                   static_cast<const ST*>(x_of<R>(L1)), planes_of<R>(L1), slot_of<R>(L1), static_cast<ST*>(p->keep),
+                   x_out, p->status);
     });
-    return cudaGetLastError();
+    return e;
 }
 
 // One CN-type step of every system (level 0 generated on the fly), result in x.
@@ -629,6 +680,7 @@ cn_status create_engine(Engine* p, const cn_desc* desc, const std::vector<int64_
     if (p->desc.block == 0) p->desc.block = kDefaultBlock;
     if (p->desc.level_block == 0) p->desc.level_block = kDefaultLevelBlock;
     if (cudaGetDevice(&p->device) != cudaSuccess) return CN_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) return CN_ERR_CUDA;
     const int ns = (int)sizes.size();
     const int ncos = desc->pot == CN_POT_COSSERIES ? desc->n_cos : 0;
     if (ncos > 0) p->cos_a.assign(cos_a, cos_a + (size_t)ncos * (size_t)ns);

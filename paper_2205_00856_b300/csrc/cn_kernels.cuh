@@ -43,6 +43,8 @@
 #include "cn_arith.cuh"
 #include "cn_prefetch.cuh"
 
+#include <cooperative_groups.h>
+
 namespace cnb {
 
 constexpr int kThreads = 128;   // threads per CTA of the reduce / substitute kernels
@@ -60,6 +62,17 @@ constexpr int kStatusNonfinite = 6;  // cn_status CN_ERR_NONFINITE
 
 __device__ __forceinline__ void flag_error(int* status, int code) {
     if (status) atomicCAS(status, 0, code);
+}
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may be scheduled while its predecessor in the stream still
+// runs.  Every kernel here first waits for the predecessor to complete and its
+// memory to be visible (a no-op for an ordinary launch), before any access to
+// global memory, then lets its own successor launch: the successor's launch
+// latency and CTA ramp overlap this kernel's run instead of following it.
+__device__ __forceinline__ void grid_dep_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // ------------------------------------------------------------------ systems and levels
@@ -267,6 +280,7 @@ __device__ __forceinline__ void write_reduced_row(bool active, int64_t t, int64_
 template <class R, class Src, class Map>
 __global__ void __launch_bounds__(kThreads)
 k_reduce(Src src0, Map sys, Map next, int m, int m_next, LevelPlanes<R> out, LevelSlot<R>* out_slot, int* status) {
+    grid_dep_enter();
     const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const bool active = g < sys.total();
     bool ok = true;
@@ -349,6 +363,7 @@ template <> __device__ __forceinline__ void put<float4, df>(float4* p, cx<df> z)
 template <class R, class Src, class Map, class XT>
 __global__ void __launch_bounds__(kThreads)
 k_substitute(Src src0, Map sys, Map next, int m, const typename Store<R>::T* x_next0, XT* x0, int* status) {
+    grid_dep_enter();
     typedef typename Store<R>::T ST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ST* zs = reinterpret_cast<ST*>(smem_raw);   // [m][kThreads]
@@ -402,6 +417,7 @@ template <class R, class Src, class Map, class XT>
 __global__ void __launch_bounds__(kThreads)
 k_substitute_gmem(Src src0, Map sys, Map next, int m, const typename Store<R>::T* x_next0, XT* x0,
                   typename Store<R>::T* zc0, int* status) {
+    grid_dep_enter();
     typedef typename Store<R>::T ST;
     const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (g >= sys.total()) return;
@@ -439,6 +455,277 @@ k_substitute_gmem(Src src0, Map sys, Map next, int m, const typename Store<R>::T
     put<XT, R>(x + J0, xL);
     if (t == P - 1) put<XT, R>(x + J0 + gap, xR);
     if (!ok) flag_error(status, kStatusNonfinite);
+}
+
+// ------------------------------------------------------------------ small levels, two warp groups
+// A level of at most one CTA of kThreads blocks per SM leaves most SMs idle, and
+// each busy scheduler issues one block walk after another.  Here a CTA of
+// 2 kWsLanes threads takes kWsLanes blocks, so a group of kThreads blocks spreads
+// over a cluster of kWsCluster CTAs.  In each CTA the first warp runs the pivot
+// chain of its blocks (r_k and 1 / a_k of Table 1's RD; 1 / m_k and c'_k of the
+// substitution's forward sweep) and the second warp the recurrences that only
+// consume it (fill-ins, RU, JD, JU; z_k and the backward values), one named
+// barrier per row behind; both first stage the rows in shared memory.  The
+// operations and their order are those of k_reduce and k_substitute, so the
+// results are the same bits, and the reduced rows keep the kThreads-block slots
+// (the JD part that crosses a CTA inside a group goes through the cluster's
+// distributed shared memory).
+constexpr int kWsRowsMax = 16;  // one named barrier (ids 1..15) per row
+constexpr int kWsLanes = 32;    // blocks per CTA
+constexpr int kWsCluster = kThreads / kWsLanes;
+
+__device__ __forceinline__ void bar_arrive_id(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_sync_id(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Staged rows of the CTA's blocks: field f (0 b, 1 a, 2 c, 3 d) of row k of lane l
+// at ((f * rows + k) * kWsLanes + l).
+template <class R> struct WsRows {
+    typedef typename Store<R>::T ST;
+    ST* p;
+    int rows, lane;
+    __device__ __forceinline__ ST* at(int f, int k) const { return p + ((f * rows + k) * kWsLanes + lane); }
+    __device__ __forceinline__ cx<R> b(int k) const { return sload(at(0, k)); }
+    __device__ __forceinline__ cx<R> a(int k) const { return sload(at(1, k)); }
+    __device__ __forceinline__ cx<R> c(int k) const { return sload(at(2, k)); }
+    __device__ __forceinline__ cx<R> d(int k) const { return sload(at(3, k)); }
+    __device__ __forceinline__ void put(int k, const Row<R>& r) const {
+        sstore(at(0, k), r.b);
+        sstore(at(1, k), r.a);
+        sstore(at(2, k), r.c);
+        sstore(at(3, k), r.d);
+    }
+    // rows k0, k0 + 2, ... <= k1, four rows' loads in flight at a time
+    template <class F> __device__ __forceinline__ void stage(int k0, int k1, F row_k) const {
+        for (int k = k0; k <= k1; k += 8) {
+            Row<R> r[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (k + 2 * j <= k1) r[j] = row_k(k + 2 * j);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (k + 2 * j <= k1) put(k + 2 * j, r[j]);
+        }
+    }
+};
+
+// Shared memory of k_reduce_ws (rows 0..m, r_k, 1 / a_k) and of k_substitute_ws
+// (rows 1..m-1, 1 / m_k, c'_k; z_k over the a field), in storage entries.
+__host__ __device__ constexpr size_t ws_reduce_entries(int m) { return 6 * (size_t)(m + 1) * kWsLanes; }
+__host__ __device__ constexpr size_t ws_subst_entries(int m) { return 6 * (size_t)m * kWsLanes; }
+
+// write_reduced_row for a group of kThreads blocks spread over a cluster: block
+// (rank, lane) is block rank * kWsLanes + lane of the group.  Every thread of every
+// CTA of the cluster calls it; writers are the consumer warp's threads.
+template <class R>
+__device__ __forceinline__ void ws_write_reduced_row(bool writer, bool active, int lane, int64_t t, int64_t P,
+                                                     JDPart<R> jd, cx<R> A0, cx<R> D0, cx<R> JUa, cx<R> JUc,
+                                                     cx<R> JUd, cx<R> Ag, cx<R> Dg, const RowSink<R>& out,
+                                                     LevelSlot<R>* out_slot) {
+    namespace cg = cooperative_groups;
+    __shared__ JDPart<R> xch[kWsLanes];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    if (writer) xch[lane] = jd;
+    cl.sync();  // the JD parts of every CTA of the group visible to the others
+    if (writer && active) {
+        if (t > 0 && (lane > 0 || rank > 0)) {
+            const JDPart<R> pj = lane > 0 ? xch[lane - 1] : *cl.map_shared_rank(&xch[kWsLanes - 1], rank - 1);
+            out.put(t, pj.b, cadd(cadd(A0, JUa), pj.a), JUc, cadd(cadd(D0, JUd), pj.d));
+        } else {
+            out.put(t, czero<R>(), cadd(A0, JUa), JUc, cadd(D0, JUd));
+        }
+        if (t == P - 1) {
+            out.put(P, jd.b, cadd(Ag, jd.a), czero<R>(), cadd(Dg, jd.d));
+        } else if (lane == kWsLanes - 1 && rank == kWsCluster - 1) {
+            LevelSlot<R> s;
+            sstore(&s.b, jd.b);
+            sstore(&s.a, jd.a);
+            sstore(&s.d, jd.d);
+            out_slot[blockIdx.x / kWsCluster + 1] = s;
+        }
+    }
+    cl.sync();  // no CTA leaves while its neighbour may still read its JD part
+}
+
+template <class R, class Map>
+__global__ void __cluster_dims__(kWsCluster, 1, 1) __launch_bounds__(2 * kWsLanes)
+k_reduce_ws(LevelSource<R> src0, Map sys, Map next, int m, int m_next, LevelPlanes<R> out, LevelSlot<R>* out_slot,
+            int* status) {
+    grid_dep_enter();
+    typedef typename Store<R>::T ST;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lt = threadIdx.x & (kWsLanes - 1);
+    const bool pivots = threadIdx.x < kWsLanes;
+    const WsRows<R> S{reinterpret_cast<ST*>(smem_raw), m + 1, lt};
+    ST* sR = S.p + 4 * (m + 1) * kWsLanes;  // r_k of row k (k = gap: the JD factor)
+    ST* sW = sR + (m + 1) * kWsLanes;       // 1 / a_k after RD
+    const int64_t g = (int64_t)blockIdx.x * kWsLanes + lt;
+    const bool active = g < sys.total();
+    int64_t t = 0, P = 0;
+    int si = 0, gap = 0;
+    if (active) {
+        si = sys.find(g);
+        const LvlSys& e = sys.at(si);
+        const LevelSource<R> src = src0.bind(e);
+        const int64_t n = e.n;
+        P = e.P;
+        t = g - e.blk_off;
+        const int64_t J0 = joint_line(t, P, m, n);
+        gap = (int)(joint_line(t + 1, P, m, n) - J0);
+        // the two warps stage alternate rows 0..gap (row gap: row 0 of the next block)
+        S.stage(pivots ? 0 : 1, gap, [&](int k) {
+            return k < gap ? src.template row<R>(t, k, J0 + k) : src.template row<R>(t + 1, 0, J0 + k);
+        });
+    }
+    __syncthreads();
+    cx<R> JUa = czero<R>(), JUc = czero<R>(), JUd = czero<R>(), A0 = czero<R>(), D0 = czero<R>();
+    cx<R> Ag = czero<R>(), Dg = czero<R>();
+    JDPart<R> jd;
+    jd.b = czero<R>(); jd.a = czero<R>(); jd.d = czero<R>();
+    if (pivots) {
+        bool ok = true;
+        cx<R> w = czero<R>(), cprev = czero<R>();
+        if (active) {
+            w = crcp(S.a(1), ok);
+            sstore(sW + kWsLanes + lt, w);
+            cprev = S.c(1);
+        }
+        for (int k = 2; k <= m; ++k) {
+            if (active && k <= gap) {
+                // RD (k < gap) and JD (k = gap): r = -b_k / a_{k-1}; a_k += r c_{k-1}
+                const cx<R> r = cneg(cmul(S.b(k), w));
+                sstore(sR + k * kWsLanes + lt, r);
+                if (k < gap) {
+                    w = crcp(cfma(S.a(k), r, cprev), ok);
+                    sstore(sW + k * kWsLanes + lt, w);
+                    cprev = S.c(k);
+                }
+            }
+            bar_arrive_id(k - 1, 2 * kWsLanes);
+        }
+        if (!ok) flag_error(status, kStatusNonfinite);
+    } else {
+        cx<R> bRD = czero<R>(), dRD = czero<R>(), cprev = czero<R>(), Q = cfrom<R>(1.0, 0.0);
+        cx<R> nb = czero<R>(), nd = czero<R>();
+        if (active) {
+            bRD = S.b(1);
+            dRD = S.d(1);
+            cprev = S.c(1);
+            nb = bRD;
+            nd = dRD;
+        }
+        for (int k = 2; k <= m; ++k) {
+            bar_sync_id(k - 1, 2 * kWsLanes);
+            if (active && k < gap) {
+                const cx<R> r = sload(sR + k * kWsLanes + lt);
+                const cx<R> wk = sload(sW + k * kWsLanes + lt);
+                bRD = cmul(r, bRD);
+                dRD = cfma(S.d(k), r, dRD);
+                // RU coefficient of row k-1: rho_{k-1} = -c_{k-1} / a_k
+                Q = cmul(Q, cneg(cmul(cprev, wk)));
+                nb = cfma(nb, Q, bRD);
+                nd = cfma(nd, Q, dRD);
+                cprev = S.c(k);
+            }
+        }
+        if (active) {
+            const cx<R> nc = cmul(Q, cprev);
+            const cx<R> r = sload(sR + gap * kWsLanes + lt);
+            jd.b = cmul(r, bRD);
+            jd.a = cmul(r, cprev);
+            jd.d = cmul(r, dRD);
+            Ag = S.a(gap);
+            Dg = S.d(gap);
+            A0 = S.a(0);
+            D0 = S.d(0);
+            const cx<R> r0u = cneg(cmul(S.c(0), sload(sW + kWsLanes + lt)));
+            JUc = cmul(r0u, nc);
+            JUa = cmul(r0u, nb);
+            JUd = cmul(r0u, nd);
+        }
+    }
+    ws_write_reduced_row<R>(!pivots, active, lt, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg,
+                            RowSink<R>(out, next.at(si), m_next), out_slot);
+}
+
+template <class R, class Map>
+__global__ void __launch_bounds__(2 * kWsLanes)
+k_substitute_ws(LevelSource<R> src0, Map sys, Map next, int m, const typename Store<R>::T* x_next0,
+                typename Store<R>::T* x0, int* status) {
+    grid_dep_enter();
+    typedef typename Store<R>::T ST;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lt = threadIdx.x & (kWsLanes - 1);
+    const bool pivots = threadIdx.x < kWsLanes;
+    const WsRows<R> S{reinterpret_cast<ST*>(smem_raw), m, lt};
+    ST* sW = S.p + 4 * m * kWsLanes;  // 1 / m_k
+    ST* sC = sW + m * kWsLanes;       // c'_k
+    const int64_t g = (int64_t)blockIdx.x * kWsLanes + lt;
+    const bool active = g < sys.total();
+    int64_t t = 0, P = 0, J0 = 0;
+    int si = 0, gap = 0;
+    if (active) {
+        si = sys.find(g);
+        const LvlSys& e = sys.at(si);
+        const LevelSource<R> src = src0.bind(e);
+        const int64_t n = e.n;
+        P = e.P;
+        t = g - e.blk_off;
+        J0 = joint_line(t, P, m, n);
+        gap = (int)(joint_line(t + 1, P, m, n) - J0);
+        S.stage(pivots ? 1 : 2, gap - 1, [&](int k) { return src.template row<R>(t, k, J0 + k); });
+    }
+    __syncthreads();
+    if (pivots) {
+        // m_k = a_k - b_k c'_{k-1};  c'_k = c_k / m_k
+        bool ok = true;
+        cx<R> cpp = czero<R>();
+        for (int k = 1; k < m; ++k) {
+            if (active && k < gap) {
+                const cx<R> piv = (k == 1) ? S.a(k) : csub(S.a(k), cmul(S.b(k), cpp));
+                const cx<R> w = crcp(piv, ok);
+                cpp = cmul(S.c(k), w);
+                sstore(sW + k * kWsLanes + lt, w);
+                sstore(sC + k * kWsLanes + lt, cpp);
+            }
+            bar_arrive_id(k, 2 * kWsLanes);
+        }
+        if (!ok) flag_error(status, kStatusNonfinite);
+        return;
+    }
+    // z_k = (rhs_k - b_k z_{k-1}) / m_k, kept over a_k (read by the pivot group before its barrier k)
+    cx<R> xL = czero<R>(), xR = czero<R>(), zp = czero<R>();
+    if (active) {
+        const ST* x_next = x_next0 + next.at(si).row_off;
+        xL = sload(x_next + t);
+        xR = sload(x_next + t + 1);
+    }
+    for (int k = 1; k < m; ++k) {
+        bar_sync_id(k, 2 * kWsLanes);
+        if (active && k < gap) {
+            const cx<R> bk = S.b(k);
+            cx<R> rhs = S.d(k);
+            if (k == 1) rhs = csub(rhs, cmul(bk, xL));
+            if (k == gap - 1) rhs = csub(rhs, cmul(S.c(k), xR));
+            const cx<R> w = sload(sW + k * kWsLanes + lt);
+            zp = (k == 1) ? cmul(rhs, w) : cmul(csub(rhs, cmul(bk, zp)), w);
+            sstore(S.at(1, k), zp);
+        }
+    }
+    if (!active) return;
+    ST* x = x0 + sys.at(si).row_off;
+    cx<R> y = zp;
+    put<ST, R>(x + J0 + gap - 1, y);
+    for (int k = gap - 2; k >= 1; --k) {
+        y = csub(sload(S.at(1, k)), cmul(sload(sC + k * kWsLanes + lt), y));
+        put<ST, R>(x + J0 + k, y);
+    }
+    put<ST, R>(x + J0, xL);
+    if (t == P - 1) put<ST, R>(x + J0 + gap, xR);
 }
 
 // ------------------------------------------------------------------ RS stage
@@ -480,6 +767,7 @@ __device__ __forceinline__ void base_solve(const LevelSource<R>& src, typename S
 // (explicit nesting depth, where the last level can be long): z in x, c' in cs.
 template <class R>
 __global__ void k_base_serial(LevelSource<R> src, typename Store<R>::T* x, typename Store<R>::T* cs, int* status) {
+    grid_dep_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     bool ok = true;
     const int64_t n = src.n;
@@ -504,6 +792,7 @@ __global__ void k_base_serial(LevelSource<R> src, typename Store<R>::T* x, typen
 
 template <class R>
 __global__ void k_base(LevelSource<R> src, typename Store<R>::T* x, int* status) {
+    grid_dep_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     base_solve<R>(src, x, status);
 }
@@ -593,6 +882,7 @@ __device__ __forceinline__ void cr_solve(const LevelSource<R>& src, typename Sto
 template <class R>
 __global__ void __launch_bounds__(kCrThreads)
 k_base_cr(LevelSource<R> src, typename Store<R>::T* x, int* status) {
+    grid_dep_enter();
     cr_solve<R>(src, x, status);
 }
 
@@ -600,6 +890,7 @@ k_base_cr(LevelSource<R> src, typename Store<R>::T* x, int* status) {
 template <class R>
 __global__ void __launch_bounds__(kCrThreads)
 k_base_cr_many(const BaseSys<R>* sys, int* status) {
+    grid_dep_enter();
     const BaseSys<R> b = sys[blockIdx.x];
     cr_solve<R>(b.src, b.x, status);
 }
@@ -659,6 +950,7 @@ __device__ __forceinline__ double static_potential_d(const CNParams& p, int64_t 
 // tabulated once when the potential is not regenerated on the fly.
 template <class R>
 __global__ void k_beta0_table(CNParams p, SysGrid sg, int64_t n, R* tab) {
+    grid_dep_enter();
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     double x = fma((double)(j - sg.j_o), p.dx, sg.x_o);
@@ -924,6 +1216,7 @@ template <class R, int ES, class Map, class Grid>
 __global__ void __launch_bounds__(kThreads, ReduceOccupancy<R, Map>::min_blocks)
 k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, LevelPlanes<R> out, LevelSlot<R>* out_slot,
             typename Store<R>::T* keep0, int* status) {
+    grid_dep_enter();
     typedef typename Store<R>::T ST;
     const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const bool active = g < sys.total();
@@ -962,6 +1255,7 @@ template <class R, int ES, class Map, class Grid>
 __global__ void __launch_bounds__(kThreads)
 k_cn_substitute(CNStep st, Map sys, Map next, Grid grid, int m, const typename Store<R>::T* x_next0, double2* x0,
                 int* status) {
+    grid_dep_enter();
     typedef typename Store<R>::T ST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ST* zs = reinterpret_cast<ST*>(smem_raw);   // [m][kThreads]
@@ -1016,6 +1310,7 @@ template <class R, class Map>
 __global__ void __launch_bounds__(kThreads)
 k_cn_substitute_kept(Map sys, Map next, int m, const typename Store<R>::T* keep0,
                      const typename Store<R>::T* x_next0, double2* x0, int*) {
+    grid_dep_enter();
     typedef typename Store<R>::T ST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ST* zs = reinterpret_cast<ST*>(smem_raw);   // [m][kTileStride]
@@ -1105,6 +1400,7 @@ template <class R, class Map>
 __global__ void __launch_bounds__(kThreads)
 k_cn_substitute_kept_gmem(Map sys, Map next, int m, const typename Store<R>::T* keep0,
                           const typename Store<R>::T* x_next0, double2* x0, typename Store<R>::T* zs0) {
+    grid_dep_enter();
     typedef typename Store<R>::T ST;
     const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (g >= sys.total()) return;
@@ -1205,6 +1501,7 @@ template <class R, int ES, class Map, class Grid, bool kStore>
 __global__ void __launch_bounds__(kThreads, FusedOccupancy<R, Map>::min_blocks)
 k_cn_fused(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, const typename Store<R>::T* x_next0,
            LevelPlanes<R> out, LevelSlot<R>* out_slot, typename Store<R>::T* keep0, double2* x_out, int* status) {
+    grid_dep_enter();
     typedef typename Store<R>::T ST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ST* ys = reinterpret_cast<ST*>(smem_raw);  // [m + 2][kTileStride]
@@ -1347,6 +1644,7 @@ template <class R>
 __global__ void __launch_bounds__(kAdjThreads)
 k_adjoint_finish(CNParams p, SysGrid sg, int64_t n, const double2* mu, const double2* lam_np1, const double2* psi_n,
                  const double2* psi_np1, double2* lam_n, R* part, unsigned int* ticket, double dt, double* dLdE) {
+    grid_dep_enter();
     __shared__ R red[kAdjThreads];
     __shared__ bool last;
     R acc = RealOps<R>::from_d(0.0);
@@ -1392,6 +1690,7 @@ __device__ __forceinline__ void hat_locate(double t, double t_final, int64_t nc,
 
 static __global__ void k_hat_field(const double* u, int64_t nc, double t_final, double t0, double dt, int64_t nsteps,
                             double* E_mid) {
+    grid_dep_enter();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nsteps) return;
     int64_t i0;
@@ -1402,6 +1701,7 @@ static __global__ void k_hat_field(const double* u, int64_t nc, double t_final, 
 
 static __global__ void k_hat_field_grad(const double* dLdE, int64_t nsteps, double t_final, double t0, double dt,
                                  int64_t nc, double* g) {
+    grid_dep_enter();
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nc) return;
     const double h = t_final / (double)(nc - 1);

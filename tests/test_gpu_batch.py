@@ -93,6 +93,27 @@ def test_batch_equals_single_plans_bitwise(arith, blocks):
         assert np.array_equal(out[b.offsets[s]:b.offsets[s + 1]], ref), (s, n)
 
 
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_batch_two_group_levels(arith):
+    # systems deep enough that level 2 is reduced, by the two-warp-group kernels
+    # (few blocks per SM), across system boundaries inside a cluster
+    sizes = [200001, 3001, 150001, 77]
+    parts = batch_state(sizes, seed=3)
+    b = cnb.Batch(sizes, DX, DT, pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith, block=8, level_block=8,
+                  level1_block=8)
+    out = b.step(torch.from_numpy(np.concatenate(parts)).to(DEV), 4).cpu().numpy()
+    b.check()
+    for s, n in enumerate(sizes):
+        prob = oracle.Problem(n, DX, DT, -(n // 2) * DX, pot=oracle.POT_SOFTCOULOMB, soft_s=2.0)
+        got = out[b.offsets[s]:b.offsets[s + 1]]
+        assert rel(got, oracle.cn_run(prob, parts[s], 4)) <= 1e-11, (s, n)
+        p = cnb.Plan(n, DX, DT, -(n // 2) * DX, pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith,
+                     flags=cnb.FLAG_COEFF_TABLE, block=8, level_block=8, level1_block=8)
+        ref = p.step(torch.from_numpy(parts[s]).to(DEV), 4).cpu().numpy()
+        p.close()
+        assert np.array_equal(got, ref), (s, n)
+
+
 def test_batch_field_and_x_min_vs_oracle():
     sizes = [2000, 3001, 515]
     x_min = [-120.0, -150.05, -20.0]

@@ -31,9 +31,9 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-def plan_for(cfg, arith=cnb.ARITH_F64, block=0, flags=0):
+def plan_for(cfg, arith=cnb.ARITH_F64, block=0, flags=0, **kw):
     return cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cfg.get("pot", 0),
-                    soft_s=cfg.get("soft_s", 2.0), block=block, arith=arith, flags=flags)
+                    soft_s=cfg.get("soft_s", 2.0), block=block, arith=arith, flags=flags, **kw)
 
 
 def oracle_problem(cfg):
@@ -214,6 +214,31 @@ def test_last_row_after_full_tiles(n, block, arith):
         assert rel(out, ref) <= 1e-11 and abs(out[-1] - ref[-1]) <= 1e-12
         assert rel(st[-1], ref) <= 1e-11 and abs(st[-1][-1] - ref[-1]) <= 1e-12
     plan.check()
+    plan.close()
+
+
+# Reduced levels below level 1 with at most one CTA of blocks per SM run on the
+# two-warp-group kernels (clusters of four CTAs of 32 blocks): several clusters,
+# a partial last cluster with idle lanes, and the largest block they take (16).
+@pytest.mark.parametrize("n,blocks", [(200001, (8, 8, 8)), (1000003, (13, 10, 12)), (300001, (8, 8, 16)),
+                                      (400009, (4, 4, 3))])
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_two_group_levels_vs_oracle(n, blocks, arith):
+    m0, m1, ml = blocks
+    cfg = W.soft_coulomb_config(n=n, nsteps=3)
+    psi0 = W.gaussian(n, cfg["dx"], cfg["x_min"], 0.0, 0.05 * n * cfg["dx"], 0.8)  # amplitude on every level
+    E = W.field_midpoints(3, cfg["dt"], t0=150.0)
+    plan = plan_for(cfg, block=m0, level1_block=m1, level_block=ml, arith=arith)
+    rows = plan.info()["level_rows"]
+    assert len(rows) >= 4 and rows[2] > 1024  # level 2 is reduced
+    assert (rows[2] - 1) // ml <= 148 * 128  # ... by the two-group kernels
+    out = plan.step(to_dev(psi0), 3, E_mid=to_dev(E)).cpu().numpy()
+    st = plan.step_states(to_dev(psi0), 3, E_mid=to_dev(E)).cpu().numpy()
+    plan.check()
+    ref = oracle.cn_run(oracle_problem(cfg), psi0, 3, E_mid=E)
+    assert rel(out, ref) <= 1e-11
+    assert np.array_equal(st[-1], out) or arith == cnb.ARITH_DF64
+    assert rel(st[-1], ref) <= 1e-11
     plan.close()
 
 
