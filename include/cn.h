@@ -25,7 +25,11 @@
  *     frees it;
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream); device
  *     work is enqueued on it and the call returns without synchronising,
- *     except where stated;
+ *     except where stated; the kernels are launched with programmatic
+ *     stream serialization, so one may be scheduled while the work before
+ *     it in the stream still runs, but each waits on the device for that
+ *     work to complete before it reads or writes any memory: the effects
+ *     are in plain stream order;
  *   - argument errors are detected on the host before any work is enqueued
  *     and returned as a cn_status; nothing is enqueued then;
  *   - errors raised on the device (non-finite pivots, exhausted waits) are
