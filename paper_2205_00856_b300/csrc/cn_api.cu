@@ -402,6 +402,9 @@ cudaError_t set_smem_limits_map(int m0, int ml) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute<R, 0, Map, Grid>, a, (int)subst_smem(m0));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute_kept<R, Map>, a, (int)kept_smem(m0));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_fused<R, -1, Map, Grid, false>, a, (int)fused_smem(m0));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cn_fused<R, -1, Map, Grid, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_fused<R, -1, Map, Grid, true>, a, (int)fused_smem(m0));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr<R>, a, (int)cr_smem());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr_many<R>, a, (int)cr_smem());

@@ -245,12 +245,23 @@ template <class R> struct RowSink {
 // Writes row t of the next level from this block's JU part and the previous
 // block's JD part: from shared memory when that block ran in the same CTA, else
 // (first thread of a CTA, t > 0) the next level adds it from the CTA slot.  The
-// last block of a system also writes row P.
-template <class R>
+// last block of a system also writes row P.  kAlias: the exchange goes through
+// the first kThreads * sizeof(JDPart) bytes of `scratch` (the caller's dynamic
+// shared memory, free once every thread is past this call's first barrier)
+// instead of a static array, so the kernel holds no shared memory beside its tile.
+template <class R, bool kAlias = false>
 __device__ __forceinline__ void write_reduced_row(bool active, int64_t t, int64_t P, JDPart<R> jd, cx<R> A0, cx<R> D0,
                                                   cx<R> JUa, cx<R> JUc, cx<R> JUd, cx<R> Ag, cx<R> Dg,
-                                                  const RowSink<R>& out, LevelSlot<R>* out_slot) {
-    __shared__ JDPart<R> xch[kThreads];
+                                                  const RowSink<R>& out, LevelSlot<R>* out_slot,
+                                                  void* scratch = nullptr) {
+    JDPart<R>* xch;
+    if constexpr (kAlias) {
+        __syncthreads();  // every thread is done with the scratch it held
+        xch = reinterpret_cast<JDPart<R>*>(scratch);
+    } else {
+        __shared__ JDPart<R> xch_static[kThreads];
+        xch = xch_static;
+    }
     const int tid = threadIdx.x;
     xch[tid] = jd;
     __syncthreads();
@@ -1485,6 +1496,11 @@ template <class R, int ES> struct CNRowFused {
 // CTAs per SM the fused kernel is compiled for (as the level-0 reduction's: 6 for
 // double-float single systems, measured best against 5 and 4).
 template <class R, class Map> struct FusedOccupancy { static constexpr int min_blocks = ReduceOccupancy<R, Map>::min_blocks; };
+// One system: seven CTAs per SM (72 registers, a 24-byte spill; the row exchange
+// aliased into the tile so that seven tiles fit) measured 0.455 vs 0.472 ms per
+// step at N = 2^24 on B300 against six (80 registers, no spill); a batch keeps six
+// (seven spilled 72 bytes and ran 5 % slower).
+template <> struct FusedOccupancy<df, OneSys> { static constexpr int min_blocks = 7; };
 
 // SS of step n and the level-0 reduction of step n + 1 in one pass over the kept
 // values: the block's psi_{n+1} never leaves the SM (no store and reload of the
@@ -1578,9 +1594,11 @@ k_cn_fused(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, const typ
         rs.init(st, e, grid.at(si), J0, col);
         cn_reduce_block<R>(rs, gap, t == P - 1, keep, A0, D0, JUa, JUc, JUd, jd, Ag, Dg, ok);
     }
-    // (its barrier also orders every thread's tile writes before the tile store)
-    write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, RowSink<R>(out, next.at(si), m_next),
-                         out_slot);
+    // (its barrier also orders every thread's tile writes before the tile store;
+    // without the store, the exchange reuses the tile and the CTA holds no other
+    // shared memory: seven CTAs per SM fit at m = 13)
+    write_reduced_row<R, !kStore>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg,
+                                  RowSink<R>(out, next.at(si), m_next), out_slot, smem_raw);
     if (!ok) flag_error(status, kStatusNonfinite);
     if (kStore && regular) {  // uniform per CTA: every thread is active; rows 0..m-1 of each column
         double2* x = x_out + sys.at(s0).row_off;
