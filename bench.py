@@ -610,7 +610,7 @@ def largest_bench(torch, cnb, args, dev):
     n, dx, dt, nst = cfg["n"], cfg["dx"], cfg["dt"], cfg["nsteps"]
     arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
     kw = dict(pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith)
-    m0, ml, tt = cnb.autotune_plan(n, dx, dt, cfg["x_min"], candidates=[(8, 8), (12, 12), (16, 12)], steps=4,
+    m0, ml, tt = cnb.autotune_plan(n, dx, dt, cfg["x_min"], candidates=[(8, 8), (12, 12), (13, 12), (16, 12)], steps=4,
                                    repeats=1, **kw)
     torch.cuda.empty_cache()
     nw = 1 << 20
