@@ -6,9 +6,9 @@ One bench "step" is one Crank-Nicolson time step over the whole grid: the
 coefficient generation, explicit half-step, N-shaped reduction (RD+JD, RU+JU)
 on every nesting level, the RS stage and the substitution (SS) back down.  The
 timed region runs the steps through cn_step calls of --steps-per-call steps
-each (default 50: the step loop of a propagation, where one step's level-0
-substitution and the next step's level-0 reduction run as one kernel and only
-the last step of a call writes psi; 1: one call per step).  Field samples
+each (default 1000, the whole propagation in one call: the step loop, where one
+step's level-0 substitution and the next step's level-0 reduction run as one
+kernel and only the last step of a call writes psi; 1: one call per step).  Field samples
 E(t + dt/2) follow the sin^2 pulse over the 1000-step run.  The level-0 arrays
 (state 256 MiB, kept values 512 MiB) are larger than the 126 MB L2, so no flush
 is needed between steps.
@@ -666,12 +666,13 @@ def main():
     ap.add_argument("--arith", choices=["f64", "df64"], default="df64")
     ap.add_argument("--f64-steps", type=int, default=100,
                     help="also time the native-FP64 path for this many steps (0: skip)")
-    # 13 / level 1: 10 / 12, from sweeps on B300 of the fused step loop (level-0 blocks
+    # 13 / level 1: 10 / 16, from sweeps on B300 of the fused step loop (level-0 blocks
     # 10..16: 13 best, 0.482 vs 0.485 ms at 12; the top candidates are within 1 % of
     # each other, so a run-time pick would wander between them and away from the
-    # block size the committed ncu captures were taken at)
+    # block size the committed ncu captures were taken at; level blocks 12..16 with
+    # the two-group kernels on levels 2 and 3: 16 best, 0.4531 vs 0.4544 ms at 12)
     ap.add_argument("--block", type=int, default=13, help="level-0 block rows (0: autotune with --level-block)")
-    ap.add_argument("--level-block", type=int, default=12, help="rows per block on levels >= 1 (0: autotune)")
+    ap.add_argument("--level-block", type=int, default=16, help="rows per block on levels >= 1 (0: autotune)")
     # level 1 in blocks of 10: 0.502 vs 0.506 ms per step at 12 (swept 10..24 with level blocks 8 and 12)
     ap.add_argument("--level1-block", type=int, default=10, help="rows per block on level 1 alone (0: --level-block)")
     ap.add_argument("--coeff-table", dest="coeff_table", action="store_true", default=True,
@@ -679,7 +680,8 @@ def main():
     ap.add_argument("--no-coeff-table", dest="coeff_table", action="store_false",
                     help="regenerate V(x) every step instead")
     ap.add_argument("--n", type=int, default=1 << 24, help="grid points (profiling runs use smaller grids)")
-    ap.add_argument("--steps-per-call", type=int, default=50,
+    # 1000 (the propagation's length): 0.4494 vs 0.4544 ms per step in calls of 50
+    ap.add_argument("--steps-per-call", type=int, default=1000,
                     help="CN steps per cn_step call in the timed region (1: one call per step)")
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--e2e-inner", type=int, default=50, help="CN steps per end-to-end call")

@@ -308,17 +308,17 @@ def test_full_size_soft_coulomb_2pow24(arith, blocks, flags):
     assert abs(np.sum(np.abs(out) ** 2) / np.sum(np.abs(psi0) ** 2) - 1) <= 1e-12
 
 
-@pytest.mark.parametrize("block,level1_block", [(13, 10), (12, 10), (13, 20)])
-def test_full_size_soft_coulomb_2pow24_bench_configuration(block, level1_block):
+@pytest.mark.parametrize("block,level1_block,level_block", [(13, 10, 16), (13, 10, 12), (12, 10, 12), (13, 20, 12)])
+def test_full_size_soft_coulomb_2pow24_bench_configuration(block, level1_block, level_block):
     # bench.py's launch configuration: double-float, blocks 13 / level-1 blocks 10 /
-    # level blocks 12, static diagonal part tabulated, the steps in one call (fused
-    # step loop); the previous default (12) and a level-1 block of 20
+    # level blocks 16, static diagonal part tabulated, the steps in one call (fused
+    # step loop); the previous defaults and a level-1 block of 20
     f = _full_size_reference()
     cfg, nsteps, psi0, E, ref = f["cfg"], f["nsteps"], f["psi0"], f["E"], f["ref"]
     plan = cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0,
-                    arith=cnb.ARITH_DF64, block=block, level_block=12, level1_block=level1_block,
+                    arith=cnb.ARITH_DF64, block=block, level_block=level_block, level1_block=level1_block,
                     flags=cnb.FLAG_COEFF_TABLE)
-    assert plan.info()["level_block"][:3] == [block, level1_block, 12]
+    assert plan.info()["level_block"][:3] == [block, level1_block, level_block]
     out = plan.step(to_dev(psi0), nsteps, E_mid=to_dev(E)).cpu().numpy()
     plan.check()
     plan.close()
