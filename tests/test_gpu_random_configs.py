@@ -49,7 +49,7 @@ def _case(seed):
     return c
 
 
-@pytest.mark.parametrize("seed", range(60))
+@pytest.mark.parametrize("seed", range(200))
 def test_random_configuration_vs_oracle(seed):
     c = _case(seed)
     n = c["n"]
