@@ -294,7 +294,12 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
+    # a window of the N = 2^24 grid per step: 2^21 points for up to 300 steps, smaller
+    # (a power of two, at least 2^16) for longer runs, so that a run stays within
+    # about a minute of host time whatever --steps is
     n = 1 << 21
+    while n > (1 << 16) and n * max(args.steps, 1) > 300 * (1 << 21):
+        n >>= 1
     cfg = W.soft_coulomb_config(n=n)
     prob = oracle.Problem(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=oracle.POT_SOFTCOULOMB, soft_s=2.0)
     psi = W.initial_state(cfg)
@@ -307,8 +312,8 @@ def run_reference(args):
         psi = oracle.cn_run(prob, psi, 1, E_mid=E[j:j + 1])
     el = time.perf_counter() - t0
     value = n * args.steps / el
-    sample = (f"each step: one CN step of the serial FP64 oracle on a 2^21-point window of the N=2^24 "
-              f"soft-Coulomb grid")
+    sample = (f"each step: one CN step of the serial FP64 oracle on a 2^{n.bit_length() - 1}-point window of the "
+              f"N=2^24 soft-Coulomb grid")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
