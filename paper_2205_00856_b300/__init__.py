@@ -36,7 +36,7 @@ EXPORTS = ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_s
            "cn_batch_step", "cn_batch_status", "cn_plan_create_levels", "cn_step_states")
 NOALLOC_MAX_N = 1048576
 # (level-0 block, level block) pairs autotune_plan tries by default
-PLAN_TUNE_CANDIDATES = tuple((m0, ml) for m0 in (8, 10, 12, 16) for ml in (8, 12, 16, 24))
+PLAN_TUNE_CANDIDATES = tuple((m0, ml) for m0 in (8, 10, 12, 13, 16) for ml in (8, 12, 16, 24))
 MAX_LEVELS = 24
 PROFILE_CLASSES = ("reduce_level0", "substitute_level0", "reduce_levels_ge1", "substitute_levels_ge1", "rs_stage",
                    "fused_level0")
