@@ -289,17 +289,22 @@ def cpu_baseline_batched(cfg: dict, budget_s: float = 10.0) -> dict:
                       f"over {procs} processes, largest first ({el:.1f} s)", **host_info()}
 
 
+def reference_window(steps: int) -> int:
+    """Points of the N = 2^24 grid the reference arm steps per bench step: 2^21 for up
+    to 300 steps, halved (a power of two, at least 2^16) while the run would hold more
+    than 300 x 2^21 unknown-steps, so that it stays near a minute of host time."""
+    n = 1 << 21
+    while n > (1 << 16) and n * max(steps, 1) > 300 * (1 << 21):
+        n >>= 1
+    return n
+
+
 def run_reference(args):
     rank = env_int("RANK", 0)
     if rank != 0:
         return 0
     import oracle
-    # a window of the N = 2^24 grid per step: 2^21 points for up to 300 steps, smaller
-    # (a power of two, at least 2^16) for longer runs, so that a run stays within
-    # about a minute of host time whatever --steps is
-    n = 1 << 21
-    while n > (1 << 16) and n * max(args.steps, 1) > 300 * (1 << 21):
-        n >>= 1
+    n = reference_window(args.steps)
     cfg = W.soft_coulomb_config(n=n)
     prob = oracle.Problem(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=oracle.POT_SOFTCOULOMB, soft_s=2.0)
     psi = W.initial_state(cfg)

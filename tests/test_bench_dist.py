@@ -85,6 +85,17 @@ def test_reference_arm_rank0_line(monkeypatch, capsys):
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
 
 
+def test_reference_arm_window_bounds_the_run():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reference_window(1) == bench.reference_window(300) == 1 << 21
+    assert bench.reference_window(2000) == 1 << 18  # the default run: ~5e8 unknown-steps
+    assert bench.reference_window(10 ** 7) == 1 << 16  # the floor
+    for k in (1, 50, 300, 301, 1000, 2000, 5000):
+        n = bench.reference_window(k)
+        assert n & (n - 1) == 0 and (n * k <= 300 * (1 << 21) or n == 1 << 16)
+
+
 def _dying_rank_main(rank, world, port, q):
     import datetime
     sys.path.insert(0, ROOT)
