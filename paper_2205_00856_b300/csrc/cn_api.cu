@@ -335,9 +335,11 @@ void with_maps_grid(const Engine* p, F f) {
 }
 
 // --------------------------------------------------------------- launches
-// Every kernel of the solve and step paths is launched with programmatic stream
-// serialization: it may be scheduled while the previous kernel in the stream is
-// still running and waits on the device (grid_dep_enter) for its results.
+// Launches a kernel of the solve and step paths.  pdl (a single system's plan
+// outside the adjoint step, Engine::pdl): programmatic stream serialization, so the
+// kernel may be scheduled while the previous kernel in the stream still runs; it
+// waits on the device (grid_dep_enter) for that kernel's results before touching
+// memory.  Otherwise an ordinary stream-ordered launch.
 template <class... KArgs, class... Args>
 cudaError_t launch(bool pdl, void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
                    Args&&... args) {
