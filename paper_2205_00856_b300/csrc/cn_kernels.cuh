@@ -538,13 +538,18 @@ __device__ __forceinline__ void ws_write_reduced_row(bool writer, bool active, i
                                                      LevelSlot<R>* out_slot) {
     namespace cg = cooperative_groups;
     __shared__ JDPart<R> xch[kWsLanes];
+    __shared__ JDPart<R> from_prev;  // the previous CTA's last JD part, stored here by that CTA
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    if (writer) xch[lane] = jd;
-    cl.sync();  // the JD parts of every CTA of the group visible to the others
+    if (writer) {
+        xch[lane] = jd;
+        if (lane == kWsLanes - 1 && rank < kWsCluster - 1) *cl.map_shared_rank(&from_prev, rank + 1) = jd;
+    }
+    // the JD parts in place; after this barrier no CTA touches another's shared memory
+    cl.sync();
     if (writer && active) {
         if (t > 0 && (lane > 0 || rank > 0)) {
-            const JDPart<R> pj = lane > 0 ? xch[lane - 1] : *cl.map_shared_rank(&xch[kWsLanes - 1], rank - 1);
+            const JDPart<R> pj = lane > 0 ? xch[lane - 1] : from_prev;
             out.put(t, pj.b, cadd(cadd(A0, JUa), pj.a), JUc, cadd(cadd(D0, JUd), pj.d));
         } else {
             out.put(t, czero<R>(), cadd(A0, JUa), JUc, cadd(D0, JUd));
@@ -559,7 +564,6 @@ __device__ __forceinline__ void ws_write_reduced_row(bool writer, bool active, i
             out_slot[blockIdx.x / kWsCluster + 1] = s;
         }
     }
-    cl.sync();  // no CTA leaves while its neighbour may still read its JD part
 }
 
 template <class R, class Map>
