@@ -255,8 +255,10 @@ cn_status cn_plan_profile_read(cn_plan plan, double* ms, int64_t* launches, int3
  *     before any work is enqueued;
  *   arith: CN_ARITH_F64 or CN_ARITH_DF64; blocks of 8 rows on every level;
  *   stream: as elsewhere; the call returns without synchronising.
- * The first call on each device looks up the device address of the array
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call looks up the device address of the array on the current device
+ * (cudaGetSymbolAddress), so a device reset between calls is harmless; the
+ * first call on a device also loads the library's kernels there, so make that
+ * first call before any stream capture.
  * Every call uses the same array: calls that may overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  * Each call writes every scratch word it reads, so nothing has to be cleared

@@ -38,6 +38,10 @@ NOALLOC_MAX_N = 1048576
 # (level-0 block, level block) pairs autotune_plan tries by default
 PLAN_TUNE_CANDIDATES = tuple((m0, ml) for m0 in (8, 10, 12, 13, 16) for ml in (8, 12, 16, 24))
 MAX_LEVELS = 24
+# Launch configuration for large single systems (N ~ 2^24, coefficient table on),
+# from block-size sweeps of the soft-Coulomb step on B300: (level-0 block, level-1
+# block, block of the deeper levels) per arithmetic.
+LARGE_GRID_BLOCKS = {ARITH_F64: (13, 10, 16), ARITH_DF64: (13, 10, 16)}
 PROFILE_CLASSES = ("reduce_level0", "substitute_level0", "reduce_levels_ge1", "substitute_levels_ge1", "rs_stage",
                    "fused_level0")
 

@@ -58,7 +58,7 @@ struct Engine {
     SysGrid* d_grid = nullptr;    // device copy (batches)
     double2* state = nullptr;     // ping-pong state (recompute mode)
     void* keep = nullptr;         // 2 m entries per level-0 block: d^ and pivot (store mode)
-    void* tab = nullptr;          // bt0 table (compute type) or NULL
+    void* tab = nullptr;          // coefficient table (CoefTab<R>::T per row) or NULL
     int* status = nullptr;        // device status word
     CNParams cnp;
     std::vector<double> cos_a;    // n_cos coefficients per system
@@ -657,7 +657,8 @@ cudaError_t cn_steps(Engine* p, const double2* in, double2* out, const double* E
     return cudaSuccess;
 }
 
-size_t real_size(int arith) { return arith == CN_ARITH_DF64 ? sizeof(df) : sizeof(double); }
+// bytes per row of the coefficient table (CoefTab: bt0 in double-float, {bt0, x} in binary64)
+size_t table_entry_size(int arith) { return arith == CN_ARITH_DF64 ? sizeof(df) : sizeof(double2); }
 
 DFc split(double v) {
     df d = df_from_double(v);
@@ -715,8 +716,8 @@ cn_status create_engine(Engine* p, const cn_desc* desc, const std::vector<int64_
     if (e == cudaSuccess) e = cudaMalloc(&p->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(int));
     if (e == cudaSuccess && use_table) {
-        p->workspace_bytes += (int64_t)(real_size(desc->arith) * (size_t)rows0);
-        e = cudaMalloc(&p->tab, real_size(desc->arith) * (size_t)rows0);
+        p->workspace_bytes += (int64_t)(table_entry_size(desc->arith) * (size_t)rows0);
+        e = cudaMalloc(&p->tab, table_entry_size(desc->arith) * (size_t)rows0);
     }
     p->grid.resize(ns);
     for (int s = 0; s < ns; ++s) p->grid[s] = make_grid(x_min[s], desc->dx, sizes[s]);
@@ -756,7 +757,7 @@ cn_status create_engine(Engine* p, const cn_desc* desc, const std::vector<int64_
             }
             const unsigned g = (unsigned)ceil_div(sizes[s], 256);
             if (df_mode) k_beta0_table<df><<<g, 256>>>(cs, p->grid[s], sizes[s], static_cast<df*>(p->tab) + ro);
-            else k_beta0_table<double><<<g, 256>>>(cs, p->grid[s], sizes[s], static_cast<double*>(p->tab) + ro);
+            else k_beta0_table<double><<<g, 256>>>(cs, p->grid[s], sizes[s], static_cast<double2*>(p->tab) + ro);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -104,6 +104,36 @@ CNB_HD double d_from_bits(int64_t i) {
     double a; memcpy(&a, &i, 8); return a;
 #endif
 }
+// 1/q for binary64 q, without a division and without an FP64 comparison.
+// Seed: the top 23 bits of q's significand as a binary32 value f in [1, 2),
+// its correctly rounded binary32 reciprocal r, and q's exponent applied with
+// integer operations, so y0 = r 2^-e with |1 - q y0| <= 2^-23 + 2^-24 (the
+// truncation of f and the rounding of 1/f).  Refinement: with e = 1 - q y0,
+// 1/q = y0 / (1 - e) = y0 (1 + e + e^2 + e^3 + ...), and y = y0 + y0 (e + e^2)
+// is the series truncated after its quadratic term (the series form of the
+// Newton-Raphson reciprocal iteration: Goldschmidt, MIT thesis 1964; Markstein,
+// IBM J. Res. Dev. 34(1), 1990): three binary64 FMAs.  Error: the omitted
+// e^3 + ... < 2^-66 relative, the roundings of e and e + e^2 below 2^-74
+// relative, and the final rounding of y, 1/2 ulp: |y - 1/q| <= (1/2 + 2^-12) ulp.
+// Range: positive normal q with biased exponent 1..2044 (so that 1/q is
+// normal); anything else (zero, subnormal, negative, huge, inf, NaN) clears
+// `ok` and returns NaN.  The checks run on integer bits.  Bit-reproducible on
+// host and device (correctly rounded binary32 reciprocal, binary64 FMA).
+CNB_HD double d_rcp(double q, bool& ok) {
+    const int64_t b = d_bits(q);
+    const uint32_t hi = (uint32_t)((uint64_t)b >> 32);
+    const uint32_t E = hi >> 20;  // sign and biased exponent: 1..2044 for the valid range
+    const float f = f_from_bits((int32_t)(0x3F800000u | ((hi & 0xFFFFFu) << 3) | ((uint32_t)b >> 29)));
+    const int32_t rb = f_bits(f_rcp(f));  // r in (1/2, 1]
+    const int64_t ye = (int64_t)(rb >> 23) + 1919 - (int64_t)E;  // biased exponent of r 2^-e
+    const double y0 = d_from_bits((int64_t)((uint64_t)ye << 52) | ((int64_t)(rb & 0x7FFFFF) << 29));
+    const double e = fma(-q, y0, 1.0);
+    const double y = fma(y0, fma(e, e, e), y0);
+    const bool in = (E - 1u) < 2044u;
+    ok = ok && in;
+    return in ? y : d_from_bits(0x7FF8000000000000ll);
+}
+
 CNB_HD float i2f(int32_t i) {
 #ifdef __CUDA_ARCH__
     return __int2float_rn(i);
@@ -308,10 +338,11 @@ CNB_HD cx<double> csub2mul(cx<double> c, cx<double> a, cx<double> b, cx<double> 
     return mk(fma(-a.re, b.re, fma(a.im, b.im, fma(-e.re, f.re, fma(e.im, f.im, c.re)))),
               fma(-a.re, b.im, fma(-a.im, b.re, fma(-e.re, f.im, fma(-e.im, f.re, c.im)))));
 }
+// 1/z = conj(z) / |z|^2, the real reciprocal by d_rcp (ok cleared for |z|^2
+// zero, subnormal, above 2^1021 or not finite)
 CNB_HD cx<double> crcp(cx<double> z, bool& ok) {
-    double m2 = fma(z.re, z.re, z.im * z.im);
-    ok = ok && (m2 > 0.0 && m2 < 1.0e300);
-    double q = 1.0 / m2;
+    const double m2 = fma(z.re, z.re, z.im * z.im);
+    const double q = d_rcp(m2, ok);
     return mk(z.re * q, -(z.im * q));
 }
 

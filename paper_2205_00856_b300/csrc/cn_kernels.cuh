@@ -491,6 +491,16 @@ __device__ __forceinline__ void bar_arrive_id(int id, int count) {
 __device__ __forceinline__ void bar_sync_id(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
+// Split cluster barrier.  A CTA may touch another CTA's shared memory only once
+// that CTA is known to be running: every thread arrives at kernel entry
+// (relaxed: nothing is published yet) and waits just before the first remote
+// store, by which time the other CTAs have long arrived, so the wait costs
+// nothing and the staging and pivot work overlap it.  Every thread of every CTA
+// of the cluster executes both, unconditionally.
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait;" ::: "memory"); }
 
 // Staged rows of the CTA's blocks: field f (0 b, 1 a, 2 c, 3 d) of row k of lane l
 // at ((f * rows + k) * kWsLanes + l).
@@ -530,7 +540,8 @@ __host__ __device__ constexpr size_t ws_subst_entries(int m) { return 6 * (size_
 
 // write_reduced_row for a group of kThreads blocks spread over a cluster: block
 // (rank, lane) is block rank * kWsLanes + lane of the group.  Every thread of every
-// CTA of the cluster calls it; writers are the consumer warp's threads.
+// CTA of the cluster calls it, once, after arriving at the split cluster barrier
+// at kernel entry (cluster_arrive_relaxed); writers are the consumer warp's threads.
 template <class R>
 __device__ __forceinline__ void ws_write_reduced_row(bool writer, bool active, int lane, int64_t t, int64_t P,
                                                      JDPart<R> jd, cx<R> A0, cx<R> D0, cx<R> JUa, cx<R> JUc,
@@ -541,6 +552,9 @@ __device__ __forceinline__ void ws_write_reduced_row(bool writer, bool active, i
     __shared__ JDPart<R> from_prev;  // the previous CTA's last JD part, stored here by that CTA
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
+    // pairs with cluster_arrive_relaxed() at kernel entry: every CTA of the
+    // cluster has started, so the remote store below lands in live shared memory
+    cluster_wait();
     if (writer) {
         xch[lane] = jd;
         if (lane == kWsLanes - 1 && rank < kWsCluster - 1) *cl.map_shared_rank(&from_prev, rank + 1) = jd;
@@ -570,6 +584,7 @@ template <class R, class Map>
 __global__ void __cluster_dims__(kWsCluster, 1, 1) __launch_bounds__(2 * kWsLanes)
 k_reduce_ws(LevelSource<R> src0, Map sys, Map next, int m, int m_next, LevelPlanes<R> out, LevelSlot<R>* out_slot,
             int* status) {
+    cluster_arrive_relaxed();  // waited for in ws_write_reduced_row, before the remote store
     grid_dep_enter();
     typedef typename Store<R>::T ST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -961,45 +976,59 @@ __device__ __forceinline__ double static_potential_d(const CNParams& p, int64_t 
     }
 }
 
-// bt0_j = 2 + c1 Vs(x_j): the static part of the scaled diagonal of one system,
-// tabulated once when the potential is not regenerated on the fly.
+// Coefficient table of one system, built once when the potential is not
+// regenerated on the fly.  Double-float: bt0_j = 2 + c1 Vs(x_j), the static part
+// of the scaled diagonal (8 B per row).  Binary64: the pair {bt0_j, x_j} (16 B
+// per row), so that a step forms bt_j = bt0_j + c1 E x_j with one FMA and no
+// coordinate arithmetic; the FP64 kernels are bound by the FP64 pipe, not by
+// the 8 extra bytes per row.
+template <class R> struct CoefTab { typedef R T; };
+template <> struct CoefTab<double> { typedef double2 T; };
+__device__ __forceinline__ df coef_entry(double b0, double, df) { return df_from_double(b0); }
+__device__ __forceinline__ double2 coef_entry(double b0, double x, double) { return make_double2(b0, x); }
+
 template <class R>
-__global__ void k_beta0_table(CNParams p, SysGrid sg, int64_t n, R* tab) {
+__global__ void k_beta0_table(CNParams p, SysGrid sg, int64_t n, typename CoefTab<R>::T* tab) {
     grid_dep_enter();
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     double x = fma((double)(j - sg.j_o), p.dx, sg.x_o);
-    tab[j] = RealOps<R>::from_d(fma(p.c1, static_potential_d(p, j, x), 2.0));
+    tab[j] = coef_entry(fma(p.c1, static_potential_d(p, j, x), 2.0), x, R());
 }
 
 // Per-thread coefficient generator walking rows j0, j0+1, ...: returns bt_j for
 // the field value E (the same midpoint field for T and T^dagger, Sec. 2).
 template <class R> struct CoefGen;
 
+// The row offset from the origin point, j - j_o, is carried as a binary64
+// counter (exact below 2^53), so x_j = x_o + (j - j_o) dx costs one FMA and no
+// integer-to-binary64 conversion per row.
 template <> struct CoefGen<double> {
     const CNParams* p;
-    const double* tab;
+    const double2* tab;
     const double* V0;
     SysGrid sg;
-    double c1E, x;
+    double c1E, dj;
     int64_t j;
-    __device__ __forceinline__ double xj(int64_t jj) const { return fma((double)(jj - sg.j_o), p->dx, sg.x_o); }
-    __device__ __forceinline__ void init(const CNParams& pp, const SysGrid& g, const double* tb, const double* v0,
+    __device__ __forceinline__ void init(const CNParams& pp, const SysGrid& g, const double2* tb, const double* v0,
                                          double E, int64_t j0) {
         p = &pp; sg = g; tab = tb; V0 = v0; j = j0;
         c1E = pp.c1 * E;
-        x = xj(j0);
+        dj = (double)(j0 - g.j_o);
     }
     __device__ __forceinline__ void next(double& bt) {
-        double b0;
-        if (tab) b0 = tab[j];
-        else if (p->pot == 1) b0 = fma(p->c1, V0[j], 2.0);
-        else b0 = fma(p->c1, static_potential_d(*p, j, x), 2.0);
-        bt = fma(c1E, x, b0);
+        if (tab) {
+            const double2 v = tab[j];
+            bt = fma(c1E, v.y, v.x);
+        } else {
+            const double x = fma(dj, p->dx, sg.x_o);
+            const double b0 = p->pot == 1 ? fma(p->c1, V0[j], 2.0) : fma(p->c1, static_potential_d(*p, j, x), 2.0);
+            bt = fma(c1E, x, b0);
+        }
         ++j;
-        x = xj(j);
+        dj += 1.0;
     }
-    __device__ __forceinline__ void skip() { ++j; x = xj(j); }
+    __device__ __forceinline__ void skip() { ++j; dj += 1.0; }
 };
 
 template <> struct CoefGen<df> {
@@ -1079,7 +1108,7 @@ struct CNStep {
     int s, e;             // T_s = 1 + i s dt/2 H(E);  explicit S_e = 1 + i e dt/2 H(E);
                           // e = 0: the right-hand side is psi itself
     const double* E;      // the field at the step's midpoint (both matrices)
-    const void* tab;      // bt0 table in the compute type, or NULL (regenerate)
+    const void* tab;      // coefficient table (CoefTab<R>::T per row), or NULL (regenerate)
 };
 
 __device__ __forceinline__ double rneg(double a) { return -a; }
@@ -1110,7 +1139,8 @@ template <class R, int ES> struct CNRowStream {
         psi = st.psi + e.row_off;
         n = e.n;
         i = j0;
-        const R* tab = st.tab ? static_cast<const R*>(st.tab) + e.row_off : nullptr;
+        const typename CoefTab<R>::T* tab =
+            st.tab ? static_cast<const typename CoefTab<R>::T*>(st.tab) + e.row_off : nullptr;
         cg.init(st.p, g, tab, st.p.V0 ? st.p.V0 + e.row_off : nullptr, E, j0);
         pm = czero<R>();  // row j0 is a joint row: its stencil term with psi_{j0-1} is the block above's
         p0 = ld(j0);
@@ -1464,7 +1494,8 @@ template <class R, int ES> struct CNRowFused {
         const double E = st.E ? *st.E : 0.0;
         sg = signed_gt(st, R());
         msg = rneg(sg);
-        const R* tab = st.tab ? static_cast<const R*>(st.tab) + e.row_off : nullptr;
+        const typename CoefTab<R>::T* tab =
+            st.tab ? static_cast<const typename CoefTab<R>::T*>(st.tab) + e.row_off : nullptr;
         cg.init(st.p, g, tab, st.p.V0 ? st.p.V0 + e.row_off : nullptr, E, J0);
         ys = col;
         k = 0;

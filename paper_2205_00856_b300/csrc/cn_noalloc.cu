@@ -11,7 +11,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 
 #include "../../include/cn.h"
 #include "cn_kernels.cuh"
@@ -22,7 +21,6 @@ namespace {
 
 constexpr int kNaBlock = 8;            // rows per block on every level
 constexpr size_t kNaScratchBytes = 16u << 20;  // 16 MiB, enough for CN_NOALLOC_MAX_N rows
-constexpr int kNaMaxDevices = 64;
 constexpr int kNaMaxLevels = CN_MAX_LEVELS;
 
 }  // namespace
@@ -33,23 +31,15 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes
 
 namespace {
 
-std::mutex g_na_mutex;
-void* g_na_ptr[kNaMaxDevices] = {};
-
-// Device address of g_noalloc_scratch on the current device, looked up once per device.
+// Device address of g_noalloc_scratch on the current device.  Looked up on every
+// call rather than cached: after a device reset (or any re-creation of the
+// primary context) a cached address would be stale, and the lookup is cheap
+// next to the solve's launches.
 cudaError_t scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_na_ptr[dev] = p;
-    }
-    *out = g_na_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 

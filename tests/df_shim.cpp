@@ -1,5 +1,6 @@
-// Host build of the library's double-float arithmetic (cn_arith.cuh) for the
-// CPU checks in test_df_arith.py.  Compiled with -ffp-contract=off.
+// Host build of the library's arithmetic (cn_arith.cuh) for the CPU checks in
+// test_df_arith.py (double-float) and test_f64_rcp.py (the binary64
+// reciprocal).  Compiled with -ffp-contract=off.
 #include "../paper_2205_00856_b300/csrc/cn_arith.cuh"
 using namespace cnb;
 
@@ -59,6 +60,17 @@ void shim_cop(int op, const float* a, const float* b, const float* c, float* out
         cx<df> r = op == 0 ? cmul(A, B) : (op == 1 ? cfma(Cc, A, B) : crcp(A, k));
         out[4 * i] = r.re.hi; out[4 * i + 1] = r.re.lo; out[4 * i + 2] = r.im.hi; out[4 * i + 3] = r.im.lo;
         ok[i] = k;
+    }
+}
+// binary64 reciprocal d_rcp and complex reciprocal crcp<double>
+void shim_d_rcp(const double* q, double* y, int* ok, long n) {
+    for (long i = 0; i < n; ++i) { bool k = true; y[i] = d_rcp(q[i], k); ok[i] = k; }
+}
+void shim_crcp_d(const double* z, double* w, int* ok, long n) {
+    for (long i = 0; i < n; ++i) {
+        bool k = true;
+        cx<double> r = crcp(mk(z[2 * i], z[2 * i + 1]), k);
+        w[2 * i] = r.re; w[2 * i + 1] = r.im; ok[i] = k;
     }
 }
 }

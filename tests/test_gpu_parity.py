@@ -308,21 +308,71 @@ def test_full_size_soft_coulomb_2pow24(arith, blocks, flags):
     assert abs(np.sum(np.abs(out) ** 2) / np.sum(np.abs(psi0) ** 2) - 1) <= 1e-12
 
 
-@pytest.mark.parametrize("block,level1_block,level_block", [(13, 10, 16), (13, 10, 12), (12, 10, 12), (13, 20, 12)])
-def test_full_size_soft_coulomb_2pow24_bench_configuration(block, level1_block, level_block):
-    # bench.py's launch configuration: double-float, blocks 13 / level-1 blocks 10 /
-    # level blocks 16, static diagonal part tabulated, the steps in one call (fused
-    # step loop); the previous defaults and a level-1 block of 20
+def _bench_configs():
+    """bench.py's launch configuration per arithmetic (LARGE_GRID_BLOCKS, table on,
+    the steps in one call), then the previous double-float defaults and a level-1
+    block of 20."""
+    out = [(a,) + cnb.LARGE_GRID_BLOCKS[a] for a in (cnb.ARITH_F64, cnb.ARITH_DF64)]
+    out += [(cnb.ARITH_DF64, 13, 10, 12), (cnb.ARITH_DF64, 12, 10, 12), (cnb.ARITH_DF64, 13, 20, 12)]
+    return out
+
+
+@pytest.mark.parametrize("arith,block,level1_block,level_block", _bench_configs())
+def test_full_size_soft_coulomb_2pow24_bench_configuration(arith, block, level1_block, level_block):
     f = _full_size_reference()
     cfg, nsteps, psi0, E, ref = f["cfg"], f["nsteps"], f["psi0"], f["E"], f["ref"]
     plan = cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0,
-                    arith=cnb.ARITH_DF64, block=block, level_block=level_block, level1_block=level1_block,
+                    arith=arith, block=block, level_block=level_block, level1_block=level1_block,
                     flags=cnb.FLAG_COEFF_TABLE)
     assert plan.info()["level_block"][:3] == [block, level1_block, level_block]
     out = plan.step(to_dev(psi0), nsteps, E_mid=to_dev(E)).cpu().numpy()
     plan.check()
     plan.close()
     assert rel(out, ref) <= 1e-12
+    assert abs(np.sum(np.abs(out) ** 2) / np.sum(np.abs(psi0) ** 2) - 1) <= 1e-12
+
+
+_FULL_SUPPORT = {}
+
+
+def _full_support_reference():
+    """Oracle run of the benchmarked grid (N = 2^24, soft-Coulomb atom in the field,
+    3 steps) from a state with amplitude on every grid point, computed once: every
+    level-0 block, joint-row exchange and kept entry, and the coefficients out to
+    |x| = 8.4e5 where the field term x E dominates the diagonal, carry data."""
+    if not _FULL_SUPPORT:
+        cfg = W.soft_coulomb_config()
+        nsteps = 3
+        psi0 = W.full_support_state(cfg["n"], cfg["dx"], cfg["x_min"])
+        E = W.field_midpoints(nsteps, cfg["dt"], t0=200.0)
+        assert np.min(np.abs(E)) > 1e-3  # the field term is on
+        _FULL_SUPPORT.update(cfg=cfg, nsteps=nsteps, psi0=psi0, E=E,
+                             ref=oracle.cn_run(oracle_problem(cfg), psi0, nsteps, E_mid=E))
+    return _FULL_SUPPORT
+
+
+@pytest.mark.parametrize("flags", [cnb.FLAG_COEFF_TABLE, 0])
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_full_size_full_support_bench_configuration(arith, flags):
+    """The bench's launch configuration (and the regenerated-coefficient variant) on
+    the full-support state, element by element: rel L2 <= 1e-12 and every point
+    within 1e-12 max|ref|."""
+    f = _full_support_reference()
+    cfg, nsteps, psi0, E, ref = f["cfg"], f["nsteps"], f["psi0"], f["E"], f["ref"]
+    m0, m1, ml = cnb.LARGE_GRID_BLOCKS[arith]
+    plan = cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0,
+                    arith=arith, block=m0, level1_block=m1, level_block=ml, flags=flags)
+    out = plan.step(to_dev(psi0), nsteps, E_mid=to_dev(E)).cpu().numpy()
+    one = to_dev(psi0)
+    for k in range(nsteps):  # one call per step: the unfused path of the same plan
+        plan.step(one, 1, E_mid=to_dev(E[k:k + 1]), psi_out=one)
+    one = one.cpu().numpy()
+    plan.check()
+    plan.close()
+    scale = float(np.max(np.abs(ref)))
+    for got in (out, one):
+        assert rel(got, ref) <= 1e-12
+        assert float(np.max(np.abs(got - ref))) <= 1e-12 * scale
     assert abs(np.sum(np.abs(out) ** 2) / np.sum(np.abs(psi0) ** 2) - 1) <= 1e-12
 
 

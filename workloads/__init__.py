@@ -71,6 +71,19 @@ def initial_state(cfg: dict) -> np.ndarray:
     return gaussian(cfg["n"], cfg["dx"], cfg["x_min"], cfg["x0"], cfg["sigma"], cfg["k0"])
 
 
+def full_support_state(n: int, dx: float, x_min: float, seed: int = SEED) -> np.ndarray:
+    """A state with amplitude of order one on every grid point: seeded complex
+    normal noise plus a wave packet of width n dx / 20 and momentum 0.7 centred
+    in the box, normalised so dx sum |psi|^2 = 1.  Parity checks on it exercise
+    every block, joint row and coefficient of the grid, where a localised packet
+    leaves most of them at 0 -> 0."""
+    rng = np.random.default_rng(seed)
+    psi = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    psi += 3.0 * gaussian(n, dx, x_min, x_min + 0.5 * n * dx, max(1.0, 0.05 * n * dx), 0.7) * math.sqrt(n * dx)
+    nrm = math.sqrt(dx * float(np.sum(np.abs(psi) ** 2)))
+    return (psi / nrm).astype(np.complex128)
+
+
 def pulse(t) -> np.ndarray:
     """E(t) = E0 sin^2(pi t/Tp) cos(omega t) for 0 <= t <= Tp, else 0."""
     t = np.asarray(t, dtype=np.float64)
