@@ -44,17 +44,31 @@ UNIT = "unknown-steps/s"
 WORKLOAD_STEPS = 1000  # length of the benchmarked propagation (field samples)
 PG_TIMEOUT_S = 900     # process-group timeout: longer than any phase between two collectives
 
-# Work per grid row of the two level-0 kernels (soft-Coulomb potential, store
-# mode), m = rows per level-0 block.  The static diagonal part 2 + 2 dx^2 V(x) is
-# either regenerated every step (x^2 + s, a reciprocal square root, a scale) or
-# read from a table built once (table=True).
+# Work per grid row of the level-0 kernels (soft-Coulomb potential, store mode),
+# m = rows per level-0 block.  The static diagonal part 2 + 2 dx^2 V(x) is either
+# regenerated every step (x^2 + s, a reciprocal square root, a scale) or read
+# from a table built once (table=True; binary64: the pair {bt0, x}).
 #
-# Flops (FMA = 2, reciprocal / rsqrt = 1), flops_per_row:
-#   FP64:          reduce 59 - 30/m (table: 54 - 30/m), substitute 16 - 14/m
-#   double-float:  reduce 548 - 261/m (table: 477 - 261/m), substitute 150 - 128/m  (binary32 flops)
-# binary32 operations of the double-float kernels (add, multiply and FMA count one
-# each: what the FP32 pipe retires per lane and clock), ops_per_row:
-#   reduce 465 - 212/m (table: 402 - 212/m), substitute 126 - 126/m
+# Binary64 (FP64 pipe operations: DFMA, DADD and DMUL count one each, as the pipe
+# issues them; flops count an FMA as 2).  Reduction loop row: coefficient 1 (FMA
+# with the tabulated x), explicit row 6 (2 DADD, 4 DFMA), RD: d 4, pivot 2 +
+# complex reciprocal 7 (|z|^2 2, the division-free real reciprocal 3, 2 DMUL), RU:
+# Q 4, S 4, d 4  ->  32 operations (23 DFMA, 4 DADD, 5 DMUL: 55 flops).  Per block
+# rows 0 and 1, JD/JU and the joint-row exchange add 48 operations (80 flops) and
+# spare the two loop rows they replace: 32 - 16/m per grid row (55 - 30/m flops).
+# Regenerating V(x) adds the coordinate (DADD, DFMA), x^2 + s, the binary64
+# reciprocal square root and a scale: about 10 operations per row.  Substitution
+# (kept values): a forward step (2 DADD, 2 DMUL, 2 DFMA) and a back step (4 DFMA)
+# per interior row: 10 - 10/m (flops 16 - 16/m).
+# Double-float: binary32 operations of the FP32 pipe, see ops_per_row.
+def f64_ops_per_row(kernel: str, m: int, table: bool = True) -> float:
+    if kernel == "fused_level0":
+        return f64_ops_per_row("substitute_level0", m, table) + f64_ops_per_row("reduce_level0", m, table)
+    if kernel == "reduce_level0":
+        return (32.0 if table else 42.0) - 16.0 / m
+    return 10.0 - 10.0 / m
+
+
 def flops_per_row(kernel: str, arith: str, m: int, table: bool = False) -> float:
     """Flops per grid row of the level-0 kernels (FMA = 2; binary32 flops of the
     double-float formulation, binary64 flops of the FP64 one).  A block of m rows
@@ -64,7 +78,7 @@ def flops_per_row(kernel: str, arith: str, m: int, table: bool = False) -> float
     if kernel == "fused_level0":  # SS of one step + the level-0 reduction of the next
         return flops_per_row("substitute_level0", arith, m, table) + flops_per_row("reduce_level0", arith, m, table)
     if arith == "f64":
-        return (54.0 if table else 59.0) - 30.0 / m if kernel == "reduce_level0" else 16.0 - 14.0 / m
+        return (55.0 if table else 72.0) - 30.0 / m if kernel == "reduce_level0" else 16.0 - 16.0 / m
     if kernel == "reduce_level0":
         return (477.0 if table else 548.0) - 261.0 / m
     return 150.0 - 128.0 / m
@@ -85,13 +99,18 @@ def ops_per_row(kernel: str, m: int, table: bool = False) -> float:
 
 
 STEP_BYTES_PER_ROW = 32.0   # read psi_n, write psi_n+1
-TABLE_BYTES_PER_ROW = 8.0   # read the tabulated static diagonal part (double-float)
-# Recipe nominal FP64 rate of a B300 (MEASURED_PEAKS.json carries no FP64 figure).
-FP64_NOMINAL_TFLOPS = 1.25
-# FP32 pipe peak: 148 SMs x 128 lanes x 2.032 GHz binary32 operations per second
-# (x 2 flops when every operation is an FMA).
-FP32_PEAK_TOPS = 148 * 128 * 2.032e9 / 1e12
-FP32_PEAK_TFLOPS = 2 * FP32_PEAK_TOPS
+TABLE_BYTES_PER_ROW = {"f64": 16.0, "df64": 8.0}  # the tabulated coefficients read per row
+# FP64 pipe throughput of this machine's B300, measured by a probe of independent
+# DFMA / DADD / DMUL chains (all SMs, CUDA events, best of 5; profiles/fp64_pipe_b300.md):
+# operations per second of the whole GPU.
+FP64_MEASURED_OPS = None
+FP64_PEAK_SOURCE = "not measured"
+
+
+def fp32_peak_tops(sms: int, mhz: float) -> float:
+    """FP32 pipe peak: SMs x 128 lanes x SM clock, binary32 operations per second (x 2
+    flops when every operation is an FMA), in units of 10^12."""
+    return sms * 128 * mhz * 1e6 / 1e12
 
 
 def max_over_ranks(dist, value: float, device) -> float:
@@ -160,58 +179,78 @@ def ncu_traffic(kernel_class: str, arith: str, n: int, m: int, table: bool = Fal
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """SM clock, its maximum and the active clock-event (throttle) reasons, sampled
+    every 50 ms in a background thread during the timed region: through NVML
+    (what nvidia-smi reads), else by one-shot nvidia-smi queries (a long-running
+    `nvidia-smi -lms` writes through a block buffer into a pipe and loses its
+    last samples when stopped).  Reading only: no setting is changed."""
 
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, gpu_id: str):
-        self.gpu_id = gpu_id
-        self.proc = None
-        self.lines = []
+    def __init__(self, uuid: str):
+        self.uuid = uuid
+        self.rows = []  # (sm_mhz, max_mhz, {reasons})
+        self.stop = threading.Event()
         self.t = None
+        self.source = None
+
+    def _nvml_reader(self):
+        import pynvml as N
+        N.nvmlInit()
+        h = N.nvmlDeviceGetHandleByUUID(self.uuid)
+        bits = (N.nvmlClocksEventReasonHwSlowdown, N.nvmlClocksEventReasonHwThermalSlowdown,
+                N.nvmlClocksEventReasonSwThermalSlowdown, N.nvmlClocksEventReasonSwPowerCap)
+        mx = float(N.nvmlDeviceGetMaxClockInfo(h, N.NVML_CLOCK_SM))
+
+        def read():
+            r = N.nvmlDeviceGetCurrentClocksEventReasons(h)
+            return (float(N.nvmlDeviceGetClockInfo(h, N.NVML_CLOCK_SM)), mx,
+                    {nm for nm, b in zip(self.NAMES, bits) if r & b})
+        return read
+
+    def _smi_reader(self):
+        def read():
+            out = subprocess.run(["nvidia-smi", "-i", self.uuid, f"--query-gpu={self.Q}",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10).stdout
+            p = [x.strip() for x in out.strip().split(",")]
+            return (float(p[0]), float(p[1]), {nm for nm, v in zip(self.NAMES, p[3:7]) if v.lower() == "active"})
+        return read
 
     def __enter__(self):
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
+        read = None
+        for src, mk in (("nvml", self._nvml_reader), ("nvidia-smi", self._smi_reader)):
+            try:
+                read = mk()
+                self.rows.append(read())
+                self.source = src
+                break
+            except Exception:
+                read = None
+        if read is not None:
+            def loop():
+                while not self.stop.wait(0.05):
+                    try:
+                        self.rows.append(read())
+                    except Exception:
+                        pass
+            self.t = threading.Thread(target=loop, daemon=True)
             self.t.start()
-        except OSError:
-            self.proc = None
         return self
 
-    def _read(self):
-        for ln in self.proc.stdout:
-            self.lines.append(ln.strip())
-
     def __exit__(self, *a):
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-            self.t.join(timeout=2)
+        self.stop.set()
+        if self.t is not None:
+            self.t.join(timeout=15)
 
     def summary(self):
-        rows = []
-        for ln in self.lines:
-            p = [x.strip() for x in ln.split(",")]
-            if len(p) < 8:
-                continue
-            try:
-                rows.append((float(p[0]), float(p[1]), p[4:8]))
-            except ValueError:
-                continue
-        if not rows:
+        if not self.rows:
             return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        reasons = sorted(set().union(*(r[2] for r in self.rows)))
+        return {"sm_mhz": statistics.median(r[0] for r in self.rows), "sm_max_mhz": max(r[1] for r in self.rows),
+                "reasons": reasons, "samples": len(self.rows), "source": self.source}
 
 
 def cpu_baseline_oracle(budget_s: float = 10.0):
@@ -319,33 +358,50 @@ def run_reference(args):
     value = n * args.steps / el
     sample = (f"each step: one CN step of the serial FP64 oracle on a 2^{n.bit_length() - 1}-point window of the "
               f"N=2^24 soft-Coulomb grid")
+    # the CUDA arm's config (its launch parameters are constants of the package;
+    # nothing of the package runs here and its library is not loaded)
+    import paper_2205_00856_b300 as cnb
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args),
+            "data": "synthetic", "config": workload_config(args, make_leg(cnb, args, args.arith, True)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def workload_config(args):
+def workload_config(args, leg):
     return {"workload": "soft_coulomb_laser_1d_cn", "n": getattr(args, "n", 1 << 24), "dx": 0.1, "dt": 0.02,
             "potential": "-1/sqrt(x^2+2) + x E(t)", "field": "0.05 sin^2(pi t/T) cos(0.057 t), T = 4*2pi/0.057",
             "steps_per_bench_step": 1, "steps_per_call": getattr(args, "steps_per_call", 1),
-            "workload_steps": WORKLOAD_STEPS, "block": args.block,
-            "level_block": getattr(args, "level_block", 8), "level1_block": getattr(args, "level1_block", 0),
-            "coefficients": "static part tabulated once" if getattr(args, "coeff_table", False)
+            "workload_steps": WORKLOAD_STEPS, "block": leg["block"], "level1_block": leg["level1_block"],
+            "level_block": leg["level_block"],
+            "coefficients": "static part tabulated once" if leg["table"]
             else "regenerated from V(x) and E(t) every step",
-            "arith": args.arith, "l2": "inputs larger than L2 (2 x 256 MiB states vs 126 MB L2), no flush",
-            "parallelism": f"replicas x{args.gpus}"}
+            "arith": leg["arith"], "l2": "inputs larger than L2 (2 x 256 MiB states vs 126 MB L2), no flush",
+            "parallelism": f"replicas x{getattr(args, 'gpus', 1)}"}
 
 
-def make_plan(cnb, cfg, args, arith):
+def make_leg(cnb, args, arith: str, from_args: bool) -> dict:
+    """Launch configuration of one arithmetic: the command line's blocks for the
+    headline arithmetic (None: the library's large-grid defaults), the library's
+    defaults for the other."""
+    code = cnb.ARITH_DF64 if arith == "df64" else cnb.ARITH_F64
+    m0, m1, ml = cnb.LARGE_GRID_BLOCKS[code]
+    if from_args:
+        pick = lambda v, d: d if v is None else v  # noqa: E731
+        m0 = pick(getattr(args, "block", None), m0)
+        m1 = pick(getattr(args, "level1_block", None), m1)
+        ml = pick(getattr(args, "level_block", None), ml)
+    return {"arith": arith, "code": code, "block": m0, "level1_block": m1, "level_block": ml,
+            "table": bool(getattr(args, "coeff_table", True))}
+
+
+def make_plan(cnb, cfg, leg):
     return cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0,
-                    block=args.block, arith=arith, level_block=args.level_block,
-                    level1_block=getattr(args, "level1_block", 0),
-                    flags=cnb.FLAG_COEFF_TABLE if args.coeff_table else 0)
+                    block=leg["block"], arith=leg["code"], level_block=leg["level_block"],
+                    level1_block=leg["level1_block"], flags=cnb.FLAG_COEFF_TABLE if leg["table"] else 0)
 
 
 def time_steps(torch, plan, psi0, E, steps, warmup, dist, dev, sample_clocks, per_call=1):
@@ -398,37 +454,60 @@ def time_steps(torch, plan, psi0, E, steps, warmup, dist, dev, sample_clocks, pe
     return ms, prof, (clk.summary() if clk else None)
 
 
-def roofline(prof, n, arith, peaks, m, table=False):
+def roofline(prof, n, arith, peaks, m, table, sms):
+    """The dominant level-0 kernel against the pipe that bounds it: achieved
+    operations per second (this implementation's count per grid row x rows /
+    the kernel class's average CUDA-event launch time) over the pipe's peak."""
     dom = max(("reduce_level0", "substitute_level0", "fused_level0"), key=lambda c: prof.get(c, (0.0, 0))[0])
     dom_ms, dom_launches = prof[dom]
     avg_s = dom_ms * 1e-3 / max(dom_launches, 1)
     fl = flops_per_row(dom, arith, m, table)
     if arith == "f64":
-        achieved = fl * n / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_NOMINAL_TFLOPS,
-                "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table; no FP64 figure in MEASURED_PEAKS.json)",
-                "basis": "algorithmic FP64 flops per grid row (FMA = 2)"}
+        ops = f64_ops_per_row(dom, m, table)
+        achieved = ops * n / avg_s / 1e12
+        peak = FP64_MEASURED_OPS / 1e12 if FP64_MEASURED_OPS else None
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
+                "frac": achieved / peak if peak else None, "peak_source": FP64_PEAK_SOURCE,
+                "basis": "binary64 operations of the FP64 pipe (DFMA, DADD, DMUL: one each) per grid row, "
+                         "this implementation's count",
+                "ops_per_row": ops,
+                "flops": {"achieved": fl * n / avg_s / 1e12, "unit": "TFLOP/s", "basis": "binary64 flops, FMA = 2",
+                          "peak": 2 * peak if peak else None,
+                          "frac": (fl * n / avg_s / 1e12) / (2 * peak) if peak else None}}
     else:
         # The double-float kernels are bound by the FP32 pipe's operation rate:
         # mostly additions (the error-free transformations), so the flop rate with
         # FMA = 2 understates how busy the pipe is; both are given.
+        mhz = float(peaks.get("sm_max_mhz", 2032.0))
+        pk = fp32_peak_tops(sms, mhz)
         ops = ops_per_row(dom, m, table)
         achieved = ops * n / avg_s / 1e12
         tflops = fl * n / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TOPS, "unit": "Top/s",
-                "frac": achieved / FP32_PEAK_TOPS,
-                "peak_source": "FP32 pipe peak 148 SM x 128 lanes x 2.032 GHz (recipe unit counts and clock)",
+        roof = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "Top/s", "frac": achieved / pk,
+                "peak_source": f"FP32 pipe peak {sms} SM x 128 lanes x {mhz:.0f} MHz (device SM count, "
+                               "maximum SM clock; recipe unit counts)",
                 "basis": "binary32 operations (add, mul, FMA: one each) of the double-float formulation per grid row",
                 "ops_per_row": ops,
-                "flops": {"achieved": tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                          "frac": tflops / FP32_PEAK_TFLOPS, "basis": "binary32 flops, FMA = 2"}}
+                "flops": {"achieved": tflops, "peak": 2 * pk, "unit": "TFLOP/s",
+                          "frac": tflops / (2 * pk), "basis": "binary32 flops, FMA = 2"}}
     roof.update({"kernel": dom, "avg_launch_ms": avg_s * 1e3, "flops_per_row": fl,
                  "traffic": ncu_traffic(dom, arith, n, m, table)})
     return roof
 
 
-def adjoint_ratio(torch, cnb, args, dev):
+def hbm_roofline(value, arith, table, peaks):
+    """The metric's fraction of the measured HBM copy rate at the step's algorithmic
+    bytes (read psi and, with a table, the tabulated coefficients; write psi')."""
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    step_bytes = STEP_BYTES_PER_ROW + (TABLE_BYTES_PER_ROW[arith] if table else 0.0)
+    achieved = step_bytes * value / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "basis": f"{step_bytes:.0f} B per unknown-step (read psi" + (" and the tabulated coefficients" if table else "")
+                     + ", write psi')",
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback 6400"}
+
+
+def adjoint_ratio(torch, cnb, args, dev, leg):
     """Gradient run: soft-Coulomb atom, N = 2^20, dt = 0.02, E(t) from 500 control
     samples (sin^2 pulse), loss = population outside |x| < 20; backward (sqrt(T)
     checkpoint recompute + adjoint steps) time over forward time, CUDA events."""
@@ -436,10 +515,9 @@ def adjoint_ratio(torch, cnb, args, dev):
     cfg = W.gradient_config()
     n, nsteps, nc = cfg["n"], args.adjoint_steps, cfg["n_controls"]
     tf = nsteps * cfg["dt"]
-    arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
-    plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith,
-                    block=args.block, level_block=args.level_block, level1_block=args.level1_block,
-                    flags=cnb.FLAG_COEFF_TABLE if args.coeff_table else 0)
+    plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=leg["code"],
+                    block=leg["block"], level_block=leg["level_block"], level1_block=leg["level1_block"],
+                    flags=cnb.FLAG_COEFF_TABLE if leg["table"] else 0)
     psi0 = torch.from_numpy(W.initial_state(cfg)).to(dev)
     u0 = torch.from_numpy(W.initial_controls(nc, tf)).to(dev)
     wt = torch.from_numpy(W.outside_mask_weights(n, cfg["dx"], cfg["loss_cut"])).to(dev)
@@ -460,7 +538,7 @@ def adjoint_ratio(torch, cnb, args, dev):
     plan.check()
     plan.close()
     return {"workload": "soft_coulomb_laser_1d_gradient", "n": n, "steps": nsteps, "controls": nc,
-            "dtype": args.arith, "coefficients": "static part tabulated once" if args.coeff_table else "regenerated",
+            "dtype": leg["arith"], "coefficients": "static part tabulated once" if leg["table"] else "regenerated",
             "forward_ms": fw[-1], "backward_ms": bw[-1], "ratio": bw[-1] / fw[-1],
             "grad_norm": float(torch.linalg.norm(u.grad).item()), "loss": float(loss.item()),
             "checkpoints": int(np.ceil(np.sqrt(nsteps)))}
@@ -481,7 +559,7 @@ def batch_gaussians(torch, sizes_t, offsets_t, dx, dev, seed):
     return psi
 
 
-def small_bench(torch, cnb, args, dev):
+def small_bench(torch, cnb, args, dev, leg, cpu: bool):
     """Free packet, N = 4096, 100 steps (latency-bound: microseconds per step, no
     roofline): one cn_step call of 100 steps, with the paper's P = 16 partition
     (one level of 256-row blocks, serial RS on 17 rows) and with the default
@@ -489,8 +567,8 @@ def small_bench(torch, cnb, args, dev):
     cfg = W.free_packet_config()
     n, nst = cfg["n"], cfg["nsteps"]
     psi0 = W.initial_state(cfg)
-    arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
-    out = {"workload": cfg["name"], "n": n, "steps": nst, "dtype": args.arith}
+    arith = leg["code"]
+    out = {"workload": cfg["name"], "n": n, "steps": nst, "dtype": leg["arith"]}
     stream = torch.cuda.current_stream()
     for key, kw in (("p16", {"levels": [256]}), ("default", {})):
         plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], arith=arith, **kw)
@@ -511,7 +589,7 @@ def small_bench(torch, cnb, args, dev):
         out[key] = {"us_per_step": 1e3 * ev0.elapsed_time(ev1) / (reps * nst), "level_rows": info["level_rows"],
                     "launches_per_step": info["launches_per_step"]}
         plan.close()
-    if not args.no_cpu_baseline:
+    if cpu:
         import oracle
         prob = oracle.Problem(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=oracle.POT_NONE)
         t0 = time.perf_counter()
@@ -524,7 +602,7 @@ def small_bench(torch, cnb, args, dev):
     return out
 
 
-def batched_bench(torch, cnb, args, dev):
+def batched_bench(torch, cnb, args, dev, leg, cpu: bool):
     """4096 independent CN systems, sizes log-uniform in [1024, 2^20], random
     8-term cosine potentials, dx = 0.1, dt = 0.01: (block, level_block) picked
     by the autotuner on every 8th system, then 200 steps of the whole batch
@@ -532,7 +610,7 @@ def batched_bench(torch, cnb, args, dev):
     (one launch sequence) per system -- eager, and captured in a graph."""
     cfg = W.batched_config(n_systems=args.batched_systems)
     sizes, cos_a, dx, dt = cfg["sizes"], cfg["cos_a"], cfg["dx"], cfg["dt"]
-    arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
+    arith = leg["code"]
     kw = dict(pot=cnb.POT_COSSERIES, arith=arith)
     m0, ml, tune = cnb.autotune_batch(sizes[::8], dx, dt, cos_a=cos_a[::8], steps=3, repeats=2, **kw)
     b = cnb.Batch(sizes, dx, dt, cos_a=cos_a, block=m0, level_block=ml, **kw)
@@ -599,7 +677,7 @@ def batched_bench(torch, cnb, args, dev):
     torch.cuda.empty_cache()
     ms = g_ms / nst
     return {"workload": cfg["name"], "systems": int(len(sizes)), "total_rows": int(total),
-            "size_min": int(sizes.min()), "size_max": int(sizes.max()), "steps": nst, "dtype": args.arith,
+            "size_min": int(sizes.min()), "size_max": int(sizes.max()), "steps": nst, "dtype": leg["arith"],
             "block": m0, "level_block": ml, "autotune_ms_per_step": {f"{a}x{c}": t for (a, c), t in tune.items()},
             "autotune_sample": "every 8th system",
             "value": total * nst / (g_ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
@@ -607,7 +685,7 @@ def batched_bench(torch, cnb, args, dev):
             "per_system_eager_ms_per_step": ps_ms, "per_system_graph_ms_per_step": psg_ms,
             "speedup_vs_per_system": ps_ms / ms, "speedup_vs_per_system_graph": psg_ms / ms,
             "per_system_steps_timed": reps,
-            "cpu_baseline": cpu_baseline_batched(cfg) if args.batched_cpu_baseline else None}
+            "cpu_baseline": cpu_baseline_batched(cfg) if cpu else None}
 
 
 def largest_bench(torch, cnb, args, dev):
@@ -619,6 +697,7 @@ def largest_bench(torch, cnb, args, dev):
     cfg = W.largest_config()
     n, dx, dt, nst = cfg["n"], cfg["dx"], cfg["dt"], cfg["nsteps"]
     arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     kw = dict(pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith)
     m0, ml, tt = cnb.autotune_plan(n, dx, dt, cfg["x_min"], candidates=[(8, 8), (12, 12), (13, 12), (16, 12)], steps=4,
                                    repeats=1, **kw)
@@ -660,7 +739,7 @@ def largest_bench(torch, cnb, args, dev):
                        "coefficients": "regenerated from V(x) and E(t) every step",
                        "state": "64 GiB complex128, in place (store mode)"},
             "levels": info["level_rows"], "workspace_bytes": info["workspace_bytes"],
-            "roofline": roofline(prof, n, args.arith, peaks, m0, False),
+            "roofline": roofline(prof, n, args.arith, peaks, m0, False, sms),
             "roofline_hbm": {"bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
                              "frac": hbm / hbm_peak, "basis": "32 B per unknown-step (read psi, write psi')"},
             "steps_per_call": nst,
@@ -673,24 +752,22 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
-    ap.add_argument("--arith", choices=["f64", "df64"], default="df64")
-    ap.add_argument("--f64-steps", type=int, default=100,
-                    help="also time the native-FP64 path for this many steps (0: skip)")
-    # 13 / level 1: 10 / 16, from sweeps on B300 of the fused step loop (level-0 blocks
-    # 10..16: 13 best, 0.482 vs 0.485 ms at 12; the top candidates are within 1 % of
-    # each other, so a run-time pick would wander between them and away from the
-    # block size the committed ncu captures were taken at; level blocks 12..16 with
-    # the two-group kernels on levels 2 and 3: 16 best, 0.4531 vs 0.4544 ms at 12)
-    ap.add_argument("--block", type=int, default=13, help="level-0 block rows (0: autotune with --level-block)")
-    ap.add_argument("--level-block", type=int, default=16, help="rows per block on levels >= 1 (0: autotune)")
-    # level 1 in blocks of 10: 0.502 vs 0.506 ms per step at 12 (swept 10..24 with level blocks 8 and 12)
-    ap.add_argument("--level1-block", type=int, default=10, help="rows per block on level 1 alone (0: --level-block)")
+    ap.add_argument("--arith", choices=["f64", "df64"], default="f64",
+                    help="arithmetic of the headline (f64: native binary64, the complex128 metric's own)")
+    ap.add_argument("--df64-steps", type=int, default=2000,
+                    help="also time the other arithmetic (double-float when the headline is f64) for this many "
+                         "steps as an extra (0: skip)")
+    # None: the library's large-grid defaults for the arithmetic (LARGE_GRID_BLOCKS, from
+    # block-size sweeps on B300)
+    ap.add_argument("--block", type=int, default=None, help="level-0 block rows (0: autotune with --level-block)")
+    ap.add_argument("--level-block", type=int, default=None, help="rows per block on levels >= 2 (0: autotune)")
+    ap.add_argument("--level1-block", type=int, default=None, help="rows per block on level 1 (0: --level-block)")
     ap.add_argument("--coeff-table", dest="coeff_table", action="store_true", default=True,
                     help="tabulate the static diagonal part 2 + 2 dx^2 V(x) once (default)")
     ap.add_argument("--no-coeff-table", dest="coeff_table", action="store_false",
                     help="regenerate V(x) every step instead")
     ap.add_argument("--n", type=int, default=1 << 24, help="grid points (profiling runs use smaller grids)")
-    # 1000 (the propagation's length): 0.4494 vs 0.4544 ms per step in calls of 50
+    # 1000 (the propagation's length): one call for the whole run
     ap.add_argument("--steps-per-call", type=int, default=1000,
                     help="CN steps per cn_step call in the timed region (1: one call per step)")
     ap.add_argument("--e2e-calls", type=int, default=3)
@@ -720,6 +797,7 @@ def main():
     rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     dist = None
     if world > 1:
         import datetime
@@ -741,22 +819,25 @@ def main():
     psi0 = W.initial_state(cfg)
     E_host = W.field_midpoints(WORKLOAD_STEPS, cfg["dt"])
     E = torch.from_numpy(E_host).to(dev)
-    arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
+    leg = make_leg(cnb, args, args.arith, True)
+    other = make_leg(cnb, args, "df64" if args.arith == "f64" else "f64", False)
     tune = None
-    if args.block == 0 or args.level_block == 0:
+    if leg["block"] == 0 or leg["level_block"] == 0:
         b0, l0, tt = cnb.autotune_plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0,
-                                       arith=arith, flags=cnb.FLAG_COEFF_TABLE if args.coeff_table else 0)
-        args.block = args.block or b0
-        args.level_block = args.level_block or l0
+                                       arith=leg["code"], flags=cnb.FLAG_COEFF_TABLE if leg["table"] else 0)
+        leg["block"] = leg["block"] or b0
+        leg["level_block"] = leg["level_block"] or l0
+        leg["level1_block"] = 0
         tune = {f"{a}x{c}": t for (a, c), t in tt.items()}
-    plan = make_plan(cnb, cfg, args, arith)
+    plan = make_plan(cnb, cfg, leg)
     info = plan.info()
     ms, prof, clocks = time_steps(torch, plan, psi0, E, args.steps, args.warmup, dist, dev, rank == 0,
                                   args.steps_per_call)
     value = job_rate(n * args.steps, world, ms)
 
-    # end to end through the C ABI with host buffers: H2D of psi and E, inner
-    # CN steps, D2H of psi, every call
+    # end to end through the C ABI with host buffers: every call copies psi and the
+    # call's field samples from pinned host memory, runs e2e_inner CN steps and
+    # copies psi back; the bytes are reported per CN step (per call / e2e_inner)
     psi_h = torch.from_numpy(psi0).pin_memory()
     out_h = torch.empty_like(psi_h).pin_memory()
     E_h = torch.from_numpy(np.ascontiguousarray(E_host[:args.e2e_inner])).pin_memory()
@@ -771,62 +852,69 @@ def main():
     e2e_val = job_rate(n * args.e2e_inner * args.e2e_calls, world, e2e_s * 1e3)
     plan.close()
 
-    alt = None
-    if args.f64_steps > 0 and args.arith != "f64":
-        plan64 = make_plan(cnb, cfg, args, cnb.ARITH_F64)
-        ms64, prof64, _ = time_steps(torch, plan64, psi0, E, args.f64_steps, args.warmup, dist, dev, False,
-                                     args.steps_per_call)
-        plan64.close()
-        alt = {"dtype": "f64", "value": n * args.f64_steps * world / (ms64 * 1e-3), "unit": UNIT,
-               "steps": args.f64_steps, "ms_per_step": ms64 / args.f64_steps,
-               "roofline": roofline(prof64, n, "f64", measured_peaks(), args.block, args.coeff_table)
-               if rank == 0 else None}
+    peaks = measured_peaks()
+    extra = None
+    if args.df64_steps > 0:
+        plan2 = make_plan(cnb, cfg, other)
+        steps2 = args.df64_steps
+        ms2, prof2, clocks2 = time_steps(torch, plan2, psi0, E, steps2, args.warmup, dist, dev, rank == 0,
+                                         args.steps_per_call)
+        plan2.close()
+        v2 = job_rate(n * steps2, world, ms2)
+        extra = {"dtype": other["arith"], "value": v2, "unit": UNIT, "steps": steps2, "ms_per_step": ms2 / steps2,
+                 "config": workload_config(args, other), "clocks": clocks2,
+                 "kernel_ms": {k: v[0] for k, v in prof2.items()},
+                 "roofline": roofline(prof2, n, other["arith"], peaks, other["block"], other["table"], sms)
+                 if rank == 0 else None,
+                 "roofline_hbm": hbm_roofline(v2, other["arith"], other["table"], peaks)}
 
-    adj = adjoint_ratio(torch, cnb, args, dev) if (args.adjoint_steps > 0 and rank == 0) else None
-    bat = batched_bench(torch, cnb, args, dev) if (args.batched_systems > 0 and rank == 0) else None
-    small = small_bench(torch, cnb, args, dev) if (args.small and rank == 0) else None
+    adj = adj2 = bat = bat2 = small = small2 = None
+    if rank == 0:
+        if args.adjoint_steps > 0:
+            adj = adjoint_ratio(torch, cnb, args, dev, leg)
+            adj2 = adjoint_ratio(torch, cnb, args, dev, other)
+        if args.batched_systems > 0:
+            bat = batched_bench(torch, cnb, args, dev, leg, args.batched_cpu_baseline)
+            bat2 = batched_bench(torch, cnb, args, dev, other, False)
+        if args.small:
+            small = small_bench(torch, cnb, args, dev, leg, not args.no_cpu_baseline)
+            small2 = small_bench(torch, cnb, args, dev, other, False)
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
 
-    peaks = measured_peaks()
-    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
-    roof = roofline(prof, n, args.arith, peaks, args.block, args.coeff_table)
-    step_s = ms * 1e-3 / args.steps
-    step_bytes = STEP_BYTES_PER_ROW + (TABLE_BYTES_PER_ROW if args.coeff_table else 0.0)
-    hbm_achieved = step_bytes * n / step_s / 1e9
-    roof_hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": hbm_achieved / hbm_peak,
-                "basis": ("40 B per unknown-step (read psi and the tabulated diagonal part, write psi')"
-                          if args.coeff_table else "32 B per unknown-step (read psi, write psi')"),
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback 6400"}
-
+    roof = roofline(prof, n, leg["arith"], peaks, leg["block"], leg["table"], sms)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": args.arith, "data": "synthetic", "config": workload_config(args),
-            "roofline": roof, "roofline_hbm": roof_hbm,
+            "vs_baseline": None, "dtype": leg["arith"], "data": "synthetic", "config": workload_config(args, leg),
+            "roofline": roof, "roofline_hbm": hbm_roofline(value, leg["arith"], leg["table"], peaks),
             "kernel_ms": {k: v[0] for k, v in prof.items()}, "kernel_launches": {k: v[1] for k, v in prof.items()},
             "kernel_timing": "per-kernel-class CUDA events on the launching stream, over a second pass of the same "
                              "steps right after the timed region (events between kernels would add gaps to it)",
             # the profiled pass repeats the timed region's call pattern launch for launch
             "gpu_launches": sum(v[1] for v in prof.values()),
             "levels": info["level_rows"],
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * n + 8 * args.e2e_inner,
-                    "d2h_bytes_per_step": 16 * n, "cn_steps_per_call": args.e2e_inner,
-                    "calls": args.e2e_calls},
+            "e2e": {"value": e2e_val, "unit": UNIT,
+                    "h2d_bytes_per_step": (16 * n + 8 * args.e2e_inner) / max(args.e2e_inner, 1),
+                    "d2h_bytes_per_step": 16 * n / max(args.e2e_inner, 1), "cn_steps_per_call": args.e2e_inner,
+                    "bytes_per_call": {"h2d": 16 * n + 8 * args.e2e_inner, "d2h": 16 * n},
+                    "calls": args.e2e_calls, "api": "cn_step_host (pinned host psi and field in, psi out)"},
             "clocks": clocks}
     if tune:
         line["config"]["autotune_ms_per_step"] = tune
-    if alt:
-        line["f64_path"] = alt
+    if extra:
+        line[f"{other['arith']}_path"] = extra
     if adj:
         line["adjoint"] = adj
+        line[f"adjoint_{other['arith']}"] = adj2
     if bat:
         line["batched"] = bat
+        line[f"batched_{other['arith']}"] = bat2
     if small:
         line["small"] = small
+        line[f"small_{other['arith']}"] = small2
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle()
     print(json.dumps(line), flush=True)

@@ -268,9 +268,72 @@ cn_status cn_plan_profile_read(cn_plan plan, double* ms, int64_t* launches, int3
 cn_status cn_solve_tridiag_noalloc(const void* b, const void* a, const void* c, const void* d, void* x,
                                    int64_t n, int32_t arith, void* stream);
 
+/* ---- Slabs of a sharded grid (Sec. 6.2, MPI implementation; Sec. 4.1.3, the
+ * joint-line exchange).
+ *
+ * A grid of n points is split by joint lines J_0 = 0 < J_1 < ... < J_G = n - 1
+ * into G slabs; slab r owns rows J_r .. J_{r+1} (both joint lines included)
+ * and lives in one process / on one GPU.  One CN step of the whole grid is
+ *   1. cn_slab_reduce on every slab: coefficients, explicit half-step and the
+ *      N-shaped reduction of the slab's rows (Table 1, nested by Eq. iteration)
+ *      down to its two edge rows, whose six values -- the slab's share of the
+ *      joint-line system -- go to share_out;
+ *   2. an all-gather of the G x 6 shares, in rank order (the only exchange:
+ *      6 G complex values per step, whatever n; no halo);
+ *   3. cn_slab_finish on every slab: the (G + 1)-row joint-line system solved
+ *      redundantly (one CUDA thread, Thomas: the RS stage), then the slab's
+ *      substitution (SS) at every level with its two support values.
+ * A slab plan is a cn_plan: cn_plan_destroy, cn_plan_query, cn_plan_status,
+ * cn_plan_profile and cn_plan_fill_workspace apply; cn_step, cn_step_states,
+ * cn_step_host, cn_solve_tridiag and cn_adjoint_step return CN_ERR_UNSUPPORTED.
+ * The slabs' joint values agree bitwise after every step (every rank solves the
+ * same joint system in the same order). */
+#define CN_SLAB_MAX 65536
+
+/* Create the plan of slab `rank` (0 .. nslabs-1) of the grid desc describes
+ * (desc->n: the WHOLE grid; x_min, the potential and every other field as for
+ * cn_plan_create; CN_POT_ARRAY: desc->V0 is the whole grid's array, of which
+ * the slab reads its rows).  joints: host int64[nslabs + 1], J_0 = 0 <
+ * J_1 < ... < J_G = n - 1 with gaps of at least 2, or NULL for
+ * J_r = floor(r (n - 1) / nslabs).  The slab's hierarchy is nested with
+ * desc->block / level1_block / level_block until its two edge rows remain.
+ * CN_FLAG_RECOMPUTE is not supported (CN_ERR_UNSUPPORTED at the first step).
+ * Allocates the slab's workspace on the current device, as cn_plan_create
+ * does, plus 32 (nslabs + 1) bytes for the joint-line solve. */
+cn_status cn_slab_create(const cn_desc* desc, int32_t nslabs, int32_t rank, const int64_t* joints, cn_plan* out);
+
+/* Rows of the whole grid the slab holds: *lo = J_rank, *hi = J_{rank+1};
+ * the slab's local arrays have hi - lo + 1 complex128 entries. */
+cn_status cn_slab_range(cn_plan slab, int64_t* lo, int64_t* hi);
+
+/* Step part 1: psi_local (device complex128[hi - lo + 1]: the slab's rows,
+ * both joint values included), E_mid (device pointer to E(t + dt/2); NULL:
+ * 0) -> share_out (device complex128[6]: c, a, d of row J_rank and b, a, d of
+ * row J_{rank+1}, the slab's share of the joint-line system after its
+ * interior rows are eliminated).  The slab keeps what step part 2 needs;
+ * psi_local is not written. */
+cn_status cn_slab_reduce(cn_plan slab, const void* psi_local, const double* E_mid, void* share_out, void* stream);
+
+/* Step part 2: shares (device complex128[6 nslabs], every slab's share_out in
+ * rank order) -> psi_local_out (device complex128[hi - lo + 1], the slab's
+ * rows after the step; may be the psi_local of part 1). */
+cn_status cn_slab_finish(cn_plan slab, const void* shares, void* psi_local_out, void* stream);
+
 /* Wait for the plan's stream work to finish (device synchronise) and return
  * the first device-side error recorded since the last call (then clear it). */
 cn_status cn_plan_status(cn_plan plan);
+
+/* Debugging aid (the check that stands in for a memory sanitizer): synchronise
+ * the device, then fill every scratch buffer the plan owns with the byte value
+ * `byte` (0..255; 0xFF makes every binary64 and binary32 word a NaN) -- the
+ * kept right-hand sides and pivots, the reduced systems, CTA slots and
+ * solutions of every nesting level, the long-block and serial-RS scratch, the
+ * adjoint's mu buffer and the staging buffers of cn_step_host.  Not touched:
+ * the coefficient table and the per-system tables built at creation, the
+ * status word and the adjoint's ticket counter.  Since every call writes each
+ * scratch word before it reads it, results after a fill are bitwise those
+ * without it.  CN_ERR_INVALID_ARG for byte outside 0..255.  Synchronous. */
+cn_status cn_plan_fill_workspace(cn_plan plan, int32_t byte);
 
 /* ---- Batches: many independent systems of uneven sizes in one launch per stage.
  *
@@ -314,6 +377,9 @@ cn_status cn_batch_step(cn_batch batch, const void* psi_in, void* psi_out, const
 
 /* As cn_plan_status, for a batch. */
 cn_status cn_batch_status(cn_batch batch);
+
+/* As cn_plan_fill_workspace, for a batch. */
+cn_status cn_batch_fill_workspace(cn_batch batch, int32_t byte);
 
 /* Static description of a status code. */
 const char* cn_status_string(cn_status s);

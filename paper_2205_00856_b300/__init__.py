@@ -33,7 +33,10 @@ EXPORTS = ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_s
            "cn_plan_query", "cn_plan_profile", "cn_plan_profile_read", "cn_plan_status", "cn_status_string",
            "cn_version", "cn_solve_tridiag_noalloc", "cn_adjoint_step", "cn_field_from_controls",
            "cn_field_grad_to_controls", "cn_batch_create", "cn_batch_destroy", "cn_batch_offsets",
-           "cn_batch_step", "cn_batch_status", "cn_plan_create_levels", "cn_step_states")
+           "cn_batch_step", "cn_batch_status", "cn_plan_create_levels", "cn_step_states", "cn_plan_fill_workspace",
+           "cn_batch_fill_workspace", "cn_slab_create", "cn_slab_range", "cn_slab_reduce", "cn_slab_finish")
+SLAB_MAX = 65536
+SLAB_SHARE = 6  # complex values one slab contributes to the joint-line system per step
 NOALLOC_MAX_N = 1048576
 # (level-0 block, level block) pairs autotune_plan tries by default
 PLAN_TUNE_CANDIDATES = tuple((m0, ml) for m0 in (8, 10, 12, 13, 16) for ml in (8, 12, 16, 24))
@@ -115,7 +118,15 @@ def load(build_if_missing: bool = True):
             lib.cn_batch_offsets.argtypes = [vp, vp]
             lib.cn_batch_step.argtypes = [vp, vp, vp, vp, i64, vp]
             lib.cn_batch_status.argtypes = [vp]
-            for f in ("cn_batch_create", "cn_batch_destroy", "cn_batch_offsets", "cn_batch_step", "cn_batch_status"):
+            lib.cn_plan_fill_workspace.argtypes = [vp, C.c_int32]
+            lib.cn_slab_create.argtypes = [C.POINTER(_Desc), C.c_int32, C.c_int32, vp, C.POINTER(vp)]
+            lib.cn_slab_range.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+            lib.cn_slab_reduce.argtypes = [vp, vp, vp, vp, vp]
+            lib.cn_slab_finish.argtypes = [vp, vp, vp, vp]
+            lib.cn_batch_fill_workspace.argtypes = [vp, C.c_int32]
+            for f in ("cn_batch_create", "cn_batch_destroy", "cn_batch_offsets", "cn_batch_step", "cn_batch_status",
+                      "cn_plan_fill_workspace", "cn_batch_fill_workspace", "cn_slab_create", "cn_slab_range",
+                      "cn_slab_reduce", "cn_slab_finish"):
                 getattr(lib, f).restype = C.c_int
             for f in ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_solve_tridiag",
                       "cn_plan_status", "cn_plan_query", "cn_plan_profile", "cn_plan_profile_read"):
@@ -160,23 +171,26 @@ class Plan:
     cyclic reduction.
     """
 
-    def __init__(self, n, dx, dt, x_min, pot=POT_NONE, V0=None, soft_s=2.0, cos_a=None, L=1.0,
-                 block=0, arith=ARITH_F64, flags=0, level_block=0, levels=None, level1_block=0):
+    def _desc(self, n, dx, dt, x_min, pot, V0, soft_s, cos_a, L, block, arith, flags, level_block, level1_block):
         import torch
         self._lib = load()
-        self.n = int(n)
         self.dt = float(dt)
         self.arith = int(arith)
         self._V0 = None
         v0p = None
         if pot == POT_ARRAY:
             self._V0 = V0
-            v0p = _dev_ptr(V0, torch.float64, self.n, "V0")
+            v0p = _dev_ptr(V0, torch.float64, int(n), "V0")
         self._cos = None if cos_a is None else np.ascontiguousarray(cos_a, dtype=np.float64)
-        d = _Desc(self.n, float(dx), float(dt), float(x_min), int(pot),
-                  0 if self._cos is None else len(self._cos), v0p, float(soft_s),
-                  None if self._cos is None else self._cos.ctypes.data, float(L), int(block), self.arith,
-                  int(flags), int(level_block), int(level1_block))
+        return _Desc(int(n), float(dx), float(dt), float(x_min), int(pot),
+                     0 if self._cos is None else len(self._cos), v0p, float(soft_s),
+                     None if self._cos is None else self._cos.ctypes.data, float(L), int(block), self.arith,
+                     int(flags), int(level_block), int(level1_block))
+
+    def __init__(self, n, dx, dt, x_min, pot=POT_NONE, V0=None, soft_s=2.0, cos_a=None, L=1.0,
+                 block=0, arith=ARITH_F64, flags=0, level_block=0, levels=None, level1_block=0):
+        self.n = int(n)
+        d = self._desc(n, dx, dt, x_min, pot, V0, soft_s, cos_a, L, block, arith, flags, level_block, level1_block)
         h = C.c_void_p()
         if levels is None:
             _check(self._lib.cn_plan_create(C.byref(d), C.byref(h)), "cn_plan_create")
@@ -302,8 +316,58 @@ class Plan:
         """Synchronise and return (then clear) the device-side status code."""
         return int(self._lib.cn_plan_status(self._h))
 
+    def fill_workspace(self, byte: int = 0xFF) -> None:
+        """Fill every scratch buffer of the plan with `byte` (cn_plan_fill_workspace)."""
+        _check(self._lib.cn_plan_fill_workspace(self._h, int(byte)), "cn_plan_fill_workspace")
+
     def check(self) -> None:
         _check(self.status(), "device status")
+
+
+class Slab(Plan):
+    """Slab `rank` of a grid of n points sharded over `nslabs` ranks (cn_slab_create):
+    the rows lo..hi of the grid between two joint lines (both included).  One CN
+    step of the whole grid is reduce() on every slab, an all-gather of the
+    6-value shares in rank order, and finish() on every slab (the driver is
+    paper_2205_00856_b300.sharded).  joints: nslabs + 1 joint lines (None: the
+    library's even split)."""
+
+    def __init__(self, n, dx, dt, x_min, nslabs, rank, joints=None, pot=POT_NONE, V0=None, soft_s=2.0, cos_a=None,
+                 L=1.0, block=0, arith=ARITH_F64, flags=0, level_block=0, level1_block=0):
+        d = self._desc(n, dx, dt, x_min, pot, V0, soft_s, cos_a, L, block, arith, flags, level_block, level1_block)
+        self.global_n, self.nslabs, self.rank = int(n), int(nslabs), int(rank)
+        jp = None
+        if joints is not None:
+            self._joints = np.ascontiguousarray(joints, dtype=np.int64)
+            if self._joints.size != self.nslabs + 1:
+                raise ValueError("joints needs nslabs + 1 entries")
+            jp = self._joints.ctypes.data
+        h = C.c_void_p()
+        _check(self._lib.cn_slab_create(C.byref(d), self.nslabs, self.rank, jp, C.byref(h)), "cn_slab_create")
+        self._h = h
+        lo, hi = C.c_int64(), C.c_int64()
+        _check(self._lib.cn_slab_range(self._h, C.byref(lo), C.byref(hi)), "cn_slab_range")
+        self.lo, self.hi = int(lo.value), int(hi.value)
+        self.n = self.hi - self.lo + 1  # rows of the slab's local arrays
+
+    def reduce(self, psi_local, E_mid=None, share_out=None, stream=None):
+        """Step part 1: the slab's share of the joint-line system (6 complex128 on the device)."""
+        import torch
+        pin = _dev_ptr(psi_local, torch.complex128, self.n, "psi_local")
+        if share_out is None:
+            share_out = torch.empty(SLAB_SHARE, dtype=torch.complex128, device=psi_local.device)
+        ps = _dev_ptr(share_out, torch.complex128, SLAB_SHARE, "share_out")
+        pe = None if E_mid is None else _dev_ptr(E_mid, torch.float64, E_mid.numel(), "E_mid")
+        _check(self._lib.cn_slab_reduce(self._h, pin, pe, ps, _stream_handle(stream)), "cn_slab_reduce")
+        return share_out
+
+    def finish(self, shares, psi_out, stream=None):
+        """Step part 2: every slab's share in rank order (6 nslabs complex128) -> the slab's rows."""
+        import torch
+        pa = _dev_ptr(shares, torch.complex128, SLAB_SHARE * self.nslabs, "shares")
+        po = _dev_ptr(psi_out, torch.complex128, self.n, "psi_out")
+        _check(self._lib.cn_slab_finish(self._h, pa, po, _stream_handle(stream)), "cn_slab_finish")
+        return psi_out
 
 
 class Batch:
@@ -390,6 +454,10 @@ class Batch:
 
     def status(self) -> int:
         return int(self._lib.cn_batch_status(self._h))
+
+    def fill_workspace(self, byte: int = 0xFF) -> None:
+        """Fill every scratch buffer of the batch with `byte` (cn_batch_fill_workspace)."""
+        _check(self._lib.cn_batch_fill_workspace(self._h, int(byte)), "cn_batch_fill_workspace")
 
     def check(self) -> None:
         _check(self.status(), "device status")

@@ -78,6 +78,13 @@ struct Engine {
     size_t ev_used = 0;                // events handed out since the last read
     std::vector<int> rec_class;        // class of record r (events 2r, 2r+1)
     int64_t workspace_bytes = 0;
+    // slab of a sharded grid (cn_slab_create): the hierarchy is nested down to the
+    // slab's two edge rows; rows slab_lo .. slab_hi of the global grid
+    bool slab = false;
+    bool own_last = true;           // the slab holds the global grid's last row
+    int nslabs = 1, slab_rank = 0;
+    int64_t slab_lo = 0, slab_hi = 0;
+    double2* joint_work = nullptr;  // 2 (nslabs + 1): forward-sweep scratch, then the joint values
 };
 
 struct cn_plan_s : Engine {};
@@ -141,6 +148,7 @@ void free_engine(Engine* p) {
     cudaFree(p->h_E);
     cudaFree(p->mu);
     cudaFree(p->part);
+    cudaFree(p->joint_work);
 }
 
 // --------------------------------------------------------------- kernel timing
@@ -217,8 +225,9 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
             e.n = q.P > 0 ? q.P + 1 : 0;
             e.P = 0;
             if (e.n > 0) {
-                // explicit depth: reduce exactly nlev levels; else until the CR stage can take it
-                const bool base = nlev ? (l == nlev) : (e.n <= kCrMax);
+                // explicit depth: reduce exactly nlev levels; a slab: down to its two edge
+                // rows; else until the CR stage can take it
+                const bool base = p->slab ? (e.n == 2) : nlev ? (l == nlev) : (e.n <= kCrMax);
                 if (base) p->base_level[s] = l;
                 else if (e.n < 3) return cudaErrorInvalidValue;  // too short to cut into blocks
                 else e.P = ceil_div(e.n - 1, L.m);
@@ -424,9 +433,10 @@ cudaError_t set_smem_limits(const Engine* p) {
     return set_smem_limits_map<R, OneSys, OneGrid>(m0, ml);
 }
 
-// Levels >= 1 of the nested solve: reductions down, RS, substitutions up.
+// Levels >= 1 of the nested solve: reductions down (reduce_levels), the RS
+// stage (rs_stage), substitutions up (substitute_levels).
 template <class R>
-cudaError_t solve_levels(Engine* p, cudaStream_t st) {
+cudaError_t reduce_levels(Engine* p, cudaStream_t st) {
     const size_t L = p->lv.size();
     cudaError_t e = cudaSuccess;
     for (size_t l = 1; l + 1 < L && e == cudaSuccess; ++l) {
@@ -443,24 +453,29 @@ cudaError_t solve_levels(Engine* p, cudaStream_t st) {
             }
         });
     }
-    if (e != cudaSuccess) return e;
-    {
-        ProfScope ps(p, kProfBase, st);
-        if (p->batched) {
-            e = launch(p->pdl, k_base_cr_many<R>, (unsigned)p->nsys, kCrThreads, cr_smem(), st,
-                       static_cast<const BaseSys<R>*>(p->d_base), p->status);
-        } else {
-            const LevelData& B = p->lv[(size_t)p->base_level[0]];
-            const LevelSource<R> src = level_source<R>(B).bind(B.sys[0]);
-            if (p->lvl_m.empty())
-                e = launch(p->pdl, k_base_cr<R>, 1, kCrThreads, cr_smem(), st, src, x_of<R>(B), p->status);
-            else if (p->base_cs)
-                e = launch(p->pdl, k_base_serial<R>, 1, 32, 0, st, src, x_of<R>(B),
-                           static_cast<typename Store<R>::T*>(p->base_cs), p->status);
-            else
-                e = launch(p->pdl, k_base<R>, 1, 32, 0, st, src, x_of<R>(B), p->status);
-        }
-    }
+    return e;
+}
+
+template <class R>
+cudaError_t rs_stage(Engine* p, cudaStream_t st) {
+    ProfScope ps(p, kProfBase, st);
+    if (p->batched)
+        return launch(p->pdl, k_base_cr_many<R>, (unsigned)p->nsys, kCrThreads, cr_smem(), st,
+                      static_cast<const BaseSys<R>*>(p->d_base), p->status);
+    const LevelData& B = p->lv[(size_t)p->base_level[0]];
+    const LevelSource<R> src = level_source<R>(B).bind(B.sys[0]);
+    if (p->lvl_m.empty())
+        return launch(p->pdl, k_base_cr<R>, 1, kCrThreads, cr_smem(), st, src, x_of<R>(B), p->status);
+    if (p->base_cs)
+        return launch(p->pdl, k_base_serial<R>, 1, 32, 0, st, src, x_of<R>(B),
+                      static_cast<typename Store<R>::T*>(p->base_cs), p->status);
+    return launch(p->pdl, k_base<R>, 1, 32, 0, st, src, x_of<R>(B), p->status);
+}
+
+template <class R>
+cudaError_t substitute_levels(Engine* p, cudaStream_t st) {
+    const size_t L = p->lv.size();
+    cudaError_t e = cudaSuccess;
     for (size_t l = L - 2; l >= 1 && e == cudaSuccess; --l) {
         ProfScope ps(p, kProfSubstL, st);
         with_maps(p, l, [&](auto a, auto b) {
@@ -476,6 +491,14 @@ cudaError_t solve_levels(Engine* p, cudaStream_t st) {
             }
         });
     }
+    return e;
+}
+
+template <class R>
+cudaError_t solve_levels(Engine* p, cudaStream_t st) {
+    cudaError_t e = reduce_levels<R>(p, st);
+    if (e == cudaSuccess) e = rs_stage<R>(p, st);
+    if (e == cudaSuccess) e = substitute_levels<R>(p, st);
     return e;
 }
 
@@ -615,6 +638,7 @@ cudaError_t cn_steps(Engine* p, const double2* in, double2* out, const double* E
         s.e = -1;
         s.E = E_mid ? E_mid + k : nullptr;
         s.tab = p->tab;
+        s.own_last = p->own_last ? 1 : 0;
         return s;
     };
     if (fuses_steps(p)) {
@@ -683,7 +707,7 @@ SysGrid make_grid(double x_min, double dx, int64_t n) {
 // (n_cos per system, row-major) for CN_POT_COSSERIES with period desc->L if
 // > 0, else the system's own length n_s dx.
 cn_status create_engine(Engine* p, const cn_desc* desc, const std::vector<int64_t>& sizes,
-                        const std::vector<double>& x_min, const double* cos_a) {
+                        const std::vector<double>& x_min, const double* cos_a, const SysGrid* grid0 = nullptr) {
     p->desc = *desc;
     if (p->desc.block == 0) p->desc.block = kDefaultBlock;
     if (p->desc.level_block == 0) p->desc.level_block = kDefaultLevelBlock;
@@ -721,6 +745,7 @@ cn_status create_engine(Engine* p, const cn_desc* desc, const std::vector<int64_
     }
     p->grid.resize(ns);
     for (int s = 0; s < ns; ++s) p->grid[s] = make_grid(x_min[s], desc->dx, sizes[s]);
+    if (grid0) p->grid[0] = *grid0;  // a slab: the global grid's coordinates, shifted
     if (e == cudaSuccess && p->batched) {
         p->workspace_bytes += (int64_t)(sizeof(SysGrid) * (size_t)ns);
         e = cudaMalloc(&p->d_grid, sizeof(SysGrid) * (size_t)ns);
@@ -772,6 +797,7 @@ cn_status create_engine(Engine* p, const cn_desc* desc, const std::vector<int64_
 
 cn_status run_steps(Engine* p, const void* psi_in, void* psi_out, const double* E_mid, int64_t nsteps, void* stream,
                     void* states = nullptr) {
+    if (p->slab) return CN_ERR_UNSUPPORTED;  // a slab steps through cn_slab_reduce / cn_slab_finish
     if (!psi_in || (!psi_out && !states) || nsteps < 0) return CN_ERR_INVALID_ARG;
     if (!aligned16(psi_in) || (psi_out && !aligned16(psi_out)) || (states && !aligned16(states)))
         return CN_ERR_INVALID_ARG;
@@ -787,6 +813,43 @@ cn_status run_steps(Engine* p, const void* psi_in, void* psi_out, const double* 
     double2* sts = static_cast<double2*>(states);
     cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? cn_steps<df>(p, in, out, E_mid, nsteps, st, sts)
                                                      : cn_steps<double>(p, in, out, E_mid, nsteps, st, sts);
+    return cuda_status(e);
+}
+
+// Fill every scratch buffer of the engine with `byte` (synchronously): the kept
+// right-hand sides and pivots (or the recompute-mode state buffer), the reduced
+// systems, CTA slots and solutions of every level, the long-block and serial-RS
+// scratch, the adjoint's mu buffer and the host-call staging buffers.  Not
+// touched: the coefficient table and the per-system tables (built once at
+// creation, read-only afterwards), the status word and the adjoint's ticket
+// counter (which must be zero between calls).
+cn_status fill_workspace(Engine* p, int byte) {
+    if (byte < 0 || byte > 255) return CN_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return CN_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    auto fill = [&](void* ptr, size_t bytes) {
+        if (e == cudaSuccess && ptr && bytes) e = cudaMemset(ptr, byte, bytes);
+    };
+    const int64_t rows0 = p->lv[0].rows_total;
+    if (p->keep)
+        fill(p->keep, kCplx * 2 * (size_t)p->lv[0].m * (size_t)grid_for(p->lv[0].total) * kThreads);
+    fill(p->state, kCplx * (size_t)rows0);
+    for (size_t l = 1; l < p->lv.size(); ++l) {
+        const LevelData& L = p->lv[l];
+        fill(L.rows, 4 * kCplx * (size_t)std::max<int64_t>(L.L, 1));
+        fill(L.slot, 3 * kCplx * (grid_for(p->lv[l - 1].total) + 1));
+        fill(L.x, kCplx * (size_t)L.rows_total);
+    }
+    size_t zc_entries = 0;
+    for (size_t l = 0; l + 1 < p->lv.size(); ++l)
+        if (p->lv[l].m > kSmemRowsMax) zc_entries = std::max(zc_entries, 2 * (size_t)p->lv[l].rows_total);
+    fill(p->zc, kCplx * zc_entries);
+    if (p->base_cs) fill(p->base_cs, kCplx * (size_t)p->lv[(size_t)p->base_level[0]].sys[0].n);
+    fill(p->mu, sizeof(double2) * (size_t)p->desc.n);
+    fill(p->h_in, sizeof(double2) * (size_t)p->desc.n);
+    fill(p->h_out, sizeof(double2) * (size_t)p->desc.n);
+    if (p->h_E) fill(p->h_E, sizeof(double) * (size_t)p->h_E_cap);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return cuda_status(e);
 }
 
@@ -885,6 +948,7 @@ cn_status cn_step_states(cn_plan p, const void* psi_in, void* states_out, const 
 cn_status cn_step_host(cn_plan p, const void* psi_in_host, void* psi_out_host, const double* E_mid_host,
                        int64_t nsteps, void* stream) {
     if (!p || !psi_in_host || !psi_out_host || nsteps < 0) return CN_ERR_INVALID_ARG;
+    if (p->slab) return CN_ERR_UNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t bytes = sizeof(double2) * (size_t)p->desc.n;
     cudaError_t e = cudaSuccess;
@@ -912,6 +976,7 @@ cn_status cn_step_host(cn_plan p, const void* psi_in_host, void* psi_out_host, c
 cn_status cn_solve_tridiag(cn_plan p, const void* b, const void* a, const void* c, const void* d, void* x, int64_t n,
                            void* stream) {
     if (!p || !b || !a || !c || !d || !x) return CN_ERR_INVALID_ARG;
+    if (p->slab) return CN_ERR_UNSUPPORTED;
     if (n != p->desc.n) return CN_ERR_INVALID_ARG;
     if (!aligned16(b) || !aligned16(a) || !aligned16(c) || !aligned16(d) || !aligned16(x)) return CN_ERR_INVALID_ARG;
     if (x == b || x == a || x == c) return CN_ERR_INVALID_ARG;
@@ -930,6 +995,7 @@ cn_status cn_solve_tridiag(cn_plan p, const void* b, const void* a, const void* 
 cn_status cn_adjoint_step(cn_plan p, const void* psi_n, const void* psi_np1, const void* lam_np1, void* lam_n,
                           const double* E_mid, double* dLdE, void* stream) {
     if (!p || !psi_n || !psi_np1 || !lam_np1 || !lam_n || !dLdE) return CN_ERR_INVALID_ARG;
+    if (p->slab) return CN_ERR_UNSUPPORTED;
     if (!aligned16(psi_n) || !aligned16(psi_np1) || !aligned16(lam_np1) || !aligned16(lam_n)) return CN_ERR_INVALID_ARG;
     if (!aligned8(dLdE) || (E_mid && !aligned8(E_mid))) return CN_ERR_INVALID_ARG;
     const int nparts = 148 * 4;
@@ -964,6 +1030,7 @@ cn_status cn_adjoint_step(cn_plan p, const void* psi_n, const void* psi_np1, con
     s.e = 0;   // right-hand side lam_{n+1} itself
     s.E = E_mid;
     s.tab = p->tab;
+    s.own_last = 1;
     const bool dfm = p->desc.arith == CN_ARITH_DF64;
     e = dfm ? cn_solve<df>(p, s, p->mu, st) : cn_solve<double>(p, s, p->mu, st);
     if (e != cudaSuccess) return CN_ERR_CUDA;
@@ -1045,6 +1112,132 @@ cn_status cn_plan_status(cn_plan p) {
     return read_status(p);
 }
 
+cn_status cn_plan_fill_workspace(cn_plan p, int32_t byte) {
+    if (!p) return CN_ERR_INVALID_ARG;
+    return fill_workspace(p, byte);
+}
+
+// ------------------------------------------------------------------ slabs of a sharded grid
+cn_status cn_slab_create(const cn_desc* desc, int32_t nslabs, int32_t rank, const int64_t* joints, cn_plan* out) {
+    if (!out) return CN_ERR_INVALID_ARG;
+    *out = nullptr;
+    cn_status v = validate_desc(desc, true);
+    if (v != CN_OK) return v;
+    if (nslabs < 1 || nslabs > CN_SLAB_MAX || rank < 0 || rank >= nslabs) return CN_ERR_INVALID_ARG;
+    const int64_t n = desc->n;
+    std::vector<int64_t> J((size_t)nslabs + 1);
+    for (int r = 0; r <= nslabs; ++r) {
+        J[(size_t)r] = joints ? joints[r] : (int64_t)(((__int128)r * (n - 1)) / nslabs);
+        if (r > 0 && J[(size_t)r] - J[(size_t)r - 1] < 2) return CN_ERR_INVALID_ARG;
+    }
+    if (J[0] != 0 || J[(size_t)nslabs] != n - 1) return CN_ERR_INVALID_ARG;
+    const int64_t lo = J[(size_t)rank], hi = J[(size_t)rank + 1];
+    cn_desc d = *desc;
+    d.n = hi - lo + 1;
+    d.x_min = desc->x_min + (double)lo * desc->dx;  // informational: the grid below is the global one
+    if (d.pot == CN_POT_ARRAY) d.V0 = desc->V0 + lo;
+    // the global grid's coordinates x_j = x_o + (j - j_o) dx, j counted from this slab's row 0
+    SysGrid g = make_grid(desc->x_min, desc->dx, n);
+    g.j_o -= lo;
+    cn_plan p = new (std::nothrow) cn_plan_s();
+    if (!p) return CN_ERR_OOM;
+    p->slab = true;
+    p->own_last = rank == nslabs - 1;
+    p->nslabs = nslabs;
+    p->slab_rank = rank;
+    p->slab_lo = lo;
+    p->slab_hi = hi;
+    v = create_engine(p, &d, std::vector<int64_t>{d.n}, std::vector<double>{d.x_min}, d.cos_a, &g);
+    if (v == CN_OK) {
+        p->workspace_bytes += (int64_t)(2 * sizeof(double2) * ((size_t)nslabs + 1));
+        if (cudaMalloc(&p->joint_work, 2 * sizeof(double2) * ((size_t)nslabs + 1)) != cudaSuccess)
+            v = alloc_status(cudaErrorMemoryAllocation);
+    }
+    if (v != CN_OK) {
+        destroy_engine(p);
+        delete p;
+        return v;
+    }
+    *out = p;
+    return CN_OK;
+}
+
+cn_status cn_slab_range(cn_plan p, int64_t* lo, int64_t* hi) {
+    if (!p || !p->slab || !lo || !hi) return CN_ERR_INVALID_ARG;
+    *lo = p->slab_lo;
+    *hi = p->slab_hi;
+    return CN_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <class R>
+cudaError_t slab_reduce(Engine* p, const double2* psi, const double* E_mid, double2* share, cudaStream_t st) {
+    CNStep s;
+    s.p = p->cnp;
+    s.psi = psi;
+    s.s = 1;
+    s.e = -1;
+    s.E = E_mid;
+    s.tab = p->tab;
+    s.own_last = p->own_last ? 1 : 0;
+    cudaError_t e = cn_reduce0<R>(p, s, st);
+    if (e == cudaSuccess) e = reduce_levels<R>(p, st);
+    if (e == cudaSuccess) {
+        const LevelData& B = p->lv.back();
+        e = launch(p->pdl, k_slab_export<R>, 1, 32, 0, st, level_source<R>(B).bind(B.sys[0]), share);
+    }
+    return e;
+}
+
+template <class R>
+cudaError_t slab_finish(Engine* p, const double2* shares, double2* psi_out, cudaStream_t st) {
+    const LevelData& B = p->lv.back();
+    cudaError_t e = launch(p->pdl, k_slab_joints<R>, 1, 32, 0, st, shares, p->nslabs, p->slab_rank, p->joint_work,
+                           p->joint_work + p->nslabs + 1, x_of<R>(B), p->status);
+    if (e == cudaSuccess) e = substitute_levels<R>(p, st);
+    if (e == cudaSuccess) {
+        CNStep s;
+        s.p = p->cnp;
+        s.psi = nullptr;
+        s.s = 1;
+        s.e = -1;
+        s.E = nullptr;
+        s.tab = p->tab;
+        s.own_last = p->own_last ? 1 : 0;
+        e = cn_subst0<R>(p, s, psi_out, st);
+    }
+    return e;
+}
+}  // namespace
+
+extern "C" {
+
+cn_status cn_slab_reduce(cn_plan p, const void* psi_local, const double* E_mid, void* share_out, void* stream) {
+    if (!p || !p->slab || !psi_local || !share_out) return CN_ERR_INVALID_ARG;
+    if (!p->keep) return CN_ERR_UNSUPPORTED;  // recompute mode keeps no right-hand sides
+    if (!aligned16(psi_local) || !aligned16(share_out) || (E_mid && !aligned8(E_mid))) return CN_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const double2* in = static_cast<const double2*>(psi_local);
+    double2* sh = static_cast<double2*>(share_out);
+    cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? slab_reduce<df>(p, in, E_mid, sh, st)
+                                                     : slab_reduce<double>(p, in, E_mid, sh, st);
+    return cuda_status(e);
+}
+
+cn_status cn_slab_finish(cn_plan p, const void* shares, void* psi_local_out, void* stream) {
+    if (!p || !p->slab || !shares || !psi_local_out) return CN_ERR_INVALID_ARG;
+    if (!p->keep) return CN_ERR_UNSUPPORTED;
+    if (!aligned16(shares) || !aligned16(psi_local_out)) return CN_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const double2* sh = static_cast<const double2*>(shares);
+    double2* out = static_cast<double2*>(psi_local_out);
+    cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? slab_finish<df>(p, sh, out, st)
+                                                     : slab_finish<double>(p, sh, out, st);
+    return cuda_status(e);
+}
+
 // ------------------------------------------------------------------ batches
 cn_status cn_batch_create(const cn_desc* common, int64_t nsys, const int64_t* sizes, const double* x_min,
                           const double* cos_a, cn_batch* out) {
@@ -1105,6 +1298,11 @@ cn_status cn_batch_step(cn_batch p, const void* psi_in, void* psi_out, const dou
 cn_status cn_batch_status(cn_batch p) {
     if (!p) return CN_ERR_INVALID_ARG;
     return read_status(p);
+}
+
+cn_status cn_batch_fill_workspace(cn_batch p, int32_t byte) {
+    if (!p) return CN_ERR_INVALID_ARG;
+    return fill_workspace(p, byte);
 }
 
 }  // extern "C"

@@ -1109,6 +1109,9 @@ struct CNStep {
                           // e = 0: the right-hand side is psi itself
     const double* E;      // the field at the step's midpoint (both matrices)
     const void* tab;      // coefficient table (CoefTab<R>::T per row), or NULL (regenerate)
+    int own_last;         // 1: the system's last row J_P is its own (its diagonal and its
+                          // explicit term with psi_{J_P}); 0: a slab of a larger grid that
+                          // ends on a joint line the next slab starts with, which owns them
 };
 
 __device__ __forceinline__ double rneg(double a) { return -a; }
@@ -1283,7 +1286,7 @@ k_cn_reduce(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, LevelPla
         const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
         CNRowStream<R, ES> rs;
         rs.init(st, e, grid.at(si), J0);
-        cn_reduce_block<R>(rs, gap, t == P - 1, keep, A0, D0, JUa, JUc, JUd, jd, Ag, Dg, ok);
+        cn_reduce_block<R>(rs, gap, t == P - 1 && st.own_last, keep, A0, D0, JUa, JUc, JUd, jd, Ag, Dg, ok);
     }
     write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, RowSink<R>(out, next.at(si), m_next),
                          out_slot);
@@ -1627,7 +1630,7 @@ k_cn_fused(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, const typ
         // reduction of step n + 1 from psi_{n+1}
         CNRowFused<R, ES> rs;
         rs.init(st, e, grid.at(si), J0, col);
-        cn_reduce_block<R>(rs, gap, t == P - 1, keep, A0, D0, JUa, JUc, JUd, jd, Ag, Dg, ok);
+        cn_reduce_block<R>(rs, gap, t == P - 1 && st.own_last, keep, A0, D0, JUa, JUc, JUd, jd, Ag, Dg, ok);
     }
     // (its barrier also orders every thread's tile writes before the tile store;
     // without the store, the exchange reuses the tile and the CTA holds no other
@@ -1643,6 +1646,71 @@ k_cn_fused(CNStep st, Map sys, Map next, Grid grid, int m, int m_next, const typ
             store128(x + base + i, sload(ys + k * kTileStride + b));
         }
     }
+}
+
+// ------------------------------------------------------------------ slabs of a sharded grid
+// A slab of a grid distributed over G ranks (Sec. 6.2, MPI implementation) is
+// nested down to a level of two rows: its first and last rows, the joint lines
+// J_r and J_{r+1} it shares with its neighbours.  Those two rows, after every
+// interior row of the slab has been eliminated (Table 1 at every level), are
+// the slab's share of the joint-line system: row J_r with its own diagonal and
+// explicit term (the slab starts there) plus JU, row J_{r+1} with the JD part
+// only (its own terms belong to the next slab, or to this one for the grid's
+// last row).  Six values per slab, the "values obtained on the joint lines" of
+// the communication section.
+//   out6 = { c(J_r), a(J_r), d(J_r), b(J_{r+1}), a(J_{r+1}), d(J_{r+1}) }
+template <class R>
+__global__ void k_slab_export(LevelSource<R> src, double2* out6) {
+    grid_dep_enter();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const Row<R> r0 = src.template row_at<R>(0);
+    const Row<R> r1 = src.template row_at<R>(1);
+    store128(out6 + 0, r0.c);
+    store128(out6 + 1, r0.a);
+    store128(out6 + 2, r0.d);
+    store128(out6 + 3, r1.b);
+    store128(out6 + 4, r1.a);
+    store128(out6 + 5, r1.d);
+}
+
+// The joint-line system of all G slabs, solved redundantly by every rank (one
+// thread, Thomas in binary64 on G + 1 rows; the paper's RS stage on a root
+// process, here without the second message): joint w couples to w - 1 through
+// slab w - 1 and to w + 1 through slab w,
+//   b_w = b(slab w-1 last row),  c_w = c(slab w row 0),
+//   a_w = a(slab w row 0) + a(slab w-1 last row),  d_w likewise,
+// in that fixed order.  This rank's two support values go to the two-row level
+// x_base, all G + 1 joint values to psiJ; cp: G + 1 entries of scratch for the
+// forward sweep.
+template <class R>
+__global__ void k_slab_joints(const double2* all6, int G, int rank, double2* cp, double2* psiJ,
+                              typename Store<R>::T* x_base, int* status) {
+    grid_dep_enter();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    bool ok = true;
+    const cx<double> zero = mk(0.0, 0.0);
+    auto ld = [&](int s, int k) { return load128<double>(all6 + 6 * s + k); };
+    // forward: c'_w = c_w / m_w, z_w = (d_w - b_w z_{w-1}) / m_w, m_w = a_w - b_w c'_{w-1}
+    cx<double> cpp = zero, zp = zero;
+    for (int w = 0; w <= G; ++w) {
+        cx<double> b = zero, a = zero, c = zero, d = zero;
+        if (w < G) { c = ld(w, 0); a = ld(w, 1); d = ld(w, 2); }
+        if (w > 0) { b = ld(w - 1, 3); a = cadd(a, ld(w - 1, 4)); d = cadd(d, ld(w - 1, 5)); }
+        const cx<double> iv = crcp(w == 0 ? a : csub(a, cmul(b, cpp)), ok);
+        zp = cmul(w == 0 ? d : csub(d, cmul(b, zp)), iv);
+        cpp = cmul(c, iv);
+        store128(cp + w, cpp);
+        store128(psiJ + w, zp);
+    }
+    cx<double> y = zp;
+    for (int w = G - 1; w >= 0; --w) {
+        y = csub(load128<double>(psiJ + w), cmul(load128<double>(cp + w), y));
+        store128(psiJ + w, y);
+    }
+    const cx<double> lo = load128<double>(psiJ + rank), hi = load128<double>(psiJ + rank + 1);
+    sstore(x_base + 0, mk(RealOps<R>::from_d(lo.re), RealOps<R>::from_d(lo.im)));
+    sstore(x_base + 1, mk(RealOps<R>::from_d(hi.re), RealOps<R>::from_d(hi.im)));
+    if (!ok) flag_error(status, kStatusNonfinite);
 }
 
 // ------------------------------------------------------------------ adjoint step

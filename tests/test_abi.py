@@ -103,3 +103,31 @@ def test_null_batch_arguments_rejected():
     assert lib.cn_batch_offsets(None, None) == 1
     assert lib.cn_batch_status(None) == 1
     assert lib.cn_batch_destroy(None) == 0
+
+
+@pytest.mark.parametrize("case", ["nslabs0", "rank_out", "joint_gap1", "joint_ends", "too_many"])
+def test_invalid_slab_rejected_on_host(case):
+    import numpy as np
+    lib = cnb.load()
+    h = C.c_void_p()
+    d = _desc(n=100)
+    G, r, J = 3, 0, None
+    if case == "nslabs0":
+        G = 0
+    elif case == "rank_out":
+        r = 3
+    elif case == "joint_gap1":
+        J = np.array([0, 10, 11, 99], np.int64)
+    elif case == "joint_ends":
+        J = np.array([1, 10, 50, 99], np.int64)
+    else:
+        G = cnb.SLAB_MAX + 1
+    rc = lib.cn_slab_create(C.byref(d), G, r, None if J is None else J.ctypes.data, C.byref(h))
+    assert rc == 1 and not h.value
+
+
+def test_slab_calls_reject_null_and_plain_plans():
+    lib = cnb.load()
+    assert lib.cn_slab_reduce(None, None, None, None, None) == 1
+    assert lib.cn_slab_finish(None, None, None, None) == 1
+    assert lib.cn_slab_range(None, None, None) == 1

@@ -78,7 +78,8 @@ def test_reference_arm_rank0_line(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "0")
 
     class A:
-        steps, warmup, gpus, block, level_block, arith, n, coeff_table = 1, 1, 1, 0, 0, "df64", 1 << 24, False
+        steps, warmup, gpus, block, level_block, level1_block, arith, n, coeff_table = (
+            1, 1, 1, None, None, None, "f64", 1 << 24, True)
     assert bench.run_reference(A()) == 0
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "unknown-steps/s" and line["value"] > 0
