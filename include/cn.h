@@ -58,7 +58,9 @@ typedef enum {
     CN_ERR_OOM = 3,          /* device workspace allocation failed               */
     CN_ERR_CUDA = 4,         /* a CUDA runtime call failed                       */
     CN_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out               */
-    CN_ERR_NONFINITE = 6     /* a pivot or result was zero / inf / NaN           */
+    CN_ERR_NONFINITE = 6,    /* a pivot or result was zero / inf / NaN           */
+    CN_ERR_BOUNDS = 7        /* debug build: an access outside every registered
+                                buffer was caught and skipped (cn_debug_report)  */
 } cn_status;
 
 /* Static part Vs(x) of V(x, t) = Vs(x) + x E(t) (length-gauge field term). */
@@ -384,8 +386,34 @@ cn_status cn_batch_fill_workspace(cn_batch batch, int32_t byte);
 /* Static description of a status code. */
 const char* cn_status_string(cn_status s);
 
-/* Library build information: "<version> sm_<arch>". */
+/* Library build information: "<version> sm_<arch>", with " debug" appended
+ * in the CN_DEBUG build. */
 const char* cn_version(void);
+
+/* Name of the last CUDA runtime error (cudaGetErrorName) that a call of the
+ * calling host thread turned into CN_ERR_CUDA or CN_ERR_OOM; "cudaSuccess" if
+ * none.  The string is static. */
+const char* cn_cuda_error_string(void);
+
+/* ---- The CN_DEBUG build (libcn_b300_debug.so; the stand-in for a memory
+ * sanitizer).  Every global-memory load and store of the kernels is checked
+ * against the extents of the buffers the enqueuing call may touch -- the
+ * plan's workspace and the caller's arrays at the sizes the call implies --
+ * registered by the host before the call's first launch.  An access outside
+ * all of them is recorded (the first one: address and size) and skipped: a
+ * load returns zero, a store is dropped.  Calls that share a stream see
+ * their own registrations; the debug build is for tests, one stream at a time.
+ *
+ * cn_debug_report: synchronise the device, then return CN_ERR_BOUNDS and the
+ * recorded access (*addr, *bytes; either may be NULL) if one was caught since
+ * the previous report, and clear the record; CN_OK if none.  The default
+ * build returns CN_ERR_UNSUPPORTED (nothing is checked there).
+ * cn_debug_selftest: plant one access just outside a registered extent (inside
+ * a live allocation, so nothing outside it is touched even if the check
+ * failed) and return CN_OK if the checks caught and reported it;
+ * CN_ERR_UNSUPPORTED in the default build. */
+cn_status cn_debug_report(uint64_t* addr, uint64_t* bytes);
+cn_status cn_debug_selftest(void);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,7 @@ FLAG_COEFF_TABLE = 1
 FLAG_RECOMPUTE = 2
 
 _STATUS = {0: "CN_OK", 1: "CN_ERR_INVALID_ARG", 2: "CN_ERR_UNSUPPORTED", 3: "CN_ERR_OOM", 4: "CN_ERR_CUDA",
-           5: "CN_ERR_TIMEOUT", 6: "CN_ERR_NONFINITE"}
+           5: "CN_ERR_TIMEOUT", 6: "CN_ERR_NONFINITE", 7: "CN_ERR_BOUNDS"}
 
 # every symbol declared in include/cn.h
 EXPORTS = ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_solve_tridiag",
@@ -34,7 +34,8 @@ EXPORTS = ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_s
            "cn_version", "cn_solve_tridiag_noalloc", "cn_adjoint_step", "cn_field_from_controls",
            "cn_field_grad_to_controls", "cn_batch_create", "cn_batch_destroy", "cn_batch_offsets",
            "cn_batch_step", "cn_batch_status", "cn_plan_create_levels", "cn_step_states", "cn_plan_fill_workspace",
-           "cn_batch_fill_workspace", "cn_slab_create", "cn_slab_range", "cn_slab_reduce", "cn_slab_finish")
+           "cn_batch_fill_workspace", "cn_slab_create", "cn_slab_range", "cn_slab_reduce", "cn_slab_finish",
+           "cn_cuda_error_string", "cn_debug_report", "cn_debug_selftest")
 SLAB_MAX = 65536
 SLAB_SHARE = 6  # complex values one slab contributes to the joint-line system per step
 NOALLOC_MAX_N = 1048576
@@ -44,7 +45,7 @@ MAX_LEVELS = 24
 # Launch configuration for large single systems (N ~ 2^24, coefficient table on),
 # from block-size sweeps of the soft-Coulomb step on B300: (level-0 block, level-1
 # block, block of the deeper levels) per arithmetic.
-LARGE_GRID_BLOCKS = {ARITH_F64: (13, 10, 16), ARITH_DF64: (13, 10, 16)}
+LARGE_GRID_BLOCKS = {ARITH_F64: (24, 8, 8), ARITH_DF64: (13, 10, 16)}
 PROFILE_CLASSES = ("reduce_level0", "substitute_level0", "reduce_levels_ge1", "substitute_levels_ge1", "rs_stage",
                    "fused_level0")
 
@@ -52,7 +53,10 @@ PROFILE_CLASSES = ("reduce_level0", "substitute_level0", "reduce_levels_ge1", "s
 class CNError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
-        super().__init__(f"{what}: {_STATUS.get(code, code)}")
+        msg = f"{what}: {_STATUS.get(code, code)}"
+        if code in (3, 4) and _lib is not None:
+            msg += f" ({_lib.cn_cuda_error_string().decode()})"
+        super().__init__(msg)
 
 
 class _Desc(C.Structure):
@@ -70,10 +74,21 @@ class _Info(C.Structure):
 
 _lib = None
 _lock = threading.Lock()
+_use_debug = False
+
+
+def use_debug_library() -> None:
+    """Load the CN_DEBUG build (bounds-checked kernels; include/cn.h) instead of
+    the default library.  Must be called before the first call that loads it."""
+    global _use_debug
+    with _lock:
+        if _lib is not None and not _use_debug:
+            raise RuntimeError("the default library is already loaded in this process")
+        _use_debug = True
 
 
 def library_path() -> str:
-    return _build.LIB
+    return _build.DEBUG_LIB if _use_debug else _build.LIB
 
 
 def load(build_if_missing: bool = True):
@@ -81,11 +96,12 @@ def load(build_if_missing: bool = True):
     global _lib
     with _lock:
         if _lib is None:
-            if build_if_missing and _build.needs_build():
-                _build.build()
-            if not os.path.exists(_build.LIB):
-                raise OSError(f"libcn_b300.so not built ({_build.LIB})")
-            lib = C.CDLL(_build.LIB)
+            path = _build.DEBUG_LIB if _use_debug else _build.LIB
+            if build_if_missing and _build.needs_build(path):
+                _build.build(debug=_use_debug)
+            if not os.path.exists(path):
+                raise OSError(f"{os.path.basename(path)} not built ({path})")
+            lib = C.CDLL(path)
             vp, i64 = C.c_void_p, C.c_int64
             lib.cn_plan_create.argtypes = [C.POINTER(_Desc), C.POINTER(vp)]
             lib.cn_plan_destroy.argtypes = [vp]
@@ -111,6 +127,12 @@ def load(build_if_missing: bool = True):
             lib.cn_status_string.restype = C.c_char_p
             lib.cn_version.argtypes = []
             lib.cn_version.restype = C.c_char_p
+            lib.cn_cuda_error_string.argtypes = []
+            lib.cn_cuda_error_string.restype = C.c_char_p
+            lib.cn_debug_report.argtypes = [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
+            lib.cn_debug_report.restype = C.c_int
+            lib.cn_debug_selftest.argtypes = []
+            lib.cn_debug_selftest.restype = C.c_int
             lib.cn_plan_create_levels.argtypes = [C.POINTER(_Desc), C.c_int32, vp, C.POINTER(vp)]
             lib.cn_plan_create_levels.restype = C.c_int
             lib.cn_batch_create.argtypes = [C.POINTER(_Desc), i64, vp, vp, vp, C.POINTER(vp)]
@@ -563,3 +585,12 @@ def field_grad_to_controls(dLdE, t_final: float, t0: float, dt: float, n_control
 
 def version() -> str:
     return load().cn_version().decode()
+
+
+def debug_report():
+    """CN_DEBUG build: (status, address, bytes) of the first out-of-bounds access
+    caught since the previous report (status 0: none; 7: CN_ERR_BOUNDS); the
+    default build returns status 2 (CN_ERR_UNSUPPORTED)."""
+    a, b = C.c_uint64(), C.c_uint64()
+    rc = load().cn_debug_report(C.byref(a), C.byref(b))
+    return int(rc), int(a.value), int(b.value)

@@ -9,6 +9,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <initializer_list>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -92,9 +96,18 @@ struct cn_batch_s : Engine {};
 
 namespace {
 
-cn_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CN_OK : CN_ERR_CUDA; }
+// The last CUDA runtime error a call of this thread turned into CN_ERR_CUDA or
+// CN_ERR_OOM (cn_cuda_error_string).
+thread_local cudaError_t t_last_cuda_error = cudaSuccess;
+
+cn_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return CN_OK;
+    t_last_cuda_error = e;
+    return CN_ERR_CUDA;
+}
 cn_status alloc_status(cudaError_t e) {
     cudaGetLastError();
+    t_last_cuda_error = e;
     return e == cudaErrorMemoryAllocation ? CN_ERR_OOM : CN_ERR_CUDA;
 }
 
@@ -149,6 +162,82 @@ void free_engine(Engine* p) {
     cudaFree(p->mu);
     cudaFree(p->part);
     cudaFree(p->joint_work);
+}
+
+// --------------------------------------------------------------- debug build: bounds registry
+// Extents of the buffers a call may touch, installed in the kernels' range table
+// (cn_debug.cuh) on the call's stream before its first launch.  No-ops in the
+// default build.
+#if defined(CN_DEBUG)
+struct DbgList {
+    std::vector<std::pair<const void*, size_t>> v;
+    void add(const void* p, size_t bytes) {
+        if (p && bytes) v.push_back({p, bytes});
+    }
+};
+
+size_t keep_bytes(const Engine* p) {
+    return p->keep ? kCplx * 2 * (size_t)p->lv[0].m * (size_t)grid_for(p->lv[0].total) * kThreads : 0;
+}
+
+void dbg_engine(const Engine* p, DbgList& L) {
+    const int64_t rows0 = p->lv[0].rows_total;
+    L.add(p->keep, keep_bytes(p));
+    L.add(p->state, kCplx * (size_t)rows0);
+    L.add(p->tab, (p->desc.arith == CN_ARITH_DF64 ? sizeof(df) : sizeof(double2)) * (size_t)rows0);
+    L.add(p->status, sizeof(int));
+    for (size_t l = 1; l < p->lv.size(); ++l) {
+        const LevelData& Lv = p->lv[l];
+        L.add(Lv.rows, 4 * kCplx * (size_t)std::max<int64_t>(Lv.L, 1));
+        L.add(Lv.slot, 3 * kCplx * (grid_for(p->lv[l - 1].total) + 1));
+        L.add(Lv.x, kCplx * (size_t)Lv.rows_total);
+    }
+    for (const LevelData& Lv : p->lv) L.add(Lv.d_sys, sizeof(LvlSys) * (size_t)p->nsys);
+    size_t zc_entries = 0;
+    for (size_t l = 0; l + 1 < p->lv.size(); ++l)
+        if (p->lv[l].m > kSmemRowsMax) zc_entries = std::max(zc_entries, 2 * (size_t)p->lv[l].rows_total);
+    L.add(p->zc, kCplx * zc_entries);
+    if (p->base_cs) L.add(p->base_cs, kCplx * (size_t)p->lv[(size_t)p->base_level[0]].sys[0].n);
+    L.add(p->d_base, std::max(sizeof(BaseSys<double>), sizeof(BaseSys<df>)) * (size_t)p->nsys);
+    L.add(p->d_grid, sizeof(SysGrid) * (size_t)p->nsys);
+    L.add(p->mu, sizeof(double2) * (size_t)p->desc.n);
+    L.add(p->part, 16 * (size_t)p->part_n + 16);
+    L.add(p->h_in, sizeof(double2) * (size_t)p->desc.n);
+    L.add(p->h_out, sizeof(double2) * (size_t)p->desc.n);
+    L.add(p->h_E, sizeof(double) * (size_t)p->h_E_cap);
+    L.add(p->joint_work, 2 * sizeof(double2) * ((size_t)p->nslabs + 1));
+    if (p->desc.pot == CN_POT_ARRAY) L.add(p->desc.V0, sizeof(double) * (size_t)rows0);
+}
+
+cudaError_t dbg_install(const DbgList& L, cudaStream_t st) {
+    DbgRange r[kDbgMaxRanges];
+    int n = 0;
+    for (const auto& e : L.v) {
+        if (n == kDbgMaxRanges) break;
+        r[n].lo = (unsigned long long)reinterpret_cast<uintptr_t>(e.first);
+        r[n].hi = r[n].lo + (unsigned long long)e.second;
+        ++n;
+    }
+    cudaError_t e = n ? cudaMemcpyToSymbolAsync(g_dbg_ranges, r, sizeof(DbgRange) * (size_t)n, 0,
+                                                cudaMemcpyHostToDevice, st)
+                      : cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_dbg_nranges, &n, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+    return e;
+}
+#endif
+
+cudaError_t dbg_register(const Engine* p, cudaStream_t st, std::initializer_list<std::pair<const void*, size_t>> extra) {
+#if defined(CN_DEBUG)
+    DbgList L;
+    if (p) dbg_engine(p, L);
+    for (const auto& e : extra) L.add(e.first, e.second);
+    return dbg_install(L, st);
+#else
+    (void)p;
+    (void)st;
+    (void)extra;
+    return cudaSuccess;
+#endif
 }
 
 // --------------------------------------------------------------- kernel timing
@@ -403,24 +492,42 @@ cudaError_t launch_substitute(bool pdl, const Src& src, Map sys, Map next, int m
 }
 
 // Opt the substitution kernels into the dynamic shared memory their largest block needs.
+// A kernel's dynamic shared memory limit is a property of the function for the
+// whole process (per device), shared by every plan: a plan may only raise it,
+// never lower it below what another live plan launches with.  The largest value
+// requested so far is kept per (device, kernel) and set again on every request
+// (so a device reset, which clears the attribute, is repaired by the next plan).
+std::mutex g_smem_mutex;
+std::map<std::pair<int, const void*>, int> g_smem_max;
+
+template <class... KArgs>
+cudaError_t raise_smem_limit(void (*kernel)(KArgs...), size_t bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_smem_mutex);
+    int& cur = g_smem_max[{dev, reinterpret_cast<const void*>(kernel)}];
+    cur = std::max(cur, (int)bytes);
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cur);
+}
+
 template <class R, class Map, class Grid>
 cudaError_t set_smem_limits_map(int m0, int ml) {
     typedef typename Store<R>::T ST;
-    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(k_substitute<R, ArraySource, Map, double2>, a, (int)subst_smem(m0));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_substitute<R, LevelSource<R>, Map, ST>, a, (int)subst_smem(ml));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute<R, -1, Map, Grid>, a, (int)subst_smem(m0));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute<R, 0, Map, Grid>, a, (int)subst_smem(m0));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_substitute_kept<R, Map>, a, (int)kept_smem(m0));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_fused<R, -1, Map, Grid, false>, a, (int)fused_smem(m0));
+    cudaError_t e = raise_smem_limit(k_substitute<R, ArraySource, Map, double2>, subst_smem(m0));
+    if (e == cudaSuccess) e = raise_smem_limit(k_substitute<R, LevelSource<R>, Map, ST>, subst_smem(ml));
+    if (e == cudaSuccess) e = raise_smem_limit(k_cn_substitute<R, -1, Map, Grid>, subst_smem(m0));
+    if (e == cudaSuccess) e = raise_smem_limit(k_cn_substitute<R, 0, Map, Grid>, subst_smem(m0));
+    if (e == cudaSuccess) e = raise_smem_limit(k_cn_substitute_kept<R, Map>, kept_smem(m0));
+    if (e == cudaSuccess) e = raise_smem_limit(k_cn_fused<R, -1, Map, Grid, false>, fused_smem(m0));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_cn_fused<R, -1, Map, Grid, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cn_fused<R, -1, Map, Grid, true>, a, (int)fused_smem(m0));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr<R>, a, (int)cr_smem());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_base_cr_many<R>, a, (int)cr_smem());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_reduce_ws<R, Map>, a, (int)ws_reduce_smem(kWsRowsMax));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_substitute_ws<R, Map>, a, (int)ws_subst_smem(kWsRowsMax));
+    if (e == cudaSuccess) e = raise_smem_limit(k_cn_fused<R, -1, Map, Grid, true>, fused_smem(m0));
+    if (e == cudaSuccess) e = raise_smem_limit(k_base_cr<R>, cr_smem());
+    if (e == cudaSuccess) e = raise_smem_limit(k_base_cr_many<R>, cr_smem());
+    if (e == cudaSuccess) e = raise_smem_limit(k_reduce_ws<R, Map>, ws_reduce_smem(kWsRowsMax));
+    if (e == cudaSuccess) e = raise_smem_limit(k_substitute_ws<R, Map>, ws_subst_smem(kWsRowsMax));
     return e;
 }
 
@@ -769,6 +876,7 @@ cn_status create_engine(Engine* p, const cn_desc* desc, const std::vector<int64_
     c.gt_f = split(c.gt);
     c.soft_f = split(c.soft_s);
     const double two_pi = 2.0 * 3.14159265358979323846;
+    if (use_table && e == cudaSuccess) e = dbg_register(p, nullptr, {});
     if (use_table) {
         // static part of the diagonal, one system at a time (once per plan or batch)
         for (int s = 0; s < ns && e == cudaSuccess; ++s) {
@@ -811,8 +919,12 @@ cn_status run_steps(Engine* p, const void* psi_in, void* psi_out, const double* 
     const double2* in = static_cast<const double2*>(psi_in);
     double2* out = static_cast<double2*>(psi_out);
     double2* sts = static_cast<double2*>(states);
-    cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? cn_steps<df>(p, in, out, E_mid, nsteps, st, sts)
-                                                     : cn_steps<double>(p, in, out, E_mid, nsteps, st, sts);
+    const size_t sb = sizeof(double2) * (size_t)p->lv[0].rows_total;
+    cudaError_t e = dbg_register(p, st, {{psi_in, sb}, {psi_out, sb}, {states, sb * (size_t)nsteps},
+                                         {E_mid, sizeof(double) * (size_t)nsteps}});
+    if (e == cudaSuccess)
+        e = (p->desc.arith == CN_ARITH_DF64) ? cn_steps<df>(p, in, out, E_mid, nsteps, st, sts)
+                                             : cn_steps<double>(p, in, out, E_mid, nsteps, st, sts);
     return cuda_status(e);
 }
 
@@ -879,11 +991,87 @@ const char* cn_status_string(cn_status s) {
     case CN_ERR_CUDA: return "CUDA runtime error";
     case CN_ERR_TIMEOUT: return "device-side wait timed out";
     case CN_ERR_NONFINITE: return "zero or non-finite pivot / result";
+    case CN_ERR_BOUNDS: return "debug build: out-of-bounds access caught and skipped";
     default: return "unknown status";
     }
 }
 
-const char* cn_version(void) { return "cn_b300 0.5 sm_103a"; }
+const char* cn_version(void) {
+#if defined(CN_DEBUG)
+    return "cn_b300 0.6 sm_103a debug";
+#else
+    return "cn_b300 0.6 sm_103a";
+#endif
+}
+
+const char* cn_cuda_error_string(void) { return cudaGetErrorName(t_last_cuda_error); }
+
+}  // extern "C"
+
+namespace cnb_noalloc_debug {
+int read_and_clear(unsigned long long* addr, unsigned long long* bytes);  // cn_noalloc.cu
+}
+
+#if defined(CN_DEBUG)
+namespace {
+__global__ void k_dbg_selftest(const double2* p, double2* out) {
+    // p[0] is registered, p[1] lies in the same allocation but outside every
+    // registered extent: the check must catch it and skip the load
+    out[0] = dbg_ld(p + 1);
+}
+}  // namespace
+#endif
+
+extern "C" {
+
+cn_status cn_debug_report(uint64_t* addr, uint64_t* bytes) {
+#if defined(CN_DEBUG)
+    if (cudaDeviceSynchronize() != cudaSuccess) return CN_ERR_CUDA;
+    int flag = 0;
+    unsigned long long a = 0, b = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&flag, g_dbg_flag, sizeof(int)) != cudaSuccess) return CN_ERR_CUDA;
+    if (flag) {
+        cudaMemcpyFromSymbol(&a, g_dbg_addr, sizeof(a));
+        cudaMemcpyFromSymbol(&b, g_dbg_bytes, sizeof(b));
+        const int z = 0;
+        cudaMemcpyToSymbol(g_dbg_flag, &z, sizeof(int));
+        cudaMemcpyToSymbol(g_dbg_addr, &zero, sizeof(zero));
+    } else {
+        flag = cnb_noalloc_debug::read_and_clear(&a, &b);
+    }
+    if (addr) *addr = a;
+    if (bytes) *bytes = b;
+    return flag ? CN_ERR_BOUNDS : CN_OK;
+#else
+    if (addr) *addr = 0;
+    if (bytes) *bytes = 0;
+    return CN_ERR_UNSUPPORTED;
+#endif
+}
+
+cn_status cn_debug_selftest(void) {
+#if defined(CN_DEBUG)
+    double2* buf = nullptr;
+    if (cudaMalloc(&buf, 4 * sizeof(double2)) != cudaSuccess) return alloc_status(cudaErrorMemoryAllocation);
+    cn_status r = CN_OK;
+    uint64_t a = 0, b = 0;
+    cn_debug_report(nullptr, nullptr);  // start from a clear record
+    cudaError_t e = dbg_register(nullptr, nullptr, {{buf, sizeof(double2)}, {buf + 2, 2 * sizeof(double2)}});
+    if (e == cudaSuccess) {
+        k_dbg_selftest<<<1, 1>>>(buf, buf + 2);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) r = cuda_status(e);
+    else if (cn_debug_report(&a, &b) != CN_ERR_BOUNDS || a != reinterpret_cast<uintptr_t>(buf + 1) ||
+             b != sizeof(double2))
+        r = CN_ERR_CUDA;  // the check missed the planted access
+    dbg_register(nullptr, nullptr, {});
+    cudaFree(buf);
+    return r;
+#else
+    return CN_ERR_UNSUPPORTED;
+#endif
+}
 
 cn_status cn_plan_create(const cn_desc* desc, cn_plan* out) {
     if (!out) return CN_ERR_INVALID_ARG;
@@ -987,8 +1175,11 @@ cn_status cn_solve_tridiag(cn_plan p, const void* b, const void* a, const void* 
     s.d = static_cast<const double2*>(d);
     s.n = n;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? solve_arrays<df>(p, s, static_cast<double2*>(x), st)
-                                                     : solve_arrays<double>(p, s, static_cast<double2*>(x), st);
+    const size_t vb = sizeof(double2) * (size_t)n;
+    cudaError_t e = dbg_register(p, st, {{b, vb}, {a, vb}, {c, vb}, {d, vb}, {x, vb}});
+    if (e == cudaSuccess)
+        e = (p->desc.arith == CN_ARITH_DF64) ? solve_arrays<df>(p, s, static_cast<double2*>(x), st)
+                                             : solve_arrays<double>(p, s, static_cast<double2*>(x), st);
     return cuda_status(e);
 }
 
@@ -1032,6 +1223,10 @@ cn_status cn_adjoint_step(cn_plan p, const void* psi_n, const void* psi_np1, con
     s.tab = p->tab;
     s.own_last = 1;
     const bool dfm = p->desc.arith == CN_ARITH_DF64;
+    const size_t vb = sizeof(double2) * (size_t)p->desc.n;
+    e = dbg_register(p, st, {{psi_n, vb}, {psi_np1, vb}, {lam_np1, vb}, {lam_n, vb}, {E_mid, sizeof(double)},
+                             {dLdE, sizeof(double)}});
+    if (e != cudaSuccess) return cuda_status(e);
     e = dfm ? cn_solve<df>(p, s, p->mu, st) : cn_solve<double>(p, s, p->mu, st);
     if (e != cudaSuccess) return CN_ERR_CUDA;
     const SysGrid& g = p->grid[0];
@@ -1056,6 +1251,9 @@ cn_status cn_field_from_controls(const double* u, int64_t n_controls, double t_f
         !std::isfinite(dt) || dt == 0.0)
         return CN_ERR_INVALID_ARG;
     if (nsteps == 0) return CN_OK;
+    cudaError_t e = dbg_register(nullptr, static_cast<cudaStream_t>(stream),
+                                 {{u, sizeof(double) * (size_t)n_controls}, {E_mid, sizeof(double) * (size_t)nsteps}});
+    if (e != cudaSuccess) return cuda_status(e);
     k_hat_field<<<(unsigned)ceil_div(nsteps, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         u, n_controls, t_final, t0, dt, nsteps, E_mid);
     return cuda_status(cudaGetLastError());
@@ -1066,6 +1264,9 @@ cn_status cn_field_grad_to_controls(const double* dLdE, int64_t nsteps, double t
     if (!dLdE || !grad_u || n_controls < 2 || nsteps < 0 || !(t_final > 0.0) || !std::isfinite(t0) ||
         !(dt > 0.0))
         return CN_ERR_INVALID_ARG;
+    cudaError_t e = dbg_register(nullptr, static_cast<cudaStream_t>(stream),
+                                 {{dLdE, sizeof(double) * (size_t)nsteps}, {grad_u, sizeof(double) * (size_t)n_controls}});
+    if (e != cudaSuccess) return cuda_status(e);
     k_hat_field_grad<<<(unsigned)ceil_div(n_controls, 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
         dLdE, nsteps, t_final, t0, dt, n_controls, grad_u);
     return cuda_status(cudaGetLastError());
@@ -1221,8 +1422,11 @@ cn_status cn_slab_reduce(cn_plan p, const void* psi_local, const double* E_mid, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const double2* in = static_cast<const double2*>(psi_local);
     double2* sh = static_cast<double2*>(share_out);
-    cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? slab_reduce<df>(p, in, E_mid, sh, st)
-                                                     : slab_reduce<double>(p, in, E_mid, sh, st);
+    cudaError_t e = dbg_register(p, st, {{psi_local, sizeof(double2) * (size_t)p->desc.n}, {E_mid, sizeof(double)},
+                                         {share_out, 6 * sizeof(double2)}});
+    if (e == cudaSuccess)
+        e = (p->desc.arith == CN_ARITH_DF64) ? slab_reduce<df>(p, in, E_mid, sh, st)
+                                             : slab_reduce<double>(p, in, E_mid, sh, st);
     return cuda_status(e);
 }
 
@@ -1233,8 +1437,11 @@ cn_status cn_slab_finish(cn_plan p, const void* shares, void* psi_local_out, voi
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const double2* sh = static_cast<const double2*>(shares);
     double2* out = static_cast<double2*>(psi_local_out);
-    cudaError_t e = (p->desc.arith == CN_ARITH_DF64) ? slab_finish<df>(p, sh, out, st)
-                                                     : slab_finish<double>(p, sh, out, st);
+    cudaError_t e = dbg_register(p, st, {{shares, 6 * sizeof(double2) * (size_t)p->nslabs},
+                                         {psi_local_out, sizeof(double2) * (size_t)p->desc.n}});
+    if (e == cudaSuccess)
+        e = (p->desc.arith == CN_ARITH_DF64) ? slab_finish<df>(p, sh, out, st)
+                                             : slab_finish<double>(p, sh, out, st);
     return cuda_status(e);
 }
 

@@ -31,6 +31,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
+
+#include "cn_debug.cuh"
 #if !defined(__CUDA_ARCH__)
 #include <math.h>
 #endif
@@ -392,21 +394,21 @@ template <class R> struct Store;
 template <> struct Store<double> { typedef double2 T; };
 template <> struct Store<df> { typedef float4 T; };
 
-CNB_HD cx<double> sload(const double2* p) { double2 v = *p; return mk(v.x, v.y); }
-CNB_HD void sstore(double2* p, cx<double> z) { *p = make_double2(z.re, z.im); }
+CNB_HD cx<double> sload(const double2* p) { double2 v = dbg_ld(p); return mk(v.x, v.y); }
+CNB_HD void sstore(double2* p, cx<double> z) { dbg_st(p, make_double2(z.re, z.im)); }
 CNB_HD cx<df> sload(const float4* p) {
-    float4 v = *p;
+    float4 v = dbg_ld(p);
     return mk(df_make(v.x, v.y), df_make(v.z, v.w));
 }
-CNB_HD void sstore(float4* p, cx<df> z) { *p = make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo); }
+CNB_HD void sstore(float4* p, cx<df> z) { dbg_st(p, make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo)); }
 
 // complex128 in memory <-> cx<R>
 template <class R> CNB_HD cx<R> load128(const double2* p) {
-    double2 v = *p;
+    double2 v = dbg_ld(p);
     return mk<R>(RealOps<R>::from_d(v.x), RealOps<R>::from_d(v.y));
 }
 template <class R> CNB_HD void store128(double2* p, cx<R> z) {
-    *p = make_double2(RealOps<R>::to_d(z.re), RealOps<R>::to_d(z.im));
+    dbg_st(p, make_double2(RealOps<R>::to_d(z.re), RealOps<R>::to_d(z.im)));
 }
 
 }  // namespace cnb

@@ -61,6 +61,9 @@ __host__ __device__ __forceinline__ int64_t joint_line(int64_t t, int64_t P, int
 constexpr int kStatusNonfinite = 6;  // cn_status CN_ERR_NONFINITE
 
 __device__ __forceinline__ void flag_error(int* status, int code) {
+#if defined(CN_DEBUG)
+    if (status && !dbg_ok(status, sizeof(int))) return;
+#endif
     if (status) atomicCAS(status, 0, code);
 }
 
@@ -132,12 +135,17 @@ struct ManySys {
         int lo = 0, hi = nsys - 1;
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
-            if (tab[mid].blk_off <= g) lo = mid;
+            if (dbg_ld(&tab[mid].blk_off) <= g) lo = mid;
             else hi = mid - 1;
         }
         return lo;
     }
-    __device__ __forceinline__ const LvlSys& at(int s) const { return tab[s]; }
+    __device__ __forceinline__ const LvlSys& at(int s) const {
+#if defined(CN_DEBUG)
+        if (!dbg_ok(tab + s, sizeof(LvlSys))) return tab[0];
+#endif
+        return tab[s];
+    }
 };
 
 // ------------------------------------------------------------------ reduced rows
@@ -282,7 +290,7 @@ __device__ __forceinline__ void write_reduced_row(bool active, int64_t t, int64_
         sstore(&s.b, jd.b);
         sstore(&s.a, jd.a);
         sstore(&s.d, jd.d);
-        out_slot[blockIdx.x + 1] = s;
+        dbg_st(&out_slot[blockIdx.x + 1], s);
     }
 }
 
@@ -575,7 +583,7 @@ __device__ __forceinline__ void ws_write_reduced_row(bool writer, bool active, i
             sstore(&s.b, jd.b);
             sstore(&s.a, jd.a);
             sstore(&s.d, jd.d);
-            out_slot[blockIdx.x / kWsCluster + 1] = s;
+            dbg_st(&out_slot[blockIdx.x / kWsCluster + 1], s);
         }
     }
 }
@@ -905,7 +913,7 @@ __device__ __forceinline__ void cr_solve(const LevelSource<R>& src, typename Sto
         }
         __syncthreads();
     }
-    for (int i = tid; i < n; i += kCrThreads) x[i] = sx[i];
+    for (int i = tid; i < n; i += kCrThreads) dbg_st(&x[i], sx[i]);
     if (!ok) flag_error(status, kStatusNonfinite);
 }
 
@@ -921,7 +929,7 @@ template <class R>
 __global__ void __launch_bounds__(kCrThreads)
 k_base_cr_many(const BaseSys<R>* sys, int* status) {
     grid_dep_enter();
-    const BaseSys<R> b = sys[blockIdx.x];
+    const BaseSys<R> b = dbg_ld(&sys[blockIdx.x]);
     cr_solve<R>(b.src, b.x, status);
 }
 
@@ -959,13 +967,18 @@ struct OneGrid {
 };
 struct ManyGrid {
     const SysGrid* tab;
-    __device__ __forceinline__ const SysGrid& at(int s) const { return tab[s]; }
+    __device__ __forceinline__ const SysGrid& at(int s) const {
+#if defined(CN_DEBUG)
+        if (!dbg_ok(tab + s, sizeof(SysGrid))) return tab[0];
+#endif
+        return tab[s];
+    }
 };
 
 // Static potential Vs(x_j) in binary64 (the FP64 path and the table builder).
 __device__ __forceinline__ double static_potential_d(const CNParams& p, int64_t j, double x) {
     switch (p.pot) {
-    case 1: return p.V0[j];
+    case 1: return dbg_ld(&p.V0[j]);
     case 2: return -rsqrt(fma(x, x, p.soft_s));
     case 3: {
         double v = 0.0;
@@ -993,7 +1006,7 @@ __global__ void k_beta0_table(CNParams p, SysGrid sg, int64_t n, typename CoefTa
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     double x = fma((double)(j - sg.j_o), p.dx, sg.x_o);
-    tab[j] = coef_entry(fma(p.c1, static_potential_d(p, j, x), 2.0), x, R());
+    dbg_st(&tab[j], coef_entry(fma(p.c1, static_potential_d(p, j, x), 2.0), x, R()));
 }
 
 // Per-thread coefficient generator walking rows j0, j0+1, ...: returns bt_j for
@@ -1018,11 +1031,12 @@ template <> struct CoefGen<double> {
     }
     __device__ __forceinline__ void next(double& bt) {
         if (tab) {
-            const double2 v = tab[j];
+            const double2 v = dbg_ld(&tab[j]);
             bt = fma(c1E, v.y, v.x);
         } else {
             const double x = fma(dj, p->dx, sg.x_o);
-            const double b0 = p->pot == 1 ? fma(p->c1, V0[j], 2.0) : fma(p->c1, static_potential_d(*p, j, x), 2.0);
+            const double b0 =
+                p->pot == 1 ? fma(p->c1, dbg_ld(&V0[j]), 2.0) : fma(p->c1, static_potential_d(*p, j, x), 2.0);
             bt = fma(c1E, x, b0);
         }
         ++j;
@@ -1053,7 +1067,7 @@ template <> struct CoefGen<df> {
     __device__ __forceinline__ void next(df& bt) {
         df b0;
         if (tab) {
-            b0 = tab[j];
+            b0 = dbg_ld(&tab[j]);
         } else if (pot == 2) {
             // bt0 = 2 - c1 / sqrt(x^2 + s)
             df q = df_add(df_mul(x, x), soft_s);
@@ -1136,7 +1150,7 @@ template <class R, int ES> struct CNRowStream {
         return (j >= 0 && j < n) ? load128<R>(psi + j) : czero<R>();
     }
     __device__ __forceinline__ void init(const CNStep& st, const LvlSys& e, const SysGrid& g, int64_t j0) {
-        const double E = st.E ? *st.E : 0.0;
+        const double E = st.E ? dbg_ld(st.E) : 0.0;
         sg = signed_gt(st, R());
         msg = rneg(sg);  // imaginary part of a~: -s g~
         psi = st.psi + e.row_off;
@@ -1494,7 +1508,7 @@ template <class R, int ES> struct CNRowFused {
     const ST* ys;      // row j of the block at ys[j * kTileStride]: xL at 0, psi at 1..g-1, xR at g, 0 at g+1
     __device__ __forceinline__ void init(const CNStep& st, const LvlSys& e, const SysGrid& g, int64_t J0,
                                          const ST* col) {
-        const double E = st.E ? *st.E : 0.0;
+        const double E = st.E ? dbg_ld(st.E) : 0.0;
         sg = signed_gt(st, R());
         msg = rneg(sg);
         const typename CoefTab<R>::T* tab =
@@ -1723,6 +1737,9 @@ __global__ void k_slab_joints(const double2* all6, int G, int rank, double2* cp,
 // that finishes last (a ticket counter) adds all partials in a fixed tree order
 // (deterministic), accumulates dt * sum into *dLdE and resets the ticket.
 constexpr int kAdjThreads = 256;
+#if defined(CN_DEBUG)
+static __device__ unsigned int dbg_spare_ticket;  // stands in for an unregistered ticket (debug build)
+#endif
 
 __device__ __forceinline__ double adj_term(cx<double> mu, cx<double> s, double x) {
     // Im(conj(mu) s) x = (mu.re s.im - mu.im s.re) x
@@ -1743,8 +1760,16 @@ __device__ __forceinline__ df xcoord(const CNParams& p, const SysGrid& g, int64_
     return df_add(dfc(g.xo_f), df_add(df_mul_f(df_mul_f(dx, jh), 65536.0f), df_mul_f(dx, jl)));
 }
 // L2-coherent loads of another CTA's partial (not through this SM's L1)
-__device__ __forceinline__ double ld_part(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ double ld_part(const double* p) {
+#if defined(CN_DEBUG)
+    if (!dbg_ok(p, sizeof(double))) return 0.0;
+#endif
+    return __ldcg(p);
+}
 __device__ __forceinline__ df ld_part(const df* p) {
+#if defined(CN_DEBUG)
+    if (!dbg_ok(p, sizeof(df))) return df_make(0.0f, 0.0f);
+#endif
     const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
     return df_make(v.x, v.y);
 }
@@ -1778,8 +1803,11 @@ k_adjoint_finish(CNParams p, SysGrid sg, int64_t n, const double2* mu, const dou
     }
     const R blk = cta_sum(acc, red);
     if (threadIdx.x == 0) {
-        part[blockIdx.x] = blk;
+        dbg_st(&part[blockIdx.x], blk);
         __threadfence();
+#if defined(CN_DEBUG)
+        if (!dbg_ok(ticket, sizeof(unsigned int))) ticket = &dbg_spare_ticket;
+#endif
         last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
@@ -1790,8 +1818,8 @@ k_adjoint_finish(CNParams p, SysGrid sg, int64_t n, const double2* mu, const dou
     __syncthreads();  // red is reused
     const R tot = cta_sum(t, red);
     if (threadIdx.x == 0) {
-        *dLdE += dt * RealOps<R>::to_d(tot);
-        *ticket = 0u;
+        dbg_st(dLdE, dbg_ld(dLdE) + dt * RealOps<R>::to_d(tot));
+        dbg_st(ticket, 0u);
     }
 }
 
@@ -1817,7 +1845,7 @@ static __global__ void k_hat_field(const double* u, int64_t nc, double t_final, 
     int64_t i0;
     double f;
     hat_locate(t0 + ((double)k + 0.5) * dt, t_final, nc, i0, f);
-    E_mid[k] = (1.0 - f) * u[i0] + f * u[i0 + 1];
+    dbg_st(&E_mid[k], (1.0 - f) * dbg_ld(&u[i0]) + f * dbg_ld(&u[i0 + 1]));
 }
 
 static __global__ void k_hat_field_grad(const double* dLdE, int64_t nsteps, double t_final, double t0, double dt,
@@ -1838,10 +1866,10 @@ static __global__ void k_hat_field_grad(const double* dLdE, int64_t nsteps, doub
         int64_t i0;
         double f;
         hat_locate(t0 + ((double)k + 0.5) * dt, t_final, nc, i0, f);
-        if (i0 == c) acc = fma(dLdE[k], 1.0 - f, acc);
-        else if (i0 + 1 == c) acc = fma(dLdE[k], f, acc);
+        if (i0 == c) acc = fma(dbg_ld(&dLdE[k]), 1.0 - f, acc);
+        else if (i0 + 1 == c) acc = fma(dbg_ld(&dLdE[k]), f, acc);
     }
-    g[c] = acc;
+    dbg_st(&g[c], acc);
 }
 
 }  // namespace cnb

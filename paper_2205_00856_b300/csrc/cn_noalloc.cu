@@ -123,6 +123,26 @@ cudaError_t na_solve(unsigned char* base, const NaLevel* lv, int L, const ArrayS
 
 }  // namespace
 
+// Debug build: the violation record of this translation unit's bounds checks
+// (cn_debug.cuh), read and cleared by cn_debug_report.
+namespace cnb_noalloc_debug {
+int read_and_clear(unsigned long long* addr, unsigned long long* bytes) {
+#if defined(CN_DEBUG)
+    int flag = 0;
+    if (cudaMemcpyFromSymbol(&flag, g_dbg_flag, sizeof(int)) != cudaSuccess || !flag) return 0;
+    cudaMemcpyFromSymbol(addr, g_dbg_addr, sizeof(*addr));
+    cudaMemcpyFromSymbol(bytes, g_dbg_bytes, sizeof(*bytes));
+    const int z = 0;
+    cudaMemcpyToSymbol(g_dbg_flag, &z, sizeof(int));
+    return 1;
+#else
+    (void)addr;
+    (void)bytes;
+    return 0;
+#endif
+}
+}  // namespace cnb_noalloc_debug
+
 extern "C" cn_status cn_solve_tridiag_noalloc(const void* b, const void* a, const void* c, const void* d, void* x,
                                               int64_t n, int32_t arith, void* stream) {
     if (!b || !a || !c || !d || !x || n < 3) return CN_ERR_INVALID_ARG;
@@ -147,6 +167,22 @@ extern "C" cn_status cn_solve_tridiag_noalloc(const void* b, const void* a, cons
     s.n = n;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned char* p = static_cast<unsigned char*>(base);
+#if defined(CN_DEBUG)
+    {
+        const size_t vb = sizeof(double2) * (size_t)n;
+        const void* ptrs[6] = {b, a, c, d, x, base};
+        const size_t sizes[6] = {vb, vb, vb, vb, vb, kNaScratchBytes};
+        DbgRange r[6];
+        for (int i = 0; i < 6; ++i) {
+            r[i].lo = (unsigned long long)reinterpret_cast<uintptr_t>(ptrs[i]);
+            r[i].hi = r[i].lo + sizes[i];
+        }
+        const int nr = 6;
+        if (cudaMemcpyToSymbolAsync(g_dbg_ranges, r, sizeof(r), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyToSymbolAsync(g_dbg_nranges, &nr, sizeof(int), 0, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return CN_ERR_CUDA;
+    }
+#endif
     cudaError_t e = (arith == CN_ARITH_DF64) ? na_solve<df>(p, lv, L, s, static_cast<double2*>(x), st)
                                              : na_solve<double>(p, lv, L, s, static_cast<double2*>(x), st);
     return e == cudaSuccess ? CN_OK : CN_ERR_CUDA;

@@ -6,9 +6,14 @@
 #pragma once
 #include <cstdint>
 
+#include "cn_debug.cuh"
+
 namespace cnb {
 
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+#if defined(CN_DEBUG)
+    if (!dbg_ok(src, bytes)) return;  // a range outside the registered buffers is a layout error
+#endif
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 

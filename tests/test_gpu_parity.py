@@ -451,3 +451,22 @@ def test_norm_conservation_1000_steps_2pow20(arith):
     plan.check()
     n0, n1 = np.sum(np.abs(psi0) ** 2), np.sum(np.abs(out) ** 2)
     assert abs(n1 / n0 - 1) <= (1e-12 if arith == cnb.ARITH_F64 else 1e-11)
+
+
+def test_plans_with_different_blocks_coexist():
+    """A plan created after another with smaller blocks must not lower the
+    shared-memory limit the first plan's kernels launch with (the limit is a
+    property of each kernel for the whole process)."""
+    cfg = W.soft_coulomb_config(n=200003, nsteps=3)
+    psi0 = W.initial_state(cfg)
+    E = W.field_midpoints(3, cfg["dt"], t0=60.0)
+    ref = oracle.cn_run(oracle_problem(cfg), psi0, 3, E_mid=E)
+    for arith in (cnb.ARITH_F64, cnb.ARITH_DF64):
+        big = plan_for(cfg, arith=arith, block=32, level_block=32, level1_block=32)
+        small = plan_for(cfg, arith=arith, block=3, level_block=3)
+        for p in (big, small, big):
+            out = p.step(to_dev(psi0), 3, E_mid=to_dev(E)).cpu().numpy()
+            p.check()
+            assert rel(out, ref) <= 1e-11
+        big.close()
+        small.close()
