@@ -110,13 +110,23 @@ typedef struct {
  * both from psi instead, and the plan holds one n-point state buffer (16 B per
  * point) for the step ping-pong -- for grids whose 32 B per point do not fit. */
 #define CN_FLAG_RECOMPUTE 2
+/* cn_desc.flags: run every stage below level 0 as its own launch (one per stage
+ * and level) instead of the default single persistent launch (see
+ * cn_plan_create). */
+#define CN_FLAG_LEVEL_LAUNCHES 4
 
 /* Create a plan for systems of size desc->n.  The N-shaped solve is nested
  * (Eq. iteration): level 0 is cut into blocks of desc->block rows, level 1 into
  * blocks of desc->level1_block rows (if nonzero), every other reduced level into
  * blocks of desc->level_block rows, until a level has at most 1024
  * rows; that system (the RS stage) is solved inside one CTA by cyclic
- * reduction.  Allocates the device workspace on the current device: the
+ * reduction.  The stages below level 0 -- the reductions of levels 1 .. L-1,
+ * the RS stage and the substitutions back up -- run in ONE persistent
+ * cooperative launch (all its CTAs resident at once, one per multiprocessor,
+ * stages separated by grid-wide barriers bounded by a time limit: a barrier
+ * that gives up records CN_ERR_TIMEOUT, see cn_plan_set_wait_limit), unless
+ * desc->flags has CN_FLAG_LEVEL_LAUNCHES or the kernel cannot be resident;
+ * either way the results are the same bits.  Allocates the device workspace on the current device: the
  * reduced systems of every level (~80 B per row of level 1 and below), 32 B
  * per grid point of kept right-hand sides and pivots (16 B of state buffer
  * instead with CN_FLAG_RECOMPUTE), the optional coefficient table, a status
@@ -150,14 +160,15 @@ cn_status cn_plan_destroy(cn_plan plan);
  * E_mid: device array of nsteps doubles, E_mid[k] = E(t0 + (k + 1/2) dt), the
  * field at the midpoint of step k (Sec. 2: T is built at t + dt/2); NULL
  * means E = 0.  psi_in may equal psi_out; psi_in is otherwise not modified.
- * nsteps = 0 copies psi_in to psi_out.  In double-float store mode the steps
- * of one call pass psi on chip: each step's level-0 substitution and the next
- * step's level-0 reduction run as one kernel, and psi is written once, by the
- * last step.  psi then keeps its double-float form between the steps of a
- * call instead of being rounded to complex128, so a call of K steps and K
- * calls of one step agree to rounding (bitwise in binary64, recompute mode and
- * blocks longer than 32 rows, which keep every step separate).  Asynchronous
- * on `stream`; device-side errors go to the plan status (cn_plan_status). */
+ * nsteps = 0 copies psi_in to psi_out.  In store mode (blocks of at most 32
+ * rows) the steps of one call pass psi on chip: each step's level-0
+ * substitution and the next step's level-0 reduction run as one kernel, and
+ * psi is written once, by the last step.  In binary64 a call of K steps and K
+ * calls of one step give the same bits; in double-float psi keeps its
+ * double-float form between the steps of a call instead of being rounded to
+ * complex128, so the two agree to rounding.  Recompute mode and blocks longer
+ * than 32 rows keep every step separate.  Asynchronous on `stream`;
+ * device-side errors go to the plan status (cn_plan_status). */
 cn_status cn_step(cn_plan plan, const void* psi_in, void* psi_out, const double* E_mid,
                   int64_t nsteps, void* stream);
 
@@ -165,9 +176,9 @@ cn_status cn_step(cn_plan plan, const void* psi_in, void* psi_out, const double*
  * writes psi_{k+1} to states_out + k n (device, complex128[nsteps n], the
  * states back to back) -- what a backward pass that recomputes a segment of a
  * propagation needs.  psi_in must not overlap states_out (CN_ERR_INVALID_ARG).
- * In double-float store mode the steps run as in cn_step's step loop (psi
- * stays on chip from one step to the next; the stored state is its complex128
- * rounding), so states_out[nsteps-1] equals cn_step's result bitwise. */
+ * In store mode the steps run as in cn_step's step loop (psi stays on chip
+ * from one step to the next; the stored state is its complex128 rounding), so
+ * states_out[nsteps-1] equals cn_step's result bitwise. */
 cn_status cn_step_states(cn_plan plan, const void* psi_in, void* states_out, const double* E_mid,
                          int64_t nsteps, void* stream);
 
@@ -221,7 +232,8 @@ typedef struct {
                                          /* is solved by the RS stage (one CTA, cyclic    */
                                          /* reduction; serial for cn_plan_create_levels)  */
     int32_t launches_per_step;           /* kernels one single-step cn_step / one solve
-                                            launches (2 levels + 1); inside a cn_step of
+                                            launches: 3 with the persistent launch below
+                                            level 0, else 2 levels + 1; inside a cn_step of
                                             nsteps >= 2 in store mode a step launches one
                                             fewer, plus one substitution per call          */
     int64_t level_rows[CN_MAX_LEVELS];   /* rows of level 0 .. levels                     */
@@ -238,9 +250,10 @@ cn_status cn_plan_query(cn_plan plan, cn_plan_info* out);
  * (RD+JD+RU+JU), 1 = level-0 substitution (SS), 2 = reductions of levels >= 1,
  * 3 = substitutions of levels >= 1, 4 = RS stage, 5 = level-0 SS of one step
  * fused with the level-0 reduction of the next (cn_step with nsteps >= 2 in
- * store mode).  cap = entries available in ms / launches (at most 6 are
- * written). */
-#define CN_PROFILE_CLASSES 6
+ * store mode), 6 = the persistent launch of every stage below level 0 (classes
+ * 2 .. 4 then stay empty).  cap = entries available in ms / launches (at most
+ * 7 are written). */
+#define CN_PROFILE_CLASSES 7
 cn_status cn_plan_profile(cn_plan plan, int enable);
 cn_status cn_plan_profile_read(cn_plan plan, double* ms, int64_t* launches, int32_t cap);
 
@@ -324,6 +337,15 @@ cn_status cn_slab_finish(cn_plan slab, const void* shares, void* psi_local_out, 
 /* Wait for the plan's stream work to finish (device synchronise) and return
  * the first device-side error recorded since the last call (then clear it). */
 cn_status cn_plan_status(cn_plan plan);
+
+/* The bounded waits of the persistent launch below level 0: every grid-wide
+ * barrier gives up after timeout_ns nanoseconds (default 2e9), records
+ * CN_ERR_TIMEOUT in the plan's status and lets the launch end; cn_plan_status
+ * returns it and restores the barrier.  missing_ctas > 0 is a test hook: the
+ * barriers then wait for that many CTAs beyond the launch, which never arrive,
+ * so every barrier runs out (the results of such a step are not valid).
+ * CN_ERR_INVALID_ARG for timeout_ns <= 0 or missing_ctas < 0. */
+cn_status cn_plan_set_wait_limit(cn_plan plan, int64_t timeout_ns, int32_t missing_ctas);
 
 /* Debugging aid (the check that stands in for a memory sanitizer): synchronise
  * the device, then fill every scratch buffer the plan owns with the byte value

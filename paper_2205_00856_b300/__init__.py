@@ -24,6 +24,7 @@ POT_NONE, POT_ARRAY, POT_SOFTCOULOMB, POT_COSSERIES = 0, 1, 2, 3
 ARITH_F64, ARITH_DF64 = 0, 1
 FLAG_COEFF_TABLE = 1
 FLAG_RECOMPUTE = 2
+FLAG_LEVEL_LAUNCHES = 4
 
 _STATUS = {0: "CN_OK", 1: "CN_ERR_INVALID_ARG", 2: "CN_ERR_UNSUPPORTED", 3: "CN_ERR_OOM", 4: "CN_ERR_CUDA",
            5: "CN_ERR_TIMEOUT", 6: "CN_ERR_NONFINITE", 7: "CN_ERR_BOUNDS"}
@@ -35,7 +36,7 @@ EXPORTS = ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_s
            "cn_field_grad_to_controls", "cn_batch_create", "cn_batch_destroy", "cn_batch_offsets",
            "cn_batch_step", "cn_batch_status", "cn_plan_create_levels", "cn_step_states", "cn_plan_fill_workspace",
            "cn_batch_fill_workspace", "cn_slab_create", "cn_slab_range", "cn_slab_reduce", "cn_slab_finish",
-           "cn_cuda_error_string", "cn_debug_report", "cn_debug_selftest")
+           "cn_cuda_error_string", "cn_debug_report", "cn_debug_selftest", "cn_plan_set_wait_limit")
 SLAB_MAX = 65536
 SLAB_SHARE = 6  # complex values one slab contributes to the joint-line system per step
 NOALLOC_MAX_N = 1048576
@@ -47,7 +48,7 @@ MAX_LEVELS = 24
 # block, block of the deeper levels) per arithmetic.
 LARGE_GRID_BLOCKS = {ARITH_F64: (24, 8, 8), ARITH_DF64: (13, 10, 16)}
 PROFILE_CLASSES = ("reduce_level0", "substitute_level0", "reduce_levels_ge1", "substitute_levels_ge1", "rs_stage",
-                   "fused_level0")
+                   "fused_level0", "levels_persistent")
 
 
 class CNError(RuntimeError):
@@ -141,6 +142,7 @@ def load(build_if_missing: bool = True):
             lib.cn_batch_step.argtypes = [vp, vp, vp, vp, i64, vp]
             lib.cn_batch_status.argtypes = [vp]
             lib.cn_plan_fill_workspace.argtypes = [vp, C.c_int32]
+            lib.cn_plan_set_wait_limit.argtypes = [vp, i64, C.c_int32]
             lib.cn_slab_create.argtypes = [C.POINTER(_Desc), C.c_int32, C.c_int32, vp, C.POINTER(vp)]
             lib.cn_slab_range.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
             lib.cn_slab_reduce.argtypes = [vp, vp, vp, vp, vp]
@@ -148,7 +150,7 @@ def load(build_if_missing: bool = True):
             lib.cn_batch_fill_workspace.argtypes = [vp, C.c_int32]
             for f in ("cn_batch_create", "cn_batch_destroy", "cn_batch_offsets", "cn_batch_step", "cn_batch_status",
                       "cn_plan_fill_workspace", "cn_batch_fill_workspace", "cn_slab_create", "cn_slab_range",
-                      "cn_slab_reduce", "cn_slab_finish"):
+                      "cn_slab_reduce", "cn_slab_finish", "cn_plan_set_wait_limit"):
                 getattr(lib, f).restype = C.c_int
             for f in ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_solve_tridiag",
                       "cn_plan_status", "cn_plan_query", "cn_plan_profile", "cn_plan_profile_read"):
@@ -337,6 +339,12 @@ class Plan:
     def status(self) -> int:
         """Synchronise and return (then clear) the device-side status code."""
         return int(self._lib.cn_plan_status(self._h))
+
+    def set_wait_limit(self, timeout_ns: int, missing_ctas: int = 0) -> None:
+        """Time limit of the persistent launch's grid barriers; missing_ctas > 0 is a
+        test hook that makes every barrier run out (cn_plan_set_wait_limit)."""
+        _check(self._lib.cn_plan_set_wait_limit(self._h, int(timeout_ns), int(missing_ctas)),
+               "cn_plan_set_wait_limit")
 
     def fill_workspace(self, byte: int = 0xFF) -> None:
         """Fill every scratch buffer of the plan with `byte` (cn_plan_fill_workspace)."""

@@ -89,6 +89,13 @@ struct Engine {
     int nslabs = 1, slab_rank = 0;
     int64_t slab_lo = 0, slab_hi = 0;
     double2* joint_work = nullptr;  // 2 (nslabs + 1): forward-sweep scratch, then the joint values
+    // levels >= 1 in one persistent cooperative launch (k_levels)
+    bool persistent = false;
+    unsigned int* pbar = nullptr;   // grid barrier words {arrivals, generation}
+    int p_grid = 0;                 // CTAs of the launch (all resident)
+    size_t p_smem = 0;              // dynamic shared memory of the launch
+    long long wait_ns = 2000000000ll;  // a grid barrier gives up after this long
+    unsigned int wait_missing = 0;  // test hook: CTAs a barrier waits for beyond the grid
 };
 
 struct cn_plan_s : Engine {};
@@ -135,7 +142,8 @@ cn_status validate_desc(const cn_desc* d, bool need_n) {
     if (d->level_block != 0 && (d->level_block < 3 || d->level_block > kMaxBlockRows)) return CN_ERR_INVALID_ARG;
     if (d->level1_block != 0 && (d->level1_block < 3 || d->level1_block > kMaxBlockRows)) return CN_ERR_INVALID_ARG;
     if (d->arith != CN_ARITH_F64 && d->arith != CN_ARITH_DF64) return CN_ERR_INVALID_ARG;
-    if ((d->flags & ~(CN_FLAG_COEFF_TABLE | CN_FLAG_RECOMPUTE)) != 0) return CN_ERR_INVALID_ARG;
+    if ((d->flags & ~(CN_FLAG_COEFF_TABLE | CN_FLAG_RECOMPUTE | CN_FLAG_LEVEL_LAUNCHES)) != 0)
+        return CN_ERR_INVALID_ARG;
     return CN_OK;
 }
 
@@ -162,6 +170,7 @@ void free_engine(Engine* p) {
     cudaFree(p->mu);
     cudaFree(p->part);
     cudaFree(p->joint_work);
+    cudaFree(p->pbar);
 }
 
 // --------------------------------------------------------------- debug build: bounds registry
@@ -206,6 +215,7 @@ void dbg_engine(const Engine* p, DbgList& L) {
     L.add(p->h_out, sizeof(double2) * (size_t)p->desc.n);
     L.add(p->h_E, sizeof(double) * (size_t)p->h_E_cap);
     L.add(p->joint_work, 2 * sizeof(double2) * ((size_t)p->nslabs + 1));
+    L.add(p->pbar, 2 * sizeof(unsigned int));
     if (p->desc.pot == CN_POT_ARRAY) L.add(p->desc.V0, sizeof(double) * (size_t)rows0);
 }
 
@@ -241,7 +251,8 @@ cudaError_t dbg_register(const Engine* p, cudaStream_t st, std::initializer_list
 }
 
 // --------------------------------------------------------------- kernel timing
-enum { kProfReduce0 = 0, kProfSubst0 = 1, kProfReduceL = 2, kProfSubstL = 3, kProfBase = 4, kProfFused0 = 5 };
+enum { kProfReduce0 = 0, kProfSubst0 = 1, kProfReduceL = 2, kProfSubstL = 3, kProfBase = 4, kProfFused0 = 5,
+       kProfLevels = 6 };
 
 // Two events per record; the pool grows on demand and is reused after a read.
 bool reserve_events(Engine* p, size_t k) {
@@ -540,6 +551,44 @@ cudaError_t set_smem_limits(const Engine* p) {
     return set_smem_limits_map<R, OneSys, OneGrid>(m0, ml);
 }
 
+// The persistent launch of the levels below level 0 (k_levels) serves a single
+// system of the default hierarchy (reduced to <= 1024 rows, cyclic-reduction RS
+// stage) unless CN_FLAG_LEVEL_LAUNCHES asks for one launch per stage and level:
+// its shared memory holds the RS stage's arrays and as many groups' substitution
+// staging as fit, one CTA per multiprocessor (512 threads, <= 128 registers).
+template <class R>
+cudaError_t setup_persistent(Engine* p) {
+    p->persistent = false;
+    if (p->batched || p->slab || !p->lvl_m.empty() || (p->desc.flags & CN_FLAG_LEVEL_LAUNCHES) || p->lv.size() < 3)
+        return cudaSuccess;
+    size_t smem = cr_smem();
+    for (size_t l = 1; l + 1 < p->lv.size(); ++l) {
+        if (p->lv[l].m > kSmemRowsMax) return cudaSuccess;
+        smem = std::max(smem, kPGroups * subst_smem(p->lv[l].m));
+    }
+    const size_t cap = 200 * 1024;  // leaves room for the kernel's static exchange arrays
+    smem = std::min(smem, cap);
+    for (size_t l = 1; l + 1 < p->lv.size(); ++l)
+        if (subst_smem(p->lv[l].m) > smem) return cudaSuccess;
+    cudaError_t e = raise_smem_limit(k_levels<R>, smem);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levels<R>, kPThreads, smem);
+    if (e != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return cudaSuccess;  // not resident: keep the per-level launches
+    }
+    if (!p->pbar) {
+        e = cudaMalloc(&p->pbar, 2 * sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemset(p->pbar, 0, 2 * sizeof(unsigned int));
+        if (e != cudaSuccess) return e;
+        p->workspace_bytes += 2 * sizeof(unsigned int);
+    }
+    p->p_smem = smem;
+    p->p_grid = per_sm * p->sms;
+    p->persistent = true;
+    return cudaSuccess;
+}
+
 // Levels >= 1 of the nested solve: reductions down (reduce_levels), the RS
 // stage (rs_stage), substitutions up (substitute_levels).
 template <class R>
@@ -601,8 +650,53 @@ cudaError_t substitute_levels(Engine* p, cudaStream_t st) {
     return e;
 }
 
+// All stages below level 0 in one cooperative launch of k_levels.
+template <class R>
+cudaError_t persistent_levels(Engine* p, cudaStream_t st) {
+    ProfScope ps(p, kProfLevels, st);
+    PLevels<R> a;
+    std::memset(&a, 0, sizeof(a));
+    const size_t L = p->lv.size();  // levels 0 .. L-1; L-1 is the RS level
+    a.nl = (int)L - 2;
+    for (int l = 1; l <= a.nl; ++l) {
+        const LevelData& Lv = p->lv[(size_t)l];
+        const LevelData& N = p->lv[(size_t)l + 1];
+        PLevel<R>& q = a.lv[l - 1];
+        q.src = level_source<R>(Lv);
+        q.sys = OneSys{Lv.sys[0]};
+        q.next = OneSys{N.sys[0]};
+        q.m = Lv.m;
+        q.m_next = N.m;
+        q.sub_groups = (int)std::min<size_t>(kPGroups, p->p_smem / subst_smem(Lv.m));
+        q.out = planes_of<R>(N);
+        q.out_slot = slot_of<R>(N);
+        q.x = x_of<R>(Lv);
+        q.x_next = x_of<R>(N);
+        q.ranges = (int64_t)grid_for(Lv.total);
+    }
+    const LevelData& B = p->lv[L - 1];
+    a.base = level_source<R>(B).bind(B.sys[0]);
+    a.base_x = x_of<R>(B);
+    a.status = p->status;
+    a.bar = p->pbar;
+    a.expect = (unsigned)p->p_grid + p->wait_missing;
+    a.timeout_ns = p->wait_ns;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)p->p_grid);
+    cfg.blockDim = dim3(kPThreads);
+    cfg.dynamicSmemBytes = p->p_smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_levels<R>, a);
+}
+
 template <class R>
 cudaError_t solve_levels(Engine* p, cudaStream_t st) {
+    if (p->persistent) return persistent_levels<R>(p, st);
     cudaError_t e = reduce_levels<R>(p, st);
     if (e == cudaSuccess) e = rs_stage<R>(p, st);
     if (e == cudaSuccess) e = substitute_levels<R>(p, st);
@@ -714,14 +808,13 @@ cudaError_t cn_solve(Engine* p, const CNStep& s, double2* x, cudaStream_t st) {
     return e;
 }
 
-// Whether consecutive steps pass psi on chip (double-float store mode with the
-// block staged in shared memory): step k's substitution and step k + 1's level-0
-// reduction then run as one kernel, and only the last step writes psi.  The
-// binary64 kernels are bound by the FP64 pipe, where the fused kernel gains
-// nothing from the saved traffic (measured 2 % slower), so they stay apart.
-bool fuses_steps(const Engine* p) {
-    return p->keep != nullptr && p->lv[0].m <= kSmemRowsMax && p->desc.arith == CN_ARITH_DF64;
-}
+// Whether consecutive steps pass psi on chip (store mode with the block staged
+// in shared memory): step k's substitution and step k + 1's level-0 reduction
+// then run as one kernel, and only the last step writes psi.  In binary64 too:
+// at N = 2^24 with blocks of 24 the fused kernel took 1.23 ms per step where the
+// two level-0 kernels took 1.01 + 0.37 ms (the substitution's latency hides
+// behind the reduction's FP64 work of the other warps).
+bool fuses_steps(const Engine* p) { return p->keep != nullptr && p->lv[0].m <= kSmemRowsMax; }
 
 // nsteps CN steps from in; the result goes to out, or with states != NULL every
 // step's result to states + k rows (k = 0 .. nsteps-1; in must not lie in states).
@@ -899,6 +992,7 @@ cn_status create_engine(Engine* p, const cn_desc* desc, const std::vector<int64_
         for (int k = 0; k < ncos; ++k) c.cos_a[k] = p->cos_a[(size_t)k];
     }
     if (e == cudaSuccess) e = df_mode ? set_smem_limits<df>(p) : set_smem_limits<double>(p);
+    if (e == cudaSuccess) e = df_mode ? setup_persistent<df>(p) : setup_persistent<double>(p);
     if (e != cudaSuccess) return alloc_status(e);
     return CN_OK;
 }
@@ -970,6 +1064,9 @@ cn_status read_status(Engine* p) {
     int h = 0;
     if (cudaMemcpy(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CN_ERR_CUDA;
     if (h != 0 && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) return CN_ERR_CUDA;
+    // a grid barrier that gave up leaves its words mid-count: start them afresh
+    if (h == CN_ERR_TIMEOUT && p->pbar && cudaMemset(p->pbar, 0, 2 * sizeof(unsigned int)) != cudaSuccess)
+        return CN_ERR_CUDA;
     return static_cast<cn_status>(h);
 }
 
@@ -1281,7 +1378,7 @@ cn_status cn_plan_query(cn_plan p, cn_plan_info* out) {
         out->level_rows[l] = p->lv[(size_t)l].sys[0].n;
         out->level_block[l] = (l < out->levels) ? p->lv[(size_t)l].m : 0;
     }
-    out->launches_per_step = 2 * out->levels + 1;
+    out->launches_per_step = p->persistent ? 3 : 2 * out->levels + 1;
     out->workspace_bytes = p->workspace_bytes;
     return CN_OK;
 }
@@ -1316,6 +1413,13 @@ cn_status cn_plan_status(cn_plan p) {
 cn_status cn_plan_fill_workspace(cn_plan p, int32_t byte) {
     if (!p) return CN_ERR_INVALID_ARG;
     return fill_workspace(p, byte);
+}
+
+cn_status cn_plan_set_wait_limit(cn_plan p, int64_t timeout_ns, int32_t missing_ctas) {
+    if (!p || timeout_ns <= 0 || missing_ctas < 0) return CN_ERR_INVALID_ARG;
+    p->wait_ns = timeout_ns;
+    p->wait_missing = (unsigned)missing_ctas;
+    return CN_OK;
 }
 
 // ------------------------------------------------------------------ slabs of a sharded grid

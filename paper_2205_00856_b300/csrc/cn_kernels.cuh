@@ -257,22 +257,27 @@ template <class R> struct RowSink {
 // the first kThreads * sizeof(JDPart) bytes of `scratch` (the caller's dynamic
 // shared memory, free once every thread is past this call's first barrier)
 // instead of a static array, so the kernel holds no shared memory beside its tile.
-template <class R, bool kAlias = false>
-__device__ __forceinline__ void write_reduced_row(bool active, int64_t t, int64_t P, JDPart<R> jd, cx<R> A0, cx<R> D0,
-                                                  cx<R> JUa, cx<R> JUc, cx<R> JUd, cx<R> Ag, cx<R> Dg,
-                                                  const RowSink<R>& out, LevelSlot<R>* out_slot,
-                                                  void* scratch = nullptr) {
-    JDPart<R>* xch;
-    if constexpr (kAlias) {
-        __syncthreads();  // every thread is done with the scratch it held
-        xch = reinterpret_cast<JDPart<R>*>(scratch);
-    } else {
-        __shared__ JDPart<R> xch_static[kThreads];
-        xch = xch_static;
+// Barriers over the threads that share one exchange: the whole CTA, or one
+// group of kThreads threads (named barrier 1 + group) of a larger CTA.
+struct CtaSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct GroupSync {
+    int id;
+    __device__ __forceinline__ void operator()() const {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kThreads) : "memory");
     }
-    const int tid = threadIdx.x;
+};
+
+// The exchange of kThreads blocks that form the range `cta` of the level: xch is
+// their kThreads-entry exchange array, tid the block's index in the range.
+template <class R, class Sync>
+__device__ __forceinline__ void write_reduced_row_at(JDPart<R>* xch, int tid, int64_t cta, Sync sync, bool active,
+                                                     int64_t t, int64_t P, JDPart<R> jd, cx<R> A0, cx<R> D0,
+                                                     cx<R> JUa, cx<R> JUc, cx<R> JUd, cx<R> Ag, cx<R> Dg,
+                                                     const RowSink<R>& out, LevelSlot<R>* out_slot) {
     xch[tid] = jd;
-    __syncthreads();
+    sync();
     if (!active) return;
     if (tid > 0 && t > 0) {
         const JDPart<R> pj = xch[tid - 1];
@@ -290,17 +295,36 @@ __device__ __forceinline__ void write_reduced_row(bool active, int64_t t, int64_
         sstore(&s.b, jd.b);
         sstore(&s.a, jd.a);
         sstore(&s.d, jd.d);
-        dbg_st(&out_slot[blockIdx.x + 1], s);
+        dbg_st(&out_slot[cta + 1], s);
     }
+}
+
+template <class R, bool kAlias = false>
+__device__ __forceinline__ void write_reduced_row(bool active, int64_t t, int64_t P, JDPart<R> jd, cx<R> A0, cx<R> D0,
+                                                  cx<R> JUa, cx<R> JUc, cx<R> JUd, cx<R> Ag, cx<R> Dg,
+                                                  const RowSink<R>& out, LevelSlot<R>* out_slot,
+                                                  void* scratch = nullptr) {
+    JDPart<R>* xch;
+    if constexpr (kAlias) {
+        __syncthreads();  // every thread is done with the scratch it held
+        xch = reinterpret_cast<JDPart<R>*>(scratch);
+    } else {
+        __shared__ JDPart<R> xch_static[kThreads];
+        xch = xch_static;
+    }
+    write_reduced_row_at<R>(xch, threadIdx.x, blockIdx.x, CtaSync{}, active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg,
+                            out, out_slot);
 }
 
 // ------------------------------------------------------------------ generic reduction
 // One thread per block: RD + JD downwards with RU + JU accumulated on the way.
-template <class R, class Src, class Map>
-__global__ void __launch_bounds__(kThreads)
-k_reduce(Src src0, Map sys, Map next, int m, int m_next, LevelPlanes<R> out, LevelSlot<R>* out_slot, int* status) {
-    grid_dep_enter();
-    const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+// The blocks of range `cta` (kThreads consecutive blocks of the level, thread tid
+// taking block cta kThreads + tid), exchanging through xch with barrier sync.
+template <class R, class Src, class Map, class Sync>
+__device__ __forceinline__ void reduce_cta(int64_t cta, int tid, JDPart<R>* xch, Sync sync, Src src0, Map sys,
+                                           Map next, int m, int m_next, LevelPlanes<R> out, LevelSlot<R>* out_slot,
+                                           int* status) {
+    const int64_t g = cta * kThreads + tid;
     const bool active = g < sys.total();
     bool ok = true;
     cx<R> JUa = czero<R>(), JUc = czero<R>(), JUd = czero<R>(), A0 = czero<R>(), D0 = czero<R>();
@@ -364,9 +388,17 @@ k_reduce(Src src0, Map sys, Map next, int m, int m_next, LevelPlanes<R> out, Lev
         JUa = cmul(r0u, nb);
         JUd = cmul(r0u, nd);
     }
-    write_reduced_row<R>(active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg, RowSink<R>(out, next.at(si), m_next),
-                         out_slot);
+    write_reduced_row_at<R>(xch, tid, cta, sync, active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg,
+                            RowSink<R>(out, next.at(si), m_next), out_slot);
     if (!ok) flag_error(status, kStatusNonfinite);
+}
+
+template <class R, class Src, class Map>
+__global__ void __launch_bounds__(kThreads)
+k_reduce(Src src0, Map sys, Map next, int m, int m_next, LevelPlanes<R> out, LevelSlot<R>* out_slot, int* status) {
+    grid_dep_enter();
+    __shared__ JDPart<R> xch[kThreads];
+    reduce_cta<R>(blockIdx.x, threadIdx.x, xch, CtaSync{}, src0, sys, next, m, m_next, out, out_slot, status);
 }
 
 // ------------------------------------------------------------------ generic substitution
@@ -379,16 +411,14 @@ template <> __device__ __forceinline__ void put<double2, double>(double2* p, cx<
 template <> __device__ __forceinline__ void put<double2, df>(double2* p, cx<df> z) { store128(p, z); }
 template <> __device__ __forceinline__ void put<float4, df>(float4* p, cx<df> z) { sstore(p, z); }
 
+// The blocks of range `cta` (thread tid: block cta kThreads + tid); zs, cs: the
+// range's [m][kThreads] staging arrays in shared memory.
 template <class R, class Src, class Map, class XT>
-__global__ void __launch_bounds__(kThreads)
-k_substitute(Src src0, Map sys, Map next, int m, const typename Store<R>::T* x_next0, XT* x0, int* status) {
-    grid_dep_enter();
+__device__ __forceinline__ void substitute_cta(int64_t cta, int tid, typename Store<R>::T* zs,
+                                               typename Store<R>::T* cs, Src src0, Map sys, Map next, int m,
+                                               const typename Store<R>::T* x_next0, XT* x0, int* status) {
     typedef typename Store<R>::T ST;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    ST* zs = reinterpret_cast<ST*>(smem_raw);   // [m][kThreads]
-    ST* cs = zs + (size_t)m * kThreads;         // [m][kThreads]
-    const int tid = threadIdx.x;
-    const int64_t g = (int64_t)blockIdx.x * kThreads + tid;
+    const int64_t g = cta * kThreads + tid;
     if (g >= sys.total()) return;
     bool ok = true;
     const int si = sys.find(g);
@@ -426,6 +456,17 @@ k_substitute(Src src0, Map sys, Map next, int m, const typename Store<R>::T* x_n
     put<XT, R>(x + J0, xL);
     if (t == P - 1) put<XT, R>(x + J0 + gap, xR);
     if (!ok) flag_error(status, kStatusNonfinite);
+}
+
+template <class R, class Src, class Map, class XT>
+__global__ void __launch_bounds__(kThreads)
+k_substitute(Src src0, Map sys, Map next, int m, const typename Store<R>::T* x_next0, XT* x0, int* status) {
+    grid_dep_enter();
+    typedef typename Store<R>::T ST;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ST* zs = reinterpret_cast<ST*>(smem_raw);   // [m][kThreads]
+    ST* cs = zs + (size_t)m * kThreads;         // [m][kThreads]
+    substitute_cta<R>(blockIdx.x, threadIdx.x, zs, cs, src0, sys, next, m, x_next0, x0, status);
 }
 
 // Same substitution for blocks longer than the shared-memory staging allows:
@@ -931,6 +972,119 @@ k_base_cr_many(const BaseSys<R>* sys, int* status) {
     grid_dep_enter();
     const BaseSys<R> b = dbg_ld(&sys[blockIdx.x]);
     cr_solve<R>(b.src, b.x, status);
+}
+
+// ------------------------------------------------------------------ levels >= 1 in one persistent launch
+// Every stage below level 0 of one system -- the reductions of levels 1 .. L-2,
+// the RS stage and the substitutions back up -- in one cooperative launch: a
+// grid of CTAs that are all resident at once, each of kPGroups groups of
+// kThreads threads.  A stage's ranges of kThreads blocks (a level's "CTAs" of the
+// per-level kernels, with the same exchange and slots) are dealt to the groups,
+// ranges g, g + groups, ...; the groups of a CTA run independently (named
+// barriers) and stage through disjoint parts of the shared memory.  Stages are
+// separated by a grid barrier; the RS stage is CTA 0's cyclic reduction.  The
+// per-block arithmetic and its order are those of k_reduce / k_substitute /
+// k_base_cr, so the results are the same bits.
+constexpr int kPGroups = 4;
+constexpr int kPThreads = kPGroups * kThreads;  // 512 = kCrThreads
+static_assert(kPThreads == kCrThreads, "the RS stage runs on one persistent CTA");
+constexpr int kStatusTimeout = 5;  // cn_status CN_ERR_TIMEOUT
+
+template <class R> struct PLevel {
+    LevelSource<R> src;             // the level's rows, bound to the system
+    OneSys sys, next;               // entries of this level and of the next
+    int m, m_next;                  // block sizes of this level and of the next
+    int sub_groups;                 // groups per CTA that substitute at once (their staging must fit)
+    LevelPlanes<R> out;             // the next level's planes
+    LevelSlot<R>* out_slot;         // the next level's CTA slots
+    typename Store<R>::T* x;        // this level's solution
+    const typename Store<R>::T* x_next;  // the next level's solution
+    int64_t ranges;                 // ceil(P / kThreads)
+};
+template <class R> struct PLevels {
+    PLevel<R> lv[24];               // levels 1 .. nl (index l - 1)
+    int nl;                         // reduced levels below level 0 (the RS stage solves level nl + 1)
+    LevelSource<R> base;            // the RS level
+    typename Store<R>::T* base_x;
+    int* status;
+    unsigned int* bar;              // {arrivals, generation}: zero between launches
+    unsigned int expect;            // arrivals a barrier waits for (gridDim.x)
+    long long timeout_ns;           // a barrier gives up after this long
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch, bounded: the last CTA to arrive
+// resets the count and bumps the generation the others wait on; a CTA that has
+// waited timeout_ns gives up, records CN_ERR_TIMEOUT and returns false (then
+// every CTA leaves the kernel at its next barrier or its own time-out, and
+// cn_plan_status repairs the barrier words).  Every thread of every CTA calls it.
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int expect, long long timeout_ns,
+                                             int* status) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int* gen = bar + 1;
+        const unsigned int g0 = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) + 1u == expect) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*gen == g0) {
+                if ((long long)(global_ns() - t0) > timeout_ns) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    if (!ok_s) flag_error(status, kStatusTimeout);
+    return ok_s != 0;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kPThreads, 1) k_levels(const __grid_constant__ PLevels<R> a) {
+    grid_dep_enter();
+    typedef typename Store<R>::T ST;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ JDPart<R> xch[kPGroups][kThreads];
+    const int grp = threadIdx.x / kThreads, tid = threadIdx.x % kThreads;
+    const GroupSync gsync{1 + grp};
+    const int64_t slot0 = (int64_t)blockIdx.x * kPGroups + grp, stride = (int64_t)gridDim.x * kPGroups;
+    for (int l = 0; l < a.nl; ++l) {
+        const PLevel<R>& L = a.lv[l];
+        for (int64_t c = slot0; c < L.ranges; c += stride) {
+            reduce_cta<R>(c, tid, xch[grp], gsync, L.src, L.sys, L.next, L.m, L.m_next, L.out, L.out_slot,
+                          a.status);
+            gsync();  // the group's exchange array is free again
+        }
+        if (!grid_barrier(a.bar, a.expect, a.timeout_ns, a.status)) return;
+    }
+    if (blockIdx.x == 0) cr_solve<R>(a.base, a.base_x, a.status);
+    if (!grid_barrier(a.bar, a.expect, a.timeout_ns, a.status)) return;
+    for (int l = a.nl - 1; l >= 0; --l) {
+        const PLevel<R>& L = a.lv[l];
+        if (grp < L.sub_groups) {
+            ST* zs = reinterpret_cast<ST*>(smem_raw) + (size_t)grp * 2 * L.m * kThreads;
+            ST* cs = zs + (size_t)L.m * kThreads;
+            const int64_t s0 = (int64_t)blockIdx.x * L.sub_groups + grp, st = (int64_t)gridDim.x * L.sub_groups;
+            for (int64_t c = s0; c < L.ranges; c += st)
+                substitute_cta<R>(c, tid, zs, cs, L.src, L.sys, L.next, L.m, L.x_next, L.x, a.status);
+        }
+        if (l > 0 && !grid_barrier(a.bar, a.expect, a.timeout_ns, a.status)) return;
+    }
 }
 
 // ------------------------------------------------------------------ CN level 0

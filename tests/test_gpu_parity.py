@@ -119,13 +119,12 @@ def test_soft_coulomb_field_100_steps(n, block, arith, flags):
 @pytest.mark.parametrize("block", [3, 8, 12, 32])
 @pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
 def test_multi_step_call_matches_single_steps(arith, block, table):
-    # double-float: a cn_step of K steps runs each step's level-0 substitution fused
-    # with the next step's level-0 reduction (psi stays on chip, split joint-row
-    # stencils); K calls of one step round-trip psi through complex128 between the
-    # steps.  psi keeps its ~48-bit form instead of being rounded to binary64 and
-    # back, so the two agree to rounding.  Binary64 keeps the two kernels (its FP64
-    # pipe is the bound): the same launches either way, bitwise.  Both against the
-    # oracle as well.
+    # a cn_step of K steps runs each step's level-0 substitution fused with the
+    # next step's level-0 reduction (psi stays on chip, split joint-row stencils);
+    # K calls of one step round-trip psi through complex128 between the steps.  In
+    # double-float psi keeps its ~48-bit form instead of being rounded to binary64
+    # and back, so the two agree to rounding; in binary64 the value on chip is the
+    # one the single steps store and reload: bitwise.  Both against the oracle.
     cfg = W.soft_coulomb_config(n=20011, nsteps=24)
     psi0 = W.initial_state(cfg)
     E = W.field_midpoints(24, cfg["dt"], t0=60.0)
@@ -144,11 +143,10 @@ def test_multi_step_call_matches_single_steps(arith, block, table):
     plan.profile(False)
     plan.close()
     a, b = fused.cpu().numpy(), single.cpu().numpy()
+    assert prof["fused_level0"][1] == 23 and prof["reduce_level0"][1] == 1 and prof["substitute_level0"][1] == 1
     if arith == cnb.ARITH_F64:
-        assert prof["fused_level0"][1] == 0 and prof["reduce_level0"][1] == 24 and prof["substitute_level0"][1] == 24
-        assert np.array_equal(a, b)
+        assert np.array_equal(a, b)  # psi on chip is the binary64 value the single steps store and reload
     else:
-        assert prof["fused_level0"][1] == 23 and prof["reduce_level0"][1] == 1 and prof["substitute_level0"][1] == 1
         assert rel(a, b) <= 1e-13
     ref = oracle.cn_run(oracle_problem(cfg), psi0, 24, E_mid=E)
     assert rel(a, ref) <= 1e-11
@@ -228,7 +226,9 @@ def test_two_group_levels_vs_oracle(n, blocks, arith):
     cfg = W.soft_coulomb_config(n=n, nsteps=3)
     psi0 = W.gaussian(n, cfg["dx"], cfg["x_min"], 0.0, 0.05 * n * cfg["dx"], 0.8)  # amplitude on every level
     E = W.field_midpoints(3, cfg["dt"], t0=150.0)
-    plan = plan_for(cfg, block=m0, level1_block=m1, level_block=ml, arith=arith)
+    # one launch per stage and level: the two-group kernels (the persistent launch
+    # runs the one-thread-per-block code on every level)
+    plan = plan_for(cfg, block=m0, level1_block=m1, level_block=ml, arith=arith, flags=cnb.FLAG_LEVEL_LAUNCHES)
     rows = plan.info()["level_rows"]
     assert len(rows) >= 4 and rows[2] > 1024  # level 2 is reduced
     assert (rows[2] - 1) // ml <= 148 * 128  # ... by the two-group kernels
@@ -470,3 +470,64 @@ def test_plans_with_different_blocks_coexist():
             assert rel(out, ref) <= 1e-11
         big.close()
         small.close()
+
+
+@pytest.mark.parametrize("n,blocks", [(20011, (8, 8, 8)), (200001, (8, 8, 8)), (1000003, (13, 10, 12)),
+                                      (400009, (4, 4, 3)), (1 << 22, None)])
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+def test_persistent_levels_match_per_level_launches_bitwise(n, blocks, arith):
+    """Every stage below level 0 in one persistent cooperative launch gives the
+    bits of one launch per stage and level (same per-block arithmetic, same
+    order), in multi-step calls and single steps, and matches the oracle."""
+    m0, m1, ml = cnb.LARGE_GRID_BLOCKS[arith] if blocks is None else blocks
+    cfg = W.soft_coulomb_config(n=n, nsteps=4)
+    psi0 = W.full_support_state(n, cfg["dx"], cfg["x_min"], seed=7)
+    E = to_dev(W.field_midpoints(4, cfg["dt"], t0=90.0))
+    kw = dict(arith=arith, block=m0, level1_block=m1, level_block=ml, flags=cnb.FLAG_COEFF_TABLE)
+    pers = plan_for(cfg, **kw)
+    per_level = plan_for(cfg, **{**kw, "flags": cnb.FLAG_COEFF_TABLE | cnb.FLAG_LEVEL_LAUNCHES})
+    assert pers.info()["launches_per_step"] == 3
+    assert per_level.info()["launches_per_step"] == 2 * per_level.info()["levels"] + 1
+    pers.profile(True)
+    pers.profile_read()
+    a = pers.step(to_dev(psi0), 4, E_mid=E).cpu().numpy()
+    prof = pers.profile_read()
+    pers.profile(False)
+    assert prof["levels_persistent"][1] == 4 and prof["reduce_levels_ge1"][1] == 0 and prof["rs_stage"][1] == 0
+    b = per_level.step(to_dev(psi0), 4, E_mid=E).cpu().numpy()
+    one = to_dev(psi0)
+    for k in range(2):
+        pers.step(one, 1, E_mid=E[k:k + 1], psi_out=one)
+    one2 = to_dev(psi0)
+    for k in range(2):
+        per_level.step(one2, 1, E_mid=E[k:k + 1], psi_out=one2)
+    pers.check()
+    per_level.check()
+    assert np.array_equal(a, b)
+    assert np.array_equal(one.cpu().numpy(), one2.cpu().numpy())
+    if n <= 1000003:
+        ref = oracle.cn_run(oracle_problem(cfg), psi0, 4, E_mid=E.cpu().numpy())
+        assert rel(a, ref) <= 1e-11
+    pers.close()
+    per_level.close()
+
+
+def test_persistent_barrier_times_out_and_recovers():
+    """The grid barriers of the persistent launch are bounded: with a barrier told
+    to wait for one CTA that never arrives, every barrier gives up after the
+    limit, the step reports CN_ERR_TIMEOUT through the plan status and the context
+    stays usable; with the limit restored the next steps are correct again."""
+    cfg = W.soft_coulomb_config(n=200001, nsteps=2)
+    psi0 = W.initial_state(cfg)
+    E = W.field_midpoints(2, cfg["dt"], t0=30.0)
+    plan = plan_for(cfg)
+    assert plan.info()["launches_per_step"] == 3
+    plan.set_wait_limit(50_000_000, missing_ctas=1)  # 50 ms
+    plan.step(to_dev(psi0), 2, E_mid=to_dev(E))
+    assert plan.status() == 5  # CN_ERR_TIMEOUT
+    assert plan.status() == 0  # read and cleared
+    plan.set_wait_limit(2_000_000_000, missing_ctas=0)
+    out = plan.step(to_dev(psi0), 2, E_mid=to_dev(E)).cpu().numpy()
+    plan.check()
+    plan.close()
+    assert rel(out, oracle.cn_run(oracle_problem(cfg), psi0, 2, E_mid=E)) <= 1e-11
