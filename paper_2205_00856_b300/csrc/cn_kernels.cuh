@@ -1062,7 +1062,9 @@ __global__ void __launch_bounds__(kPThreads, 1) k_levels(const __grid_constant__
     __shared__ JDPart<R> xch[kPGroups][kThreads];
     const int grp = threadIdx.x / kThreads, tid = threadIdx.x % kThreads;
     const GroupSync gsync{1 + grp};
-    const int64_t slot0 = (int64_t)blockIdx.x * kPGroups + grp, stride = (int64_t)gridDim.x * kPGroups;
+    // ranges go to the CTAs first (range c to CTA c mod grid, group c / grid): a
+    // small level spreads over as many multiprocessors as it has ranges
+    const int64_t slot0 = (int64_t)grp * gridDim.x + blockIdx.x, stride = (int64_t)gridDim.x * kPGroups;
     for (int l = 0; l < a.nl; ++l) {
         const PLevel<R>& L = a.lv[l];
         for (int64_t c = slot0; c < L.ranges; c += stride) {
@@ -1079,7 +1081,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_levels(const __grid_constant__
         if (grp < L.sub_groups) {
             ST* zs = reinterpret_cast<ST*>(smem_raw) + (size_t)grp * 2 * L.m * kThreads;
             ST* cs = zs + (size_t)L.m * kThreads;
-            const int64_t s0 = (int64_t)blockIdx.x * L.sub_groups + grp, st = (int64_t)gridDim.x * L.sub_groups;
+            const int64_t s0 = (int64_t)grp * gridDim.x + blockIdx.x, st = (int64_t)gridDim.x * L.sub_groups;
             for (int64_t c = s0; c < L.ranges; c += st)
                 substitute_cta<R>(c, tid, zs, cs, L.src, L.sys, L.next, L.m, L.x_next, L.x, a.status);
         }
