@@ -100,9 +100,10 @@ def ops_per_row(kernel: str, m: int, table: bool = False) -> float:
 
 STEP_BYTES_PER_ROW = 32.0   # read psi_n, write psi_n+1
 TABLE_BYTES_PER_ROW = {"f64": 16.0, "df64": 8.0}  # the tabulated coefficients read per row
-# FP64 pipe throughput of this machine's B300, measured by a probe of independent
-# DFMA / DADD / DMUL chains (all SMs, CUDA events, best of 5; profiles/fp64_pipe_b300.md):
-# operations per second of the whole GPU.
+# FP64 pipe throughput: measured live at the start of the run by the library's
+# calibration kernels (cn_measure_fp64_rate: independent binary64 FMA chains on every
+# multiprocessor, the best of five CUDA-event timings), operations per second of the
+# whole GPU; the value committed in profiles/fp64_pipe_b300.md is the same measurement.
 FP64_MEASURED_OPS = None
 FP64_PEAK_SOURCE = "not measured"
 
@@ -806,6 +807,12 @@ def main():
         # a rank that dies makes the others' next collective fail after this long
         # instead of waiting for ever
         dist.init_process_group("nccl", device_id=dev, timeout=datetime.timedelta(seconds=PG_TIMEOUT_S))
+
+    global FP64_MEASURED_OPS, FP64_PEAK_SOURCE
+    fma_rate, add_rate = cnb.fp64_rate()
+    FP64_MEASURED_OPS = fma_rate
+    FP64_PEAK_SOURCE = (f"measured in this run: binary64 FMA chains on all {sms} SMs, {fma_rate:.4g} op/s "
+                        f"(additions: {add_rate:.4g} op/s; cn_measure_fp64_rate)")
 
     if args.largest:
         if rank == 0:

@@ -110,10 +110,14 @@ typedef struct {
  * both from psi instead, and the plan holds one n-point state buffer (16 B per
  * point) for the step ping-pong -- for grids whose 32 B per point do not fit. */
 #define CN_FLAG_RECOMPUTE 2
-/* cn_desc.flags: run every stage below level 0 as its own launch (one per stage
- * and level) instead of the default single persistent launch (see
- * cn_plan_create). */
+/* cn_desc.flags: how the stages below level 0 are launched (see cn_plan_create):
+ * one launch per stage and level (CN_FLAG_LEVEL_LAUNCHES) or all of them in one
+ * persistent launch (CN_FLAG_PERSISTENT_LEVELS); not both.  Without either the
+ * library picks per arithmetic the faster one on B300: the persistent launch for
+ * CN_ARITH_F64, one launch per stage and level for CN_ARITH_DF64.  The results
+ * are the same bits either way. */
 #define CN_FLAG_LEVEL_LAUNCHES 4
+#define CN_FLAG_PERSISTENT_LEVELS 8
 
 /* Create a plan for systems of size desc->n.  The N-shaped solve is nested
  * (Eq. iteration): level 0 is cut into blocks of desc->block rows, level 1 into
@@ -121,12 +125,14 @@ typedef struct {
  * blocks of desc->level_block rows, until a level has at most 1024
  * rows; that system (the RS stage) is solved inside one CTA by cyclic
  * reduction.  The stages below level 0 -- the reductions of levels 1 .. L-1,
- * the RS stage and the substitutions back up -- run in ONE persistent
- * cooperative launch (all its CTAs resident at once, one per multiprocessor,
- * stages separated by grid-wide barriers bounded by a time limit: a barrier
- * that gives up records CN_ERR_TIMEOUT, see cn_plan_set_wait_limit), unless
- * desc->flags has CN_FLAG_LEVEL_LAUNCHES or the kernel cannot be resident;
- * either way the results are the same bits.  Allocates the device workspace on the current device: the
+ * the RS stage and the substitutions back up -- run either as one launch per
+ * stage and level or in ONE persistent cooperative launch (all its CTAs
+ * resident at once, one per multiprocessor, stages separated by grid-wide
+ * barriers bounded by a time limit: a barrier that gives up records
+ * CN_ERR_TIMEOUT, see cn_plan_set_wait_limit), chosen by CN_FLAG_LEVEL_LAUNCHES /
+ * CN_FLAG_PERSISTENT_LEVELS or per arithmetic; the persistent launch serves
+ * single systems of this default hierarchy whose kernel can be resident, else
+ * the per-level launches run.  Either way the results are the same bits.  Allocates the device workspace on the current device: the
  * reduced systems of every level (~80 B per row of level 1 and below), 32 B
  * per grid point of kept right-hand sides and pivots (16 B of state buffer
  * instead with CN_FLAG_RECOMPUTE), the optional coefficient table, a status
@@ -416,6 +422,13 @@ const char* cn_version(void);
  * calling host thread turned into CN_ERR_CUDA or CN_ERR_OOM; "cudaSuccess" if
  * none.  The string is static. */
 const char* cn_cuda_error_string(void);
+
+/* Throughput of the current device's FP64 pipe, the denominator of the binary64
+ * path's ALU roofline: independent chains of binary64 FMAs (*fma_per_s) and of
+ * binary64 additions (*add_per_s) on every multiprocessor, in operations per
+ * second of the whole device (best of five CUDA-event timings, about 20 ms of
+ * GPU time).  Synchronises the device; allocates and frees a small buffer. */
+cn_status cn_measure_fp64_rate(double* fma_per_s, double* add_per_s);
 
 /* ---- The CN_DEBUG build (libcn_b300_debug.so; the stand-in for a memory
  * sanitizer).  Every global-memory load and store of the kernels is checked

@@ -25,6 +25,7 @@ ARITH_F64, ARITH_DF64 = 0, 1
 FLAG_COEFF_TABLE = 1
 FLAG_RECOMPUTE = 2
 FLAG_LEVEL_LAUNCHES = 4
+FLAG_PERSISTENT_LEVELS = 8
 
 _STATUS = {0: "CN_OK", 1: "CN_ERR_INVALID_ARG", 2: "CN_ERR_UNSUPPORTED", 3: "CN_ERR_OOM", 4: "CN_ERR_CUDA",
            5: "CN_ERR_TIMEOUT", 6: "CN_ERR_NONFINITE", 7: "CN_ERR_BOUNDS"}
@@ -36,7 +37,8 @@ EXPORTS = ("cn_plan_create", "cn_plan_destroy", "cn_step", "cn_step_host", "cn_s
            "cn_field_grad_to_controls", "cn_batch_create", "cn_batch_destroy", "cn_batch_offsets",
            "cn_batch_step", "cn_batch_status", "cn_plan_create_levels", "cn_step_states", "cn_plan_fill_workspace",
            "cn_batch_fill_workspace", "cn_slab_create", "cn_slab_range", "cn_slab_reduce", "cn_slab_finish",
-           "cn_cuda_error_string", "cn_debug_report", "cn_debug_selftest", "cn_plan_set_wait_limit")
+           "cn_cuda_error_string", "cn_debug_report", "cn_debug_selftest", "cn_plan_set_wait_limit",
+           "cn_measure_fp64_rate")
 SLAB_MAX = 65536
 SLAB_SHARE = 6  # complex values one slab contributes to the joint-line system per step
 NOALLOC_MAX_N = 1048576
@@ -46,7 +48,7 @@ MAX_LEVELS = 24
 # Launch configuration for large single systems (N ~ 2^24, coefficient table on),
 # from block-size sweeps of the soft-Coulomb step on B300: (level-0 block, level-1
 # block, block of the deeper levels) per arithmetic.
-LARGE_GRID_BLOCKS = {ARITH_F64: (24, 8, 8), ARITH_DF64: (13, 10, 16)}
+LARGE_GRID_BLOCKS = {ARITH_F64: (32, 16, 8), ARITH_DF64: (13, 10, 16)}
 PROFILE_CLASSES = ("reduce_level0", "substitute_level0", "reduce_levels_ge1", "substitute_levels_ge1", "rs_stage",
                    "fused_level0", "levels_persistent")
 
@@ -134,6 +136,8 @@ def load(build_if_missing: bool = True):
             lib.cn_debug_report.restype = C.c_int
             lib.cn_debug_selftest.argtypes = []
             lib.cn_debug_selftest.restype = C.c_int
+            lib.cn_measure_fp64_rate.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            lib.cn_measure_fp64_rate.restype = C.c_int
             lib.cn_plan_create_levels.argtypes = [C.POINTER(_Desc), C.c_int32, vp, C.POINTER(vp)]
             lib.cn_plan_create_levels.restype = C.c_int
             lib.cn_batch_create.argtypes = [C.POINTER(_Desc), i64, vp, vp, vp, C.POINTER(vp)]
@@ -593,6 +597,14 @@ def field_grad_to_controls(dLdE, t_final: float, t0: float, dt: float, n_control
 
 def version() -> str:
     return load().cn_version().decode()
+
+
+def fp64_rate():
+    """Measured throughput of the device's FP64 pipe: (binary64 FMAs per second,
+    binary64 additions per second) of the whole device (cn_measure_fp64_rate)."""
+    f, a = C.c_double(), C.c_double()
+    _check(load().cn_measure_fp64_rate(C.byref(f), C.byref(a)), "cn_measure_fp64_rate")
+    return float(f.value), float(a.value)
 
 
 def debug_report():

@@ -17,7 +17,7 @@ LIB = os.path.join(PKG, "libcn_b300.so")
 DEBUG_LIB = os.path.join(PKG, "libcn_b300_debug.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
-SOURCES = [os.path.join(CSRC, "cn_api.cu"), os.path.join(CSRC, "cn_noalloc.cu")]
+SOURCES = [os.path.join(CSRC, "cn_api.cu"), os.path.join(CSRC, "cn_noalloc.cu"), os.path.join(CSRC, "cn_probe.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(ROOT, "include", "cn.h")]
 

@@ -142,8 +142,9 @@ cn_status validate_desc(const cn_desc* d, bool need_n) {
     if (d->level_block != 0 && (d->level_block < 3 || d->level_block > kMaxBlockRows)) return CN_ERR_INVALID_ARG;
     if (d->level1_block != 0 && (d->level1_block < 3 || d->level1_block > kMaxBlockRows)) return CN_ERR_INVALID_ARG;
     if (d->arith != CN_ARITH_F64 && d->arith != CN_ARITH_DF64) return CN_ERR_INVALID_ARG;
-    if ((d->flags & ~(CN_FLAG_COEFF_TABLE | CN_FLAG_RECOMPUTE | CN_FLAG_LEVEL_LAUNCHES)) != 0)
+    if ((d->flags & ~(CN_FLAG_COEFF_TABLE | CN_FLAG_RECOMPUTE | CN_FLAG_LEVEL_LAUNCHES | CN_FLAG_PERSISTENT_LEVELS)) != 0)
         return CN_ERR_INVALID_ARG;
+    if ((d->flags & CN_FLAG_LEVEL_LAUNCHES) && (d->flags & CN_FLAG_PERSISTENT_LEVELS)) return CN_ERR_INVALID_ARG;
     return CN_OK;
 }
 
@@ -559,8 +560,14 @@ cudaError_t set_smem_limits(const Engine* p) {
 template <class R>
 cudaError_t setup_persistent(Engine* p) {
     p->persistent = false;
-    if (p->batched || p->slab || !p->lvl_m.empty() || (p->desc.flags & CN_FLAG_LEVEL_LAUNCHES) || p->lv.size() < 3)
-        return cudaSuccess;
+    // the default per arithmetic, from N = 2^24 measurements on B300: binary64
+    // 1.515 (persistent) vs 1.520 ms per step (blocks 32 / 16 / 8), double-float
+    // 0.460 vs 0.446 ms (blocks 13 / 10 / 16: the two-group kernels of levels 2
+    // and 3 and the programmatic launch overlap outweigh the saved launches)
+    const int fl = p->desc.flags;
+    const bool want = (fl & CN_FLAG_PERSISTENT_LEVELS) ||
+                      (!(fl & CN_FLAG_LEVEL_LAUNCHES) && p->desc.arith == CN_ARITH_F64);
+    if (!want || p->batched || p->slab || !p->lvl_m.empty() || p->lv.size() < 3) return cudaSuccess;
     size_t smem = cr_smem();
     for (size_t l = 1; l + 1 < p->lv.size(); ++l) {
         if (p->lv[l].m > kSmemRowsMax) return cudaSuccess;

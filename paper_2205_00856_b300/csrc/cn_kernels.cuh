@@ -431,21 +431,25 @@ __device__ __forceinline__ void substitute_cta(int64_t cta, int tid, typename St
     const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
     const cx<R> xL = sload(x_next + t);
     const cx<R> xR = sload(x_next + t + 1);
-    cx<R> zp = czero<R>(), cpp = czero<R>();
+    // m_k = a_k - b_k c'_{k-1};  z_k = (d_k - b_k z_{k-1}) / m_k;  c'_k = c_k / m_k,
+    // from z_0 = xL and c'_0 = 0 (row 0 is the support value), so row 1 needs no
+    // special case; row g-1 also subtracts c_{g-1} xR (peeled: a condition in the
+    // loop would be evaluated as arithmetic on every row)
+    cx<R> zp = xL, cpp = czero<R>();
     Row<R> nxt = src.template row<R>(t, 1, J0 + 1);
-    for (int k = 1; k < gap; ++k) {
+    for (int k = 1; k < gap - 1; ++k) {
         const Row<R> rk = nxt;
-        if (k + 1 < gap) nxt = src.template row<R>(t, k + 1, J0 + k + 1);
-        cx<R> rhs = rk.d;
-        if (k == 1) rhs = csub(rhs, cmul(rk.b, xL));
-        if (k == gap - 1) rhs = csub(rhs, cmul(rk.c, xR));
-        // m_k = a_k - b_k c'_{k-1};  z_k = (rhs_k - b_k z_{k-1}) / m_k;  c'_k = c_k / m_k
-        const cx<R> piv = (k == 1) ? rk.a : csub(rk.a, cmul(rk.b, cpp));
-        const cx<R> w = crcp(piv, ok);
-        zp = (k == 1) ? cmul(rhs, w) : cmul(csub(rhs, cmul(rk.b, zp)), w);
+        nxt = src.template row<R>(t, k + 1, J0 + k + 1);
+        const cx<R> w = crcp(csub(rk.a, cmul(rk.b, cpp)), ok);
+        zp = cmul(csub(rk.d, cmul(rk.b, zp)), w);
         cpp = cmul(rk.c, w);
         sstore(zs + k * kThreads + tid, zp);
         sstore(cs + k * kThreads + tid, cpp);
+    }
+    {
+        const Row<R> rk = nxt;
+        const cx<R> w = crcp(csub(rk.a, cmul(rk.b, cpp)), ok);
+        zp = cmul(csub(csub(rk.d, cmul(rk.c, xR)), cmul(rk.b, zp)), w);
     }
     cx<R> y = zp;
     put<XT, R>(x + J0 + gap - 1, y);
@@ -493,18 +497,20 @@ k_substitute_gmem(Src src0, Map sys, Map next, int m, const typename Store<R>::T
     ST* zc = zc0 + 2 * (e.row_off + J0);
     const cx<R> xL = sload(x_next + t);
     const cx<R> xR = sload(x_next + t + 1);
-    cx<R> zp = czero<R>(), cpp = czero<R>();
-    for (int k = 1; k < gap; ++k) {
+    // as k_substitute: z_0 = xL, c'_0 = 0, row g-1 peeled
+    cx<R> zp = xL, cpp = czero<R>();
+    for (int k = 1; k < gap - 1; ++k) {
         const Row<R> rk = src.template row<R>(t, k, J0 + k);
-        cx<R> rhs = rk.d;
-        if (k == 1) rhs = csub(rhs, cmul(rk.b, xL));
-        if (k == gap - 1) rhs = csub(rhs, cmul(rk.c, xR));
-        const cx<R> piv = (k == 1) ? rk.a : csub(rk.a, cmul(rk.b, cpp));
-        const cx<R> w = crcp(piv, ok);
-        zp = (k == 1) ? cmul(rhs, w) : cmul(csub(rhs, cmul(rk.b, zp)), w);
+        const cx<R> w = crcp(csub(rk.a, cmul(rk.b, cpp)), ok);
+        zp = cmul(csub(rk.d, cmul(rk.b, zp)), w);
         cpp = cmul(rk.c, w);
         sstore(zc + 2 * k, zp);
         sstore(zc + 2 * k + 1, cpp);
+    }
+    {
+        const Row<R> rk = src.template row<R>(t, gap - 1, J0 + gap - 1);
+        const cx<R> w = crcp(csub(rk.a, cmul(rk.b, cpp)), ok);
+        zp = cmul(csub(csub(rk.d, cmul(rk.c, xR)), cmul(rk.b, zp)), w);
     }
     cx<R> y = zp;
     put<XT, R>(x + J0 + gap - 1, y);
@@ -765,8 +771,7 @@ k_substitute_ws(LevelSource<R> src0, Map sys, Map next, int m, const typename St
         cx<R> cpp = czero<R>();
         for (int k = 1; k < m; ++k) {
             if (active && k < gap) {
-                const cx<R> piv = (k == 1) ? S.a(k) : csub(S.a(k), cmul(S.b(k), cpp));
-                const cx<R> w = crcp(piv, ok);
+                const cx<R> w = crcp(csub(S.a(k), cmul(S.b(k), cpp)), ok);  // c'_0 = 0, as k_substitute
                 cpp = cmul(S.c(k), w);
                 sstore(sW + k * kWsLanes + lt, w);
                 sstore(sC + k * kWsLanes + lt, cpp);
@@ -783,15 +788,15 @@ k_substitute_ws(LevelSource<R> src0, Map sys, Map next, int m, const typename St
         xL = sload(x_next + t);
         xR = sload(x_next + t + 1);
     }
+    zp = xL;  // z_0 = xL, as k_substitute
     for (int k = 1; k < m; ++k) {
         bar_sync_id(k, 2 * kWsLanes);
         if (active && k < gap) {
             const cx<R> bk = S.b(k);
             cx<R> rhs = S.d(k);
-            if (k == 1) rhs = csub(rhs, cmul(bk, xL));
             if (k == gap - 1) rhs = csub(rhs, cmul(S.c(k), xR));
             const cx<R> w = sload(sW + k * kWsLanes + lt);
-            zp = (k == 1) ? cmul(rhs, w) : cmul(csub(rhs, cmul(bk, zp)), w);
+            zp = cmul(csub(rhs, cmul(bk, zp)), w);
             sstore(S.at(1, k), zp);
         }
     }
@@ -1194,11 +1199,14 @@ template <> struct CoefGen<double> {
             const double b0 =
                 p->pot == 1 ? fma(p->c1, dbg_ld(&V0[j]), 2.0) : fma(p->c1, static_potential_d(*p, j, x), 2.0);
             bt = fma(c1E, x, b0);
+            dj += 1.0;  // the counter is only needed without the table
         }
         ++j;
-        dj += 1.0;
     }
-    __device__ __forceinline__ void skip() { ++j; dj += 1.0; }
+    __device__ __forceinline__ void skip() {
+        ++j;
+        if (!tab) dj += 1.0;
+    }
 };
 
 template <> struct CoefGen<df> {
@@ -1564,18 +1572,19 @@ k_cn_substitute_kept(Map sys, Map next, int m, const typename Store<R>::T* keep0
         const cx<R> xL = sload(x_next + t);
         const cx<R> xR = sload(x_next + t + 1);
         cx<R> zp = xL;
-        cx<R> dn = sload(keep + 2 * kThreads), wn = sload(keep + 3 * kThreads);
-        for (int k = 1; k < gap; ++k) {
-            const cx<R> d = dn, w = wn;
-            if (k + 1 < gap) {  // next row's values, issued before this row's arithmetic
-                dn = sload(keep + (2 * k + 2) * kThreads);
-                wn = sload(keep + (2 * k + 3) * kThreads);
-            }
-            cx<R> rhs = cadd(d, zp);
-            if (k == gap - 1) rhs = cadd(rhs, xR);
-            zp = cmul(rhs, w);
+        cx<R> d = sload(keep + 2 * kThreads), w = sload(keep + 3 * kThreads);
+        // rows 1 .. g-2, then row g-1 with xR (peeled: a condition inside the loop
+        // becomes an addition of zero on every row)
+        for (int k = 1; k < gap - 1; ++k) {
+            const cx<R> dn = sload(keep + (2 * k + 2) * kThreads);  // next row's values first
+            const cx<R> wn = sload(keep + (2 * k + 3) * kThreads);
+            zp = cmul(cadd(d, zp), w);
             sstore(zs + k * kTileStride + tid, zp);
+            d = dn;
+            w = wn;
         }
+        zp = cmul(cadd(cadd(d, zp), xR), w);
+        sstore(zs + (gap - 1) * kTileStride + tid, zp);
         cx<R> y = zp;
         if (regular) {
             sstore(zs + tid, xL);  // row 0 of the block: its top joint line

@@ -44,6 +44,7 @@ SCRIPT = textwrap.dedent("""
         m0, m1, ml = cnb.LARGE_GRID_BLOCKS[arith]
         for n, kw in ((100003, {{}}), (1 << 21, dict(block=m0, level1_block=m1, level_block=ml,
                                                     flags=cnb.FLAG_COEFF_TABLE)),
+                      (1 << 20, dict(flags=cnb.FLAG_PERSISTENT_LEVELS)), (1 << 20, dict(flags=cnb.FLAG_LEVEL_LAUNCHES)),
                       (200001, dict(levels=[40, 20])), (70001, dict(flags=cnb.FLAG_RECOMPUTE))):
             cfg = W.soft_coulomb_config(n=n, nsteps=5)
             prob = oracle.Problem(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=oracle.POT_SOFTCOULOMB, soft_s=2.0)

@@ -483,9 +483,9 @@ def test_persistent_levels_match_per_level_launches_bitwise(n, blocks, arith):
     cfg = W.soft_coulomb_config(n=n, nsteps=4)
     psi0 = W.full_support_state(n, cfg["dx"], cfg["x_min"], seed=7)
     E = to_dev(W.field_midpoints(4, cfg["dt"], t0=90.0))
-    kw = dict(arith=arith, block=m0, level1_block=m1, level_block=ml, flags=cnb.FLAG_COEFF_TABLE)
-    pers = plan_for(cfg, **kw)
-    per_level = plan_for(cfg, **{**kw, "flags": cnb.FLAG_COEFF_TABLE | cnb.FLAG_LEVEL_LAUNCHES})
+    kw = dict(arith=arith, block=m0, level1_block=m1, level_block=ml)
+    pers = plan_for(cfg, **kw, flags=cnb.FLAG_COEFF_TABLE | cnb.FLAG_PERSISTENT_LEVELS)
+    per_level = plan_for(cfg, **kw, flags=cnb.FLAG_COEFF_TABLE | cnb.FLAG_LEVEL_LAUNCHES)
     assert pers.info()["launches_per_step"] == 3
     assert per_level.info()["launches_per_step"] == 2 * per_level.info()["levels"] + 1
     pers.profile(True)
@@ -520,7 +520,12 @@ def test_persistent_barrier_times_out_and_recovers():
     cfg = W.soft_coulomb_config(n=200001, nsteps=2)
     psi0 = W.initial_state(cfg)
     E = W.field_midpoints(2, cfg["dt"], t0=30.0)
-    plan = plan_for(cfg)
+    for arith in (cnb.ARITH_F64, cnb.ARITH_DF64):
+        _barrier_timeout_case(cfg, psi0, E, arith)
+
+
+def _barrier_timeout_case(cfg, psi0, E, arith):
+    plan = plan_for(cfg, arith=arith, flags=cnb.FLAG_PERSISTENT_LEVELS)
     assert plan.info()["launches_per_step"] == 3
     plan.set_wait_limit(50_000_000, missing_ctas=1)  # 50 ms
     plan.step(to_dev(psi0), 2, E_mid=to_dev(E))

@@ -52,6 +52,8 @@ def plan_cases():
         m0, m1, ml = cnb.LARGE_GRID_BLOCKS[arith]
         out.append(("bench_blocks", arith, 1 << 22,
                     dict(block=m0, level1_block=m1, level_block=ml, flags=cnb.FLAG_COEFF_TABLE)))
+        out.append(("persistent", arith, 1 << 21, dict(flags=cnb.FLAG_PERSISTENT_LEVELS)))
+        out.append(("per_level", arith, 1 << 21, dict(flags=cnb.FLAG_LEVEL_LAUNCHES)))
         out.append(("long_blocks", arith, 200001, dict(levels=[40, 20])))
         out.append(("recompute", arith, 70001, dict(flags=cnb.FLAG_RECOMPUTE)))
     return out
