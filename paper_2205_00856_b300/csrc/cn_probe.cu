@@ -16,15 +16,19 @@
 namespace {
 
 constexpr int kChains = 8;
-constexpr int kIters = 4096;
+constexpr int kIters = 2048;
 constexpr int kProbeThreads = 256;
 
+// iters arrives at run time and the outer loop stays rolled, so every iteration
+// issues the kChains independent operations back to back (a trip count known to
+// the compiler let it regroup the chains and measured latency, not throughput)
 template <bool kFma>
-__global__ void __launch_bounds__(kProbeThreads) k_fp64_rate(double* out, double a, double b) {
+__global__ void __launch_bounds__(kProbeThreads) k_fp64_rate(double* out, int iters, double a, double b) {
     double v[kChains];
 #pragma unroll
     for (int k = 0; k < kChains; ++k) v[k] = 1e-3 * threadIdx.x + k;
-    for (int it = 0; it < kIters; ++it) {
+#pragma unroll 1
+    for (int it = 0; it < iters; ++it) {
 #pragma unroll
         for (int k = 0; k < kChains; ++k) v[k] = kFma ? fma(v[k], a, b) : v[k] + b;
     }
@@ -42,7 +46,7 @@ cudaError_t time_rate(double* out, unsigned grid, double* rate) {
     float best = 0.0f;
     for (int r = 0; r < 6 && e == cudaSuccess; ++r) {  // the first run warms up
         e = cudaEventRecord(e0, nullptr);
-        if (e == cudaSuccess) k_fp64_rate<kFma><<<grid, kProbeThreads>>>(out, 0.999999, 1e-9);
+        if (e == cudaSuccess) k_fp64_rate<kFma><<<grid, kProbeThreads>>>(out, kIters, 0.999999, 1e-9);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
