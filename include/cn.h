@@ -358,9 +358,10 @@ cn_status cn_plan_set_wait_limit(cn_plan plan, int64_t timeout_ns, int32_t missi
  * `byte` (0..255; 0xFF makes every binary64 and binary32 word a NaN) -- the
  * kept right-hand sides and pivots, the reduced systems, CTA slots and
  * solutions of every nesting level, the long-block and serial-RS scratch, the
- * adjoint's mu buffer and the staging buffers of cn_step_host.  Not touched:
- * the coefficient table and the per-system tables built at creation, the
- * status word and the adjoint's ticket counter.  Since every call writes each
+ * adjoint's mu buffer, the staging buffers of cn_step_host and a slab's
+ * joint-solve scratch.  Not touched: the coefficient table and the per-system
+ * tables built at creation, the status word, the adjoint's ticket counter and
+ * the persistent launch's barrier words.  Since every call writes each
  * scratch word before it reads it, results after a fill are bitwise those
  * without it.  CN_ERR_INVALID_ARG for byte outside 0..255.  Synchronous. */
 cn_status cn_plan_fill_workspace(cn_plan plan, int32_t byte);

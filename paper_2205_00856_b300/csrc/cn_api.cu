@@ -1032,10 +1032,11 @@ cn_status run_steps(Engine* p, const void* psi_in, void* psi_out, const double* 
 // Fill every scratch buffer of the engine with `byte` (synchronously): the kept
 // right-hand sides and pivots (or the recompute-mode state buffer), the reduced
 // systems, CTA slots and solutions of every level, the long-block and serial-RS
-// scratch, the adjoint's mu buffer and the host-call staging buffers.  Not
-// touched: the coefficient table and the per-system tables (built once at
-// creation, read-only afterwards), the status word and the adjoint's ticket
-// counter (which must be zero between calls).
+// scratch, the adjoint's mu buffer, the host-call staging buffers and a slab's
+// joint-solve scratch.  Not touched: the coefficient table and the per-system
+// tables (built once at creation, read-only afterwards), the status word, the
+// adjoint's ticket counter and the persistent launch's barrier words (which
+// must hold their between-calls values).
 cn_status fill_workspace(Engine* p, int byte) {
     if (byte < 0 || byte > 255) return CN_ERR_INVALID_ARG;
     if (cudaDeviceSynchronize() != cudaSuccess) return CN_ERR_CUDA;
@@ -1062,6 +1063,7 @@ cn_status fill_workspace(Engine* p, int byte) {
     fill(p->h_in, sizeof(double2) * (size_t)p->desc.n);
     fill(p->h_out, sizeof(double2) * (size_t)p->desc.n);
     if (p->h_E) fill(p->h_E, sizeof(double) * (size_t)p->h_E_cap);
+    fill(p->joint_work, 2 * sizeof(double2) * ((size_t)p->nslabs + 1));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return cuda_status(e);
 }
