@@ -191,8 +191,10 @@ class ClockSampler:
          "clocks_event_reasons.sw_power_cap")
     NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, uuid: str):
-        self.uuid = uuid
+    def __init__(self, uuid: str, pci: str = ""):
+        self.uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        self.pci = pci
+        self.errors = []
         self.rows = []  # (sm_mhz, max_mhz, {reasons})
         self.stop = threading.Event()
         self.t = None
@@ -201,7 +203,10 @@ class ClockSampler:
     def _nvml_reader(self):
         import pynvml as N
         N.nvmlInit()
-        h = N.nvmlDeviceGetHandleByUUID(self.uuid)
+        try:
+            h = N.nvmlDeviceGetHandleByUUID(self.uuid)
+        except Exception:  # the same device by its PCI bus id
+            h = N.nvmlDeviceGetHandleByPciBusId(self.pci)
         bits = (N.nvmlClocksEventReasonHwSlowdown, N.nvmlClocksEventReasonHwThermalSlowdown,
                 N.nvmlClocksEventReasonSwThermalSlowdown, N.nvmlClocksEventReasonSwPowerCap)
         mx = float(N.nvmlDeviceGetMaxClockInfo(h, N.NVML_CLOCK_SM))
@@ -228,7 +233,8 @@ class ClockSampler:
                 self.rows.append(read())
                 self.source = src
                 break
-            except Exception:
+            except Exception as e:
+                self.errors.append(f"{src}: {type(e).__name__}: {e}"[:200])
                 read = None
         if read is not None:
             def loop():
@@ -250,8 +256,20 @@ class ClockSampler:
         if not self.rows:
             return None
         reasons = sorted(set().union(*(r[2] for r in self.rows)))
-        return {"sm_mhz": statistics.median(r[0] for r in self.rows), "sm_max_mhz": max(r[1] for r in self.rows),
-                "reasons": reasons, "samples": len(self.rows), "source": self.source}
+        out = {"sm_mhz": statistics.median(r[0] for r in self.rows), "sm_max_mhz": max(r[1] for r in self.rows),
+               "reasons": reasons, "samples": len(self.rows), "source": self.source}
+        if self.errors:
+            out["unused_sources"] = self.errors
+        return out
+
+
+def device_ids(torch, dev):
+    """(UUID, PCI bus id) of the torch device, for NVML / nvidia-smi."""
+    pr = torch.cuda.get_device_properties(dev)
+    pci = ""
+    if hasattr(pr, "pci_bus_id"):
+        pci = f"{getattr(pr, 'pci_domain_id', 0):08x}:{pr.pci_bus_id:02x}:{getattr(pr, 'pci_device_id', 0):02x}.0"
+    return str(pr.uuid), pci
 
 
 def cpu_baseline_oracle(budget_s: float = 10.0):
@@ -430,9 +448,8 @@ def time_steps(torch, plan, psi0, E, steps, warmup, dist, dev, sample_clocks, pe
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    clk = ClockSampler(*device_ids(torch, dev)) if sample_clocks else None
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clk = ClockSampler(uuid) if sample_clocks else None
     if clk:
         clk.__enter__()
     ev0.record(stream)
@@ -700,8 +717,10 @@ def largest_bench(torch, cnb, args, dev):
     arith = cnb.ARITH_DF64 if args.arith == "df64" else cnb.ARITH_F64
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     kw = dict(pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith)
-    m0, ml, tt = cnb.autotune_plan(n, dx, dt, cfg["x_min"], candidates=[(8, 8), (12, 12), (13, 12), (16, 12)], steps=4,
-                                   repeats=1, **kw)
+    # candidates per arithmetic: binary64 favours long level-0 blocks (its per-block and level
+    # costs shrink as 1/m), double-float shorter ones
+    cands = [(16, 12), (24, 8), (32, 8), (32, 12)] if arith == cnb.ARITH_F64 else [(8, 8), (12, 12), (13, 12), (16, 12)]
+    m0, ml, tt = cnb.autotune_plan(n, dx, dt, cfg["x_min"], candidates=cands, steps=4, repeats=1, **kw)
     torch.cuda.empty_cache()
     nw = 1 << 20
     j0 = n // 2 - nw // 2
@@ -713,8 +732,7 @@ def largest_bench(torch, cnb, args, dev):
     stream = torch.cuda.current_stream()
     plan.step(psi, args.warmup, E_mid=E[:args.warmup], psi_out=psi, stream=stream)
     torch.cuda.synchronize()
-    uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    clk = ClockSampler(uuid)
+    clk = ClockSampler(*device_ids(torch, dev))
     clk.__enter__()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
