@@ -16,6 +16,24 @@ from __future__ import annotations
 from . import SLAB_SHARE, Slab
 
 
+def allgather_shares(share, shares_out, group=None):
+    """The step's one exchange: every rank's SLAB_SHARE complex values (`share`)
+    gathered into `shares_out` (SLAB_SHARE * world values) in rank order.  With
+    NCCL the gather runs on the device; with any other backend (gloo) through
+    host memory.  Works on CPU tensors with gloo too."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    if dist.get_backend(group) == "nccl":
+        dist.all_gather_into_tensor(shares_out, share, group=group)
+        return shares_out
+    mine = share.cpu()
+    parts = [torch.empty_like(mine) for _ in range(world)]
+    dist.all_gather(parts, mine, group=group)
+    shares_out.copy_(torch.cat(parts))
+    return shares_out
+
+
 class ShardedCN:
     """This rank's slab of a grid of n points over the ranks of `group` (default:
     the world), plus the exchange buffers.  plan_kw: as for Slab (pot, soft_s,
@@ -30,19 +48,11 @@ class ShardedCN:
         self.device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.slab = Slab(n, dx, dt, x_min, self.world, self.rank, joints=joints, **plan_kw)
         self.lo, self.hi, self.rows = self.slab.lo, self.slab.hi, self.slab.n
-        self.host_staged = dist.get_backend(group) != "nccl"
         self.share = torch.empty(SLAB_SHARE, dtype=torch.complex128, device=self.device)
         self.shares = torch.empty(SLAB_SHARE * self.world, dtype=torch.complex128, device=self.device)
 
     def _exchange(self):
-        import torch
-        if not self.host_staged:
-            self.dist.all_gather_into_tensor(self.shares, self.share, group=self.group)
-            return
-        mine = self.share.cpu()
-        parts = [torch.empty_like(mine) for _ in range(self.world)]
-        self.dist.all_gather(parts, mine, group=self.group)
-        self.shares.copy_(torch.cat(parts))
+        allgather_shares(self.share, self.shares, self.group)
 
     def step(self, psi_local, nsteps: int, E_mid=None, stream=None):
         """nsteps CN steps of the whole grid, this rank's rows in place
