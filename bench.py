@@ -15,6 +15,7 @@ is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--arith f64|df64]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+  python bench.py --sharded [--sharded-backend nccl|gloo] ...   # one grid, one slab per rank
 
 Prints one JSON line (rank 0).
 """
@@ -120,6 +121,8 @@ def max_over_ranks(dist, value: float, device) -> float:
     if not dist:
         return value
     import torch
+    if dist.get_backend() != "nccl":
+        device = "cpu"  # gloo reduces host tensors
     t = torch.tensor([float(value)], device=device, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
@@ -765,6 +768,124 @@ def largest_bench(torch, cnb, args, dev):
             "kernel_ms_3_steps": {k: v[0] for k, v in prof.items()}, "clocks": clk.summary()}
 
 
+def sharded_bench(torch, cnb, args, dev, rank, world, dist):
+    """--sharded: one grid of args.n points cut into `world` slabs (the paper's MPI
+    decomposition, Sec. 6.2), one per rank.  A CN step is the slab's reduction,
+    one all-gather of six complex values per rank (Sec. 4.1.3's joint-line
+    exchange) and the slab's joint solve and substitution
+    (paper_2205_00856_b300.sharded.ShardedCN).  Strong scaling: the job's work is
+    the one grid whatever the number of ranks.  Returns rank 0's line (None on
+    the other ranks)."""
+    from paper_2205_00856_b300.sharded import ShardedCN
+    cfg = W.soft_coulomb_config(n=args.n)
+    n = cfg["n"]
+    leg = make_leg(cnb, args, args.arith, True)
+    sh = ShardedCN(n, cfg["dx"], cfg["dt"], cfg["x_min"], device=dev, pot=cnb.POT_SOFTCOULOMB, soft_s=2.0,
+                   block=leg["block"], arith=leg["code"], level_block=leg["level_block"],
+                   level1_block=leg["level1_block"], flags=cnb.FLAG_COEFF_TABLE if leg["table"] else 0)
+    psi0 = W.initial_state(cfg)
+    mine = np.ascontiguousarray(psi0[sh.lo:sh.hi + 1])
+    cur = torch.from_numpy(mine).to(dev)
+    E = torch.from_numpy(W.field_midpoints(WORKLOAD_STEPS, cfg["dt"])).to(dev)
+
+    def run(k0, count, psi):
+        k = 0
+        while k < count:
+            j = (k0 + k) % WORKLOAD_STEPS
+            c = min(count - k, WORKLOAD_STEPS - j)
+            sh.step(psi, c, E_mid=E[j:j + c])
+            k += c
+
+    run(0, args.warmup, cur)
+    torch.cuda.synchronize()
+    sh.slab.check()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(*device_ids(torch, dev)) if rank == 0 else None
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if clk:
+        clk.__enter__()
+    ev0.record(stream)
+    run(args.warmup, args.steps, cur)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__()
+    ms = max_over_ranks(dist, ev0.elapsed_time(ev1), dev)
+    # kernel breakdown of this rank's slab: the same steps again, per-kernel-class events
+    sh.slab.profile(True)
+    sh.slab.profile_read()
+    run(args.warmup + args.steps, args.steps, cur)
+    torch.cuda.synchronize()
+    sh.slab.profile(False)
+    prof = sh.slab.profile_read()
+    sh.slab.check()
+    dist.barrier()
+
+    # end to end: the slab's rows from pinned host memory, e2e_inner steps, back to the host
+    host_in = torch.from_numpy(mine).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    work = torch.empty_like(cur)
+
+    def e2e_call():
+        work.copy_(host_in, non_blocking=True)
+        run(0, args.e2e_inner, work)
+        host_out.copy_(work, non_blocking=True)
+        torch.cuda.synchronize()
+    if args.e2e_calls > 0:
+        e2e_call()
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_calls):
+        e2e_call()
+    e2e_s = max_over_ranks(dist, max(time.perf_counter() - t0, 1e-9), dev)
+    rows = sh.rows
+    sh.close()
+    if rank != 0:
+        return None
+    value = n * args.steps / (ms * 1e-3)
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    conf = workload_config(args, leg)
+    conf["parallelism"] = f"slabs x{world} ({dist.get_backend()} all-gather of 6 complex values per rank and step)"
+    conf["steps_per_call"] = 1
+    conf["rank0_rows"] = rows
+    # per step: the profiled launches plus the share export and the joint solve (not profiled)
+    launches = sum(v[1] for v in prof.values()) + 2 * args.steps
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": leg["arith"], "data": "synthetic", "config": conf,
+            "roofline": roofline(prof, rows, leg["arith"], peaks, leg["block"], leg["table"], sms),
+            "roofline_hbm": hbm_roofline(value / world, leg["arith"], leg["table"], peaks),
+            "kernel_ms_rank0": {k: v[0] for k, v in prof.items()}, "gpu_launches": launches,
+            "e2e": {"value": n * args.e2e_inner * args.e2e_calls / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": 16 * rows / max(args.e2e_inner, 1),
+                    "d2h_bytes_per_step": 16 * rows / max(args.e2e_inner, 1), "cn_steps_per_call": args.e2e_inner,
+                    "calls": args.e2e_calls, "bytes": "rank 0's slab rows",
+                    "api": "ShardedCN.step on a slab copied from pinned host memory and back"},
+            "clocks": clk.summary() if clk else None}
+
+
+def init_process_group(dev, backend):
+    """The job's process group (torchrun's env rendezvous); a one-rank group on
+    127.0.0.1 when the bench was started without torchrun."""
+    import datetime
+
+    import torch.distributed as dist
+    if "MASTER_ADDR" not in os.environ:
+        import socket
+        with socket.socket() as s:
+            s.bind(("127.0.0.1", 0))
+            port = s.getsockname()[1]
+        os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK="0", WORLD_SIZE="1")
+    kw = {"device_id": dev} if backend == "nccl" else {}
+    # a rank that dies makes the others' next collective fail after this long
+    # instead of waiting for ever
+    dist.init_process_group(backend, timeout=datetime.timedelta(seconds=PG_TIMEOUT_S), **kw)
+    return dist
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -803,6 +924,12 @@ def main():
                     help="steps of the one-plan-per-system baseline timed")
     ap.add_argument("--largest", action="store_true",
                     help="instead: the largest single system, N = 2^32, dx = 0.05, dt = 0.01, 50 steps")
+    ap.add_argument("--sharded", action="store_true",
+                    help="instead: one grid of --n points in one slab per rank (strong scaling; the paper's "
+                         "MPI decomposition), the joint-line shares all-gathered every step")
+    ap.add_argument("--sharded-backend", choices=["nccl", "gloo"], default="nccl",
+                    help="--sharded collective: nccl on the device, or gloo through host memory (ranks may "
+                         "then share one GPU)")
     ap.add_argument("--adjoint-steps", type=int, default=2000,
                     help="gradient run (N=2^20, 500 controls): steps for the adjoint/forward ratio (0: skip)")
     args = ap.parse_args()
@@ -814,17 +941,14 @@ def main():
     import paper_2205_00856_b300 as cnb
 
     rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    # several gloo ranks may share one device (--sharded-backend gloo)
+    local = local % max(torch.cuda.device_count(), 1) if args.sharded_backend == "gloo" else local
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     dist = None
-    if world > 1:
-        import datetime
-
-        import torch.distributed as dist
-        # a rank that dies makes the others' next collective fail after this long
-        # instead of waiting for ever
-        dist.init_process_group("nccl", device_id=dev, timeout=datetime.timedelta(seconds=PG_TIMEOUT_S))
+    if world > 1 or args.sharded:
+        dist = init_process_group(dev, args.sharded_backend if args.sharded else "nccl")
 
     global FP64_MEASURED_OPS, FP64_PEAK_SOURCE
     fma_rate, add_rate = cnb.fp64_rate()
@@ -837,6 +961,12 @@ def main():
             print(json.dumps(largest_bench(torch, cnb, args, dev)), flush=True)
         if dist:
             dist.destroy_process_group()
+        return 0
+    if args.sharded:
+        line = sharded_bench(torch, cnb, args, dev, rank, world, dist)
+        if line:
+            print(json.dumps(line), flush=True)
+        dist.destroy_process_group()
         return 0
 
     cfg = W.soft_coulomb_config(n=args.n)

@@ -127,3 +127,52 @@ def test_two_gloo_processes_match_oracle(tmp_path, arith):
         parts.append(vals)
     assert parts[0][-1].tobytes() == parts[1][0].tobytes()
     _check(full, ref)
+
+
+def _bench_line(out: str) -> dict:
+    import json
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out
+    return json.loads(lines[0])
+
+
+BENCH_ARGS = ["--sharded", "--n", "200003", "--steps", "20", "--warmup", "3", "--e2e-calls", "1",
+              "--e2e-inner", "5"]
+
+
+@pytest.mark.parametrize("arith", ["f64", "df64"])
+def test_bench_sharded_one_rank_nccl(arith):
+    """bench.py --sharded without torchrun: a one-rank NCCL group, one slab."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("MASTER_ADDR", "MASTER_PORT", "RANK", "WORLD_SIZE")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), *BENCH_ARGS, "--arith", arith],
+                       capture_output=True, text=True, timeout=600, cwd=root, env=env)
+    assert r.returncode == 0, r.stderr[-3000:]
+    line = _bench_line(r.stdout)
+    assert line["n_gpus"] == 1 and line["scaling"] == "strong" and line["dtype"] == arith
+    assert line["value"] > 0 and line["e2e"]["value"] > 0 and line["gpu_launches"] > 0
+    assert line["config"]["rank0_rows"] == 200003
+
+
+def test_bench_sharded_two_gloo_ranks_one_gpu():
+    """bench.py --sharded under torchrun with two gloo ranks on the one GPU (the
+    exchange through host memory: the two processes' kernels never wait on one
+    another)."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(root, "bench.py"),
+           *BENCH_ARGS, "--sharded-backend", "gloo"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=900, cwd=root)
+    assert r.returncode == 0, r.stderr[-3000:]
+    line = _bench_line(r.stdout)
+    assert line["n_gpus"] == 2 and line["scaling"] == "strong"
+    assert "gloo" in line["config"]["parallelism"]
+    assert 100000 <= line["config"]["rank0_rows"] <= 100003
+    assert line["value"] > 0 and line["gpu_launches"] > 0
