@@ -174,6 +174,13 @@ void free_engine(Engine* p) {
     cudaFree(p->pbar);
 }
 
+// Substitution scratch (two entries per row) for level-0 blocks longer than the
+// shared-memory staging allows; the levels below substitute from their kept RD
+// results and need none.
+size_t zc_entries_of(const Engine* p) {
+    return p->lv[0].m > kSmemRowsMax ? 2 * (size_t)p->lv[0].rows_total : 0;
+}
+
 // --------------------------------------------------------------- debug build: bounds registry
 // Extents of the buffers a call may touch, installed in the kernels' range table
 // (cn_debug.cuh) on the call's stream before its first launch.  No-ops in the
@@ -203,9 +210,7 @@ void dbg_engine(const Engine* p, DbgList& L) {
         L.add(Lv.x, kCplx * (size_t)Lv.rows_total);
     }
     for (const LevelData& Lv : p->lv) L.add(Lv.d_sys, sizeof(LvlSys) * (size_t)p->nsys);
-    size_t zc_entries = 0;
-    for (size_t l = 0; l + 1 < p->lv.size(); ++l)
-        if (p->lv[l].m > kSmemRowsMax) zc_entries = std::max(zc_entries, 2 * (size_t)p->lv[l].rows_total);
+    const size_t zc_entries = zc_entries_of(p);
     L.add(p->zc, kCplx * zc_entries);
     if (p->base_cs) L.add(p->base_cs, kCplx * (size_t)p->lv[(size_t)p->base_level[0]].sys[0].n);
     L.add(p->d_base, std::max(sizeof(BaseSys<double>), sizeof(BaseSys<df>)) * (size_t)p->nsys);
@@ -367,9 +372,7 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
         if (e == cudaSuccess) e = cudaMemset(L.slot, 0, 3 * kCplx * nslot);
     }
     // long blocks (substitution scratch, two entries per row) and a long last level (serial RS)
-    size_t zc_entries = 0;
-    for (size_t l = 0; l + 1 < p->lv.size(); ++l)
-        if (p->lv[l].m > kSmemRowsMax) zc_entries = std::max(zc_entries, 2 * (size_t)p->lv[l].rows_total);
+    const size_t zc_entries = zc_entries_of(p);
     if (e == cudaSuccess && zc_entries) {
         p->workspace_bytes += (int64_t)(kCplx * zc_entries);
         e = cudaMalloc(&p->zc, kCplx * zc_entries);
@@ -472,7 +475,6 @@ size_t kept_smem(int m) { return (size_t)m * kTileStride * kCplx; }
 size_t fused_smem(int m) { return (size_t)(m + 2) * kTileStride * kCplx; }  // rows 0..g+1 per column
 size_t cr_smem() { return 6 * (size_t)kCrMax * kCplx; }
 size_t ws_reduce_smem(int m) { return ws_reduce_entries(m) * kCplx; }
-size_t ws_subst_smem(int m) { return ws_subst_entries(m) * kCplx; }
 
 // The two-group kernels take the reduced levels below level 1 that need at most
 // one CTA of kThreads blocks per multiprocessor, with blocks of at most
@@ -496,6 +498,9 @@ template <class R, class Src, class Map, class XT>
 cudaError_t launch_substitute(bool pdl, const Src& src, Map sys, Map next, int m, const LevelData& nextL, XT* x,
                               int* status, int64_t total, void* zc, cudaStream_t st) {
     if (total == 0) return cudaSuccess;
+    if constexpr (Src::kKeepsRD)  // a reduced level: the RD results are in its planes
+        return launch(pdl, k_substitute_rd<R, Map>, grid_for(total), kThreads, 0, st, src, sys, next, m,
+                      x_of<R>(nextL), x);
     if (m > kSmemRowsMax)
         return launch(pdl, k_substitute_gmem<R, Src, Map, XT>, grid_for(total), kThreads, 0, st, src, sys, next, m,
                       x_of<R>(nextL), x, static_cast<typename Store<R>::T*>(zc), status);
@@ -524,10 +529,8 @@ cudaError_t raise_smem_limit(void (*kernel)(KArgs...), size_t bytes) {
 }
 
 template <class R, class Map, class Grid>
-cudaError_t set_smem_limits_map(int m0, int ml) {
-    typedef typename Store<R>::T ST;
+cudaError_t set_smem_limits_map(int m0) {
     cudaError_t e = raise_smem_limit(k_substitute<R, ArraySource, Map, double2>, subst_smem(m0));
-    if (e == cudaSuccess) e = raise_smem_limit(k_substitute<R, LevelSource<R>, Map, ST>, subst_smem(ml));
     if (e == cudaSuccess) e = raise_smem_limit(k_cn_substitute<R, -1, Map, Grid>, subst_smem(m0));
     if (e == cudaSuccess) e = raise_smem_limit(k_cn_substitute<R, 0, Map, Grid>, subst_smem(m0));
     if (e == cudaSuccess) e = raise_smem_limit(k_cn_substitute_kept<R, Map>, kept_smem(m0));
@@ -539,24 +542,23 @@ cudaError_t set_smem_limits_map(int m0, int ml) {
     if (e == cudaSuccess) e = raise_smem_limit(k_base_cr<R>, cr_smem());
     if (e == cudaSuccess) e = raise_smem_limit(k_base_cr_many<R>, cr_smem());
     if (e == cudaSuccess) e = raise_smem_limit(k_reduce_ws<R, Map>, ws_reduce_smem(kWsRowsMax));
-    if (e == cudaSuccess) e = raise_smem_limit(k_substitute_ws<R, Map>, ws_subst_smem(kWsRowsMax));
     return e;
 }
 
 template <class R>
 cudaError_t set_smem_limits(const Engine* p) {
-    // the largest staged block per kernel kind (longer blocks take the scratch variants)
-    int m0 = std::min(p->lv[0].m, kSmemRowsMax), ml = 3;
-    for (size_t l = 1; l + 1 < p->lv.size(); ++l) ml = std::max(ml, std::min(p->lv[l].m, kSmemRowsMax));
-    if (p->batched) return set_smem_limits_map<R, ManySys, ManyGrid>(m0, ml);
-    return set_smem_limits_map<R, OneSys, OneGrid>(m0, ml);
+    // the largest staged level-0 block (longer blocks take the scratch variants;
+    // the levels below substitute from their kept RD results, unstaged)
+    const int m0 = std::min(p->lv[0].m, kSmemRowsMax);
+    if (p->batched) return set_smem_limits_map<R, ManySys, ManyGrid>(m0);
+    return set_smem_limits_map<R, OneSys, OneGrid>(m0);
 }
 
 // The persistent launch of the levels below level 0 (k_levels) serves a single
 // system of the default hierarchy (reduced to <= 1024 rows, cyclic-reduction RS
 // stage) unless CN_FLAG_LEVEL_LAUNCHES asks for one launch per stage and level:
-// its shared memory holds the RS stage's arrays and as many groups' substitution
-// staging as fit, one CTA per multiprocessor (512 threads, <= 128 registers).
+// its shared memory holds the RS stage's arrays, one CTA per multiprocessor (512
+// threads, <= 128 registers).
 template <class R>
 cudaError_t setup_persistent(Engine* p) {
     p->persistent = false;
@@ -568,15 +570,7 @@ cudaError_t setup_persistent(Engine* p) {
     const bool want = (fl & CN_FLAG_PERSISTENT_LEVELS) ||
                       (!(fl & CN_FLAG_LEVEL_LAUNCHES) && p->desc.arith == CN_ARITH_F64);
     if (!want || p->batched || p->slab || !p->lvl_m.empty() || p->lv.size() < 3) return cudaSuccess;
-    size_t smem = cr_smem();
-    for (size_t l = 1; l + 1 < p->lv.size(); ++l) {
-        if (p->lv[l].m > kSmemRowsMax) return cudaSuccess;
-        smem = std::max(smem, kPGroups * subst_smem(p->lv[l].m));
-    }
-    const size_t cap = 200 * 1024;  // leaves room for the kernel's static exchange arrays
-    smem = std::min(smem, cap);
-    for (size_t l = 1; l + 1 < p->lv.size(); ++l)
-        if (subst_smem(p->lv[l].m) > smem) return cudaSuccess;
+    const size_t smem = cr_smem();
     cudaError_t e = raise_smem_limit(k_levels<R>, smem);
     int per_sm = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levels<R>, kPThreads, smem);
@@ -644,14 +638,8 @@ cudaError_t substitute_levels(Engine* p, cudaStream_t st) {
         with_maps(p, l, [&](auto a, auto b) {
             const LevelData& L = p->lv[l];
             const LevelData& N = p->lv[l + 1];
-            if (two_group_level(p, l)) {
-                e = launch(p->pdl, k_substitute_ws<R, decltype(a)>, (unsigned)ceil_div(L.total, kWsLanes), 2 * kWsLanes,
-                           ws_subst_smem(L.m), st, level_source<R>(L), a, b, L.m, x_of<R>(N), x_of<R>(L),
-                           p->status);
-            } else {
-                e = launch_substitute<R>(p->pdl, level_source<R>(L), a, b, L.m, N, x_of<R>(L), p->status, L.total,
-                                         p->zc, st);
-            }
+            e = launch_substitute<R>(p->pdl, level_source<R>(L), a, b, L.m, N, x_of<R>(L), p->status, L.total,
+                                     p->zc, st);
         });
     }
     return e;
@@ -674,7 +662,6 @@ cudaError_t persistent_levels(Engine* p, cudaStream_t st) {
         q.next = OneSys{N.sys[0]};
         q.m = Lv.m;
         q.m_next = N.m;
-        q.sub_groups = (int)std::min<size_t>(kPGroups, p->p_smem / subst_smem(Lv.m));
         q.out = planes_of<R>(N);
         q.out_slot = slot_of<R>(N);
         q.x = x_of<R>(Lv);
@@ -1054,9 +1041,7 @@ cn_status fill_workspace(Engine* p, int byte) {
         fill(L.slot, 3 * kCplx * (grid_for(p->lv[l - 1].total) + 1));
         fill(L.x, kCplx * (size_t)L.rows_total);
     }
-    size_t zc_entries = 0;
-    for (size_t l = 0; l + 1 < p->lv.size(); ++l)
-        if (p->lv[l].m > kSmemRowsMax) zc_entries = std::max(zc_entries, 2 * (size_t)p->lv[l].rows_total);
+    const size_t zc_entries = zc_entries_of(p);
     fill(p->zc, kCplx * zc_entries);
     if (p->base_cs) fill(p->base_cs, kCplx * (size_t)p->lv[(size_t)p->base_level[0]].sys[0].n);
     fill(p->mu, sizeof(double2) * (size_t)p->desc.n);

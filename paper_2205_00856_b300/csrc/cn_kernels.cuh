@@ -169,6 +169,7 @@ template <class R> struct Row {
 // General tridiagonal system in four complex128 arrays (cn_solve_tridiag, one
 // system); b_0 and c_{n-1} are taken as 0.
 struct ArraySource {
+    static constexpr bool kKeepsRD = false;  // the caller's arrays: read only
     const double2 *b, *a, *c, *d;
     int64_t n;
     __device__ __forceinline__ ArraySource bind(const LvlSys&) const { return *this; }
@@ -189,7 +190,8 @@ struct ArraySource {
 // block was the first thread of a CTA (slot, indexed by that CTA).
 template <class R> struct LevelSource {
     typedef typename Store<R>::T ST;
-    const ST* b;              // b plane at the bound system's slot_off; a, c, d follow at L apart
+    static constexpr bool kKeepsRD = true;  // the reduction keeps its RD results in the planes
+    ST* b;                    // b plane at the bound system's slot_off; a, c, d follow at L apart
     int64_t L;
     const LevelSlot<R>* slot;
     int64_t n;                // rows of the bound system
@@ -224,6 +226,27 @@ template <class R> struct LevelSource {
     // row i of a system kept in row order (the RS stage's level)
     template <class RR>
     __device__ __forceinline__ Row<R> row_at(int64_t i) const { return row<RR>(0, 0, i); }
+    // The RD results of interior row k of block t (row i of the system), written
+    // over the row's b, a and d entries once its reduction has read the row (no
+    // other block reads an interior row): the fill-in b^RD_k (the coupling to the
+    // block's first joint line), 1 / a^RD_k and d^RD_k; c_k stays.  Raw entries:
+    // the slot contribution was added when the row was read.
+    __device__ __forceinline__ void keep_rd(int64_t t, int64_t k, int64_t i, cx<R> bRD, cx<R> w, cx<R> dRD) const {
+        ST* q = b + (stride ? k * stride + t : i);
+        sstore(q, bRD);
+        sstore(q + L, w);
+        sstore(q + 3 * L, dRD);
+    }
+    // ... read back by the substitution: b = b^RD_k, a = 1 / a^RD_k, c = c_k, d = d^RD_k
+    __device__ __forceinline__ Row<R> kept_rd(int64_t t, int64_t k, int64_t i) const {
+        const ST* q = b + (stride ? k * stride + t : i);
+        Row<R> r;
+        r.b = sload(q);
+        r.a = sload(q + L);
+        r.c = sload(q + 2 * L);
+        r.d = sload(q + 3 * L);
+        return r;
+    }
 };
 
 // Where a block writes the rows of the next level: that level's planes bound to
@@ -352,6 +375,7 @@ __device__ __forceinline__ void reduce_cta(int64_t cta, int tid, JDPart<R>* xch,
         // row 1: untouched by RD
         const Row<R> r1 = row_k(1);
         cx<R> w = crcp(r1.a, ok);       // 1 / a_k^RD of the previous row
+        if constexpr (Src::kKeepsRD) src.keep_rd(t, 1, J0 + 1, r1.b, w, r1.d);
         const cx<R> w1 = w;
         cx<R> bRD = r1.b, dRD = r1.d;   // RD fill-in column J0 and rhs of the previous row
         cx<R> cprev = r1.c;             // upper diagonal of the previous row
@@ -366,6 +390,7 @@ __device__ __forceinline__ void reduce_cta(int64_t cta, int tid, JDPart<R>* xch,
             bRD = cmul(r, bRD);
             dRD = cfma(rk.d, r, dRD);
             const cx<R> wk = crcp(cfma(rk.a, r, cprev), ok);
+            if constexpr (Src::kKeepsRD) src.keep_rd(t, k, J0 + k, bRD, wk, dRD);
             // RU coefficient of row k-1: rho_{k-1} = -c_{k-1} / a_k
             Q = cmul(Q, cneg(cmul(cprev, wk)));
             nb = cfma(nb, Q, bRD);
@@ -473,6 +498,53 @@ k_substitute(Src src0, Map sys, Map next, int m, const typename Store<R>::T* x_n
     substitute_cta<R>(blockIdx.x, threadIdx.x, zs, cs, src0, sys, next, m, x_next0, x0, status);
 }
 
+// SS of a level >= 1 from the RD results its reduction kept in place
+// (LevelSource::keep_rd).  After RD, interior row k of a block (1 <= k < g)
+// couples only to the block's first joint line and to row k + 1:
+//   b^RD_k x_L + a^RD_k x_k + c_k x_{k+1} = d^RD_k
+// (Table 1's RD; b holds column J_t, as Sec. 4.1.2 describes), so with the
+// support values x_L = x_{J_t} and x_g = x_R = x_{J_{t+1}} known, upward
+//   x_k = (d^RD_k - b^RD_k x_L - c_k x_{k+1}) / a^RD_k,
+// the term in x_L off the chain (binary64: 12 operations a row, none of them a
+// reciprocal), and no staging.  (The rows' own a, b, d are gone: a level is reduced and
+// substituted once per solve.)
+template <class R, class Map, class XT>
+__device__ __forceinline__ void substitute_rd_cta(int64_t cta, int tid, const LevelSource<R>& src0, Map sys,
+                                                  Map next, int m, const typename Store<R>::T* x_next0, XT* x0) {
+    typedef typename Store<R>::T ST;
+    const int64_t g = cta * kThreads + tid;
+    if (g >= sys.total()) return;
+    const int si = sys.find(g);
+    const LvlSys& e = sys.at(si);
+    const LevelSource<R> src = src0.bind(e);
+    const int64_t n = e.n, P = e.P, t = g - e.blk_off;
+    const ST* x_next = x_next0 + next.at(si).row_off;
+    XT* x = x0 + e.row_off;
+    const int64_t J0 = joint_line(t, P, m, n);
+    const int gap = (int)(joint_line(t + 1, P, m, n) - J0);
+    const cx<R> xL = sload(x_next + t);
+    const cx<R> xR = sload(x_next + t + 1);
+    cx<R> y = xR;
+    Row<R> nxt = src.kept_rd(t, gap - 1, J0 + gap - 1);
+    for (int k = gap - 1; k >= 1; --k) {
+        const Row<R> rk = nxt;
+        const int kn = k > 1 ? k - 1 : 1;  // one row ahead (row 1 again on the last row)
+        nxt = src.kept_rd(t, kn, J0 + kn);
+        y = cmul(csub2mul(rk.d, rk.c, y, rk.b, xL), rk.a);
+        put<XT, R>(x + J0 + k, y);
+    }
+    put<XT, R>(x + J0, xL);
+    if (t == P - 1) put<XT, R>(x + J0 + gap, xR);
+}
+
+template <class R, class Map>
+__global__ void __launch_bounds__(kThreads)
+k_substitute_rd(LevelSource<R> src0, Map sys, Map next, int m, const typename Store<R>::T* x_next0,
+                typename Store<R>::T* x0) {
+    grid_dep_enter();
+    substitute_rd_cta<R>(blockIdx.x, threadIdx.x, src0, sys, next, m, x_next0, x0);
+}
+
 // Same substitution for blocks longer than the shared-memory staging allows:
 // z_k and c'_k go to a scratch array of two entries per row of the level
 // (zc[2 r], zc[2 r + 1] for row r; a thread's rows are contiguous) and the
@@ -528,14 +600,15 @@ k_substitute_gmem(Src src0, Map sys, Map next, int m, const typename Store<R>::T
 // each busy scheduler issues one block walk after another.  Here a CTA of
 // 2 kWsLanes threads takes kWsLanes blocks, so a group of kThreads blocks spreads
 // over a cluster of kWsCluster CTAs.  In each CTA the first warp runs the pivot
-// chain of its blocks (r_k and 1 / a_k of Table 1's RD; 1 / m_k and c'_k of the
-// substitution's forward sweep) and the second warp the recurrences that only
-// consume it (fill-ins, RU, JD, JU; z_k and the backward values), one named
-// barrier per row behind; both first stage the rows in shared memory.  The
-// operations and their order are those of k_reduce and k_substitute, so the
-// results are the same bits, and the reduced rows keep the kThreads-block slots
-// (the JD part that crosses a CTA inside a group goes through the cluster's
-// distributed shared memory).
+// chain of its blocks (r_k and 1 / a_k of Table 1's RD) and the second warp the
+// recurrences that only consume it (fill-ins, RU, JD, JU, and the RD results
+// kept for the substitution), one named barrier per row behind; both first
+// stage the rows in shared memory.  The operations and their order are those of
+// k_reduce, so the results are the same bits, and the reduced rows keep the
+// kThreads-block slots (the JD part that crosses a CTA inside a group goes
+// through the cluster's distributed shared memory).  The substitution of such a
+// level needs no split: from the kept RD results it is one short chain a block
+// (k_substitute_rd).
 constexpr int kWsRowsMax = 16;  // one named barrier (ids 1..15) per row
 constexpr int kWsLanes = 32;    // blocks per CTA
 constexpr int kWsCluster = kThreads / kWsLanes;
@@ -588,10 +661,8 @@ template <class R> struct WsRows {
     }
 };
 
-// Shared memory of k_reduce_ws (rows 0..m, r_k, 1 / a_k) and of k_substitute_ws
-// (rows 1..m-1, 1 / m_k, c'_k; z_k over the a field), in storage entries.
+// Shared memory of k_reduce_ws (rows 0..m, r_k, 1 / a_k), in storage entries.
 __host__ __device__ constexpr size_t ws_reduce_entries(int m) { return 6 * (size_t)(m + 1) * kWsLanes; }
-__host__ __device__ constexpr size_t ws_subst_entries(int m) { return 6 * (size_t)m * kWsLanes; }
 
 // write_reduced_row for a group of kThreads blocks spread over a cluster: block
 // (rank, lane) is block rank * kWsLanes + lane of the group.  Every thread of every
@@ -650,16 +721,17 @@ k_reduce_ws(LevelSource<R> src0, Map sys, Map next, int m, int m_next, LevelPlan
     ST* sW = sR + (m + 1) * kWsLanes;       // 1 / a_k after RD
     const int64_t g = (int64_t)blockIdx.x * kWsLanes + lt;
     const bool active = g < sys.total();
-    int64_t t = 0, P = 0;
+    int64_t t = 0, P = 0, J0 = 0;
     int si = 0, gap = 0;
+    LevelSource<R> src = src0;
     if (active) {
         si = sys.find(g);
         const LvlSys& e = sys.at(si);
-        const LevelSource<R> src = src0.bind(e);
+        src = src0.bind(e);
         const int64_t n = e.n;
         P = e.P;
         t = g - e.blk_off;
-        const int64_t J0 = joint_line(t, P, m, n);
+        J0 = joint_line(t, P, m, n);
         gap = (int)(joint_line(t + 1, P, m, n) - J0);
         // the two warps stage alternate rows 0..gap (row gap: row 0 of the next block)
         S.stage(pivots ? 0 : 1, gap, [&](int k) {
@@ -710,6 +782,8 @@ k_reduce_ws(LevelSource<R> src0, Map sys, Map next, int m, int m_next, LevelPlan
                 const cx<R> wk = sload(sW + k * kWsLanes + lt);
                 bRD = cmul(r, bRD);
                 dRD = cfma(S.d(k), r, dRD);
+                // every row is staged (and the pivots read it) before the first barrier
+                src.keep_rd(t, k, J0 + k, bRD, wk, dRD);
                 // RU coefficient of row k-1: rho_{k-1} = -c_{k-1} / a_k
                 Q = cmul(Q, cneg(cmul(cprev, wk)));
                 nb = cfma(nb, Q, bRD);
@@ -727,7 +801,9 @@ k_reduce_ws(LevelSource<R> src0, Map sys, Map next, int m, int m_next, LevelPlan
             Dg = S.d(gap);
             A0 = S.a(0);
             D0 = S.d(0);
-            const cx<R> r0u = cneg(cmul(S.c(0), sload(sW + kWsLanes + lt)));
+            const cx<R> w1 = sload(sW + kWsLanes + lt);
+            src.keep_rd(t, 1, J0 + 1, S.b(1), w1, S.d(1));
+            const cx<R> r0u = cneg(cmul(S.c(0), w1));
             JUc = cmul(r0u, nc);
             JUa = cmul(r0u, nb);
             JUd = cmul(r0u, nd);
@@ -735,81 +811,6 @@ k_reduce_ws(LevelSource<R> src0, Map sys, Map next, int m, int m_next, LevelPlan
     }
     ws_write_reduced_row<R>(!pivots, active, lt, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg,
                             RowSink<R>(out, next.at(si), m_next), out_slot);
-}
-
-template <class R, class Map>
-__global__ void __launch_bounds__(2 * kWsLanes)
-k_substitute_ws(LevelSource<R> src0, Map sys, Map next, int m, const typename Store<R>::T* x_next0,
-                typename Store<R>::T* x0, int* status) {
-    grid_dep_enter();
-    typedef typename Store<R>::T ST;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lt = threadIdx.x & (kWsLanes - 1);
-    const bool pivots = threadIdx.x < kWsLanes;
-    const WsRows<R> S{reinterpret_cast<ST*>(smem_raw), m, lt};
-    ST* sW = S.p + 4 * m * kWsLanes;  // 1 / m_k
-    ST* sC = sW + m * kWsLanes;       // c'_k
-    const int64_t g = (int64_t)blockIdx.x * kWsLanes + lt;
-    const bool active = g < sys.total();
-    int64_t t = 0, P = 0, J0 = 0;
-    int si = 0, gap = 0;
-    if (active) {
-        si = sys.find(g);
-        const LvlSys& e = sys.at(si);
-        const LevelSource<R> src = src0.bind(e);
-        const int64_t n = e.n;
-        P = e.P;
-        t = g - e.blk_off;
-        J0 = joint_line(t, P, m, n);
-        gap = (int)(joint_line(t + 1, P, m, n) - J0);
-        S.stage(pivots ? 1 : 2, gap - 1, [&](int k) { return src.template row<R>(t, k, J0 + k); });
-    }
-    __syncthreads();
-    if (pivots) {
-        // m_k = a_k - b_k c'_{k-1};  c'_k = c_k / m_k
-        bool ok = true;
-        cx<R> cpp = czero<R>();
-        for (int k = 1; k < m; ++k) {
-            if (active && k < gap) {
-                const cx<R> w = crcp(csub(S.a(k), cmul(S.b(k), cpp)), ok);  // c'_0 = 0, as k_substitute
-                cpp = cmul(S.c(k), w);
-                sstore(sW + k * kWsLanes + lt, w);
-                sstore(sC + k * kWsLanes + lt, cpp);
-            }
-            bar_arrive_id(k, 2 * kWsLanes);
-        }
-        if (!ok) flag_error(status, kStatusNonfinite);
-        return;
-    }
-    // z_k = (rhs_k - b_k z_{k-1}) / m_k, kept over a_k (read by the pivot group before its barrier k)
-    cx<R> xL = czero<R>(), xR = czero<R>(), zp = czero<R>();
-    if (active) {
-        const ST* x_next = x_next0 + next.at(si).row_off;
-        xL = sload(x_next + t);
-        xR = sload(x_next + t + 1);
-    }
-    zp = xL;  // z_0 = xL, as k_substitute
-    for (int k = 1; k < m; ++k) {
-        bar_sync_id(k, 2 * kWsLanes);
-        if (active && k < gap) {
-            const cx<R> bk = S.b(k);
-            cx<R> rhs = S.d(k);
-            if (k == gap - 1) rhs = csub(rhs, cmul(S.c(k), xR));
-            const cx<R> w = sload(sW + k * kWsLanes + lt);
-            zp = cmul(csub(rhs, cmul(bk, zp)), w);
-            sstore(S.at(1, k), zp);
-        }
-    }
-    if (!active) return;
-    ST* x = x0 + sys.at(si).row_off;
-    cx<R> y = zp;
-    put<ST, R>(x + J0 + gap - 1, y);
-    for (int k = gap - 2; k >= 1; --k) {
-        y = csub(sload(S.at(1, k)), cmul(sload(sC + k * kWsLanes + lt), y));
-        put<ST, R>(x + J0 + k, y);
-    }
-    put<ST, R>(x + J0, xL);
-    if (t == P - 1) put<ST, R>(x + J0 + gap, xR);
 }
 
 // ------------------------------------------------------------------ RS stage
@@ -986,10 +987,10 @@ k_base_cr_many(const BaseSys<R>* sys, int* status) {
 // kThreads threads.  A stage's ranges of kThreads blocks (a level's "CTAs" of the
 // per-level kernels, with the same exchange and slots) are dealt to the groups,
 // ranges g, g + groups, ...; the groups of a CTA run independently (named
-// barriers) and stage through disjoint parts of the shared memory.  Stages are
-// separated by a grid barrier; the RS stage is CTA 0's cyclic reduction.  The
-// per-block arithmetic and its order are those of k_reduce / k_substitute /
-// k_base_cr, so the results are the same bits.
+// barriers around their exchange arrays).  Stages are separated by a grid
+// barrier; the RS stage is CTA 0's cyclic reduction, the only user of the
+// dynamic shared memory.  The per-block arithmetic and its order are those of
+// k_reduce / k_substitute_rd / k_base_cr, so the results are the same bits.
 constexpr int kPGroups = 4;
 constexpr int kPThreads = kPGroups * kThreads;  // 512 = kCrThreads
 static_assert(kPThreads == kCrThreads, "the RS stage runs on one persistent CTA");
@@ -999,7 +1000,6 @@ template <class R> struct PLevel {
     LevelSource<R> src;             // the level's rows, bound to the system
     OneSys sys, next;               // entries of this level and of the next
     int m, m_next;                  // block sizes of this level and of the next
-    int sub_groups;                 // groups per CTA that substitute at once (their staging must fit)
     LevelPlanes<R> out;             // the next level's planes
     LevelSlot<R>* out_slot;         // the next level's CTA slots
     typename Store<R>::T* x;        // this level's solution
@@ -1062,8 +1062,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int exp
 template <class R>
 __global__ void __launch_bounds__(kPThreads, 1) k_levels(const __grid_constant__ PLevels<R> a) {
     grid_dep_enter();
-    typedef typename Store<R>::T ST;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ JDPart<R> xch[kPGroups][kThreads];
     const int grp = threadIdx.x / kThreads, tid = threadIdx.x % kThreads;
     const GroupSync gsync{1 + grp};
@@ -1083,13 +1081,8 @@ __global__ void __launch_bounds__(kPThreads, 1) k_levels(const __grid_constant__
     if (!grid_barrier(a.bar, a.expect, a.timeout_ns, a.status)) return;
     for (int l = a.nl - 1; l >= 0; --l) {
         const PLevel<R>& L = a.lv[l];
-        if (grp < L.sub_groups) {
-            ST* zs = reinterpret_cast<ST*>(smem_raw) + (size_t)grp * 2 * L.m * kThreads;
-            ST* cs = zs + (size_t)L.m * kThreads;
-            const int64_t s0 = (int64_t)grp * gridDim.x + blockIdx.x, st = (int64_t)gridDim.x * L.sub_groups;
-            for (int64_t c = s0; c < L.ranges; c += st)
-                substitute_cta<R>(c, tid, zs, cs, L.src, L.sys, L.next, L.m, L.x_next, L.x, a.status);
-        }
+        for (int64_t c = slot0; c < L.ranges; c += stride)
+            substitute_rd_cta<R>(c, tid, L.src, L.sys, L.next, L.m, L.x_next, L.x);
         if (l > 0 && !grid_barrier(a.bar, a.expect, a.timeout_ns, a.status)) return;
     }
 }

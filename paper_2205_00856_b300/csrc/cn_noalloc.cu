@@ -113,9 +113,10 @@ cudaError_t na_solve(unsigned char* base, const NaLevel* lv, int L, const ArrayS
                                                                           kNaBlock, kNaBlock, planes(l + 1), slot(l + 1),
                                                                           nullptr);
     k_base<R><<<1, 32, 0, st>>>(lsrc(L), xs(L), nullptr);
+    // levels >= 1 substitute from the RD results their reductions kept in place
     for (int l = L - 1; l >= 1; --l)
-        k_substitute<R, LevelSource<R>, OneSys, ST><<<grid(l), kThreads, smem, st>>>(
-            lsrc(l), na_sys(lv, l), na_sys(lv, l + 1), kNaBlock, xs(l + 1), xs(l), nullptr);
+        k_substitute_rd<R, OneSys><<<grid(l), kThreads, 0, st>>>(lsrc(l), na_sys(lv, l), na_sys(lv, l + 1),
+                                                                  kNaBlock, xs(l + 1), xs(l));
     k_substitute<R, ArraySource, OneSys, double2><<<grid(0), kThreads, smem, st>>>(
         src, na_sys(lv, 0), na_sys(lv, 1), kNaBlock, xs(1), x, nullptr);
     return cudaGetLastError();
