@@ -48,7 +48,7 @@ MAX_LEVELS = 24
 # Launch configuration for large single systems (N ~ 2^24, coefficient table on),
 # from block-size sweeps of the soft-Coulomb step on B300: (level-0 block, level-1
 # block, block of the deeper levels) per arithmetic.
-LARGE_GRID_BLOCKS = {ARITH_F64: (32, 16, 8), ARITH_DF64: (13, 10, 16)}
+LARGE_GRID_BLOCKS = {ARITH_F64: (32, 16, 8), ARITH_DF64: (13, 10, 8)}
 PROFILE_CLASSES = ("reduce_level0", "substitute_level0", "reduce_levels_ge1", "substitute_levels_ge1", "rs_stage",
                    "fused_level0", "levels_persistent")
 

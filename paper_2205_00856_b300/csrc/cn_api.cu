@@ -39,7 +39,8 @@ struct LevelData {
     LvlSys* d_sys = nullptr;  // device copy (batches)
     int64_t L = 0;            // entries per plane (levels >= 1): sum of the systems' slots
     void* rows = nullptr;     // planes b, a, c, d of L entries each (levels >= 1)
-    void* slot = nullptr;     // LevelSlot<R>[CTAs of the level below + 1]
+    void* slot = nullptr;     // LevelSlot<R>[exchange units of the level below + 1]
+    int slot_shift = 7;       // log2 blocks per exchange unit of the producer: 7 (a CTA), 5 (a warp)
     void* x = nullptr;        // Store<R>::T[rows_total]: solution (levels >= 1)
 };
 
@@ -174,6 +175,10 @@ void free_engine(Engine* p) {
     cudaFree(p->pbar);
 }
 
+// Slots of level l (l >= 1): one per exchange unit of the level below, at the
+// finest unit (a warp of 32 blocks), plus one.
+size_t slot_entries(const Engine* p, size_t l) { return (size_t)ceil_div(p->lv[l - 1].total, 32) + 1; }
+
 // Substitution scratch (two entries per row) for level-0 blocks longer than the
 // shared-memory staging allows; the levels below substitute from their kept RD
 // results and need none.
@@ -206,7 +211,7 @@ void dbg_engine(const Engine* p, DbgList& L) {
     for (size_t l = 1; l < p->lv.size(); ++l) {
         const LevelData& Lv = p->lv[l];
         L.add(Lv.rows, 4 * kCplx * (size_t)std::max<int64_t>(Lv.L, 1));
-        L.add(Lv.slot, 3 * kCplx * (grid_for(p->lv[l - 1].total) + 1));
+        L.add(Lv.slot, 3 * kCplx * slot_entries(p, l));
         L.add(Lv.x, kCplx * (size_t)Lv.rows_total);
     }
     for (const LevelData& Lv : p->lv) L.add(Lv.d_sys, sizeof(LvlSys) * (size_t)p->nsys);
@@ -364,7 +369,7 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
     cudaError_t e = cudaSuccess;
     for (size_t l = 1; l < p->lv.size() && e == cudaSuccess; ++l) {
         LevelData& L = p->lv[l];
-        const size_t nslot = grid_for(p->lv[l - 1].total) + 1;
+        const size_t nslot = slot_entries(p, l);
         p->workspace_bytes += (int64_t)(4 * kCplx * L.L + kCplx * L.rows_total + 3 * kCplx * nslot);
         e = cudaMalloc(&L.rows, 4 * kCplx * (size_t)std::max<int64_t>(L.L, 1));
         if (e == cudaSuccess) e = cudaMalloc(&L.slot, 3 * kCplx * nslot);
@@ -411,6 +416,7 @@ template <class R> LevelSource<R> level_source(const LevelData& L) {
     s.n = 0;
     s.prod = 0;
     s.stride = 0;
+    s.slot_shift = L.slot_shift;
     return s;
 }
 
@@ -562,6 +568,7 @@ cudaError_t set_smem_limits(const Engine* p) {
 template <class R>
 cudaError_t setup_persistent(Engine* p) {
     p->persistent = false;
+    for (LevelData& L : p->lv) L.slot_shift = 7;  // the per-level kernels' exchange unit
     // the default per arithmetic, from N = 2^24 measurements on B300: binary64
     // 1.515 (persistent) vs 1.520 ms per step (blocks 32 / 16 / 8), double-float
     // 0.460 vs 0.446 ms (blocks 13 / 10 / 16: the two-group kernels of levels 2
@@ -587,6 +594,8 @@ cudaError_t setup_persistent(Engine* p) {
     p->p_smem = smem;
     p->p_grid = per_sm * p->sms;
     p->persistent = true;
+    // levels 2 .. L-1 are produced by k_levels' warp-unit reductions
+    for (size_t l = 2; l < p->lv.size(); ++l) p->lv[l].slot_shift = 5;
     return cudaSuccess;
 }
 
@@ -666,7 +675,10 @@ cudaError_t persistent_levels(Engine* p, cudaStream_t st) {
         q.out_slot = slot_of<R>(N);
         q.x = x_of<R>(Lv);
         q.x_next = x_of<R>(N);
-        q.ranges = (int64_t)grid_for(Lv.total);
+        q.units = ceil_div(Lv.total, 32);
+        // a level of at most one unit per CTA reduces on four warps a unit
+        q.split4 = (Lv.m >= 2 && Lv.m <= kSplitRowsMax && q.units <= p->p_grid &&
+                    split4_entries(Lv.m) * kCplx <= p->p_smem) ? 1 : 0;
     }
     const LevelData& B = p->lv[L - 1];
     a.base = level_source<R>(B).bind(B.sys[0]);
@@ -1038,7 +1050,7 @@ cn_status fill_workspace(Engine* p, int byte) {
     for (size_t l = 1; l < p->lv.size(); ++l) {
         const LevelData& L = p->lv[l];
         fill(L.rows, 4 * kCplx * (size_t)std::max<int64_t>(L.L, 1));
-        fill(L.slot, 3 * kCplx * (grid_for(p->lv[l - 1].total) + 1));
+        fill(L.slot, 3 * kCplx * slot_entries(p, l));
         fill(L.x, kCplx * (size_t)L.rows_total);
     }
     const size_t zc_entries = zc_entries_of(p);

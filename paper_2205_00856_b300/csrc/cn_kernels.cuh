@@ -197,6 +197,7 @@ template <class R> struct LevelSource {
     int64_t n;                // rows of the bound system
     int64_t prod;             // global block index that produced row 0 of the bound system
     int64_t stride;           // layout of the bound system (LvlSys)
+    int slot_shift;           // log2 of the producer's exchange unit: 7 (kThreads blocks), 5 (a warp)
     __host__ __device__ __forceinline__ LevelSource bind(const LvlSys& e) const {
         LevelSource r = *this;
         r.b = b + e.slot_off;
@@ -215,8 +216,8 @@ template <class R> struct LevelSource {
         r.c = sload(q + 2 * L);
         r.d = sload(q + 3 * L);
         const int64_t g = prod + i;
-        if (i > 0 && i < n - 1 && (g % kThreads) == 0) {
-            const LevelSlot<R>* s = slot + g / kThreads;
+        if (i > 0 && i < n - 1 && (g & ((INT64_C(1) << slot_shift) - 1)) == 0) {
+            const LevelSlot<R>* s = slot + (g >> slot_shift);
             r.b = sload(&s->b);
             r.a = cadd(r.a, sload(&s->a));
             r.d = cadd(r.d, sload(&s->d));
@@ -280,16 +281,9 @@ template <class R> struct RowSink {
 // the first kThreads * sizeof(JDPart) bytes of `scratch` (the caller's dynamic
 // shared memory, free once every thread is past this call's first barrier)
 // instead of a static array, so the kernel holds no shared memory beside its tile.
-// Barriers over the threads that share one exchange: the whole CTA, or one
-// group of kThreads threads (named barrier 1 + group) of a larger CTA.
+// The barrier over the threads that share one exchange: the whole CTA.
 struct CtaSync {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
-};
-struct GroupSync {
-    int id;
-    __device__ __forceinline__ void operator()() const {
-        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kThreads) : "memory");
-    }
 };
 
 // The exchange of kThreads blocks that form the range `cta` of the level: xch is
@@ -341,14 +335,26 @@ __device__ __forceinline__ void write_reduced_row(bool active, int64_t t, int64_
 
 // ------------------------------------------------------------------ generic reduction
 // One thread per block: RD + JD downwards with RU + JU accumulated on the way.
-// The blocks of range `cta` (kThreads consecutive blocks of the level, thread tid
-// taking block cta kThreads + tid), exchanging through xch with barrier sync.
-template <class R, class Src, class Map, class Sync>
-__device__ __forceinline__ void reduce_cta(int64_t cta, int tid, JDPart<R>* xch, Sync sync, Src src0, Map sys,
-                                           Map next, int m, int m_next, LevelPlanes<R> out, LevelSlot<R>* out_slot,
-                                           int* status) {
-    const int64_t g = cta * kThreads + tid;
+// reduce_block reduces block g of the level (all systems' blocks numbered
+// consecutively); its writers then combine each block's JU part with the JD
+// part of the block before it: reduce_cta for a range of kThreads blocks that
+// exchange through shared memory, reduce_warp for 32 blocks that exchange by
+// shuffles.
+template <class R> struct BlockOut {
+    bool active;
+    int si;             // system of the block
+    int64_t t, P;       // block index in the system, blocks of the system
+    JDPart<R> jd;       // JD contribution to row J_{t+1} (next level's row t + 1)
+    cx<R> A0, D0;       // row J_t's own diagonal and right-hand side
+    cx<R> JUa, JUc, JUd;
+    cx<R> Ag, Dg;       // row J_P of the system (last block only)
+};
+
+template <class R, class Src, class Map>
+__device__ __forceinline__ BlockOut<R> reduce_block(int64_t g, Src src0, Map sys, int m, int* status) {
+    BlockOut<R> o;
     const bool active = g < sys.total();
+    o.active = active;
     bool ok = true;
     cx<R> JUa = czero<R>(), JUc = czero<R>(), JUd = czero<R>(), A0 = czero<R>(), D0 = czero<R>();
     cx<R> Ag = czero<R>(), Dg = czero<R>();
@@ -413,9 +419,77 @@ __device__ __forceinline__ void reduce_cta(int64_t cta, int tid, JDPart<R>* xch,
         JUa = cmul(r0u, nb);
         JUd = cmul(r0u, nd);
     }
-    write_reduced_row_at<R>(xch, tid, cta, sync, active, t, P, jd, A0, D0, JUa, JUc, JUd, Ag, Dg,
-                            RowSink<R>(out, next.at(si), m_next), out_slot);
     if (!ok) flag_error(status, kStatusNonfinite);
+    o.si = si;
+    o.t = t;
+    o.P = P;
+    o.jd = jd;
+    o.A0 = A0;
+    o.D0 = D0;
+    o.JUa = JUa;
+    o.JUc = JUc;
+    o.JUd = JUd;
+    o.Ag = Ag;
+    o.Dg = Dg;
+    return o;
+}
+
+// The blocks of range `cta` (kThreads consecutive blocks of the level, thread tid
+// taking block cta kThreads + tid), exchanging through xch with barrier sync.
+template <class R, class Src, class Map, class Sync>
+__device__ __forceinline__ void reduce_cta(int64_t cta, int tid, JDPart<R>* xch, Sync sync, Src src0, Map sys,
+                                           Map next, int m, int m_next, LevelPlanes<R> out, LevelSlot<R>* out_slot,
+                                           int* status) {
+    const BlockOut<R> o = reduce_block<R>(cta * kThreads + tid, src0, sys, m, status);
+    write_reduced_row_at<R>(xch, tid, cta, sync, o.active, o.t, o.P, o.jd, o.A0, o.D0, o.JUa, o.JUc, o.JUd, o.Ag,
+                            o.Dg, RowSink<R>(out, next.at(o.si), m_next), out_slot);
+}
+
+// The 32 blocks of warp unit `u` (lane l taking block 32 u + l): the JD part
+// crosses to the next lane by a shuffle, and the last lane's goes to slot u + 1,
+// which the next level's reader adds to row 32 (u + 1) (LevelSource with
+// slot_shift 5).  Every lane of the warp calls it.  The sums are formed as in
+// write_reduced_row_at ((A0 + JU) + JD, on either path), so the rows are the
+// same bits.
+template <class T> __device__ __forceinline__ T shfl_up_one(const T& v) {
+    static_assert(sizeof(T) % sizeof(int) == 0, "shuffled in 32-bit words");
+    constexpr int nw = (int)(sizeof(T) / sizeof(int));
+    int w[nw];
+    memcpy(w, &v, sizeof(T));
+#pragma unroll
+    for (int i = 0; i < nw; ++i) w[i] = __shfl_up_sync(0xffffffffu, w[i], 1);
+    T r;
+    memcpy(&r, w, sizeof(T));
+    return r;
+}
+
+template <class R, class Map>
+__device__ __forceinline__ void write_unit_rows(int64_t u, int lane, const BlockOut<R>& o, Map next, int m_next,
+                                                LevelPlanes<R> out, LevelSlot<R>* out_slot) {
+    __syncwarp();
+    const JDPart<R> pj = shfl_up_one(o.jd);
+    if (!o.active) return;
+    const RowSink<R> sink(out, next.at(o.si), m_next);
+    if (lane > 0 && o.t > 0)
+        sink.put(o.t, pj.b, cadd(cadd(o.A0, o.JUa), pj.a), o.JUc, cadd(cadd(o.D0, o.JUd), pj.d));
+    else
+        sink.put(o.t, czero<R>(), cadd(o.A0, o.JUa), o.JUc, cadd(o.D0, o.JUd));
+    if (o.t == o.P - 1) {
+        sink.put(o.P, o.jd.b, cadd(o.Ag, o.jd.a), czero<R>(), cadd(o.Dg, o.jd.d));
+    } else if (lane == 31) {
+        LevelSlot<R> s;
+        sstore(&s.b, o.jd.b);
+        sstore(&s.a, o.jd.a);
+        sstore(&s.d, o.jd.d);
+        dbg_st(&out_slot[u + 1], s);
+    }
+}
+
+template <class R, class Src, class Map>
+__device__ __forceinline__ void reduce_warp(int64_t u, int lane, Src src0, Map sys, Map next, int m, int m_next,
+                                            LevelPlanes<R> out, LevelSlot<R>* out_slot, int* status) {
+    const BlockOut<R> o = reduce_block<R>(u * 32 + lane, src0, sys, m, status);
+    write_unit_rows<R>(u, lane, o, next, m_next, out, out_slot);
 }
 
 template <class R, class Src, class Map>
@@ -509,10 +583,9 @@ k_substitute(Src src0, Map sys, Map next, int m, const typename Store<R>::T* x_n
 // reciprocal), and no staging.  (The rows' own a, b, d are gone: a level is reduced and
 // substituted once per solve.)
 template <class R, class Map, class XT>
-__device__ __forceinline__ void substitute_rd_cta(int64_t cta, int tid, const LevelSource<R>& src0, Map sys,
-                                                  Map next, int m, const typename Store<R>::T* x_next0, XT* x0) {
+__device__ __forceinline__ void substitute_rd_block(int64_t g, const LevelSource<R>& src0, Map sys, Map next, int m,
+                                                    const typename Store<R>::T* x_next0, XT* x0) {
     typedef typename Store<R>::T ST;
-    const int64_t g = cta * kThreads + tid;
     if (g >= sys.total()) return;
     const int si = sys.find(g);
     const LvlSys& e = sys.at(si);
@@ -542,7 +615,7 @@ __global__ void __launch_bounds__(kThreads)
 k_substitute_rd(LevelSource<R> src0, Map sys, Map next, int m, const typename Store<R>::T* x_next0,
                 typename Store<R>::T* x0) {
     grid_dep_enter();
-    substitute_rd_cta<R>(blockIdx.x, threadIdx.x, src0, sys, next, m, x_next0, x0);
+    substitute_rd_block<R>((int64_t)blockIdx.x * kThreads + threadIdx.x, src0, sys, next, m, x_next0, x0);
 }
 
 // Same substitution for blocks longer than the shared-memory staging allows:
@@ -980,19 +1053,199 @@ k_base_cr_many(const BaseSys<R>* sys, int* status) {
     cr_solve<R>(b.src, b.x, status);
 }
 
+// ------------------------------------------------------------------ small levels: one unit, four warps
+// On a level with at most one warp unit per CTA, one warp walking 32 blocks is
+// bound by its own instruction stream: a B300 SM sub-partition retires one
+// binary64 warp instruction about every 64 clocks, however few lanes are busy,
+// so the ~39 operations of a row cost ~2.9k clocks.  Here four warps of the CTA
+// (four sub-partitions) share the unit's rows: warp 0 the pivot chain (r_k and
+// 1 / a_k: 15 operations a row), warp 1 the fill-in and right-hand side (b^RD,
+// d^RD, and the kept RD results), warp 2 RU's product Q, warp 3 RU's sums, each
+// a row behind the one it reads through shared memory, with two named barriers
+// a row (ids 1 .. 2 (m - 1); id 15 frames the unit); the JD and JU products at
+// the end are shared out the same way.  The operations and their order are
+// those of reduce_block, so the rows are the same bits.
+constexpr int kSplitRowsMax = 8;  // 2 (m - 1) row barriers <= 14
+constexpr int kSplitThreads = 128;
+// shared memory of one unit, in storage entries: staged rows 0..m (4 fields),
+// r_k, 1 / a_k, b^RD_k, d^RD_k, Q_k (rows 0..m) and seven final values
+__host__ __device__ constexpr size_t split4_entries(int m) { return (9 * (size_t)(m + 1) + 7) * 32; }
+
+template <class R>
+__device__ __forceinline__ void reduce_unit4(int64_t u, int warp, int lane, typename Store<R>::T* smem,
+                                             const LevelSource<R>& src0, OneSys sys, OneSys next, int m, int m_next,
+                                             LevelPlanes<R> out, LevelSlot<R>* out_slot, int* status) {
+    typedef typename Store<R>::T ST;
+    const WsRows<R> S{smem, m + 1, lane};
+    ST* const sR = smem + 4 * (m + 1) * 32;
+    ST* const sW = sR + (m + 1) * 32;
+    ST* const sB = sW + (m + 1) * 32;
+    ST* const sD = sB + (m + 1) * 32;
+    ST* const sQ = sD + (m + 1) * 32;
+    ST* const sF = sQ + (m + 1) * 32;  // final values, entry f at f * 32 + lane
+    auto at = [lane](ST* base, int k) { return base + k * 32 + lane; };
+    const int64_t g = u * 32 + lane;
+    const bool active = g < sys.total();
+    int64_t t = 0, P = 0, J0 = 0;
+    int gap = 0;
+    LevelSource<R> src = src0;
+    __syncwarp();
+    bar_sync_id(15, kSplitThreads);  // the previous unit's rows are written
+    if (active) {
+        const LvlSys& e = sys.at(0);
+        src = src0.bind(e);
+        P = e.P;
+        t = g - e.blk_off;
+        J0 = joint_line(t, P, m, e.n);
+        gap = (int)(joint_line(t + 1, P, m, e.n) - J0);
+        // the warps stage rows warp, warp + 4, warp + 8 of 0..gap (row gap: row 0 of the
+        // next block), every load in flight before the first store
+        Row<R> rr[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int k = warp + 4 * j;
+            if (k <= gap) rr[j] = k < gap ? src.template row<R>(t, k, J0 + k) : src.template row<R>(t + 1, 0, J0 + k);
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            if (warp + 4 * j <= gap) S.put(warp + 4 * j, rr[j]);
+    }
+    __syncwarp();
+    bar_sync_id(15, kSplitThreads);
+    if (warp == 0) {
+        bool ok = true;
+        cx<R> w = czero<R>(), cprev = czero<R>();
+        if (active) {
+            w = crcp(S.a(1), ok);
+            sstore(at(sW, 1), w);
+            cprev = S.c(1);
+        }
+        for (int k = 2; k <= m; ++k) {
+            if (active && k <= gap) {
+                // RD (k < gap) and JD (k = gap): r = -b_k / a_{k-1}; a_k += r c_{k-1}
+                const cx<R> r = cneg(cmul(S.b(k), w));
+                sstore(at(sR, k), r);
+                if (k < gap) {
+                    w = crcp(cfma(S.a(k), r, cprev), ok);
+                    sstore(at(sW, k), w);
+                    cprev = S.c(k);
+                }
+            }
+            __syncwarp();
+            bar_arrive_id(k - 1, 3 * 32);
+        }
+        // JD on row J_{t+1}: a += r c_{g-1}
+        if (active) sstore(at(sF, 0), cmul(sload(at(sR, gap)), cprev));
+        if (!ok) flag_error(status, kStatusNonfinite);
+    } else if (warp == 1) {
+        cx<R> bRD = czero<R>(), dRD = czero<R>();
+        if (active) {
+            bRD = S.b(1);
+            dRD = S.d(1);
+        }
+        for (int k = 2; k <= m; ++k) {
+            __syncwarp();
+            bar_sync_id(k - 1, 3 * 32);
+            if (active && k == 2) src.keep_rd(t, 1, J0 + 1, S.b(1), sload(at(sW, 1)), S.d(1));
+            if (active && k < gap) {
+                const cx<R> r = sload(at(sR, k));
+                bRD = cmul(r, bRD);
+                dRD = cfma(S.d(k), r, dRD);
+                sstore(at(sB, k), bRD);
+                sstore(at(sD, k), dRD);
+                src.keep_rd(t, k, J0 + k, bRD, sload(at(sW, k)), dRD);
+            }
+            __syncwarp();
+            bar_arrive_id(m - 2 + k, 3 * 32);
+        }
+        // JD on row J_{t+1}: b = r b_{g-1};  d += r d_{g-1}  (r written before the last barrier read)
+        if (active) {
+            const cx<R> r = sload(at(sR, gap));
+            sstore(at(sF, 1), cmul(r, bRD));
+            sstore(at(sF, 2), cmul(r, dRD));
+        }
+    } else if (warp == 2) {
+        cx<R> Q = cfrom<R>(1.0, 0.0), cprev = czero<R>();
+        if (active) cprev = S.c(1);
+        for (int k = 2; k <= m; ++k) {
+            __syncwarp();
+            bar_sync_id(k - 1, 3 * 32);
+            // JU on row J_t with row 1 after RU: r = -c_0 / a_1 (for warp 3, which reads
+            // it after its first barrier)
+            if (active && k == 2) sstore(at(sF, 5), cneg(cmul(S.c(0), sload(at(sW, 1)))));
+            if (active && k < gap) {
+                // RU coefficient of row k-1: rho_{k-1} = -c_{k-1} / a_k
+                Q = cmul(Q, cneg(cmul(cprev, sload(at(sW, k)))));
+                sstore(at(sQ, k), Q);
+                cprev = S.c(k);
+            }
+            __syncwarp();
+            bar_arrive_id(m - 2 + k, 3 * 32);
+        }
+        if (active) sstore(at(sF, 3), cmul(sload(at(sF, 5)), cmul(Q, cprev)));  // c_1 after RU = Q_{g-1} c_{g-1}
+    } else {
+        cx<R> nb = czero<R>(), nd = czero<R>();
+        if (active) {
+            nb = S.b(1);
+            nd = S.d(1);
+        }
+        for (int k = 2; k <= m; ++k) {
+            __syncwarp();
+            bar_sync_id(m - 2 + k, 3 * 32);
+            if (active && k < gap) {
+                const cx<R> Q = sload(at(sQ, k));
+                nb = cfma(nb, Q, sload(at(sB, k)));
+                nd = cfma(nd, Q, sload(at(sD, k)));
+            }
+        }
+        if (active) {
+            const cx<R> r0u = sload(at(sF, 5));
+            sstore(at(sF, 4), cmul(r0u, nb));
+            sstore(at(sF, 6), cmul(r0u, nd));
+        }
+    }
+    __syncwarp();
+    bar_sync_id(15, kSplitThreads);
+    if (warp != 3) return;
+    BlockOut<R> o;
+    o.active = active;
+    o.si = 0;
+    o.t = t;
+    o.P = P;
+    o.jd.b = czero<R>(); o.jd.a = czero<R>(); o.jd.d = czero<R>();
+    o.A0 = o.D0 = o.JUa = o.JUc = o.JUd = o.Ag = o.Dg = czero<R>();
+    if (active) {
+        o.jd.a = sload(at(sF, 0));
+        o.jd.b = sload(at(sF, 1));
+        o.jd.d = sload(at(sF, 2));
+        o.JUc = sload(at(sF, 3));
+        o.JUa = sload(at(sF, 4));
+        o.JUd = sload(at(sF, 6));
+        o.Ag = S.a(gap);
+        o.Dg = S.d(gap);
+        o.A0 = S.a(0);
+        o.D0 = S.d(0);
+    }
+    write_unit_rows<R>(u, lane, o, next, m_next, out, out_slot);
+}
+
 // ------------------------------------------------------------------ levels >= 1 in one persistent launch
 // Every stage below level 0 of one system -- the reductions of levels 1 .. L-2,
 // the RS stage and the substitutions back up -- in one cooperative launch: a
-// grid of CTAs that are all resident at once, each of kPGroups groups of
-// kThreads threads.  A stage's ranges of kThreads blocks (a level's "CTAs" of the
-// per-level kernels, with the same exchange and slots) are dealt to the groups,
-// ranges g, g + groups, ...; the groups of a CTA run independently (named
-// barriers around their exchange arrays).  Stages are separated by a grid
-// barrier; the RS stage is CTA 0's cyclic reduction, the only user of the
-// dynamic shared memory.  The per-block arithmetic and its order are those of
-// k_reduce / k_substitute_rd / k_base_cr, so the results are the same bits.
-constexpr int kPGroups = 4;
-constexpr int kPThreads = kPGroups * kThreads;  // 512 = kCrThreads
+// grid of CTAs that are all resident at once, 16 warps each.  A stage's work is
+// dealt in warp units of 32 consecutive blocks, CTA first (unit u to CTA
+// u mod grid, warp u / grid): B300's FP64 pipe is shared by a multiprocessor's
+// warps (~2 operations per clock per SM), so a level of a few thousand blocks
+// runs fastest spread one warp per SM, and a level of tens of thousands evenly
+// over all SMs.  In a reduction the JD part crosses lanes by a shuffle and
+// warp units by the next level's slots (reduce_warp: the levels this kernel
+// produces have slot_shift 5; level 1, produced by the level-0 kernel, keeps
+// one slot per kThreads blocks).  Stages are separated by a grid barrier; the RS
+// stage is CTA 0's cyclic reduction, the only user of the dynamic shared
+// memory.  The per-block arithmetic and its order are those of k_reduce /
+// k_substitute_rd / k_base_cr, so the results are the same bits.
+constexpr int kPWarps = 16;
+constexpr int kPThreads = kPWarps * 32;  // 512 = kCrThreads
 static_assert(kPThreads == kCrThreads, "the RS stage runs on one persistent CTA");
 constexpr int kStatusTimeout = 5;  // cn_status CN_ERR_TIMEOUT
 
@@ -1004,7 +1257,8 @@ template <class R> struct PLevel {
     LevelSlot<R>* out_slot;         // the next level's CTA slots
     typename Store<R>::T* x;        // this level's solution
     const typename Store<R>::T* x_next;  // the next level's solution
-    int64_t ranges;                 // ceil(P / kThreads)
+    int64_t units;                  // ceil(P / 32)
+    int split4;                     // reduce one unit per CTA on four warps (reduce_unit4)
 };
 template <class R> struct PLevels {
     PLevel<R> lv[24];               // levels 1 .. nl (index l - 1)
@@ -1062,18 +1316,20 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int exp
 template <class R>
 __global__ void __launch_bounds__(kPThreads, 1) k_levels(const __grid_constant__ PLevels<R> a) {
     grid_dep_enter();
-    __shared__ JDPart<R> xch[kPGroups][kThreads];
-    const int grp = threadIdx.x / kThreads, tid = threadIdx.x % kThreads;
-    const GroupSync gsync{1 + grp};
-    // ranges go to the CTAs first (range c to CTA c mod grid, group c / grid): a
-    // small level spreads over as many multiprocessors as it has ranges
-    const int64_t slot0 = (int64_t)grp * gridDim.x + blockIdx.x, stride = (int64_t)gridDim.x * kPGroups;
+    const int lane = threadIdx.x & 31;
+    const int64_t u0 = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x, ustride = (int64_t)gridDim.x * kPWarps;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typedef typename Store<R>::T ST;
     for (int l = 0; l < a.nl; ++l) {
         const PLevel<R>& L = a.lv[l];
-        for (int64_t c = slot0; c < L.ranges; c += stride) {
-            reduce_cta<R>(c, tid, xch[grp], gsync, L.src, L.sys, L.next, L.m, L.m_next, L.out, L.out_slot,
-                          a.status);
-            gsync();  // the group's exchange array is free again
+        if (L.split4) {
+            if (threadIdx.x < kSplitThreads)
+                for (int64_t u = blockIdx.x; u < L.units; u += gridDim.x)
+                    reduce_unit4<R>(u, threadIdx.x >> 5, lane, reinterpret_cast<ST*>(smem_raw), L.src, L.sys, L.next,
+                                    L.m, L.m_next, L.out, L.out_slot, a.status);
+        } else {
+            for (int64_t u = u0; u < L.units; u += ustride)
+                reduce_warp<R>(u, lane, L.src, L.sys, L.next, L.m, L.m_next, L.out, L.out_slot, a.status);
         }
         if (!grid_barrier(a.bar, a.expect, a.timeout_ns, a.status)) return;
     }
@@ -1081,8 +1337,8 @@ __global__ void __launch_bounds__(kPThreads, 1) k_levels(const __grid_constant__
     if (!grid_barrier(a.bar, a.expect, a.timeout_ns, a.status)) return;
     for (int l = a.nl - 1; l >= 0; --l) {
         const PLevel<R>& L = a.lv[l];
-        for (int64_t c = slot0; c < L.ranges; c += stride)
-            substitute_rd_cta<R>(c, tid, L.src, L.sys, L.next, L.m, L.x_next, L.x);
+        for (int64_t u = u0; u < L.units; u += ustride)
+            substitute_rd_block<R>(u * 32 + lane, L.src, L.sys, L.next, L.m, L.x_next, L.x);
         if (l > 0 && !grid_barrier(a.bar, a.expect, a.timeout_ns, a.status)) return;
     }
 }

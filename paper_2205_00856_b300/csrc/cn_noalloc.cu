@@ -102,6 +102,7 @@ cudaError_t na_solve(unsigned char* base, const NaLevel* lv, int L, const ArrayS
         s.n = lv[l].n;
         s.prod = 0;
         s.stride = 0;
+        s.slot_shift = 7;  // k_reduce: one slot per kThreads blocks
         return s;
     };
     auto grid = [&](int l) { return (unsigned)na_ceil_div(lv[l].P, kThreads); };
