@@ -570,8 +570,8 @@ cudaError_t setup_persistent(Engine* p) {
     p->persistent = false;
     for (LevelData& L : p->lv) L.slot_shift = 7;  // the per-level kernels' exchange unit
     // the default per arithmetic, from N = 2^24 measurements on B300: binary64
-    // 1.515 (persistent) vs 1.520 ms per step (blocks 32 / 16 / 8), double-float
-    // 0.460 vs 0.446 ms (blocks 13 / 10 / 16: the two-group kernels of levels 2
+    // 1.402 (persistent) vs 1.422 ms per step (blocks 32 / 16 / 8), double-float
+    // 0.459 vs 0.442 ms (blocks 13 / 10 / 8: the two-group kernels of levels 2
     // and 3 and the programmatic launch overlap outweigh the saved launches)
     const int fl = p->desc.flags;
     const bool want = (fl & CN_FLAG_PERSISTENT_LEVELS) ||
