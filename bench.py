@@ -906,7 +906,9 @@ def main():
                     help="tabulate the static diagonal part 2 + 2 dx^2 V(x) once (default)")
     ap.add_argument("--no-coeff-table", dest="coeff_table", action="store_false",
                     help="regenerate V(x) every step instead")
-    ap.add_argument("--n", type=int, default=1 << 24, help="grid points (profiling runs use smaller grids)")
+    # --points: the same under torchrun, whose own option prefixes make "--n" ambiguous
+    ap.add_argument("--n", "--points", dest="n", type=int, default=1 << 24,
+                    help="grid points (profiling runs use smaller grids)")
     # 1000 (the propagation's length): one call for the whole run
     ap.add_argument("--steps-per-call", type=int, default=1000,
                     help="CN steps per cn_step call in the timed region (1: one call per step)")

@@ -1055,10 +1055,10 @@ k_base_cr_many(const BaseSys<R>* sys, int* status) {
 
 // ------------------------------------------------------------------ small levels: one unit, four warps
 // On a level with at most one warp unit per CTA, one warp walking 32 blocks is
-// bound by its own instruction stream: a B300 SM sub-partition retires one
-// binary64 warp instruction about every 64 clocks, however few lanes are busy,
-// so the ~39 operations of a row cost ~2.9k clocks.  Here four warps of the CTA
-// (four sub-partitions) share the unit's rows: warp 0 the pivot chain (r_k and
+// bound by its own in-order stream of dependent binary64 operations: on B300 a
+// dependent binary64 result takes ~64 clocks however few lanes are busy, so the
+// ~39 operations of a row cost ~2.9k clocks.  Here four warps of the CTA share
+// the unit's rows: warp 0 the pivot chain (r_k and
 // 1 / a_k: 15 operations a row), warp 1 the fill-in and right-hand side (b^RD,
 // d^RD, and the kept RD results), warp 2 RU's product Q, warp 3 RU's sums, each
 // a row behind the one it reads through shared memory, with two named barriers
@@ -1098,17 +1098,9 @@ __device__ __forceinline__ void reduce_unit4(int64_t u, int warp, int lane, type
         t = g - e.blk_off;
         J0 = joint_line(t, P, m, e.n);
         gap = (int)(joint_line(t + 1, P, m, e.n) - J0);
-        // the warps stage rows warp, warp + 4, warp + 8 of 0..gap (row gap: row 0 of the
-        // next block), every load in flight before the first store
-        Row<R> rr[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const int k = warp + 4 * j;
-            if (k <= gap) rr[j] = k < gap ? src.template row<R>(t, k, J0 + k) : src.template row<R>(t + 1, 0, J0 + k);
-        }
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            if (warp + 4 * j <= gap) S.put(warp + 4 * j, rr[j]);
+        // the warps stage rows warp, warp + 4, ... of 0..gap (row gap: row 0 of the next block)
+        for (int k = warp; k <= gap; k += 4)
+            S.put(k, k < gap ? src.template row<R>(t, k, J0 + k) : src.template row<R>(t + 1, 0, J0 + k));
     }
     __syncwarp();
     bar_sync_id(15, kSplitThreads);

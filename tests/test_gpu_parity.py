@@ -473,12 +473,15 @@ def test_plans_with_different_blocks_coexist():
 
 
 @pytest.mark.parametrize("n,blocks", [(20011, (8, 8, 8)), (200001, (8, 8, 8)), (1000003, (13, 10, 12)),
-                                      (400009, (4, 4, 3)), (1 << 22, None)])
+                                      (400009, (4, 4, 3)), (100003, (5, 6, 7)), (3000017, (16, 16, 6)),
+                                      (1 << 22, None)])
 @pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
 def test_persistent_levels_match_per_level_launches_bitwise(n, blocks, arith):
     """Every stage below level 0 in one persistent cooperative launch gives the
     bits of one launch per stage and level (same per-block arithmetic, same
-    order), in multi-step calls and single steps, and matches the oracle."""
+    order), in multi-step calls and single steps, and matches the oracle.  The
+    shapes cover warp units over many CTAs, levels reduced on four warps a unit
+    (blocks of 3 to 8 rows, ragged tails of 2-row blocks) and longer level blocks."""
     m0, m1, ml = cnb.LARGE_GRID_BLOCKS[arith] if blocks is None else blocks
     cfg = W.soft_coulomb_config(n=n, nsteps=4)
     psi0 = W.full_support_state(n, cfg["dx"], cfg["x_min"], seed=7)
@@ -505,7 +508,7 @@ def test_persistent_levels_match_per_level_launches_bitwise(n, blocks, arith):
     per_level.check()
     assert np.array_equal(a, b)
     assert np.array_equal(one.cpu().numpy(), one2.cpu().numpy())
-    if n <= 1000003:
+    if n <= 3000017:
         ref = oracle.cn_run(oracle_problem(cfg), psi0, 4, E_mid=E.cpu().numpy())
         assert rel(a, ref) <= 1e-11
     pers.close()

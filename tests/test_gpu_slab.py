@@ -136,7 +136,7 @@ def _bench_line(out: str) -> dict:
     return json.loads(lines[0])
 
 
-BENCH_ARGS = ["--sharded", "--n", "200003", "--steps", "20", "--warmup", "3", "--e2e-calls", "1",
+BENCH_ARGS = ["--sharded", "--points", "200003", "--steps", "20", "--warmup", "3", "--e2e-calls", "1",
               "--e2e-inner", "5"]
 
 
