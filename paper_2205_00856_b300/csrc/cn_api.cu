@@ -482,11 +482,11 @@ size_t fused_smem(int m) { return (size_t)(m + 2) * kTileStride * kCplx; }  // r
 size_t cr_smem() { return 6 * (size_t)kCrMax * kCplx; }
 size_t ws_reduce_smem(int m) { return ws_reduce_entries(m) * kCplx; }
 
-// The two-group kernels take the reduced levels below level 1 that need at most
-// one CTA of kThreads blocks per multiprocessor, with blocks of at most
-// kWsRowsMax rows.  (Level 1 stays on the one-thread-per-block kernels: where it
-// qualifies, at n = 2^20, the two-group kernels there made the step 5 % slower
-// on B300, while levels 2 and 3 at n = 2^24 gain 1.3 % of the step.)
+// In per-level launches the two-group reduction takes the levels below level 1
+// that need at most one CTA of kThreads blocks per multiprocessor, with blocks of
+// at most kWsRowsMax rows.  (Level 1 stays on the one-thread-per-block kernel:
+// where it qualifies, at n = 2^20, the two-group kernels there made the step 5 %
+// slower on B300, while levels 2 and 3 at n = 2^24 gained 1.3 % of the step.)
 bool two_group_level(const Engine* p, size_t l) {
     const LevelData& L = p->lv[l];
     return l >= 2 && L.m <= kWsRowsMax && L.total > 0 && (int64_t)grid_for(L.total) <= (int64_t)p->sms;
