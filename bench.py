@@ -185,7 +185,8 @@ def ncu_traffic(kernel_class: str, arith: str, n: int, m: int, table: bool = Fal
 class ClockSampler:
     """SM clock, its maximum and the active clock-event (throttle) reasons, sampled
     every 50 ms in a background thread during the timed region: through NVML
-    (what nvidia-smi reads), else by one-shot nvidia-smi queries (a long-running
+    (what nvidia-smi reads; its Python binding, else its C library by ctypes), else
+    by one-shot nvidia-smi queries (a long-running
     `nvidia-smi -lms` writes through a block buffer into a pipe and loses its
     last samples when stopped).  Reading only: no setting is changed."""
 
@@ -220,6 +221,42 @@ class ClockSampler:
                     {nm for nm, b in zip(self.NAMES, bits) if r & b})
         return read
 
+    # NVML's C API (nvml.h) through ctypes, for hosts without its Python binding:
+    # the SM clock id and the clock-event reason bits of NAMES
+    NVML_CLOCK_SM = 1
+    NVML_REASON_BITS = (0x8, 0x40, 0x20, 0x4)
+
+    def _nvml_ctypes_reader(self):
+        import ctypes as C
+        lib = C.CDLL("libnvidia-ml.so.1")
+        dev_p, uint_p = C.POINTER(C.c_void_p), C.POINTER(C.c_uint)
+        lib.nvmlInit_v2.restype = C.c_int
+        lib.nvmlDeviceGetHandleByUUID.argtypes = [C.c_char_p, dev_p]
+        lib.nvmlDeviceGetHandleByPciBusId_v2.argtypes = [C.c_char_p, dev_p]
+        lib.nvmlDeviceGetMaxClockInfo.argtypes = [C.c_void_p, C.c_int, uint_p]
+        lib.nvmlDeviceGetClockInfo.argtypes = [C.c_void_p, C.c_int, uint_p]
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        if reasons is None:
+            reasons = lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        reasons.argtypes = [C.c_void_p, C.POINTER(C.c_ulonglong)]
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit_v2 failed")
+        h = C.c_void_p()
+        if lib.nvmlDeviceGetHandleByUUID(self.uuid.encode(), C.byref(h)) != 0:
+            if not self.pci or lib.nvmlDeviceGetHandleByPciBusId_v2(self.pci.encode(), C.byref(h)) != 0:
+                raise OSError("no NVML handle for the device")
+        v = C.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(h, self.NVML_CLOCK_SM, C.byref(v)) != 0:
+            raise OSError("nvmlDeviceGetMaxClockInfo failed")
+        mx = float(v.value)
+
+        def read():
+            c, r = C.c_uint(), C.c_ulonglong()
+            if lib.nvmlDeviceGetClockInfo(h, self.NVML_CLOCK_SM, C.byref(c)) != 0 or reasons(h, C.byref(r)) != 0:
+                raise OSError("NVML query failed")
+            return (float(c.value), mx, {nm for nm, b in zip(self.NAMES, self.NVML_REASON_BITS) if r.value & b})
+        return read
+
     def _smi_reader(self):
         def read():
             out = subprocess.run(["nvidia-smi", "-i", self.uuid, f"--query-gpu={self.Q}",
@@ -230,7 +267,8 @@ class ClockSampler:
 
     def __enter__(self):
         read = None
-        for src, mk in (("nvml", self._nvml_reader), ("nvidia-smi", self._smi_reader)):
+        for src, mk in (("nvml", self._nvml_reader), ("nvml (ctypes)", self._nvml_ctypes_reader),
+                        ("nvidia-smi", self._smi_reader)):
             try:
                 read = mk()
                 self.rows.append(read())
