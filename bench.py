@@ -952,6 +952,8 @@ def main():
                     help="CN steps per cn_step call in the timed region (1: one call per step)")
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--e2e-inner", type=int, default=50, help="CN steps per end-to-end call")
+    ap.add_argument("--no-e2e-propagation", dest="e2e_propagation", action="store_false",
+                    help="skip the end-to-end call of the whole 1000-step propagation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched-systems", type=int, default=4096,
                     help="batched uneven-size workload: systems (0: skip)")
@@ -1045,6 +1047,19 @@ def main():
         plan.step_host(psi_h, args.e2e_inner, E_mid=E_h, psi_out=out_h)
     e2e_s = max_over_ranks(dist, max(time.perf_counter() - t0, 1e-9), dev)
     e2e_val = job_rate(n * args.e2e_inner * args.e2e_calls, world, e2e_s * 1e3)
+    # the workload's whole propagation (WORKLOAD_STEPS steps) as one host-buffer call:
+    # psi and the field in from pinned host memory, psi back
+    e2e_prop = None
+    if args.e2e_calls > 0 and args.e2e_propagation:
+        E_all = torch.from_numpy(np.ascontiguousarray(E_host[:WORKLOAD_STEPS])).pin_memory()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        plan.step_host(psi_h, WORKLOAD_STEPS, E_mid=E_all, psi_out=out_h)
+        s_prop = max_over_ranks(dist, max(time.perf_counter() - t0, 1e-9), dev)
+        e2e_prop = {"value": job_rate(n * WORKLOAD_STEPS, world, s_prop * 1e3), "unit": UNIT,
+                    "cn_steps_per_call": WORKLOAD_STEPS, "calls": 1, "seconds": s_prop,
+                    "bytes_per_call": {"h2d": 16 * n + 8 * WORKLOAD_STEPS, "d2h": 16 * n}}
     plan.close()
 
     peaks = measured_peaks()
@@ -1095,7 +1110,8 @@ def main():
                     "h2d_bytes_per_step": (16 * n + 8 * args.e2e_inner) / max(args.e2e_inner, 1),
                     "d2h_bytes_per_step": 16 * n / max(args.e2e_inner, 1), "cn_steps_per_call": args.e2e_inner,
                     "bytes_per_call": {"h2d": 16 * n + 8 * args.e2e_inner, "d2h": 16 * n},
-                    "calls": args.e2e_calls, "api": "cn_step_host (pinned host psi and field in, psi out)"},
+                    "calls": args.e2e_calls, "api": "cn_step_host (pinned host psi and field in, psi out)",
+                    "full_propagation": e2e_prop},
             "clocks": clocks}
     if tune:
         line["config"]["autotune_ms_per_step"] = tune
