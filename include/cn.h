@@ -146,9 +146,11 @@ cn_status cn_plan_create(const cn_desc* desc, cn_plan* out);
  * 1) / blocks[i]) parallel blocks, one thread each) and reduced; level
  * nlevels is solved by the serial RS stage whatever its size (one thread).
  *   nlevels: 1 .. CN_MAX_LEVELS - 1;
- *   blocks: host int32[nlevels], each 3 .. CN_LEVELS_MAX_BLOCK; blocks longer
- *     than 32 rows take a substitution that stages its values in device
- *     scratch instead of shared memory (the plan allocates it);
+ *   blocks: host int32[nlevels], each 3 .. CN_LEVELS_MAX_BLOCK; a level-0 block
+ *     longer than 32 rows takes a substitution that stages its values in
+ *     device scratch instead of shared memory (the plan allocates it); the
+ *     levels below substitute, at any block length, from the RD results their
+ *     reductions keep in place of their rows;
  *   desc: as for cn_plan_create; desc->block, desc->level_block and
  *     desc->level1_block are ignored.
  * Returns CN_ERR_INVALID_ARG if some level i < nlevels has fewer than 3 rows,
