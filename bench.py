@@ -621,8 +621,9 @@ def batch_gaussians(torch, sizes_t, offsets_t, dx, dev, seed):
 def small_bench(torch, cnb, args, dev, leg, cpu: bool):
     """Free packet, N = 4096, 100 steps (latency-bound: microseconds per step, no
     roofline): one cn_step call of 100 steps, with the paper's P = 16 partition
-    (one level of 256-row blocks, serial RS on 17 rows) and with the default
-    hierarchy; and the oracle's full run on one host core."""
+    (one level of 256-row blocks, each reduced and substituted by one warp's prefix
+    scans, serial RS on 17 rows) and with the default hierarchy; and the oracle's
+    full run on one host core."""
     cfg = W.free_packet_config()
     n, nst = cfg["n"], cfg["nsteps"]
     psi0 = W.initial_state(cfg)
@@ -646,7 +647,7 @@ def small_bench(torch, cnb, args, dev, leg, cpu: bool):
         plan.check()
         info = plan.info()
         out[key] = {"us_per_step": 1e3 * ev0.elapsed_time(ev1) / (reps * nst), "level_rows": info["level_rows"],
-                    "launches_per_step": info["launches_per_step"]}
+                    "launches_per_step": info["launches_per_step"], "level0_lanes": info["level0_lanes"]}
         plan.close()
     if cpu:
         import oracle

@@ -247,6 +247,10 @@ typedef struct {
     int64_t level_rows[CN_MAX_LEVELS];   /* rows of level 0 .. levels                     */
     int32_t level_block[CN_MAX_LEVELS];  /* rows per block of level 0 .. levels-1         */
     int64_t workspace_bytes;             /* device memory the plan holds                  */
+    int32_t level0_lanes;                /* threads that reduce and substitute one level-0
+                                            block: 1, or 32 (a warp, the recurrences as
+                                            prefix scans) for few blocks of 64 .. 1024 rows
+                                            of one system in store mode                    */
 } cn_plan_info;
 cn_status cn_plan_query(cn_plan plan, cn_plan_info* out);
 

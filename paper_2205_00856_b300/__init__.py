@@ -72,7 +72,7 @@ class _Desc(C.Structure):
 class _Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("levels", C.c_int32), ("launches_per_step", C.c_int32),
                 ("level_rows", C.c_int64 * MAX_LEVELS), ("level_block", C.c_int32 * MAX_LEVELS),
-                ("workspace_bytes", C.c_int64)]
+                ("workspace_bytes", C.c_int64), ("level0_lanes", C.c_int32)]
 
 
 _lib = None
@@ -326,7 +326,7 @@ class Plan:
         L = inf.levels
         return dict(n=inf.n, levels=L, launches_per_step=inf.launches_per_step,
                     level_rows=list(inf.level_rows[:L + 1]), level_block=list(inf.level_block[:L]),
-                    workspace_bytes=inf.workspace_bytes)
+                    workspace_bytes=inf.workspace_bytes, level0_lanes=inf.level0_lanes)
 
     def profile(self, enable: bool = True) -> None:
         """Bracket every kernel launch with CUDA events (see profile_read)."""

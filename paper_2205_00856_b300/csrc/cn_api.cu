@@ -20,6 +20,7 @@
 
 #include "../../include/cn.h"
 #include "cn_kernels.cuh"
+#include "cn_scan.cuh"
 
 using namespace cnb;
 
@@ -52,6 +53,7 @@ struct Engine {
     int sms = 0;                  // multiprocessors of the device
     bool pdl = true;              // launch with programmatic stream serialization
     bool batched = false;
+    bool scan0 = false;           // level 0 by one warp per block (cn_scan.cuh): few long blocks
     int nsys = 0;
     std::vector<LevelData> lv;    // lv[0]: the systems themselves
     std::vector<int> base_level;  // per system: the level the RS stage solves
@@ -176,8 +178,12 @@ void free_engine(Engine* p) {
 }
 
 // Slots of level l (l >= 1): one per exchange unit of the level below, at the
-// finest unit (a warp of 32 blocks), plus one.
-size_t slot_entries(const Engine* p, size_t l) { return (size_t)ceil_div(p->lv[l - 1].total, 32) + 1; }
+// finest unit (a warp of 32 blocks; one block for a level produced by the scan
+// kernels), plus one.
+size_t slot_entries(const Engine* p, size_t l) {
+    const int64_t units = p->lv[l].slot_shift == 0 ? p->lv[l - 1].total : ceil_div(p->lv[l - 1].total, 32);
+    return (size_t)units + 1;
+}
 
 // Substitution scratch (two entries per row) for level-0 blocks longer than the
 // shared-memory staging allows; the levels below substitute from their kept RD
@@ -366,6 +372,11 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
         p->lv.push_back(std::move(L));
         if (boff == 0) break;
     }
+    // few long level-0 blocks of one system (store mode): one warp per block, the
+    // recurrences as warp scans (cn_scan.cuh); level 1 then takes one slot per block
+    p->scan0 = !p->batched && !p->slab && !(p->desc.flags & CN_FLAG_RECOMPUTE) && p->lv.size() >= 2 &&
+               p->lv[0].m >= kScanMinRows && p->lv[0].m <= kScanMaxRows && p->lv[0].total <= kScanMaxBlocks;
+    if (p->scan0) p->lv[1].slot_shift = 0;
     cudaError_t e = cudaSuccess;
     for (size_t l = 1; l < p->lv.size() && e == cudaSuccess; ++l) {
         LevelData& L = p->lv[l];
@@ -552,10 +563,22 @@ cudaError_t set_smem_limits_map(int m0) {
 }
 
 template <class R>
+cudaError_t set_scan_smem_limits(int m0) {
+    cudaError_t e = raise_smem_limit(k_cn_reduce_scan<R, -1>, scan_reduce_entries(m0) * kCplx);
+    if (e == cudaSuccess) e = raise_smem_limit(k_cn_reduce_scan<R, 0>, scan_reduce_entries(m0) * kCplx);
+    if (e == cudaSuccess) e = raise_smem_limit(k_cn_substitute_scan<R>, scan_subst_entries(m0) * kCplx);
+    return e;
+}
+
+template <class R>
 cudaError_t set_smem_limits(const Engine* p) {
     // the largest staged level-0 block (longer blocks take the scratch variants;
     // the levels below substitute from their kept RD results, unstaged)
     const int m0 = std::min(p->lv[0].m, kSmemRowsMax);
+    if (p->scan0) {
+        cudaError_t e = set_scan_smem_limits<R>(p->lv[0].m);
+        if (e != cudaSuccess) return e;
+    }
     if (p->batched) return set_smem_limits_map<R, ManySys, ManyGrid>(m0);
     return set_smem_limits_map<R, OneSys, OneGrid>(m0);
 }
@@ -568,7 +591,7 @@ cudaError_t set_smem_limits(const Engine* p) {
 template <class R>
 cudaError_t setup_persistent(Engine* p) {
     p->persistent = false;
-    for (LevelData& L : p->lv) L.slot_shift = 7;  // the per-level kernels' exchange unit
+    for (size_t l = 2; l < p->lv.size(); ++l) p->lv[l].slot_shift = 7;  // the per-level kernels' exchange unit
     // the default per arithmetic, from N = 2^24 measurements on B300: binary64
     // 1.402 (persistent) vs 1.422 ms per step (blocks 32 / 16 / 8), double-float
     // 0.459 vs 0.442 ms (blocks 13 / 10 / 8: the two-group kernels of levels 2
@@ -745,6 +768,13 @@ cudaError_t cn_reduce0(Engine* p, const CNStep& s, cudaStream_t st) {
     const LevelData& L0 = p->lv[0];
     const LevelData& L1 = p->lv[1];
     ProfScope ps(p, kProfReduce0, st);
+    if (p->scan0)
+        return with_es(s, [&](auto es) {
+            return launch(p->pdl, k_cn_reduce_scan<R, decltype(es)::value>, (unsigned)L0.total, 32,
+                          scan_reduce_entries(L0.m) * kCplx, st, s, OneSys{L0.sys[0]}, OneSys{L1.sys[0]},
+                          OneGrid{p->grid[0]}, L0.m, L1.m, planes_of<R>(L1), slot_of<R>(L1),
+                          static_cast<ST*>(p->keep), p->status);
+        });
     return with_es(s, [&](auto es) {
         cudaError_t e = cudaSuccess;
         with_maps_grid(p, [&](auto a, auto b, auto gr) {
@@ -764,6 +794,10 @@ cudaError_t cn_subst0(Engine* p, const CNStep& s, double2* x, cudaStream_t st) {
     const unsigned grid = grid_for(L0.total);
     ST* keep = static_cast<ST*>(p->keep);
     ProfScope ps(p, kProfSubst0, st);
+    if (p->scan0)
+        return launch(p->pdl, k_cn_substitute_scan<R>, (unsigned)L0.total, 32, scan_subst_entries(L0.m) * kCplx, st,
+                      OneSys{L0.sys[0]}, OneSys{L1.sys[0]}, L0.m, static_cast<const ST*>(keep),
+                      static_cast<const ST*>(x_of<R>(L1)), x);
     return with_es(s, [&](auto es) {
         cudaError_t e = cudaSuccess;
         with_maps_grid(p, [&](auto a, auto b, auto gr) {
@@ -1386,6 +1420,7 @@ cn_status cn_plan_query(cn_plan p, cn_plan_info* out) {
     }
     out->launches_per_step = p->persistent ? 3 : 2 * out->levels + 1;
     out->workspace_bytes = p->workspace_bytes;
+    out->level0_lanes = p->scan0 ? 32 : 1;
     return CN_OK;
 }
 

@@ -930,8 +930,10 @@ __global__ void k_base_serial(LevelSource<R> src, typename Store<R>::T* x, typen
     bool ok = true;
     const int64_t n = src.n;
     cx<R> zp = czero<R>(), cpp = czero<R>();
+    Row<R> nxt = src.template row_at<R>(0);  // one row ahead: its loads overlap this row's chain
     for (int64_t w = 0; w < n; ++w) {
-        const Row<R> r = src.template row_at<R>(w);
+        const Row<R> r = nxt;
+        if (w + 1 < n) nxt = src.template row_at<R>(w + 1);
         // m_w = a_w - b_w c'_{w-1};  z_w = (d_w - b_w z_{w-1}) / m_w;  c'_w = c_w / m_w
         const cx<R> piv = (w == 0) ? r.a : csub(r.a, cmul(r.b, cpp));
         const cx<R> iv = crcp(piv, ok);
@@ -941,8 +943,18 @@ __global__ void k_base_serial(LevelSource<R> src, typename Store<R>::T* x, typen
         sstore(cs + w, cpp);
     }
     cx<R> y = zp;
+    cx<R> zn = czero<R>(), cn = czero<R>();
+    if (n >= 2) {
+        zn = sload(x + n - 2);
+        cn = sload(cs + n - 2);
+    }
     for (int64_t w = n - 2; w >= 0; --w) {
-        y = csub(sload(x + w), cmul(sload(cs + w), y));
+        const cx<R> z = zn, c = cn;
+        if (w >= 1) {  // the next row's values first
+            zn = sload(x + w - 1);
+            cn = sload(cs + w - 1);
+        }
+        y = csub(z, cmul(c, y));
         sstore(x + w, y);
     }
     if (!ok) flag_error(status, kStatusNonfinite);

@@ -1,0 +1,399 @@
+// Level 0 of few long blocks: one warp per block, prefix scans.
+//
+// The paper's own partition of its small case (n = 4096 in P = 16 blocks of 256
+// rows, Sec. 4.1.1) walks each block with one thread.  On B300 every dependent
+// binary64 operation costs a warp ~64 clocks, so a 256-row walk is ~0.7 M clocks
+// per step however few blocks there are.  Here the 32 lanes of a warp share one
+// block's rows (ceil((g - 1) / 32) consecutive rows each) and every recurrence of
+// Table 1's RD/RU on the block and of its SS becomes a warp prefix scan:
+//   pivots       w_k = 1 / (a~_k - w_{k-1}), w_0 = 0: a Moebius map of w_{k-1},
+//                composed as the 2x2 matrices F_k = [[0, 1], [-1, a~_k]]
+//                (w_k = num / den of F_k ... F_1 (0, 1)^T);
+//   RD's d       d_k = d^_k + w_{k-1} d_{k-1}: affine maps y -> w_{k-1} y + d^_k;
+//   RU's Q       Q_k = Q_{k-1} w_k (k >= 2, Q_1 = 1): products;
+//   RU's sums    S = sum_{k>=2} Q_k Q_{k-1},  d_1 + sum_{k>=2} Q_k d_k: reductions;
+//   SS           z_k = (d^_k + z_{k-1}) w_k from z_0 = x_L, then
+//                x_k = z_k + w_k x_{k+1} from x_{g-1} = z_{g-1}: affine maps.
+// Each lane composes the maps of its rows, a Kogge-Stone scan over the lanes
+// gives every lane the composition of the rows before its own (after them, for
+// the backward sweep), and each lane then re-runs its rows' recurrences from
+// that start value exactly as the one-thread kernels do.  The results are those
+// of the one-thread elimination up to rounding (the start values of the lanes'
+// chains are formed in a different order).  Projective matrix products are
+// rescaled by powers of two (exact) so that they neither overflow nor vanish.
+// The level-1 rows take this block's JU part; its JD part goes to slot t + 1,
+// one slot per block (the level's slot_shift 0), and the reader adds it.
+#pragma once
+#include "cn_kernels.cuh"
+
+namespace cnb {
+
+constexpr int kScanMinRows = 64;     // level-0 blocks at least this long take the scan kernels
+constexpr int kScanMaxRows = 1024;   // ... and at most this long (shared memory per warp)
+constexpr int64_t kScanMaxBlocks = 4096;  // latency regime only: few blocks
+
+// shared memory of the scan kernels, in storage entries: a~, d^, w, d^RD, Q (reduction)
+// or d^, w, z (substitution) for rows 0..m
+__host__ __device__ constexpr size_t scan_reduce_entries(int m) { return 5 * (size_t)(m + 1); }
+__host__ __device__ constexpr size_t scan_subst_entries(int m) { return 3 * (size_t)(m + 1); }
+
+template <class T> __device__ __forceinline__ T shfl_word_up(const T& v, int d) {
+    static_assert(sizeof(T) % sizeof(int) == 0, "shuffled in 32-bit words");
+    constexpr int nw = (int)(sizeof(T) / sizeof(int));
+    int w[nw];
+    memcpy(w, &v, sizeof(T));
+#pragma unroll
+    for (int i = 0; i < nw; ++i) w[i] = __shfl_up_sync(0xffffffffu, w[i], d);
+    T r;
+    memcpy(&r, w, sizeof(T));
+    return r;
+}
+template <class T> __device__ __forceinline__ T shfl_word_down(const T& v, int d) {
+    constexpr int nw = (int)(sizeof(T) / sizeof(int));
+    int w[nw];
+    memcpy(w, &v, sizeof(T));
+#pragma unroll
+    for (int i = 0; i < nw; ++i) w[i] = __shfl_down_sync(0xffffffffu, w[i], d);
+    T r;
+    memcpy(&r, w, sizeof(T));
+    return r;
+}
+template <class T> __device__ __forceinline__ T shfl_word_xor(const T& v, int d) {
+    constexpr int nw = (int)(sizeof(T) / sizeof(int));
+    int w[nw];
+    memcpy(w, &v, sizeof(T));
+#pragma unroll
+    for (int i = 0; i < nw; ++i) w[i] = __shfl_xor_sync(0xffffffffu, w[i], d);
+    T r;
+    memcpy(&r, w, sizeof(T));
+    return r;
+}
+
+// magnitude exponent of a complex number and exact scaling by 2^e
+__device__ __forceinline__ double mx2(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float mx2(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double cmag(cx<double> z) { return fmax(fabs(z.re), fabs(z.im)); }
+__device__ __forceinline__ int mag_exp(double m) { return m > 0.0 ? ilogb(m) : 0; }
+__device__ __forceinline__ cx<double> cscale(cx<double> z, int e) { return mk(scalbn(z.re, e), scalbn(z.im, e)); }
+__device__ __forceinline__ float cmag(cx<df> z) { return fmaxf(fabsf(z.re.hi), fabsf(z.im.hi)); }
+__device__ __forceinline__ int mag_exp(float m) { return m > 0.0f ? ilogbf(m) : 0; }
+__device__ __forceinline__ df dscale(df a, int e) { return df_make(ldexpf(a.hi, e), ldexpf(a.lo, e)); }
+__device__ __forceinline__ cx<df> cscale(cx<df> z, int e) { return mk(dscale(z.re, e), dscale(z.im, e)); }
+
+// 2x2 complex matrix [[a, b], [c, d]] acting on (w, 1): a projective (Moebius) map
+template <class R> struct Mob {
+    cx<R> a, b, c, d;
+};
+template <class R> __device__ __forceinline__ Mob<R> mob_identity() {
+    Mob<R> m;
+    m.a = m.d = cfrom<R>(1.0, 0.0);
+    m.b = m.c = czero<R>();
+    return m;
+}
+// the same map with its entries scaled to a largest magnitude in [1, 2)
+template <class R> __device__ __forceinline__ Mob<R> mob_normalize(Mob<R> m) {
+    const auto mx = mx2(mx2(cmag(m.a), cmag(m.b)), mx2(cmag(m.c), cmag(m.d)));
+    const int e = -mag_exp(mx);
+    m.a = cscale(m.a, e);
+    m.b = cscale(m.b, e);
+    m.c = cscale(m.c, e);
+    m.d = cscale(m.d, e);
+    return m;
+}
+// later o earlier: the matrix product L E
+template <class R> __device__ __forceinline__ Mob<R> mob_after(const Mob<R>& L, const Mob<R>& E) {
+    Mob<R> r;
+    r.a = cfma(cmul(L.a, E.a), L.b, E.c);
+    r.b = cfma(cmul(L.a, E.b), L.b, E.d);
+    r.c = cfma(cmul(L.c, E.a), L.d, E.c);
+    r.d = cfma(cmul(L.c, E.b), L.d, E.d);
+    return mob_normalize(r);
+}
+// F_k M, F_k = [[0, 1], [-1, a~_k]]: row k's pivot map after M
+template <class R> __device__ __forceinline__ Mob<R> mob_pivot_after(cx<R> at, const Mob<R>& M) {
+    Mob<R> r;
+    r.a = M.c;
+    r.b = M.d;
+    r.c = csub(cmul(at, M.c), M.a);
+    r.d = csub(cmul(at, M.d), M.b);
+    return r;
+}
+
+// affine map y -> m y + a
+template <class R> struct Aff {
+    cx<R> m, a;
+};
+template <class R> __device__ __forceinline__ Aff<R> aff_identity() {
+    Aff<R> f;
+    f.m = cfrom<R>(1.0, 0.0);
+    f.a = czero<R>();
+    return f;
+}
+template <class R> __device__ __forceinline__ Aff<R> aff_after(const Aff<R>& L, const Aff<R>& E) {
+    Aff<R> r;
+    r.m = cmul(L.m, E.m);
+    r.a = cfma(L.a, L.m, E.a);
+    return r;
+}
+// Kogge-Stone scans over the 32 lanes: "up" composes lane l with every lane below
+// it (forward recurrences), "down" with every lane above it (backward ones);
+// the exclusive forms give each lane the composition of the others' maps only.
+template <class R> __device__ __forceinline__ Mob<R> scan_up_exclusive(Mob<R> v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const Mob<R> o = shfl_word_up(v, d);
+        if (lane >= d) v = mob_after(v, o);
+    }
+    const Mob<R> x = shfl_word_up(v, 1);
+    return lane == 0 ? mob_identity<R>() : x;
+}
+template <class R> __device__ __forceinline__ Aff<R> scan_up_exclusive(Aff<R> v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const Aff<R> o = shfl_word_up(v, d);
+        if (lane >= d) v = aff_after(v, o);
+    }
+    const Aff<R> x = shfl_word_up(v, 1);
+    return lane == 0 ? aff_identity<R>() : x;
+}
+template <class R> __device__ __forceinline__ Aff<R> scan_down_exclusive(Aff<R> v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const Aff<R> o = shfl_word_down(v, d);
+        if (lane + d < 32) v = aff_after(v, o);
+    }
+    const Aff<R> x = shfl_word_down(v, 1);
+    return lane == 31 ? aff_identity<R>() : x;
+}
+template <class R> __device__ __forceinline__ cx<R> warp_sum(cx<R> v) {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) v = cadd(v, shfl_word_xor(v, d));
+    return v;
+}
+
+// Block t's rows 1..g-1 are dealt to the lanes in runs of c = ceil((g - 1) / 32):
+// lane l takes rows k0 = 1 + l c .. k1 - 1 (none if k0 >= g).
+struct ScanRows {
+    int gap, k0, k1;
+    __device__ __forceinline__ ScanRows(int g, int lane) : gap(g) {
+        const int c = (g - 1 + 31) / 32;
+        k0 = 1 + lane * c;
+        k1 = min(g, k0 + c);
+    }
+};
+// keep entries of block t, row k, field j (0: d^, 1: w), in the one-thread kernels' layout
+template <class ST> __device__ __forceinline__ ST* scan_keep(ST* keep0, int64_t t, int m, int k, int j) {
+    return keep0 + (t >> 7) * (2 * (int64_t)m * kThreads) + (int64_t)(2 * k + j) * kThreads + (t & (kThreads - 1));
+}
+
+// Level-0 reduction of block t = blockIdx.x by one warp: coefficients and explicit
+// rows, RD/JD with RU/JU (the scans above), the kept (d^, w) of every interior row,
+// and the block's JU part of level-1 row t (JD part to slot t + 1; the system's last
+// block writes row P whole).  Same arithmetic per row as cn_reduce_block.
+template <class R, int ES>
+__global__ void __launch_bounds__(32)
+k_cn_reduce_scan(CNStep st, OneSys sys, OneSys next, OneGrid grid, int m, int m_next, LevelPlanes<R> out,
+                 LevelSlot<R>* out_slot, typename Store<R>::T* keep0, int* status) {
+    grid_dep_enter();
+    typedef typename Store<R>::T ST;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ST* const sA = reinterpret_cast<ST*>(smem_raw);  // a~_k
+    ST* const sD = sA + (m + 1);                      // d^_k
+    ST* const sW = sD + (m + 1);                      // w_k, w_0 = 0
+    ST* const sR = sW + (m + 1);                      // RD's d_k
+    ST* const sQ = sR + (m + 1);                      // RU's Q_k
+    const int lane = threadIdx.x;
+    const int64_t t = blockIdx.x;
+    const LvlSys& e = sys.at(0);
+    const int64_t n = e.n, P = e.P;
+    const int64_t J0 = joint_line(t, P, m, n);
+    const ScanRows rw((int)(joint_line(t + 1, P, m, n) - J0), lane);
+    const int gap = rw.gap, k0 = rw.k0, k1 = rw.k1;
+    bool ok = true;
+    // scaled rows: a~_k and d^_k (row k0's stencil takes psi_{k0 - 1}: not a joint row)
+    if (k0 < k1) {
+        CNRowStream<R, ES> rs;
+        rs.init(st, e, grid.at(0), J0 + k0);
+        rs.pm = rs.ld(J0 + k0 - 1);
+        for (int k = k0; k < k1; ++k) {
+            cx<R> a, d;
+            rs.next(a, d);
+            sstore(sA + k, a);
+            sstore(sD + k, d);
+        }
+    }
+    if (lane == 0) sstore(sW, czero<R>());
+    __syncwarp();
+    // RD pivots: w_k = 1 / (a~_k - w_{k-1})
+    {
+        Mob<R> M = mob_identity<R>();
+        for (int k = k0; k < k1; ++k) {
+            M = mob_pivot_after(sload(sA + k), M);
+            if (((k - k0) & 7) == 7) M = mob_normalize(M);
+        }
+        const Mob<R> X = scan_up_exclusive(mob_normalize(M), lane);
+        cx<R> w = cmul(X.b, crcp(X.d, ok));  // w_{k0 - 1}: X applied to (w_0, 1) = (0, 1)
+        for (int k = k0; k < k1; ++k) {
+            w = crcp(csub(sload(sA + k), w), ok);
+            sstore(sW + k, w);
+        }
+    }
+    __syncwarp();
+    // RD right-hand side: d_k = d^_k + w_{k-1} d_{k-1}
+    {
+        Aff<R> F = aff_identity<R>();
+        for (int k = k0; k < k1; ++k) {
+            Aff<R> f;
+            f.m = sload(sW + k - 1);
+            f.a = sload(sD + k);
+            F = aff_after(f, F);
+        }
+        cx<R> y = scan_up_exclusive(F, lane).a;  // d_{k0 - 1} (d_0 = 0)
+        for (int k = k0; k < k1; ++k) {
+            y = k == 1 ? sload(sD + 1) : cfma(sload(sD + k), sload(sW + k - 1), y);
+            sstore(sR + k, y);
+        }
+    }
+    // RU products: Q_1 = 1, Q_k = Q_{k-1} w_k
+    {
+        Aff<R> F = aff_identity<R>();
+        for (int k = max(k0, 2); k < k1; ++k) {
+            Aff<R> f;
+            f.m = sload(sW + k);
+            f.a = czero<R>();
+            F = aff_after(f, F);
+        }
+        cx<R> q = scan_up_exclusive(F, lane).m;  // Q_{k0 - 1}
+        for (int k = k0; k < k1; ++k) {
+            q = k == 1 ? cfrom<R>(1.0, 0.0) : cmul(q, sload(sW + k));
+            sstore(sQ + k, q);
+        }
+    }
+    __syncwarp();
+    // RU sums: S = sum_{k>=2} Q_k Q_{k-1},  nd = d_1 + sum_{k>=2} Q_k d_k
+    cx<R> s = czero<R>(), nd = czero<R>();
+    for (int k = k0; k < k1; ++k) {
+        if (k == 1) {
+            nd = sload(sR + 1);
+            continue;
+        }
+        const cx<R> Qk = sload(sQ + k);
+        s = cfma(s, Qk, sload(sQ + k - 1));
+        nd = cfma(nd, Qk, sload(sR + k));
+    }
+    const cx<R> S = warp_sum(s), ND = warp_sum(nd);
+    // the kept values of the substitution
+    for (int k = k0; k < k1; ++k) {
+        sstore(scan_keep(keep0, t, m, k, 0), sload(sD + k));
+        sstore(scan_keep(keep0, t, m, k, 1), sload(sW + k));
+    }
+    if (!ok) flag_error(status, kStatusNonfinite);
+    if (lane != 0) return;
+    // JD on row J_{t+1}, JU on row J_t (as cn_reduce_block)
+    const cx<R> one = cfrom<R>(1.0, 0.0);
+    const cx<R> w1 = sload(sW + 1), wl = sload(sW + gap - 1), dl = sload(sR + gap - 1), Ql = sload(sQ + gap - 1);
+    CNRowStream<R, ES> r0;  // row J_t, its own share (psi_{J_t - 1} is the block above's)
+    r0.init(st, e, grid.at(0), J0);
+    cx<R> A0, D0;
+    r0.next(A0, D0);
+    const cx<R> wQ = cneg(cmul(w1, Ql));
+    JDPart<R> jd;
+    jd.b = wQ;
+    jd.a = cneg(wl);
+    jd.d = cmul(wl, dl);
+    if constexpr (ES != 0) {  // this block's part of row J_{t+1}'s term in psi_{J_{t+1} - 1}
+        const cx<R> pm = r0.ld(J0 + gap - 1);
+        jd.d = ES > 0 ? csub(jd.d, pm) : cadd(jd.d, pm);
+    }
+    const cx<R> JUc = wQ;
+    const cx<R> JUa = cneg(cmul(w1, cfma(one, w1, S)));
+    const cx<R> JUd = cmul(w1, ND);
+    const RowSink<R> sink(out, next.at(0), m_next);
+    sink.put(t, czero<R>(), cadd(A0, JUa), JUc, cadd(D0, JUd));
+    if (t == P - 1) {
+        cx<R> Ag = czero<R>(), Dg = czero<R>();
+        if (st.own_last) {  // row J_P, the system's last: its own share
+            CNRowStream<R, ES> rg;
+            rg.init(st, e, grid.at(0), J0 + gap);
+            rg.next(Ag, Dg);
+        }
+        sink.put(P, jd.b, cadd(Ag, jd.a), czero<R>(), cadd(Dg, jd.d));
+    } else {
+        LevelSlot<R> sl;
+        sstore(&sl.b, jd.b);
+        sstore(&sl.a, jd.a);
+        sstore(&sl.d, jd.d);
+        dbg_st(&out_slot[t + 1], sl);
+    }
+}
+
+// Level-0 substitution of block t = blockIdx.x by one warp from the kept (d^, w):
+//   z_k = (d^_k + z_{k-1}) w_k from z_0 = x_L (row g-1 also adds x_R), then
+//   x_k = z_k + w_k x_{k+1} from x_{g-1} = z_{g-1}
+// (the forward and backward sweeps of k_cn_substitute_kept, as scans).
+template <class R>
+__global__ void __launch_bounds__(32)
+k_cn_substitute_scan(OneSys sys, OneSys next, int m, const typename Store<R>::T* keep0,
+                     const typename Store<R>::T* x_next0, double2* x_out) {
+    grid_dep_enter();
+    typedef typename Store<R>::T ST;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ST* const sD = reinterpret_cast<ST*>(smem_raw);
+    ST* const sW = sD + (m + 1);
+    ST* const sZ = sW + (m + 1);
+    const int lane = threadIdx.x;
+    const int64_t t = blockIdx.x;
+    const LvlSys& e = sys.at(0);
+    const int64_t n = e.n, P = e.P;
+    const int64_t J0 = joint_line(t, P, m, n);
+    const ScanRows rw((int)(joint_line(t + 1, P, m, n) - J0), lane);
+    const int gap = rw.gap, k0 = rw.k0, k1 = rw.k1;
+    const ST* x_next = x_next0 + next.at(0).row_off;
+    const cx<R> xL = sload(x_next + t), xR = sload(x_next + t + 1);
+    for (int k = k0; k < k1; ++k) {
+        sstore(sD + k, sload(scan_keep(keep0, t, m, k, 0)));
+        sstore(sW + k, sload(scan_keep(keep0, t, m, k, 1)));
+    }
+    // forward sweep
+    {
+        Aff<R> F = aff_identity<R>();
+        for (int k = k0; k < k1; ++k) {
+            const cx<R> w = sload(sW + k);
+            const cx<R> dd = k == gap - 1 ? cadd(sload(sD + k), xR) : sload(sD + k);
+            Aff<R> f;  // z -> w z + w (d^ (+ x_R))
+            f.m = w;
+            f.a = cmul(dd, w);
+            F = aff_after(f, F);
+        }
+        const Aff<R> Z = scan_up_exclusive(F, lane);
+        cx<R> z = cfma(Z.a, Z.m, xL);  // z_{k0 - 1}
+        for (int k = k0; k < k1; ++k) {
+            const cx<R> w = sload(sW + k), d = sload(sD + k);
+            z = k == gap - 1 ? cmul(cadd(cadd(d, z), xR), w) : cmul(cadd(d, z), w);
+            sstore(sZ + k, z);
+        }
+    }
+    __syncwarp();
+    // backward sweep over rows g-2 .. 1
+    const cx<R> ztop = sload(sZ + gap - 1);
+    const int b1 = min(k1, gap - 1);  // the lane's rows below g - 1: k0 .. b1 - 1
+    Aff<R> B = aff_identity<R>();
+    for (int k = b1 - 1; k >= k0; --k) {
+        Aff<R> f;  // y -> w_k y + z_k
+        f.m = sload(sW + k);
+        f.a = sload(sZ + k);
+        B = aff_after(f, B);
+    }
+    const Aff<R> Yb = scan_down_exclusive(B, lane);
+    double2* x = x_out + e.row_off;
+    cx<R> y = cfma(Yb.a, Yb.m, ztop);  // x_{b1}
+    for (int k = b1 - 1; k >= k0; --k) {
+        y = cfma(sload(sZ + k), sload(sW + k), y);
+        store128(x + J0 + k, y);
+    }
+    if (k0 <= gap - 1 && gap - 1 < k1) store128(x + J0 + gap - 1, ztop);
+    if (lane == 0) store128(x + J0, xL);
+    if (lane == 0 && t == P - 1) store128(x + J0 + gap, xR);
+}
+
+}  // namespace cnb
