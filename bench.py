@@ -621,16 +621,18 @@ def batch_gaussians(torch, sizes_t, offsets_t, dx, dev, seed):
 def small_bench(torch, cnb, args, dev, leg, cpu: bool):
     """Free packet, N = 4096, 100 steps (latency-bound: microseconds per step, no
     roofline): one cn_step call of 100 steps, with the paper's P = 16 partition
-    (one level of 256-row blocks, each reduced and substituted by one warp's prefix
-    scans, serial RS on 17 rows) and with the default hierarchy; and the oracle's
-    full run on one host core."""
+    (one level of 256-row blocks, serial RS on 17 rows) reduced and substituted by
+    one warp's prefix scans per block and, as the paper does, by one thread per
+    block (p16_serial); with the default hierarchy; and the oracle's full run on
+    one host core."""
     cfg = W.free_packet_config()
     n, nst = cfg["n"], cfg["nsteps"]
     psi0 = W.initial_state(cfg)
     arith = leg["code"]
     out = {"workload": cfg["name"], "n": n, "steps": nst, "dtype": leg["arith"]}
     stream = torch.cuda.current_stream()
-    for key, kw in (("p16", {"levels": [256]}), ("default", {})):
+    for key, kw in (("p16", {"levels": [256]}), ("p16_serial", {"levels": [256], "flags": cnb.FLAG_SERIAL_BLOCKS}),
+                    ("default", {})):
         plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], arith=arith, **kw)
         psi = torch.from_numpy(psi0).to(dev)
         res = torch.empty_like(psi)

@@ -118,6 +118,13 @@ typedef struct {
  * are the same bits either way. */
 #define CN_FLAG_LEVEL_LAUNCHES 4
 #define CN_FLAG_PERSISTENT_LEVELS 8
+/* cn_desc.flags: level 0 one thread per block whatever the blocks (the paper's
+ * per-process serial elimination, Sec. 4.1; the partition study's model).  Without
+ * it, a single system in store mode whose level-0 blocks are 64 .. 1024 rows long
+ * and at most 4096 in number is reduced and substituted by one warp per block, the
+ * recurrences as warp prefix scans (cn_plan_info.level0_lanes = 32): the same
+ * solution up to rounding, at a fraction of the latency. */
+#define CN_FLAG_SERIAL_BLOCKS 16
 
 /* Create a plan for systems of size desc->n.  The N-shaped solve is nested
  * (Eq. iteration): level 0 is cut into blocks of desc->block rows, level 1 into

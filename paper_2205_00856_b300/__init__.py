@@ -26,6 +26,7 @@ FLAG_COEFF_TABLE = 1
 FLAG_RECOMPUTE = 2
 FLAG_LEVEL_LAUNCHES = 4
 FLAG_PERSISTENT_LEVELS = 8
+FLAG_SERIAL_BLOCKS = 16
 
 _STATUS = {0: "CN_OK", 1: "CN_ERR_INVALID_ARG", 2: "CN_ERR_UNSUPPORTED", 3: "CN_ERR_OOM", 4: "CN_ERR_CUDA",
            5: "CN_ERR_TIMEOUT", 6: "CN_ERR_NONFINITE", 7: "CN_ERR_BOUNDS"}

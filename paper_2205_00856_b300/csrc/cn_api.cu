@@ -145,7 +145,8 @@ cn_status validate_desc(const cn_desc* d, bool need_n) {
     if (d->level_block != 0 && (d->level_block < 3 || d->level_block > kMaxBlockRows)) return CN_ERR_INVALID_ARG;
     if (d->level1_block != 0 && (d->level1_block < 3 || d->level1_block > kMaxBlockRows)) return CN_ERR_INVALID_ARG;
     if (d->arith != CN_ARITH_F64 && d->arith != CN_ARITH_DF64) return CN_ERR_INVALID_ARG;
-    if ((d->flags & ~(CN_FLAG_COEFF_TABLE | CN_FLAG_RECOMPUTE | CN_FLAG_LEVEL_LAUNCHES | CN_FLAG_PERSISTENT_LEVELS)) != 0)
+    if ((d->flags & ~(CN_FLAG_COEFF_TABLE | CN_FLAG_RECOMPUTE | CN_FLAG_LEVEL_LAUNCHES | CN_FLAG_PERSISTENT_LEVELS |
+                      CN_FLAG_SERIAL_BLOCKS)) != 0)
         return CN_ERR_INVALID_ARG;
     if ((d->flags & CN_FLAG_LEVEL_LAUNCHES) && (d->flags & CN_FLAG_PERSISTENT_LEVELS)) return CN_ERR_INVALID_ARG;
     return CN_OK;
@@ -374,7 +375,8 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
     }
     // few long level-0 blocks of one system (store mode): one warp per block, the
     // recurrences as warp scans (cn_scan.cuh); level 1 then takes one slot per block
-    p->scan0 = !p->batched && !p->slab && !(p->desc.flags & CN_FLAG_RECOMPUTE) && p->lv.size() >= 2 &&
+    p->scan0 = !p->batched && !p->slab && !(p->desc.flags & (CN_FLAG_RECOMPUTE | CN_FLAG_SERIAL_BLOCKS)) &&
+               p->lv.size() >= 2 &&
                p->lv[0].m >= kScanMinRows && p->lv[0].m <= kScanMaxRows && p->lv[0].total <= kScanMaxBlocks;
     if (p->scan0) p->lv[1].slot_shift = 0;
     cudaError_t e = cudaSuccess;

@@ -155,8 +155,9 @@ def sweep(n: int, depths, nbl1_grid, arith: str = "f64", steps: int = 10, reps: 
             if counts[0] < 1 or (L > 1 and min(counts) < 1):
                 continue
             try:
+                # one thread per block: the per-block serial elimination the paper's model times
                 plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0,
-                                arith=ar, levels=blocks)
+                                arith=ar, levels=blocks, flags=cnb.FLAG_SERIAL_BLOCKS)
             except cnb.CNError:
                 continue  # depth too deep for this first level
             ms = time_plan(torch, cnb, plan, n, cfg, steps, reps)

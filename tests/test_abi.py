@@ -49,7 +49,7 @@ def _desc(**kw):
 @pytest.mark.parametrize("kw", [dict(n=2), dict(n=-5), dict(dx=0.0), dict(dx=float("nan")), dict(dt=0.0),
                                 dict(pot=9), dict(pot=1), dict(pot=2, soft_s=0.0), dict(pot=3, n_cos=17, L=1.0),
                                 dict(pot=3, n_cos=2, L=1.0), dict(block=2), dict(block=33), dict(arith=3),
-                                dict(flags=16), dict(flags=12), dict(level_block=2), dict(level_block=40), dict(level1_block=2),
+                                dict(flags=32), dict(flags=12), dict(level_block=2), dict(level_block=40), dict(level1_block=2),
                                 dict(level1_block=33)])
 def test_invalid_descriptor_rejected_on_host(kw):
     lib = cnb.load()

@@ -47,6 +47,12 @@ def test_paper_small_case_p16_vs_oracle(arith):
     plan.check()
     ref = oracle.cn_run(oracle.Problem(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=oracle.POT_NONE), psi0, nst)
     check(out, ref)
+    serial = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], arith=arith, levels=[256], flags=cnb.FLAG_SERIAL_BLOCKS)
+    assert serial.info()["level0_lanes"] == 1
+    out_s = serial.step(to_dev(psi0), nst).cpu().numpy()
+    serial.check()
+    check(out_s, ref)
+    check(out, out_s)
 
 
 @pytest.mark.parametrize("arith", ARITHS)
@@ -110,9 +116,10 @@ def test_scan_adjoint_steps_vs_oracle(arith, tol):
     assert np.linalg.norm(lam0 - lam0_ref) <= tol * np.linalg.norm(lam0_ref)
 
 
-def test_scan_not_taken_for_many_blocks_or_short_blocks():
+def test_scan_not_taken_for_many_blocks_short_blocks_or_serial_flag():
     cfg = W.soft_coulomb_config(n=1 << 20)
-    for kw in (dict(levels=[32]), dict(levels=[64])):  # 32-row blocks; 64-row but 16384 blocks
+    # 32-row blocks; 64-row but 16384 blocks; asked for one thread per block
+    for kw in (dict(levels=[32]), dict(levels=[64]), dict(levels=[300], flags=cnb.FLAG_SERIAL_BLOCKS)):
         plan = cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, **kw)
         assert plan.info()["level0_lanes"] == 1
         plan.close()
