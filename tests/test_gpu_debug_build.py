@@ -5,7 +5,8 @@ cn_debug_report) -- the stand-in for a memory sanitizer.  Runs in a fresh
 process (the package loads one library per process): the planted-access self
 test, then every entry point over configurations that reach every kernel --
 ragged sizes, the large-grid blocks with the coefficient table, long blocks
-with device scratch and the serial RS stage, recompute mode, the adjoint, the
+with device scratch and the serial RS stage, few long blocks on one warp each
+(prefix scans), recompute mode, the adjoint, the
 host-buffer step, a batch, slabs with tiny and uneven joint lines, the
 no-allocation solve and the control-field maps -- with no violation reported,
 and the results against the oracle."""
@@ -45,7 +46,8 @@ SCRIPT = textwrap.dedent("""
         for n, kw in ((100003, {{}}), (1 << 21, dict(block=m0, level1_block=m1, level_block=ml,
                                                     flags=cnb.FLAG_COEFF_TABLE)),
                       (1 << 20, dict(flags=cnb.FLAG_PERSISTENT_LEVELS)), (1 << 20, dict(flags=cnb.FLAG_LEVEL_LAUNCHES)),
-                      (200001, dict(levels=[40, 20])), (70001, dict(flags=cnb.FLAG_RECOMPUTE))):
+                      (200001, dict(levels=[40, 20])), (70001, dict(flags=cnb.FLAG_RECOMPUTE)),
+                      (20011, dict(levels=[300, 8]))):
             cfg = W.soft_coulomb_config(n=n, nsteps=5)
             prob = oracle.Problem(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=oracle.POT_SOFTCOULOMB, soft_s=2.0)
             psi0 = W.full_support_state(n, cfg["dx"], cfg["x_min"], seed=n)
