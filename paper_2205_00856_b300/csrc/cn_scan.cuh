@@ -100,6 +100,19 @@ template <class R> __device__ __forceinline__ Mob<R> mob_normalize(Mob<R> m) {
     m.d = cscale(m.d, e);
     return m;
 }
+// binary64: the largest exponent field by integer operations and one multiply by
+// the power of two per component (no binary64 operation besides the multiplies)
+__device__ __forceinline__ int efield(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
+__device__ __forceinline__ int efield(cx<double> z) { return max(efield(z.re), efield(z.im)); }
+template <> __device__ __forceinline__ Mob<double> mob_normalize(Mob<double> m) {
+    const int em = min(max(max(efield(m.a), efield(m.b)), max(efield(m.c), efield(m.d))), 2045);
+    const double f = __longlong_as_double((long long)(2046 - em) << 52);  // 2^(1023 - em)
+    m.a = mk(m.a.re * f, m.a.im * f);
+    m.b = mk(m.b.re * f, m.b.im * f);
+    m.c = mk(m.c.re * f, m.c.im * f);
+    m.d = mk(m.d.re * f, m.d.im * f);
+    return m;
+}
 // later o earlier: the matrix product L E
 template <class R> __device__ __forceinline__ Mob<R> mob_after(const Mob<R>& L, const Mob<R>& E) {
     Mob<R> r;
