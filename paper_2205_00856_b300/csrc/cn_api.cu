@@ -12,6 +12,7 @@
 #include <initializer_list>
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <utility>
 #include <cstdint>
 #include <cstring>
@@ -567,6 +568,8 @@ cudaError_t set_smem_limits_map(int m0) {
 template <class R>
 cudaError_t set_scan_smem_limits(int m0) {
     cudaError_t e = raise_smem_limit(k_cn_reduce_scan<R, -1>, scan_reduce_entries(m0) * kCplx);
+    if (e == cudaSuccess && std::is_same<R, double>::value)
+        e = raise_smem_limit(k_base_scan<R>, scan_rs_entries(kScanRsMax) * kCplx);
     if (e == cudaSuccess) e = raise_smem_limit(k_cn_reduce_scan<R, 0>, scan_reduce_entries(m0) * kCplx);
     if (e == cudaSuccess) e = raise_smem_limit(k_cn_substitute_scan<R>, scan_subst_entries(m0) * kCplx);
     return e;
@@ -657,6 +660,11 @@ cudaError_t rs_stage(Engine* p, cudaStream_t st) {
     const LevelSource<R> src = level_source<R>(B).bind(B.sys[0]);
     if (p->lvl_m.empty())
         return launch(p->pdl, k_base_cr<R>, 1, kCrThreads, cr_smem(), st, src, x_of<R>(B), p->status);
+    // level 0 on warps, binary64: the RS stage on one warp too (17 rows of the paper's small
+    // case: 30 -> 21 us on B300; in double-float the one-thread walk is the faster, 16 us)
+    if (std::is_same<R, double>::value && p->scan0 && src.n <= kScanRsMax)
+        return launch(p->pdl, k_base_scan<R>, 1, 32, scan_rs_entries((int)src.n) * kCplx, st, src, x_of<R>(B),
+                      p->status);
     if (p->base_cs)
         return launch(p->pdl, k_base_serial<R>, 1, 32, 0, st, src, x_of<R>(B),
                       static_cast<typename Store<R>::T*>(p->base_cs), p->status);

@@ -410,3 +410,104 @@ k_cn_substitute_scan(OneSys sys, OneSys next, int m, const typename Store<R>::T*
 }
 
 }  // namespace cnb
+
+namespace cnb {
+
+// The RS stage of a plan whose level 0 runs on warps (explicit depth, last reduced
+// system of at most kScanRsMax rows): Thomas' recurrences as warp scans, one warp
+//   c'_k = c_k / (a_k - b_k c'_{k-1}):  Moebius maps [[0, c_k], [-b_k, a_k]] of c'_{k-1}
+//   z_k = (d_k - b_k z_{k-1}) / m_k:    affine maps;   x_k = z_k - c'_k x_{k+1}: affine maps
+// with each lane re-running its rows as k_base_serial does.  Taken in binary64;
+// in double-float the one-thread walk is the faster (its dependent operations
+// cost a few clocks, not ~64).
+constexpr int kScanRsMax = 512;
+__host__ __device__ constexpr size_t scan_rs_entries(int n) { return 7 * (size_t)n; }
+
+template <class R>
+__global__ void __launch_bounds__(32)
+k_base_scan(LevelSource<R> src, typename Store<R>::T* x, int* status) {
+    grid_dep_enter();
+    typedef typename Store<R>::T ST;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = (int)src.n;
+    ST* const sa = reinterpret_cast<ST*>(smem_raw);
+    ST* const sb = sa + n;
+    ST* const sc = sb + n;
+    ST* const sd = sc + n;
+    ST* const si = sd + n;  // 1 / m_k
+    ST* const sp = si + n;  // c'_k
+    ST* const sz = sp + n;  // z_k
+    const int lane = threadIdx.x;
+    const int c = (n + 31) / 32;
+    const int k0 = min(n, lane * c), k1 = min(n, k0 + c);
+    bool ok = true;
+    for (int k = k0; k < k1; ++k) {
+        const Row<R> r = src.template row_at<R>(k);
+        sstore(sa + k, r.a);
+        sstore(sb + k, r.b);
+        sstore(sc + k, r.c);
+        sstore(sd + k, r.d);
+    }
+    // pivots and c'
+    {
+        Mob<R> M = mob_identity<R>();
+        for (int k = k0; k < k1; ++k) {
+            const cx<R> a = sload(sa + k), b = sload(sb + k), cc = sload(sc + k);
+            Mob<R> r;  // [[0, c], [-b, a]] M
+            r.a = cmul(cc, M.c);
+            r.b = cmul(cc, M.d);
+            r.c = csub(cmul(a, M.c), cmul(b, M.a));
+            r.d = csub(cmul(a, M.d), cmul(b, M.b));
+            M = ((k - k0) & 7) == 7 ? mob_normalize(r) : r;
+        }
+        const Mob<R> X = scan_up_exclusive(mob_normalize(M), lane);
+        cx<R> cp = cmul(X.b, crcp(X.d, ok));  // c'_{k0 - 1} (c'_{-1} = 0)
+        for (int k = k0; k < k1; ++k) {
+            const cx<R> a = sload(sa + k);
+            const cx<R> piv = k == 0 ? a : csub(a, cmul(sload(sb + k), cp));
+            const cx<R> iv = crcp(piv, ok);
+            cp = cmul(sload(sc + k), iv);
+            sstore(si + k, iv);
+            sstore(sp + k, cp);
+        }
+    }
+    __syncwarp();
+    // z
+    {
+        Aff<R> F = aff_identity<R>();
+        for (int k = k0; k < k1; ++k) {
+            const cx<R> iv = sload(si + k);
+            Aff<R> f;  // z -> -b iv z + d iv
+            f.m = k == 0 ? czero<R>() : cneg(cmul(sload(sb + k), iv));
+            f.a = cmul(sload(sd + k), iv);
+            F = aff_after(f, F);
+        }
+        cx<R> z = scan_up_exclusive(F, lane).a;  // z_{k0 - 1}
+        for (int k = k0; k < k1; ++k) {
+            const cx<R> d = sload(sd + k), iv = sload(si + k);
+            z = k == 0 ? cmul(d, iv) : cmul(csub(d, cmul(sload(sb + k), z)), iv);
+            sstore(sz + k, z);
+        }
+    }
+    __syncwarp();
+    // x, backward from x_{n-1} = z_{n-1}
+    const cx<R> ztop = sload(sz + n - 1);
+    const int b1 = min(k1, n - 1);
+    Aff<R> B = aff_identity<R>();
+    for (int k = b1 - 1; k >= k0; --k) {
+        Aff<R> f;  // y -> -c' y + z
+        f.m = cneg(sload(sp + k));
+        f.a = sload(sz + k);
+        B = aff_after(f, B);
+    }
+    const Aff<R> Yb = scan_down_exclusive(B, lane);
+    cx<R> y = cfma(Yb.a, Yb.m, ztop);
+    for (int k = b1 - 1; k >= k0; --k) {
+        y = csub(sload(sz + k), cmul(sload(sp + k), y));
+        sstore(x + k, y);
+    }
+    if (k0 <= n - 1 && n - 1 < k1) sstore(x + n - 1, ztop);
+    if (!ok) flag_error(status, kStatusNonfinite);
+}
+
+}  // namespace cnb
