@@ -34,8 +34,9 @@ constexpr int64_t kScanMaxBlocks = 4096;  // latency regime only: few blocks
 
 // shared memory of the scan kernels, in storage entries: a~, d^, w, d^RD, Q (reduction)
 // or d^, w, z (substitution) for rows 0..m
-__host__ __device__ constexpr size_t scan_reduce_entries(int m) { return 5 * (size_t)(m + 1); }
-__host__ __device__ constexpr size_t scan_subst_entries(int m) { return 3 * (size_t)(m + 1); }
+constexpr int kScanPad = 32;
+__host__ __device__ constexpr size_t scan_reduce_entries(int m) { return 5 * (size_t)(m + kScanPad); }
+__host__ __device__ constexpr size_t scan_subst_entries(int m) { return 3 * (size_t)(m + kScanPad); }
 
 template <class T> __device__ __forceinline__ T shfl_word_up(const T& v, int d) {
     static_assert(sizeof(T) % sizeof(int) == 0, "shuffled in 32-bit words");
@@ -178,6 +179,16 @@ template <class R> __device__ __forceinline__ Aff<R> scan_down_exclusive(Aff<R> 
     const Aff<R> x = shfl_word_down(v, 1);
     return lane == 31 ? aff_identity<R>() : x;
 }
+// products: each lane gets the product of the lanes below it (1 on lane 0)
+template <class R> __device__ __forceinline__ cx<R> scan_up_exclusive_prod(cx<R> v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const cx<R> o = shfl_word_up(v, d);
+        if (lane >= d) v = cmul(o, v);
+    }
+    const cx<R> x = shfl_word_up(v, 1);
+    return lane == 0 ? cfrom<R>(1.0, 0.0) : x;
+}
 template <class R> __device__ __forceinline__ cx<R> warp_sum(cx<R> v) {
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) v = cadd(v, shfl_word_xor(v, d));
@@ -186,13 +197,24 @@ template <class R> __device__ __forceinline__ cx<R> warp_sum(cx<R> v) {
 
 // Block t's rows 1..g-1 are dealt to the lanes in runs of c = ceil((g - 1) / 32):
 // lane l takes rows k0 = 1 + l c .. k1 - 1 (none if k0 >= g).
+// Row k's entry in the warp's shared arrays: lane-interleaved (the j-th row of every
+// lane's run side by side), so that a warp's access to its lanes' rows is
+// conflict-free; row 0 after them.  Arrays hold kScanPad + m entries.
 struct ScanRows {
-    int gap, k0, k1;
-    __device__ __forceinline__ ScanRows(int g, int lane) : gap(g) {
-        const int c = (g - 1 + 31) / 32;
-        k0 = 1 + lane * c;
+    int gap, c, k0, k1, lane;
+    __device__ __forceinline__ ScanRows(int g, int l) : gap(g), lane(l) {
+        c = (g - 1 + 31) / 32;
+        k0 = 1 + l * c;
         k1 = min(g, k0 + c);
     }
+    // any row
+    __device__ __forceinline__ int pos(int k) const {
+        if (k == 0) return 32 * c;
+        const int l = (k - 1) / c;
+        return (k - 1 - l * c) * 32 + l;
+    }
+    // one of the lane's own rows k0 .. k1 - 1
+    __device__ __forceinline__ int own(int k) const { return (k - k0) * 32 + lane; }
 };
 // keep entries of block t, row k, field j (0: d^, 1: w), in the one-thread kernels' layout
 template <class ST> __device__ __forceinline__ ST* scan_keep(ST* keep0, int64_t t, int m, int k, int j) {
@@ -211,10 +233,10 @@ k_cn_reduce_scan(CNStep st, OneSys sys, OneSys next, OneGrid grid, int m, int m_
     typedef typename Store<R>::T ST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ST* const sA = reinterpret_cast<ST*>(smem_raw);  // a~_k
-    ST* const sD = sA + (m + 1);                      // d^_k
-    ST* const sW = sD + (m + 1);                      // w_k, w_0 = 0
-    ST* const sR = sW + (m + 1);                      // RD's d_k
-    ST* const sQ = sR + (m + 1);                      // RU's Q_k
+    ST* const sD = sA + (m + kScanPad);               // d^_k
+    ST* const sW = sD + (m + kScanPad);               // w_k, w_0 = 0
+    ST* const sR = sW + (m + kScanPad);               // RD's d_k
+    ST* const sQ = sR + (m + kScanPad);               // RU's Q_k
     const int lane = threadIdx.x;
     const int64_t t = blockIdx.x;
     const LvlSys& e = sys.at(0);
@@ -223,7 +245,21 @@ k_cn_reduce_scan(CNStep st, OneSys sys, OneSys next, OneGrid grid, int m, int m_
     const ScanRows rw((int)(joint_line(t + 1, P, m, n) - J0), lane);
     const int gap = rw.gap, k0 = rw.k0, k1 = rw.k1;
     bool ok = true;
-    // scaled rows: a~_k and d^_k (row k0's stencil takes psi_{k0 - 1}: not a joint row)
+    // scaled rows: a~_k and d^_k (row k0's stencil takes psi_{k0 - 1}: not a joint row);
+    // the lane's psi and coefficient-table spans are fetched into L1 first, all lines
+    // in flight together
+    if (k0 < k1) {
+        const char* ps = st.psi ? reinterpret_cast<const char*>(st.psi + e.row_off + J0 + k0 - 1) : nullptr;
+        const char* pe = st.psi ? reinterpret_cast<const char*>(st.psi + e.row_off + min(J0 + k1 + 1, n)) : nullptr;
+        for (const char* q = ps; q < pe; q += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
+        if (st.tab) {
+            typedef typename CoefTab<R>::T TT;
+            const TT* tb = static_cast<const TT*>(st.tab) + e.row_off;
+            const char* ts = reinterpret_cast<const char*>(tb + J0 + k0);
+            const char* te = reinterpret_cast<const char*>(tb + J0 + k1);
+            for (const char* q = ts; q < te; q += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
+        }
+    }
     if (k0 < k1) {
         CNRowStream<R, ES> rs;
         rs.init(st, e, grid.at(0), J0 + k0);
@@ -231,80 +267,85 @@ k_cn_reduce_scan(CNStep st, OneSys sys, OneSys next, OneGrid grid, int m, int m_
         for (int k = k0; k < k1; ++k) {
             cx<R> a, d;
             rs.next(a, d);
-            sstore(sA + k, a);
-            sstore(sD + k, d);
+            sstore(sA + rw.own(k), a);
+            sstore(sD + rw.own(k), d);
         }
     }
-    if (lane == 0) sstore(sW, czero<R>());
+    if (lane == 0) sstore(sW + rw.pos(0), czero<R>());
     __syncwarp();
     // RD pivots: w_k = 1 / (a~_k - w_{k-1})
     {
         Mob<R> M = mob_identity<R>();
         for (int k = k0; k < k1; ++k) {
-            M = mob_pivot_after(sload(sA + k), M);
+            M = mob_pivot_after(sload(sA + rw.own(k)), M);
             if (((k - k0) & 7) == 7) M = mob_normalize(M);
         }
         const Mob<R> X = scan_up_exclusive(mob_normalize(M), lane);
         cx<R> w = cmul(X.b, crcp(X.d, ok));  // w_{k0 - 1}: X applied to (w_0, 1) = (0, 1)
         for (int k = k0; k < k1; ++k) {
-            w = crcp(csub(sload(sA + k), w), ok);
-            sstore(sW + k, w);
+            w = crcp(csub(sload(sA + rw.own(k)), w), ok);
+            sstore(sW + rw.own(k), w);
         }
     }
     __syncwarp();
     // RD right-hand side: d_k = d^_k + w_{k-1} d_{k-1}
     {
+        const cx<R> wk0 = k0 < k1 ? sload(sW + rw.pos(k0 - 1)) : czero<R>();  // w_{k0 - 1}
         Aff<R> F = aff_identity<R>();
+        cx<R> wp = wk0;
         for (int k = k0; k < k1; ++k) {
             Aff<R> f;
-            f.m = sload(sW + k - 1);
-            f.a = sload(sD + k);
+            f.m = wp;
+            f.a = sload(sD + rw.own(k));
             F = aff_after(f, F);
+            wp = sload(sW + rw.own(k));
         }
         cx<R> y = scan_up_exclusive(F, lane).a;  // d_{k0 - 1} (d_0 = 0)
+        wp = wk0;
         for (int k = k0; k < k1; ++k) {
-            y = k == 1 ? sload(sD + 1) : cfma(sload(sD + k), sload(sW + k - 1), y);
-            sstore(sR + k, y);
+            y = k == 1 ? sload(sD + rw.own(1)) : cfma(sload(sD + rw.own(k)), wp, y);
+            sstore(sR + rw.own(k), y);
+            wp = sload(sW + rw.own(k));
         }
     }
     // RU products: Q_1 = 1, Q_k = Q_{k-1} w_k
     {
-        Aff<R> F = aff_identity<R>();
-        for (int k = max(k0, 2); k < k1; ++k) {
-            Aff<R> f;
-            f.m = sload(sW + k);
-            f.a = czero<R>();
-            F = aff_after(f, F);
-        }
-        cx<R> q = scan_up_exclusive(F, lane).m;  // Q_{k0 - 1}
+        cx<R> F = cfrom<R>(1.0, 0.0);
+        for (int k = max(k0, 2); k < k1; ++k) F = cmul(F, sload(sW + rw.own(k)));
+        cx<R> q = scan_up_exclusive_prod(F, lane);  // Q_{k0 - 1}
         for (int k = k0; k < k1; ++k) {
-            q = k == 1 ? cfrom<R>(1.0, 0.0) : cmul(q, sload(sW + k));
-            sstore(sQ + k, q);
+            q = k == 1 ? cfrom<R>(1.0, 0.0) : cmul(q, sload(sW + rw.own(k)));
+            sstore(sQ + rw.own(k), q);
         }
     }
     __syncwarp();
     // RU sums: S = sum_{k>=2} Q_k Q_{k-1},  nd = d_1 + sum_{k>=2} Q_k d_k
     cx<R> s = czero<R>(), nd = czero<R>();
-    for (int k = k0; k < k1; ++k) {
-        if (k == 1) {
-            nd = sload(sR + 1);
-            continue;
+    {
+        cx<R> qp = k0 > 1 && k0 < k1 ? sload(sQ + rw.pos(k0 - 1)) : czero<R>();  // Q_{k0 - 1}
+        for (int k = k0; k < k1; ++k) {
+            const cx<R> Qk = sload(sQ + rw.own(k));
+            if (k == 1) {
+                nd = sload(sR + rw.own(1));
+            } else {
+                s = cfma(s, Qk, qp);
+                nd = cfma(nd, Qk, sload(sR + rw.own(k)));
+            }
+            qp = Qk;
         }
-        const cx<R> Qk = sload(sQ + k);
-        s = cfma(s, Qk, sload(sQ + k - 1));
-        nd = cfma(nd, Qk, sload(sR + k));
     }
     const cx<R> S = warp_sum(s), ND = warp_sum(nd);
     // the kept values of the substitution
     for (int k = k0; k < k1; ++k) {
-        sstore(scan_keep(keep0, t, m, k, 0), sload(sD + k));
-        sstore(scan_keep(keep0, t, m, k, 1), sload(sW + k));
+        sstore(scan_keep(keep0, t, m, k, 0), sload(sD + rw.own(k)));
+        sstore(scan_keep(keep0, t, m, k, 1), sload(sW + rw.own(k)));
     }
     if (!ok) flag_error(status, kStatusNonfinite);
     if (lane != 0) return;
     // JD on row J_{t+1}, JU on row J_t (as cn_reduce_block)
     const cx<R> one = cfrom<R>(1.0, 0.0);
-    const cx<R> w1 = sload(sW + 1), wl = sload(sW + gap - 1), dl = sload(sR + gap - 1), Ql = sload(sQ + gap - 1);
+    const cx<R> w1 = sload(sW + rw.pos(1)), wl = sload(sW + rw.pos(gap - 1));
+    const cx<R> dl = sload(sR + rw.pos(gap - 1)), Ql = sload(sQ + rw.pos(gap - 1));
     CNRowStream<R, ES> r0;  // row J_t, its own share (psi_{J_t - 1} is the block above's)
     r0.init(st, e, grid.at(0), J0);
     cx<R> A0, D0;
@@ -352,8 +393,8 @@ k_cn_substitute_scan(OneSys sys, OneSys next, int m, const typename Store<R>::T*
     typedef typename Store<R>::T ST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ST* const sD = reinterpret_cast<ST*>(smem_raw);
-    ST* const sW = sD + (m + 1);
-    ST* const sZ = sW + (m + 1);
+    ST* const sW = sD + (m + kScanPad);
+    ST* const sZ = sW + (m + kScanPad);
     const int lane = threadIdx.x;
     const int64_t t = blockIdx.x;
     const LvlSys& e = sys.at(0);
@@ -364,15 +405,15 @@ k_cn_substitute_scan(OneSys sys, OneSys next, int m, const typename Store<R>::T*
     const ST* x_next = x_next0 + next.at(0).row_off;
     const cx<R> xL = sload(x_next + t), xR = sload(x_next + t + 1);
     for (int k = k0; k < k1; ++k) {
-        sstore(sD + k, sload(scan_keep(keep0, t, m, k, 0)));
-        sstore(sW + k, sload(scan_keep(keep0, t, m, k, 1)));
+        sstore(sD + rw.own(k), sload(scan_keep(keep0, t, m, k, 0)));
+        sstore(sW + rw.own(k), sload(scan_keep(keep0, t, m, k, 1)));
     }
     // forward sweep
     {
         Aff<R> F = aff_identity<R>();
         for (int k = k0; k < k1; ++k) {
-            const cx<R> w = sload(sW + k);
-            const cx<R> dd = k == gap - 1 ? cadd(sload(sD + k), xR) : sload(sD + k);
+            const cx<R> w = sload(sW + rw.own(k));
+            const cx<R> dd = k == gap - 1 ? cadd(sload(sD + rw.own(k)), xR) : sload(sD + rw.own(k));
             Aff<R> f;  // z -> w z + w (d^ (+ x_R))
             f.m = w;
             f.a = cmul(dd, w);
@@ -381,27 +422,27 @@ k_cn_substitute_scan(OneSys sys, OneSys next, int m, const typename Store<R>::T*
         const Aff<R> Z = scan_up_exclusive(F, lane);
         cx<R> z = cfma(Z.a, Z.m, xL);  // z_{k0 - 1}
         for (int k = k0; k < k1; ++k) {
-            const cx<R> w = sload(sW + k), d = sload(sD + k);
+            const cx<R> w = sload(sW + rw.own(k)), d = sload(sD + rw.own(k));
             z = k == gap - 1 ? cmul(cadd(cadd(d, z), xR), w) : cmul(cadd(d, z), w);
-            sstore(sZ + k, z);
+            sstore(sZ + rw.own(k), z);
         }
     }
     __syncwarp();
     // backward sweep over rows g-2 .. 1
-    const cx<R> ztop = sload(sZ + gap - 1);
+    const cx<R> ztop = sload(sZ + rw.pos(gap - 1));
     const int b1 = min(k1, gap - 1);  // the lane's rows below g - 1: k0 .. b1 - 1
     Aff<R> B = aff_identity<R>();
     for (int k = b1 - 1; k >= k0; --k) {
         Aff<R> f;  // y -> w_k y + z_k
-        f.m = sload(sW + k);
-        f.a = sload(sZ + k);
+        f.m = sload(sW + rw.own(k));
+        f.a = sload(sZ + rw.own(k));
         B = aff_after(f, B);
     }
     const Aff<R> Yb = scan_down_exclusive(B, lane);
     double2* x = x_out + e.row_off;
     cx<R> y = cfma(Yb.a, Yb.m, ztop);  // x_{b1}
     for (int k = b1 - 1; k >= k0; --k) {
-        y = cfma(sload(sZ + k), sload(sW + k), y);
+        y = cfma(sload(sZ + rw.own(k)), sload(sW + rw.own(k)), y);
         store128(x + J0 + k, y);
     }
     if (k0 <= gap - 1 && gap - 1 < k1) store128(x + J0 + gap - 1, ztop);
