@@ -121,9 +121,10 @@ typedef struct {
 /* cn_desc.flags: level 0 one thread per block whatever the blocks (the paper's
  * per-process serial elimination, Sec. 4.1; the partition study's model).  Without
  * it, a single system in store mode whose level-0 blocks are 64 .. 1024 rows long
- * and at most 4096 in number is reduced and substituted by one warp per block, the
- * recurrences as warp prefix scans (cn_plan_info.level0_lanes = 32): the same
- * solution up to rounding, at a fraction of the latency. */
+ * and at most 4096 in number is reduced and substituted by one CTA per block (up
+ * to four warps, two rows a thread or more), the recurrences as prefix scans
+ * (cn_plan_info.level0_lanes threads, 32 .. 128): the same solution up to
+ * rounding, at a fraction of the latency. */
 #define CN_FLAG_SERIAL_BLOCKS 16
 
 /* Create a plan for systems of size desc->n.  The N-shaped solve is nested
@@ -255,9 +256,9 @@ typedef struct {
     int32_t level_block[CN_MAX_LEVELS];  /* rows per block of level 0 .. levels-1         */
     int64_t workspace_bytes;             /* device memory the plan holds                  */
     int32_t level0_lanes;                /* threads that reduce and substitute one level-0
-                                            block: 1, or 32 (a warp, the recurrences as
-                                            prefix scans) for few blocks of 64 .. 1024 rows
-                                            of one system in store mode                    */
+                                            block: 1, or 32 .. 128 (a CTA, the recurrences
+                                            as prefix scans) for few blocks of 64 .. 1024
+                                            rows of one system in store mode               */
 } cn_plan_info;
 cn_status cn_plan_query(cn_plan plan, cn_plan_info* out);
 

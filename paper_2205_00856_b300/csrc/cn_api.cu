@@ -54,7 +54,7 @@ struct Engine {
     int sms = 0;                  // multiprocessors of the device
     bool pdl = true;              // launch with programmatic stream serialization
     bool batched = false;
-    bool scan0 = false;           // level 0 by one warp per block (cn_scan.cuh): few long blocks
+    bool scan0 = false;           // level 0 by one CTA per block (cn_scan.cuh): few long blocks
     int nsys = 0;
     std::vector<LevelData> lv;    // lv[0]: the systems themselves
     std::vector<int> base_level;  // per system: the level the RS stage solves
@@ -198,6 +198,14 @@ size_t zc_entries_of(const Engine* p) {
 // Extents of the buffers a call may touch, installed in the kernels' range table
 // (cn_debug.cuh) on the call's stream before its first launch.  No-ops in the
 // default build.
+// kept (d^, w) of level 0 (store mode), in entries: 2 m per block in chunks of 128
+// blocks (one per CTA of the one-thread kernels' grid), or the scan kernels' 2 (m + nt)
+// per block
+size_t keep_entries(const Engine* p) {
+    const LevelData& L0 = p->lv[0];
+    if (p->scan0) return scan_keep_entries(L0.m, L0.total);
+    return 2 * (size_t)L0.m * (size_t)grid_for(L0.total) * kThreads;
+}
 #if defined(CN_DEBUG)
 struct DbgList {
     std::vector<std::pair<const void*, size_t>> v;
@@ -207,7 +215,7 @@ struct DbgList {
 };
 
 size_t keep_bytes(const Engine* p) {
-    return p->keep ? kCplx * 2 * (size_t)p->lv[0].m * (size_t)grid_for(p->lv[0].total) * kThreads : 0;
+    return p->keep ? kCplx * keep_entries(p) : 0;
 }
 
 void dbg_engine(const Engine* p, DbgList& L) {
@@ -374,8 +382,8 @@ cudaError_t build_hierarchy(Engine* p, const std::vector<int64_t>& sizes) {
         p->lv.push_back(std::move(L));
         if (boff == 0) break;
     }
-    // few long level-0 blocks of one system (store mode): one warp per block, the
-    // recurrences as warp scans (cn_scan.cuh); level 1 then takes one slot per block
+    // few long level-0 blocks of one system (store mode): one CTA per block, the
+    // recurrences as prefix scans (cn_scan.cuh); level 1 then takes one slot per block
     p->scan0 = !p->batched && !p->slab && !(p->desc.flags & (CN_FLAG_RECOMPUTE | CN_FLAG_SERIAL_BLOCKS)) &&
                p->lv.size() >= 2 &&
                p->lv[0].m >= kScanMinRows && p->lv[0].m <= kScanMaxRows && p->lv[0].total <= kScanMaxBlocks;
@@ -660,7 +668,7 @@ cudaError_t rs_stage(Engine* p, cudaStream_t st) {
     const LevelSource<R> src = level_source<R>(B).bind(B.sys[0]);
     if (p->lvl_m.empty())
         return launch(p->pdl, k_base_cr<R>, 1, kCrThreads, cr_smem(), st, src, x_of<R>(B), p->status);
-    // level 0 on warps, binary64: the RS stage on one warp too (17 rows of the paper's small
+    // level 0 by scans, binary64: the RS stage on one warp too (17 rows of the paper's small
     // case: 30 -> 21 us on B300; in double-float the one-thread walk is the faster, 16 us)
     if (std::is_same<R, double>::value && p->scan0 && src.n <= kScanRsMax)
         return launch(p->pdl, k_base_scan<R>, 1, 32, scan_rs_entries((int)src.n) * kCplx, st, src, x_of<R>(B),
@@ -780,7 +788,8 @@ cudaError_t cn_reduce0(Engine* p, const CNStep& s, cudaStream_t st) {
     ProfScope ps(p, kProfReduce0, st);
     if (p->scan0)
         return with_es(s, [&](auto es) {
-            return launch(p->pdl, k_cn_reduce_scan<R, decltype(es)::value>, (unsigned)L0.total, 32,
+            return launch(p->pdl, k_cn_reduce_scan<R, decltype(es)::value>, (unsigned)L0.total,
+                          (unsigned)scan_threads(L0.m),
                           scan_reduce_entries(L0.m) * kCplx, st, s, OneSys{L0.sys[0]}, OneSys{L1.sys[0]},
                           OneGrid{p->grid[0]}, L0.m, L1.m, planes_of<R>(L1), slot_of<R>(L1),
                           static_cast<ST*>(p->keep), p->status);
@@ -805,7 +814,8 @@ cudaError_t cn_subst0(Engine* p, const CNStep& s, double2* x, cudaStream_t st) {
     ST* keep = static_cast<ST*>(p->keep);
     ProfScope ps(p, kProfSubst0, st);
     if (p->scan0)
-        return launch(p->pdl, k_cn_substitute_scan<R>, (unsigned)L0.total, 32, scan_subst_entries(L0.m) * kCplx, st,
+        return launch(p->pdl, k_cn_substitute_scan<R>, (unsigned)L0.total, (unsigned)scan_threads(L0.m),
+                      scan_subst_entries(L0.m) * kCplx, st,
                       OneSys{L0.sys[0]}, OneSys{L1.sys[0]}, L0.m, static_cast<const ST*>(keep),
                       static_cast<const ST*>(x_of<R>(L1)), x);
     return with_es(s, [&](auto es) {
@@ -982,11 +992,10 @@ cn_status create_engine(Engine* p, const cn_desc* desc, const std::vector<int64_
     if (e == cudaErrorInvalidValue) return p->lvl_m.empty() ? CN_ERR_UNSUPPORTED : CN_ERR_INVALID_ARG;
     if (e != cudaSuccess) return alloc_status(e);
     const int64_t rows0 = p->lv[0].rows_total;
-    // keep: 2 m entries per block, in chunks of 128 blocks (one per CTA of the level-0 grid)
-    const size_t keep_entries = 2 * (size_t)p->lv[0].m * (size_t)grid_for(p->lv[0].total) * kThreads;
-    p->workspace_bytes += (int64_t)(recompute ? kCplx * rows0 : kCplx * keep_entries) + (int64_t)sizeof(int);
+    const size_t kept = keep_entries(p);
+    p->workspace_bytes += (int64_t)(recompute ? kCplx * rows0 : kCplx * kept) + (int64_t)sizeof(int);
     if (recompute) e = cudaMalloc(&p->state, kCplx * (size_t)rows0);
-    else e = cudaMalloc(&p->keep, kCplx * keep_entries);
+    else e = cudaMalloc(&p->keep, kCplx * kept);
     if (e == cudaSuccess) e = cudaMalloc(&p->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(int));
     if (e == cudaSuccess && use_table) {
@@ -1089,7 +1098,7 @@ cn_status fill_workspace(Engine* p, int byte) {
     };
     const int64_t rows0 = p->lv[0].rows_total;
     if (p->keep)
-        fill(p->keep, kCplx * 2 * (size_t)p->lv[0].m * (size_t)grid_for(p->lv[0].total) * kThreads);
+        fill(p->keep, kCplx * keep_entries(p));
     fill(p->state, kCplx * (size_t)rows0);
     for (size_t l = 1; l < p->lv.size(); ++l) {
         const LevelData& L = p->lv[l];
@@ -1430,7 +1439,7 @@ cn_status cn_plan_query(cn_plan p, cn_plan_info* out) {
     }
     out->launches_per_step = p->persistent ? 3 : 2 * out->levels + 1;
     out->workspace_bytes = p->workspace_bytes;
-    out->level0_lanes = p->scan0 ? 32 : 1;
+    out->level0_lanes = p->scan0 ? scan_threads(p->lv[0].m) : 1;
     return CN_OK;
 }
 

@@ -1,11 +1,11 @@
-// Level 0 of few long blocks: one warp per block, prefix scans.
+// Level 0 of few long blocks: one CTA per block, prefix scans.
 //
 // The paper's own partition of its small case (n = 4096 in P = 16 blocks of 256
 // rows, Sec. 4.1.1) walks each block with one thread.  On B300 every dependent
 // binary64 operation costs a warp ~64 clocks, so a 256-row walk is ~0.7 M clocks
-// per step however few blocks there are.  Here the 32 lanes of a warp share one
-// block's rows (ceil((g - 1) / 32) consecutive rows each) and every recurrence of
-// Table 1's RD/RU on the block and of its SS becomes a warp prefix scan:
+// per step however few blocks there are.  Here the threads of a CTA share one
+// block's rows (about kScanRowsPerThread consecutive rows each) and every
+// recurrence of Table 1's RD/RU on the block and of its SS becomes a prefix scan:
 //   pivots       w_k = 1 / (a~_k - w_{k-1}), w_0 = 0: a Moebius map of w_{k-1},
 //                composed as the 2x2 matrices F_k = [[0, 1], [-1, a~_k]]
 //                (w_k = num / den of F_k ... F_1 (0, 1)^T);
@@ -14,29 +14,25 @@
 //   RU's sums    S = sum_{k>=2} Q_k Q_{k-1},  d_1 + sum_{k>=2} Q_k d_k: reductions;
 //   SS           z_k = (d^_k + z_{k-1}) w_k from z_0 = x_L, then
 //                x_k = z_k + w_k x_{k+1} from x_{g-1} = z_{g-1}: affine maps.
-// Each lane composes the maps of its rows, a Kogge-Stone scan over the lanes
-// gives every lane the composition of the rows before its own (after them, for
-// the backward sweep), and each lane then re-runs its rows' recurrences from
-// that start value exactly as the one-thread kernels do.  The results are those
-// of the one-thread elimination up to rounding (the start values of the lanes'
-// chains are formed in a different order).  Projective matrix products are
-// rescaled by powers of two (exact) so that they neither overflow nor vanish.
-// The level-1 rows take this block's JU part; its JD part goes to slot t + 1,
-// one slot per block (the level's slot_shift 0), and the reader adds it.
+// Each thread composes the maps of its rows, a Kogge-Stone scan over the lanes of
+// each warp and one over the warps' totals give every thread the composition of
+// the rows before its own (after them, for the backward sweep), and each thread
+// then re-runs its rows' recurrences from that start value exactly as the
+// one-thread kernels do.  The results are those of the one-thread elimination up
+// to rounding (the start values of the threads' chains are formed in a different
+// order).  Projective matrix products are rescaled by powers of two (exact) so
+// that they neither overflow nor vanish.  The level-1 rows take this block's JU
+// part; its JD part goes to slot t + 1, one slot per block (the level's
+// slot_shift 0), and the reader adds it.  The RS stage of such plans, when short,
+// runs Thomas' recurrences as scans over one warp (k_base_scan, binary64).
 #pragma once
 #include "cn_kernels.cuh"
 
 namespace cnb {
 
 constexpr int kScanMinRows = 64;     // level-0 blocks at least this long take the scan kernels
-constexpr int kScanMaxRows = 1024;   // ... and at most this long (shared memory per warp)
+constexpr int kScanMaxRows = 1024;   // ... and at most this long (shared memory per CTA)
 constexpr int64_t kScanMaxBlocks = 4096;  // latency regime only: few blocks
-
-// shared memory of the scan kernels, in storage entries: a~, d^, w, d^RD, Q (reduction)
-// or d^, w, z (substitution) for rows 0..m
-constexpr int kScanPad = 32;
-__host__ __device__ constexpr size_t scan_reduce_entries(int m) { return 5 * (size_t)(m + kScanPad); }
-__host__ __device__ constexpr size_t scan_subst_entries(int m) { return 3 * (size_t)(m + kScanPad); }
 
 template <class T> __device__ __forceinline__ T shfl_word_up(const T& v, int d) {
     static_assert(sizeof(T) % sizeof(int) == 0, "shuffled in 32-bit words");
@@ -149,117 +145,187 @@ template <class R> __device__ __forceinline__ Aff<R> aff_after(const Aff<R>& L, 
     r.a = cfma(L.a, L.m, E.a);
     return r;
 }
-// Kogge-Stone scans over the 32 lanes: "up" composes lane l with every lane below
-// it (forward recurrences), "down" with every lane above it (backward ones);
-// the exclusive forms give each lane the composition of the others' maps only.
-template <class R> __device__ __forceinline__ Mob<R> scan_up_exclusive(Mob<R> v, int lane) {
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const Mob<R> o = shfl_word_up(v, d);
-        if (lane >= d) v = mob_after(v, o);
-    }
-    const Mob<R> x = shfl_word_up(v, 1);
-    return lane == 0 ? mob_identity<R>() : x;
+// products of complex numbers, earlier factor first
+template <class R> struct Prod {
+    cx<R> v;
+};
+// "L after E" for the three kinds of map, and their identities
+template <class R> __device__ __forceinline__ Mob<R> after(const Mob<R>& L, const Mob<R>& E) { return mob_after(L, E); }
+template <class R> __device__ __forceinline__ Aff<R> after(const Aff<R>& L, const Aff<R>& E) { return aff_after(L, E); }
+template <class R> __device__ __forceinline__ Prod<R> after(const Prod<R>& L, const Prod<R>& E) {
+    Prod<R> r;
+    r.v = cmul(E.v, L.v);
+    return r;
 }
-template <class R> __device__ __forceinline__ Aff<R> scan_up_exclusive(Aff<R> v, int lane) {
+template <class R> __device__ __forceinline__ void set_identity(Mob<R>& v) { v = mob_identity<R>(); }
+template <class R> __device__ __forceinline__ void set_identity(Aff<R>& v) { v = aff_identity<R>(); }
+template <class R> __device__ __forceinline__ void set_identity(Prod<R>& v) { v.v = cfrom<R>(1.0, 0.0); }
+
+// Kogge-Stone scans over the lanes 0 .. width-1 of a warp: "up" composes lane l
+// with every lane below it (forward recurrences), "down" with every lane above it
+// (backward ones); the exclusive forms give each lane the composition of the
+// others' maps only.
+template <class V> __device__ __forceinline__ V warp_inclusive_up(V v, int lane, int width) {
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const Aff<R> o = shfl_word_up(v, d);
-        if (lane >= d) v = aff_after(v, o);
+    for (int d = 1; d < width; d <<= 1) {
+        const V o = shfl_word_up(v, d);
+        if (lane >= d) v = after(v, o);
     }
-    const Aff<R> x = shfl_word_up(v, 1);
-    return lane == 0 ? aff_identity<R>() : x;
+    return v;
 }
-template <class R> __device__ __forceinline__ Aff<R> scan_down_exclusive(Aff<R> v, int lane) {
+template <class V> __device__ __forceinline__ V warp_inclusive_down(V v, int lane, int width) {
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const Aff<R> o = shfl_word_down(v, d);
-        if (lane + d < 32) v = aff_after(v, o);
+    for (int d = 1; d < width; d <<= 1) {
+        const V o = shfl_word_down(v, d);
+        if (lane + d < width) v = after(v, o);
     }
-    const Aff<R> x = shfl_word_down(v, 1);
-    return lane == 31 ? aff_identity<R>() : x;
+    return v;
 }
-// products: each lane gets the product of the lanes below it (1 on lane 0)
-template <class R> __device__ __forceinline__ cx<R> scan_up_exclusive_prod(cx<R> v, int lane) {
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const cx<R> o = shfl_word_up(v, d);
-        if (lane >= d) v = cmul(o, v);
+template <class V> __device__ __forceinline__ V scan_up_exclusive(V v, int lane) {
+    v = warp_inclusive_up(v, lane, 32);
+    V x = shfl_word_up(v, 1);
+    if (lane == 0) set_identity(x);
+    return x;
+}
+template <class V> __device__ __forceinline__ V scan_down_exclusive(V v, int lane) {
+    v = warp_inclusive_down(v, lane, 32);
+    V x = shfl_word_down(v, 1);
+    if (lane == 31) set_identity(x);
+    return x;
+}
+// The same over the whole CTA (blockDim.x a multiple of 32, a few warps): each
+// warp scans its lanes, then composes the totals of the warps before its own
+// (after it, for "down") and its exclusive result with them.  tot: 32 entries of
+// shared memory, free again on return.
+template <class V> __device__ __forceinline__ V block_up_exclusive(V v, V* tot) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_inclusive_up(v, lane, 32);
+    V x = shfl_word_up(v, 1);
+    if (lane == 0) set_identity(x);
+    if (nw == 1) return x;
+    if (lane == 31) tot[wid] = v;
+    __syncthreads();
+    if (wid > 0) {
+        V pre = tot[0];
+        for (int i = 1; i < wid; ++i) pre = after(tot[i], pre);
+        x = after(x, pre);
     }
-    const cx<R> x = shfl_word_up(v, 1);
-    return lane == 0 ? cfrom<R>(1.0, 0.0) : x;
+    __syncthreads();
+    return x;
+}
+template <class V> __device__ __forceinline__ V block_down_exclusive(V v, V* tot) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_inclusive_down(v, lane, 32);
+    V x = shfl_word_down(v, 1);
+    if (lane == 31) set_identity(x);
+    if (nw == 1) return x;
+    if (lane == 0) tot[wid] = v;
+    __syncthreads();
+    if (wid < nw - 1) {
+        V pre = tot[nw - 1];
+        for (int i = nw - 2; i > wid; --i) pre = after(tot[i], pre);
+        x = after(x, pre);
+    }
+    __syncthreads();
+    return x;
 }
 template <class R> __device__ __forceinline__ cx<R> warp_sum(cx<R> v) {
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) v = cadd(v, shfl_word_xor(v, d));
     return v;
 }
+// two CTA-wide sums, valid in warp 0; tot: 64 entries of shared memory
+template <class R> __device__ __forceinline__ void block_sum2(cx<R>& s, cx<R>& u, cx<R>* tot) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    s = warp_sum(s);
+    u = warp_sum(u);
+    if (nw == 1) return;
+    if (lane == 0) {
+        tot[wid] = s;
+        tot[32 + wid] = u;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        s = tot[0];
+        u = tot[32];
+        for (int i = 1; i < nw; ++i) {
+            s = cadd(s, tot[i]);
+            u = cadd(u, tot[32 + i]);
+        }
+    }
+}
 
-// Block t's rows 1..g-1 are dealt to the lanes in runs of c = ceil((g - 1) / 32):
-// lane l takes rows k0 = 1 + l c .. k1 - 1 (none if k0 >= g).
-// Row k's entry in the warp's shared arrays: lane-interleaved (the j-th row of every
-// lane's run side by side), so that a warp's access to its lanes' rows is
-// conflict-free; row 0 after them.  Arrays hold kScanPad + m entries.
+// Block t's rows 1..g-1 are dealt to the CTA's nt threads in runs of
+// c = ceil((g - 1) / nt): thread i takes rows k0 = 1 + i c .. k1 - 1 (none if
+// k0 >= g).  Row k's entry in the CTA's shared arrays: thread-interleaved (the
+// j-th row of every thread's run side by side), so that a warp's access to its
+// threads' rows is conflict-free; row 0 after them.  Arrays hold m + nt entries.
 struct ScanRows {
-    int gap, c, k0, k1, lane;
-    __device__ __forceinline__ ScanRows(int g, int l) : gap(g), lane(l) {
-        c = (g - 1 + 31) / 32;
-        k0 = 1 + l * c;
+    int gap, c, k0, k1, tid, nt;
+    __device__ __forceinline__ explicit ScanRows(int g) : gap(g), tid((int)threadIdx.x), nt((int)blockDim.x) {
+        c = (g - 1 + nt - 1) / nt;
+        k0 = 1 + tid * c;
         k1 = min(g, k0 + c);
     }
     // any row
     __device__ __forceinline__ int pos(int k) const {
-        if (k == 0) return 32 * c;
+        if (k == 0) return nt * c;
         const int l = (k - 1) / c;
-        return (k - 1 - l * c) * 32 + l;
+        return (k - 1 - l * c) * nt + l;
     }
-    // one of the lane's own rows k0 .. k1 - 1
-    __device__ __forceinline__ int own(int k) const { return (k - k0) * 32 + lane; }
+    // one of the thread's own rows k0 .. k1 - 1
+    __device__ __forceinline__ int own(int k) const { return (k - k0) * nt + tid; }
 };
-// keep entries of block t, row k, field j (0: d^, 1: w), in the one-thread kernels' layout
-template <class ST> __device__ __forceinline__ ST* scan_keep(ST* keep0, int64_t t, int m, int k, int j) {
-    return keep0 + (t >> 7) * (2 * (int64_t)m * kThreads) + (int64_t)(2 * k + j) * kThreads + (t & (kThreads - 1));
+// threads of the CTA that takes one level-0 block of m rows: about kScanRowsPerThread
+// rows each, whole warps, at most kScanMaxThreads.  A warp on B300 issues a binary64
+// instruction every ~64 clocks whatever its other warps do, and an SM takes about
+// four at a time (one per scheduler): the scans' cost is their depth in binary64
+// instructions, so four warps, each with its own scheduler, and runs of two rows
+// (m = 256 on B300: 60 us a step at 2 rows and 4 warps, 74 at 1 row and 8 warps,
+// 70 at 4 rows and 2 warps; m = 512: 74 at 4 warps, 82 at 8, 113 at 16)
+constexpr int kScanRowsPerThread = 2;
+constexpr int kScanMaxThreads = 128;
+__host__ __device__ constexpr int scan_threads(int m) {
+    const int t = ((m - 1 + kScanRowsPerThread - 1) / kScanRowsPerThread + 31) / 32 * 32;
+    return t < 32 ? 32 : (t > kScanMaxThreads ? kScanMaxThreads : t);
 }
+// entries of one shared array / one kept field per block
+__host__ __device__ constexpr size_t scan_ld(int m) { return (size_t)m + (size_t)scan_threads(m); }
+// shared memory of the scan kernels, in storage entries: a~, d^, w, d^RD, Q (reduction)
+// or d^, w, z (substitution)
+__host__ __device__ constexpr size_t scan_reduce_entries(int m) { return 5 * scan_ld(m); }
+__host__ __device__ constexpr size_t scan_subst_entries(int m) { return 3 * scan_ld(m); }
+// kept (d^, w) of block t: field j at keep0 + (2 t + j) ld, row k at its shared position
+__host__ __device__ constexpr size_t scan_keep_entries(int m, int64_t blocks) { return 2 * scan_ld(m) * (size_t)blocks; }
 
-// Level-0 reduction of block t = blockIdx.x by one warp: coefficients and explicit
+// Level-0 reduction of block t = blockIdx.x by one CTA: coefficients and explicit
 // rows, RD/JD with RU/JU (the scans above), the kept (d^, w) of every interior row,
 // and the block's JU part of level-1 row t (JD part to slot t + 1; the system's last
 // block writes row P whole).  Same arithmetic per row as cn_reduce_block.
 template <class R, int ES>
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(kScanMaxThreads)
 k_cn_reduce_scan(CNStep st, OneSys sys, OneSys next, OneGrid grid, int m, int m_next, LevelPlanes<R> out,
                  LevelSlot<R>* out_slot, typename Store<R>::T* keep0, int* status) {
     grid_dep_enter();
     typedef typename Store<R>::T ST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) unsigned char tot_raw[32 * sizeof(Mob<R>)];
+    const int ld = (int)scan_ld(m);
     ST* const sA = reinterpret_cast<ST*>(smem_raw);  // a~_k
-    ST* const sD = sA + (m + kScanPad);               // d^_k
-    ST* const sW = sD + (m + kScanPad);               // w_k, w_0 = 0
-    ST* const sR = sW + (m + kScanPad);               // RD's d_k
-    ST* const sQ = sR + (m + kScanPad);               // RU's Q_k
-    const int lane = threadIdx.x;
+    ST* const sD = sA + ld;                           // d^_k
+    ST* const sW = sD + ld;                           // w_k, w_0 = 0
+    ST* const sR = sW + ld;                           // RD's d_k
+    ST* const sQ = sR + ld;                           // RU's Q_k
+    const int tid = threadIdx.x;
     const int64_t t = blockIdx.x;
     const LvlSys& e = sys.at(0);
     const int64_t n = e.n, P = e.P;
     const int64_t J0 = joint_line(t, P, m, n);
-    const ScanRows rw((int)(joint_line(t + 1, P, m, n) - J0), lane);
+    const ScanRows rw((int)(joint_line(t + 1, P, m, n) - J0));
     const int gap = rw.gap, k0 = rw.k0, k1 = rw.k1;
+    ST* const keep = keep0 + 2 * t * ld;
     bool ok = true;
-    // scaled rows: a~_k and d^_k (row k0's stencil takes psi_{k0 - 1}: not a joint row);
-    // the lane's psi and coefficient-table spans are fetched into L1 first, all lines
-    // in flight together
-    if (k0 < k1) {
-        const char* ps = st.psi ? reinterpret_cast<const char*>(st.psi + e.row_off + J0 + k0 - 1) : nullptr;
-        const char* pe = st.psi ? reinterpret_cast<const char*>(st.psi + e.row_off + min(J0 + k1 + 1, n)) : nullptr;
-        for (const char* q = ps; q < pe; q += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
-        if (st.tab) {
-            typedef typename CoefTab<R>::T TT;
-            const TT* tb = static_cast<const TT*>(st.tab) + e.row_off;
-            const char* ts = reinterpret_cast<const char*>(tb + J0 + k0);
-            const char* te = reinterpret_cast<const char*>(tb + J0 + k1);
-            for (const char* q = ts; q < te; q += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
-        }
-    }
+    // scaled rows: a~_k and d^_k (row k0's stencil takes psi_{k0 - 1}: not a joint row)
     if (k0 < k1) {
         CNRowStream<R, ES> rs;
         rs.init(st, e, grid.at(0), J0 + k0);
@@ -271,8 +337,8 @@ k_cn_reduce_scan(CNStep st, OneSys sys, OneSys next, OneGrid grid, int m, int m_
             sstore(sD + rw.own(k), d);
         }
     }
-    if (lane == 0) sstore(sW + rw.pos(0), czero<R>());
-    __syncwarp();
+    if (tid == 0) sstore(sW + rw.pos(0), czero<R>());
+    __syncthreads();
     // RD pivots: w_k = 1 / (a~_k - w_{k-1})
     {
         Mob<R> M = mob_identity<R>();
@@ -280,14 +346,14 @@ k_cn_reduce_scan(CNStep st, OneSys sys, OneSys next, OneGrid grid, int m, int m_
             M = mob_pivot_after(sload(sA + rw.own(k)), M);
             if (((k - k0) & 7) == 7) M = mob_normalize(M);
         }
-        const Mob<R> X = scan_up_exclusive(mob_normalize(M), lane);
+        const Mob<R> X = block_up_exclusive(mob_normalize(M), reinterpret_cast<Mob<R>*>(tot_raw));
         cx<R> w = cmul(X.b, crcp(X.d, ok));  // w_{k0 - 1}: X applied to (w_0, 1) = (0, 1)
         for (int k = k0; k < k1; ++k) {
             w = crcp(csub(sload(sA + rw.own(k)), w), ok);
             sstore(sW + rw.own(k), w);
         }
     }
-    __syncwarp();
+    __syncthreads();
     // RD right-hand side: d_k = d^_k + w_{k-1} d_{k-1}
     {
         const cx<R> wk0 = k0 < k1 ? sload(sW + rw.pos(k0 - 1)) : czero<R>();  // w_{k0 - 1}
@@ -300,7 +366,7 @@ k_cn_reduce_scan(CNStep st, OneSys sys, OneSys next, OneGrid grid, int m, int m_
             F = aff_after(f, F);
             wp = sload(sW + rw.own(k));
         }
-        cx<R> y = scan_up_exclusive(F, lane).a;  // d_{k0 - 1} (d_0 = 0)
+        cx<R> y = block_up_exclusive(F, reinterpret_cast<Aff<R>*>(tot_raw)).a;  // d_{k0 - 1} (d_0 = 0)
         wp = wk0;
         for (int k = k0; k < k1; ++k) {
             y = k == 1 ? sload(sD + rw.own(1)) : cfma(sload(sD + rw.own(k)), wp, y);
@@ -310,38 +376,39 @@ k_cn_reduce_scan(CNStep st, OneSys sys, OneSys next, OneGrid grid, int m, int m_
     }
     // RU products: Q_1 = 1, Q_k = Q_{k-1} w_k
     {
-        cx<R> F = cfrom<R>(1.0, 0.0);
-        for (int k = max(k0, 2); k < k1; ++k) F = cmul(F, sload(sW + rw.own(k)));
-        cx<R> q = scan_up_exclusive_prod(F, lane);  // Q_{k0 - 1}
+        Prod<R> F;
+        F.v = cfrom<R>(1.0, 0.0);
+        for (int k = max(k0, 2); k < k1; ++k) F.v = cmul(F.v, sload(sW + rw.own(k)));
+        cx<R> q = block_up_exclusive(F, reinterpret_cast<Prod<R>*>(tot_raw)).v;  // Q_{k0 - 1}
         for (int k = k0; k < k1; ++k) {
             q = k == 1 ? cfrom<R>(1.0, 0.0) : cmul(q, sload(sW + rw.own(k)));
             sstore(sQ + rw.own(k), q);
         }
     }
-    __syncwarp();
+    __syncthreads();
     // RU sums: S = sum_{k>=2} Q_k Q_{k-1},  nd = d_1 + sum_{k>=2} Q_k d_k
-    cx<R> s = czero<R>(), nd = czero<R>();
+    cx<R> S = czero<R>(), ND = czero<R>();
     {
         cx<R> qp = k0 > 1 && k0 < k1 ? sload(sQ + rw.pos(k0 - 1)) : czero<R>();  // Q_{k0 - 1}
         for (int k = k0; k < k1; ++k) {
             const cx<R> Qk = sload(sQ + rw.own(k));
             if (k == 1) {
-                nd = sload(sR + rw.own(1));
+                ND = sload(sR + rw.own(1));
             } else {
-                s = cfma(s, Qk, qp);
-                nd = cfma(nd, Qk, sload(sR + rw.own(k)));
+                S = cfma(S, Qk, qp);
+                ND = cfma(ND, Qk, sload(sR + rw.own(k)));
             }
             qp = Qk;
         }
     }
-    const cx<R> S = warp_sum(s), ND = warp_sum(nd);
+    block_sum2(S, ND, reinterpret_cast<cx<R>*>(tot_raw));
     // the kept values of the substitution
     for (int k = k0; k < k1; ++k) {
-        sstore(scan_keep(keep0, t, m, k, 0), sload(sD + rw.own(k)));
-        sstore(scan_keep(keep0, t, m, k, 1), sload(sW + rw.own(k)));
+        dbg_st(keep + rw.own(k), sD[rw.own(k)]);
+        dbg_st(keep + ld + rw.own(k), sW[rw.own(k)]);
     }
     if (!ok) flag_error(status, kStatusNonfinite);
-    if (lane != 0) return;
+    if (tid != 0) return;
     // JD on row J_{t+1}, JU on row J_t (as cn_reduce_block)
     const cx<R> one = cfrom<R>(1.0, 0.0);
     const cx<R> w1 = sload(sW + rw.pos(1)), wl = sload(sW + rw.pos(gap - 1));
@@ -381,32 +448,36 @@ k_cn_reduce_scan(CNStep st, OneSys sys, OneSys next, OneGrid grid, int m, int m_
     }
 }
 
-// Level-0 substitution of block t = blockIdx.x by one warp from the kept (d^, w):
+// Level-0 substitution of block t = blockIdx.x by one CTA from the kept (d^, w):
 //   z_k = (d^_k + z_{k-1}) w_k from z_0 = x_L (row g-1 also adds x_R), then
 //   x_k = z_k + w_k x_{k+1} from x_{g-1} = z_{g-1}
 // (the forward and backward sweeps of k_cn_substitute_kept, as scans).
 template <class R>
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(kScanMaxThreads)
 k_cn_substitute_scan(OneSys sys, OneSys next, int m, const typename Store<R>::T* keep0,
                      const typename Store<R>::T* x_next0, double2* x_out) {
     grid_dep_enter();
     typedef typename Store<R>::T ST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) unsigned char tot_raw[32 * sizeof(Aff<R>)];
+    Aff<R>* const tot = reinterpret_cast<Aff<R>*>(tot_raw);
+    const int ld = (int)scan_ld(m);
     ST* const sD = reinterpret_cast<ST*>(smem_raw);
-    ST* const sW = sD + (m + kScanPad);
-    ST* const sZ = sW + (m + kScanPad);
-    const int lane = threadIdx.x;
+    ST* const sW = sD + ld;
+    ST* const sZ = sW + ld;
+    const int tid = threadIdx.x;
     const int64_t t = blockIdx.x;
     const LvlSys& e = sys.at(0);
     const int64_t n = e.n, P = e.P;
     const int64_t J0 = joint_line(t, P, m, n);
-    const ScanRows rw((int)(joint_line(t + 1, P, m, n) - J0), lane);
+    const ScanRows rw((int)(joint_line(t + 1, P, m, n) - J0));
     const int gap = rw.gap, k0 = rw.k0, k1 = rw.k1;
+    const ST* const keep = keep0 + 2 * t * ld;
     const ST* x_next = x_next0 + next.at(0).row_off;
     const cx<R> xL = sload(x_next + t), xR = sload(x_next + t + 1);
     for (int k = k0; k < k1; ++k) {
-        sstore(sD + rw.own(k), sload(scan_keep(keep0, t, m, k, 0)));
-        sstore(sW + rw.own(k), sload(scan_keep(keep0, t, m, k, 1)));
+        sD[rw.own(k)] = dbg_ld(keep + rw.own(k));
+        sW[rw.own(k)] = dbg_ld(keep + ld + rw.own(k));
     }
     // forward sweep
     {
@@ -419,7 +490,7 @@ k_cn_substitute_scan(OneSys sys, OneSys next, int m, const typename Store<R>::T*
             f.a = cmul(dd, w);
             F = aff_after(f, F);
         }
-        const Aff<R> Z = scan_up_exclusive(F, lane);
+        const Aff<R> Z = block_up_exclusive(F, tot);
         cx<R> z = cfma(Z.a, Z.m, xL);  // z_{k0 - 1}
         for (int k = k0; k < k1; ++k) {
             const cx<R> w = sload(sW + rw.own(k)), d = sload(sD + rw.own(k));
@@ -427,10 +498,10 @@ k_cn_substitute_scan(OneSys sys, OneSys next, int m, const typename Store<R>::T*
             sstore(sZ + rw.own(k), z);
         }
     }
-    __syncwarp();
+    __syncthreads();
     // backward sweep over rows g-2 .. 1
     const cx<R> ztop = sload(sZ + rw.pos(gap - 1));
-    const int b1 = min(k1, gap - 1);  // the lane's rows below g - 1: k0 .. b1 - 1
+    const int b1 = min(k1, gap - 1);  // the thread's rows below g - 1: k0 .. b1 - 1
     Aff<R> B = aff_identity<R>();
     for (int k = b1 - 1; k >= k0; --k) {
         Aff<R> f;  // y -> w_k y + z_k
@@ -438,7 +509,7 @@ k_cn_substitute_scan(OneSys sys, OneSys next, int m, const typename Store<R>::T*
         f.a = sload(sZ + rw.own(k));
         B = aff_after(f, B);
     }
-    const Aff<R> Yb = scan_down_exclusive(B, lane);
+    const Aff<R> Yb = block_down_exclusive(B, tot);
     double2* x = x_out + e.row_off;
     cx<R> y = cfma(Yb.a, Yb.m, ztop);  // x_{b1}
     for (int k = b1 - 1; k >= k0; --k) {
@@ -446,8 +517,8 @@ k_cn_substitute_scan(OneSys sys, OneSys next, int m, const typename Store<R>::T*
         store128(x + J0 + k, y);
     }
     if (k0 <= gap - 1 && gap - 1 < k1) store128(x + J0 + gap - 1, ztop);
-    if (lane == 0) store128(x + J0, xL);
-    if (lane == 0 && t == P - 1) store128(x + J0 + gap, xR);
+    if (tid == 0) store128(x + J0, xL);
+    if (tid == 0 && t == P - 1) store128(x + J0 + gap, xR);
 }
 
 }  // namespace cnb

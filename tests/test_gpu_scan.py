@@ -1,10 +1,11 @@
-"""Level 0 of few long blocks reduced and substituted by one warp per block, the
-recurrences of Table 1's RD/RU and of the SS as warp prefix scans
-(csrc/cn_scan.cuh), against the FP64 oracle element by element:
+"""Level 0 of few long blocks reduced and substituted by one CTA per block (about
+two rows a thread), the recurrences of Table 1's RD/RU and of the SS as prefix
+scans over the CTA (csrc/cn_scan.cuh), against the FP64 oracle element by element:
   - the paper's own small case: the free packet, n = 4096 in P = 16 blocks of
     256 rows (Sec. 4.1.1), 100 steps;
   - ragged partitions (blocks of 2 rows at the tail), the longest blocks (1024
-    rows), more nesting levels below level 0, a full-support state and a field;
+    rows, 8 a thread), one warp (64-row blocks), threads left without rows, more
+    nesting levels below level 0, a full-support state and a field;
   - one-step calls bitwise equal to one multi-step call, and the adjoint step.
 """
 import numpy as np
@@ -25,6 +26,13 @@ DEV = torch.device("cuda:0")
 ARITHS = [cnb.ARITH_F64, cnb.ARITH_DF64]
 
 
+def scan_threads(m):
+    """Threads of the CTA that takes one level-0 block of m rows: about two rows each,
+    whole warps, 32 .. 128."""
+    t = -(-(-(-(m - 1) // 2)) // 32) * 32
+    return min(max(t, 32), 128)
+
+
 def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
@@ -42,7 +50,7 @@ def test_paper_small_case_p16_vs_oracle(arith):
     psi0 = W.initial_state(cfg)
     plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], arith=arith, levels=[256])
     info = plan.info()
-    assert info["level0_lanes"] == 32 and info["level_rows"] == [4096, 17]
+    assert info["level0_lanes"] == scan_threads(256) == 128 and info["level_rows"] == [4096, 17]
     out = plan.step(to_dev(psi0), nst).cpu().numpy()
     plan.check()
     ref = oracle.cn_run(oracle.Problem(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=oracle.POT_NONE), psi0, nst)
@@ -65,7 +73,7 @@ def test_scan_level0_soft_coulomb_vs_oracle(arith, n, levels):
     E = W.field_midpoints(nsteps, cfg["dt"], t0=150.0)
     plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith,
                     levels=levels)
-    assert plan.info()["level0_lanes"] == 32
+    assert plan.info()["level0_lanes"] == scan_threads(levels[0])
     out = plan.step(to_dev(psi0), nsteps, E_mid=to_dev(E)).cpu().numpy()
     plan.check()
     prob = oracle.Problem(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=oracle.POT_SOFTCOULOMB, soft_s=2.0)
@@ -99,7 +107,7 @@ def test_scan_adjoint_steps_vs_oracle(arith, tol):
     L_ref, g_ref, lam0_ref = oracle.adjoint_run(prob, psi0, nsteps, wgt, E_mid=E, want_lam0=True)
     plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith,
                     levels=[150])
-    assert plan.info()["level0_lanes"] == 32
+    assert plan.info()["level0_lanes"] == scan_threads(150) == 96
     Ed = to_dev(E)
     states = [to_dev(psi0)]
     for k in range(nsteps):
