@@ -281,8 +281,8 @@ struct ScanRows {
 // instruction every ~64 clocks whatever its other warps do, and an SM takes about
 // four at a time (one per scheduler): the scans' cost is their depth in binary64
 // instructions, so four warps, each with its own scheduler, and runs of two rows
-// (m = 256 on B300: 60 us a step at 2 rows and 4 warps, 74 at 1 row and 8 warps,
-// 70 at 4 rows and 2 warps; m = 512: 74 at 4 warps, 82 at 8, 113 at 16)
+// (m = 256 on B300: 59 us a step at 2 rows and 4 warps, 74 at 1 row and 8 warps,
+// 70 at 4 rows and 2 warps; m = 512: 72 at 4 warps, 82 at 8, 113 at 16)
 constexpr int kScanRowsPerThread = 2;
 constexpr int kScanMaxThreads = 128;
 __host__ __device__ constexpr int scan_threads(int m) {
