@@ -753,6 +753,15 @@ cudaError_t solve_levels(Engine* p, cudaStream_t st) {
 // General tridiagonal solve (arrays at level 0, one system).
 template <class R>
 cudaError_t solve_arrays(Engine* p, const ArraySource& src, double2* x, cudaStream_t st) {
+    // level 0 of arrays runs the one-thread kernels, which leave one JD slot per CTA
+    // of kThreads blocks, also in a plan whose CN steps reduce level 0 by scans (one
+    // slot per block): level 1 is read accordingly for this call
+    struct SlotShift {
+        int& v;
+        const int old;
+        SlotShift(int& r, int s) : v(r), old(r) { v = s; }
+        ~SlotShift() { v = old; }
+    } level1_slots(p->lv[1].slot_shift, 7);
     cudaError_t e = cudaSuccess;
     {
         ProfScope ps(p, kProfReduce0, st);

@@ -47,7 +47,7 @@ SCRIPT = textwrap.dedent("""
                                                     flags=cnb.FLAG_COEFF_TABLE)),
                       (1 << 20, dict(flags=cnb.FLAG_PERSISTENT_LEVELS)), (1 << 20, dict(flags=cnb.FLAG_LEVEL_LAUNCHES)),
                       (200001, dict(levels=[40, 20])), (70001, dict(flags=cnb.FLAG_RECOMPUTE)),
-                      (20011, dict(levels=[300, 8]))):
+                      (20011, dict(levels=[300, 8])), (5001, dict(levels=[1024]))):
             cfg = W.soft_coulomb_config(n=n, nsteps=5)
             prob = oracle.Problem(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=oracle.POT_SOFTCOULOMB, soft_s=2.0)
             psi0 = W.full_support_state(n, cfg["dx"], cfg["x_min"], seed=n)

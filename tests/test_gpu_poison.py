@@ -56,6 +56,9 @@ def plan_cases():
         out.append(("per_level", arith, 1 << 21, dict(flags=cnb.FLAG_LEVEL_LAUNCHES)))
         out.append(("long_blocks", arith, 200001, dict(levels=[40, 20])))
         out.append(("recompute", arith, 70001, dict(flags=cnb.FLAG_RECOMPUTE)))
+        # level 0 by one CTA per block (prefix scans): two and four warps, a ragged tail
+        out.append(("scan_blocks", arith, 70001, dict(levels=[200, 16])))
+        out.append(("scan_long_blocks", arith, 5001, dict(levels=[1024])))
     return out
 
 

@@ -131,3 +131,28 @@ def test_scan_not_taken_for_many_blocks_short_blocks_or_serial_flag():
         plan = cnb.Plan(cfg["n"], cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, **kw)
         assert plan.info()["level0_lanes"] == 1
         plan.close()
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("n,levels", [(4096, [256]), (20011, [300, 8]), (5001, [1024])])
+def test_general_solve_on_a_scan_plan_vs_thomas(arith, n, levels):
+    """cn_solve_tridiag on a plan whose CN steps reduce level 0 by scans: the general
+    solve runs the one-thread level-0 kernels (one JD slot per CTA), before and after
+    CN steps that leave one slot per block in the same level-1 buffers."""
+    cfg = W.soft_coulomb_config(n=n, nsteps=2)
+    plan = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith,
+                    levels=levels)
+    assert plan.info()["level0_lanes"] == scan_threads(levels[0])
+    b, a, c, d = W.random_system(n, np.random.default_rng(n + 5))
+    ref = oracle.thomas(b, a, c, d)
+    t = [to_dev(v) for v in (b, a, c, d)]
+    x0 = plan.solve_tridiag(*t).cpu().numpy()
+    psi0 = W.full_support_state(n, cfg["dx"], cfg["x_min"], seed=n)
+    E = W.field_midpoints(2, cfg["dt"], t0=40.0)
+    out = plan.step(to_dev(psi0), 2, E_mid=to_dev(E)).cpu().numpy()
+    x1 = plan.solve_tridiag(*t).cpu().numpy()
+    plan.check()
+    check(x0, ref, 1e-12)
+    assert np.array_equal(x0, x1)
+    prob = oracle.Problem(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=oracle.POT_SOFTCOULOMB, soft_s=2.0)
+    check(out, oracle.cn_run(prob, psi0, 2, E_mid=E))
