@@ -1507,9 +1507,9 @@ __device__ __forceinline__ cx<double> explicit_row(cx<double> pm, cx<double> p0,
                                                    double sg) {
     static_assert(ES == -1 || ES == 0 || ES == 1, "e s is -1, 0 or 1");
     if constexpr (ES == 0) {
-        return mk(sg * p0.im, -sg * p0.re);
+        return mk(d_mul(sg, p0.im), d_mul(-sg, p0.re));
     } else {
-        double sr = pm.re + pp.re, si = pm.im + pp.im;
+        double sr = d_add(pm.re, pp.re), si = d_add(pm.im, pp.im);
         const double eb = ES > 0 ? bt : -bt;
         if (ES > 0) { sr = -sr; si = -si; }
         return mk(fma(eb, p0.re, fma(sg, p0.im, sr)), fma(eb, p0.im, fma(-sg, p0.re, si)));
