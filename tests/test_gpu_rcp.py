@@ -51,3 +51,48 @@ def test_device_rcp_matches_host_build_and_cuda_division(tmp_path):
     assert d.max() <= 1.0
     assert np.mean(y[v] == ref[v]) > 0.999
     assert np.isnan(y[~v]).all()
+
+
+@pytest.mark.gpu
+def test_fma_forms_of_add_sub_mul_are_bitwise_the_plain_operations(tmp_path):
+    """d_add / d_sub / d_mul (the binary64 kernels' additions, subtractions and
+    multiplications, issued as FMAs with 1 or -0 from constant memory) against the
+    device's own correctly rounded __dadd_rn / __dsub_rn / __dmul_rn: bitwise equal,
+    signed zeros, subnormals, overflow and infinities included (NaN results: NaN)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = _build(tmp_path, os.path.join(ROOT, "tests", "rcp_probe.cu"),
+                 ["/usr/local/cuda/bin/nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                  "-shared", "-Xcompiler", "-fPIC", "-cudart", "shared"])
+    P = C.c_void_p
+    dev.fma_form_probe.argtypes = [P, P, P, C.c_long]
+    rng = np.random.default_rng(107)
+    n = 1 << 18
+
+    def wide(k):
+        s = np.where(rng.random(k) < 0.5, -1.0, 1.0)
+        return s * np.ldexp(1.0 + rng.random(k), rng.integers(-1074, 1024, k))
+    a, b = wide(n), wide(n)
+    c = np.ldexp(1.0 + rng.random(n), rng.integers(-40, 40, n)) * np.where(rng.random(n) < 0.5, -1, 1)
+    d = -c * (1.0 + np.ldexp(rng.integers(-3, 4, n).astype(float), -52))  # cancellation, exact zeros
+    special = np.array([0.0, -0.0, 5e-324, -5e-324, 2.0 ** -1022, np.inf, -np.inf, np.nan, 1.0, -1.0,
+                        2.0 ** 1023, 1.5 * 2.0 ** 1023, 2.0 ** -537, 3.0])
+    sa, sb = np.meshgrid(special, special)
+    A = np.ascontiguousarray(np.concatenate([a, c, sa.ravel(), c]))
+    B = np.ascontiguousarray(np.concatenate([b, d, sb.ravel(), np.ldexp(d, -560)]))
+    m = len(A)
+    out = np.empty(6 * m)
+    pt = lambda v: v.ctypes.data_as(P)  # noqa: E731
+    assert dev.fma_form_probe(pt(A), pt(B), pt(out), m) == 0
+    out = out.reshape(m, 6)
+    for k in (0, 2, 4):
+        got, ref = out[:, k], out[:, k + 1]
+        nan = np.isnan(ref)
+        assert np.array_equal(np.isnan(got), nan)
+        assert np.array_equal(got[~nan].view(np.int64), ref[~nan].view(np.int64))
+    # the plain operations are IEEE: pin them to numpy's on the same inputs
+    with np.errstate(all="ignore"):
+        for k, ref in ((1, A + B), (3, A - B), (5, A * B)):
+            nan = np.isnan(ref)
+            assert np.array_equal(out[~nan, k].view(np.int64), ref[~nan].view(np.int64))
