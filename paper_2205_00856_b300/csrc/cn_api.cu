@@ -668,8 +668,13 @@ cudaError_t rs_stage(Engine* p, cudaStream_t st) {
     const LevelSource<R> src = level_source<R>(B).bind(B.sys[0]);
     if (p->lvl_m.empty())
         return launch(p->pdl, k_base_cr<R>, 1, kCrThreads, cr_smem(), st, src, x_of<R>(B), p->status);
-    // level 0 by scans, binary64: the RS stage on one warp too (17 rows of the paper's small
-    // case: 30 -> 21 us on B300; in double-float the one-thread walk is the faster, 16 us)
+    // a reduced system of at most 32 rows: parallel cyclic reduction on one warp (unless
+    // the blocks are to be walked serially, the partition study's model)
+    if (src.n <= kPcrMax && !(p->desc.flags & CN_FLAG_SERIAL_BLOCKS))
+        return launch(p->pdl, k_base_pcr<R>, 1, 32, 0, st, src, x_of<R>(B), p->status);
+    // level 0 by scans, binary64, 33 .. 512 rows (65 for 64-row blocks of n = 4096): the RS
+    // stage by scans on one warp too (the paper's P = 16, 17 rows, before the above: 30 ->
+    // 21 us on B300; in double-float the one-thread walk is the faster, 16 us)
     if (std::is_same<R, double>::value && p->scan0 && src.n <= kScanRsMax)
         return launch(p->pdl, k_base_scan<R>, 1, 32, scan_rs_entries((int)src.n) * kCplx, st, src, x_of<R>(B),
                       p->status);

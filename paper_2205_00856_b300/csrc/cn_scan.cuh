@@ -23,8 +23,9 @@
 // order).  Projective matrix products are rescaled by powers of two (exact) so
 // that they neither overflow nor vanish.  The level-1 rows take this block's JU
 // part; its JD part goes to slot t + 1, one slot per block (the level's
-// slot_shift 0), and the reader adds it.  The RS stage of such plans, when short,
-// runs Thomas' recurrences as scans over one warp (k_base_scan, binary64).
+// slot_shift 0), and the reader adds it.  The RS stage of an explicit-depth plan
+// runs on one warp when short: parallel cyclic reduction up to 32 rows
+// (k_base_pcr), Thomas' recurrences as scans up to 512 (k_base_scan, binary64).
 #pragma once
 #include "cn_kernels.cuh"
 
@@ -519,6 +520,60 @@ k_cn_substitute_scan(OneSys sys, OneSys next, int m, const typename Store<R>::T*
 }  // namespace cnb
 
 namespace cnb {
+
+// The RS stage of an explicit-depth plan whose last reduced system has at most
+// kPcrMax rows: parallel cyclic reduction (Hockney, J. ACM 12(1), 1965) on one
+// warp, one row per lane.  In the step with stride s every row eliminates its
+// couplings to rows i - s and i + s with those rows' equations,
+//   k1 = b_i / a_{i-s},  k2 = c_i / a_{i+s},
+//   a_i -= k1 c_{i-s} + k2 b_{i+s},  d_i -= k1 d_{i-s} + k2 d_{i+s},
+//   b_i = -k1 b_{i-s},  c_i = -k2 c_{i+s},
+// after which it couples to i -+ 2s (a row beyond the system contributes
+// nothing); once 2s >= n every row stands alone and x_i = d_i / a_i.  Five steps
+// for 17 rows, each ~39 binary64 operations in every lane at once, where Thomas'
+// recurrences walk the rows one after another.  Lanes beyond the system hold the
+// identity row.
+constexpr int kPcrMax = 32;
+template <class R> struct PcrRow {
+    cx<R> q, b, c, d;  // q = 1 / a
+};
+template <class R>
+__global__ void __launch_bounds__(32)
+k_base_pcr(LevelSource<R> src, typename Store<R>::T* x, int* status) {
+    grid_dep_enter();
+    const int n = (int)src.n, i = threadIdx.x;
+    bool ok = true;
+    cx<R> a = cfrom<R>(1.0, 0.0), b = czero<R>(), c = czero<R>(), d = czero<R>();
+    if (i < n) {
+        const Row<R> r = src.template row_at<R>(i);
+        a = r.a;
+        b = i > 0 ? r.b : czero<R>();
+        c = i < n - 1 ? r.c : czero<R>();
+        d = r.d;
+    }
+    for (int s = 1; s < n; s <<= 1) {
+        PcrRow<R> me;
+        me.q = crcp(a, ok);
+        me.b = b;
+        me.c = c;
+        me.d = d;
+        const PcrRow<R> lo = shfl_word_up(me, s), hi = shfl_word_down(me, s);
+        const bool has_lo = i >= s, has_hi = i + s < n;
+        const cx<R> k1 = has_lo ? cmul(b, lo.q) : czero<R>();
+        const cx<R> k2 = has_hi ? cmul(c, hi.q) : czero<R>();
+        const cx<R> lb = has_lo ? lo.b : czero<R>(), lc = has_lo ? lo.c : czero<R>();
+        const cx<R> ld = has_lo ? lo.d : czero<R>();
+        const cx<R> hb = has_hi ? hi.b : czero<R>(), hc = has_hi ? hi.c : czero<R>();
+        const cx<R> hd = has_hi ? hi.d : czero<R>();
+        a = csub2mul(a, k1, lc, k2, hb);
+        d = csub2mul(d, k1, ld, k2, hd);
+        b = cneg(cmul(k1, lb));
+        c = cneg(cmul(k2, hc));
+    }
+    const cx<R> xi = cmul(d, crcp(a, ok));
+    if (i < n) sstore(x + i, xi);
+    if (!ok) flag_error(status, kStatusNonfinite);
+}
 
 // The RS stage of a plan whose level 0 runs on warps (explicit depth, last reduced
 // system of at most kScanRsMax rows): Thomas' recurrences as warp scans, one warp
