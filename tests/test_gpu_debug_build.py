@@ -5,8 +5,8 @@ cn_debug_report) -- the stand-in for a memory sanitizer.  Runs in a fresh
 process (the package loads one library per process): the planted-access self
 test, then every entry point over configurations that reach every kernel --
 ragged sizes, the large-grid blocks with the coefficient table, long blocks
-with device scratch and the serial RS stage, few long blocks on one warp each
-(prefix scans), recompute mode, the adjoint, the
+with device scratch and the serial RS stage, few long blocks on one CTA each
+(prefix scans) with the RS stage on one warp, recompute mode, the adjoint, the
 host-buffer step, a batch, slabs with tiny and uneven joint lines, the
 no-allocation solve and the control-field maps -- with no violation reported,
 and the results against the oracle."""
