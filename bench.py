@@ -51,22 +51,23 @@ PG_TIMEOUT_S = 900     # process-group timeout: longer than any phase between tw
 # from a table built once (table=True; binary64: the pair {bt0, x}).
 #
 # Binary64 (FP64 pipe operations: DFMA, DADD and DMUL count one each, as the pipe
-# issues them; flops count an FMA as 2).  Reduction loop row: coefficient 1 (FMA
-# with the tabulated x), explicit row 6 (2 DADD, 4 DFMA), RD: d 4, pivot 2 +
-# complex reciprocal 7 (|z|^2 2, the division-free real reciprocal 3, 2 DMUL), RU:
-# Q 4, S 4, d 4  ->  32 operations (23 DFMA, 4 DADD, 5 DMUL: 55 flops).  Per block
-# rows 0 and 1, JD/JU and the joint-row exchange add 48 operations (80 flops) and
-# spare the two loop rows they replace: 32 - 16/m per grid row (55 - 30/m flops).
-# Regenerating V(x) adds the coordinate (DADD, DFMA), x^2 + s, the binary64
-# reciprocal square root and a scale: about 10 operations per row.  Substitution
-# (kept values): a forward step (2 DADD, 2 DMUL, 2 DFMA) and a back step (4 DFMA)
-# per interior row: 10 - 10/m (flops 16 - 16/m).
+# issues them -- on the device every addition and multiplication is issued as an
+# FMA; flops count an FMA as 2).  Reduction loop row: coefficient 1 (FMA with the
+# tabulated x), explicit row 6 (2 additions, 4 FMAs), RD: d 4, pivot 2 + complex
+# reciprocal 5 (|z|^2 2, the real reciprocal 1 FMA and integer rounding, 2
+# multiplications), RU: Q 4, S 4, d 4  ->  30 operations (51 flops).  Per block
+# rows 0 and 1, JD/JU and the joint-row exchange add 46 operations (76 flops) and
+# spare the two loop rows they replace: 30 - 14/m per grid row (51 - 26/m flops).
+# Regenerating V(x) adds the coordinate (an addition and an FMA), x^2 + s, the
+# binary64 reciprocal square root and a scale: about 10 operations per row.
+# Substitution (kept values): a forward step (2 additions, 2 multiplications, 2
+# FMAs) and a back step (4 FMAs) per interior row: 10 - 10/m (flops 16 - 16/m).
 # Double-float: binary32 operations of the FP32 pipe, see ops_per_row.
 def f64_ops_per_row(kernel: str, m: int, table: bool = True) -> float:
     if kernel == "fused_level0":
         return f64_ops_per_row("substitute_level0", m, table) + f64_ops_per_row("reduce_level0", m, table)
     if kernel == "reduce_level0":
-        return (32.0 if table else 42.0) - 16.0 / m
+        return (30.0 if table else 40.0) - 14.0 / m
     return 10.0 - 10.0 / m
 
 
@@ -79,7 +80,7 @@ def flops_per_row(kernel: str, arith: str, m: int, table: bool = False) -> float
     if kernel == "fused_level0":  # SS of one step + the level-0 reduction of the next
         return flops_per_row("substitute_level0", arith, m, table) + flops_per_row("reduce_level0", arith, m, table)
     if arith == "f64":
-        return (55.0 if table else 72.0) - 30.0 / m if kernel == "reduce_level0" else 16.0 - 16.0 / m
+        return (51.0 if table else 68.0) - 26.0 / m if kernel == "reduce_level0" else 16.0 - 16.0 / m
     if kernel == "reduce_level0":
         return (477.0 if table else 548.0) - 261.0 / m
     return 150.0 - 128.0 / m

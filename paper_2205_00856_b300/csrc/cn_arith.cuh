@@ -106,21 +106,43 @@ CNB_HD double d_from_bits(int64_t i) {
     double a; memcpy(&a, &i, 8); return a;
 #endif
 }
-// 1/q for binary64 q, without a division and without an FP64 comparison.
+// high 64 bits of a 64 x 64-bit product; leading zeros of a nonzero word
+CNB_HD uint64_t u64_mulhi(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+CNB_HD int u64_clz(uint64_t a) {
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)a);
+#else
+    return __builtin_clzll(a);
+#endif
+}
+
+// 1/q for binary64 q, without a division and with one binary64 operation.
 // Seed: the top 23 bits of q's significand as a binary32 value f in [1, 2),
 // its correctly rounded binary32 reciprocal r, and q's exponent applied with
 // integer operations, so y0 = r 2^-e with |1 - q y0| <= 2^-23 + 2^-24 (the
-// truncation of f and the rounding of 1/f).  Refinement: with e = 1 - q y0,
-// 1/q = y0 / (1 - e) = y0 (1 + e + e^2 + e^3 + ...), and y = y0 + y0 (e + e^2)
-// is the series truncated after its quadratic term (the series form of the
-// Newton-Raphson reciprocal iteration: Goldschmidt, MIT thesis 1964; Markstein,
-// IBM J. Res. Dev. 34(1), 1990): three binary64 FMAs.  Error: the omitted
-// e^3 + ... < 2^-66 relative, the roundings of e and e + e^2 below 2^-74
-// relative, and the final rounding of y, 1/2 ulp: |y - 1/q| <= (1/2 + 2^-12) ulp.
-// Range: positive normal q with biased exponent 1..2044 (so that 1/q is
-// normal); anything else (zero, subnormal, negative, huge, inf, NaN) clears
-// `ok` and returns NaN.  The checks run on integer bits.  Bit-reproducible on
-// host and device (correctly rounded binary32 reciprocal, binary64 FMA).
+// truncation of f and the rounding of 1/f).  Refinement: with e = 1 - q y0 (one
+// binary64 FMA), 1/q = y0 / (1 - e) = y0 (1 + e + e^2 + e^3 + ...), the series
+// form of the Newton-Raphson reciprocal iteration (Goldschmidt, MIT thesis 1964;
+// Markstein, IBM J. Res. Dev. 34(1), 1990), evaluated here to its cubic term in
+// integer fixed point -- T = (e + e^2 + e^3) 2^75 from e's bits (|e| < 2^-22, so
+// |e| 2^75 < 2^53), Z = R (2^75 + T) exactly in 128 bits, R = r's 24-bit
+// significand -- and rounded once to 53 bits, to nearest even.  On B300 the
+// FP64 pipe is the binary64 kernels' limit while the integer pipe idles, so the
+// ~60 integer instructions replace two FMAs of the FP64 pipe.  Error: the omitted
+// e^4 + ... < 2^-88 relative, the truncations of the three terms and the
+// rounding of e below 4 units of 2^-75 relative, and the final rounding, 1/2 ulp:
+// |y - 1/q| <= (1/2 + 2^-20) ulp.  Range: positive normal q with biased
+// exponent 1..2044 (so that 1/q is normal); anything else (zero, subnormal,
+// negative, huge, inf, NaN) clears `ok` and returns NaN.  The checks run on
+// integer bits, and every shift count stays in 0..63 for any input.
+// Bit-reproducible on host and device (correctly rounded binary32 reciprocal,
+// binary64 FMA, integer arithmetic).
 CNB_HD double d_rcp(double q, bool& ok) {
     const int64_t b = d_bits(q);
     const uint32_t hi = (uint32_t)((uint64_t)b >> 32);
@@ -130,7 +152,32 @@ CNB_HD double d_rcp(double q, bool& ok) {
     const int64_t ye = (int64_t)(rb >> 23) + 1919 - (int64_t)E;  // biased exponent of r 2^-e
     const double y0 = d_from_bits((int64_t)((uint64_t)ye << 52) | ((int64_t)(rb & 0x7FFFFF) << 29));
     const double e = fma(-q, y0, 1.0);
-    const double y = fma(y0, fma(e, e, e), y0);
+    // |e| 2^75 = M 2^(x - 1000), x e's biased exponent (<= 1000), truncated to an integer
+    const uint64_t eb = (uint64_t)d_bits(e);
+    const int x = (int)((eb >> 52) & 0x7FF);
+    const int s1 = 1000 - x;
+    const uint64_t M = (eb & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const uint64_t E1 = (x != 0 && s1 >= 0 && s1 < 64) ? (M >> s1) : 0;  // |e| 2^75
+    const uint64_t E2 = u64_mulhi(E1, E1) >> 11;                            // e^2 2^75
+    const uint64_t E3 = u64_mulhi(E1, E2) >> 11;                            // |e|^3 2^75
+    const int64_t T = (eb >> 63) ? (int64_t)E2 - (int64_t)(E1 + E3) : (int64_t)(E1 + E2 + E3);
+    // Z = R (2^75 + T) = y in units of 2^(er - 98 - eq), er = r's and eq = q's exponent
+    const uint64_t R = (uint64_t)((rb & 0x7FFFFF) | 0x800000);
+    const uint64_t Ta = T < 0 ? (uint64_t)0 - (uint64_t)T : (uint64_t)T;
+    const uint64_t Pl = R * Ta, Ph = u64_mulhi(R, Ta);
+    const uint64_t Zl = T < 0 ? (uint64_t)0 - Pl : Pl;
+    const uint64_t Zh = T < 0 ? (R << 11) - Ph - (uint64_t)(Pl != 0) : (R << 11) + Ph;
+    // Z's leading bit is bit 52 + sh of the 128 (sh = 45..47 for valid q): 53 bits from
+    // there, round to nearest even on the next bit and the sticky bits below it
+    const int sh0 = 75 - u64_clz(Zh | 1);
+    const int sh = sh0 < 2 ? 2 : (sh0 > 63 ? 63 : sh0);
+    uint64_t mant = (Zh << (64 - sh)) | (Zl >> sh);
+    const uint64_t rnd = (Zl >> (sh - 1)) & 1u;
+    const uint64_t sticky = (Zl << (65 - sh)) != 0;
+    mant += rnd & (sticky | (mant & 1u));
+    // biased exponent sh + er - E + 2000; the implicit bit in mant carries into it
+    const int64_t Ey = (int64_t)sh + (int64_t)(rb >> 23) - 127 - (int64_t)E + 2000;
+    const double y = d_from_bits((int64_t)(((uint64_t)(Ey - 1) << 52) + mant));
     const bool in = (E - 1u) < 2044u;
     ok = ok && in;
     return in ? y : d_from_bits(0x7FF8000000000000ll);

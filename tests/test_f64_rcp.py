@@ -2,12 +2,13 @@
 complex reciprocal crcp<double> in csrc/cn_arith.cuh, built for the host) against
 exact rational arithmetic.
 
-d_rcp forms 1/q from a binary32 seed and the series y0 (1 + e + e^2), e = 1 - q y0
-(Goldschmidt; Markstein).  Its stated bound is |y - 1/q| <= (1/2 + 2^-12) ulp(1/q)
-on positive normal q whose reciprocal is normal (biased exponent 1..2044); every
-other input clears the ok flag and gives NaN.  The host build is bit-identical to
-the device code (correctly rounded binary32 reciprocal, binary64 FMA), which the
-GPU test in test_gpu_rcp.py checks.
+d_rcp forms 1/q from a binary32 seed y0 and the series y0 (1 + e + e^2 + e^3),
+e = 1 - q y0 (Goldschmidt; Markstein), the series in integer fixed point and
+rounded once.  Its stated bound is |y - 1/q| <= (1/2 + 2^-20) ulp(1/q) on positive
+normal q whose reciprocal is normal (biased exponent 1..2044); every other input
+clears the ok flag and gives NaN.  The host build is bit-identical to the device
+code (correctly rounded binary32 reciprocal, binary64 FMA, integer arithmetic),
+which the GPU test in test_gpu_rcp.py checks.
 """
 import ctypes as C
 import math
@@ -77,12 +78,12 @@ def test_rcp_error_bound_against_exact_rationals(shim):
     y, ok = d_rcp(shim, q)
     assert ok.all()
     worst = max(err_ulps(float(a), float(b)) for a, b in zip(q, y))
-    assert worst <= 0.5 + 2.0 ** -12, worst
+    assert worst <= 0.5 + 2.0 ** -20, worst
 
 
 def test_rcp_agrees_with_correctly_rounded_division(shim):
-    """Within the bound, y is the correctly rounded 1/q except in rare near-halfway
-    cases, where it is the other neighbour (one ulp)."""
+    """Within the bound, y is the correctly rounded 1/q except in near-halfway cases
+    closer than 2^-20 ulp, where it may be the other neighbour (one ulp)."""
     rng = np.random.default_rng(7)
     q = sample_valid(rng, 200000)
     y, ok = d_rcp(shim, q)
@@ -90,7 +91,7 @@ def test_rcp_agrees_with_correctly_rounded_division(shim):
     ref = 1.0 / q  # IEEE division: correctly rounded
     d = np.abs(y - ref) / np.spacing(ref)
     assert d.max() <= 1.0
-    assert np.mean(y == ref) > 0.999
+    assert np.mean(y == ref) > 0.99999
 
 
 def test_rcp_edges_of_the_range(shim):
@@ -100,7 +101,7 @@ def test_rcp_edges_of_the_range(shim):
     y, ok = d_rcp(shim, q)
     assert ok.all()
     for a, b in zip(q, y):
-        assert err_ulps(float(a), float(b)) <= 0.5 + 2.0 ** -12, a
+        assert err_ulps(float(a), float(b)) <= 0.5 + 2.0 ** -20, a
     assert y[0] == 1.0 and y[1] == 0.5 and y[2] == 2.0 and y[11] == 0.125
 
 

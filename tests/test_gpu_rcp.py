@@ -49,7 +49,7 @@ def test_device_rcp_matches_host_build_and_cuda_division(tmp_path):
     assert v.sum() == m - 6
     d = np.abs(y[v] - ref[v]) / np.spacing(ref[v])
     assert d.max() <= 1.0
-    assert np.mean(y[v] == ref[v]) > 0.999
+    assert np.mean(y[v] == ref[v]) > 0.99999
     assert np.isnan(y[~v]).all()
 
 
