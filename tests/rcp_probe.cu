@@ -72,3 +72,35 @@ extern "C" int fma_form_probe(const double* a, const double* b, double* out, lon
     cudaFree(dout);
     return (int)e;
 }
+
+// The complex reciprocal crcp<double> (integer arithmetic) on the device: z and w
+// interleaved (re, im), ok per element.
+__global__ void k_crcp_probe(const double* z, double* w, int* ok, long n) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool k = true;
+    const cnb::cx<double> r = cnb::crcp(cnb::mk(z[2 * i], z[2 * i + 1]), k);
+    w[2 * i] = r.re;
+    w[2 * i + 1] = r.im;
+    ok[i] = k;
+}
+
+extern "C" int crcp_probe(const double* z, double* w, int* ok, long n) {
+    double *dz = nullptr, *dw = nullptr;
+    int* dk = nullptr;
+    const size_t b = 2 * sizeof(double) * (size_t)n;
+    cudaError_t e = cudaMalloc(&dz, b);
+    if (e == cudaSuccess) e = cudaMalloc(&dw, b);
+    if (e == cudaSuccess) e = cudaMalloc(&dk, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpy(dz, z, b, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_crcp_probe<<<(unsigned)((n + 255) / 256), 256>>>(dz, dw, dk, n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(w, dw, b, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(ok, dk, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(dz);
+    cudaFree(dw);
+    cudaFree(dk);
+    return (int)e;
+}

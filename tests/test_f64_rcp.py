@@ -112,6 +112,28 @@ def test_rcp_out_of_range_inputs_flag_and_give_nan(shim):
     assert np.isnan(y).all()
 
 
+def test_complex_rcp_signs_of_zero_components(shim):
+    """conj(z) |z|^-2 keeps re's sign and flips im's, zeros included."""
+    t = np.ascontiguousarray(np.array([complex(1.0, 0.0), complex(1.0, -0.0), complex(-0.0, 2.0),
+                                       complex(-2.0, -0.0)]))
+    w = np.empty_like(t)
+    ok = np.empty(len(t), np.int32)
+    shim.shim_crcp_d(ptr(t), ptr(w), ptr(ok), len(t))
+    assert ok.all()
+    assert list(np.signbit(w.real)) == list(np.signbit(t.real))
+    assert list(np.signbit(w.imag)) == list(~np.signbit(t.imag))
+
+
+def test_complex_rcp_out_of_range_inputs_flag_and_give_nan(shim):
+    z = np.ascontiguousarray(np.array([0j, complex(np.inf, 0), complex(np.nan, 1), 1e-200 + 0j, 1e200 + 0j,
+                                       2.0 ** 511 + 1j], dtype=np.complex128))
+    w = np.empty_like(z)
+    ok = np.empty(len(z), np.int32)
+    shim.shim_crcp_d(ptr(z), ptr(w), ptr(ok), len(z))
+    assert not ok.any()
+    assert np.isnan(w.real).all() and np.isnan(w.imag).all()
+
+
 def test_complex_rcp_relative_error(shim):
     """crcp<double> = conj(z) |z|^-2: a few ulps of |1/z| per component."""
     rng = np.random.default_rng(11)

@@ -96,3 +96,43 @@ def test_fma_forms_of_add_sub_mul_are_bitwise_the_plain_operations(tmp_path):
         for k, ref in ((1, A + B), (3, A - B), (5, A * B)):
             nan = np.isnan(ref)
             assert np.array_equal(out[~nan, k].view(np.int64), ref[~nan].view(np.int64))
+
+
+@pytest.mark.gpu
+def test_device_complex_rcp_matches_host_build(tmp_path):
+    """crcp<double> (|z|^2 and the products as FMAs, d_rcp's integer rounding; its
+    error checked against exact rationals on the host in test_f64_rcp.py) bit for bit
+    the same on the B300 as on the host, over a wide magnitude sweep, both axes,
+    subnormal results and out-of-range inputs."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = _build(tmp_path, os.path.join(ROOT, "tests", "rcp_probe.cu"),
+                 ["/usr/local/cuda/bin/nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                  "-shared", "-Xcompiler", "-fPIC", "-cudart", "shared"])
+    host = _build(tmp_path, os.path.join(ROOT, "tests", "df_shim.cpp"),
+                  ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-I/usr/local/cuda/include"])
+    P = C.c_void_p
+    dev.crcp_probe.argtypes = [P, P, P, C.c_long]
+    host.shim_crcp_d.argtypes = [P, P, P, C.c_long]
+    rng = np.random.default_rng(109)
+    n = 1 << 20
+    mag = np.exp2(rng.uniform(-505, 505, n))  # |z|^2 inside the valid range
+    z = mag * np.exp(2j * np.pi * rng.random(n))
+    z[:4096] = mag[:4096]
+    z[4096:8192] = 1j * mag[4096:8192]
+    edge = np.array([1 + 5e-324j, 1e-310 + 1j, 0j, complex(np.inf, 0), complex(np.nan, 1), 1e-200 + 0j,
+                     2.0 ** 511 + 1j, complex(-0.0, 2.0)])
+    z = np.ascontiguousarray(np.concatenate([z, edge]).astype(np.complex128))
+    m = len(z)
+    w, hw = np.empty_like(z), np.empty_like(z)
+    ok, hok = np.empty(m, np.int32), np.empty(m, np.int32)
+    pt = lambda a: a.ctypes.data_as(P)  # noqa: E731
+    assert dev.crcp_probe(pt(z), pt(w), pt(ok), m) == 0
+    host.shim_crcp_d(pt(z), pt(hw), pt(hok), m)
+    assert np.array_equal(ok, hok)
+    assert np.array_equal(w.view(np.int64), hw.view(np.int64))  # bitwise, NaNs included
+    v = ok.astype(bool)
+    assert v.sum() >= m - 16
+    ref = 1.0 / z[v]
+    assert np.max(np.abs(w[v] - ref) / np.abs(ref)) < 1e-15
