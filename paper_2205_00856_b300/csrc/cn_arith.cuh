@@ -215,6 +215,65 @@ CNB_HD double d_mul(double a, double b) {
 #endif
 }
 
+// x + y on the integer pipe, the IEEE binary64 sum rounded to nearest even bit for
+// bit (signed zeros, subnormals, overflow, infinities; a NaN result is a quiet NaN):
+// the operands ordered by magnitude, their significands with three guard bits (the
+// lowest a sticky bit) aligned, added or subtracted, normalised by at most one place
+// right or any number left (not below the subnormal exponent), and rounded.  For
+// additions off the kernels' dependency chains, where the FP64 pipe is the limit and
+// the integer pipe idles.
+// The operands' bits move to integer registers through an opaque move: the compiler
+// would otherwise fold the sign-bit masks below back into FP64 absolute values.
+CNB_HD uint64_t d_bits_opaque(double a) {
+#ifdef __CUDA_ARCH__
+    uint64_t r;
+    asm("mov.b64 %0, %1;" : "=l"(r) : "d"(a));
+    return r;
+#else
+    return (uint64_t)d_bits(a);
+#endif
+}
+CNB_HD double d_add_int(double x, double y) {
+    const uint64_t SIGN = 0x8000000000000000ull, FRAC = 0xFFFFFFFFFFFFFull, HID = 0x10000000000000ull;
+    uint64_t a = d_bits_opaque(x), b = d_bits_opaque(y);
+    if ((a & ~SIGN) < (b & ~SIGN)) {
+        const uint64_t t = a;
+        a = b;
+        b = t;
+    }
+    const uint64_t am = a & ~SIGN, bm = b & ~SIGN;
+    const int ea = (int)(am >> 52), eb = (int)(bm >> 52);
+    if (ea == 2047) {  // an infinity or a NaN, the larger magnitude
+        if (am > 0x7FF0000000000000ull) return d_from_bits((int64_t)(a | 0x0008000000000000ull));
+        if (bm == 0x7FF0000000000000ull && ((a ^ b) & SIGN)) return d_from_bits(0x7FF8000000000000ll);
+        return d_from_bits((int64_t)a);
+    }
+    if (bm == 0) return d_from_bits((int64_t)(am == 0 ? (a & b) : a));  // (-0) + (-0) = -0, else +0
+    const int e0 = ea ? ea : 1;
+    const int d = e0 - (eb ? eb : 1);  // >= 0
+    const uint64_t ma = ((am & FRAC) | (ea ? HID : 0)) << 3;
+    const uint64_t mb0 = ((bm & FRAC) | (eb ? HID : 0)) << 3;
+    const uint64_t mb = d == 0 ? mb0 : (d >= 64 ? (uint64_t)1 : ((mb0 >> d) | (uint64_t)((mb0 << (64 - d)) != 0)));
+    uint64_t m = ((a ^ b) & SIGN) ? ma - mb : ma + mb;
+    if (m == 0) return 0.0;  // exact cancellation: +0
+    int e = e0;
+    const int lz = u64_clz(m) - 8;  // the leading bit belongs at bit 55
+    if (lz < 0) {
+        m = (m >> 1) | (m & 1u);
+        e += 1;
+    } else if (lz > 0) {
+        const int sl = lz < e - 1 ? lz : e - 1;
+        m <<= sl;
+        e -= sl;
+    }
+    if (e >= 2047) return d_from_bits((int64_t)((a & SIGN) | 0x7FF0000000000000ull));
+    const uint64_t g = m & 7u;
+    uint64_t q = m >> 3;
+    q += (uint64_t)(g > 4u || (g == 4u && (q & 1u)));
+    // normal: q holds the hidden bit (a carry into 2^53 bumps the exponent); subnormal: e == 1
+    return d_from_bits((int64_t)((a & SIGN) | (((uint64_t)(e - 1) << 52) + q)));
+}
+
 CNB_HD float i2f(int32_t i) {
 #ifdef __CUDA_ARCH__
     return __int2float_rn(i);

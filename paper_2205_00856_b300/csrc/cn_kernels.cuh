@@ -1509,7 +1509,7 @@ __device__ __forceinline__ cx<double> explicit_row(cx<double> pm, cx<double> p0,
     if constexpr (ES == 0) {
         return mk(d_mul(sg, p0.im), d_mul(-sg, p0.re));
     } else {
-        double sr = d_add(pm.re, pp.re), si = d_add(pm.im, pp.im);
+        double sr = d_add_int(pm.re, pp.re), si = d_add_int(pm.im, pp.im);  // off the pivot chain
         const double eb = ES > 0 ? bt : -bt;
         if (ES > 0) { sr = -sr; si = -si; }
         return mk(fma(eb, p0.re, fma(sg, p0.im, sr)), fma(eb, p0.im, fma(-sg, p0.re, si)));

@@ -62,6 +62,10 @@ void shim_cop(int op, const float* a, const float* b, const float* c, float* out
         ok[i] = k;
     }
 }
+// binary64 addition on the integer pipe
+void shim_d_add_int(const double* x, const double* y, double* z, long n) {
+    for (long i = 0; i < n; ++i) z[i] = d_add_int(x[i], y[i]);
+}
 // binary64 reciprocal d_rcp and complex reciprocal crcp<double>
 void shim_d_rcp(const double* q, double* y, int* ok, long n) {
     for (long i = 0; i < n; ++i) { bool k = true; y[i] = d_rcp(q[i], k); ok[i] = k; }

@@ -40,18 +40,20 @@ extern "C" int rcp_probe(const double* q, double* y, double* ref, int* ok, long 
 
 // The FMA forms of binary64 addition, subtraction and multiplication (d_add,
 // d_sub, d_mul: fma with 1 or -0 from constant memory) next to the plain
-// operations, element i of out holding (d_add, a + b, d_sub, a - b, d_mul, a b).
+// operations, element i of out holding (d_add, a + b, d_sub, a - b, d_mul, a b,
+// d_add_int: the addition on the integer pipe).
 __global__ void k_fma_form_probe(const double* a, const double* b, double* out, long n) {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double x = a[i], y = b[i];
-    double* o = out + 6 * i;
+    double* o = out + 7 * i;
     o[0] = cnb::d_add(x, y);
     o[1] = __dadd_rn(x, y);
     o[2] = cnb::d_sub(x, y);
     o[3] = __dsub_rn(x, y);
     o[4] = cnb::d_mul(x, y);
     o[5] = __dmul_rn(x, y);
+    o[6] = cnb::d_add_int(x, y);
 }
 
 extern "C" int fma_form_probe(const double* a, const double* b, double* out, long n) {
@@ -59,14 +61,14 @@ extern "C" int fma_form_probe(const double* a, const double* b, double* out, lon
     const size_t bytes = sizeof(double) * (size_t)n;
     cudaError_t e = cudaMalloc(&da, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&db, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&dout, 6 * bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, 7 * bytes);
     if (e == cudaSuccess) e = cudaMemcpy(da, a, bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(db, b, bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         k_fma_form_probe<<<(unsigned)((n + 255) / 256), 256>>>(da, db, dout, n);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpy(out, dout, 6 * bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, 7 * bytes, cudaMemcpyDeviceToHost);
     cudaFree(da);
     cudaFree(db);
     cudaFree(dout);

@@ -56,9 +56,10 @@ def test_device_rcp_matches_host_build_and_cuda_division(tmp_path):
 @pytest.mark.gpu
 def test_fma_forms_of_add_sub_mul_are_bitwise_the_plain_operations(tmp_path):
     """d_add / d_sub / d_mul (the binary64 kernels' additions, subtractions and
-    multiplications, issued as FMAs with 1 or -0 from constant memory) against the
-    device's own correctly rounded __dadd_rn / __dsub_rn / __dmul_rn: bitwise equal,
-    signed zeros, subnormals, overflow and infinities included (NaN results: NaN)."""
+    multiplications, issued as FMAs with 1 or -0 from constant memory) and d_add_int
+    (the addition on the integer pipe) against the device's own correctly rounded
+    __dadd_rn / __dsub_rn / __dmul_rn: bitwise equal, signed zeros, subnormals,
+    overflow and infinities included (NaN results: NaN)."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -82,12 +83,12 @@ def test_fma_forms_of_add_sub_mul_are_bitwise_the_plain_operations(tmp_path):
     A = np.ascontiguousarray(np.concatenate([a, c, sa.ravel(), c]))
     B = np.ascontiguousarray(np.concatenate([b, d, sb.ravel(), np.ldexp(d, -560)]))
     m = len(A)
-    out = np.empty(6 * m)
+    out = np.empty(7 * m)
     pt = lambda v: v.ctypes.data_as(P)  # noqa: E731
     assert dev.fma_form_probe(pt(A), pt(B), pt(out), m) == 0
-    out = out.reshape(m, 6)
-    for k in (0, 2, 4):
-        got, ref = out[:, k], out[:, k + 1]
+    out = out.reshape(m, 7)
+    for k, r in ((0, 1), (2, 3), (4, 5), (6, 1)):  # (6, 1): d_add_int against __dadd_rn
+        got, ref = out[:, k], out[:, r]
         nan = np.isnan(ref)
         assert np.array_equal(np.isnan(got), nan)
         assert np.array_equal(got[~nan].view(np.int64), ref[~nan].view(np.int64))
