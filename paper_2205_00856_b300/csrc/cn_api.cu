@@ -1041,6 +1041,11 @@ cn_status create_engine(Engine* p, const cn_desc* desc, const std::vector<int64_
     c.c1_f = split(c.c1);
     c.gt_f = split(c.gt);
     c.soft_f = split(c.soft_s);
+    // the explicit row's additions on the integer pipe where level 0 fills the GPU (two
+    // or more CTAs of kThreads blocks per SM): the FP64 pipe bounds such steps (N = 2^24:
+    // 1.299 -> 1.260 ms), while a latency-bound small grid only gets longer threads
+    // (n = 4096: 43 -> 46 us)
+    c.sigma_int = p->lv[0].total >= 2 * (int64_t)p->sms * kThreads ? 1 : 0;
     const double two_pi = 2.0 * 3.14159265358979323846;
     if (use_table && e == cudaSuccess) e = dbg_register(p, nullptr, {});
     if (use_table) {
