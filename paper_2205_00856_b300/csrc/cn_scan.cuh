@@ -98,17 +98,27 @@ template <class R> __device__ __forceinline__ Mob<R> mob_normalize(Mob<R> m) {
     m.d = cscale(m.d, e);
     return m;
 }
-// binary64: the largest exponent field by integer operations and one multiply by
-// the power of two per component (no binary64 operation besides the multiplies)
+// binary64: the largest exponent field and the scaling by integer operations only
+// (no binary64 operation: each would cost a warp ~64 clocks of the FP64 pipe)
 __device__ __forceinline__ int efield(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
 __device__ __forceinline__ int efield(cx<double> z) { return max(efield(z.re), efield(z.im)); }
+// v 2^k by an integer add to the exponent field, exact; zeros, subnormals and
+// values that would leave the normal range become signed zeros (entries 2^-1022
+// below the matrix's largest, which it then leaves at ~1, contribute nothing)
+__device__ __forceinline__ double scale_exp(double v, int k) {
+    const uint64_t b = d_bits_opaque(v);
+    const int e = (int)((b >> 52) & 0x7ff), e2 = e + k;
+    const uint64_t sgn = b & 0x8000000000000000ull;
+    if (e == 0 || e2 <= 0) return __longlong_as_double((long long)sgn);
+    return __longlong_as_double((long long)((b & 0x800FFFFFFFFFFFFFull) | ((uint64_t)e2 << 52)));
+}
 template <> __device__ __forceinline__ Mob<double> mob_normalize(Mob<double> m) {
     const int em = min(max(max(efield(m.a), efield(m.b)), max(efield(m.c), efield(m.d))), 2045);
-    const double f = __longlong_as_double((long long)(2046 - em) << 52);  // 2^(1023 - em)
-    m.a = mk(m.a.re * f, m.a.im * f);
-    m.b = mk(m.b.re * f, m.b.im * f);
-    m.c = mk(m.c.re * f, m.c.im * f);
-    m.d = mk(m.d.re * f, m.d.im * f);
+    const int k = 1023 - em;  // the largest entry to [1, 2)
+    m.a = mk(scale_exp(m.a.re, k), scale_exp(m.a.im, k));
+    m.b = mk(scale_exp(m.b.re, k), scale_exp(m.b.im, k));
+    m.c = mk(scale_exp(m.c.re, k), scale_exp(m.c.im, k));
+    m.d = mk(scale_exp(m.d.re, k), scale_exp(m.d.im, k));
     return m;
 }
 // later o earlier: the matrix product L E
