@@ -74,3 +74,28 @@ def test_too_deep_rejected():
     with pytest.raises(cnb.CNError) as ei:
         cnb.Plan(1000, 0.1, 0.01, -50.0, levels=[100], flags=cnb.FLAG_RECOMPUTE)
     assert ei.value.code == 2
+
+
+@pytest.mark.parametrize("arith", [cnb.ARITH_F64, cnb.ARITH_DF64])
+@pytest.mark.parametrize("n,levels,rs_rows", [(129, [64], 3), (97, [24], 5), (2001, [125], 17), (3101, [100], 32),
+                                              (4001, [8, 16], 33)])
+def test_short_reduced_systems_by_pcr_vs_oracle(arith, n, levels, rs_rows):
+    """Explicit-depth plans whose last reduced system has at most 32 rows solve it by
+    parallel cyclic reduction on one warp (33 rows: the scan or one-thread walk):
+    the general solve against Thomas and CN steps against the oracle."""
+    plan = cnb.Plan(n, 0.1, 0.01, -0.05 * n, pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith, levels=levels)
+    assert plan.info()["level_rows"][-1] == rs_rows
+    b, a, c, d = W.random_system(n, np.random.default_rng(n))
+    t = [torch.from_numpy(v).to(DEV) for v in (b, a, c, d)]
+    x = plan.solve_tridiag(*t).cpu().numpy()
+    assert rel(x, oracle.thomas(b, a, c, d)) <= 1e-12
+    cfg = W.soft_coulomb_config(n=n, nsteps=6)
+    psi0 = W.full_support_state(n, cfg["dx"], cfg["x_min"], seed=n)
+    E = W.field_midpoints(6, cfg["dt"], t0=30.0)
+    plan2 = cnb.Plan(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=cnb.POT_SOFTCOULOMB, soft_s=2.0, arith=arith,
+                     levels=levels)
+    out = plan2.step(torch.from_numpy(psi0).to(DEV), 6, E_mid=torch.from_numpy(E).to(DEV)).cpu().numpy()
+    plan.check()
+    plan2.check()
+    prob = oracle.Problem(n, cfg["dx"], cfg["dt"], cfg["x_min"], pot=oracle.POT_SOFTCOULOMB, soft_s=2.0)
+    assert rel(out, oracle.cn_run(prob, psi0, 6, E_mid=E)) <= 1e-11
