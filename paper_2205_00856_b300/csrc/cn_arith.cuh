@@ -215,13 +215,6 @@ CNB_HD double d_mul(double a, double b) {
 #endif
 }
 
-// x + y on the integer pipe, the IEEE binary64 sum rounded to nearest even bit for
-// bit (signed zeros, subnormals, overflow, infinities; a NaN result is a quiet NaN):
-// the operands ordered by magnitude, their significands with three guard bits (the
-// lowest a sticky bit) aligned, added or subtracted, normalised by at most one place
-// right or any number left (not below the subnormal exponent), and rounded.  For
-// additions off the kernels' dependency chains, where the FP64 pipe is the limit and
-// the integer pipe idles.
 // The operands' bits move to integer registers through an opaque move: the compiler
 // would otherwise fold the sign-bit masks below back into FP64 absolute values.
 CNB_HD uint64_t d_bits_opaque(double a) {
@@ -233,6 +226,14 @@ CNB_HD uint64_t d_bits_opaque(double a) {
     return (uint64_t)d_bits(a);
 #endif
 }
+
+// x + y on the integer pipe, the IEEE binary64 sum rounded to nearest even bit for
+// bit (signed zeros, subnormals, overflow, infinities; a NaN result is a quiet NaN):
+// the operands ordered by magnitude, their significands with three guard bits (the
+// lowest a sticky bit) aligned, added or subtracted, normalised by at most one place
+// right or any number left (not below the subnormal exponent), and rounded.  For
+// additions off the kernels' dependency chains, where the FP64 pipe is the limit and
+// the integer pipe idles.
 CNB_HD double d_add_int(double x, double y) {
     const uint64_t SIGN = 0x8000000000000000ull, FRAC = 0xFFFFFFFFFFFFFull, HID = 0x10000000000000ull;
     uint64_t a = d_bits_opaque(x), b = d_bits_opaque(y);
@@ -272,6 +273,121 @@ CNB_HD double d_add_int(double x, double y) {
     q += (uint64_t)(g > 4u || (g == 4u && (q & 1u)));
     // normal: q holds the hidden bit (a carry into 2^53 bumps the exponent); subnormal: e == 1
     return d_from_bits((int64_t)((a & SIGN) | (((uint64_t)(e - 1) << 52) + q)));
+}
+
+// 128-bit unsigned arithmetic for the integer-pipe FMA
+struct u128 {
+    uint64_t hi, lo;
+};
+CNB_HD u128 u128_of(uint64_t hi, uint64_t lo) {
+    u128 r;
+    r.hi = hi;
+    r.lo = lo;
+    return r;
+}
+CNB_HD u128 u128_mul(uint64_t a, uint64_t b) { return u128_of(u64_mulhi(a, b), a * b); }
+CNB_HD u128 u128_add(u128 a, u128 b) {
+    const uint64_t lo = a.lo + b.lo;
+    return u128_of(a.hi + b.hi + (uint64_t)(lo < a.lo), lo);
+}
+CNB_HD u128 u128_sub(u128 a, u128 b) {  // a >= b
+    return u128_of(a.hi - b.hi - (uint64_t)(a.lo < b.lo), a.lo - b.lo);
+}
+CNB_HD bool u128_ge(u128 a, u128 b) { return a.hi != b.hi ? a.hi > b.hi : a.lo >= b.lo; }
+// shifts by 0..127 (anything larger gives 0)
+CNB_HD u128 u128_shr(u128 a, int s) {
+    if (s <= 0) return a;
+    if (s >= 128) return u128_of(0, 0);
+    if (s >= 64) return u128_of(0, a.hi >> (s - 64));
+    return u128_of(a.hi >> s, (a.lo >> s) | (a.hi << (64 - s)));
+}
+CNB_HD u128 u128_shl(u128 a, int s) {
+    if (s <= 0) return a;
+    if (s >= 128) return u128_of(0, 0);
+    if (s >= 64) return u128_of(a.lo << (s - 64), 0);
+    return u128_of((a.hi << s) | (a.lo >> (64 - s)), a.lo << s);
+}
+// index of the leading bit (a != 0)
+CNB_HD int u128_top(u128 a) { return a.hi ? 127 - u64_clz(a.hi) : 63 - u64_clz(a.lo | 1); }
+// a 2^s: shifted left, or right with the bits shifted out OR-ed into bit 0 (sticky)
+CNB_HD u128 u128_place(u128 a, int s) {
+    if (s >= 0) return u128_shl(a, s);
+    const int r = -s;
+    u128 v = u128_shr(a, r);
+    const u128 out = r >= 128 ? a : u128_shl(a, 128 - r);
+    if ((out.hi | out.lo) != 0) v.lo |= 1u;
+    return v;
+}
+// the binary64 bits (sign clear) of U 2^X, U != 0, rounded to nearest even;
+// subnormal results by the same rounding at the subnormal position, overflow to
+// infinity
+CNB_HD uint64_t u128_round_pack(u128 U, int X) {
+    const int t = u128_top(U);
+    int Eo = t + X + 1023;  // biased exponent of a normal result
+    int sh = t - 52;        // bits below the 53 kept
+    if (Eo < 1) {
+        sh += 1 - Eo;
+        Eo = 0;
+    }
+    if (Eo >= 2047) return 0x7FF0000000000000ull;
+    uint64_t m;
+    if (sh <= 0) {
+        m = U.lo << (-sh);  // t <= 52: exact
+    } else {
+        if (sh - 1 > t) return 0;  // below half the smallest subnormal
+        m = u128_shr(U, sh).lo;
+        const uint64_t rnd = u128_shr(U, sh - 1).lo & 1u;
+        const u128 low = u128_shl(U, 129 - sh);  // the bits below the rounding bit
+        const uint64_t sticky = (low.hi | low.lo) != 0;
+        m += rnd & (sticky | (m & 1u));
+    }
+    return Eo >= 1 ? ((uint64_t)(Eo - 1) << 52) + m : m;  // a carry into 2^53 (2^52) bumps the exponent
+}
+// fma(x, y, z) on the integer pipe, the IEEE binary64 x y + z rounded once to nearest
+// even bit for bit (signed zeros, subnormals, overflow, infinities; a NaN result is
+// a quiet NaN): the exact 106-bit product and z placed in a 128-bit window whose
+// bit 125 holds the larger's leading bit (a smaller operand reaching below bit 0
+// folds into a sticky bit there, far below any rounding position: only operands
+// within ~20 binades of each other can cancel, and those fit whole), added or
+// subtracted, rounded.  For FMAs that feed no recurrence (see d_add_int).
+CNB_HD double d_fma_int(double x, double y, double z) {
+    const uint64_t SIGN = 0x8000000000000000ull, FRAC = 0xFFFFFFFFFFFFFull, HID = 0x10000000000000ull;
+    const uint64_t INF = 0x7FF0000000000000ull, QNAN = 0x7FF8000000000000ull;
+    const uint64_t a = d_bits_opaque(x), b = d_bits_opaque(y), c = d_bits_opaque(z);
+    const uint64_t sp = (a ^ b) & SIGN, sc = c & SIGN;
+    const uint64_t am = a & ~SIGN, bm = b & ~SIGN, cm = c & ~SIGN;
+    if (am > INF || bm > INF || cm > INF) return d_from_bits((int64_t)QNAN);
+    const bool pzero = am == 0 || bm == 0;
+    if (am == INF || bm == INF) {
+        if (pzero || (cm == INF && sc != sp)) return d_from_bits((int64_t)QNAN);  // inf 0, inf - inf
+        return d_from_bits((int64_t)(sp | INF));
+    }
+    if (cm == INF) return d_from_bits((int64_t)c);
+    if (pzero) return d_from_bits((int64_t)(cm == 0 ? (sp & sc) : c));  // an exact signed zero plus z
+    const int ea = (int)(am >> 52), eb = (int)(bm >> 52), ec = (int)(cm >> 52);
+    const uint64_t ma = (am & FRAC) | (ea ? HID : 0), mb = (bm & FRAC) | (eb ? HID : 0);
+    const int Xp = (ea ? ea : 1) + (eb ? eb : 1) - 2150;  // x y = P 2^Xp exactly
+    const u128 P = u128_mul(ma, mb);
+    if (cm == 0) return d_from_bits((int64_t)(sp | u128_round_pack(P, Xp)));
+    const uint64_t mc = (cm & FRAC) | (ec ? HID : 0);
+    const int Xc = (ec ? ec : 1) - 1075;  // z = mc 2^Xc
+    const int tP = u128_top(P) + Xp, tC = (63 - u64_clz(mc)) + Xc;
+    const int W0 = (tP > tC ? tP : tC) - 125;  // exponent of the window's bit 0
+    const u128 Pw = u128_place(P, Xp - W0), Cw = u128_place(u128_of(0, mc), Xc - W0);
+    u128 R;
+    uint64_t rs;
+    if (sp == sc) {
+        R = u128_add(Pw, Cw);
+        rs = sp;
+    } else if (u128_ge(Pw, Cw)) {
+        R = u128_sub(Pw, Cw);
+        rs = sp;
+    } else {
+        R = u128_sub(Cw, Pw);
+        rs = sc;
+    }
+    if ((R.hi | R.lo) == 0) return 0.0;  // exact cancellation: +0
+    return d_from_bits((int64_t)(rs | u128_round_pack(R, W0)));
 }
 
 CNB_HD float i2f(int32_t i) {

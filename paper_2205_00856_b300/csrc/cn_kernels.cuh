@@ -1512,15 +1512,15 @@ __device__ __forceinline__ cx<double> explicit_row(cx<double> pm, cx<double> p0,
     if constexpr (ES == 0) {
         return mk(d_mul(sg, p0.im), d_mul(-sg, p0.re));
     } else {
-        double sr, si;  // sigma, the same bits either way; off the pivot chain
-        if (sig_int) {
-            sr = d_add_int(pm.re, pp.re);
-            si = d_add_int(pm.im, pp.im);
-        } else {
-            sr = d_add(pm.re, pp.re);
-            si = d_add(pm.im, pp.im);
-        }
+        // the same bits either way: sigma and the inner FMAs feed no recurrence, so where
+        // the FP64 pipe bounds the step they run on the integer pipe
         const double eb = ES > 0 ? bt : -bt;
+        if (sig_int) {
+            double sr = d_add_int(pm.re, pp.re), si = d_add_int(pm.im, pp.im);
+            if (ES > 0) { sr = -sr; si = -si; }
+            return mk(fma(eb, p0.re, d_fma_int(sg, p0.im, sr)), fma(eb, p0.im, d_fma_int(-sg, p0.re, si)));
+        }
+        double sr = d_add(pm.re, pp.re), si = d_add(pm.im, pp.im);
         if (ES > 0) { sr = -sr; si = -si; }
         return mk(fma(eb, p0.re, fma(sg, p0.im, sr)), fma(eb, p0.im, fma(-sg, p0.re, si)));
     }

@@ -62,9 +62,15 @@ void shim_cop(int op, const float* a, const float* b, const float* c, float* out
         ok[i] = k;
     }
 }
-// binary64 addition on the integer pipe
+// binary64 addition and FMA on the integer pipe
 void shim_d_add_int(const double* x, const double* y, double* z, long n) {
     for (long i = 0; i < n; ++i) z[i] = d_add_int(x[i], y[i]);
+}
+void shim_d_fma_int(const double* x, const double* y, const double* z, double* r, long n) {
+    for (long i = 0; i < n; ++i) r[i] = d_fma_int(x[i], y[i], z[i]);
+}
+void shim_fma(const double* x, const double* y, const double* z, double* r, long n) {
+    for (long i = 0; i < n; ++i) r[i] = fma(x[i], y[i], z[i]);
 }
 // binary64 reciprocal d_rcp and complex reciprocal crcp<double>
 void shim_d_rcp(const double* q, double* y, int* ok, long n) {

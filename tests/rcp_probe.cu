@@ -106,3 +106,34 @@ extern "C" int crcp_probe(const double* z, double* w, int* ok, long n) {
     cudaFree(dk);
     return (int)e;
 }
+
+// The FMA on the integer pipe (d_fma_int) next to the device's fma, element i of out
+// holding (d_fma_int(x, y, z), fma(x, y, z)).
+__global__ void k_fma_int_probe(const double* x, const double* y, const double* z, double* out, long n) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[2 * i] = cnb::d_fma_int(x[i], y[i], z[i]);
+    out[2 * i + 1] = __fma_rn(x[i], y[i], z[i]);
+}
+
+extern "C" int fma_int_probe(const double* x, const double* y, const double* z, double* out, long n) {
+    double *dx = nullptr, *dy = nullptr, *dz = nullptr, *dout = nullptr;
+    const size_t bytes = sizeof(double) * (size_t)n;
+    cudaError_t e = cudaMalloc(&dx, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&dy, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&dz, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, 2 * bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(dx, x, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dy, y, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dz, z, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_fma_int_probe<<<(unsigned)((n + 255) / 256), 256>>>(dx, dy, dz, dout, n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, 2 * bytes, cudaMemcpyDeviceToHost);
+    cudaFree(dx);
+    cudaFree(dy);
+    cudaFree(dz);
+    cudaFree(dout);
+    return (int)e;
+}

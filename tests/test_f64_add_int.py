@@ -1,8 +1,9 @@
-"""CPU check of the binary64 addition on the integer pipe (d_add_int in
-csrc/cn_arith.cuh, built for the host): bit for bit the IEEE sum rounded to
-nearest even (numpy's, on the host's FPU) over random operands across the whole
-exponent range, near-cancelling pairs, widely separated magnitudes, subnormals,
-and every pair of special values (NaN results compared as NaN)."""
+"""CPU checks of the binary64 addition and FMA on the integer pipe (d_add_int,
+d_fma_int in csrc/cn_arith.cuh, built for the host): bit for bit the IEEE sum
+(numpy's, on the host's FPU) and the correctly rounded fma (the C library's) over
+random operands across the whole exponent range, near-cancellation, widely
+separated magnitudes, subnormals, and every combination of special values (NaN
+results compared as NaN)."""
 import ctypes as C
 import os
 import subprocess
@@ -49,3 +50,19 @@ def test_add_int_is_the_ieee_sum_bit_for_bit(shim):
     nan = np.isnan(R)
     assert np.array_equal(np.isnan(Z), nan)
     assert np.array_equal(Z[~nan].view(np.int64), R[~nan].view(np.int64))
+
+
+def test_fma_int_is_the_correctly_rounded_fma_bit_for_bit(shim):
+    """d_fma_int against the host's fma (correctly rounded, C99): random triples,
+    near-cancellation, z far above and below x y, subnormal results, specials."""
+    from test_gpu_rcp import fma_cases
+    shim.shim_d_fma_int.argtypes = [C.c_void_p] * 4 + [C.c_long]
+    shim.shim_fma.argtypes = [C.c_void_p] * 4 + [C.c_long]
+    X, Y, Z = fma_cases(np.random.default_rng(9), 200_000)
+    R, Rr = np.empty_like(X), np.empty_like(X)
+    p = lambda v: v.ctypes.data_as(C.c_void_p)  # noqa: E731
+    shim.shim_d_fma_int(p(X), p(Y), p(Z), p(R), len(X))
+    shim.shim_fma(p(X), p(Y), p(Z), p(Rr), len(X))
+    nan = np.isnan(Rr)
+    assert np.array_equal(np.isnan(R), nan)
+    assert np.array_equal(R[~nan].view(np.int64), Rr[~nan].view(np.int64))

@@ -137,3 +137,48 @@ def test_device_complex_rcp_matches_host_build(tmp_path):
     assert v.sum() >= m - 16
     ref = 1.0 / z[v]
     assert np.max(np.abs(w[v] - ref) / np.abs(ref)) < 1e-15
+
+
+def fma_cases(rng, n):
+    """Random triples over wide exponent ranges, near-cancelling x y + z, z far above
+    and far below the product, subnormal results, and every triple of special values."""
+    def signs(k):
+        return np.where(rng.random(k) < 0.5, -1.0, 1.0)
+
+    def wide(k, lo=-1074, hi=1024):
+        return signs(k) * np.ldexp(1.0 + rng.random(k), rng.integers(lo, hi, k))
+    x1, y1, z1 = wide(n, -600, 600), wide(n, -600, 600), wide(n)
+    x2, y2 = wide(n, -300, 300), wide(n, -300, 300)
+    z2 = -(x2 * y2) * (1 + np.ldexp(rng.integers(-6, 7, n).astype(float), -52))
+    x3, y3 = wide(n, -40, 40), wide(n, -40, 40)
+    z3 = (x3 * y3) * np.ldexp(1.0, rng.integers(-120, 120, n)) * signs(n)
+    x4, y4 = wide(n, -540, -500), wide(n, -540, -500)
+    z4 = signs(n) * np.ldexp(rng.random(n), -1022)
+    sp = np.array([0.0, -0.0, 5e-324, -5e-324, 2.0 ** -1022, np.inf, -np.inf, np.nan, 1.0, -1.0,
+                   1.7976931348623157e308, 2.0 ** -537, 3.0])
+    g = np.array(np.meshgrid(sp, sp, sp)).reshape(3, -1)
+    cat = lambda *v: np.ascontiguousarray(np.concatenate(v))  # noqa: E731
+    return cat(x1, x2, x3, x4, g[0]), cat(y1, y2, y3, y4, g[1]), cat(z1, z2, z3, z4, g[2])
+
+
+@pytest.mark.gpu
+def test_fma_int_is_the_device_fma_bit_for_bit(tmp_path):
+    """d_fma_int (the explicit row's inner FMAs on the integer pipe) against the
+    device's own fma: bitwise equal (NaN results: NaN)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = _build(tmp_path, os.path.join(ROOT, "tests", "rcp_probe.cu"),
+                 ["/usr/local/cuda/bin/nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                  "-shared", "-Xcompiler", "-fPIC", "-cudart", "shared"])
+    P = C.c_void_p
+    dev.fma_int_probe.argtypes = [P, P, P, P, C.c_long]
+    X, Y, Z = fma_cases(np.random.default_rng(113), 1 << 18)
+    m = len(X)
+    out = np.empty(2 * m)
+    pt = lambda v: v.ctypes.data_as(P)  # noqa: E731
+    assert dev.fma_int_probe(pt(X), pt(Y), pt(Z), pt(out), m) == 0
+    out = out.reshape(m, 2)
+    nan = np.isnan(out[:, 1])
+    assert np.array_equal(np.isnan(out[:, 0]), nan)
+    assert np.array_equal(out[~nan, 0].view(np.int64), out[~nan, 1].view(np.int64))
