@@ -52,7 +52,8 @@ PG_TIMEOUT_S = 900     # process-group timeout: longer than any phase between tw
 #
 # Binary64 (additions, multiplications and FMAs count one each; flops count an FMA
 # as 2).  On the device every addition and multiplication is issued as an FMA,
-# except the explicit row's two additions, which run on the integer pipe.
+# except the explicit row's two additions and two inner FMAs, which run on the
+# integer pipe in grids that fill the GPU.
 # Reduction loop row: coefficient 1 (FMA with the
 # tabulated x), explicit row 6 (2 additions, 4 FMAs), RD: d 4, pivot 2 + complex
 # reciprocal 5 (|z|^2 2, the real reciprocal 1 FMA and integer rounding, 2
@@ -527,15 +528,19 @@ def roofline(prof, n, arith, peaks, m, table, sms):
         ops = f64_ops_per_row(dom, m, table)
         achieved = ops * n / avg_s / 1e12
         peak = FP64_MEASURED_OPS / 1e12 if FP64_MEASURED_OPS else None
-        # the explicit row's two additions (sigma) run on the integer pipe: every
-        # grid row has one explicit row in the reduction and the fused kernels
-        pipe_ops = ops - (2.0 if dom in ("reduce_level0", "fused_level0") else 0.0)
+        # the explicit row's two additions (sigma) and its two inner FMAs run on the
+        # integer pipe where level 0 fills the GPU (the library's rule: two or more
+        # CTAs of 128 blocks per SM); every grid row has one explicit row in the
+        # reduction and the fused kernels
+        int_pipe = -(-(n - 1) // m) >= 2 * sms * 128 and dom in ("reduce_level0", "fused_level0")
+        pipe_ops = ops - (4.0 if int_pipe else 0.0)
         pipe_achieved = pipe_ops * n / avg_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
                 "frac": achieved / peak if peak else None, "peak_source": FP64_PEAK_SOURCE,
                 "basis": "binary64 operations of the formulation (addition, multiplication, FMA: one each) per "
                          "grid row, the real reciprocal counted as the one FMA it keeps; all on the FP64 pipe "
-                         "but the explicit row's two additions, which run on the integer pipe (fp64_pipe)",
+                         "but the explicit row's two additions and two inner FMAs, which run on the integer "
+                         "pipe at this size (fp64_pipe)",
                 "ops_per_row": ops,
                 "fp64_pipe": {"ops_per_row": pipe_ops, "achieved": pipe_achieved,
                               "frac": pipe_achieved / peak if peak else None},

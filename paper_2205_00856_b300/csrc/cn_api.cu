@@ -1041,11 +1041,14 @@ cn_status create_engine(Engine* p, const cn_desc* desc, const std::vector<int64_
     c.c1_f = split(c.c1);
     c.gt_f = split(c.gt);
     c.soft_f = split(c.soft_s);
-    // the explicit row's additions on the integer pipe where level 0 fills the GPU (two
-    // or more CTAs of kThreads blocks per SM): the FP64 pipe bounds such steps (N = 2^24:
-    // 1.299 -> 1.260 ms), while a latency-bound small grid only gets longer threads
-    // (n = 4096: 43 -> 46 us)
-    c.sigma_int = p->lv[0].total >= 2 * (int64_t)p->sms * kThreads ? 1 : 0;
+    // the explicit row on the integer pipe where level 0 fills the GPU (two or more CTAs
+    // of kThreads blocks per SM): the FP64 pipe bounds such steps (N = 2^24: 1.299 ->
+    // 1.260 ms with its additions there, 1.226 with its inner FMAs too), while a
+    // latency-bound small grid only gets longer threads (n = 4096: 43 -> 46 us).  A batch
+    // keeps its inner FMAs on the FP64 pipe: its level-0 kernels run four CTAs per SM,
+    // and the integer FMAs cost it 10 % (1.39e10 -> 1.26e10 unknown-steps/s)
+    const bool fills = p->lv[0].total >= 2 * (int64_t)p->sms * kThreads;
+    c.sigma_int = !fills ? 0 : (p->batched ? 1 : 2);
     const double two_pi = 2.0 * 3.14159265358979323846;
     if (use_table && e == cudaSuccess) e = dbg_register(p, nullptr, {});
     if (use_table) {

@@ -1365,9 +1365,10 @@ struct CNParams {
     double two_pi_over_L;
     double cos_a[kMaxCos];
     DFc dx_f, c1_f, gt_f, soft_f;  // the same constants for the double-float kernels
-    int sigma_int;                 // binary64: the explicit row's two additions on the integer pipe
-                                   // (level-0 grids of several CTAs per SM, where the FP64 pipe is the
-                                   // bound; in a latency-bound grid they would lengthen every thread)
+    int sigma_int;                 // binary64, the explicit row on the integer pipe: 1 its two additions,
+                                   // 2 also its two inner FMAs (level-0 grids of several CTAs per SM, where
+                                   // the FP64 pipe is the bound; in a latency-bound grid they would only
+                                   // lengthen every thread)
 };
 
 // Grid coordinates of one system, formed as x_j = x_o + (j - j_o) dx around the
@@ -1507,7 +1508,7 @@ template <> struct CoefGen<df> {
 // explicit matrix, the right-hand side is psi itself, d^ = -i s g~ psi).
 template <int ES>
 __device__ __forceinline__ cx<double> explicit_row(cx<double> pm, cx<double> p0, cx<double> pp, double bt,
-                                                   double sg, bool sig_int) {
+                                                   double sg, int sig_int) {
     static_assert(ES == -1 || ES == 0 || ES == 1, "e s is -1, 0 or 1");
     if constexpr (ES == 0) {
         return mk(d_mul(sg, p0.im), d_mul(-sg, p0.re));
@@ -1515,10 +1516,12 @@ __device__ __forceinline__ cx<double> explicit_row(cx<double> pm, cx<double> p0,
         // the same bits either way: sigma and the inner FMAs feed no recurrence, so where
         // the FP64 pipe bounds the step they run on the integer pipe
         const double eb = ES > 0 ? bt : -bt;
-        if (sig_int) {
+        if (sig_int != 0) {
             double sr = d_add_int(pm.re, pp.re), si = d_add_int(pm.im, pp.im);
             if (ES > 0) { sr = -sr; si = -si; }
-            return mk(fma(eb, p0.re, d_fma_int(sg, p0.im, sr)), fma(eb, p0.im, d_fma_int(-sg, p0.re, si)));
+            if (sig_int == 2)
+                return mk(fma(eb, p0.re, d_fma_int(sg, p0.im, sr)), fma(eb, p0.im, d_fma_int(-sg, p0.re, si)));
+            return mk(fma(eb, p0.re, fma(sg, p0.im, sr)), fma(eb, p0.im, fma(-sg, p0.re, si)));
         }
         double sr = d_add(pm.re, pp.re), si = d_add(pm.im, pp.im);
         if (ES > 0) { sr = -sr; si = -si; }
@@ -1526,7 +1529,7 @@ __device__ __forceinline__ cx<double> explicit_row(cx<double> pm, cx<double> p0,
     }
 }
 template <int ES>
-__device__ __forceinline__ cx<df> explicit_row(cx<df> pm, cx<df> p0, cx<df> pp, df bt, df sg, bool) {
+__device__ __forceinline__ cx<df> explicit_row(cx<df> pm, cx<df> p0, cx<df> pp, df bt, df sg, int) {
     static_assert(ES == -1 || ES == 0 || ES == 1, "e s is -1, 0 or 1");
     if constexpr (ES == 0) {
         return mk(df_mul(sg, p0.im), df_neg(df_mul(sg, p0.re)));
@@ -1571,7 +1574,7 @@ template <class R, int ES> struct CNRowStream {
     CoefGen<R> cg;
     cx<R> pm, p0, pp;  // psi_{i-1}, psi_i, psi_{i+1}: the next row's stencil is already loaded
     R sg, msg;
-    bool sig_int;
+    int sig_int;
     const double2* psi;
     int64_t n, i;
     __device__ __forceinline__ cx<R> ld(int64_t j) const {
@@ -1580,7 +1583,7 @@ template <class R, int ES> struct CNRowStream {
     __device__ __forceinline__ void init(const CNStep& st, const LvlSys& e, const SysGrid& g, int64_t j0) {
         const double E = st.E ? dbg_ld(st.E) : 0.0;
         sg = signed_gt(st, R());
-        sig_int = st.p.sigma_int != 0;
+        sig_int = st.p.sigma_int;
         msg = rneg(sg);  // imaginary part of a~: -s g~
         psi = st.psi + e.row_off;
         n = e.n;
@@ -1934,14 +1937,14 @@ template <class R, int ES> struct CNRowFused {
     CoefGen<R> cg;
     cx<R> pm, p0, pp;  // stencil of the next row to produce (pm = 0 on the joint rows)
     R sg, msg;
-    bool sig_int;
+    int sig_int;
     int k;
     const ST* ys;      // row j of the block at ys[j * kTileStride]: xL at 0, psi at 1..g-1, xR at g, 0 at g+1
     __device__ __forceinline__ void init(const CNStep& st, const LvlSys& e, const SysGrid& g, int64_t J0,
                                          const ST* col) {
         const double E = st.E ? dbg_ld(st.E) : 0.0;
         sg = signed_gt(st, R());
-        sig_int = st.p.sigma_int != 0;
+        sig_int = st.p.sigma_int;
         msg = rneg(sg);
         const typename CoefTab<R>::T* tab =
             st.tab ? static_cast<const typename CoefTab<R>::T*>(st.tab) + e.row_off : nullptr;
